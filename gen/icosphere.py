@@ -1,0 +1,282 @@
+"""Bumped icosphere particles and particle-pair scenes (seeded, synthetic).
+
+The paper's particles are spheres triangulated into |T| triangles whose
+vertices are displaced along the surface normal by a noise function (Sec. 6.1,
+"Experimental setup").  Its noise model is not specified, so these scenes use
+an i.i.d. uniform radial factor per unique vertex, which keeps every mesh
+closed and watertight.
+
+Layout produced for a scene with n particles:
+  verts      float32 [sum_v, 3]  body-frame vertex coordinates, all particles
+  vert_off   int64   [n+1]       vertex range of particle i
+  tris       int32   [sum_t, 3]  vertex indices local to the particle, CCW
+                                 seen from outside (outward normal)
+  tri_off    int64   [n+1]       triangle range of particle i
+  poses      float64 [n, 7]      world pose: translation xyz, quaternion wxyz
+  mass       float64 [n]         (4/3) pi r^3 (unit density)
+  com        float64 [n, 3]      body-frame centre of mass (the origin)
+  pairs      int32   [P, 2]      particle indices (A, B)
+  eps        float64 [P]         epsilon of the pair (both particles)
+"""
+from __future__ import annotations
+
+import dataclasses
+import functools
+import math
+
+import numpy as np
+
+BASE_SEED = 2105124150
+
+
+# ----------------------------------------------------------------------------
+# meshes
+# ----------------------------------------------------------------------------
+def _icosahedron():
+    p = (1.0 + math.sqrt(5.0)) / 2.0
+    v = np.array([
+        [-1, p, 0], [1, p, 0], [-1, -p, 0], [1, -p, 0],
+        [0, -1, p], [0, 1, p], [0, -1, -p], [0, 1, -p],
+        [p, 0, -1], [p, 0, 1], [-p, 0, -1], [-p, 0, 1],
+    ], dtype=np.float64)
+    f = np.array([
+        [0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11],
+        [1, 5, 9], [5, 11, 4], [11, 10, 2], [10, 7, 6], [7, 1, 8],
+        [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9],
+        [4, 9, 5], [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1],
+    ], dtype=np.int64)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return v, f
+
+
+@functools.lru_cache(maxsize=None)
+def icosphere(level: int):
+    """Unit icosphere after `level` midpoint subdivisions: 20*4^level faces.
+
+    Returns (vertices float64 [nv,3] on the unit sphere, faces int32 [nf,3]).
+    Shared edges get one midpoint vertex, so the mesh stays closed.
+    """
+    v, f = _icosahedron()
+    for _ in range(level):
+        e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]], axis=0)
+        key = np.sort(e, axis=1)
+        uniq, inv = np.unique(key[:, 0] * (len(v) + 1) + key[:, 1], return_inverse=True)
+        a = uniq // (len(v) + 1)
+        b = uniq % (len(v) + 1)
+        mid = v[a] + v[b]
+        mid /= np.linalg.norm(mid, axis=1, keepdims=True)
+        nf = len(f)
+        m = inv.reshape(3, nf).T + len(v)          # midpoint ids of edges 01,12,20
+        v = np.concatenate([v, mid], axis=0)
+        f = np.concatenate([
+            np.stack([f[:, 0], m[:, 0], m[:, 2]], 1),
+            np.stack([f[:, 1], m[:, 1], m[:, 0]], 1),
+            np.stack([f[:, 2], m[:, 2], m[:, 1]], 1),
+            np.stack([m[:, 0], m[:, 1], m[:, 2]], 1),
+        ], axis=0)
+    v.setflags(write=False)
+    f = f.astype(np.int32)
+    f.setflags(write=False)
+    return v, f
+
+
+def bumped_icosphere(level: int, radius: float, rng: np.random.Generator, amp: float = 0.05):
+    """Icosphere of `radius` with each unique vertex scaled by U[1-amp, 1+amp]."""
+    v, f = icosphere(level)
+    s = rng.uniform(1.0 - amp, 1.0 + amp, size=len(v)) if amp > 0 else np.ones(len(v))
+    return (v * (radius * s)[:, None]).astype(np.float32), f
+
+
+# ----------------------------------------------------------------------------
+# rigid motions
+# ----------------------------------------------------------------------------
+def random_quaternion(rng: np.random.Generator, n: int | None = None):
+    """Uniform random unit quaternion(s) (w, x, y, z), Shoemake's method."""
+    shape = () if n is None else (n,)
+    u1, u2, u3 = (rng.random(shape) for _ in range(3))
+    a, b = np.sqrt(1.0 - u1), np.sqrt(u1)
+    q = np.stack([b * np.cos(2 * np.pi * u3), a * np.sin(2 * np.pi * u2),
+                  a * np.cos(2 * np.pi * u2), b * np.sin(2 * np.pi * u3)], axis=-1)
+    return q
+
+
+def quat_to_matrix_f64(q):
+    """Rotation matrix of unit quaternion(s) q = (w, x, y, z); float64."""
+    q = np.asarray(q, dtype=np.float64)
+    w, x, y, z = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    R = np.empty(q.shape[:-1] + (3, 3))
+    R[..., 0, 0] = 1 - 2 * (y * y + z * z)
+    R[..., 0, 1] = 2 * (x * y - w * z)
+    R[..., 0, 2] = 2 * (x * z + w * y)
+    R[..., 1, 0] = 2 * (x * y + w * z)
+    R[..., 1, 1] = 1 - 2 * (x * x + z * z)
+    R[..., 1, 2] = 2 * (y * z - w * x)
+    R[..., 2, 0] = 2 * (x * z - w * y)
+    R[..., 2, 1] = 2 * (y * z + w * x)
+    R[..., 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+def support(verts_f32, q, u):
+    """max over vertices of (R(q) v) . u  (float64)."""
+    R = quat_to_matrix_f64(q)
+    return float(np.max(verts_f32.astype(np.float64) @ (R.T @ np.asarray(u, np.float64))))
+
+
+def _unit(rng):
+    v = rng.normal(size=3)
+    return v / np.linalg.norm(v)
+
+
+# ----------------------------------------------------------------------------
+# scenes
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class Scene:
+    verts: np.ndarray
+    vert_off: np.ndarray
+    tris: np.ndarray
+    tri_off: np.ndarray
+    poses: np.ndarray
+    mass: np.ndarray
+    com: np.ndarray
+    radius: np.ndarray
+    pairs: np.ndarray
+    eps: np.ndarray
+    name: str = ""
+
+    @property
+    def n_particles(self):
+        return len(self.vert_off) - 1
+
+    @property
+    def n_pairs(self):
+        return len(self.pairs)
+
+    def particle(self, i):
+        v = self.verts[self.vert_off[i]:self.vert_off[i + 1]]
+        t = self.tris[self.tri_off[i]:self.tri_off[i + 1]]
+        return v, t
+
+    def n_tri(self, i):
+        return int(self.tri_off[i + 1] - self.tri_off[i])
+
+    def subset(self, pair_ids, name=None):
+        """Scene holding only the given pairs (and their particles, renumbered)."""
+        pair_ids = np.asarray(pair_ids, dtype=np.int64)
+        used = np.unique(self.pairs[pair_ids].reshape(-1))
+        remap = -np.ones(self.n_particles, dtype=np.int64)
+        remap[used] = np.arange(len(used))
+        vs, ts, vo, to = [], [], [0], [0]
+        for i in used:
+            v, t = self.particle(i)
+            vs.append(v)
+            ts.append(t)
+            vo.append(vo[-1] + len(v))
+            to.append(to[-1] + len(t))
+        return Scene(np.concatenate(vs), np.array(vo, np.int64), np.concatenate(ts),
+                     np.array(to, np.int64), self.poses[used].copy(), self.mass[used].copy(),
+                     self.com[used].copy(), self.radius[used].copy(),
+                     remap[self.pairs[pair_ids]].astype(np.int32), self.eps[pair_ids].copy(),
+                     name or (self.name + "-subset"))
+
+
+def _assemble(meshes, poses, radius, pairs, eps, name):
+    vs = [m[0] for m in meshes]
+    ts = [m[1] for m in meshes]
+    vo = np.zeros(len(meshes) + 1, np.int64)
+    to = np.zeros(len(meshes) + 1, np.int64)
+    vo[1:] = np.cumsum([len(v) for v in vs])
+    to[1:] = np.cumsum([len(t) for t in ts])
+    radius = np.asarray(radius, np.float64)
+    return Scene(np.ascontiguousarray(np.concatenate(vs), dtype=np.float32), vo,
+                 np.ascontiguousarray(np.concatenate(ts), dtype=np.int32), to,
+                 np.asarray(poses, np.float64), (4.0 / 3.0) * np.pi * radius ** 3,
+                 np.zeros((len(meshes), 3)), radius,
+                 np.asarray(pairs, np.int32).reshape(-1, 2), np.asarray(eps, np.float64), name)
+
+
+def _place_pair(rng, mA, mB, gap, origin):
+    """Pose A at `origin`, B along a random unit u so that the support slab gap
+    between A (extent along u) and B (extent along -u) equals `gap`."""
+    qA, qB = random_quaternion(rng), random_quaternion(rng)
+    u = _unit(rng)
+    hA = support(mA[0], qA, u)
+    hB = support(mB[0], qB, -u)
+    tB = np.asarray(origin) + (hA + hB + gap) * u
+    return np.concatenate([origin, qA]), np.concatenate([tB, qB])
+
+
+def scene_pairs(levels_a, levels_b, radii_a, radii_b, eps, gaps, seed, name, amp=0.05, spread=50.0):
+    """Generic batched scene: pair k uses particles 2k (A) and 2k+1 (B)."""
+    rng = np.random.default_rng([BASE_SEED, seed])
+    meshes, poses, radius, pairs = [], [], [], []
+    for k in range(len(eps)):
+        mA = bumped_icosphere(int(levels_a[k]), float(radii_a[k]), rng, amp)
+        mB = bumped_icosphere(int(levels_b[k]), float(radii_b[k]), rng, amp)
+        origin = rng.uniform(-spread, spread, size=3)
+        pA, pB = _place_pair(rng, mA, mB, float(gaps[k]), origin)
+        meshes += [mA, mB]
+        poses += [pA, pB]
+        radius += [radii_a[k], radii_b[k]]
+        pairs.append((2 * k, 2 * k + 1))
+    return _assemble(meshes, poses, radius, pairs, eps, name)
+
+
+# Gap for the single-pair workload.  For two spheres of radius R at surface
+# gap g (negative: interpenetration), the points of A within 2*eps of B form a
+# cap of half-angle theta with R*theta^2 ~ 2*eps - g, whose area fraction is
+# ~theta^2/4.  A 5% patch therefore needs 2*eps - g ~ 0.2 R; 0.23 R gives 5% on the seeded C1 meshes.
+C1_EPS = 0.02
+C1_GAP = 2 * C1_EPS - 0.23
+
+
+def scene_c1(seed: int = 1):
+    """One pair of bumped subdivision-3 icospheres (1280 triangles), R = 1,
+    eps = 0.02, overlapping so that ~5% of A's triangles are in contact."""
+    return scene_pairs([3], [3], [1.0], [1.0], [C1_EPS], [C1_GAP], seed, "c1-one-pair-1280")
+
+
+def scene_c2(n_pairs: int = 4096, seed: int = 2):
+    """Batched workload: subdivision U{1..5} per particle (80..20480 triangles),
+    radius log-uniform in [0.1, 1], eps = 0.01 min(rA, rB), slab gap
+    U[-0.5 eps, 3 eps]."""
+    rng = np.random.default_rng([BASE_SEED, seed, 7])
+    la = rng.integers(1, 6, size=n_pairs)
+    lb = rng.integers(1, 6, size=n_pairs)
+    ra = np.exp(rng.uniform(np.log(0.1), np.log(1.0), size=n_pairs))
+    rb = np.exp(rng.uniform(np.log(0.1), np.log(1.0), size=n_pairs))
+    eps = 0.01 * np.minimum(ra, rb)
+    gaps = rng.uniform(-0.5, 3.0, size=n_pairs) * eps
+    return scene_pairs(la, lb, ra, rb, eps, gaps, seed, f"c2-batched-{n_pairs}-pairs")
+
+
+def scene_c3(n_pairs: int = 1024, seed: int = 3):
+    """Differentiation workload: subdivision-4 icospheres (5120 triangles),
+    R = 1, eps = 0.02, eps-environments overlapping by 0.3 eps: slab gap 1.7 eps,
+    so every triangle distance is >= 1.7 eps (no intersecting triangles)."""
+    eps = np.full(n_pairs, 0.02)
+    return scene_pairs(np.full(n_pairs, 4), np.full(n_pairs, 4), np.ones(n_pairs), np.ones(n_pairs),
+                       eps, 1.7 * eps, seed, f"c3-grad-{n_pairs}-pairs")
+
+
+def scene_tiny(n_pairs: int = 8, seed: int = 4, levels=(0, 1), amp=0.05):
+    """Small meshes (icosahedron, 80-triangle sphere) for exhaustive checks."""
+    rng = np.random.default_rng([BASE_SEED, seed, 11])
+    la = rng.choice(levels, size=n_pairs)
+    lb = rng.choice(levels, size=n_pairs)
+    ra = rng.uniform(0.5, 1.0, size=n_pairs)
+    rb = rng.uniform(0.5, 1.0, size=n_pairs)
+    eps = 0.02 * np.minimum(ra, rb)
+    gaps = rng.uniform(-2.0, 3.0, size=n_pairs) * eps
+    return scene_pairs(la, lb, ra, rb, eps, gaps, seed, f"tiny-{n_pairs}", amp=amp)
+
+
+def scene_regular_pair(level: int, radius: float, centre_dist: float, qA, qB, eps: float):
+    """Two unbumped icospheres at a given centre distance along +x with given
+    orientations; used for the closed-form mesh-distance checks."""
+    v, f = icosphere(level)
+    m = ((v * radius).astype(np.float32), f)
+    pA = np.concatenate([[0.0, 0.0, 0.0], qA])
+    pB = np.concatenate([[centre_dist, 0.0, 0.0], qB])
+    return _assemble([m, m], [pA, pB], [radius, radius], [(0, 1)], [eps], "regular-pair")

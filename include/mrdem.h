@@ -1,0 +1,266 @@
+/*
+ * mrdem.h -- C ABI of the GB300 multiresolution triangle-mesh contact library.
+ *
+ * Method: Noble & Weinzierl, "A multiresolution Discrete Element Method for
+ * triangulated objects with implicit time stepping" (arXiv 2105.12415).
+ * Rigid particles are closed triangle meshes.  Each particle carries a tree of
+ * surrogate triangles (Sec. 4, Definition "surrogate tree"; Algorithm 7); each
+ * surrogate has a slack delta such that every fine vertex below it lies within
+ * delta of it, which makes it conservative (Definition "conservative").  The
+ * detection (Algorithm 5) walks the two trees of a particle pair top-down:
+ * surrogate pairs whose eps-environments cannot overlap are pruned, the rest
+ * are unfolded, and at the finest level every remaining fine triangle pair is
+ * compared (Algorithm 4: the penalty sweep of Eq. 3/4 with the comparison-based
+ * distance of Sec. 3 as the exact fallback).  A fine triangle pair is a
+ * contact iff its distance d satisfies d <= 2 eps (Definition "contact point":
+ * |n| <= eps with n half the closest segment).  Penalty forces follow Sec. 2.
+ *
+ * Conventions for every call:
+ *   - return value: MRDEM_OK (0) or a negative MRDEM_ERR_* code; nothing
+ *     throws or aborts across this boundary; mrdem_status_string() names it;
+ *   - "device" pointers are CUDA device memory owned by the caller (the
+ *     Python binding allocates them with torch); "host" pointers are ordinary
+ *     host memory owned by the caller;
+ *   - arrays are dense, row-major, little-endian, without padding;
+ *   - a pose is 7 doubles (tx, ty, tz, qw, qx, qy, qz); the quaternion is
+ *     normalised before use; world = R(q) * body + t;
+ *   - stream-ordered calls (detect, forces, grad, triangle_distance) enqueue
+ *     work on the given cudaStream_t (NULL = legacy default stream), never
+ *     synchronise the host and can be captured into a CUDA graph, unless the
+ *     call's comment says otherwise.  Their device-side failures (work-list
+ *     overflow, non-finite input) are latched in the context and reported by
+ *     mrdem_check().
+ */
+#ifndef MRDEM_H_
+#define MRDEM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mrdem_ctx mrdem_ctx;
+typedef struct mrdem_hier mrdem_hier;
+typedef struct CUstream_st* mrdem_stream; /* same type as cudaStream_t */
+
+/* status codes */
+#define MRDEM_OK 0
+#define MRDEM_ERR_INVALID (-1)   /* bad argument: size, index, null pointer, degenerate triangle */
+#define MRDEM_ERR_OOM (-2)       /* host or device allocation failed */
+#define MRDEM_ERR_CUDA (-3)      /* a CUDA runtime call failed (no device, launch error, ...) */
+#define MRDEM_ERR_CAPACITY (-4)  /* a device work list or the contact buffer overflowed */
+#define MRDEM_ERR_NONFINITE (-5) /* a pose or eps was NaN/Inf, or eps <= 0 */
+
+/* arithmetic of the final distance of candidate triangle pairs */
+#define MRDEM_PREC_FP32 0 /* FP32 comparison-based distance; FP64 re-evaluation of pairs
+                             within a margin of 2 eps and of near-parallel edge pairs */
+#define MRDEM_PREC_FP64 1 /* FP64 comparison-based distance for every candidate */
+
+/* indices into the int64 statistics array filled by mrdem_detect */
+#define MRDEM_STAT_LEVELS 8
+#define MRDEM_STAT_TESTS 0       /* [0..7]  surrogate-pair tests at unfold step l (0 = roots) */
+#define MRDEM_STAT_SURVIVORS 8   /* [8..15] of which not pruned */
+#define MRDEM_STAT_TILES 16      /* leaf-pair tiles reaching the finest level */
+#define MRDEM_STAT_FINE_TESTS 17 /* fine triangle-pair sweeps (iterative tests) */
+#define MRDEM_STAT_CANDIDATES 18 /* fine pairs not pruned by the sweep's certificate */
+#define MRDEM_STAT_UNCONVERGED 19 /* candidates whose sweep had not converged (the paper's odot) */
+#define MRDEM_STAT_CONTACTS 20   /* contacts written (or that would have been written) */
+#define MRDEM_STAT_FP64 21       /* candidates re-evaluated in FP64 */
+#define MRDEM_STAT_COUNT 32
+
+typedef struct mrdem_params {
+  int32_t n_iter;   /* penalty-sweep iterations N_iterative (paper: 4) */
+  float rho_reg;    /* alpha_regulariser = rho_reg * s, s = mean squared edge length of the pair */
+  float rho_iter;   /* alpha_iterative   = rho_iter * s */
+  float conv_c;     /* C: converged iff the contact point moved <= C eps in the last iteration */
+  int32_t fanout;   /* N_surrogate: clusters per split (paper: 8) */
+  int32_t leaf_max; /* a node with more fine triangles than this is split (<= 32) */
+  int32_t leaf_min; /* split into fewer than fanout clusters if they would hold fewer */
+  int32_t kmeans_iters;
+  int64_t cap_level;      /* capacity (items) of each per-level work list */
+  int64_t cap_tiles;      /* capacity of the leaf-pair tile list */
+  int64_t cap_candidates; /* capacity of the fine candidate list */
+  int32_t tile_warps;     /* warps per block of the finest-level kernel (autotuned) */
+  int32_t tile_blocks_per_sm;
+  int32_t level_warps;
+  int32_t exact_threads;
+} mrdem_params;
+
+/* Contact output.  All arrays are caller-owned device memory of `capacity`
+ * entries; `count` is one device int64 written by mrdem_detect (it may exceed
+ * capacity, in which case entries beyond capacity were dropped and
+ * mrdem_check reports MRDEM_ERR_CAPACITY).  Entry k is a fine triangle pair
+ * (tri_a of particle A, tri_b of particle B, input numbering) of pair[k] with
+ * distance dist[k] <= 2 eps and closest points point_a/point_b (world frame;
+ * equal when the triangles cross, dist = 0).  Order is unspecified. */
+typedef struct mrdem_contacts {
+  int64_t capacity;
+  int64_t* count;
+  int32_t* pair;
+  int32_t* tri_a;
+  int32_t* tri_b;
+  double* dist;
+  double* point_a; /* [capacity * 3] */
+  double* point_b; /* [capacity * 3] */
+} mrdem_contacts;
+
+/* Host-side description of a built hierarchy (see mrdem_hier_export). */
+typedef struct mrdem_hier_info {
+  int32_t n_particles;
+  int32_t max_depth; /* largest number of surrogate levels of any particle */
+  int64_t n_nodes;
+  int64_t n_tri;     /* fine triangles (input count) */
+  int64_t n_tri_pad; /* stored slots: leaves are padded to a multiple of 4 */
+  int64_t n_verts;
+} mrdem_hier_info;
+
+/* Fill *p with the defaults (paper constants where it gives them:
+ * N_iterative = 4, C = 1, N_surrogate = 8). */
+void mrdem_default_params(mrdem_params* p);
+
+/* Text for a status code (static storage). */
+const char* mrdem_status_string(int status);
+
+/* Create a context on CUDA device `device` with parameters *p (NULL =
+ * defaults).  Allocates the device work lists (capacities from *p).
+ * Errors: INVALID (bad parameter), CUDA (no such device), OOM. */
+int mrdem_create(mrdem_ctx** out, int device, const mrdem_params* p);
+int mrdem_destroy(mrdem_ctx* ctx);
+int mrdem_get_params(const mrdem_ctx* ctx, mrdem_params* out);
+/* Change the sweep constants / launch shapes (not the capacities) of a context. */
+int mrdem_set_params(mrdem_ctx* ctx, const mrdem_params* p);
+/* Reallocate the work lists (0 keeps a capacity).  Synchronises the device. */
+int mrdem_reserve(mrdem_ctx* ctx, int64_t cap_level, int64_t cap_tiles, int64_t cap_candidates);
+
+/* Build the surrogate trees of n_particles meshes (Sec. 4, Algorithm 7,
+ * Appendix A) on the host.  Host inputs: vert_off [n+1] and tri_off [n+1]
+ * (int64 prefix offsets), verts [vert_off[n] * 3] float32 body-frame
+ * coordinates, tris [tri_off[n] * 3] int32 vertex indices local to each
+ * particle, counter-clockwise seen from outside.  Each node of a tree holds one
+ * surrogate triangle; a node with more than leaf_max fine triangles is split by
+ * balanced k-means of the triangle centroids into fanout clusters (fewer if
+ * clusters would be smaller than leaf_min); leaves hold their fine triangles.
+ * Each surrogate's slack delta is the largest FP64 distance from any fine
+ * vertex below it to the (float32-rounded) surrogate triangle, rounded up to
+ * float32 (the smallest eps that keeps it conservative, Algorithm 7).
+ * Deterministic.  `params` supplies fanout/leaf_max/leaf_min/kmeans_iters
+ * (NULL = defaults).  *out owns host arrays only (no device memory).
+ * Errors: INVALID (index out of range, degenerate triangle, empty particle),
+ * OOM. */
+int mrdem_build_hierarchy_host(const mrdem_params* params, int32_t n_particles,
+                               const int64_t* vert_off, const float* verts,
+                               const int64_t* tri_off, const int32_t* tris, mrdem_hier** out);
+/* Copy a host-built hierarchy to ctx's device (synchronous). */
+int mrdem_hier_upload(mrdem_ctx* ctx, mrdem_hier* hier);
+/* mrdem_build_hierarchy_host followed by mrdem_hier_upload. */
+int mrdem_build_hierarchy(mrdem_ctx* ctx, int32_t n_particles, const int64_t* vert_off,
+                          const float* verts, const int64_t* tri_off, const int32_t* tris,
+                          mrdem_hier** out);
+int mrdem_hier_destroy(mrdem_hier* hier);
+int mrdem_hier_get_info(const mrdem_hier* hier, mrdem_hier_info* out);
+/* Copy the host arrays of a hierarchy into caller host buffers (any may be
+ * NULL), sized from mrdem_hier_info:
+ *   node_tri    float [n_nodes*9]  surrogate triangle (body frame)
+ *   node_delta  float [n_nodes]    slack delta
+ *   node_child  int32 [n_nodes*2]  (begin, count): count > 0: child nodes
+ *                                  [begin, begin+count); count < 0: leaf with
+ *                                  -count fine slots [begin, begin-count)
+ *   node_level  int32 [n_nodes]    1 = root
+ *   root        int32 [n_particles]
+ *   slot_tri    int32 [n_tri_pad]  input triangle index (local) of each fine
+ *                                  slot, -1 for padding
+ *   slot_particle int32 [n_tri_pad] particle of each slot, -1 for padding */
+int mrdem_hier_export(const mrdem_hier* hier, float* node_tri, float* node_delta,
+                      int32_t* node_child, int32_t* node_level, int32_t* root,
+                      int32_t* slot_tri, int32_t* slot_particle);
+
+/* Multiresolution contact detection (Algorithm 5 with the hybrid test of
+ * Algorithm 4) for n_pairs particle pairs.  Device inputs: pair_ab [n_pairs*2]
+ * int32 particle indices of hier (A, B; A != B not required), pair_eps
+ * [n_pairs] eps of each pair (both particles), poses [n_particles*7].
+ * `precision` is MRDEM_PREC_FP32 or MRDEM_PREC_FP64.  Writes the contact set
+ * of every pair into *out (count overwritten).  stats: NULL or device int64
+ * [MRDEM_STAT_COUNT], overwritten.  The result equals the brute-force contact
+ * set over all fine triangle pairs (Lemma 1).  Errors returned directly:
+ * INVALID (sizes, null pointers, hier not uploaded to ctx), CUDA. */
+int mrdem_detect(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
+                 const double* pair_eps, const double* poses, int32_t precision,
+                 const mrdem_contacts* out, int64_t* stats, mrdem_stream stream);
+
+/* Synchronise `stream` and report the latched device-side status of ctx since
+ * the last check: CAPACITY (a work list or a contact buffer overflowed; the
+ * required sizes go to required[0..3] = level list, tiles, candidates,
+ * contacts when required != NULL), NONFINITE, or OK.  Clears the latch. */
+int mrdem_check(mrdem_ctx* ctx, mrdem_stream stream, int64_t* required);
+
+/* Penalty forces of a contact set (Sec. 2, F(c)):
+ *   F = K_s sqrt(mu) (1 - d/(2 eps)) u on A and -F on B,
+ *   mu = 1/(1/M_A + 1/M_B), u = (point_a - point_b)/d (at d = 0: minus the
+ *   outward unit normal of A's triangle), applied at the contact point
+ *   (point_a + point_b)/2; torques about each world centre of mass.
+ * Device inputs: the detect inputs, mass [n_particles], com [n_particles*3]
+ * (body frame).  Device outputs (accumulated, caller zeroes):
+ * force_torque [n_particles*6] (force xyz, torque xyz, world frame) and
+ * energy [1] += sum K_s sqrt(mu) eps (1 - d/(2 eps))^2 (whose negative
+ * d-derivative is |F|).  Either output may be NULL. */
+int mrdem_contact_forces(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
+                         const int32_t* pair_ab, const double* pair_eps, const double* poses,
+                         const mrdem_contacts* contacts, const double* mass, const double* com,
+                         double k_s, double* force_torque, double* energy, mrdem_stream stream);
+
+/* Adjoint of the contact energy E = sum_c e(d_c) (the energy of
+ * mrdem_contact_forces), scaled by dE_scale (the upstream gradient).  The
+ * closest points of each contact are recomputed in FP64 from the triangles;
+ * nothing per pair is stored between detect and this call.  Outputs
+ * (accumulated, caller zeroes; each may be NULL):
+ *   dE_dverts float [n_verts*3]  gradient w.r.t. body-frame vertex positions
+ *                                (vertex numbering of the hierarchy's input)
+ *   dE_dpose  double [n_particles*6] gradient w.r.t. a world translation and
+ *                                a world rotation increment theta about the
+ *                                particle origin (R <- exp([theta]x) R)
+ *   jac       double [n_pairs*144] per pair, the Gauss-Newton block
+ *                                sum_c e''(d) J J^T of the 12 pose unknowns
+ *                                (t_A, theta_A, t_B, theta_B), barycentrics
+ *                                frozen, e'' = K_s sqrt(mu)/(2 eps).
+ * The paper's implicit step uses Picard iterations (Algorithm 3); these
+ * derivatives are what a Newton step needs instead. */
+int mrdem_contact_grad(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
+                       const int32_t* pair_ab, const double* pair_eps, const double* poses,
+                       const mrdem_contacts* contacts, const double* mass, double k_s,
+                       double dE_scale, float* dE_dverts, double* dE_dpose, double* jac,
+                       mrdem_stream stream);
+
+/* Plain GPU form (reported baseline): the contact set by FP64 comparison-based
+ * distance over ALL fine triangle pairs of each pair (Algorithm 2), no
+ * hierarchy, one kernel launch per particle pair.  Same inputs and outputs as
+ * mrdem_detect.  Copies pair_ab to the host and synchronises `stream` (not
+ * capturable). */
+int mrdem_detect_plain_fp64(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
+                            const int32_t* pair_ab, const double* pair_eps, const double* poses,
+                            const mrdem_contacts* out, mrdem_stream stream);
+
+/* Triangle-pair kernel entry (Sec. 3): for n explicit pairs of triangles
+ * P[k], Q[k] (device double [n*9] each, vertices v0 v1 v2, any common frame)
+ * and eps[k]:
+ *   dist/point_a/point_b/feature: exact distance by the comparison-based
+ *     method in the requested precision (FP32: the float-rounded triangles
+ *     relative to P's first vertex; FP64: as given).  feature codes: k (0..2)
+ *     vertex k of P vs Q; 3+k vertex k of Q vs P; 6+3i+j edge i of P vs edge j
+ *     of Q (edge i joins vertex i and i+1 mod 3); 100+i edge i of P crosses Q;
+ *     103+j edge j of Q crosses P.
+ *   sweep_x [n*4], sweep_gap [n], sweep_conv [n]: the FP32 penalty sweep of
+ *     Eq. 3/4 (ctx's constants) on the float-rounded triangles: final
+ *     barycentric unknowns (a1, b1, a2, b2), the certified lower bound of the
+ *     distance along the final iterate's direction (-inf if undefined), and
+ *     whether the contact point moved <= C eps in the last iteration.
+ * Any output may be NULL. */
+int mrdem_triangle_distance(mrdem_ctx* ctx, int64_t n, const double* P, const double* Q,
+                            const double* eps, int32_t precision, double* dist, double* point_a,
+                            double* point_b, int32_t* feature, float* sweep_x, float* sweep_gap,
+                            int32_t* sweep_conv, mrdem_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRDEM_H_ */
