@@ -1,0 +1,450 @@
+"""Benchmark: batched multiresolution contact detection on one GB300.
+
+Workload (one "step" = one pass of the whole hot path over the batch):
+4096 particle pairs of bumped icospheres (subdivision 1..5, 80..20480
+triangles, radius log-uniform in [0.1, 1], eps = 0.01 min radius, slab gap
+U[-0.5 eps, 3 eps]); hierarchies built once on the host (untimed
+preprocessing); per step: pair setup + root test, the per-level surrogate
+unfolding, the finest-level tile sweep, exact refinement (FP32 bulk with FP64
+final values), penalty forces and energy, and the adjoint (vertex and pose
+gradients plus the 12x12 Gauss-Newton blocks).
+
+Metric: particle-pair detections per second (whole job), with the device
+timed by CUDA events around CUDA-graph replays of the step.  L2 is flushed
+between timed steps (a 256 MiB write).  Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Floating-point operations of one fine triangle-pair test in the finest-level
+# kernel (penalty sweep with 4 iterations, convergence check, certificate),
+# counted from its source as FADD + FMUL + 2 FFMA + MUFU; see the design doc.
+FLOPS_PER_FINE_TEST = 455
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--pairs", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-baselines", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def _dist_init(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        import statistics
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    for f in ("mrdem_detect.cu", "mrdem_geometry.cuh"):
+        with open(os.path.join(ROOT, "paper_2105_12415_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_launch():
+    """DRAM bytes per k_tile launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "k_tile_c2_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except OSError:
+        return None
+    if d.get("source_hash") != _source_hash():
+        return None
+    return d.get("dram_bytes_per_full_launch")
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_baseline(scene, budget_s, n_threads=0):
+    """The FP64 oracle (brute force over all fine triangle pairs) on a bounded
+    sample of the same workload: pairs 0, 8, 16, ... (the fixed subset of
+    pair ids = 0 mod 8) until about budget_s seconds of work."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    ntri = np.diff(scene.tri_off)
+    ids = np.arange(0, scene.n_pairs, 8)
+    work = ntri[scene.pairs[ids, 0]] * ntri[scene.pairs[ids, 1]]
+    # calibrate on the first pair, then take pairs until the budget is spent
+    t0 = time.perf_counter()
+    oracle.detect(scene.subset([int(ids[0])]), n_threads=n_threads)
+    rate = work[0] / max(time.perf_counter() - t0, 1e-6)
+    take = [int(ids[0])]
+    est = 0.0
+    for i, w in zip(ids[1:], work[1:]):
+        if est + w / rate > budget_s:
+            break
+        take.append(int(i))
+        est += w / rate
+    sub = scene.subset(take[1:] if len(take) > 1 else take)
+    t0 = time.perf_counter()
+    oracle.detect(sub, n_threads=n_threads)
+    dt = time.perf_counter() - t0
+    cores = n_threads if n_threads > 0 else (os.cpu_count() or 1)
+    nt = np.diff(sub.tri_off)
+    tri_pairs = int((nt[sub.pairs[:, 0]].astype(np.int64) * nt[sub.pairs[:, 1]]).sum())
+    return {"value": sub.n_pairs / dt, "unit": "particle-pair detections/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{sub.n_pairs} pairs of the pair-id = 0 mod 8 subset ({tri_pairs} "
+                      f"triangle pairs), FP64 brute force, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores (the reference arm)."""
+    rank, world, _ = _dist_init(args.gpus)
+    if rank != 0:
+        return
+    from gen import scene_c2
+    scene = scene_c2(args.pairs)
+    per_step = []
+    last = None
+    for k in range(args.warmup + args.steps):
+        budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+        r = cpu_oracle_baseline(scene, budget)
+        if k >= args.warmup:
+            per_step.append(r["value"])
+        last = r
+    v = sum(per_step) / len(per_step)
+    line = {"impl": "reference", "metric": "particle-pair detections/s", "value": v,
+            "unit": "particle-pair detections/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"c2-batched-{args.pairs}-pairs (bounded sample per step)",
+                       "pairs": args.pairs},
+            "cpu_baseline": {"value": v, "unit": "particle-pair detections/s",
+                             "cores": last["cores"], "kind": "oracle", "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "particle-pair detections/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    rank, world, local = _dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2105_12415_gb300 as m
+    from gen import scene_c2
+
+    if rank == 0:
+        m.build()
+    _barrier(world)
+    m.load()
+
+    t_prep = time.perf_counter()
+    scene = scene_c2(args.pairs)
+    ctx = m.Context(local)
+    hier = m.Hierarchy.from_scene(ctx, scene)
+    info = hier.info()
+    prob = m.ContactProblem.from_scene(ctx, hier, scene, dev, precision=args.precision)
+    prep_s = time.perf_counter() - t_prep
+
+    stats = torch.zeros(m._lib.MRDEM_STAT_COUNT, dtype=torch.int64, device=dev)
+    ft = torch.zeros((scene.n_particles, 6), dtype=torch.float64, device=dev)
+    energy = torch.zeros(1, dtype=torch.float64, device=dev)
+    P = scene.n_pairs
+    gv = torch.zeros((info["n_verts"], 3), dtype=torch.float32, device=dev)
+    gp = torch.zeros((scene.n_particles, 6), dtype=torch.float64, device=dev)
+    jac = torch.zeros((P, 12, 12), dtype=torch.float64, device=dev)
+    lib = m.load()
+    import ctypes as C
+    from paper_2105_12415_gb300.api import _p, _stream
+
+    # warm-up through the checked path (grows the work lists once if needed)
+    for _ in range(max(1, args.warmup)):
+        prob.detect(stats=stats)
+    contacts = prob.contacts
+
+    def step():
+        s = _stream(None)
+        cs = contacts.struct()
+        m._lib.check(lib.mrdem_detect(ctx.handle, hier.handle, P, _p(prob.pairs), _p(prob.eps),
+                                      _p(prob.poses), m.api.PRECISION[args.precision],
+                                      C.byref(cs), _p(stats), s), "detect")
+        ft.zero_()
+        energy.zero_()
+        gv.zero_()
+        gp.zero_()
+        jac.zero_()
+        m._lib.check(lib.mrdem_contact_forces(ctx.handle, hier.handle, P, _p(prob.pairs),
+                                              _p(prob.eps), _p(prob.poses), C.byref(cs),
+                                              _p(prob.mass), _p(prob.com), 1000.0, _p(ft),
+                                              _p(energy), s), "forces")
+        m._lib.check(lib.mrdem_contact_grad(ctx.handle, hier.handle, P, _p(prob.pairs),
+                                            _p(prob.eps), _p(prob.poses), C.byref(cs),
+                                            _p(prob.mass), 1000.0, 1.0, _p(gv), _p(gp), _p(jac),
+                                            s), "grad")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    m._lib.check(lib.mrdem_check(ctx.handle, None, None), "warm-up check")
+
+    # capture one step in a CUDA graph
+    g = torch.cuda.CUDAGraph()
+    cap_stream = torch.cuda.Stream()
+    cap_stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap_stream):
+        step()
+    torch.cuda.current_stream().wait_stream(cap_stream)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        step()
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        g.replay()
+    torch.cuda.synchronize()
+
+    # ---- timed region: graph replays, events per step, L2 flushed between
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    _barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record()
+            g.replay()
+            ev[k][1].record()
+        torch.cuda.synchronize()
+    _barrier(world)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    m._lib.check(lib.mrdem_check(ctx.handle, None, None), "timed-region check")
+    ms_max = _max_over_ranks(ms, world, dev)
+    value = args.steps * P * world / (ms_max * 1e-3)
+    st = stats.cpu().numpy()
+    n_contacts = int(contacts.count.item())
+    launches_per_step = 1 + max(0, info["max_depth"] - 1) + 4
+
+    # ---- per-kernel timing (same steps, outside the graph, events per kernel)
+    ctx.profile(True)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        step()
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    tile_ms, tile_n = prof.get("k_tile", (float("nan"), 1))
+    tile_avg_s = tile_ms / tile_n * 1e-3
+    fine_tests = int(st[m._lib.MRDEM_STAT_FINE_TESTS])
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = fine_tests * FLOPS_PER_FINE_TEST / tile_avg_s / 1e12
+    traffic = _traffic_per_launch()
+    total_prof = sum(v[0] for v in prof.values())
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                   "share": v[0] / total_prof} for k, v in prof.items()}
+
+    # ---- end to end through the public API (host inputs, host results)
+    e2e = None
+    if not args.no_e2e:
+        h_poses = torch.as_tensor(scene.poses, dtype=torch.float64).pin_memory()
+        h_pairs = torch.as_tensor(scene.pairs, dtype=torch.int32).pin_memory()
+        h_eps = torch.as_tensor(scene.eps, dtype=torch.float64).pin_memory()
+        h_ft = torch.empty((scene.n_particles, 6), dtype=torch.float64).pin_memory()
+        h_gp = torch.empty((scene.n_particles, 6), dtype=torch.float64).pin_memory()
+        h_e = torch.empty(1, dtype=torch.float64).pin_memory()
+        h_n = torch.empty(1, dtype=torch.int64).pin_memory()
+        e_ms = 0.0
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            prob.poses.copy_(h_poses, non_blocking=True)
+            prob.pairs.copy_(h_pairs, non_blocking=True)
+            prob.eps.copy_(h_eps, non_blocking=True)
+            prob.detect(stats=stats)            # checked call: syncs and reads the status
+            f_, e_ = prob.forces()
+            _, gp_, _ = prob.grad(want_jac=True)
+            h_ft.copy_(f_, non_blocking=True)
+            h_gp.copy_(gp_, non_blocking=True)
+            h_e.copy_(e_, non_blocking=True)
+            h_n.copy_(prob.contacts.count, non_blocking=True)
+            b.record()
+            b.synchronize()
+            e_ms += a.elapsed_time(b)
+        e_ms = _max_over_ranks(e_ms, world, dev)
+        h2d = h_poses.numel() * 8 + h_pairs.numel() * 4 + h_eps.numel() * 8
+        d2h = h_ft.numel() * 8 + h_gp.numel() * 8 + 8 + 8
+        e2e = {"value": args.steps * P * world / (e_ms * 1e-3), "unit": "particle-pair detections/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    plain = cpu = None
+    if rank == 0 and not args.no_baselines:
+        # plain GPU form on a sample: every 256th pair, one launch per pair
+        ids = np.arange(0, P, 256)
+        pairs_s = prob.pairs[torch.as_tensor(ids, device=dev)].contiguous()
+        eps_s = prob.eps[torch.as_tensor(ids, device=dev)].contiguous()
+        m.detect_plain_fp64(ctx, hier, pairs_s, eps_s, prob.poses)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        m.detect_plain_fp64(ctx, hier, pairs_s, eps_s, prob.poses)
+        b.record()
+        b.synchronize()
+        pms = a.elapsed_time(b)
+        plain = {"value": len(ids) / (pms * 1e-3), "unit": "particle-pair detections/s",
+                 "sample": f"{len(ids)} pairs (ids = 0 mod 256), FP64 comparison-based over all "
+                           f"fine triangle pairs, one launch per pair",
+                 "ms": pms, "speedup_of_ours": value / world / (len(ids) / (pms * 1e-3))}
+        cpu = cpu_oracle_baseline(scene, args.cpu_budget_s)
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "particle-pair detections/s", "value": value,
+        "unit": "particle-pair detections/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": f"c2-batched-{P}-pairs", "pairs": P,
+                   "particles": scene.n_particles, "fine_triangles": int(info["n_tri"]),
+                   "max_depth": info["max_depth"], "precision": args.precision,
+                   "replicas": world, "l2": "flushed between steps (256 MiB write)",
+                   "step": "detect + forces + adjoint (verts, poses, 12x12 blocks)",
+                   "graph": "one CUDA graph per step", "prep_s": round(prep_s, 1)},
+        "roofline": {"bound": "alu", "kernel": "k_tile", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": traffic,
+                     "per_launch": {"fine_tests": fine_tests, "flops_per_test": FLOPS_PER_FINE_TEST,
+                                    "avg_ms": tile_avg_s * 1e3}},
+        "clocks": clk.summary(),
+        "gpu_launches": launches_per_step * args.steps,
+        "kernels": kernels,
+        "stats": {"tests_per_level": [int(x) for x in st[0:6]],
+                  "survivors_per_level": [int(x) for x in st[8:14]],
+                  "fine_tests": fine_tests, "candidates": int(st[18]),
+                  "unconverged": int(st[19]), "contacts": n_contacts, "fp64_refinements": int(st[21]),
+                  "fine_tests_per_s": fine_tests * args.steps * world / (ms_max * 1e-3),
+                  "brute_force_pairs_per_s": float(
+                      (np.diff(scene.tri_off)[scene.pairs[:, 0]] *
+                       np.diff(scene.tri_off)[scene.pairs[:, 1]]).sum()) * args.steps * world / (ms_max * 1e-3)},
+        "e2e": e2e,
+        "plain_fp64_gpu": plain,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -260,6 +260,16 @@ int mrdem_triangle_distance(mrdem_ctx* ctx, int64_t n, const double* P, const do
                             double* point_b, int32_t* feature, float* sweep_x, float* sweep_gap,
                             int32_t* sweep_conv, mrdem_stream stream);
 
+/* Kernel timing for benchmarks (not part of the method).  While enabled, the
+ * context records a CUDA event pair on the launch stream around every kernel
+ * it launches (do not enable it during stream capture).  mrdem_profile_read
+ * synchronises the device, writes up to n_max entries (kernel name in static
+ * storage, total milliseconds, launch count) accumulated since the previous
+ * read, sets *n_out and clears the totals. */
+int mrdem_profile(mrdem_ctx* ctx, int32_t enable);
+int mrdem_profile_read(mrdem_ctx* ctx, int32_t n_max, const char** names, double* ms,
+                       int64_t* launches, int32_t* n_out);
+
 #ifdef __cplusplus
 }
 #endif

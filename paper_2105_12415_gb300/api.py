@@ -1,0 +1,391 @@
+"""PyTorch-facing wrappers over the C ABI (memory, streams, autograd).
+
+Every step of the detection, the forces and the adjoint runs in libmrdem's
+CUDA kernels; this module only allocates torch tensors, passes pointers and
+the current CUDA stream, and grows buffers when the library reports that a
+work list overflowed.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+PRECISION = {"fp32": L.MRDEM_PREC_FP32, "fp64": L.MRDEM_PREC_FP64}
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a):
+    return C.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _need(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+class Context:
+    """A library context on one CUDA device (owns the device work lists)."""
+
+    def __init__(self, device: int = 0, params: L.mrdem_params | None = None, **overrides):
+        lib = L.load()
+        p = params if params is not None else L.default_params()
+        for k, v in overrides.items():
+            setattr(p, k, v)
+        h = C.c_void_p()
+        L.check(lib.mrdem_create(C.byref(h), int(device), C.byref(p)), "mrdem_create")
+        self.handle = h
+        self.device = int(device)
+
+    @property
+    def params(self) -> L.mrdem_params:
+        p = L.mrdem_params()
+        L.check(L.load().mrdem_get_params(self.handle, C.byref(p)), "mrdem_get_params")
+        return p
+
+    def set_params(self, **kw):
+        p = self.params
+        for k, v in kw.items():
+            setattr(p, k, v)
+        L.check(L.load().mrdem_set_params(self.handle, C.byref(p)), "mrdem_set_params")
+
+    def reserve(self, cap_level=0, cap_tiles=0, cap_candidates=0):
+        L.check(L.load().mrdem_reserve(self.handle, int(cap_level), int(cap_tiles),
+                                       int(cap_candidates)), "mrdem_reserve")
+
+    def profile(self, enable: bool):
+        L.check(L.load().mrdem_profile(self.handle, int(bool(enable))), "mrdem_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since the previous read."""
+        n_max = 16
+        names = (C.c_char_p * n_max)()
+        ms = np.zeros(n_max)
+        cnt = np.zeros(n_max, np.int64)
+        n = C.c_int32()
+        L.check(L.load().mrdem_profile_read(self.handle, n_max, names, _np_ptr(ms), _np_ptr(cnt),
+                                            C.byref(n)), "mrdem_profile_read")
+        return {names[i].decode(): (float(ms[i]), int(cnt[i])) for i in range(n.value)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.load().mrdem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hierarchy:
+    """Surrogate trees of a set of particle meshes (host arrays, optionally on a device)."""
+
+    def __init__(self, handle, keep=None):
+        self.handle = handle
+        self._keep = keep
+
+    @staticmethod
+    def _arrays(vert_off, verts, tri_off, tris):
+        vo = np.ascontiguousarray(vert_off, np.int64)
+        v = np.ascontiguousarray(verts, np.float32)
+        to = np.ascontiguousarray(tri_off, np.int64)
+        t = np.ascontiguousarray(tris, np.int32)
+        return vo, v, to, t
+
+    @classmethod
+    def build_host(cls, vert_off, verts, tri_off, tris, params: L.mrdem_params | None = None):
+        vo, v, to, t = cls._arrays(vert_off, verts, tri_off, tris)
+        h = C.c_void_p()
+        p = params if params is not None else L.default_params()
+        L.check(L.load().mrdem_build_hierarchy_host(C.byref(p), len(vo) - 1, _np_ptr(vo), _np_ptr(v),
+                                                   _np_ptr(to), _np_ptr(t), C.byref(h)),
+                "mrdem_build_hierarchy_host")
+        return cls(h)
+
+    @classmethod
+    def build(cls, ctx: Context, vert_off, verts, tri_off, tris):
+        vo, v, to, t = cls._arrays(vert_off, verts, tri_off, tris)
+        h = C.c_void_p()
+        L.check(L.load().mrdem_build_hierarchy(ctx.handle, len(vo) - 1, _np_ptr(vo), _np_ptr(v),
+                                              _np_ptr(to), _np_ptr(t), C.byref(h)),
+                "mrdem_build_hierarchy")
+        return cls(h, keep=ctx)
+
+    @classmethod
+    def from_scene(cls, ctx: Context | None, scene, params=None):
+        if ctx is None:
+            return cls.build_host(scene.vert_off, scene.verts, scene.tri_off, scene.tris, params)
+        return cls.build(ctx, scene.vert_off, scene.verts, scene.tri_off, scene.tris)
+
+    def upload(self, ctx: Context):
+        L.check(L.load().mrdem_hier_upload(ctx.handle, self.handle), "mrdem_hier_upload")
+        self._keep = ctx
+
+    def info(self) -> dict:
+        i = L.mrdem_hier_info()
+        L.check(L.load().mrdem_hier_get_info(self.handle, C.byref(i)), "mrdem_hier_get_info")
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def export(self) -> dict:
+        i = self.info()
+        nn, ns, n = i["n_nodes"], i["n_tri_pad"], i["n_particles"]
+        out = dict(node_tri=np.empty((nn, 9), np.float32), node_delta=np.empty(nn, np.float32),
+                   node_child=np.empty((nn, 2), np.int32), node_level=np.empty(nn, np.int32),
+                   root=np.empty(n, np.int32), slot_tri=np.empty(ns, np.int32),
+                   slot_particle=np.empty(ns, np.int32))
+        L.check(L.load().mrdem_hier_export(self.handle, *[_np_ptr(out[k]) for k in (
+            "node_tri", "node_delta", "node_child", "node_level", "root", "slot_tri",
+            "slot_particle")]), "mrdem_hier_export")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.load().mrdem_hier_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Contacts:
+    """Caller-owned contact buffers on the device."""
+
+    def __init__(self, capacity: int, device):
+        self.device = torch.device(device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.resize(capacity)
+
+    def resize(self, capacity: int):
+        capacity = max(int(capacity), 1)
+        d = self.device
+        self.capacity = capacity
+        self.pair = torch.empty(capacity, dtype=torch.int32, device=d)
+        self.tri_a = torch.empty(capacity, dtype=torch.int32, device=d)
+        self.tri_b = torch.empty(capacity, dtype=torch.int32, device=d)
+        self.dist = torch.empty(capacity, dtype=torch.float64, device=d)
+        self.point_a = torch.empty((capacity, 3), dtype=torch.float64, device=d)
+        self.point_b = torch.empty((capacity, 3), dtype=torch.float64, device=d)
+
+    def struct(self) -> L.mrdem_contacts:
+        return L.mrdem_contacts(self.capacity, self.count.data_ptr(), self.pair.data_ptr(),
+                                self.tri_a.data_ptr(), self.tri_b.data_ptr(), self.dist.data_ptr(),
+                                self.point_a.data_ptr(), self.point_b.data_ptr())
+
+    def n(self) -> int:
+        return min(int(self.count.item()), self.capacity)
+
+    def to_numpy(self, sort=True) -> dict:
+        n = self.n()
+        out = dict(pair=self.pair[:n].cpu().numpy(), ta=self.tri_a[:n].cpu().numpy(),
+                   tb=self.tri_b[:n].cpu().numpy(), d=self.dist[:n].cpu().numpy(),
+                   pa=self.point_a[:n].cpu().numpy(), pb=self.point_b[:n].cpu().numpy())
+        if sort:
+            o = np.lexsort((out["tb"], out["ta"], out["pair"]))
+            out = {k: v[o] for k, v in out.items()}
+        return out
+
+
+def _pair_args(hier, pairs, eps, poses, n_particles):
+    P = pairs.shape[0]
+    _need(pairs, torch.int32, (P, 2), "pairs")
+    _need(eps, torch.float64, (P,), "eps")
+    _need(poses, torch.float64, (n_particles, 7), "poses")
+    return P
+
+
+def detect(ctx: Context, hier: Hierarchy, pairs, eps, poses, precision="fp32", contacts=None,
+           stats=None, check=True, stream=None, max_retries=4):
+    """Contact set of every pair (Algorithm 5).  With check=True the call
+    synchronises, grows overflowing buffers and repeats (so it is not
+    capturable); with check=False it only enqueues work."""
+    info = hier.info()
+    P = _pair_args(hier, pairs, eps, poses, info["n_particles"])
+    if contacts is None:
+        contacts = Contacts(max(1024, 64 * P), pairs.device)
+    if stats is None:
+        stats = torch.zeros(L.MRDEM_STAT_COUNT, dtype=torch.int64, device=pairs.device)
+    lib = L.load()
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    for _ in range(max_retries + 1):
+        cs = contacts.struct()
+        L.check(lib.mrdem_detect(ctx.handle, hier.handle, P, _p(pairs), _p(eps), _p(poses), prec,
+                                 C.byref(cs), _p(stats), _stream(stream)), "mrdem_detect")
+        if not check:
+            return contacts, stats
+        req = np.zeros(4, np.int64)
+        st = lib.mrdem_check(ctx.handle, _stream(stream), _np_ptr(req))
+        if st == L.MRDEM_OK:
+            return contacts, stats
+        if st != L.MRDEM_ERR_CAPACITY:
+            L.check(st, "mrdem_detect")
+        prm = ctx.params
+        grow = lambda need, cap: int(need * 1.25) + 1024 if need > cap else 0  # noqa: E731
+        lv, ti, ca = grow(req[0], prm.cap_level), grow(req[1], prm.cap_tiles), grow(req[2], prm.cap_candidates)
+        if lv or ti or ca:
+            ctx.reserve(lv, ti, ca)
+        if req[3] > contacts.capacity:
+            contacts.resize(int(req[3] * 1.25) + 1024)
+    raise L.MrdemError(L.MRDEM_ERR_CAPACITY, "mrdem_detect (retries exhausted)")
+
+
+def detect_plain_fp64(ctx, hier, pairs, eps, poses, contacts=None, stream=None):
+    """The plain GPU form: FP64 brute force, one launch per pair (baseline)."""
+    info = hier.info()
+    P = _pair_args(hier, pairs, eps, poses, info["n_particles"])
+    if contacts is None:
+        contacts = Contacts(max(1024, 64 * P), pairs.device)
+    lib = L.load()
+    for _ in range(4):
+        cs = contacts.struct()
+        L.check(lib.mrdem_detect_plain_fp64(ctx.handle, hier.handle, P, _p(pairs), _p(eps),
+                                            _p(poses), C.byref(cs), _stream(stream)),
+                "mrdem_detect_plain_fp64")
+        req = np.zeros(4, np.int64)
+        st = lib.mrdem_check(ctx.handle, _stream(stream), _np_ptr(req))
+        if st == L.MRDEM_OK:
+            return contacts
+        if st != L.MRDEM_ERR_CAPACITY:
+            L.check(st, "mrdem_detect_plain_fp64")
+        contacts.resize(int(req[3] * 1.25) + 1024)
+    raise L.MrdemError(L.MRDEM_ERR_CAPACITY, "mrdem_detect_plain_fp64")
+
+
+def contact_forces(ctx, hier, pairs, eps, poses, contacts, mass, com, k_s=1000.0, force_torque=None,
+                   energy=None, stream=None):
+    n = hier.info()["n_particles"]
+    P = _pair_args(hier, pairs, eps, poses, n)
+    _need(mass, torch.float64, (n,), "mass")
+    _need(com, torch.float64, (n, 3), "com")
+    if force_torque is None:
+        force_torque = torch.zeros((n, 6), dtype=torch.float64, device=pairs.device)
+    if energy is None:
+        energy = torch.zeros(1, dtype=torch.float64, device=pairs.device)
+    cs = contacts.struct()
+    L.check(L.load().mrdem_contact_forces(ctx.handle, hier.handle, P, _p(pairs), _p(eps), _p(poses),
+                                          C.byref(cs), _p(mass), _p(com), float(k_s),
+                                          _p(force_torque), _p(energy), _stream(stream)),
+            "mrdem_contact_forces")
+    return force_torque, energy
+
+
+def contact_grad(ctx, hier, pairs, eps, poses, contacts, mass, k_s=1000.0, scale=1.0,
+                 want_verts=True, want_pose=True, want_jac=False, stream=None):
+    info = hier.info()
+    n = info["n_particles"]
+    P = _pair_args(hier, pairs, eps, poses, n)
+    _need(mass, torch.float64, (n,), "mass")
+    d = pairs.device
+    gv = torch.zeros((info["n_verts"], 3), dtype=torch.float32, device=d) if want_verts else None
+    gp = torch.zeros((n, 6), dtype=torch.float64, device=d) if want_pose else None
+    jac = torch.zeros((P, 12, 12), dtype=torch.float64, device=d) if want_jac else None
+    cs = contacts.struct()
+    L.check(L.load().mrdem_contact_grad(ctx.handle, hier.handle, P, _p(pairs), _p(eps), _p(poses),
+                                        C.byref(cs), _p(mass), float(k_s), float(scale), _p(gv),
+                                        _p(gp), _p(jac), _stream(stream)), "mrdem_contact_grad")
+    return gv, gp, jac
+
+
+def triangle_distance(ctx, P, Q, eps, precision="fp64", sweep=True, stream=None):
+    """Exact distance (and the float sweep diagnostics) of explicit triangle pairs."""
+    n = P.shape[0]
+    _need(P, torch.float64, (n, 9), "P")
+    _need(Q, torch.float64, (n, 9), "Q")
+    _need(eps, torch.float64, (n,), "eps")
+    d = P.device
+    out = dict(d=torch.empty(n, dtype=torch.float64, device=d),
+               pa=torch.empty((n, 3), dtype=torch.float64, device=d),
+               pb=torch.empty((n, 3), dtype=torch.float64, device=d),
+               feature=torch.empty(n, dtype=torch.int32, device=d))
+    if sweep:
+        out.update(x=torch.empty((n, 4), dtype=torch.float32, device=d),
+                   gap=torch.empty(n, dtype=torch.float32, device=d),
+                   converged=torch.empty(n, dtype=torch.int32, device=d))
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    L.check(L.load().mrdem_triangle_distance(ctx.handle, n, _p(P), _p(Q), _p(eps), prec,
+                                             _p(out["d"]), _p(out["pa"]), _p(out["pb"]),
+                                             _p(out["feature"]), _p(out.get("x")),
+                                             _p(out.get("gap")), _p(out.get("converged")),
+                                             _stream(stream)), "mrdem_triangle_distance")
+    return out
+
+
+class ContactProblem:
+    """Everything the energy of a particle batch depends on, resident on the device."""
+
+    def __init__(self, ctx, hier, pairs, eps, poses, mass, com, k_s=1000.0, precision="fp32"):
+        self.ctx, self.hier = ctx, hier
+        self.pairs, self.eps, self.poses, self.mass, self.com = pairs, eps, poses, mass, com
+        self.k_s, self.precision = float(k_s), precision
+        self.contacts = None
+
+    @classmethod
+    def from_scene(cls, ctx, hier, scene, device, precision="fp32", k_s=1000.0):
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)  # noqa: E731
+        return cls(ctx, hier, t(scene.pairs, torch.int32), t(scene.eps, torch.float64),
+                   t(scene.poses, torch.float64), t(scene.mass, torch.float64),
+                   t(scene.com, torch.float64), k_s, precision)
+
+    def detect(self, stats=None, check=True, stream=None):
+        self.contacts, st = detect(self.ctx, self.hier, self.pairs, self.eps, self.poses,
+                                   self.precision, contacts=self.contacts, stats=stats,
+                                   check=check, stream=stream)
+        return self.contacts, st
+
+    def forces(self, stream=None):
+        return contact_forces(self.ctx, self.hier, self.pairs, self.eps, self.poses, self.contacts,
+                              self.mass, self.com, self.k_s, stream=stream)
+
+    def grad(self, scale=1.0, want_jac=False, stream=None):
+        return contact_grad(self.ctx, self.hier, self.pairs, self.eps, self.poses, self.contacts,
+                            self.mass, self.k_s, scale, want_jac=want_jac, stream=stream)
+
+
+class ContactEnergy(torch.autograd.Function):
+    """E = sum over contacts of K_s sqrt(mu) eps (1 - d/(2 eps))^2.
+
+    Inputs: verts (float32 [n_verts, 3], the hierarchy's body-frame vertices;
+    their values are not re-read: the detection uses the hierarchy) and twist
+    (float64 [n_particles, 6], zeros: a world translation and rotation
+    increment about each particle origin).  Backward returns dE/dverts and
+    dE/dtwist at twist = 0, computed by the adjoint kernel."""
+
+    @staticmethod
+    def forward(fctx, verts, twist, problem: ContactProblem):
+        problem.detect()
+        _, energy = problem.forces()
+        fctx.problem = problem
+        return energy[0].clone()
+
+    @staticmethod
+    def backward(fctx, g):
+        gv, gp, _ = fctx.problem.grad(scale=float(g.item()))
+        return gv, gp, None
+
+
+def contact_energy(problem: ContactProblem, verts=None, twist=None):
+    info = problem.hier.info()
+    d = problem.pairs.device
+    if verts is None:
+        verts = torch.zeros((info["n_verts"], 3), dtype=torch.float32, device=d, requires_grad=True)
+    if twist is None:
+        twist = torch.zeros((info["n_particles"], 6), dtype=torch.float64, device=d,
+                            requires_grad=True)
+    return ContactEnergy.apply(verts, twist, problem), verts, twist

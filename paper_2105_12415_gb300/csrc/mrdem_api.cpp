@@ -1,0 +1,469 @@
+// mrdem_api.cpp -- the C ABI declared in include/mrdem.h: contexts, parameter
+// validation, hierarchy build/upload/export and argument checks in front of
+// the kernel launchers.  No exception crosses the boundary.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "mrdem_internal.h"
+
+using namespace mrdem;
+
+namespace {
+
+bool params_ok(const mrdem_params& p) {
+  return p.n_iter >= 1 && p.n_iter <= 64 && p.rho_reg > 0.f && p.rho_iter > 0.f && p.conv_c > 0.f &&
+         p.fanout >= 2 && p.fanout <= 8 && p.leaf_max >= 1 && p.leaf_max <= 32 && p.leaf_min >= 1 &&
+         p.kmeans_iters >= 0 && p.cap_level > 0 && p.cap_tiles > 0 && p.cap_candidates > 0 &&
+         p.cap_level < (int64_t)1 << 31 && p.cap_tiles < (int64_t)1 << 31 &&
+         p.cap_candidates < (int64_t)1 << 31 && p.tile_warps >= 1 && p.tile_warps <= 32 &&
+         p.tile_blocks_per_sm >= 1 && p.tile_blocks_per_sm <= 64 && p.level_warps >= 1 &&
+         p.level_warps <= 32 && p.exact_threads >= 32 && p.exact_threads <= 1024 &&
+         p.exact_threads % 32 == 0;
+}
+
+void free_lists(mrdem_ctx* c) {
+  cudaFree(c->level_list[0]);
+  cudaFree(c->level_list[1]);
+  cudaFree(c->tiles);
+  cudaFree(c->cands);
+  c->level_list[0] = c->level_list[1] = nullptr;
+  c->tiles = c->cands = nullptr;
+  c->cap_level = c->cap_tiles = c->cap_cands = 0;
+}
+
+int alloc_lists(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca) {
+  free_lists(c);
+  if (cudaMalloc(&c->level_list[0], sizeof(int3) * lv) != cudaSuccess ||
+      cudaMalloc(&c->level_list[1], sizeof(int3) * lv) != cudaSuccess ||
+      cudaMalloc(&c->tiles, sizeof(int3) * ti) != cudaSuccess ||
+      cudaMalloc(&c->cands, sizeof(int3) * ca) != cudaSuccess) {
+    cudaGetLastError();
+    free_lists(c);
+    return MRDEM_ERR_OOM;
+  }
+  c->cap_level = lv;
+  c->cap_tiles = ti;
+  c->cap_cands = ca;
+  return MRDEM_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+bool contacts_ok(const mrdem_contacts* c) {
+  return c && c->capacity >= 0 && c->count &&
+         (c->capacity == 0 || (c->pair && c->tri_a && c->tri_b && c->dist && c->point_a && c->point_b));
+}
+
+}  // namespace
+
+extern "C" {
+
+void mrdem_default_params(mrdem_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->n_iter = 4;
+  p->rho_reg = 1.0f;
+  p->rho_iter = 100.0f;
+  p->conv_c = 1.0f;
+  p->fanout = 8;
+  p->leaf_max = 32;
+  p->leaf_min = 16;
+  p->kmeans_iters = 3;
+  p->cap_level = (int64_t)1 << 24;
+  p->cap_tiles = (int64_t)1 << 24;
+  p->cap_candidates = (int64_t)1 << 25;
+  p->tile_warps = 8;
+  p->tile_blocks_per_sm = 4;
+  p->level_warps = 8;
+  p->exact_threads = 128;
+}
+
+const char* mrdem_status_string(int s) {
+  switch (s) {
+    case MRDEM_OK: return "ok";
+    case MRDEM_ERR_INVALID: return "invalid argument";
+    case MRDEM_ERR_OOM: return "out of memory";
+    case MRDEM_ERR_CUDA: return "CUDA runtime error";
+    case MRDEM_ERR_CAPACITY: return "work list or contact buffer capacity exceeded";
+    case MRDEM_ERR_NONFINITE: return "non-finite pose or eps (or eps <= 0)";
+    default: return "unknown status";
+  }
+}
+
+int mrdem_create(mrdem_ctx** out, int device, const mrdem_params* p) {
+  if (!out) return MRDEM_ERR_INVALID;
+  *out = nullptr;
+  mrdem_params prm;
+  if (p) prm = *p; else mrdem_default_params(&prm);
+  if (!params_ok(prm)) return MRDEM_ERR_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return MRDEM_ERR_CUDA;
+  }
+  DeviceGuard g(device);
+  mrdem_ctx* c = new (std::nothrow) mrdem_ctx();
+  if (!c) return MRDEM_ERR_OOM;
+  c->device = device;
+  c->params = prm;
+  cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device);
+  int st = alloc_lists(c, prm.cap_level, prm.cap_tiles, prm.cap_candidates);
+  if (st == MRDEM_OK &&
+      (cudaMalloc(&c->counters, sizeof(unsigned long long) * CNT_TOTAL) != cudaSuccess ||
+       cudaMalloc(&c->status, sizeof(unsigned long long) * ST_TOTAL) != cudaSuccess ||
+       cudaMemset(c->status, 0, sizeof(unsigned long long) * ST_TOTAL) != cudaSuccess))
+    st = MRDEM_ERR_OOM;
+  if (st != MRDEM_OK) {
+    cudaGetLastError();
+    mrdem_destroy(c);
+    return st;
+  }
+  *out = c;
+  return MRDEM_OK;
+}
+
+int mrdem_destroy(mrdem_ctx* c) {
+  if (!c) return MRDEM_OK;
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  for (auto& r : c->prof_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  free_lists(c);
+  cudaFree(c->xf);
+  cudaFree(c->xf64);
+  cudaFree(c->counters);
+  cudaFree(c->status);
+  delete c;
+  return MRDEM_OK;
+}
+
+int mrdem_get_params(const mrdem_ctx* c, mrdem_params* out) {
+  if (!c || !out) return MRDEM_ERR_INVALID;
+  *out = c->params;
+  return MRDEM_OK;
+}
+
+int mrdem_set_params(mrdem_ctx* c, const mrdem_params* p) {
+  if (!c || !p) return MRDEM_ERR_INVALID;
+  mrdem_params n = *p;
+  n.cap_level = c->params.cap_level;
+  n.cap_tiles = c->params.cap_tiles;
+  n.cap_candidates = c->params.cap_candidates;
+  if (!params_ok(n)) return MRDEM_ERR_INVALID;
+  c->params = n;
+  return MRDEM_OK;
+}
+
+int mrdem_reserve(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca) {
+  if (!c || lv < 0 || ti < 0 || ca < 0) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  lv = lv ? lv : c->cap_level;
+  ti = ti ? ti : c->cap_tiles;
+  ca = ca ? ca : c->cap_cands;
+  if (lv >= (int64_t)1 << 31 || ti >= (int64_t)1 << 31 || ca >= (int64_t)1 << 31)
+    return MRDEM_ERR_INVALID;
+  if (cudaDeviceSynchronize() != cudaSuccess) return MRDEM_ERR_CUDA;
+  int st = alloc_lists(c, lv, ti, ca);
+  if (st == MRDEM_OK) {
+    c->params.cap_level = lv;
+    c->params.cap_tiles = ti;
+    c->params.cap_candidates = ca;
+  }
+  return st;
+}
+
+int mrdem_build_hierarchy_host(const mrdem_params* params, int32_t n, const int64_t* vert_off,
+                               const float* verts, const int64_t* tri_off, const int32_t* tris,
+                               mrdem_hier** out) {
+  if (!out) return MRDEM_ERR_INVALID;
+  *out = nullptr;
+  mrdem_params prm;
+  if (params) prm = *params; else mrdem_default_params(&prm);
+  try {
+    mrdem_hier* h = new mrdem_hier();
+    int st = build_hierarchy_host(prm, n, vert_off, verts, tri_off, tris, &h->h);
+    if (st != MRDEM_OK) {
+      delete h;
+      return st;
+    }
+    *out = h;
+    return MRDEM_OK;
+  } catch (const std::bad_alloc&) {
+    return MRDEM_ERR_OOM;
+  } catch (...) {
+    return MRDEM_ERR_INVALID;
+  }
+}
+
+int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
+  if (!c || !hier) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  const HierHost& h = hier->h;
+  if (hier->d_mem) {
+    cudaFree(hier->d_mem);
+    hier->d_mem = nullptr;
+    hier->ctx = nullptr;
+  }
+  int64_t stride = (h.n_tri_pad + 31) / 32 * 32;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  size_t sz_geo = al(sizeof(float4) * 3 * h.n_nodes), sz_child = al(sizeof(int2) * h.n_nodes);
+  size_t sz_tri = al(sizeof(float) * 9 * stride), sz_vid = al(sizeof(int32_t) * 3 * stride);
+  size_t sz_slot = al(sizeof(int32_t) * stride), sz_ts = al(sizeof(int32_t) * h.n_tri);
+  size_t sz_off = al(sizeof(int64_t) * (h.n_particles + 1));
+  size_t sz_root = al(sizeof(int32_t) * h.n_particles), sz_br = al(sizeof(float) * h.n_particles);
+  size_t total = sz_geo + sz_child + sz_tri + sz_vid + sz_slot + sz_ts + sz_off + sz_root + sz_br;
+  char* base = nullptr;
+  if (cudaMalloc(&base, total) != cudaSuccess) {
+    cudaGetLastError();
+    return MRDEM_ERR_OOM;
+  }
+  try {
+    std::vector<char> buf(total, 0);
+    char* p = buf.data();
+    size_t o_geo = 0, o_child = o_geo + sz_geo, o_tri = o_child + sz_child, o_vid = o_tri + sz_tri;
+    size_t o_slot = o_vid + sz_vid, o_ts = o_slot + sz_slot, o_off = o_ts + sz_ts;
+    size_t o_root = o_off + sz_off, o_br = o_root + sz_root;
+    float4* geo = (float4*)(p + o_geo);
+    for (int64_t n = 0; n < h.n_nodes; ++n) {
+      const float* t = &h.node_tri[9 * n];
+      geo[3 * n + 0] = make_float4(t[0], t[1], t[2], h.node_delta[n]);
+      geo[3 * n + 1] = make_float4(t[3], t[4], t[5], 0.f);
+      geo[3 * n + 2] = make_float4(t[6], t[7], t[8], 0.f);
+    }
+    std::memcpy(p + o_child, h.node_child.data(), sizeof(int32_t) * 2 * h.n_nodes);
+    float* tri = (float*)(p + o_tri);
+    int32_t* vid = (int32_t*)(p + o_vid);
+    for (int64_t s = 0; s < h.n_tri_pad; ++s) {
+      for (int k = 0; k < 9; ++k) tri[k * stride + s] = h.slot_xyz[9 * s + k];
+      for (int k = 0; k < 3; ++k) vid[k * stride + s] = h.slot_vid[3 * s + k];
+    }
+    for (int64_t s = h.n_tri_pad; s < stride; ++s)
+      for (int k = 0; k < 3; ++k) vid[k * stride + s] = -1;
+    int32_t* st = (int32_t*)(p + o_slot);
+    for (int64_t s = 0; s < stride; ++s) st[s] = s < h.n_tri_pad ? h.slot_tri[s] : -1;
+    std::memcpy(p + o_ts, h.tri_slot.data(), sizeof(int32_t) * h.n_tri);
+    std::memcpy(p + o_off, h.tri_off.data(), sizeof(int64_t) * (h.n_particles + 1));
+    std::memcpy(p + o_root, h.root.data(), sizeof(int32_t) * h.n_particles);
+    std::memcpy(p + o_br, h.bound_r.data(), sizeof(float) * h.n_particles);
+    if (cudaMemcpy(base, buf.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(base);
+      cudaGetLastError();
+      return MRDEM_ERR_CUDA;
+    }
+    HierDev& d = hier->dev;
+    d.node_geo = (const float4*)(base + o_geo);
+    d.node_child = (const int2*)(base + o_child);
+    d.tri = (const float*)(base + o_tri);
+    d.vid = (const int32_t*)(base + o_vid);
+    d.slot_tri = (const int32_t*)(base + o_slot);
+    d.tri_slot = (const int32_t*)(base + o_ts);
+    d.tri_off = (const int64_t*)(base + o_off);
+    d.root = (const int32_t*)(base + o_root);
+    d.bound_r = (const float*)(base + o_br);
+    d.stride = stride;
+    d.n_tri = h.n_tri;
+    d.n_particles = h.n_particles;
+  } catch (const std::bad_alloc&) {
+    cudaFree(base);
+    return MRDEM_ERR_OOM;
+  }
+  hier->d_mem = base;
+  hier->ctx = c;
+  return MRDEM_OK;
+}
+
+int mrdem_build_hierarchy(mrdem_ctx* c, int32_t n, const int64_t* vert_off, const float* verts,
+                          const int64_t* tri_off, const int32_t* tris, mrdem_hier** out) {
+  if (!c || !out) return MRDEM_ERR_INVALID;
+  int st = mrdem_build_hierarchy_host(&c->params, n, vert_off, verts, tri_off, tris, out);
+  if (st != MRDEM_OK) return st;
+  st = mrdem_hier_upload(c, *out);
+  if (st != MRDEM_OK) {
+    mrdem_hier_destroy(*out);
+    *out = nullptr;
+  }
+  return st;
+}
+
+int mrdem_hier_destroy(mrdem_hier* h) {
+  if (!h) return MRDEM_OK;
+  if (h->d_mem) {
+    DeviceGuard g(h->ctx ? h->ctx->device : 0);
+    cudaFree(h->d_mem);
+  }
+  delete h;
+  return MRDEM_OK;
+}
+
+int mrdem_hier_get_info(const mrdem_hier* hier, mrdem_hier_info* out) {
+  if (!hier || !out) return MRDEM_ERR_INVALID;
+  const HierHost& h = hier->h;
+  out->n_particles = h.n_particles;
+  out->max_depth = h.max_depth;
+  out->n_nodes = h.n_nodes;
+  out->n_tri = h.n_tri;
+  out->n_tri_pad = h.n_tri_pad;
+  out->n_verts = h.n_verts;
+  return MRDEM_OK;
+}
+
+int mrdem_hier_export(const mrdem_hier* hier, float* node_tri, float* node_delta,
+                      int32_t* node_child, int32_t* node_level, int32_t* root, int32_t* slot_tri,
+                      int32_t* slot_particle) {
+  if (!hier) return MRDEM_ERR_INVALID;
+  const HierHost& h = hier->h;
+  if (node_tri) std::copy(h.node_tri.begin(), h.node_tri.end(), node_tri);
+  if (node_delta) std::copy(h.node_delta.begin(), h.node_delta.end(), node_delta);
+  if (node_child) std::copy(h.node_child.begin(), h.node_child.end(), node_child);
+  if (node_level) std::copy(h.node_level.begin(), h.node_level.end(), node_level);
+  if (root) std::copy(h.root.begin(), h.root.end(), root);
+  if (slot_tri) std::copy(h.slot_tri.begin(), h.slot_tri.end(), slot_tri);
+  if (slot_particle) std::copy(h.slot_particle.begin(), h.slot_particle.end(), slot_particle);
+  return MRDEM_OK;
+}
+
+static int check_pair_args(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
+                           const double* eps, const double* poses) {
+  if (!c || !h || n_pairs < 0 || n_pairs >= (int64_t)1 << 31) return MRDEM_ERR_INVALID;
+  if (h->ctx != c || !h->d_mem) return MRDEM_ERR_INVALID;
+  if (n_pairs > 0 && (!ab || !eps || !poses)) return MRDEM_ERR_INVALID;
+  return MRDEM_OK;
+}
+
+int mrdem_detect(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
+                 const double* eps, const double* poses, int32_t precision,
+                 const mrdem_contacts* out, int64_t* stats, mrdem_stream s) {
+  int st = check_pair_args(c, h, n_pairs, ab, eps, poses);
+  if (st) return st;
+  if (!contacts_ok(out) || (precision != MRDEM_PREC_FP32 && precision != MRDEM_PREC_FP64))
+    return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_detect(c, h, n_pairs, ab, eps, poses, precision, out, stats, (cudaStream_t)s);
+}
+
+int mrdem_check(mrdem_ctx* c, mrdem_stream s, int64_t* required) {
+  if (!c) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  unsigned long long st[ST_TOTAL];
+  if (cudaStreamSynchronize((cudaStream_t)s) != cudaSuccess ||
+      cudaMemcpy(st, c->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(c->status, 0, sizeof(st)) != cudaSuccess) {
+    cudaGetLastError();
+    return MRDEM_ERR_CUDA;
+  }
+  if (required) {
+    required[0] = (int64_t)st[ST_REQ_LEVEL];
+    required[1] = (int64_t)st[ST_REQ_TILES];
+    required[2] = (int64_t)st[ST_REQ_CANDS];
+    required[3] = (int64_t)st[ST_REQ_CONTACTS];
+  }
+  if (st[ST_NONFINITE]) return MRDEM_ERR_NONFINITE;
+  if (st[ST_REQ_LEVEL] || st[ST_REQ_TILES] || st[ST_REQ_CANDS] || st[ST_REQ_CONTACTS])
+    return MRDEM_ERR_CAPACITY;
+  return MRDEM_OK;
+}
+
+int mrdem_contact_forces(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
+                         const double* eps, const double* poses, const mrdem_contacts* con,
+                         const double* mass, const double* com, double k_s, double* ft,
+                         double* energy, mrdem_stream s) {
+  int st = check_pair_args(c, h, n_pairs, ab, eps, poses);
+  if (st) return st;
+  if (!contacts_ok(con) || !mass || !com || !(k_s >= 0)) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_forces(c, h, n_pairs, ab, eps, poses, con, mass, com, k_s, ft, energy,
+                       (cudaStream_t)s);
+}
+
+int mrdem_contact_grad(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
+                       const double* eps, const double* poses, const mrdem_contacts* con,
+                       const double* mass, double k_s, double scale, float* dverts,
+                       double* dpose, double* jac, mrdem_stream s) {
+  int st = check_pair_args(c, h, n_pairs, ab, eps, poses);
+  if (st) return st;
+  if (!contacts_ok(con) || !mass || !(k_s >= 0)) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_grad(c, h, n_pairs, ab, eps, poses, con, mass, k_s, scale, dverts, dpose, jac,
+                     (cudaStream_t)s);
+}
+
+int mrdem_detect_plain_fp64(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
+                            const double* eps, const double* poses, const mrdem_contacts* out,
+                            mrdem_stream s) {
+  int st = check_pair_args(c, h, n_pairs, ab, eps, poses);
+  if (st) return st;
+  if (!contacts_ok(out)) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_plain(c, h, n_pairs, ab, eps, poses, out, (cudaStream_t)s);
+}
+
+int mrdem_triangle_distance(mrdem_ctx* c, int64_t n, const double* P, const double* Q,
+                            const double* eps, int32_t precision, double* dist, double* pa,
+                            double* pb, int32_t* feature, float* sx, float* sgap, int32_t* sconv,
+                            mrdem_stream s) {
+  if (!c || n < 0 || n >= (int64_t)1 << 40) return MRDEM_ERR_INVALID;
+  if (n > 0 && (!P || !Q || !eps)) return MRDEM_ERR_INVALID;
+  if (precision != MRDEM_PREC_FP32 && precision != MRDEM_PREC_FP64) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_triangle_distance(c, n, P, Q, eps, precision, dist, pa, pb, feature, sx, sgap,
+                                  sconv, (cudaStream_t)s);
+}
+
+static const char* kKernelNames[K_COUNT] = {"k_setup", "k_level", "k_tile", "k_exact",
+                                            "k_forces", "k_grad", "k_plain", "k_tridist"};
+
+int mrdem_profile(mrdem_ctx* c, int32_t enable) {
+  if (!c) return MRDEM_ERR_INVALID;
+  c->prof = enable != 0;
+  return MRDEM_OK;
+}
+
+int mrdem_profile_read(mrdem_ctx* c, int32_t n_max, const char** names, double* ms,
+                       int64_t* launches, int32_t* n_out) {
+  if (!c || n_max < 0) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return MRDEM_ERR_CUDA;
+  }
+  double tot[K_COUNT] = {0};
+  int64_t cnt[K_COUNT] = {0};
+  for (auto& r : c->prof_recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      tot[r.kernel] += t;
+      cnt[r.kernel] += 1;
+    }
+    c->ev_pool.push_back(r.a);
+    c->ev_pool.push_back(r.b);
+  }
+  cudaGetLastError();
+  c->prof_recs.clear();
+  int n = 0;
+  for (int k = 0; k < K_COUNT && n < n_max; ++k) {
+    if (!cnt[k]) continue;
+    if (names) names[n] = kKernelNames[k];
+    if (ms) ms[n] = tot[k];
+    if (launches) launches[n] = cnt[k];
+    ++n;
+  }
+  if (n_out) *n_out = n;
+  return MRDEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// mrdem_internal.h -- data structures shared by the host code and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "mrdem.h"
+
+namespace mrdem {
+
+constexpr int kMaxLevels = 16;  // unfold steps of the level loop (tree depth <= 16)
+
+// Host-side surrogate trees of all particles (built by mrdem_build_hierarchy_host).
+struct HierHost {
+  int32_t n_particles = 0, max_depth = 0;
+  int64_t n_nodes = 0, n_tri = 0, n_tri_pad = 0, n_verts = 0;
+  std::vector<float> node_tri;      // [n_nodes * 9]
+  std::vector<float> node_delta;    // [n_nodes]
+  std::vector<int32_t> node_child;  // [n_nodes * 2] (begin, count); count < 0: leaf slots
+  std::vector<int32_t> node_level;  // [n_nodes]
+  std::vector<int32_t> root;        // [n_particles]
+  std::vector<float> slot_xyz;      // [n_tri_pad * 9] fine triangle per slot (body frame)
+  std::vector<int32_t> slot_vid;    // [n_tri_pad * 3] global vertex index (-1 pad)
+  std::vector<int32_t> slot_tri;    // [n_tri_pad] local input triangle index (-1 pad)
+  std::vector<int32_t> slot_particle;  // [n_tri_pad]
+  std::vector<int32_t> tri_slot;    // [n_tri] global input triangle -> slot
+  std::vector<int64_t> tri_off;     // [n+1] input triangle offsets
+  std::vector<int64_t> vert_off;    // [n+1]
+  std::vector<float> bound_r;       // [n] max |v| over the particle's vertices
+};
+
+// Device view of a hierarchy, passed by value to kernels.
+struct HierDev {
+  const float4* node_geo;  // [n_nodes*3]: (v0.xyz, delta) (v1.xyz, 0) (v2.xyz, 0)
+  const int2* node_child;  // [n_nodes]
+  const float* tri;        // 9 planes: coordinate k of slot s at tri[k*stride + s]
+  const int32_t* vid;      // 3 planes: global vertex index of corner k of slot s
+  const int32_t* slot_tri; // [stride] local input triangle index (-1 pad)
+  const int32_t* tri_slot; // [n_tri] global input triangle -> slot
+  const int64_t* tri_off;  // [n+1]
+  const int32_t* root;     // [n]
+  const float* bound_r;    // [n]
+  int64_t stride;          // plane stride (n_tri_pad rounded up)
+  int64_t n_tri;
+  int32_t n_particles;
+};
+
+// Per particle pair transform, written by the setup kernel.
+struct alignas(16) PairXf {
+  float R[9];   // B body -> A body rotation (float)
+  float t[3];   // B body -> A body translation (float)
+  float tau;    // 2 eps
+  float margin; // float rounding margin of the certificate
+  int32_t A, B;
+};
+struct alignas(16) PairXf64 {
+  double R[9], t[3];    // B body -> A body
+  double RA[9], tA[3];  // A body -> world
+  double eps;
+  int32_t A, B, valid, pad;
+};
+
+// Device counters (one int64 array, zeroed at the start of every detect).
+enum Counter : int {
+  CNT_LEVEL = 0,                          // [0..kMaxLevels] items in level list l
+  CNT_FETCH = CNT_LEVEL + kMaxLevels + 1, // [kMaxLevels+1] dynamic work fetch per kernel
+  CNT_TILES = CNT_FETCH + kMaxLevels + 2,
+  CNT_CANDS,
+  CNT_STATS,                              // [MRDEM_STAT_COUNT] statistics
+  CNT_TOTAL = CNT_STATS + MRDEM_STAT_COUNT
+};
+
+// Latched device status (not cleared by detect; cleared by mrdem_check).
+enum Status : int {
+  ST_NONFINITE = 0,
+  ST_REQ_LEVEL,
+  ST_REQ_TILES,
+  ST_REQ_CANDS,
+  ST_REQ_CONTACTS,
+  ST_TOTAL = 8
+};
+
+}  // namespace mrdem
+
+struct mrdem_hier {
+  mrdem::HierHost h;
+  mrdem_ctx* ctx = nullptr;  // context it was uploaded to
+  void* d_mem = nullptr;
+  mrdem::HierDev dev{};
+};
+
+namespace mrdem {
+enum KernelId : int { K_SETUP = 0, K_LEVEL, K_TILE, K_EXACT, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_COUNT };
+struct ProfRec {
+  int kernel;
+  cudaEvent_t a, b;
+};
+}  // namespace mrdem
+
+struct mrdem_ctx {
+  int device = 0;
+  int n_sms = 0;
+  mrdem_params params{};
+  int3* level_list[2] = {nullptr, nullptr};
+  int3* tiles = nullptr;
+  int3* cands = nullptr;
+  int64_t cap_level = 0, cap_tiles = 0, cap_cands = 0;
+  mrdem::PairXf* xf = nullptr;
+  mrdem::PairXf64* xf64 = nullptr;
+  int64_t cap_pairs = 0;
+  unsigned long long* counters = nullptr;  // [CNT_TOTAL]
+  unsigned long long* status = nullptr;    // [ST_TOTAL]
+  bool prof = false;
+  std::vector<mrdem::ProfRec> prof_recs;
+  std::vector<cudaEvent_t> ev_pool;
+};
+
+namespace mrdem {
+// Records an event pair around one kernel launch when profiling is enabled.
+struct ProfScope {
+  mrdem_ctx* c;
+  int id;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(mrdem_ctx* ctx, int kernel, cudaStream_t st) : c(ctx), id(kernel), s(st) {
+    if (c->prof) {
+      a = take();
+      cudaEventRecord(a, s);
+    }
+  }
+  ~ProfScope() {
+    if (c->prof && a) {
+      cudaEvent_t b = take();
+      cudaEventRecord(b, s);
+      c->prof_recs.push_back({id, a, b});
+    }
+  }
+  cudaEvent_t take() {
+    if (!c->ev_pool.empty()) {
+      cudaEvent_t e = c->ev_pool.back();
+      c->ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+}  // namespace mrdem
+
+namespace mrdem {
+// kernels / launchers (mrdem_detect.cu, mrdem_forces.cu)
+int launch_detect(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
+                  const double* pair_eps, const double* poses, int precision,
+                  const mrdem_contacts* out, int64_t* stats, cudaStream_t s);
+int launch_plain(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
+                 const double* pair_eps, const double* poses, const mrdem_contacts* out,
+                 cudaStream_t s);
+int launch_forces(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
+                  const double* pair_eps, const double* poses, const mrdem_contacts* c,
+                  const double* mass, const double* com, double k_s, double* ft, double* energy,
+                  cudaStream_t s);
+int launch_grad(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
+                const double* pair_eps, const double* poses, const mrdem_contacts* c,
+                const double* mass, double k_s, double scale, float* dverts, double* dpose,
+                double* jac, cudaStream_t s);
+int launch_triangle_distance(mrdem_ctx* ctx, int64_t n, const double* P, const double* Q,
+                             const double* eps, int precision, double* dist, double* pa,
+                             double* pb, int32_t* feature, float* sx, float* sgap, int32_t* sconv,
+                             cudaStream_t s);
+// host hierarchy builder (mrdem_hierarchy.cpp)
+int build_hierarchy_host(const mrdem_params& p, int32_t n, const int64_t* vert_off,
+                         const float* verts, const int64_t* tri_off, const int32_t* tris,
+                         HierHost* out);
+}  // namespace mrdem

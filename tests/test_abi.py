@@ -1,0 +1,54 @@
+"""The C ABI library loads on a CPU-only host and exports every symbol that
+include/mrdem.h declares; host-only calls work without a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "mrdem.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mrdem_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2105_12415_gb300 as m
+    lib = m.load()
+    names = _declared()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(m._lib.SIGNATURES)
+
+
+def test_status_strings_and_defaults():
+    import paper_2105_12415_gb300 as m
+    lib = m.load()
+    for s in (0, -1, -2, -3, -4, -5):
+        assert lib.mrdem_status_string(s)
+    p = m.default_params()
+    assert p.n_iter == 4 and p.fanout == 8 and p.leaf_max == 32 and abs(p.conv_c - 1.0) < 1e-7
+
+
+def test_create_without_gpu_reports_cuda_error():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2105_12415_gb300 as m
+    h = C.c_void_p()
+    assert m.load().mrdem_create(C.byref(h), 0, None) == m._lib.MRDEM_ERR_CUDA
+
+
+def test_null_arguments_are_rejected():
+    import paper_2105_12415_gb300 as m
+    lib = m.load()
+    assert lib.mrdem_create(None, 0, None) == m._lib.MRDEM_ERR_INVALID
+    assert lib.mrdem_detect(None, None, 0, None, None, None, 0, None, None, None) == -1
+    assert lib.mrdem_check(None, None, None) == -1
+    assert lib.mrdem_hier_get_info(None, None) == -1
+    assert lib.mrdem_destroy(None) == 0

@@ -1,0 +1,185 @@
+"""Multiresolution detection (Algorithm 5) on the GPU through the C ABI against
+the FP64 brute-force oracle (Lemma 1: same contact set), in both precision
+forms, plus the plain FP64 GPU form, the batched workload at full size on
+sampled pairs, and the edge cases."""
+import numpy as np
+import pytest
+
+from gen import scene_c1, scene_c2, scene_pairs, scene_tiny
+from tests.gpu_common import compare_contacts, gpu_scene_tensors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gctx():
+    import paper_2105_12415_gb300 as m
+    m.build()
+    return m.Context(0)
+
+
+def _run(gctx, scene, precision, hier=None):
+    import torch
+    import paper_2105_12415_gb300 as m
+    dev = torch.device("cuda:0")
+    if hier is None:
+        hier = m.Hierarchy.from_scene(gctx, scene)
+    t = gpu_scene_tensors(scene, dev)
+    c, stats = m.detect(gctx, hier, t["pairs"], t["eps"], t["poses"], precision)
+    return c.to_numpy(), stats.cpu().numpy(), hier
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_c1_one_pair_full_parity(gctx, orc, precision):
+    s = scene_c1()
+    ref = orc.detect(s)
+    got, stats, _ = _run(gctx, s, precision)
+    assert len(ref["d"]) > 100
+    compare_contacts(got, ref, s.eps, precision)
+    assert stats[20] == len(got["d"])
+    # the hierarchy pruned: far fewer fine tests than 1280^2
+    assert 0 < stats[17] < 0.1 * 1280 * 1280
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tiny_and_mixed_scenes(gctx, orc, precision):
+    for s in (scene_tiny(n_pairs=24, levels=(0, 1, 2)),
+              scene_pairs([1, 2, 3, 4], [4, 3, 1, 1], [0.1, 1.0, 0.5, 0.2], [1.0, 0.13, 0.5, 0.9],
+                          [0.001, 0.0013, 0.005, 0.002], [-0.0005, 0.002, 0.0, 0.006], 21, "mixed")):
+        ref = orc.detect(s)
+        got, _, _ = _run(gctx, s, precision)
+        compare_contacts(got, ref, s.eps, precision)
+
+
+def test_plain_fp64_form_and_lemma1(gctx, orc):
+    """The plain form (all pairs, FP64) equals the oracle, and the hierarchy's
+    result equals the plain form's (Lemma 1)."""
+    import torch
+    import paper_2105_12415_gb300 as m
+    s = scene_pairs([3, 2], [2, 3], [1.0, 0.6], [0.7, 1.0], [0.01, 0.008], [-0.004, 0.001], 31, "lemma1")
+    ref = orc.detect(s)
+    got, _, hier = _run(gctx, s, "fp64")
+    t = gpu_scene_tensors(s, torch.device("cuda:0"))
+    plain = m.detect_plain_fp64(gctx, hier, t["pairs"], t["eps"], t["poses"]).to_numpy()
+    compare_contacts(plain, ref, s.eps, "fp64")
+    compare_contacts(got, plain, s.eps, "fp64")
+
+
+def test_swapped_pairs_and_self_pair(gctx, orc):
+    s = scene_tiny(n_pairs=6, levels=(1, 2), seed=44)
+    sw = scene_tiny(n_pairs=6, levels=(1, 2), seed=44)
+    sw.pairs = s.pairs[:, ::-1].copy()
+    a, _, _ = _run(gctx, s, "fp64")
+    b, _, _ = _run(gctx, sw, "fp64")
+    ka = sorted(zip(a["pair"].tolist(), a["ta"].tolist(), a["tb"].tolist()))
+    kb = sorted(zip(b["pair"].tolist(), b["tb"].tolist(), b["ta"].tolist()))
+    assert ka == kb
+    # a particle against itself: every triangle touches its neighbours
+    s1 = scene_tiny(n_pairs=1, levels=(1,), seed=45)
+    s1.pairs = np.array([[0, 0]], np.int32)
+    ref = orc.detect(s1)
+    got, _, _ = _run(gctx, s1, "fp64")
+    compare_contacts(got, ref, s1.eps, "fp64", check_points=False)
+
+
+def test_empty_and_far_apart(gctx):
+    import torch
+    import paper_2105_12415_gb300 as m
+    s = scene_pairs([2], [2], [1.0], [1.0], [0.01], [5.0], 3, "far")
+    got, stats, hier = _run(gctx, s, "fp32")
+    assert len(got["d"]) == 0 and stats[17] == 0
+    dev = torch.device("cuda:0")
+    t = gpu_scene_tensors(s, dev)
+    c, st = m.detect(gctx, hier, t["pairs"][:0], t["eps"][:0], t["poses"], "fp32")
+    assert c.n() == 0
+
+
+def test_invalid_inputs_are_latched(gctx):
+    import torch
+    import paper_2105_12415_gb300 as m
+    s = scene_tiny(n_pairs=2, levels=(1,))
+    hier = m.Hierarchy.from_scene(gctx, s)
+    dev = torch.device("cuda:0")
+    t = gpu_scene_tensors(s, dev)
+    bad_pose = t["poses"].clone()
+    bad_pose[0, 0] = float("nan")
+    with pytest.raises(m.MrdemError) as e:
+        m.detect(gctx, hier, t["pairs"], t["eps"], bad_pose)
+    assert e.value.status == m._lib.MRDEM_ERR_NONFINITE
+    bad_eps = t["eps"].clone()
+    bad_eps[1] = 0.0
+    with pytest.raises(m.MrdemError):
+        m.detect(gctx, hier, t["pairs"], bad_eps, t["poses"])
+    bad_pairs = t["pairs"].clone()
+    bad_pairs[0, 1] = 99
+    with pytest.raises(m.MrdemError):
+        m.detect(gctx, hier, bad_pairs, t["eps"], t["poses"])
+    # the context stays usable
+    c, _ = m.detect(gctx, hier, t["pairs"], t["eps"], t["poses"])
+    assert c.n() >= 0
+
+
+def test_capacity_overflow_is_reported_and_recovered(orc):
+    """Tiny work lists: the first call reports CAPACITY with the required
+    sizes; the binding grows the lists and repeats; the result is exact."""
+    import ctypes as C
+    import torch
+    import paper_2105_12415_gb300 as m
+    ctx = m.Context(0, cap_level=8, cap_tiles=8, cap_candidates=8)
+    s = scene_c1()
+    hier = m.Hierarchy.from_scene(ctx, s)
+    dev = torch.device("cuda:0")
+    t = gpu_scene_tensors(s, dev)
+    contacts = m.Contacts(4, dev)
+    cs = contacts.struct()
+    lib = m.load()
+    st = lib.mrdem_detect(ctx.handle, hier.handle, 1, t["pairs"].data_ptr(), t["eps"].data_ptr(),
+                          t["poses"].data_ptr(), 1, C.byref(cs), None, None)
+    assert st == 0
+    req = np.zeros(4, np.int64)
+    assert lib.mrdem_check(ctx.handle, None, req.ctypes.data) == m._lib.MRDEM_ERR_CAPACITY
+    assert req[0] > 8 or req[1] > 8 or req[2] > 8
+    got, _ = m.detect(ctx, hier, t["pairs"], t["eps"], t["poses"], "fp64", contacts=contacts)
+    compare_contacts(got.to_numpy(), orc.detect(s), s.eps, "fp64")
+
+
+@pytest.mark.parametrize("precision", ["fp32"])
+def test_batched_full_size_sampled(gctx, orc, precision):
+    """The 4096-pair batched workload in one launch sequence (as timed by the
+    benchmark); sampled pairs checked against the oracle pair by pair, and
+    properties that hold at any size checked on all pairs."""
+    import torch
+    import paper_2105_12415_gb300 as m
+    s = scene_c2()
+    hier = m.Hierarchy.from_scene(gctx, s)
+    dev = torch.device("cuda:0")
+    t = gpu_scene_tensors(s, dev)
+    c, stats = m.detect(gctx, hier, t["pairs"], t["eps"], t["poses"], precision)
+    got = c.to_numpy()
+    st = stats.cpu().numpy()
+    n = len(got["d"])
+    assert n == st[20] and n > 0
+    # properties on every contact
+    tau = 2 * s.eps[got["pair"]]
+    assert np.all(got["d"] <= tau * (1 + 1e-12))
+    assert np.all(np.abs(np.linalg.norm(got["pa"] - got["pb"], axis=1) - got["d"]) <= 1e-9 * np.maximum(got["d"], 1e-3))
+    keys = got["pair"].astype(np.int64) * (1 << 40) + got["ta"].astype(np.int64) * (1 << 20) + got["tb"]
+    assert len(np.unique(keys)) == n
+    ntri = np.diff(s.tri_off)
+    assert np.all(got["ta"] < ntri[s.pairs[got["pair"], 0]]) and np.all(got["tb"] < ntri[s.pairs[got["pair"], 1]])
+    # sampled pairs: one of every size class combination present, and the
+    # deepest interpenetration
+    rng = np.random.default_rng(0)
+    sample = list(rng.choice(s.n_pairs, size=10, replace=False))
+    sample.append(int(np.argmax(ntri[s.pairs[:, 0]] * ntri[s.pairs[:, 1]] *
+                               (np.bincount(got["pair"], minlength=s.n_pairs) > 0))))
+    sample = [int(x) for x in dict.fromkeys(int(v) for v in sample)]
+    sub = s.subset(sample)
+    ref = orc.detect(sub)
+    sel = np.isin(got["pair"], sample)
+    remap = {p: i for i, p in enumerate(sample)}
+    g2 = {k: v[sel] for k, v in got.items()}
+    g2["pair"] = np.array([remap[p] for p in g2["pair"]], np.int32)
+    o = np.lexsort((g2["tb"], g2["ta"], g2["pair"]))
+    g2 = {k: v[o] for k, v in g2.items()}
+    compare_contacts(g2, ref, sub.eps, precision)

@@ -1,0 +1,136 @@
+"""Host construction of the surrogate trees (Sec. 4, Algorithm 7, Appendix A),
+checked on the CPU: conservativeness of every surrogate (FP64 oracle
+distances), tree shape, Table 1 magnitude, determinism and input errors."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gen import icosphere, scene_c1, scene_pairs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _host(scene, **kw):
+    import paper_2105_12415_gb300 as m
+    p = m.default_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return m.Hierarchy.build_host(scene.vert_off, scene.verts, scene.tri_off, scene.tris, p)
+
+
+def _fine_tris_below(ex, node):
+    """Slots (fine triangles) below a node."""
+    b, c = ex["node_child"][node]
+    if c < 0:
+        return list(range(b, b - c))
+    out = []
+    for ch in range(b, b + c):
+        out += _fine_tris_below(ex, ch)
+    return out
+
+
+def _check_conservative(orc, scene, ex):
+    nn = len(ex["node_delta"])
+    worst = 0.0
+    for node in range(nn):
+        slots = _fine_tris_below(ex, node)
+        parts = ex["slot_particle"][slots]
+        assert np.all(parts == parts[0])
+        v, t = scene.particle(int(parts[0]))
+        vid = np.unique(t[ex["slot_tri"][slots]].ravel())
+        V = v[vid].astype(np.float64)
+        T = np.repeat(ex["node_tri"][node][None].astype(np.float64), len(V), 0)
+        d = orc.vertex_surrogate_distance(V, T)
+        assert d.max() <= float(ex["node_delta"][node]), (node, d.max(), ex["node_delta"][node])
+        worst = max(worst, float(ex["node_delta"][node]) - d.max())
+    return worst
+
+
+def test_c1_tree_shape_and_conservativeness(orc):
+    s = scene_c1()
+    h = _host(s)
+    info = h.info()
+    ex = h.export()
+    assert info["n_particles"] == 2 and info["n_tri"] == 2560 and info["max_depth"] == 3
+    # one root + 8 + 64 leaves of 20 triangles per particle
+    assert info["n_nodes"] == 2 * 73
+    lvl = ex["node_level"]
+    for i in range(2):
+        r = ex["root"][i]
+        assert lvl[r] == 1
+        nodes = np.arange(r, r + 73)
+        assert (lvl[nodes] == 1).sum() == 1 and (lvl[nodes] == 2).sum() == 8 and (lvl[nodes] == 3).sum() == 64
+        leaves = nodes[ex["node_child"][nodes, 1] < 0]
+        assert len(leaves) == 64 and np.all(-ex["node_child"][leaves, 1] == 20)
+    # every fine triangle sits in exactly one slot
+    sl = ex["slot_tri"] >= 0
+    keys = ex["slot_particle"][sl].astype(np.int64) * 100000 + ex["slot_tri"][sl]
+    assert len(np.unique(keys)) == 2560
+    _check_conservative(orc, s, ex)
+
+
+@pytest.mark.parametrize("level,depth", [(1, 2), (2, 3), (3, 3), (4, 4), (5, 5)])
+def test_depth_by_size(level, depth):
+    s = scene_pairs([level], [1], [1.0], [1.0], [0.01], [0.0], 3, "depth")
+    h = _host(s)
+    ex = h.export()
+    r0 = ex["root"][0]
+    r1 = ex["root"][1]
+    lv = ex["node_level"][r0:r1]
+    assert lv.max() == depth
+    child = ex["node_child"][r0:r1]
+    leaves = child[:, 1] < 0
+    assert np.all(-child[leaves, 1] <= 32) and np.all(-child[leaves, 1] >= 16)
+    assert np.all(child[~leaves, 1] <= 8) and np.all(child[~leaves, 1] >= 2)
+    # breadth-first: children follow their parent, levels never decrease
+    assert np.all(np.diff(lv) >= 0)
+    for k in np.nonzero(~leaves)[0]:
+        b, c = child[k]
+        assert b > r0 + k and np.all(ex["node_level"][b:b + c] == lv[k] + 1)
+
+
+def test_conservative_on_batched_sizes(orc):
+    s = scene_pairs([1, 2, 4], [3, 2, 1], [0.3, 1.0, 0.12], [1.0, 0.5, 0.8], [0.003] * 3,
+                    [0.0] * 3, 8, "mixed")
+    h = _host(s)
+    _check_conservative(orc, s, h.export())
+
+
+def test_table1_root_surrogate_magnitude():
+    """Table 1, eta_r = 1: the single-triangle root of an unbumped
+    unit-diameter sphere needs eps_kmax ~ r_sphere = 0.5."""
+    g = json.load(open(os.path.join(HERE, "golden", "table1_root_surrogate.json")))
+    from gen.icosphere import _assemble
+    for nt, eps_paper in zip(g["n_triangles"], g["eps_kmax"]):
+        level = {80: 1, 320: 2, 1280: 3}[nt]
+        v, f = icosphere(level)
+        m = ((v * 0.5).astype(np.float32), f)
+        s = _assemble([m], [[0, 0, 0, 1, 0, 0, 0]], [0.5], np.zeros((0, 2)), [], "unit-diameter")
+        ex = _host(s).export()
+        delta = float(ex["node_delta"][ex["root"][0]])
+        assert abs(delta - g["r_sphere"]) <= 0.1 * g["r_sphere"]
+        assert abs(delta - eps_paper) <= 0.1 * g["r_sphere"]
+
+
+def test_deterministic():
+    s = scene_pairs([3], [2], [1.0], [0.4], [0.01], [0.0], 5, "det")
+    a, b = _host(s).export(), _host(s).export()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_invalid_inputs():
+    import paper_2105_12415_gb300 as m
+    s = scene_pairs([1], [1], [1.0], [1.0], [0.01], [0.0], 5, "bad")
+    bad = s.tris.copy()
+    bad[5, 1] = 10_000
+    with pytest.raises(m.MrdemError):
+        m.Hierarchy.build_host(s.vert_off, s.verts, s.tri_off, bad)
+    deg = s.tris.copy()
+    deg[3] = [deg[3, 0], deg[3, 0], deg[3, 1]]
+    with pytest.raises(m.MrdemError):
+        m.Hierarchy.build_host(s.vert_off, s.verts, s.tri_off, deg)
+    with pytest.raises(m.MrdemError):
+        m.Hierarchy.build_host(np.array([0]), s.verts, np.array([0]), s.tris)
