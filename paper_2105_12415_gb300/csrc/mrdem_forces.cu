@@ -68,15 +68,15 @@ __global__ void __launch_bounds__(256) k_forces(HierDev H, const int32_t* __rest
                                                 const double* __restrict__ poses,
                                                 mrdem_contacts c, const double* __restrict__ mass,
                                                 const double* __restrict__ com, double k_s,
-                                                double* ft, double* energy) {
+                                                double* ft, double* energy, int64_t n_pairs) {
   int64_t n = *c.count;
   if (n > c.capacity) n = c.capacity;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     int64_t k = base + threadIdx.x;
     double e_k = 0.0;
-    if (k < n) {
-      int p = c.pair[k];
+    int p = k < n ? c.pair[k] : -1;
+    if (p >= 0 && p < n_pairs) {
       int A = ab[2 * p], B = ab[2 * p + 1];
       double e = eps[p], d = c.dist[k];
       double mu = 1.0 / (1.0 / mass[A] + 1.0 / mass[B]);
@@ -122,12 +122,13 @@ __global__ void __launch_bounds__(128) k_grad(HierDev H, const int32_t* __restri
                                               const double* __restrict__ poses, mrdem_contacts c,
                                               const double* __restrict__ mass, double k_s,
                                               double scale, float* dverts, double* dpose,
-                                              double* jac) {
+                                              double* jac, int64_t n_pairs) {
   int64_t n = *c.count;
   if (n > c.capacity) n = c.capacity;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
     int p = c.pair[k];
+    if (p < 0 || p >= n_pairs) continue;
     int A = ab[2 * p], B = ab[2 * p + 1];
     double e = eps[p];
     const double* pA = poses + 7 * (int64_t)A;
@@ -188,11 +189,10 @@ int launch_forces(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
                   const double* eps, const double* poses, const mrdem_contacts* con,
                   const double* mass, const double* com, double k_s, double* ft, double* energy,
                   cudaStream_t s) {
-  (void)n_pairs;
   if (!ft && !energy) return MRDEM_OK;
   ProfScope ps(c, K_FORCES, s);
   k_forces<<<c->n_sms * 8, 256, 0, s>>>(hier->dev, ab, eps, poses, *con, mass, com, k_s, ft,
-                                         energy);
+                                         energy, n_pairs);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
 
@@ -200,11 +200,10 @@ int launch_grad(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int
                 const double* eps, const double* poses, const mrdem_contacts* con,
                 const double* mass, double k_s, double scale, float* dverts, double* dpose,
                 double* jac, cudaStream_t s) {
-  (void)n_pairs;
   if (!dverts && !dpose && !jac) return MRDEM_OK;
   ProfScope ps(c, K_GRAD, s);
   k_grad<<<c->n_sms * 8, 128, 0, s>>>(hier->dev, ab, eps, poses, *con, mass, k_s, scale, dverts,
-                                       dpose, jac);
+                                       dpose, jac, n_pairs);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
 
