@@ -35,7 +35,7 @@ def test_c1_one_pair_full_parity(gctx, orc, precision):
     ref = orc.detect(s)
     got, stats, _ = _run(gctx, s, precision)
     assert len(ref["d"]) > 100
-    compare_contacts(got, ref, s.eps, precision)
+    compare_contacts(got, ref, s, precision)
     assert stats[20] == len(got["d"])
     # the hierarchy pruned: far fewer fine tests than 1280^2
     assert 0 < stats[17] < 0.1 * 1280 * 1280
@@ -48,7 +48,7 @@ def test_tiny_and_mixed_scenes(gctx, orc, precision):
                           [0.001, 0.0013, 0.005, 0.002], [-0.0005, 0.002, 0.0, 0.006], 21, "mixed")):
         ref = orc.detect(s)
         got, _, _ = _run(gctx, s, precision)
-        compare_contacts(got, ref, s.eps, precision)
+        compare_contacts(got, ref, s, precision)
 
 
 def test_plain_fp64_form_and_lemma1(gctx, orc):
@@ -61,8 +61,8 @@ def test_plain_fp64_form_and_lemma1(gctx, orc):
     got, _, hier = _run(gctx, s, "fp64")
     t = gpu_scene_tensors(s, torch.device("cuda:0"))
     plain = m.detect_plain_fp64(gctx, hier, t["pairs"], t["eps"], t["poses"]).to_numpy()
-    compare_contacts(plain, ref, s.eps, "fp64")
-    compare_contacts(got, plain, s.eps, "fp64")
+    compare_contacts(plain, ref, s, "fp64")
+    compare_contacts(got, plain, s, "fp64")
 
 
 def test_swapped_pairs_and_self_pair(gctx, orc):
@@ -79,7 +79,7 @@ def test_swapped_pairs_and_self_pair(gctx, orc):
     s1.pairs = np.array([[0, 0]], np.int32)
     ref = orc.detect(s1)
     got, _, _ = _run(gctx, s1, "fp64")
-    compare_contacts(got, ref, s1.eps, "fp64", check_points=False)
+    compare_contacts(got, ref, s1, "fp64", check_points=False)
 
 
 def test_empty_and_far_apart(gctx):
@@ -140,7 +140,7 @@ def test_capacity_overflow_is_reported_and_recovered(orc):
     assert lib.mrdem_check(ctx.handle, None, req.ctypes.data) == m._lib.MRDEM_ERR_CAPACITY
     assert req[0] > 8 or req[1] > 8 or req[2] > 8
     got, _ = m.detect(ctx, hier, t["pairs"], t["eps"], t["poses"], "fp64", contacts=contacts)
-    compare_contacts(got.to_numpy(), orc.detect(s), s.eps, "fp64")
+    compare_contacts(got.to_numpy(), orc.detect(s), s, "fp64")
 
 
 @pytest.mark.parametrize("precision", ["fp32"])
@@ -182,4 +182,4 @@ def test_batched_full_size_sampled(gctx, orc, precision):
     g2["pair"] = np.array([remap[p] for p in g2["pair"]], np.int32)
     o = np.lexsort((g2["tb"], g2["ta"], g2["pair"]))
     g2 = {k: v[o] for k, v in g2.items()}
-    compare_contacts(g2, ref, sub.eps, precision)
+    compare_contacts(g2, ref, sub, precision)
