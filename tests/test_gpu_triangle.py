@@ -43,10 +43,13 @@ def test_exact_distance_fp64_matches_oracle(gctx, orc):
     d = out["d"].cpu().numpy()
     err = np.abs(d - d_ref) / np.maximum(d_ref, 0.05)
     assert err.max() <= 1e-12, err.max()
-    same = out["feature"].cpu().numpy() == f_ref
-    assert same.mean() > 0.999
-    pa = out["pa"].cpu().numpy()
-    assert np.abs(pa[same] - pa_ref[same]).max() <= 1e-9
+    # the feature code is not unique (a vertex whose closest point lies on an
+    # edge ties with that edge-edge test); the closest points are, except for
+    # parallel features, so compare those
+    pa, pb = out["pa"].cpu().numpy(), out["pb"].cpu().numpy()
+    dev_pts = np.maximum(np.linalg.norm(pa - pa_ref, axis=1), np.linalg.norm(pb - pb_ref, axis=1))
+    assert np.mean(dev_pts <= 1e-9) > 0.999
+    assert np.all(np.abs(np.linalg.norm(pa - pb, axis=1) - d) <= 1e-12 * np.maximum(d, 1))
 
 
 def test_exact_distance_fp32_form(gctx, orc):
