@@ -26,10 +26,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Floating-point operations of one fine triangle-pair test in the finest-level
-# kernel (penalty sweep with 4 iterations, convergence check, certificate),
-# counted from its source as FADD + FMUL + 2 FFMA + MUFU; see the design doc.
-FLOPS_PER_FINE_TEST = 455
+# Floating-point operations in the finest-level kernel, counted from its source
+# as FADD + FMUL + 2 FFMA + MUFU (cross-checked with ncu's instruction
+# counters): one penalty sweep (4 iterations, convergence
+# check, certificate) and one bounding-sphere test of a fine pair.
+FLOPS_PER_SWEEP = 429
+FLOPS_PER_SPHERE_TEST = 11
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -342,10 +344,12 @@ def main():
     tile_ms, tile_n = prof.get("k_tile", (float("nan"), 1))
     tile_avg_s = tile_ms / tile_n * 1e-3
     fine_tests = int(st[m._lib.MRDEM_STAT_FINE_TESTS])
+    sphere_tests = int(st[m._lib.MRDEM_STAT_SPHERE_TESTS])
+    tile_flops = fine_tests * FLOPS_PER_SWEEP + sphere_tests * FLOPS_PER_SPHERE_TEST
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = fine_tests * FLOPS_PER_FINE_TEST / tile_avg_s / 1e12
+    achieved = tile_flops / tile_avg_s / 1e12
     traffic = _traffic_per_launch()
     total_prof = sum(v[0] for v in prof.values())
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
@@ -426,13 +430,16 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_tile", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": traffic,
-                     "per_launch": {"fine_tests": fine_tests, "flops_per_test": FLOPS_PER_FINE_TEST,
-                                    "avg_ms": tile_avg_s * 1e3}},
+                     "per_launch": {"sweeps": fine_tests, "flops_per_sweep": FLOPS_PER_SWEEP,
+                                    "sphere_tests": sphere_tests,
+                                    "flops_per_sphere_test": FLOPS_PER_SPHERE_TEST,
+                                    "flops": tile_flops, "avg_ms": tile_avg_s * 1e3}},
         "clocks": clk.summary(),
         "gpu_launches": launches_per_step * args.steps,
         "kernels": kernels,
         "stats": {"tests_per_level": [int(x) for x in st[0:6]],
                   "survivors_per_level": [int(x) for x in st[8:14]],
+                  "leaf_tiles": int(st[16]), "sphere_tests": sphere_tests,
                   "fine_tests": fine_tests, "candidates": int(st[18]),
                   "unconverged": int(st[19]), "contacts": n_contacts, "fp64_refinements": int(st[21]),
                   "fine_tests_per_s": fine_tests * args.steps * world / (ms_max * 1e-3),

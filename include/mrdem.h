@@ -62,11 +62,12 @@ typedef struct CUstream_st* mrdem_stream; /* same type as cudaStream_t */
 #define MRDEM_STAT_TESTS 0       /* [0..7]  surrogate-pair tests at unfold step l (0 = roots) */
 #define MRDEM_STAT_SURVIVORS 8   /* [8..15] of which not pruned */
 #define MRDEM_STAT_TILES 16      /* leaf-pair tiles reaching the finest level */
-#define MRDEM_STAT_FINE_TESTS 17 /* fine triangle-pair sweeps (iterative tests) */
+#define MRDEM_STAT_FINE_TESTS 17 /* fine triangle-pair sweeps (iterative tests) after the cull */
 #define MRDEM_STAT_CANDIDATES 18 /* fine pairs not pruned by the sweep's certificate */
 #define MRDEM_STAT_UNCONVERGED 19 /* candidates whose sweep had not converged (the paper's odot) */
 #define MRDEM_STAT_CONTACTS 20   /* contacts written (or that would have been written) */
 #define MRDEM_STAT_FP64 21       /* candidates re-evaluated in FP64 */
+#define MRDEM_STAT_SPHERE_TESTS 22 /* fine pairs of the leaf tiles (bounding-sphere cull) */
 #define MRDEM_STAT_COUNT 32
 
 typedef struct mrdem_params {

@@ -258,7 +258,33 @@ __global__ void __launch_bounds__(WARPS * 32) k_level(HierDev H, const PairXf* _
 }
 
 // ---------------------------------------------------------------------------
-// k_tile: one warp per leaf pair (dynamic fetch); one fine pair per lane.
+// k_tile: one warp per leaf pair (dynamic fetch).  Both leaves' fine
+// triangles are staged in shared memory (B moved into A's frame) together
+// with a bounding sphere each (centroid, largest vertex distance).  Pass 1
+// spreads the la x lb products over the lanes and keeps the pairs whose
+// spheres come within the threshold (|c_a - c_b| - r_a - r_b bounds the
+// distance from below); the survivors are compacted into a per-warp queue
+// (the buffered comparisons of Sec. 5.4).  Pass 2 runs the penalty sweep and
+// certificate over the queue, one fine pair per lane.
+constexpr int kTileQueue = 1024;  // 32 x 32 products
+struct TileSmem {
+  float4 a[3][32];  // A: v0, v1, v2 (xyz), w = centroid x / y / z
+  float4 b[3][32];
+  float ra[32], rb[32];
+  unsigned short q[kTileQueue];
+};
+
+__device__ __forceinline__ void stage_triangle(F3 v0, F3 v1, F3 v2, float4 (*dst)[32], float* rad,
+                                               int lane) {
+  F3 c = (1.f / 3.f) * ((v0 + v1) + v2);
+  F3 d0 = v0 - c, d1 = v1 - c, d2 = v2 - c;
+  float r2 = fmaxf(dot(d0, d0), fmaxf(dot(d1, d1), dot(d2, d2)));
+  dst[0][lane] = make_float4(v0.x, v0.y, v0.z, c.x);
+  dst[1][lane] = make_float4(v1.x, v1.y, v1.z, c.y);
+  dst[2][lane] = make_float4(v2.x, v2.y, v2.z, c.z);
+  rad[lane] = sqrtf(r2) * (1.f + 1e-6f);
+}
+
 template <bool CONV>
 __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restrict__ xf,
                                               SweepConst sc, float conv_c,
@@ -266,13 +292,12 @@ __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restric
                                               unsigned long long* cnt, unsigned long long* status,
                                               int64_t cap_tiles, int64_t cap_cands,
                                               const double* __restrict__ eps_d) {
-  extern __shared__ float smem[];
+  extern __shared__ float4 smem4[];
   const int w = threadIdx.x >> 5, lane = lane_id();
-  float* sA = smem + w * (18 * 32);
-  float* sB = sA + 9 * 32;
+  TileSmem& S = reinterpret_cast<TileSmem*>(smem4)[w];
   int64_t n_tiles = (int64_t)cnt[CNT_TILES];
   if (n_tiles > cap_tiles) n_tiles = cap_tiles;
-  WarpCount tests, ncand, nodot;
+  WarpCount tests, spheres, ncand, nodot;
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(cnt + CNT_FETCH + kMaxLevels, 1ull);
@@ -286,40 +311,67 @@ __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restric
     int2 ca = H.node_child[it.y], cb = H.node_child[it.z];
     int na = -ca.y, nb = -cb.y;
     if (lane < na) {
+      F3 v[3];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) sA[k * 32 + lane] = __ldg(H.tri + k * H.stride + ca.x + lane);
+      for (int c = 0; c < 3; ++c) {
+        v[c].x = __ldg(H.tri + (3 * c + 0) * H.stride + ca.x + lane);
+        v[c].y = __ldg(H.tri + (3 * c + 1) * H.stride + ca.x + lane);
+        v[c].z = __ldg(H.tri + (3 * c + 2) * H.stride + ca.x + lane);
+      }
+      stage_triangle(v[0], v[1], v[2], S.a, S.ra, lane);
     }
     if (lane < nb) {
       F3 v[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        v[c].x = __ldg(H.tri + (3 * c + 0) * H.stride + cb.x + lane);
-        v[c].y = __ldg(H.tri + (3 * c + 1) * H.stride + cb.x + lane);
-        v[c].z = __ldg(H.tri + (3 * c + 2) * H.stride + cb.x + lane);
-        F3 q = xf_point(X, v[c]);
-        sB[(3 * c + 0) * 32 + lane] = q.x;
-        sB[(3 * c + 1) * 32 + lane] = q.y;
-        sB[(3 * c + 2) * 32 + lane] = q.z;
+        F3 u;
+        u.x = __ldg(H.tri + (3 * c + 0) * H.stride + cb.x + lane);
+        u.y = __ldg(H.tri + (3 * c + 1) * H.stride + cb.x + lane);
+        u.z = __ldg(H.tri + (3 * c + 2) * H.stride + cb.x + lane);
+        v[c] = xf_point(X, u);
       }
+      stage_triangle(v[0], v[1], v[2], S.b, S.rb, lane);
     }
     __syncwarp();
     const float thr = X.tau + X.margin;
     const int total = na * nb;
     const float inv_nb = 1.0f / (float)nb;
+    // pass 1: bounding-sphere cull, survivors compacted into the queue
+    int nq = 0;
     for (int f0 = 0; f0 < total; f0 += 32) {
       int f = f0 + lane;
       bool act = f < total;
       int i = (int)(((float)f + 0.5f) * inv_nb);
       int j = f - i * nb;
       if (!act) { i = 0; j = 0; }
-      F3 p0 = {sA[0 * 32 + i], sA[1 * 32 + i], sA[2 * 32 + i]};
-      F3 p1 = {sA[3 * 32 + i], sA[4 * 32 + i], sA[5 * 32 + i]};
-      F3 p2 = {sA[6 * 32 + i], sA[7 * 32 + i], sA[8 * 32 + i]};
-      F3 q0 = {sB[0 * 32 + j], sB[1 * 32 + j], sB[2 * 32 + j]};
-      F3 q1 = {sB[3 * 32 + j], sB[4 * 32 + j], sB[5 * 32 + j]};
-      F3 q2 = {sB[6 * 32 + j], sB[7 * 32 + j], sB[8 * 32 + j]};
+      float dx = S.a[0][i].w - S.b[0][j].w, dy = S.a[1][i].w - S.b[1][j].w;
+      float dz = S.a[2][i].w - S.b[2][j].w;
+      float lim = S.ra[i] + S.rb[j] + thr;
+      bool keep = act && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
+      unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) S.q[nq + __popc(m & ((1u << lane) - 1u))] = (unsigned short)((i << 5) | j);
+      nq += __popc(m);
+    }
+    spheres.v += lane == 0 ? (unsigned long long)total : 0ull;
+    __syncwarp();
+    // pass 2: penalty sweep + certificate on the queued pairs
+    for (int q0 = 0; q0 < nq; q0 += 32) {
+      int k = q0 + lane;
+      bool act = k < nq;
+      int code = act ? S.q[k] : 0;
+      int i = code >> 5, j = code & 31;
+      float4 a0 = S.a[0][i], a1 = S.a[1][i], a2 = S.a[2][i];
+      float4 b0 = S.b[0][j], b1 = S.b[1][j], b2 = S.b[2][j];
       bool cv = true;
-      float gap = sweep_certificate<CONV>(p0, p1, p2, q0, q1, q2, sc, conv_tol2, &cv, nullptr);
+      float gap;
+      if (sc.n_iter == 4)
+        gap = sweep_certificate<CONV, 4>({a0.x, a0.y, a0.z}, {a1.x, a1.y, a1.z}, {a2.x, a2.y, a2.z},
+                                         {b0.x, b0.y, b0.z}, {b1.x, b1.y, b1.z}, {b2.x, b2.y, b2.z},
+                                         sc, conv_tol2, &cv, nullptr);
+      else
+        gap = sweep_certificate<CONV, 0>({a0.x, a0.y, a0.z}, {a1.x, a1.y, a1.z}, {a2.x, a2.y, a2.z},
+                                         {b0.x, b0.y, b0.z}, {b1.x, b1.y, b1.z}, {b2.x, b2.y, b2.z},
+                                         sc, conv_tol2, &cv, nullptr);
       bool s = act && !(gap > thr);
       tests.add(act);
       ncand.add(s);
@@ -330,6 +382,7 @@ __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restric
     __syncwarp();
   }
   tests.flush(cnt + CNT_STATS + MRDEM_STAT_FINE_TESTS);
+  spheres.flush(cnt + CNT_STATS + MRDEM_STAT_SPHERE_TESTS);
   ncand.flush(cnt + CNT_STATS + MRDEM_STAT_CANDIDATES);
   if (CONV) nodot.flush(cnt + CNT_STATS + MRDEM_STAT_UNCONVERGED);
 }
@@ -645,7 +698,12 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
                                                   c->cap_tiles);
     }
     int tw = prm.tile_warps;
-    size_t smem = (size_t)tw * 18 * 32 * sizeof(float);
+    size_t smem = (size_t)tw * sizeof(TileSmem);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * (int)sizeof(TileSmem));
+      attr_set = true;
+    }
     {
     ProfScope ps(c, K_TILE, s);
     k_tile<true><<<c->n_sms * prm.tile_blocks_per_sm, tw * 32, smem, s>>>(

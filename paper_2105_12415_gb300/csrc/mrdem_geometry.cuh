@@ -266,28 +266,34 @@ struct SweepConst {
   int n_iter;
 };
 
+#ifdef __CUDA_ARCH__
+#define MRDEM_SAT(x) __saturatef(x)
+#else
+#define MRDEM_SAT(x) fminf(fmaxf((x), 0.f), 1.f)
+#endif
+
 // One triangle's penalty half-step; c1 = a_it/(a_it + a_reg),
-// c2 = a_it/(2 a_it + a_reg).
+// c2 = a_it/(2 a_it + a_reg).  a - clamp(a, 0, 1) equals
+// max(0, a-1) - max(0, -a), and it is non-zero exactly when a violates one of
+// its box constraints.
 MRDEM_HD void penalty_step(float& a, float& b, float c1, float c2) {
-  float lo_a = fmaxf(-a, 0.f), hi_a = fmaxf(a - 1.f, 0.f);
-  float lo_b = fmaxf(-b, 0.f), hi_b = fmaxf(b - 1.f, 0.f);
-  float ab1 = a + b - 1.f;
+  float ea = a - MRDEM_SAT(a), eb = b - MRDEM_SAT(b);
+  float ab1 = (a + b) - 1.f;
   float sm = fmaxf(ab1, 0.f);
-  float va = hi_a - lo_a + sm;
-  float vb = hi_b - lo_b + sm;
   bool on = ab1 > 0.f;
-  float ka = (on && (a < 0.f || a > 1.f)) ? c2 : c1;
-  float kb = (on && (b < 0.f || b > 1.f)) ? c2 : c1;
-  a = fmaf(-va, ka, a);
-  b = fmaf(-vb, kb, b);
+  float ka = (on && ea != 0.f) ? c2 : c1;
+  float kb = (on && eb != 0.f) ? c2 : c1;
+  a = fmaf(-(ea + sm), ka, a);
+  b = fmaf(-(eb + sm), kb, b);
 }
 
 // Sweep + certificate for P (vertices p0..p2) against Q.  Returns the lower
 // bound gap (NaN when the final separation vector is zero: no bound).
 // conv_tol2 = (C eps)^2; *converged tells whether the contact point
 // (t1 + t2)/2 moved by at most C eps in the last iteration.  x_out (4 floats)
-// receives the final unknowns when not null.
-template <bool WANT_CONV>
+// receives the final unknowns when not null.  NIT > 0 fixes the iteration
+// count at compile time (the loop unrolls); NIT = 0 takes sc.n_iter.
+template <bool WANT_CONV, int NIT = 0>
 MRDEM_HD float sweep_certificate(V3<float> p0, V3<float> p1, V3<float> p2, V3<float> q0,
                                  V3<float> q1, V3<float> q2, const SweepConst& sc,
                                  float conv_tol2, bool* converged, float* x_out) {
@@ -300,12 +306,18 @@ MRDEM_HD float sweep_certificate(V3<float> p0, V3<float> p1, V3<float> p2, V3<fl
   float c1 = MRDEM_DIV(ait, ait + areg), c2 = MRDEM_DIV(ait, fmaf(2.f, ait, areg));
   float a1 = 0.f, b1 = 0.f, a2 = 0.f, b2 = 0.f;
   float pa1 = 0.f, pb1 = 0.f, pa2 = 0.f, pb2 = 0.f;
+  const int n_iter = NIT > 0 ? NIT : sc.n_iter;
   V3<float> r;
-  for (int it = 0; it < sc.n_iter; ++it) {
-    if (WANT_CONV) { pa1 = a1; pb1 = b1; pa2 = a2; pb2 = b2; }
-    r.x = fmaf(-b2, f2.x, fmaf(-a2, f1.x, fmaf(b1, e2.x, fmaf(a1, e1.x, d0.x))));
-    r.y = fmaf(-b2, f2.y, fmaf(-a2, f1.y, fmaf(b1, e2.y, fmaf(a1, e1.y, d0.y))));
-    r.z = fmaf(-b2, f2.z, fmaf(-a2, f1.z, fmaf(b1, e2.z, fmaf(a1, e1.z, d0.z))));
+#pragma unroll
+  for (int it = 0; it < n_iter; ++it) {
+    if (WANT_CONV && it == n_iter - 1) { pa1 = a1; pb1 = b1; pa2 = a2; pb2 = b2; }
+    if (it == 0) {
+      r = d0;  // the start x = 0 of Algorithm 4
+    } else {
+      r.x = fmaf(-b2, f2.x, fmaf(-a2, f1.x, fmaf(b1, e2.x, fmaf(a1, e1.x, d0.x))));
+      r.y = fmaf(-b2, f2.y, fmaf(-a2, f1.y, fmaf(b1, e2.y, fmaf(a1, e1.y, d0.y))));
+      r.z = fmaf(-b2, f2.z, fmaf(-a2, f1.z, fmaf(b1, e2.z, fmaf(a1, e1.z, d0.z))));
+    }
     float g1 = dot(r, e1), g2 = dot(r, e2), g3 = dot(r, f1), g4 = dot(r, f2);
     a1 = fmaf(-g1, i1, a1);
     b1 = fmaf(-g2, i2, b1);
@@ -331,10 +343,10 @@ MRDEM_HD float sweep_certificate(V3<float> p0, V3<float> p1, V3<float> p2, V3<fl
 #else
   float inv = 1.f / sqrtf(dot(r, r));
 #endif
-  V3<float> u = inv * r;
-  float mp = fminf(dot(u, p0), fminf(dot(u, p1), dot(u, p2)));
-  float mq = fmaxf(dot(u, q0), fmaxf(dot(u, q1), dot(u, q2)));
-  return mp - mq;
+  // support gap along r, normalised once at the end
+  float mp = fminf(dot(r, p0), fminf(dot(r, p1), dot(r, p2)));
+  float mq = fmaxf(dot(r, q0), fmaxf(dot(r, q1), dot(r, q2)));
+  return (mp - mq) * inv;
 }
 
 }  // namespace mrdem
