@@ -66,8 +66,9 @@ typedef struct CUstream_st* mrdem_stream; /* same type as cudaStream_t */
 #define MRDEM_STAT_CANDIDATES 18 /* fine pairs not pruned by the sweep's certificate */
 #define MRDEM_STAT_UNCONVERGED 19 /* candidates whose sweep had not converged (the paper's odot) */
 #define MRDEM_STAT_CONTACTS 20   /* contacts written (or that would have been written) */
-#define MRDEM_STAT_FP64 21       /* candidates re-evaluated in FP64 */
-#define MRDEM_STAT_SPHERE_TESTS 22 /* fine pairs of the leaf tiles (bounding-sphere cull) */
+#define MRDEM_STAT_FP64 21       /* candidates given the full FP64 comparison-based test */
+#define MRDEM_STAT_SPHERE_TESTS 22 /* fine pairs given the bounding-sphere test */
+#define MRDEM_STAT_FINE_SURROGATE 23 /* fine triangles tested against the other leaf's surrogate */
 #define MRDEM_STAT_COUNT 32
 
 typedef struct mrdem_params {
@@ -249,7 +250,10 @@ int mrdem_detect_plain_fp64(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pa
  *     relative to P's first vertex; FP64: as given).  feature codes: k (0..2)
  *     vertex k of P vs Q; 3+k vertex k of Q vs P; 6+3i+j edge i of P vs edge j
  *     of Q (edge i joins vertex i and i+1 mod 3); 100+i edge i of P crosses Q;
- *     103+j edge j of Q crosses P.
+ *     103+j edge j of Q crosses P.  In the FP32 form the code is -1 for a
+ *     pair decided to be within 2 eps by the float test (its value finished
+ *     in double), and -2 for a pair the float test decided to be beyond
+ *     2 eps (the reported distance is then the full double result).
  *   sweep_x [n*4], sweep_gap [n], sweep_conv [n]: the FP32 penalty sweep of
  *     Eq. 3/4 (ctx's constants) on the float-rounded triangles: final
  *     barycentric unknowns (a1, b1, a2, b2), the certified lower bound of the

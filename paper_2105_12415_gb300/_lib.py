@@ -31,6 +31,7 @@ MRDEM_STAT_UNCONVERGED = 19
 MRDEM_STAT_CONTACTS = 20
 MRDEM_STAT_FP64 = 21
 MRDEM_STAT_SPHERE_TESTS = 22
+MRDEM_STAT_FINE_SURROGATE = 23
 MRDEM_STAT_COUNT = 32
 
 

@@ -424,8 +424,9 @@ int mrdem_triangle_distance(mrdem_ctx* c, int64_t n, const double* P, const doub
                                   sconv, (cudaStream_t)s);
 }
 
-static const char* kKernelNames[K_COUNT] = {"k_setup", "k_level", "k_tile", "k_exact",
-                                            "k_forces", "k_grad", "k_plain", "k_tridist"};
+static const char* kKernelNames[K_COUNT] = {"k_setup",  "k_level", "k_tile",  "k_exact",
+                                            "k_exact64", "k_forces", "k_grad", "k_plain",
+                                            "k_tridist"};
 
 int mrdem_profile(mrdem_ctx* c, int32_t enable) {
   if (!c) return MRDEM_ERR_INVALID;

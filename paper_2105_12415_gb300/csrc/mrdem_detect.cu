@@ -187,6 +187,10 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
 
 // ---------------------------------------------------------------------------
 // k_level: one warp per node pair of list `level`; tests its child pairs.
+// Each child surrogate is staged with a bounding sphere of its eps-free
+// environment (centroid, largest vertex distance + delta); child pairs whose
+// spheres are farther apart than 2 eps are dropped, the rest are compacted and
+// given the penalty sweep + certificate against delta_a + delta_b + 2 eps.
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_level(HierDev H, const PairXf* __restrict__ xf,
                                                       SweepConst sc, const int3* __restrict__ in,
@@ -195,8 +199,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_level(HierDev H, const PairXf* _
                                                       unsigned long long* status,
                                                       int64_t cap_level, int64_t cap_tiles) {
   __shared__ float4 sgeo[WARPS][16][3];
+  __shared__ float4 ssph[WARPS][16];
   __shared__ int sleaf[WARPS][16];
   __shared__ int snode[WARPS][16];
+  __shared__ unsigned char squeue[WARPS][64];
   const int w = threadIdx.x >> 5, lane = lane_id();
   int64_t n_in = (int64_t)cnt[CNT_LEVEL + level];
   if (n_in > cap_level) n_in = cap_level;
@@ -209,30 +215,50 @@ __global__ void __launch_bounds__(WARPS * 32) k_level(HierDev H, const PairXf* _
     int2 ca = H.node_child[it.y], cb = H.node_child[it.z];
     int na = ca.y > 0 ? ca.y : 1, abeg = ca.y > 0 ? ca.x : it.y;
     int nb = cb.y > 0 ? cb.y : 1, bbeg = cb.y > 0 ? cb.x : it.z;
-    if (lane < na) {
-      int node = abeg + lane;
-      sgeo[w][lane][0] = H.node_geo[3 * node];
-      sgeo[w][lane][1] = H.node_geo[3 * node + 1];
-      sgeo[w][lane][2] = H.node_geo[3 * node + 2];
-      sleaf[w][lane] = H.node_child[node].y < 0;
-      snode[w][lane] = node;
-    } else if (lane >= 8 && lane < 8 + nb) {
-      int node = bbeg + lane - 8;
+    bool stage = lane < na || (lane >= 8 && lane < 8 + nb);
+    if (stage) {
+      int node = lane < 8 ? abeg + lane : bbeg + lane - 8;
       float4 g0 = H.node_geo[3 * node], g1 = H.node_geo[3 * node + 1], g2 = H.node_geo[3 * node + 2];
-      F3 q0 = xf_point(X, {g0.x, g0.y, g0.z}), q1 = xf_point(X, {g1.x, g1.y, g1.z});
-      F3 q2 = xf_point(X, {g2.x, g2.y, g2.z});
-      sgeo[w][lane][0] = make_float4(q0.x, q0.y, q0.z, g0.w);
-      sgeo[w][lane][1] = make_float4(q1.x, q1.y, q1.z, 0.f);
-      sgeo[w][lane][2] = make_float4(q2.x, q2.y, q2.z, 0.f);
+      F3 p0 = {g0.x, g0.y, g0.z}, p1 = {g1.x, g1.y, g1.z}, p2 = {g2.x, g2.y, g2.z};
+      if (lane >= 8) {
+        p0 = xf_point(X, p0);
+        p1 = xf_point(X, p1);
+        p2 = xf_point(X, p2);
+      }
+      sgeo[w][lane][0] = make_float4(p0.x, p0.y, p0.z, g0.w);
+      sgeo[w][lane][1] = make_float4(p1.x, p1.y, p1.z, 0.f);
+      sgeo[w][lane][2] = make_float4(p2.x, p2.y, p2.z, 0.f);
+      F3 c = (1.f / 3.f) * ((p0 + p1) + p2);
+      F3 d0 = p0 - c, d1 = p1 - c, d2 = p2 - c;
+      float r = sqrtf(fmaxf(dot(d0, d0), fmaxf(dot(d1, d1), dot(d2, d2)))) * (1.f + 1e-6f) + g0.w;
+      ssph[w][lane] = make_float4(c.x, c.y, c.z, r);
       sleaf[w][lane] = H.node_child[node].y < 0;
       snode[w][lane] = node;
     }
     __syncwarp();
-    int total = na * nb;
+    const int total = na * nb;
+    const float thr = X.tau + X.margin;
+    // sphere test of all child pairs, survivors queued
+    int nq = 0;
     for (int f0 = 0; f0 < total; f0 += 32) {
       int f = f0 + lane;
       bool act = f < total;
       int i = act ? f / nb : 0, j = act ? f - (f / nb) * nb : 0;
+      float4 p = ssph[w][i], q = ssph[w][8 + j];
+      float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+      float lim = (p.w + q.w) + thr;
+      bool keep = act && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
+      unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) squeue[w][nq + __popc(m & ((1u << lane) - 1u))] = (unsigned char)((i << 3) | j);
+      nq += __popc(m);
+      tests.add(act);
+    }
+    __syncwarp();
+    for (int q0 = 0; q0 < nq; q0 += 32) {
+      int k = q0 + lane;
+      bool act = k < nq;
+      int code = act ? squeue[w][k] : 0;
+      int i = code >> 3, j = code & 7;
       bool s = false;
       if (act) {
         float4 a0 = sgeo[w][i][0], a1 = sgeo[w][i][1], a2 = sgeo[w][i][2];
@@ -241,11 +267,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_level(HierDev H, const PairXf* _
         float gap = sweep_certificate<false>({a0.x, a0.y, a0.z}, {a1.x, a1.y, a1.z}, {a2.x, a2.y, a2.z},
                                              {b0.x, b0.y, b0.z}, {b1.x, b1.y, b1.z}, {b2.x, b2.y, b2.z},
                                              sc, 0.f, &cv, nullptr);
-        s = !(gap > a0.w + b0.w + X.tau + X.margin);
+        s = !(gap > a0.w + b0.w + thr);
       }
       bool leaves = act && sleaf[w][i] && sleaf[w][8 + j];
       int3 child = make_int3(it.x, act ? snode[w][i] : 0, act ? snode[w][8 + j] : 0);
-      tests.add(act);
       surv.add(s);
       warp_append(s && leaves, child, tiles, cnt + CNT_TILES, cap_tiles, status + ST_REQ_TILES);
       warp_append(s && !leaves, child, out, cnt + CNT_LEVEL + level + 1, cap_level,
@@ -268,21 +293,36 @@ __global__ void __launch_bounds__(WARPS * 32) k_level(HierDev H, const PairXf* _
 // certificate over the queue, one fine pair per lane.
 constexpr int kTileQueue = 1024;  // 32 x 32 products
 struct TileSmem {
-  float4 a[3][32];  // A: v0, v1, v2 (xyz), w = centroid x / y / z
-  float4 b[3][32];
-  float ra[32], rb[32];
-  unsigned short q[kTileQueue];
+  float4 a[3][32];  // A: v0, v1, v2 (xyz)
+  float4 b[3][32];  // B (in A's frame)
+  float4 sa[32];    // bounding spheres: centroid xyz, radius
+  float4 sb[32];
+  unsigned char ka[32], kb[32];  // triangles kept by the fine-vs-surrogate test
+  unsigned short q[kTileQueue];  // fine pairs kept by the sphere test
 };
 
-__device__ __forceinline__ void stage_triangle(F3 v0, F3 v1, F3 v2, float4 (*dst)[32], float* rad,
-                                               int lane) {
+// Stage one fine triangle: vertices and bounding sphere (centroid, largest
+// vertex distance, rounded up).
+__device__ __forceinline__ float4 stage_triangle(F3 v0, F3 v1, F3 v2, float4 (*dst)[32], int lane) {
   F3 c = (1.f / 3.f) * ((v0 + v1) + v2);
   F3 d0 = v0 - c, d1 = v1 - c, d2 = v2 - c;
   float r2 = fmaxf(dot(d0, d0), fmaxf(dot(d1, d1), dot(d2, d2)));
-  dst[0][lane] = make_float4(v0.x, v0.y, v0.z, c.x);
-  dst[1][lane] = make_float4(v1.x, v1.y, v1.z, c.y);
-  dst[2][lane] = make_float4(v2.x, v2.y, v2.z, c.z);
-  rad[lane] = sqrtf(r2) * (1.f + 1e-6f);
+  dst[0][lane] = make_float4(v0.x, v0.y, v0.z, 0.f);
+  dst[1][lane] = make_float4(v1.x, v1.y, v1.z, 0.f);
+  dst[2][lane] = make_float4(v2.x, v2.y, v2.z, 0.f);
+  return make_float4(c.x, c.y, c.z, sqrtf(r2) * (1.f + 1e-6f));
+}
+
+// Is the sphere (c, r) within `lim` + r of the surrogate triangle (g0,g1,g2)?
+// The distance from the centre to the triangle minus r bounds the distance
+// of anything inside the sphere from below.
+__device__ __forceinline__ bool sphere_near_triangle(float4 s, F3 g0, F3 g1, F3 g2, float lim) {
+  float w[3];
+  F3 c = {s.x, s.y, s.z};
+  F3 q = closest_on_triangle(c, g0, g1, g2, w);
+  F3 d = c - q;
+  float l = lim + s.w;
+  return dot(d, d) <= l * l;
 }
 
 template <bool CONV>
@@ -298,11 +338,13 @@ __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restric
   int64_t n_tiles = (int64_t)cnt[CNT_TILES];
   if (n_tiles > cap_tiles) n_tiles = cap_tiles;
   WarpCount tests, spheres, ncand, nodot;
+  unsigned long long ntile = 0, nfvs = 0;
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(cnt + CNT_FETCH + kMaxLevels, 1ull);
     t = __shfl_sync(0xffffffffu, t, 0);
     if ((int64_t)t >= n_tiles) break;
+    ++ntile;
     int3 it = tiles[t];
     PairXf X;
     load_pairxf(xf, it.x, X);
@@ -310,6 +352,17 @@ __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restric
     float conv_tol2 = ce * ce;
     int2 ca = H.node_child[it.y], cb = H.node_child[it.z];
     int na = -ca.y, nb = -cb.y;
+    const float thr = X.tau + X.margin;
+    // surrogates of the two leaves (B's moved into A's frame) with slack
+    float4 ga0 = H.node_geo[3 * it.y], ga1 = H.node_geo[3 * it.y + 1], ga2 = H.node_geo[3 * it.y + 2];
+    float4 gb0 = H.node_geo[3 * it.z], gb1 = H.node_geo[3 * it.z + 1], gb2 = H.node_geo[3 * it.z + 2];
+    F3 A0 = {ga0.x, ga0.y, ga0.z}, A1 = {ga1.x, ga1.y, ga1.z}, A2 = {ga2.x, ga2.y, ga2.z};
+    F3 B0 = xf_point(X, {gb0.x, gb0.y, gb0.z}), B1 = xf_point(X, {gb1.x, gb1.y, gb1.z});
+    F3 B2 = xf_point(X, {gb2.x, gb2.y, gb2.z});
+    // stage the fine triangles; each one is tested against the other leaf's
+    // surrogate (a fine triangle against a surrogate, as in Algorithm 5 when
+    // one side is already fine)
+    bool keep_a = false, keep_b = false;
     if (lane < na) {
       F3 v[3];
 #pragma unroll
@@ -318,7 +371,9 @@ __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restric
         v[c].y = __ldg(H.tri + (3 * c + 1) * H.stride + ca.x + lane);
         v[c].z = __ldg(H.tri + (3 * c + 2) * H.stride + ca.x + lane);
       }
-      stage_triangle(v[0], v[1], v[2], S.a, S.ra, lane);
+      float4 sp = stage_triangle(v[0], v[1], v[2], S.a, lane);
+      S.sa[lane] = sp;
+      keep_a = sphere_near_triangle(sp, B0, B1, B2, gb0.w + thr);
     }
     if (lane < nb) {
       F3 v[3];
@@ -330,23 +385,30 @@ __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restric
         u.z = __ldg(H.tri + (3 * c + 2) * H.stride + cb.x + lane);
         v[c] = xf_point(X, u);
       }
-      stage_triangle(v[0], v[1], v[2], S.b, S.rb, lane);
+      float4 sp = stage_triangle(v[0], v[1], v[2], S.b, lane);
+      S.sb[lane] = sp;
+      keep_b = sphere_near_triangle(sp, A0, A1, A2, ga0.w + thr);
     }
+    unsigned ma = __ballot_sync(0xffffffffu, keep_a), mb = __ballot_sync(0xffffffffu, keep_b);
+    if (keep_a) S.ka[__popc(ma & ((1u << lane) - 1u))] = (unsigned char)lane;
+    if (keep_b) S.kb[__popc(mb & ((1u << lane) - 1u))] = (unsigned char)lane;
+    const int ka = __popc(ma), kb = __popc(mb);
+    nfvs += (unsigned long long)(na + nb);
     __syncwarp();
-    const float thr = X.tau + X.margin;
-    const int total = na * nb;
-    const float inv_nb = 1.0f / (float)nb;
-    // pass 1: bounding-sphere cull, survivors compacted into the queue
+    const int total = ka * kb;
+    const float inv_kb = 1.0f / (float)(kb > 0 ? kb : 1);
+    // pass 1: bounding-sphere test of the kept products, survivors queued
     int nq = 0;
     for (int f0 = 0; f0 < total; f0 += 32) {
       int f = f0 + lane;
       bool act = f < total;
-      int i = (int)(((float)f + 0.5f) * inv_nb);
-      int j = f - i * nb;
-      if (!act) { i = 0; j = 0; }
-      float dx = S.a[0][i].w - S.b[0][j].w, dy = S.a[1][i].w - S.b[1][j].w;
-      float dz = S.a[2][i].w - S.b[2][j].w;
-      float lim = S.ra[i] + S.rb[j] + thr;
+      int ii = (int)(((float)f + 0.5f) * inv_kb);
+      int jj = f - ii * kb;
+      if (!act) { ii = 0; jj = 0; }
+      int i = S.ka[ii], j = S.kb[jj];
+      float4 p = S.sa[i], q = S.sb[j];
+      float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+      float lim = (p.w + q.w) + thr;
       bool keep = act && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
       unsigned m = __ballot_sync(0xffffffffu, keep);
       if (keep) S.q[nq + __popc(m & ((1u << lane) - 1u))] = (unsigned short)((i << 5) | j);
@@ -381,6 +443,10 @@ __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restric
     }
     __syncwarp();
   }
+  if (lane == 0) {
+    if (ntile) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_TILES, ntile);
+    if (nfvs) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_FINE_SURROGATE, nfvs);
+  }
   tests.flush(cnt + CNT_STATS + MRDEM_STAT_FINE_TESTS);
   spheres.flush(cnt + CNT_STATS + MRDEM_STAT_SPHERE_TESTS);
   ncand.flush(cnt + CNT_STATS + MRDEM_STAT_CANDIDATES);
@@ -388,82 +454,16 @@ __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Final distance of one candidate.  P, Q: FP64 coordinates relative to the
-// origin o (A's frame).  FP64: comparison-based in double.  FP32: the same in
-// float on the rounded local coordinates; the pair is decided in float when
-// its distance is clear of 2 eps by more than the float error bound, and the
-// winning feature's distance is then re-evaluated in double; pairs near the
-// threshold, near ties between features and near-parallel edge minima go to
-// the full double evaluation.
-struct CandResult {
-  double d;
-  D3 pa, pb;
-  int feature;
-  bool fp64_full;
-};
-
-__device__ __forceinline__ void eval_feature64(const D3 P[3], const D3 Q[3], int f, CandResult& r,
-                                               bool& ok) {
-  double w[3];
-  ok = true;
-  if (f < 3) {
-    D3 q = closest_on_triangle(P[f], Q[0], Q[1], Q[2], w);
-    r.pa = P[f]; r.pb = q;
-  } else if (f < 6) {
-    D3 p = closest_on_triangle(Q[f - 3], P[0], P[1], P[2], w);
-    r.pa = p; r.pb = Q[f - 3];
-  } else if (f < 15) {
-    int i = (f - 6) / 3, j = (f - 6) % 3;
-    int i1 = i == 2 ? 0 : i + 1, j1 = j == 2 ? 0 : j + 1;
-    double s, t;
-    bool par;
-    closest_segments(P[i], P[i1], Q[j], Q[j1], &s, &t, &par);
-    r.pa = P[i] + s * (P[i1] - P[i]);
-    r.pb = Q[j] + t * (Q[j1] - Q[j]);
-  } else {
-    ok = false;  // crossings are re-tested in full
-    return;
-  }
-  D3 dv = r.pa - r.pb;
-  r.d = sqrt(dot(dv, dv));
-  r.feature = f;
-}
-
-template <int PREC>
-__device__ __forceinline__ bool candidate_distance(const D3 P[3], const D3 Q[3], double tau,
-                                                   CandResult& r) {
-  r.fp64_full = false;
-  if (PREC == MRDEM_PREC_FP32) {
-    F3 Pf[3], Qf[3];
-    float L = 0.f;
-    for (int k = 0; k < 3; ++k) {
-      Pf[k] = {(float)P[k].x, (float)P[k].y, (float)P[k].z};
-      Qf[k] = {(float)Q[k].x, (float)Q[k].y, (float)Q[k].z};
-      L = fmaxf(L, fmaxf(fmaxf(fabsf(Pf[k].x), fabsf(Pf[k].y)), fabsf(Pf[k].z)));
-      L = fmaxf(L, fmaxf(fmaxf(fabsf(Qf[k].x), fabsf(Qf[k].y)), fabsf(Qf[k].z)));
-    }
-    float second2;
-    TriTriResult<float> rf = tri_tri_distance_ranked(Pf, Qf, &second2);
-    double err = ldexp((double)L, -15);
-    double d32 = rf.d;
-    if (d32 > tau + err) return false;  // certainly no contact
-    bool full = rf.near_parallel || fabs(d32 - tau) <= err || rf.feature >= 100 ||
-                (double)sqrtf(second2) - d32 <= 2.0 * err;
-    if (!full) {
-      bool ok;
-      eval_feature64(P, Q, rf.feature, r, ok);
-      if (ok) return r.d <= tau;
-    }
-    r.fp64_full = true;
-  }
-  TriTriResult<double> rd = tri_tri_distance(P, Q);
-  r.d = rd.d;
-  r.pa = rd.pa;
-  r.pb = rd.pb;
-  r.feature = rd.feature;
-  return r.d <= tau;
-}
-
+// Final distance of the candidates.
+//   FP64 form: the comparison-based distance in double for every candidate.
+//   FP32 form: the fifteen sub-tests in float on coordinates relative to A's
+//   first vertex (rounded from double), with an a-priori error bound
+//   err = 2^-15 max|coordinate|.  Pairs clearly beyond 2 eps are dropped;
+//   every sub-test within 2 err of the float minimum is re-evaluated in
+//   double and the smallest value is the distance (the true minimiser is
+//   always among them, so this equals the double comparison-based result).
+//   Crossing or nearly touching pairs go to a fallback list that the FP64
+//   kernel finishes.
 __device__ __forceinline__ void load_tri64(const HierDev& H, int slot, D3 T[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -473,63 +473,114 @@ __device__ __forceinline__ void load_tri64(const HierDev& H, int slot, D3 T[3]) 
   }
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(128) k_exact(HierDev H, const PairXf64* __restrict__ xf64,
-                                               const int3* __restrict__ cands,
-                                               unsigned long long* cnt, unsigned long long* status,
-                                               int64_t cap_cands, mrdem_contacts out) {
+__device__ __forceinline__ void cand_geom(const HierDev& H, const PairXf64& X, int3 c, CandGeom& g) {
+  D3 Pb[3], Qb[3];
+  load_tri64(H, c.y, Pb);
+  load_tri64(H, c.z, Qb);
+  g.o = Pb[0];
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    g.P[v] = Pb[v] - g.o;
+    g.Q[v] = xf_point64(X.R, X.t, Qb[v]) - g.o;
+  }
+  g.tau = 2.0 * X.eps;
+}
+
+__device__ __forceinline__ void write_contact(const HierDev& H, const mrdem_contacts& out,
+                                              unsigned long long* status, bool hit, int pair,
+                                              int sa, int sb, double d, D3 pa, D3 pb) {
+  unsigned m = __ballot_sync(0xffffffffu, hit);
+  if (!m) return;
+  int leader = __ffs(m) - 1;
+  unsigned long long b = 0;
+  if ((int)lane_id() == leader) b = atomicAdd((unsigned long long*)out.count, (unsigned long long)__popc(m));
+  b = __shfl_sync(0xffffffffu, b, leader);
+  if (!hit) return;
+  unsigned long long idx = b + __popc(m & ((1u << lane_id()) - 1u));
+  if ((int64_t)idx < out.capacity) {
+    out.pair[idx] = pair;
+    out.tri_a[idx] = H.slot_tri[sa];
+    out.tri_b[idx] = H.slot_tri[sb];
+    out.dist[idx] = d;
+    out.point_a[3 * idx] = pa.x; out.point_a[3 * idx + 1] = pa.y; out.point_a[3 * idx + 2] = pa.z;
+    out.point_b[3 * idx] = pb.x; out.point_b[3 * idx + 1] = pb.y; out.point_b[3 * idx + 2] = pb.z;
+  } else {
+    atomicMax(status + ST_REQ_CONTACTS, idx + 1);
+  }
+}
+
+// FP32 form, first pass over the candidates.
+__global__ void __launch_bounds__(128) k_exact32(HierDev H, const PairXf64* __restrict__ xf64,
+                                                 const int3* __restrict__ cands,
+                                                 unsigned long long* cnt,
+                                                 unsigned long long* status, int64_t cap_cands,
+                                                 int3* fallback, int64_t cap_fallback,
+                                                 mrdem_contacts out) {
   int64_t n = (int64_t)cnt[CNT_CANDS];
   if (n > cap_cands) n = cap_cands;
-  WarpCount ncon, n64;
+  WarpCount ncon;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     int64_t k = base + threadIdx.x;
-    bool is_contact = false, full = false;
-    CandResult r;
+    int res = 0;
     int3 c = make_int3(0, 0, 0);
+    double d = 0;
+    D3 pa = {0, 0, 0}, pb = {0, 0, 0};
+    const PairXf64* X = nullptr;
     if (k < n) {
       c = cands[k];
-      const PairXf64& X = xf64[c.x];
-      D3 Pb[3], Qb[3], P[3], Q[3];
-      load_tri64(H, c.y, Pb);
-      load_tri64(H, c.z, Qb);
-      D3 o = Pb[0];
-      for (int v = 0; v < 3; ++v) {
-        P[v] = Pb[v] - o;
-        Q[v] = xf_point64(X.R, X.t, Qb[v]) - o;
-      }
-      is_contact = candidate_distance<PREC>(P, Q, 2.0 * X.eps, r);
-      full = r.fp64_full;
-      if (is_contact) {
-        r.pa = xf_point64(X.RA, X.tA, r.pa + o);
-        r.pb = xf_point64(X.RA, X.tA, r.pb + o);
+      X = xf64 + c.x;
+      CandGeom g;
+      cand_geom(H, *X, c, g);
+      res = cand_fp32(g, d, pa, pb);
+      if (res == 1) {
+        pa = xf_point64(X->RA, X->tA, pa + g.o);
+        pb = xf_point64(X->RA, X->tA, pb + g.o);
       }
     }
-    ncon.add(is_contact);
-    if (PREC == MRDEM_PREC_FP32) n64.add(full);
-    unsigned m = __ballot_sync(0xffffffffu, is_contact);
-    if (m) {
-      int leader = __ffs(m) - 1;
-      unsigned long long b = 0;
-      if ((int)lane_id() == leader) b = atomicAdd((unsigned long long*)out.count, (unsigned long long)__popc(m));
-      b = __shfl_sync(0xffffffffu, b, leader);
-      if (is_contact) {
-        unsigned long long idx = b + __popc(m & ((1u << lane_id()) - 1u));
-        if ((int64_t)idx < out.capacity) {
-          out.pair[idx] = c.x;
-          out.tri_a[idx] = H.slot_tri[c.y];
-          out.tri_b[idx] = H.slot_tri[c.z];
-          out.dist[idx] = r.d;
-          out.point_a[3 * idx] = r.pa.x; out.point_a[3 * idx + 1] = r.pa.y; out.point_a[3 * idx + 2] = r.pa.z;
-          out.point_b[3 * idx] = r.pb.x; out.point_b[3 * idx + 1] = r.pb.y; out.point_b[3 * idx + 2] = r.pb.z;
-        } else {
-          atomicMax(status + ST_REQ_CONTACTS, idx + 1);
-        }
-      }
-    }
+    ncon.add(res == 1);
+    write_contact(H, out, status, res == 1, c.x, c.y, c.z, d, pa, pb);
+    warp_append(res < 0, c, fallback, cnt + CNT_FALLBACK, cap_fallback, status + ST_REQ_CANDS);
   }
   ncon.flush(cnt + CNT_STATS + MRDEM_STAT_CONTACTS);
-  if (PREC == MRDEM_PREC_FP32) n64.flush(cnt + CNT_STATS + MRDEM_STAT_FP64);
+}
+
+// Full FP64 comparison-based distance for every entry of a list (the FP64
+// form's candidates, or the FP32 form's fallback list).
+__global__ void __launch_bounds__(128) k_exact64(HierDev H, const PairXf64* __restrict__ xf64,
+                                                 const int3* __restrict__ list,
+                                                 unsigned long long* cnt, int count_slot,
+                                                 int64_t cap, unsigned long long* status,
+                                                 int stat_slot, mrdem_contacts out) {
+  int64_t n = (int64_t)cnt[count_slot];
+  if (n > cap) n = cap;
+  WarpCount ncon, nall;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    int64_t k = base + threadIdx.x;
+    bool hit = false;
+    int3 c = make_int3(0, 0, 0);
+    double d = 0;
+    D3 pa = {0, 0, 0}, pb = {0, 0, 0};
+    if (k < n) {
+      c = list[k];
+      const PairXf64& X = xf64[c.x];
+      CandGeom g;
+      cand_geom(H, X, c, g);
+      TriTriResult<double> r = tri_tri_distance(g.P, g.Q);
+      hit = r.d <= g.tau;
+      d = r.d;
+      if (hit) {
+        pa = xf_point64(X.RA, X.tA, r.pa + g.o);
+        pb = xf_point64(X.RA, X.tA, r.pb + g.o);
+      }
+    }
+    ncon.add(hit);
+    nall.add(k < n);
+    write_contact(H, out, status, hit, c.x, c.y, c.z, d, pa, pb);
+  }
+  ncon.flush(cnt + CNT_STATS + MRDEM_STAT_CONTACTS);
+  if (stat_slot >= 0) nall.flush(cnt + CNT_STATS + stat_slot);
 }
 
 // ---------------------------------------------------------------------------
@@ -594,42 +645,46 @@ __global__ void k_tridist(int64_t n, const double* __restrict__ Pin, const doubl
                           int32_t* sconv) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-    D3 P[3], Q[3];
+    CandGeom g;
     for (int v = 0; v < 3; ++v) {
-      P[v] = {Pin[9 * k + 3 * v], Pin[9 * k + 3 * v + 1], Pin[9 * k + 3 * v + 2]};
-      Q[v] = {Qin[9 * k + 3 * v], Qin[9 * k + 3 * v + 1], Qin[9 * k + 3 * v + 2]};
+      g.P[v] = {Pin[9 * k + 3 * v], Pin[9 * k + 3 * v + 1], Pin[9 * k + 3 * v + 2]};
+      g.Q[v] = {Qin[9 * k + 3 * v], Qin[9 * k + 3 * v + 1], Qin[9 * k + 3 * v + 2]};
     }
-    D3 o = P[0];
-    for (int v = 0; v < 3; ++v) { P[v] = P[v] - o; Q[v] = Q[v] - o; }
+    g.o = g.P[0];
+    for (int v = 2; v >= 0; --v) { g.P[v] = g.P[v] - g.o; g.Q[v] = g.Q[v] - g.o; }
     double e = eps[k];
+    g.tau = 2.0 * e;
     if (sx || sgap || sconv) {
       F3 Pf[3], Qf[3];
       for (int v = 0; v < 3; ++v) {
-        Pf[v] = {(float)P[v].x, (float)P[v].y, (float)P[v].z};
-        Qf[v] = {(float)Q[v].x, (float)Q[v].y, (float)Q[v].z};
+        Pf[v] = {(float)g.P[v].x, (float)g.P[v].y, (float)g.P[v].z};
+        Qf[v] = {(float)g.Q[v].x, (float)g.Q[v].y, (float)g.Q[v].z};
       }
       float ce = conv_c * (float)e;
       bool cv;
       float x[4];
-      float g = sweep_certificate<true>(Pf[0], Pf[1], Pf[2], Qf[0], Qf[1], Qf[2], sc, ce * ce, &cv, x);
+      float gp = sweep_certificate<true>(Pf[0], Pf[1], Pf[2], Qf[0], Qf[1], Qf[2], sc, ce * ce, &cv, x);
       if (sx) for (int q = 0; q < 4; ++q) sx[4 * k + q] = x[q];
-      if (sgap) sgap[k] = g;
+      if (sgap) sgap[k] = gp;
       if (sconv) sconv[k] = cv;
     }
     if (dist || pa || pb || feature) {
-      CandResult r;
-      // decide with threshold 2 eps like the pipeline; when the float path
-      // rejects a pair (clearly beyond 2 eps) report its full FP64 distance
-      bool hit = candidate_distance<PREC>(P, Q, 2.0 * e, r);
-      if (!hit && PREC == MRDEM_PREC_FP32 && !r.fp64_full) {
-        TriTriResult<double> rd = tri_tri_distance(P, Q);
-        r.d = rd.d; r.pa = rd.pa; r.pb = rd.pb; r.feature = rd.feature;
+      double d = 0;
+      D3 a = {0, 0, 0}, b = {0, 0, 0};
+      int f = -1;
+      int res = PREC == MRDEM_PREC_FP32 ? cand_fp32(g, d, a, b) : -1;
+      if (res != 1) {
+        // FP64 form, fallback, or a pair the float test put beyond 2 eps:
+        // report the full double result (feature -2 marks the float rejection)
+        TriTriResult<double> r = tri_tri_distance(g.P, g.Q);
+        d = r.d; a = r.pa; b = r.pb; f = res == 0 ? -2 : r.feature;
       }
-      if (dist) dist[k] = r.d;
-      D3 a = r.pa + o, b = r.pb + o;
+      if (dist) dist[k] = d;
+      a = a + g.o;
+      b = b + g.o;
       if (pa) { pa[3 * k] = a.x; pa[3 * k + 1] = a.y; pa[3 * k + 2] = a.z; }
       if (pb) { pb[3 * k] = b.x; pb[3 * k + 1] = b.y; pb[3 * k + 2] = b.z; }
-      if (feature) feature[k] = r.feature;
+      if (feature) feature[k] = f;
     }
   }
 }
@@ -711,13 +766,22 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
         c->cap_cands, eps);
     }
     int et = prm.exact_threads;
-    ProfScope ps(c, K_EXACT, s);
-    if (precision == MRDEM_PREC_FP64)
-      k_exact<MRDEM_PREC_FP64><<<c->n_sms * 8, et, 0, s>>>(H, c->xf64, c->cands, c->counters,
-                                                             c->status, c->cap_cands, *out);
-    else
-      k_exact<MRDEM_PREC_FP32><<<c->n_sms * 8, et, 0, s>>>(H, c->xf64, c->cands, c->counters,
-                                                             c->status, c->cap_cands, *out);
+    if (precision == MRDEM_PREC_FP64) {
+      ProfScope ps(c, K_EXACT, s);
+      k_exact64<<<c->n_sms * 8, et, 0, s>>>(H, c->xf64, c->cands, c->counters, CNT_CANDS,
+                                             c->cap_cands, c->status, MRDEM_STAT_FP64, *out);
+    } else {
+      {
+        ProfScope ps(c, K_EXACT, s);
+        // the level lists are free once the tiles are done: reuse one as the fallback list
+        k_exact32<<<c->n_sms * 8, et, 0, s>>>(H, c->xf64, c->cands, c->counters, c->status,
+                                               c->cap_cands, c->level_list[0], c->cap_level, *out);
+      }
+      ProfScope ps(c, K_EXACT64, s);
+      k_exact64<<<c->n_sms * 4, et, 0, s>>>(H, c->xf64, c->level_list[0], c->counters,
+                                             CNT_FALLBACK, c->cap_level, c->status,
+                                             MRDEM_STAT_FP64, *out);
+    }
   }
   if (stats)
     cudaMemcpyAsync(stats, c->counters + CNT_STATS, sizeof(int64_t) * MRDEM_STAT_COUNT,

@@ -249,6 +249,120 @@ MRDEM_HD TriTriResult<T> tri_tri_distance_ranked(const V3<T> P[3], const V3<T> Q
   return tri_tri_distance_impl<T, true>(P, Q, second2);
 }
 
+// All fifteen sub-tests of the comparison-based distance without early exit:
+// d2[k] is the squared distance of sub-test k (k = feature code 0..14).
+// Returns whether an edge of one triangle crosses the other (the six
+// edge-against-triangle tests).
+template <typename T>
+MRDEM_HD bool tri_tri_subtests(const V3<T> P[3], const V3<T> Q[3], T d2[15]) {
+  T w[3], t;
+  bool crossing = false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    int i1 = i == 2 ? 0 : i + 1;
+    crossing |= segment_crosses(P[i], P[i1], Q[0], Q[1], Q[2], &t, w);
+    crossing |= segment_crosses(Q[i], Q[i1], P[0], P[1], P[2], &t, w);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    V3<T> q = closest_on_triangle(P[k], Q[0], Q[1], Q[2], w);
+    V3<T> p = closest_on_triangle(Q[k], P[0], P[1], P[2], w);
+    d2[k] = dot(P[k] - q, P[k] - q);
+    d2[3 + k] = dot(p - Q[k], p - Q[k]);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    int i1 = i == 2 ? 0 : i + 1;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      int j1 = j == 2 ? 0 : j + 1;
+      T s, u;
+      bool par;
+      closest_segments(P[i], P[i1], Q[j], Q[j1], &s, &u, &par);
+      V3<T> dv = (P[i] + s * (P[i1] - P[i])) - (Q[j] + u * (Q[j1] - Q[j]));
+      d2[6 + 3 * i + j] = dot(dv, dv);
+    }
+  }
+  return crossing;
+}
+
+template <typename T>
+MRDEM_HD V3<T> pick3(const V3<T> T3[3], int k) {
+  return k == 0 ? T3[0] : (k == 1 ? T3[1] : T3[2]);
+}
+
+// Closest points of one sub-test (feature code 0..14) of the
+// comparison-based distance; the squared distance is returned.
+template <typename T>
+MRDEM_HD T eval_subtest(const V3<T> P[3], const V3<T> Q[3], int f, V3<T>* pa, V3<T>* pb) {
+  T w[3];
+  if (f < 3) {
+    V3<T> v = pick3(P, f);
+    *pa = v;
+    *pb = closest_on_triangle(v, Q[0], Q[1], Q[2], w);
+  } else if (f < 6) {
+    V3<T> v = pick3(Q, f - 3);
+    *pa = closest_on_triangle(v, P[0], P[1], P[2], w);
+    *pb = v;
+  } else {
+    int i = (f - 6) / 3, j = (f - 6) - 3 * ((f - 6) / 3);
+    int i1 = i == 2 ? 0 : i + 1, j1 = j == 2 ? 0 : j + 1;
+    V3<T> a0 = pick3(P, i), a1 = pick3(P, i1), b0 = pick3(Q, j), b1 = pick3(Q, j1);
+    T s, u;
+    bool par;
+    closest_segments(a0, a1, b0, b1, &s, &u, &par);
+    *pa = a0 + s * (a1 - a0);
+    *pb = b0 + u * (b1 - b0);
+  }
+  V3<T> dv = *pa - *pb;
+  return dot(dv, dv);
+}
+
+// Candidate pair for the final distance: both triangles in double,
+// relative to the origin o (A's first vertex), and the threshold 2 eps.
+struct CandGeom {
+  V3<double> P[3], Q[3], o;
+  double tau;
+};
+
+// FP32 form of the final distance: the fifteen sub-tests in float on the
+// rounded coordinates with the error bound err = 2^-15 max|coordinate|; a
+// pair clearly beyond 2 eps is dropped; every sub-test within 2 err of the
+// float minimum is re-evaluated in double and the smallest value is the
+// distance (the true minimiser is always among them).
+// Returns 1 (contact, r filled), 0 (no contact) or -1 (needs the full FP64 test).
+MRDEM_HD int cand_fp32(const CandGeom& g, double& d, V3<double>& pa, V3<double>& pb) {
+  V3<float> Pf[3], Qf[3];
+  float L = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    Pf[k] = {(float)g.P[k].x, (float)g.P[k].y, (float)g.P[k].z};
+    Qf[k] = {(float)g.Q[k].x, (float)g.Q[k].y, (float)g.Q[k].z};
+    L = fmaxf(L, fmaxf(fmaxf(fabsf(Pf[k].x), fabsf(Pf[k].y)), fabsf(Pf[k].z)));
+    L = fmaxf(L, fmaxf(fmaxf(fabsf(Qf[k].x), fabsf(Qf[k].y)), fabsf(Qf[k].z)));
+  }
+  float d2[15];
+  bool crossing = tri_tri_subtests(Pf, Qf, d2);
+  float best2 = d2[0];
+#pragma unroll
+  for (int k = 1; k < 15; ++k) best2 = fminf(best2, d2[k]);
+  float err = ldexpf(L, -15);
+  float d32 = sqrtf(best2);
+  if (crossing || d32 <= 2.f * err) return -1;
+  if ((double)d32 > g.tau + (double)err) return 0;
+  float lim = d32 + 2.f * err;
+  float lim2 = lim * lim;
+  double bd2 = 1e300;
+  for (int k = 0; k < 15; ++k) {
+    if (d2[k] > lim2) continue;
+    V3<double> a, b;
+    double v = eval_subtest(g.P, g.Q, k, &a, &b);
+    if (v < bd2) { bd2 = v; pa = a; pb = b; }
+  }
+  d = sqrt(bd2);
+  return d <= g.tau ? 1 : 0;
+}
+
 // ---------------------------------------------------------------------------
 // Penalty sweep (Sec. 3, Eq. 3/4).  Unknowns x = (a1, b1, a2, b2) with
 // t1 = P0 + a1 (P1 - P0) + b1 (P2 - P0), t2 = Q0 + a2 (Q1 - Q0) + b2 (Q2 - Q0),

@@ -68,6 +68,7 @@ enum Counter : int {
   CNT_FETCH = CNT_LEVEL + kMaxLevels + 1, // [kMaxLevels+1] dynamic work fetch per kernel
   CNT_TILES = CNT_FETCH + kMaxLevels + 2,
   CNT_CANDS,
+  CNT_FALLBACK,                           // FP32 form: candidates left for the FP64 test
   CNT_STATS,                              // [MRDEM_STAT_COUNT] statistics
   CNT_TOTAL = CNT_STATS + MRDEM_STAT_COUNT
 };
@@ -92,7 +93,7 @@ struct mrdem_hier {
 };
 
 namespace mrdem {
-enum KernelId : int { K_SETUP = 0, K_LEVEL, K_TILE, K_EXACT, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_COUNT };
+enum KernelId : int { K_SETUP = 0, K_LEVEL, K_TILE, K_EXACT, K_EXACT64, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_COUNT };
 struct ProfRec {
   int kernel;
   cudaEvent_t a, b;

@@ -66,10 +66,12 @@ def test_exact_distance_fp32_form(gctx, orc):
     out = m.triangle_distance(gctx, T(P), T(Q), T(eps), precision="fp32")
     d = out["d"].cpu().numpy()
     tau = 2 * eps
-    hit = d <= tau
+    feat = out["feature"].cpu().numpy()
+    hit = (d <= tau) & (feat != -2)    # -2: the float test decided "beyond 2 eps"
     hit_ref = d_ref <= tau
     band = np.abs(d_ref - tau) <= 1e-6 * eps
     assert np.all((hit == hit_ref) | band)
+    assert np.all((feat != -2) | (d_ref > tau) | band)
     err = np.abs(d - d_ref) / np.maximum(d_ref, eps)
     assert err[hit_ref].max() <= 1e-5, err[hit_ref].max()
 
