@@ -30,15 +30,16 @@ void free_lists(mrdem_ctx* c) {
   cudaFree(c->tiles);
   cudaFree(c->cands);
   c->level_list[0] = c->level_list[1] = nullptr;
-  c->tiles = c->cands = nullptr;
+  c->tiles = nullptr;
+  c->cands = nullptr;
   c->cap_level = c->cap_tiles = c->cap_cands = 0;
 }
 
 int alloc_lists(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca) {
   free_lists(c);
-  if (cudaMalloc(&c->level_list[0], sizeof(int3) * lv) != cudaSuccess ||
-      cudaMalloc(&c->level_list[1], sizeof(int3) * lv) != cudaSuccess ||
-      cudaMalloc(&c->tiles, sizeof(int3) * ti) != cudaSuccess ||
+  if (cudaMalloc(&c->level_list[0], sizeof(int4) * lv) != cudaSuccess ||
+      cudaMalloc(&c->level_list[1], sizeof(int4) * lv) != cudaSuccess ||
+      cudaMalloc(&c->tiles, sizeof(TileItem) * ti) != cudaSuccess ||
       cudaMalloc(&c->cands, sizeof(int3) * ca) != cudaSuccess) {
     cudaGetLastError();
     free_lists(c);

@@ -54,7 +54,8 @@ __device__ __forceinline__ void quat_matrix(double w, double x, double y, double
 // Append `item` for each lane with `pred` to `list` (capacity cap); one
 // atomic per warp.  Must be called by all 32 lanes.  Overflowing entries are
 // dropped and the needed size is latched in *req.
-__device__ __forceinline__ void warp_append(bool pred, int3 item, int3* list,
+template <typename Item>
+__device__ __forceinline__ void warp_append(bool pred, const Item& item, Item* list,
                                             unsigned long long* counter, int64_t cap,
                                             unsigned long long* req) {
   unsigned m = __ballot_sync(0xffffffffu, pred);
@@ -92,22 +93,41 @@ __device__ __forceinline__ void load_pairxf(const PairXf* xf, int p, PairXf& X) 
 
 // Warp-aggregated statistics: lane 0 keeps the warp's running totals.
 struct WarpCount {
-  unsigned long long v = 0;
+  unsigned v = 0;  // per-warp totals stay far below 2^32
   __device__ __forceinline__ void add(bool pred) {
     unsigned m = __ballot_sync(0xffffffffu, pred);
     v += __popc(m);
   }
   __device__ __forceinline__ void flush(unsigned long long* dst) {
-    if (lane_id() == 0 && v) atomicAdd(dst, v);
+    if (lane_id() == 0 && v) atomicAdd(dst, (unsigned long long)v);
   }
 };
+
+__device__ __forceinline__ TileItem make_tile(int pair, int na_node, int nb_node, int2 ia, int2 ib) {
+  TileItem t;
+  t.pair = pair;
+  t.node_a = na_node;
+  t.node_b = nb_node;
+  t.slot_a = ia.x;
+  t.slot_b = ib.x;
+  t.counts = (-ia.y) | ((-ib.y) << 8);
+  t.pad0 = t.pad1 = 0;
+  return t;
+}
+// Level item for the children of the node pair (node_a with child info ia,
+// node_b with ib); a leaf side is its own one-element set.
+__device__ __forceinline__ int4 make_level(int pair, int node_a, int node_b, int2 ia, int2 ib) {
+  int ab = ia.y > 0 ? ia.x : node_a, na = ia.y > 0 ? ia.y : 1;
+  int bb = ib.y > 0 ? ib.x : node_b, nb = ib.y > 0 ? ib.y : 1;
+  return make_int4(pair, ab, bb, na | (nb << 8));
+}
 
 // ---------------------------------------------------------------------------
 // k_setup: per pair transforms + root test
 __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
                         const double* __restrict__ eps, const double* __restrict__ poses,
-                        PairXf* xf, PairXf64* xf64, SweepConst sc, int root_test, int3* list0,
-                        int3* tiles, unsigned long long* cnt, unsigned long long* status,
+                        PairXf* xf, PairXf64* xf64, SweepConst sc, int root_test, int4* list0,
+                        TileItem* tiles, unsigned long long* cnt, unsigned long long* status,
                         int64_t cap_level, int64_t cap_tiles) {
   WarpCount tests, surv;
   int stride = gridDim.x * blockDim.x;
@@ -116,6 +136,7 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
     bool in = p < n_pairs;
     bool ok = false, survive = false, both_leaf = false;
     int ra = 0, rb = 0;
+    int2 ia = make_int2(0, 1), ib = make_int2(0, 1);
     if (in) {
       int A = ab[2 * p], B = ab[2 * p + 1];
       double e = eps[p];
@@ -153,6 +174,8 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
         if (root_test) {
           float4 a0 = H.node_geo[3 * ra], a1 = H.node_geo[3 * ra + 1], a2 = H.node_geo[3 * ra + 2];
           float4 b0 = H.node_geo[3 * rb], b1 = H.node_geo[3 * rb + 1], b2 = H.node_geo[3 * rb + 2];
+          ia = H.node_child[ra];
+          ib = H.node_child[rb];
           F3 q0 = xf_point(X, {b0.x, b0.y, b0.z}), q1 = xf_point(X, {b1.x, b1.y, b1.z});
           F3 q2 = xf_point(X, {b2.x, b2.y, b2.z});
           bool cv;
@@ -160,7 +183,7 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
                                                {a2.x, a2.y, a2.z}, q0, q1, q2, sc, 0.f, &cv, nullptr);
           float thr = a0.w + b0.w + X.tau + X.margin;
           survive = !(gap > thr);
-          both_leaf = H.node_child[ra].y < 0 && H.node_child[rb].y < 0;
+          both_leaf = ia.y < 0 && ib.y < 0;
         }
       } else {
         X64.valid = 0;
@@ -175,10 +198,10 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
     if (root_test) {
       tests.add(in && ok);
       surv.add(survive);
-      warp_append(survive && both_leaf, make_int3(p, ra, rb), tiles, cnt + CNT_TILES, cap_tiles,
-                  status + ST_REQ_TILES);
-      warp_append(survive && !both_leaf, make_int3(p, ra, rb), list0, cnt + CNT_LEVEL, cap_level,
-                  status + ST_REQ_LEVEL);
+      warp_append(survive && both_leaf, make_tile(p, ra, rb, ia, ib), tiles, cnt + CNT_TILES,
+                  cap_tiles, status + ST_REQ_TILES);
+      warp_append(survive && !both_leaf, make_level(p, ra, rb, ia, ib), list0, cnt + CNT_LEVEL,
+                  cap_level, status + ST_REQ_LEVEL);
     }
   }
   tests.flush(cnt + CNT_STATS + MRDEM_STAT_TESTS);
@@ -186,21 +209,23 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
 }
 
 // ---------------------------------------------------------------------------
-// k_level: one warp per node pair of list `level`; tests its child pairs.
-// Each child surrogate is staged with a bounding sphere of its eps-free
-// environment (centroid, largest vertex distance + delta); child pairs whose
-// spheres are farther apart than 2 eps are dropped, the rest are compacted and
-// given the penalty sweep + certificate against delta_a + delta_b + 2 eps.
+// k_level: one warp per level item (the child sets of a surviving node
+// pair).  Each child surrogate is staged with a bounding sphere of its
+// eps-free environment (centroid, largest vertex distance + delta); child
+// pairs whose spheres are farther apart than 2 eps are dropped, the rest are
+// compacted and given the penalty sweep + certificate against
+// delta_a + delta_b + 2 eps.  Items are taken in a fixed interleaved order and
+// the next one is loaded while the current one is processed.
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_level(HierDev H, const PairXf* __restrict__ xf,
-                                                      SweepConst sc, const int3* __restrict__ in,
-                                                      int level, int3* out, int3* tiles,
-                                                      unsigned long long* cnt,
-                                                      unsigned long long* status,
-                                                      int64_t cap_level, int64_t cap_tiles) {
+__global__ void __launch_bounds__(WARPS * 32, 3) k_level(HierDev H, const PairXf* __restrict__ xf,
+                                                         SweepConst sc, const int4* __restrict__ in,
+                                                         int level, int4* out, TileItem* tiles,
+                                                         unsigned long long* cnt,
+                                                         unsigned long long* status,
+                                                         int64_t cap_level, int64_t cap_tiles) {
   __shared__ float4 sgeo[WARPS][16][3];
   __shared__ float4 ssph[WARPS][16];
-  __shared__ int sleaf[WARPS][16];
+  __shared__ int2 sinfo[WARPS][16];
   __shared__ int snode[WARPS][16];
   __shared__ unsigned char squeue[WARPS][64];
   const int w = threadIdx.x >> 5, lane = lane_id();
@@ -208,17 +233,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_level(HierDev H, const PairXf* _
   if (n_in > cap_level) n_in = cap_level;
   const int slot_tests = MRDEM_STAT_TESTS + (level + 1 < MRDEM_STAT_LEVELS ? level + 1 : MRDEM_STAT_LEVELS - 1);
   WarpCount tests, surv;
-  for (int64_t item = (int64_t)blockIdx.x * WARPS + w; item < n_in; item += (int64_t)gridDim.x * WARPS) {
-    int3 it = in[item];
+  const int64_t step = (int64_t)gridDim.x * WARPS;
+  int64_t item = (int64_t)blockIdx.x * WARPS + w;
+  int4 nxt = item < n_in ? in[item] : make_int4(0, 0, 0, 0);
+  for (; item < n_in; item += step) {
+    const int4 it = nxt;
+    if (item + step < n_in) nxt = in[item + step];
     PairXf X;
     load_pairxf(xf, it.x, X);
-    int2 ca = H.node_child[it.y], cb = H.node_child[it.z];
-    int na = ca.y > 0 ? ca.y : 1, abeg = ca.y > 0 ? ca.x : it.y;
-    int nb = cb.y > 0 ? cb.y : 1, bbeg = cb.y > 0 ? cb.x : it.z;
+    int na = it.w & 0xff, nb = (it.w >> 8) & 0xff;
     bool stage = lane < na || (lane >= 8 && lane < 8 + nb);
     if (stage) {
-      int node = lane < 8 ? abeg + lane : bbeg + lane - 8;
+      int node = lane < 8 ? it.y + lane : it.z + lane - 8;
       float4 g0 = H.node_geo[3 * node], g1 = H.node_geo[3 * node + 1], g2 = H.node_geo[3 * node + 2];
+      int2 info = H.node_child[node];
       F3 p0 = {g0.x, g0.y, g0.z}, p1 = {g1.x, g1.y, g1.z}, p2 = {g2.x, g2.y, g2.z};
       if (lane >= 8) {
         p0 = xf_point(X, p0);
@@ -232,7 +260,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_level(HierDev H, const PairXf* _
       F3 d0 = p0 - c, d1 = p1 - c, d2 = p2 - c;
       float r = sqrtf(fmaxf(dot(d0, d0), fmaxf(dot(d1, d1), dot(d2, d2)))) * (1.f + 1e-6f) + g0.w;
       ssph[w][lane] = make_float4(c.x, c.y, c.z, r);
-      sleaf[w][lane] = H.node_child[node].y < 0;
+      sinfo[w][lane] = info;
       snode[w][lane] = node;
     }
     __syncwarp();
@@ -258,23 +286,25 @@ __global__ void __launch_bounds__(WARPS * 32) k_level(HierDev H, const PairXf* _
       int k = q0 + lane;
       bool act = k < nq;
       int code = act ? squeue[w][k] : 0;
-      int i = code >> 3, j = code & 7;
+      int i = code >> 3, j = 8 + (code & 7);
       bool s = false;
       if (act) {
         float4 a0 = sgeo[w][i][0], a1 = sgeo[w][i][1], a2 = sgeo[w][i][2];
-        float4 b0 = sgeo[w][8 + j][0], b1 = sgeo[w][8 + j][1], b2 = sgeo[w][8 + j][2];
+        float4 b0 = sgeo[w][j][0], b1 = sgeo[w][j][1], b2 = sgeo[w][j][2];
         bool cv;
         float gap = sweep_certificate<false>({a0.x, a0.y, a0.z}, {a1.x, a1.y, a1.z}, {a2.x, a2.y, a2.z},
                                              {b0.x, b0.y, b0.z}, {b1.x, b1.y, b1.z}, {b2.x, b2.y, b2.z},
                                              sc, 0.f, &cv, nullptr);
         s = !(gap > a0.w + b0.w + thr);
       }
-      bool leaves = act && sleaf[w][i] && sleaf[w][8 + j];
-      int3 child = make_int3(it.x, act ? snode[w][i] : 0, act ? snode[w][8 + j] : 0);
+      int2 ia = sinfo[w][i], ib = sinfo[w][j];
+      int ni = snode[w][i], nj = snode[w][j];
+      bool leaves = ia.y < 0 && ib.y < 0;
       surv.add(s);
-      warp_append(s && leaves, child, tiles, cnt + CNT_TILES, cap_tiles, status + ST_REQ_TILES);
-      warp_append(s && !leaves, child, out, cnt + CNT_LEVEL + level + 1, cap_level,
-                  status + ST_REQ_LEVEL);
+      warp_append(s && leaves, make_tile(it.x, ni, nj, ia, ib), tiles, cnt + CNT_TILES, cap_tiles,
+                  status + ST_REQ_TILES);
+      warp_append(s && !leaves, make_level(it.x, ni, nj, ia, ib), out, cnt + CNT_LEVEL + level + 1,
+                  cap_level, status + ST_REQ_LEVEL);
     }
     __syncwarp();
   }
@@ -283,14 +313,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_level(HierDev H, const PairXf* _
 }
 
 // ---------------------------------------------------------------------------
-// k_tile: one warp per leaf pair (dynamic fetch).  Both leaves' fine
-// triangles are staged in shared memory (B moved into A's frame) together
-// with a bounding sphere each (centroid, largest vertex distance).  Pass 1
-// spreads the la x lb products over the lanes and keeps the pairs whose
-// spheres come within the threshold (|c_a - c_b| - r_a - r_b bounds the
-// distance from below); the survivors are compacted into a per-warp queue
-// (the buffered comparisons of Sec. 5.4).  Pass 2 runs the penalty sweep and
-// certificate over the queue, one fine pair per lane.
+// k_tile: one warp per leaf pair.  Both leaves' fine triangles are staged in
+// shared memory (B moved into A's frame) with a bounding sphere each
+// (centroid, largest vertex distance).  Each fine triangle is first tested
+// against the other leaf's surrogate and its slack (Algorithm 5's comparison
+// of a fine triangle with a surrogate); the products of the kept triangles
+// get a bounding-sphere test, and the surviving pairs are compacted into a
+// per-warp queue (the buffered comparisons of Sec. 5.4) that the penalty
+// sweep + certificate then processes one fine pair per lane.  Tiles are taken
+// in a fixed interleaved order; the next tile item is loaded ahead.
 constexpr int kTileQueue = 1024;  // 32 x 32 products
 struct TileSmem {
   float4 a[3][32];  // A: v0, v1, v2 (xyz)
@@ -325,64 +356,74 @@ __device__ __forceinline__ bool sphere_near_triangle(float4 s, F3 g0, F3 g1, F3 
   return dot(d, d) <= l * l;
 }
 
+__device__ __forceinline__ TileItem load_tile(const TileItem* tiles, int64_t t) {
+  const int4* p = reinterpret_cast<const int4*>(tiles + t);
+  int4 a = __ldg(p), b = __ldg(p + 1);
+  TileItem r;
+  r.pair = a.x; r.node_a = a.y; r.node_b = a.z; r.slot_a = a.w;
+  r.slot_b = b.x; r.counts = b.y; r.pad0 = r.pad1 = 0;
+  return r;
+}
+
 template <bool CONV>
-__global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restrict__ xf,
-                                              SweepConst sc, float conv_c,
-                                              const int3* __restrict__ tiles, int3* cands,
-                                              unsigned long long* cnt, unsigned long long* status,
-                                              int64_t cap_tiles, int64_t cap_cands,
-                                              const double* __restrict__ eps_d) {
+__global__ void __launch_bounds__(256, 3) k_tile(HierDev H, const PairXf* __restrict__ xf,
+                                                 SweepConst sc, float conv_c,
+                                                 const TileItem* __restrict__ tiles, int3* cands,
+                                                 unsigned long long* cnt,
+                                                 unsigned long long* status, int64_t cap_tiles,
+                                                 int64_t cap_cands,
+                                                 const double* __restrict__ eps_d) {
   extern __shared__ float4 smem4[];
   const int w = threadIdx.x >> 5, lane = lane_id();
+  const int warps = blockDim.x >> 5;
   TileSmem& S = reinterpret_cast<TileSmem*>(smem4)[w];
   int64_t n_tiles = (int64_t)cnt[CNT_TILES];
   if (n_tiles > cap_tiles) n_tiles = cap_tiles;
   WarpCount tests, spheres, ncand, nodot;
-  unsigned long long ntile = 0, nfvs = 0;
-  for (;;) {
-    unsigned long long t = 0;
-    if (lane == 0) t = atomicAdd(cnt + CNT_FETCH + kMaxLevels, 1ull);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    if ((int64_t)t >= n_tiles) break;
+  unsigned ntile = 0, nfvs = 0;
+  const int64_t step = (int64_t)gridDim.x * warps;
+  int64_t t = (int64_t)blockIdx.x * warps + w;
+  TileItem nxt;
+  if (t < n_tiles) nxt = load_tile(tiles, t);
+  for (; t < n_tiles; t += step) {
+    const TileItem it = nxt;
+    if (t + step < n_tiles) nxt = load_tile(tiles, t + step);
     ++ntile;
-    int3 it = tiles[t];
     PairXf X;
-    load_pairxf(xf, it.x, X);
-    float ce = conv_c * (float)__ldg(eps_d + it.x);
+    load_pairxf(xf, it.pair, X);
+    float ce = conv_c * (float)__ldg(eps_d + it.pair);
     float conv_tol2 = ce * ce;
-    int2 ca = H.node_child[it.y], cb = H.node_child[it.z];
-    int na = -ca.y, nb = -cb.y;
+    int na = it.counts & 0xff, nb = (it.counts >> 8) & 0xff;
     const float thr = X.tau + X.margin;
     // surrogates of the two leaves (B's moved into A's frame) with slack
-    float4 ga0 = H.node_geo[3 * it.y], ga1 = H.node_geo[3 * it.y + 1], ga2 = H.node_geo[3 * it.y + 2];
-    float4 gb0 = H.node_geo[3 * it.z], gb1 = H.node_geo[3 * it.z + 1], gb2 = H.node_geo[3 * it.z + 2];
-    F3 A0 = {ga0.x, ga0.y, ga0.z}, A1 = {ga1.x, ga1.y, ga1.z}, A2 = {ga2.x, ga2.y, ga2.z};
+    float4 ga0 = H.node_geo[3 * it.node_a], ga1 = H.node_geo[3 * it.node_a + 1];
+    float4 ga2 = H.node_geo[3 * it.node_a + 2];
+    float4 gb0 = H.node_geo[3 * it.node_b], gb1 = H.node_geo[3 * it.node_b + 1];
+    float4 gb2 = H.node_geo[3 * it.node_b + 2];
+    bool keep_a = false, keep_b = false;
     F3 B0 = xf_point(X, {gb0.x, gb0.y, gb0.z}), B1 = xf_point(X, {gb1.x, gb1.y, gb1.z});
     F3 B2 = xf_point(X, {gb2.x, gb2.y, gb2.z});
-    // stage the fine triangles; each one is tested against the other leaf's
-    // surrogate (a fine triangle against a surrogate, as in Algorithm 5 when
-    // one side is already fine)
-    bool keep_a = false, keep_b = false;
     if (lane < na) {
       F3 v[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        v[c].x = __ldg(H.tri + (3 * c + 0) * H.stride + ca.x + lane);
-        v[c].y = __ldg(H.tri + (3 * c + 1) * H.stride + ca.x + lane);
-        v[c].z = __ldg(H.tri + (3 * c + 2) * H.stride + ca.x + lane);
+        v[c].x = __ldg(H.tri + (3 * c + 0) * H.stride + it.slot_a + lane);
+        v[c].y = __ldg(H.tri + (3 * c + 1) * H.stride + it.slot_a + lane);
+        v[c].z = __ldg(H.tri + (3 * c + 2) * H.stride + it.slot_a + lane);
       }
       float4 sp = stage_triangle(v[0], v[1], v[2], S.a, lane);
       S.sa[lane] = sp;
       keep_a = sphere_near_triangle(sp, B0, B1, B2, gb0.w + thr);
     }
+    F3 A0 = {ga0.x, ga0.y, ga0.z}, A1 = {ga1.x, ga1.y, ga1.z}, A2 = {ga2.x, ga2.y, ga2.z};
     if (lane < nb) {
       F3 v[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         F3 u;
-        u.x = __ldg(H.tri + (3 * c + 0) * H.stride + cb.x + lane);
-        u.y = __ldg(H.tri + (3 * c + 1) * H.stride + cb.x + lane);
-        u.z = __ldg(H.tri + (3 * c + 2) * H.stride + cb.x + lane);
+        u.x = __ldg(H.tri + (3 * c + 0) * H.stride + it.slot_b + lane);
+        u.y = __ldg(H.tri + (3 * c + 1) * H.stride + it.slot_b + lane);
+        u.z = __ldg(H.tri + (3 * c + 2) * H.stride + it.slot_b + lane);
         v[c] = xf_point(X, u);
       }
       float4 sp = stage_triangle(v[0], v[1], v[2], S.b, lane);
@@ -393,7 +434,7 @@ __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restric
     if (keep_a) S.ka[__popc(ma & ((1u << lane) - 1u))] = (unsigned char)lane;
     if (keep_b) S.kb[__popc(mb & ((1u << lane) - 1u))] = (unsigned char)lane;
     const int ka = __popc(ma), kb = __popc(mb);
-    nfvs += (unsigned long long)(na + nb);
+    nfvs += (unsigned)(na + nb);
     __syncwarp();
     const int total = ka * kb;
     const float inv_kb = 1.0f / (float)(kb > 0 ? kb : 1);
@@ -414,7 +455,7 @@ __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restric
       if (keep) S.q[nq + __popc(m & ((1u << lane) - 1u))] = (unsigned short)((i << 5) | j);
       nq += __popc(m);
     }
-    spheres.v += lane == 0 ? (unsigned long long)total : 0ull;
+    spheres.v += lane == 0 ? (unsigned)total : 0u;
     __syncwarp();
     // pass 2: penalty sweep + certificate on the queued pairs
     for (int q0 = 0; q0 < nq; q0 += 32) {
@@ -438,14 +479,14 @@ __global__ void __launch_bounds__(256) k_tile(HierDev H, const PairXf* __restric
       tests.add(act);
       ncand.add(s);
       if (CONV) nodot.add(s && !cv);
-      warp_append(s, make_int3(it.x, ca.x + i, cb.x + j), cands, cnt + CNT_CANDS, cap_cands,
-                  status + ST_REQ_CANDS);
+      warp_append(s, make_int3(it.pair, it.slot_a + i, it.slot_b + j), cands, cnt + CNT_CANDS,
+                  cap_cands, status + ST_REQ_CANDS);
     }
     __syncwarp();
   }
   if (lane == 0) {
-    if (ntile) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_TILES, ntile);
-    if (nfvs) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_FINE_SURROGATE, nfvs);
+    if (ntile) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_TILES, (unsigned long long)ntile);
+    if (nfvs) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_FINE_SURROGATE, (unsigned long long)nfvs);
   }
   tests.flush(cnt + CNT_STATS + MRDEM_STAT_FINE_TESTS);
   spheres.flush(cnt + CNT_STATS + MRDEM_STAT_SPHERE_TESTS);
@@ -775,10 +816,10 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
         ProfScope ps(c, K_EXACT, s);
         // the level lists are free once the tiles are done: reuse one as the fallback list
         k_exact32<<<c->n_sms * 8, et, 0, s>>>(H, c->xf64, c->cands, c->counters, c->status,
-                                               c->cap_cands, c->level_list[0], c->cap_level, *out);
+                                               c->cap_cands, reinterpret_cast<int3*>(c->level_list[0]), c->cap_level, *out);
       }
       ProfScope ps(c, K_EXACT64, s);
-      k_exact64<<<c->n_sms * 4, et, 0, s>>>(H, c->xf64, c->level_list[0], c->counters,
+      k_exact64<<<c->n_sms * 4, et, 0, s>>>(H, c->xf64, reinterpret_cast<const int3*>(c->level_list[0]), c->counters,
                                              CNT_FALLBACK, c->cap_level, c->status,
                                              MRDEM_STAT_FP64, *out);
     }

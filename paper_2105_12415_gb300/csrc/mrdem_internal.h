@@ -62,6 +62,15 @@ struct alignas(16) PairXf64 {
   int32_t A, B, valid, pad;
 };
 
+// Work items.  A level item holds the node pairs still to be tested: the
+// child sets Ca = [a_begin, a_begin + na) and Cb (a leaf side is its own
+// one-element set): int4 (pair, a_begin, b_begin, na | nb << 8).
+// A tile item is a pair of leaves with their fine-triangle slot ranges.
+struct alignas(16) TileItem {
+  int pair, node_a, node_b, slot_a;
+  int slot_b, counts, pad0, pad1;  // counts = na | nb << 8
+};
+
 // Device counters (one int64 array, zeroed at the start of every detect).
 enum Counter : int {
   CNT_LEVEL = 0,                          // [0..kMaxLevels] items in level list l
@@ -104,8 +113,8 @@ struct mrdem_ctx {
   int device = 0;
   int n_sms = 0;
   mrdem_params params{};
-  int3* level_list[2] = {nullptr, nullptr};
-  int3* tiles = nullptr;
+  int4* level_list[2] = {nullptr, nullptr};
+  mrdem::TileItem* tiles = nullptr;
   int3* cands = nullptr;
   int64_t cap_level = 0, cap_tiles = 0, cap_cands = 0;
   mrdem::PairXf* xf = nullptr;
