@@ -18,7 +18,7 @@ bool params_ok(const mrdem_params& p) {
          p.fanout >= 2 && p.fanout <= 8 && p.leaf_max >= 1 && p.leaf_max <= 32 && p.leaf_min >= 1 &&
          p.kmeans_iters >= 0 && p.cap_level > 0 && p.cap_tiles > 0 && p.cap_candidates > 0 &&
          p.cap_level < (int64_t)1 << 31 && p.cap_tiles < (int64_t)1 << 31 &&
-         p.cap_candidates < (int64_t)1 << 31 && p.tile_warps >= 1 && p.tile_warps <= 32 &&
+         p.cap_candidates < (int64_t)1 << 31 && p.tile_warps >= 1 && p.tile_warps <= 8 &&
          p.tile_blocks_per_sm >= 1 && p.tile_blocks_per_sm <= 64 && p.level_warps >= 1 &&
          p.level_warps <= 32 && p.exact_threads >= 32 && p.exact_threads <= 1024 &&
          p.exact_threads % 32 == 0;
@@ -167,6 +167,7 @@ int mrdem_set_params(mrdem_ctx* c, const mrdem_params* p) {
   n.cap_candidates = c->params.cap_candidates;
   if (!params_ok(n)) return MRDEM_ERR_INVALID;
   c->params = n;
+  for (int& o : c->occ) o = 0;  // launch shapes may have changed
   return MRDEM_OK;
 }
 

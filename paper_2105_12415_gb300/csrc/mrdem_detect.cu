@@ -752,6 +752,22 @@ static int ensure_pairs(mrdem_ctx* c, int64_t n) {
   return MRDEM_OK;
 }
 
+// Blocks for a persistent launch: exactly the blocks that fit on the GPU at
+// once (SMs x resident blocks per SM), so that interleaved work assignment
+// has no second wave.
+template <typename K>
+static int one_wave(mrdem_ctx* c, int id, K kernel, int threads, size_t smem) {
+  if (c->occ[id] <= 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess || b <= 0) {
+      cudaGetLastError();
+      b = 1;
+    }
+    c->occ[id] = b;
+  }
+  return c->occ[id] * c->n_sms;
+}
+
 static SweepConst sweep_const(const mrdem_params& p) {
   SweepConst sc;
   sc.rho_reg = p.rho_reg;
@@ -787,8 +803,9 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
     int steps = std::min(hier->h.max_depth - 1, kMaxLevels - 1);
     for (int l = 0; l < steps; ++l) {
       constexpr int W = 8;
+      int lb = one_wave(c, K_LEVEL, k_level<W>, W * 32, 0);
       ProfScope ps(c, K_LEVEL, s);
-      k_level<W><<<c->n_sms * 8, W * 32, 0, s>>>(H, c->xf, sc, c->level_list[l & 1], l,
+      k_level<W><<<lb, W * 32, 0, s>>>(H, c->xf, sc, c->level_list[l & 1], l,
                                                   c->level_list[(l + 1) & 1], c->tiles,
                                                   c->counters, c->status, c->cap_level,
                                                   c->cap_tiles);
@@ -801,8 +818,9 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
       attr_set = true;
     }
     {
+    int tb = one_wave(c, K_TILE, k_tile<true>, tw * 32, smem);
     ProfScope ps(c, K_TILE, s);
-    k_tile<true><<<c->n_sms * prm.tile_blocks_per_sm, tw * 32, smem, s>>>(
+    k_tile<true><<<tb, tw * 32, smem, s>>>(
         H, c->xf, sc, prm.conv_c, c->tiles, c->cands, c->counters, c->status, c->cap_tiles,
         c->cap_cands, eps);
     }

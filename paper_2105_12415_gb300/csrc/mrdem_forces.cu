@@ -117,68 +117,144 @@ __global__ void __launch_bounds__(256) k_forces(HierDev H, const int32_t* __rest
   }
 }
 
-__global__ void __launch_bounds__(128) k_grad(HierDev H, const int32_t* __restrict__ ab,
-                                              const double* __restrict__ eps,
-                                              const double* __restrict__ poses, mrdem_contacts c,
-                                              const double* __restrict__ mass, double k_s,
-                                              double scale, float* dverts, double* dpose,
-                                              double* jac, int64_t n_pairs) {
+// Adjoint: one thread per contact.  Closest points and barycentric weights
+// are recomputed from the triangles in A's frame: float sub-tests select the
+// minimising sub-test(s), which are finished in double (the same scheme as
+// the detection's FP32 form); crossing or nearly touching pairs use the full
+// double test.  Gauss-Newton blocks of contacts that share a pair within a
+// warp are summed in shared memory before one set of atomics per pair.
+constexpr int kGradThreads = 128;
+__global__ void __launch_bounds__(kGradThreads) k_grad(HierDev H, const int32_t* __restrict__ ab,
+                                                       const double* __restrict__ eps,
+                                                       const double* __restrict__ poses,
+                                                       mrdem_contacts c,
+                                                       const double* __restrict__ mass, double k_s,
+                                                       double scale, float* dverts, double* dpose,
+                                                       double* jac, int64_t n_pairs) {
+  __shared__ double sJ[kGradThreads / 32][32][13];  // 12 Jacobian entries and the weight e''
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t n = *c.count;
   if (n > c.capacity) n = c.capacity;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-    int p = c.pair[k];
-    if (p < 0 || p >= n_pairs) continue;
-    int A = ab[2 * p], B = ab[2 * p + 1];
-    double e = eps[p];
-    const double* pA = poses + 7 * (int64_t)A;
-    const double* pB = poses + 7 * (int64_t)B;
-    double RA[9], RB[9];
-    pose_matrix(pA, RA);
-    pose_matrix(pB, RB);
-    int sa = H.tri_slot[H.tri_off[A] + c.tri_a[k]];
-    int sb = H.tri_slot[H.tri_off[B] + c.tri_b[k]];
-    D3 TA[3], TB[3];
-    world_tri(H, sa, RA, pA, TA);
-    world_tri(H, sb, RB, pB, TB);
-    TriTriResult<double> r = tri_tri_distance(TA, TB);
-    double d = r.d;
-    if (!(d <= 2.0 * e)) continue;
-    double mu = 1.0 / (1.0 / mass[A] + 1.0 / mass[B]);
-    double ks = k_s * sqrt(mu);
-    D3 u = d > 0.0 ? (1.0 / d) * (r.pa - r.pb) : -1.0 * unit_normal(TA);
-    double de = -ks * (1.0 - d / (2.0 * e)) * scale;
-    D3 g = de * u;
-    if (dverts) {
-      for (int v = 0; v < 3; ++v) {
-        int ia = H.vid[v * H.stride + sa], ib = H.vid[v * H.stride + sb];
-        D3 ga = mul_t(RA, r.wa[v] * g);
-        D3 gb = mul_t(RB, (-r.wb[v]) * g);
-        atomicAdd(dverts + 3 * (int64_t)ia, (float)ga.x);
-        atomicAdd(dverts + 3 * (int64_t)ia + 1, (float)ga.y);
-        atomicAdd(dverts + 3 * (int64_t)ia + 2, (float)ga.z);
-        atomicAdd(dverts + 3 * (int64_t)ib, (float)gb.x);
-        atomicAdd(dverts + 3 * (int64_t)ib + 1, (float)gb.y);
-        atomicAdd(dverts + 3 * (int64_t)ib + 2, (float)gb.z);
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    int64_t k = base + threadIdx.x;
+    int p = k < n ? c.pair[k] : -1;
+    bool ok = p >= 0 && p < n_pairs;
+    double J[12], h = 0.0;
+    if (ok) {
+      int A = ab[2 * p], B = ab[2 * p + 1];
+      double e = eps[p];
+      const double* pA = poses + 7 * (int64_t)A;
+      const double* pB = poses + 7 * (int64_t)B;
+      double RA[9], RB[9];
+      pose_matrix(pA, RA);
+      pose_matrix(pB, RB);
+      int sa = H.tri_slot[H.tri_off[A] + c.tri_a[k]];
+      int sb = H.tri_slot[H.tri_off[B] + c.tri_b[k]];
+      // both triangles in A's frame relative to A's first vertex
+      double Rab[9], tab[3];
+      for (int r = 0; r < 3; ++r) {
+        for (int q = 0; q < 3; ++q)
+          Rab[3 * r + q] = RA[r] * RB[q] + RA[3 + r] * RB[3 + q] + RA[6 + r] * RB[6 + q];
+        tab[r] = RA[r] * (pB[0] - pA[0]) + RA[3 + r] * (pB[1] - pA[1]) + RA[6 + r] * (pB[2] - pA[2]);
       }
-    }
-    D3 ra = r.pa - D3{pA[0], pA[1], pA[2]};
-    D3 rb = r.pb - D3{pB[0], pB[1], pB[2]};
-    if (dpose) {
-      add3(dpose + 6 * (int64_t)A, g);
-      add3(dpose + 6 * (int64_t)A + 3, cross(ra, g));
-      add3(dpose + 6 * (int64_t)B, -1.0 * g);
-      add3(dpose + 6 * (int64_t)B + 3, cross(rb, -1.0 * g));
+      CandGeom g;
+      D3 Pb[3], Qb[3];
+      for (int q = 0; q < 3; ++q) {
+        Pb[q] = {(double)H.tri[(3 * q) * H.stride + sa], (double)H.tri[(3 * q + 1) * H.stride + sa],
+                 (double)H.tri[(3 * q + 2) * H.stride + sa]};
+        Qb[q] = {(double)H.tri[(3 * q) * H.stride + sb], (double)H.tri[(3 * q + 1) * H.stride + sb],
+                 (double)H.tri[(3 * q + 2) * H.stride + sb]};
+      }
+      g.o = Pb[0];
+      for (int q = 0; q < 3; ++q) {
+        g.P[q] = Pb[q] - g.o;
+        D3 y = mul(Rab, Qb[q]);
+        g.Q[q] = D3{y.x + tab[0], y.y + tab[1], y.z + tab[2]} - g.o;
+      }
+      g.tau = 1e300;
+      double d, wa[3], wb[3];
+      D3 pa, pb;
+      if (cand_fp32(g, d, pa, pb, wa, wb) != 1) {
+        TriTriResult<double> r = tri_tri_distance(g.P, g.Q);
+        d = r.d; pa = r.pa; pb = r.pb;
+        for (int q = 0; q < 3; ++q) { wa[q] = r.wa[q]; wb[q] = r.wb[q]; }
+      }
+      ok = d <= 2.0 * e;
+      if (ok) {
+        double mu = 1.0 / (1.0 / mass[A] + 1.0 / mass[B]);
+        double ks = k_s * sqrt(mu);
+        // world frame: points, direction
+        D3 paw = mul(RA, pa + g.o), pbw = mul(RA, pb + g.o);
+        paw = {paw.x + pA[0], paw.y + pA[1], paw.z + pA[2]};
+        pbw = {pbw.x + pA[0], pbw.y + pA[1], pbw.z + pA[2]};
+        D3 u;
+        if (d > 0.0) {
+          u = (1.0 / d) * (paw - pbw);
+        } else {
+          D3 n = cross(g.P[1] - g.P[0], g.P[2] - g.P[0]);
+          u = (-1.0 / sqrt(dot(n, n))) * mul(RA, n);
+        }
+        double de = -ks * (1.0 - d / (2.0 * e)) * scale;
+        D3 gv = de * u;
+        if (dverts) {
+          for (int v = 0; v < 3; ++v) {
+            int ia = H.vid[v * H.stride + sa], ib = H.vid[v * H.stride + sb];
+            D3 ga = mul_t(RA, wa[v] * gv);
+            D3 gb = mul_t(RB, (-wb[v]) * gv);
+            atomicAdd(dverts + 3 * (int64_t)ia, (float)ga.x);
+            atomicAdd(dverts + 3 * (int64_t)ia + 1, (float)ga.y);
+            atomicAdd(dverts + 3 * (int64_t)ia + 2, (float)ga.z);
+            atomicAdd(dverts + 3 * (int64_t)ib, (float)gb.x);
+            atomicAdd(dverts + 3 * (int64_t)ib + 1, (float)gb.y);
+            atomicAdd(dverts + 3 * (int64_t)ib + 2, (float)gb.z);
+          }
+        }
+        D3 ra = paw - D3{pA[0], pA[1], pA[2]};
+        D3 rb = pbw - D3{pB[0], pB[1], pB[2]};
+        if (dpose) {
+          add3(dpose + 6 * (int64_t)A, gv);
+          add3(dpose + 6 * (int64_t)A + 3, cross(ra, gv));
+          add3(dpose + 6 * (int64_t)B, -1.0 * gv);
+          add3(dpose + 6 * (int64_t)B + 3, cross(rb, -1.0 * gv));
+        }
+        D3 c1 = cross(ra, u), c2 = cross(rb, u);
+        J[0] = u.x; J[1] = u.y; J[2] = u.z; J[3] = c1.x; J[4] = c1.y; J[5] = c1.z;
+        J[6] = -u.x; J[7] = -u.y; J[8] = -u.z; J[9] = -c2.x; J[10] = -c2.y; J[11] = -c2.z;
+        h = ks / (2.0 * e) * scale;
+      }
     }
     if (jac) {
-      D3 c1 = cross(ra, u), c2 = cross(rb, u);
-      double J[12] = {u.x, u.y, u.z, c1.x, c1.y, c1.z, -u.x, -u.y, -u.z, -c2.x, -c2.y, -c2.z};
-      double h = ks / (2.0 * e) * scale;
-      double* o = jac + 144 * (int64_t)p;
-      for (int i = 0; i < 12; ++i) {
-        double hi = h * J[i];
-        for (int j = 0; j < 12; ++j) atomicAdd(o + 12 * i + j, hi * J[j]);
+      // group the warp's contacts by pair; each group's 78 distinct block
+      // entries are summed by the lanes in turn and added once
+      for (int q = 0; q < 12; ++q) sJ[w][lane][q] = ok ? J[q] : 0.0;
+      sJ[w][lane][12] = ok ? h : 0.0;
+      __syncwarp();
+      unsigned pending = __ballot_sync(0xffffffffu, ok);
+      int mykey = ok ? p : -1;
+      while (pending) {
+        int leader = __ffs(pending) - 1;
+        int key = __shfl_sync(0xffffffffu, mykey, leader);
+        unsigned grp = __ballot_sync(0xffffffffu, ok && mykey == key);
+        pending &= ~grp;
+        for (int e2 = lane; e2 < 78; e2 += 32) {
+          // e2 -> (r, q) with r <= q in the upper triangle of 12 x 12
+          int r = 0, rem = e2;
+          while (rem >= 12 - r) { rem -= 12 - r; ++r; }
+          int q = r + rem;
+          double acc = 0.0;
+          unsigned gm = grp;
+          while (gm) {
+            int l = __ffs(gm) - 1;
+            gm &= gm - 1;
+            acc += sJ[w][l][12] * sJ[w][l][r] * sJ[w][l][q];
+          }
+          double* o = jac + 144 * (int64_t)key;
+          atomicAdd(o + 12 * r + q, acc);
+          if (q != r) atomicAdd(o + 12 * q + r, acc);
+        }
       }
+      __syncwarp();
     }
   }
 }
@@ -202,7 +278,7 @@ int launch_grad(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int
                 double* jac, cudaStream_t s) {
   if (!dverts && !dpose && !jac) return MRDEM_OK;
   ProfScope ps(c, K_GRAD, s);
-  k_grad<<<c->n_sms * 8, 128, 0, s>>>(hier->dev, ab, eps, poses, *con, mass, k_s, scale, dverts,
+  k_grad<<<c->n_sms * 8, kGradThreads, 0, s>>>(hier->dev, ab, eps, poses, *con, mass, k_s, scale, dverts,
                                        dpose, jac, n_pairs);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }

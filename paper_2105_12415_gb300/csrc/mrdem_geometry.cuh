@@ -292,18 +292,24 @@ MRDEM_HD V3<T> pick3(const V3<T> T3[3], int k) {
 }
 
 // Closest points of one sub-test (feature code 0..14) of the
-// comparison-based distance; the squared distance is returned.
+// comparison-based distance, with their barycentric weights in P and Q; the
+// squared distance is returned.
 template <typename T>
-MRDEM_HD T eval_subtest(const V3<T> P[3], const V3<T> Q[3], int f, V3<T>* pa, V3<T>* pb) {
+MRDEM_HD T eval_subtest(const V3<T> P[3], const V3<T> Q[3], int f, V3<T>* pa, V3<T>* pb,
+                        T wa[3], T wb[3]) {
   T w[3];
   if (f < 3) {
     V3<T> v = pick3(P, f);
     *pa = v;
     *pb = closest_on_triangle(v, Q[0], Q[1], Q[2], w);
+    wa[0] = f == 0; wa[1] = f == 1; wa[2] = f == 2;
+    wb[0] = w[0]; wb[1] = w[1]; wb[2] = w[2];
   } else if (f < 6) {
     V3<T> v = pick3(Q, f - 3);
     *pa = closest_on_triangle(v, P[0], P[1], P[2], w);
     *pb = v;
+    wa[0] = w[0]; wa[1] = w[1]; wa[2] = w[2];
+    wb[0] = f == 3; wb[1] = f == 4; wb[2] = f == 5;
   } else {
     int i = (f - 6) / 3, j = (f - 6) - 3 * ((f - 6) / 3);
     int i1 = i == 2 ? 0 : i + 1, j1 = j == 2 ? 0 : j + 1;
@@ -313,6 +319,12 @@ MRDEM_HD T eval_subtest(const V3<T> P[3], const V3<T> Q[3], int f, V3<T>* pa, V3
     closest_segments(a0, a1, b0, b1, &s, &u, &par);
     *pa = a0 + s * (a1 - a0);
     *pb = b0 + u * (b1 - b0);
+    wa[0] = (i == 0) * (T(1) - s) + (i1 == 0) * s;
+    wa[1] = (i == 1) * (T(1) - s) + (i1 == 1) * s;
+    wa[2] = (i == 2) * (T(1) - s) + (i1 == 2) * s;
+    wb[0] = (j == 0) * (T(1) - u) + (j1 == 0) * u;
+    wb[1] = (j == 1) * (T(1) - u) + (j1 == 1) * u;
+    wb[2] = (j == 2) * (T(1) - u) + (j1 == 2) * u;
   }
   V3<T> dv = *pa - *pb;
   return dot(dv, dv);
@@ -331,7 +343,11 @@ struct CandGeom {
 // float minimum is re-evaluated in double and the smallest value is the
 // distance (the true minimiser is always among them).
 // Returns 1 (contact, r filled), 0 (no contact) or -1 (needs the full FP64 test).
-MRDEM_HD int cand_fp32(const CandGeom& g, double& d, V3<double>& pa, V3<double>& pb) {
+// Returns 1 (distance <= 2 eps: d, pa, pb and the weights filled), 0 (beyond
+// 2 eps) or -1 (crossing or nearly touching: needs the full double test).
+// With tau = +inf every non-crossing pair is finished (used by the adjoint).
+MRDEM_HD int cand_fp32(const CandGeom& g, double& d, V3<double>& pa, V3<double>& pb,
+                       double* wa = nullptr, double* wb = nullptr) {
   V3<float> Pf[3], Qf[3];
   float L = 0.f;
 #pragma unroll
@@ -356,8 +372,15 @@ MRDEM_HD int cand_fp32(const CandGeom& g, double& d, V3<double>& pa, V3<double>&
   for (int k = 0; k < 15; ++k) {
     if (d2[k] > lim2) continue;
     V3<double> a, b;
-    double v = eval_subtest(g.P, g.Q, k, &a, &b);
-    if (v < bd2) { bd2 = v; pa = a; pb = b; }
+    double xa[3], xb[3];
+    double v = eval_subtest(g.P, g.Q, k, &a, &b, xa, xb);
+    if (v < bd2) {
+      bd2 = v;
+      pa = a;
+      pb = b;
+      if (wa) { wa[0] = xa[0]; wa[1] = xa[1]; wa[2] = xa[2]; }
+      if (wb) { wb[0] = xb[0]; wb[1] = xb[1]; wb[2] = xb[2]; }
+    }
   }
   d = sqrt(bd2);
   return d <= g.tau ? 1 : 0;

@@ -122,6 +122,7 @@ struct mrdem_ctx {
   int64_t cap_pairs = 0;
   unsigned long long* counters = nullptr;  // [CNT_TOTAL]
   unsigned long long* status = nullptr;    // [ST_TOTAL]
+  int occ[16] = {0};  // resident blocks per SM of each kernel (0 = not queried yet)
   bool prof = false;
   std::vector<mrdem::ProfRec> prof_recs;
   std::vector<cudaEvent_t> ev_pool;
