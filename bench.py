@@ -30,7 +30,9 @@ sys.path.insert(0, ROOT)
 # as FADD + FMUL + 2 FFMA + MUFU (cross-checked with ncu's instruction
 # counters): one penalty sweep (4 iterations, convergence
 # check, certificate) and one bounding-sphere test of a fine pair.
-FLOPS_PER_SWEEP = 429
+FLOPS_PER_SWEEP = 429           # sweep + convergence check + certificate
+FLOPS_PER_XFORM = 54            # moving B's triangle into A's frame (27 FFMA)
+FLOPS_PER_NODE_SWEEP = 398 + 54  # the surrogate sweep has no convergence check
 FLOPS_PER_SPHERE_TEST = 11
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -331,7 +333,7 @@ def main():
     value = args.steps * P * world / (ms_max * 1e-3)
     st = stats.cpu().numpy()
     n_contacts = int(contacts.count.item())
-    launches_per_step = 1 + max(0, info["max_depth"] - 1) + 4
+    launches_per_step = 1 + 2 * max(0, info["max_depth"] - 1) + 6
 
     # ---- per-kernel timing (same steps, outside the graph, events per kernel)
     ctx.profile(True)
@@ -341,19 +343,28 @@ def main():
     torch.cuda.synchronize()
     ctx.profile(False)
     prof = ctx.profile_read()
-    tile_ms, tile_n = prof.get("k_tile", (float("nan"), 1))
-    tile_avg_s = tile_ms / tile_n * 1e-3
     fine_tests = int(st[m._lib.MRDEM_STAT_FINE_TESTS])
     sphere_tests = int(st[m._lib.MRDEM_STAT_SPHERE_TESTS])
-    tile_flops = fine_tests * FLOPS_PER_SWEEP + sphere_tests * FLOPS_PER_SPHERE_TEST
+    level_sweeps = int(st[m._lib.MRDEM_STAT_LEVEL_SWEEPS])
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = tile_flops / tile_avg_s / 1e12
-    traffic = _traffic_per_launch()
     total_prof = sum(v[0] for v in prof.values())
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                    "share": v[0] / total_prof} for k, v in prof.items()}
+    # algorithmic FP32 flops per step of the sweep kernels
+    flops = {"k_sweep_fine": fine_tests * (FLOPS_PER_SWEEP + FLOPS_PER_XFORM),
+             "k_sweep_nodes": level_sweeps * FLOPS_PER_NODE_SWEEP}
+    rl = {}
+    for k, f in flops.items():
+        if k in prof:
+            avg_s = prof[k][0] / prof[k][1] * 1e-3
+            per_launch = f / (prof[k][1] / args.steps)
+            ach = per_launch / avg_s / 1e12
+            rl[k] = {"achieved": ach, "frac": ach / fp32_peak, "flops_per_launch": per_launch,
+                     "avg_ms": avg_s * 1e3}
+    traffic = _traffic_per_launch()
+    fin = rl.get("k_sweep_fine", {"achieved": float("nan"), "frac": float("nan"), "avg_ms": float("nan")})
 
     # ---- end to end through the public API (host inputs, host results)
     e2e = None
@@ -427,19 +438,21 @@ def main():
                    "replicas": world, "l2": "flushed between steps (256 MiB write)",
                    "step": "detect + forces + adjoint (verts, poses, 12x12 blocks)",
                    "graph": "one CUDA graph per step", "prep_s": round(prep_s, 1)},
-        "roofline": {"bound": "alu", "kernel": "k_tile", "achieved": achieved,
-                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+        "roofline": {"bound": "alu", "kernel": "k_sweep_fine", "achieved": fin["achieved"],
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": fin["frac"],
                      "traffic": traffic,
-                     "per_launch": {"sweeps": fine_tests, "flops_per_sweep": FLOPS_PER_SWEEP,
-                                    "sphere_tests": sphere_tests,
-                                    "flops_per_sphere_test": FLOPS_PER_SPHERE_TEST,
-                                    "flops": tile_flops, "avg_ms": tile_avg_s * 1e3}},
+                     "per_launch": {"sweeps": fine_tests,
+                                    "flops_per_sweep": FLOPS_PER_SWEEP + FLOPS_PER_XFORM,
+                                    "avg_ms": fin["avg_ms"]},
+                     "peak_note": "152 SMs x 128 FP32 lanes x 2 x max SM clock (nominal)",
+                     "all": rl},
         "clocks": clk.summary(),
         "gpu_launches": launches_per_step * args.steps,
         "kernels": kernels,
         "stats": {"tests_per_level": [int(x) for x in st[0:6]],
                   "survivors_per_level": [int(x) for x in st[8:14]],
                   "leaf_tiles": int(st[16]), "sphere_tests": sphere_tests,
+                  "level_sweeps": level_sweeps, "fine_vs_surrogate": int(st[23]),
                   "fine_tests": fine_tests, "candidates": int(st[18]),
                   "unconverged": int(st[19]), "contacts": n_contacts, "fp64_refinements": int(st[21]),
                   "fine_tests_per_s": fine_tests * args.steps * world / (ms_max * 1e-3),

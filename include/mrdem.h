@@ -59,8 +59,8 @@ typedef struct CUstream_st* mrdem_stream; /* same type as cudaStream_t */
 
 /* indices into the int64 statistics array filled by mrdem_detect */
 #define MRDEM_STAT_LEVELS 8
-#define MRDEM_STAT_TESTS 0       /* [0..7]  surrogate-pair tests at unfold step l (0 = roots) */
-#define MRDEM_STAT_SURVIVORS 8   /* [8..15] of which not pruned */
+#define MRDEM_STAT_TESTS 0       /* [0..7]  surrogate pairs examined at unfold step l (0 = roots) */
+#define MRDEM_STAT_SURVIVORS 8   /* [8..15] of which not pruned (sphere test, then sweep) */
 #define MRDEM_STAT_TILES 16      /* leaf-pair tiles reaching the finest level */
 #define MRDEM_STAT_FINE_TESTS 17 /* fine triangle-pair sweeps (iterative tests) after the cull */
 #define MRDEM_STAT_CANDIDATES 18 /* fine pairs not pruned by the sweep's certificate */
@@ -69,6 +69,7 @@ typedef struct CUstream_st* mrdem_stream; /* same type as cudaStream_t */
 #define MRDEM_STAT_FP64 21       /* candidates given the full FP64 comparison-based test */
 #define MRDEM_STAT_SPHERE_TESTS 22 /* fine pairs given the bounding-sphere test */
 #define MRDEM_STAT_FINE_SURROGATE 23 /* fine triangles tested against the other leaf's surrogate */
+#define MRDEM_STAT_LEVEL_SWEEPS 24 /* surrogate pairs given the penalty sweep (all levels) */
 #define MRDEM_STAT_COUNT 32
 
 typedef struct mrdem_params {
@@ -87,6 +88,7 @@ typedef struct mrdem_params {
   int32_t tile_blocks_per_sm;
   int32_t level_warps;
   int32_t exact_threads;
+  int64_t cap_sweep;      /* capacity of the list of pairs waiting for the penalty sweep */
 } mrdem_params;
 
 /* Contact output.  All arrays are caller-owned device memory of `capacity`
@@ -133,7 +135,8 @@ int mrdem_get_params(const mrdem_ctx* ctx, mrdem_params* out);
 /* Change the sweep constants / launch shapes (not the capacities) of a context. */
 int mrdem_set_params(mrdem_ctx* ctx, const mrdem_params* p);
 /* Reallocate the work lists (0 keeps a capacity).  Synchronises the device. */
-int mrdem_reserve(mrdem_ctx* ctx, int64_t cap_level, int64_t cap_tiles, int64_t cap_candidates);
+int mrdem_reserve(mrdem_ctx* ctx, int64_t cap_level, int64_t cap_tiles, int64_t cap_candidates,
+                  int64_t cap_sweep);
 
 /* Build the surrogate trees of n_particles meshes (Sec. 4, Algorithm 7,
  * Appendix A) on the host.  Host inputs: vert_off [n+1] and tri_off [n+1]
@@ -192,8 +195,9 @@ int mrdem_detect(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const 
 
 /* Synchronise `stream` and report the latched device-side status of ctx since
  * the last check: CAPACITY (a work list or a contact buffer overflowed; the
- * required sizes go to required[0..3] = level list, tiles, candidates,
- * contacts when required != NULL), NONFINITE, or OK.  Clears the latch. */
+ * required sizes go to required[0..4] = level list, tiles, candidates,
+ * contacts, sweep list when required != NULL), NONFINITE, or OK.  Clears the
+ * latch. */
 int mrdem_check(mrdem_ctx* ctx, mrdem_stream stream, int64_t* required);
 
 /* Penalty forces of a contact set (Sec. 2, F(c)):

@@ -32,6 +32,7 @@ MRDEM_STAT_CONTACTS = 20
 MRDEM_STAT_FP64 = 21
 MRDEM_STAT_SPHERE_TESTS = 22
 MRDEM_STAT_FINE_SURROGATE = 23
+MRDEM_STAT_LEVEL_SWEEPS = 24
 MRDEM_STAT_COUNT = 32
 
 
@@ -42,7 +43,7 @@ class mrdem_params(C.Structure):
         ("leaf_min", C.c_int32), ("kmeans_iters", C.c_int32), ("cap_level", C.c_int64),
         ("cap_tiles", C.c_int64), ("cap_candidates", C.c_int64), ("tile_warps", C.c_int32),
         ("tile_blocks_per_sm", C.c_int32), ("level_warps", C.c_int32),
-        ("exact_threads", C.c_int32),
+        ("exact_threads", C.c_int32), ("cap_sweep", C.c_int64),
     ]
 
 
@@ -73,7 +74,7 @@ SIGNATURES = {
     "mrdem_destroy": (C.c_int, [_P]),
     "mrdem_get_params": (C.c_int, [_P, C.POINTER(mrdem_params)]),
     "mrdem_set_params": (C.c_int, [_P, C.POINTER(mrdem_params)]),
-    "mrdem_reserve": (C.c_int, [_P, _I64, _I64, _I64]),
+    "mrdem_reserve": (C.c_int, [_P, _I64, _I64, _I64, _I64]),
     "mrdem_build_hierarchy_host": (C.c_int, [C.POINTER(mrdem_params), _I, _P, _P, _P, _P,
                                              C.POINTER(_P)]),
     "mrdem_hier_upload": (C.c_int, [_P, _P]),

@@ -62,9 +62,9 @@ class Context:
             setattr(p, k, v)
         L.check(L.load().mrdem_set_params(self.handle, C.byref(p)), "mrdem_set_params")
 
-    def reserve(self, cap_level=0, cap_tiles=0, cap_candidates=0):
+    def reserve(self, cap_level=0, cap_tiles=0, cap_candidates=0, cap_sweep=0):
         L.check(L.load().mrdem_reserve(self.handle, int(cap_level), int(cap_tiles),
-                                       int(cap_candidates)), "mrdem_reserve")
+                                       int(cap_candidates), int(cap_sweep)), "mrdem_reserve")
 
     def profile(self, enable: bool):
         L.check(L.load().mrdem_profile(self.handle, int(bool(enable))), "mrdem_profile")
@@ -230,7 +230,7 @@ def detect(ctx: Context, hier: Hierarchy, pairs, eps, poses, precision="fp32", c
                                  C.byref(cs), _p(stats), _stream(stream)), "mrdem_detect")
         if not check:
             return contacts, stats
-        req = np.zeros(4, np.int64)
+        req = np.zeros(5, np.int64)
         st = lib.mrdem_check(ctx.handle, _stream(stream), _np_ptr(req))
         if st == L.MRDEM_OK:
             return contacts, stats
@@ -239,8 +239,9 @@ def detect(ctx: Context, hier: Hierarchy, pairs, eps, poses, precision="fp32", c
         prm = ctx.params
         grow = lambda need, cap: int(need * 1.25) + 1024 if need > cap else 0  # noqa: E731
         lv, ti, ca = grow(req[0], prm.cap_level), grow(req[1], prm.cap_tiles), grow(req[2], prm.cap_candidates)
-        if lv or ti or ca:
-            ctx.reserve(lv, ti, ca)
+        sw = grow(req[4], prm.cap_sweep)
+        if lv or ti or ca or sw:
+            ctx.reserve(lv, ti, ca, sw)
         if req[3] > contacts.capacity:
             contacts.resize(int(req[3] * 1.25) + 1024)
     raise L.MrdemError(L.MRDEM_ERR_CAPACITY, "mrdem_detect (retries exhausted)")
@@ -258,7 +259,7 @@ def detect_plain_fp64(ctx, hier, pairs, eps, poses, contacts=None, stream=None):
         L.check(lib.mrdem_detect_plain_fp64(ctx.handle, hier.handle, P, _p(pairs), _p(eps),
                                             _p(poses), C.byref(cs), _stream(stream)),
                 "mrdem_detect_plain_fp64")
-        req = np.zeros(4, np.int64)
+        req = np.zeros(5, np.int64)
         st = lib.mrdem_check(ctx.handle, _stream(stream), _np_ptr(req))
         if st == L.MRDEM_OK:
             return contacts

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -18,7 +19,8 @@ bool params_ok(const mrdem_params& p) {
          p.fanout >= 2 && p.fanout <= 8 && p.leaf_max >= 1 && p.leaf_max <= 32 && p.leaf_min >= 1 &&
          p.kmeans_iters >= 0 && p.cap_level > 0 && p.cap_tiles > 0 && p.cap_candidates > 0 &&
          p.cap_level < (int64_t)1 << 31 && p.cap_tiles < (int64_t)1 << 31 &&
-         p.cap_candidates < (int64_t)1 << 31 && p.tile_warps >= 1 && p.tile_warps <= 8 &&
+         p.cap_candidates < (int64_t)1 << 31 && p.cap_sweep > 0 && p.cap_sweep < (int64_t)1 << 31 &&
+         p.tile_warps >= 1 && p.tile_warps <= 8 &&
          p.tile_blocks_per_sm >= 1 && p.tile_blocks_per_sm <= 64 && p.level_warps >= 1 &&
          p.level_warps <= 32 && p.exact_threads >= 32 && p.exact_threads <= 1024 &&
          p.exact_threads % 32 == 0;
@@ -29,18 +31,21 @@ void free_lists(mrdem_ctx* c) {
   cudaFree(c->level_list[1]);
   cudaFree(c->tiles);
   cudaFree(c->cands);
+  cudaFree(c->sweep);
+  c->sweep = nullptr;
   c->level_list[0] = c->level_list[1] = nullptr;
   c->tiles = nullptr;
   c->cands = nullptr;
-  c->cap_level = c->cap_tiles = c->cap_cands = 0;
+  c->cap_level = c->cap_tiles = c->cap_cands = c->cap_sweep = 0;
 }
 
-int alloc_lists(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca) {
+int alloc_lists(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca, int64_t sw) {
   free_lists(c);
   if (cudaMalloc(&c->level_list[0], sizeof(int4) * lv) != cudaSuccess ||
       cudaMalloc(&c->level_list[1], sizeof(int4) * lv) != cudaSuccess ||
       cudaMalloc(&c->tiles, sizeof(TileItem) * ti) != cudaSuccess ||
-      cudaMalloc(&c->cands, sizeof(int3) * ca) != cudaSuccess) {
+      cudaMalloc(&c->cands, sizeof(int3) * ca) != cudaSuccess ||
+      cudaMalloc(&c->sweep, sizeof(int4) * sw) != cudaSuccess) {
     cudaGetLastError();
     free_lists(c);
     return MRDEM_ERR_OOM;
@@ -48,6 +53,7 @@ int alloc_lists(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca) {
   c->cap_level = lv;
   c->cap_tiles = ti;
   c->cap_cands = ca;
+  c->cap_sweep = sw;
   return MRDEM_OK;
 }
 
@@ -89,6 +95,7 @@ void mrdem_default_params(mrdem_params* p) {
   p->tile_blocks_per_sm = 4;
   p->level_warps = 8;
   p->exact_threads = 128;
+  p->cap_sweep = (int64_t)1 << 25;
 }
 
 const char* mrdem_status_string(int s) {
@@ -120,7 +127,7 @@ int mrdem_create(mrdem_ctx** out, int device, const mrdem_params* p) {
   c->device = device;
   c->params = prm;
   cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device);
-  int st = alloc_lists(c, prm.cap_level, prm.cap_tiles, prm.cap_candidates);
+  int st = alloc_lists(c, prm.cap_level, prm.cap_tiles, prm.cap_candidates, prm.cap_sweep);
   if (st == MRDEM_OK &&
       (cudaMalloc(&c->counters, sizeof(unsigned long long) * CNT_TOTAL) != cudaSuccess ||
        cudaMalloc(&c->status, sizeof(unsigned long long) * ST_TOTAL) != cudaSuccess ||
@@ -165,26 +172,30 @@ int mrdem_set_params(mrdem_ctx* c, const mrdem_params* p) {
   n.cap_level = c->params.cap_level;
   n.cap_tiles = c->params.cap_tiles;
   n.cap_candidates = c->params.cap_candidates;
+  n.cap_sweep = c->params.cap_sweep;
   if (!params_ok(n)) return MRDEM_ERR_INVALID;
   c->params = n;
   for (int& o : c->occ) o = 0;  // launch shapes may have changed
   return MRDEM_OK;
 }
 
-int mrdem_reserve(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca) {
-  if (!c || lv < 0 || ti < 0 || ca < 0) return MRDEM_ERR_INVALID;
+int mrdem_reserve(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca, int64_t sw) {
+  if (!c || lv < 0 || ti < 0 || ca < 0 || sw < 0) return MRDEM_ERR_INVALID;
   DeviceGuard g(c->device);
   lv = lv ? lv : c->cap_level;
   ti = ti ? ti : c->cap_tiles;
   ca = ca ? ca : c->cap_cands;
-  if (lv >= (int64_t)1 << 31 || ti >= (int64_t)1 << 31 || ca >= (int64_t)1 << 31)
+  sw = sw ? sw : c->cap_sweep;
+  if (lv >= (int64_t)1 << 31 || ti >= (int64_t)1 << 31 || ca >= (int64_t)1 << 31 ||
+      sw >= (int64_t)1 << 31)
     return MRDEM_ERR_INVALID;
   if (cudaDeviceSynchronize() != cudaSuccess) return MRDEM_ERR_CUDA;
-  int st = alloc_lists(c, lv, ti, ca);
+  int st = alloc_lists(c, lv, ti, ca, sw);
   if (st == MRDEM_OK) {
     c->params.cap_level = lv;
     c->params.cap_tiles = ti;
     c->params.cap_candidates = ca;
+    c->params.cap_sweep = sw;
   }
   return st;
 }
@@ -224,11 +235,13 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
   int64_t stride = (h.n_tri_pad + 31) / 32 * 32;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   size_t sz_geo = al(sizeof(float4) * 3 * h.n_nodes), sz_child = al(sizeof(int2) * h.n_nodes);
+  size_t sz_sph = al(sizeof(float4) * h.n_nodes);
   size_t sz_tri = al(sizeof(float) * 9 * stride), sz_vid = al(sizeof(int32_t) * 3 * stride);
   size_t sz_slot = al(sizeof(int32_t) * stride), sz_ts = al(sizeof(int32_t) * h.n_tri);
   size_t sz_off = al(sizeof(int64_t) * (h.n_particles + 1));
   size_t sz_root = al(sizeof(int32_t) * h.n_particles), sz_br = al(sizeof(float) * h.n_particles);
-  size_t total = sz_geo + sz_child + sz_tri + sz_vid + sz_slot + sz_ts + sz_off + sz_root + sz_br;
+  size_t total = sz_geo + sz_child + sz_tri + sz_vid + sz_slot + sz_ts + sz_off + sz_root + sz_br +
+                 sz_sph;
   char* base = nullptr;
   if (cudaMalloc(&base, total) != cudaSuccess) {
     cudaGetLastError();
@@ -239,13 +252,29 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     char* p = buf.data();
     size_t o_geo = 0, o_child = o_geo + sz_geo, o_tri = o_child + sz_child, o_vid = o_tri + sz_tri;
     size_t o_slot = o_vid + sz_vid, o_ts = o_slot + sz_slot, o_off = o_ts + sz_ts;
-    size_t o_root = o_off + sz_off, o_br = o_root + sz_root;
+    size_t o_root = o_off + sz_off, o_br = o_root + sz_root, o_sph = o_br + sz_br;
     float4* geo = (float4*)(p + o_geo);
     for (int64_t n = 0; n < h.n_nodes; ++n) {
       const float* t = &h.node_tri[9 * n];
       geo[3 * n + 0] = make_float4(t[0], t[1], t[2], h.node_delta[n]);
       geo[3 * n + 1] = make_float4(t[3], t[4], t[5], 0.f);
       geo[3 * n + 2] = make_float4(t[6], t[7], t[8], 0.f);
+    }
+    // node spheres: centroid of the surrogate triangle and the largest vertex
+    // distance plus delta, computed in double and rounded up
+    float4* sph = (float4*)(p + o_sph);
+    for (int64_t n = 0; n < h.n_nodes; ++n) {
+      const float* t = &h.node_tri[9 * n];
+      double c[3];
+      for (int k = 0; k < 3; ++k) c[k] = ((double)t[k] + (double)t[3 + k] + (double)t[6 + k]) / 3.0;
+      double r2 = 0;
+      for (int v = 0; v < 3; ++v) {
+        double d2 = 0;
+        for (int k = 0; k < 3; ++k) d2 += ((double)t[3 * v + k] - c[k]) * ((double)t[3 * v + k] - c[k]);
+        r2 = std::max(r2, d2);
+      }
+      double r = (std::sqrt(r2) + (double)h.node_delta[n]) * (1.0 + 1e-6) + 1e-30;
+      sph[n] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)r);
     }
     std::memcpy(p + o_child, h.node_child.data(), sizeof(int32_t) * 2 * h.n_nodes);
     float* tri = (float*)(p + o_tri);
@@ -277,6 +306,7 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     d.tri_off = (const int64_t*)(base + o_off);
     d.root = (const int32_t*)(base + o_root);
     d.bound_r = (const float*)(base + o_br);
+    d.node_sph = (const float4*)(base + o_sph);
     d.stride = stride;
     d.n_tri = h.n_tri;
     d.n_particles = h.n_particles;
@@ -373,9 +403,11 @@ int mrdem_check(mrdem_ctx* c, mrdem_stream s, int64_t* required) {
     required[1] = (int64_t)st[ST_REQ_TILES];
     required[2] = (int64_t)st[ST_REQ_CANDS];
     required[3] = (int64_t)st[ST_REQ_CONTACTS];
+    required[4] = (int64_t)st[ST_REQ_SWEEP];
   }
   if (st[ST_NONFINITE]) return MRDEM_ERR_NONFINITE;
-  if (st[ST_REQ_LEVEL] || st[ST_REQ_TILES] || st[ST_REQ_CANDS] || st[ST_REQ_CONTACTS])
+  if (st[ST_REQ_LEVEL] || st[ST_REQ_TILES] || st[ST_REQ_CANDS] || st[ST_REQ_CONTACTS] ||
+      st[ST_REQ_SWEEP])
     return MRDEM_ERR_CAPACITY;
   return MRDEM_OK;
 }
@@ -426,9 +458,9 @@ int mrdem_triangle_distance(mrdem_ctx* c, int64_t n, const double* P, const doub
                                   sconv, (cudaStream_t)s);
 }
 
-static const char* kKernelNames[K_COUNT] = {"k_setup",  "k_level", "k_tile",  "k_exact",
-                                            "k_exact64", "k_forces", "k_grad", "k_plain",
-                                            "k_tridist"};
+static const char* kKernelNames[K_COUNT] = {
+    "k_setup", "k_expand", "k_sweep_nodes", "k_tile",  "k_sweep_fine", "k_exact",
+    "k_exact64", "k_forces", "k_grad",       "k_plain", "k_tridist"};
 
 int mrdem_profile(mrdem_ctx* c, int32_t enable) {
   if (!c) return MRDEM_ERR_INVALID;

@@ -209,138 +209,139 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
 }
 
 // ---------------------------------------------------------------------------
-// k_level: one warp per level item (the child sets of a surviving node
-// pair).  Each child surrogate is staged with a bounding sphere of its
-// eps-free environment (centroid, largest vertex distance + delta); child
-// pairs whose spheres are farther apart than 2 eps are dropped, the rest are
-// compacted and given the penalty sweep + certificate against
-// delta_a + delta_b + 2 eps.  Items are taken in a fixed interleaved order and
-// the next one is loaded while the current one is processed.
+// The surrogate and fine tests are split into cheap culling kernels that
+// emit compact lists of surviving pairs (the buffered comparisons of
+// Sec. 5.4) and thread-per-pair sweep kernels that process those lists with
+// every lane busy:
+//   k_expand       one warp per level item: the child pairs of a surviving
+//                  node pair get a bounding-sphere test (node spheres
+//                  precomputed in the body frame, radius including delta);
+//                  survivors go to the sweep list;
+//   k_sweep_nodes  one thread per listed node pair: penalty sweep + certificate
+//                  against delta_a + delta_b + 2 eps; survivors become the
+//                  next level's items, or leaf-pair tiles when both are leaves;
+//   k_tile         one warp per leaf pair: fine triangles staged in shared
+//                  memory, each tested against the other leaf's surrogate
+//                  (Algorithm 5's fine-against-surrogate comparison), then the
+//                  kept products against each other's bounding spheres;
+//                  survivors go to the fine list;
+//   k_sweep_fine   one thread per listed fine pair: the penalty sweep of
+//                  Eq. 3/4 and the certificate at 2 eps; survivors are the
+//                  candidates of the exact distance.
+// Lists are taken in a fixed interleaved order by grids of exactly one
+// resident wave.
+
+// k_expand --------------------------------------------------------------------
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 3) k_level(HierDev H, const PairXf* __restrict__ xf,
-                                                         SweepConst sc, const int4* __restrict__ in,
-                                                         int level, int4* out, TileItem* tiles,
-                                                         unsigned long long* cnt,
-                                                         unsigned long long* status,
-                                                         int64_t cap_level, int64_t cap_tiles) {
-  __shared__ float4 sgeo[WARPS][16][3];
+__global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* __restrict__ xf,
+                                                       const int4* __restrict__ in, int level,
+                                                       int4* sweep, unsigned long long* cnt,
+                                                       unsigned long long* status,
+                                                       int64_t cap_level, int64_t cap_sweep) {
   __shared__ float4 ssph[WARPS][16];
-  __shared__ int2 sinfo[WARPS][16];
-  __shared__ int snode[WARPS][16];
-  __shared__ unsigned char squeue[WARPS][64];
   const int w = threadIdx.x >> 5, lane = lane_id();
   int64_t n_in = (int64_t)cnt[CNT_LEVEL + level];
   if (n_in > cap_level) n_in = cap_level;
   const int slot_tests = MRDEM_STAT_TESTS + (level + 1 < MRDEM_STAT_LEVELS ? level + 1 : MRDEM_STAT_LEVELS - 1);
-  WarpCount tests, surv;
+  WarpCount tests;
   const int64_t step = (int64_t)gridDim.x * WARPS;
   int64_t item = (int64_t)blockIdx.x * WARPS + w;
   int4 nxt = item < n_in ? in[item] : make_int4(0, 0, 0, 0);
   for (; item < n_in; item += step) {
     const int4 it = nxt;
     if (item + step < n_in) nxt = in[item + step];
-    PairXf X;
-    load_pairxf(xf, it.x, X);
     int na = it.w & 0xff, nb = (it.w >> 8) & 0xff;
-    bool stage = lane < na || (lane >= 8 && lane < 8 + nb);
-    if (stage) {
-      int node = lane < 8 ? it.y + lane : it.z + lane - 8;
-      float4 g0 = H.node_geo[3 * node], g1 = H.node_geo[3 * node + 1], g2 = H.node_geo[3 * node + 2];
-      int2 info = H.node_child[node];
-      F3 p0 = {g0.x, g0.y, g0.z}, p1 = {g1.x, g1.y, g1.z}, p2 = {g2.x, g2.y, g2.z};
-      if (lane >= 8) {
-        p0 = xf_point(X, p0);
-        p1 = xf_point(X, p1);
-        p2 = xf_point(X, p2);
-      }
-      sgeo[w][lane][0] = make_float4(p0.x, p0.y, p0.z, g0.w);
-      sgeo[w][lane][1] = make_float4(p1.x, p1.y, p1.z, 0.f);
-      sgeo[w][lane][2] = make_float4(p2.x, p2.y, p2.z, 0.f);
-      F3 c = (1.f / 3.f) * ((p0 + p1) + p2);
-      F3 d0 = p0 - c, d1 = p1 - c, d2 = p2 - c;
-      float r = sqrtf(fmaxf(dot(d0, d0), fmaxf(dot(d1, d1), dot(d2, d2)))) * (1.f + 1e-6f) + g0.w;
-      ssph[w][lane] = make_float4(c.x, c.y, c.z, r);
-      sinfo[w][lane] = info;
-      snode[w][lane] = node;
+    if (lane < na) {
+      ssph[w][lane] = __ldg(H.node_sph + it.y + lane);
+    } else if (lane >= 8 && lane < 8 + nb) {
+      PairXf X;
+      load_pairxf(xf, it.x, X);
+      float4 sp = __ldg(H.node_sph + it.z + lane - 8);
+      F3 c = xf_point(X, {sp.x, sp.y, sp.z});
+      ssph[w][lane] = make_float4(c.x, c.y, c.z, sp.w + X.tau + X.margin);
     }
     __syncwarp();
     const int total = na * nb;
-    const float thr = X.tau + X.margin;
-    // sphere test of all child pairs, survivors queued
-    int nq = 0;
     for (int f0 = 0; f0 < total; f0 += 32) {
       int f = f0 + lane;
       bool act = f < total;
       int i = act ? f / nb : 0, j = act ? f - (f / nb) * nb : 0;
       float4 p = ssph[w][i], q = ssph[w][8 + j];
       float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-      float lim = (p.w + q.w) + thr;
+      float lim = p.w + q.w;  // q.w carries 2 eps + margin
       bool keep = act && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
-      unsigned m = __ballot_sync(0xffffffffu, keep);
-      if (keep) squeue[w][nq + __popc(m & ((1u << lane) - 1u))] = (unsigned char)((i << 3) | j);
-      nq += __popc(m);
       tests.add(act);
-    }
-    __syncwarp();
-    for (int q0 = 0; q0 < nq; q0 += 32) {
-      int k = q0 + lane;
-      bool act = k < nq;
-      int code = act ? squeue[w][k] : 0;
-      int i = code >> 3, j = 8 + (code & 7);
-      bool s = false;
-      if (act) {
-        float4 a0 = sgeo[w][i][0], a1 = sgeo[w][i][1], a2 = sgeo[w][i][2];
-        float4 b0 = sgeo[w][j][0], b1 = sgeo[w][j][1], b2 = sgeo[w][j][2];
-        bool cv;
-        float gap = sweep_certificate<false>({a0.x, a0.y, a0.z}, {a1.x, a1.y, a1.z}, {a2.x, a2.y, a2.z},
-                                             {b0.x, b0.y, b0.z}, {b1.x, b1.y, b1.z}, {b2.x, b2.y, b2.z},
-                                             sc, 0.f, &cv, nullptr);
-        s = !(gap > a0.w + b0.w + thr);
-      }
-      int2 ia = sinfo[w][i], ib = sinfo[w][j];
-      int ni = snode[w][i], nj = snode[w][j];
-      bool leaves = ia.y < 0 && ib.y < 0;
-      surv.add(s);
-      warp_append(s && leaves, make_tile(it.x, ni, nj, ia, ib), tiles, cnt + CNT_TILES, cap_tiles,
-                  status + ST_REQ_TILES);
-      warp_append(s && !leaves, make_level(it.x, ni, nj, ia, ib), out, cnt + CNT_LEVEL + level + 1,
-                  cap_level, status + ST_REQ_LEVEL);
+      warp_append(keep, make_int4(it.x, it.y + i, it.z + j, 0), sweep, cnt + CNT_SWEEP, cap_sweep,
+                  status + ST_REQ_SWEEP);
     }
     __syncwarp();
   }
   tests.flush(cnt + CNT_STATS + slot_tests);
-  surv.flush(cnt + CNT_STATS + slot_tests + MRDEM_STAT_SURVIVORS);
 }
 
-// ---------------------------------------------------------------------------
-// k_tile: one warp per leaf pair.  Both leaves' fine triangles are staged in
-// shared memory (B moved into A's frame) with a bounding sphere each
-// (centroid, largest vertex distance).  Each fine triangle is first tested
-// against the other leaf's surrogate and its slack (Algorithm 5's comparison
-// of a fine triangle with a surrogate); the products of the kept triangles
-// get a bounding-sphere test, and the surviving pairs are compacted into a
-// per-warp queue (the buffered comparisons of Sec. 5.4) that the penalty
-// sweep + certificate then processes one fine pair per lane.  Tiles are taken
-// in a fixed interleaved order; the next tile item is loaded ahead.
-constexpr int kTileQueue = 1024;  // 32 x 32 products
+// k_sweep_nodes ---------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sweep_nodes(HierDev H, const PairXf* __restrict__ xf,
+                                                     SweepConst sc, const int4* __restrict__ sweep,
+                                                     int level, int4* out, TileItem* tiles,
+                                                     unsigned long long* cnt,
+                                                     unsigned long long* status, int64_t cap_sweep,
+                                                     int64_t cap_level, int64_t cap_tiles) {
+  int64_t n = (int64_t)cnt[CNT_SWEEP];
+  if (n > cap_sweep) n = cap_sweep;
+  const int slot_surv = MRDEM_STAT_SURVIVORS + (level + 1 < MRDEM_STAT_LEVELS ? level + 1 : MRDEM_STAT_LEVELS - 1);
+  WarpCount nsweep, surv;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    int64_t k = base + threadIdx.x;
+    bool act = k < n, s = false;
+    int4 e = act ? sweep[k] : make_int4(0, 0, 0, 0);
+    int2 ia = make_int2(0, 1), ib = make_int2(0, 1);
+    if (act) {
+      PairXf X;
+      load_pairxf(xf, e.x, X);
+      float4 a0 = __ldg(H.node_geo + 3 * e.y), a1 = __ldg(H.node_geo + 3 * e.y + 1);
+      float4 a2 = __ldg(H.node_geo + 3 * e.y + 2);
+      float4 b0 = __ldg(H.node_geo + 3 * e.z), b1 = __ldg(H.node_geo + 3 * e.z + 1);
+      float4 b2 = __ldg(H.node_geo + 3 * e.z + 2);
+      ia = __ldg(H.node_child + e.y);
+      ib = __ldg(H.node_child + e.z);
+      F3 q0 = xf_point(X, {b0.x, b0.y, b0.z}), q1 = xf_point(X, {b1.x, b1.y, b1.z});
+      F3 q2 = xf_point(X, {b2.x, b2.y, b2.z});
+      bool cv;
+      float gap;
+      if (sc.n_iter == 4)
+        gap = sweep_certificate<false, 4>({a0.x, a0.y, a0.z}, {a1.x, a1.y, a1.z}, {a2.x, a2.y, a2.z},
+                                          q0, q1, q2, sc, 0.f, &cv, nullptr);
+      else
+        gap = sweep_certificate<false, 0>({a0.x, a0.y, a0.z}, {a1.x, a1.y, a1.z}, {a2.x, a2.y, a2.z},
+                                          q0, q1, q2, sc, 0.f, &cv, nullptr);
+      s = !(gap > a0.w + b0.w + X.tau + X.margin);
+    }
+    bool leaves = ia.y < 0 && ib.y < 0;
+    nsweep.add(act);
+    surv.add(s);
+    warp_append(s && leaves, make_tile(e.x, e.y, e.z, ia, ib), tiles, cnt + CNT_TILES, cap_tiles,
+                status + ST_REQ_TILES);
+    warp_append(s && !leaves, make_level(e.x, e.y, e.z, ia, ib), out, cnt + CNT_LEVEL + level + 1,
+                cap_level, status + ST_REQ_LEVEL);
+  }
+  nsweep.flush(cnt + CNT_STATS + MRDEM_STAT_LEVEL_SWEEPS);
+  surv.flush(cnt + CNT_STATS + slot_surv);
+}
+
+// k_tile ----------------------------------------------------------------------
 struct TileSmem {
-  float4 a[3][32];  // A: v0, v1, v2 (xyz)
-  float4 b[3][32];  // B (in A's frame)
-  float4 sa[32];    // bounding spheres: centroid xyz, radius
+  float4 sa[32];  // bounding spheres: centroid xyz, radius
   float4 sb[32];
   unsigned char ka[32], kb[32];  // triangles kept by the fine-vs-surrogate test
-  unsigned short q[kTileQueue];  // fine pairs kept by the sphere test
 };
 
-// Stage one fine triangle: vertices and bounding sphere (centroid, largest
-// vertex distance, rounded up).
-__device__ __forceinline__ float4 stage_triangle(F3 v0, F3 v1, F3 v2, float4 (*dst)[32], int lane) {
+// Bounding sphere of a triangle: centroid and largest vertex distance
+// (rounded up).
+__device__ __forceinline__ float4 tri_sphere(F3 v0, F3 v1, F3 v2) {
   F3 c = (1.f / 3.f) * ((v0 + v1) + v2);
   F3 d0 = v0 - c, d1 = v1 - c, d2 = v2 - c;
   float r2 = fmaxf(dot(d0, d0), fmaxf(dot(d1, d1), dot(d2, d2)));
-  dst[0][lane] = make_float4(v0.x, v0.y, v0.z, 0.f);
-  dst[1][lane] = make_float4(v1.x, v1.y, v1.z, 0.f);
-  dst[2][lane] = make_float4(v2.x, v2.y, v2.z, 0.f);
   return make_float4(c.x, c.y, c.z, sqrtf(r2) * (1.f + 1e-6f));
 }
 
@@ -365,24 +366,26 @@ __device__ __forceinline__ TileItem load_tile(const TileItem* tiles, int64_t t) 
   return r;
 }
 
-template <bool CONV>
-__global__ void __launch_bounds__(256, 3) k_tile(HierDev H, const PairXf* __restrict__ xf,
-                                                 SweepConst sc, float conv_c,
-                                                 const TileItem* __restrict__ tiles, int3* cands,
-                                                 unsigned long long* cnt,
-                                                 unsigned long long* status, int64_t cap_tiles,
-                                                 int64_t cap_cands,
-                                                 const double* __restrict__ eps_d) {
-  extern __shared__ float4 smem4[];
+__device__ __forceinline__ F3 load_vertex(const HierDev& H, int slot, int c) {
+  return {__ldg(H.tri + (3 * c + 0) * H.stride + slot), __ldg(H.tri + (3 * c + 1) * H.stride + slot),
+          __ldg(H.tri + (3 * c + 2) * H.stride + slot)};
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_tile(HierDev H, const PairXf* __restrict__ xf,
+                                                     const TileItem* __restrict__ tiles,
+                                                     int4* fine, unsigned long long* cnt,
+                                                     unsigned long long* status, int64_t cap_tiles,
+                                                     int64_t cap_fine) {
+  __shared__ TileSmem smem[WARPS];
   const int w = threadIdx.x >> 5, lane = lane_id();
-  const int warps = blockDim.x >> 5;
-  TileSmem& S = reinterpret_cast<TileSmem*>(smem4)[w];
+  TileSmem& S = smem[w];
   int64_t n_tiles = (int64_t)cnt[CNT_TILES];
   if (n_tiles > cap_tiles) n_tiles = cap_tiles;
-  WarpCount tests, spheres, ncand, nodot;
+  WarpCount spheres;
   unsigned ntile = 0, nfvs = 0;
-  const int64_t step = (int64_t)gridDim.x * warps;
-  int64_t t = (int64_t)blockIdx.x * warps + w;
+  const int64_t step = (int64_t)gridDim.x * WARPS;
+  int64_t t = (int64_t)blockIdx.x * WARPS + w;
   TileItem nxt;
   if (t < n_tiles) nxt = load_tile(tiles, t);
   for (; t < n_tiles; t += step) {
@@ -391,44 +394,30 @@ __global__ void __launch_bounds__(256, 3) k_tile(HierDev H, const PairXf* __rest
     ++ntile;
     PairXf X;
     load_pairxf(xf, it.pair, X);
-    float ce = conv_c * (float)__ldg(eps_d + it.pair);
-    float conv_tol2 = ce * ce;
     int na = it.counts & 0xff, nb = (it.counts >> 8) & 0xff;
     const float thr = X.tau + X.margin;
-    // surrogates of the two leaves (B's moved into A's frame) with slack
-    float4 ga0 = H.node_geo[3 * it.node_a], ga1 = H.node_geo[3 * it.node_a + 1];
-    float4 ga2 = H.node_geo[3 * it.node_a + 2];
-    float4 gb0 = H.node_geo[3 * it.node_b], gb1 = H.node_geo[3 * it.node_b + 1];
-    float4 gb2 = H.node_geo[3 * it.node_b + 2];
     bool keep_a = false, keep_b = false;
-    F3 B0 = xf_point(X, {gb0.x, gb0.y, gb0.z}), B1 = xf_point(X, {gb1.x, gb1.y, gb1.z});
-    F3 B2 = xf_point(X, {gb2.x, gb2.y, gb2.z});
     if (lane < na) {
-      F3 v[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        v[c].x = __ldg(H.tri + (3 * c + 0) * H.stride + it.slot_a + lane);
-        v[c].y = __ldg(H.tri + (3 * c + 1) * H.stride + it.slot_a + lane);
-        v[c].z = __ldg(H.tri + (3 * c + 2) * H.stride + it.slot_a + lane);
-      }
-      float4 sp = stage_triangle(v[0], v[1], v[2], S.a, lane);
+      float4 gb0 = __ldg(H.node_geo + 3 * it.node_b), gb1 = __ldg(H.node_geo + 3 * it.node_b + 1);
+      float4 gb2 = __ldg(H.node_geo + 3 * it.node_b + 2);
+      F3 v0 = load_vertex(H, it.slot_a + lane, 0), v1 = load_vertex(H, it.slot_a + lane, 1);
+      F3 v2 = load_vertex(H, it.slot_a + lane, 2);
+      float4 sp = tri_sphere(v0, v1, v2);
       S.sa[lane] = sp;
-      keep_a = sphere_near_triangle(sp, B0, B1, B2, gb0.w + thr);
+      keep_a = sphere_near_triangle(sp, xf_point(X, {gb0.x, gb0.y, gb0.z}),
+                                    xf_point(X, {gb1.x, gb1.y, gb1.z}),
+                                    xf_point(X, {gb2.x, gb2.y, gb2.z}), gb0.w + thr);
     }
-    F3 A0 = {ga0.x, ga0.y, ga0.z}, A1 = {ga1.x, ga1.y, ga1.z}, A2 = {ga2.x, ga2.y, ga2.z};
     if (lane < nb) {
-      F3 v[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        F3 u;
-        u.x = __ldg(H.tri + (3 * c + 0) * H.stride + it.slot_b + lane);
-        u.y = __ldg(H.tri + (3 * c + 1) * H.stride + it.slot_b + lane);
-        u.z = __ldg(H.tri + (3 * c + 2) * H.stride + it.slot_b + lane);
-        v[c] = xf_point(X, u);
-      }
-      float4 sp = stage_triangle(v[0], v[1], v[2], S.b, lane);
+      float4 ga0 = __ldg(H.node_geo + 3 * it.node_a), ga1 = __ldg(H.node_geo + 3 * it.node_a + 1);
+      float4 ga2 = __ldg(H.node_geo + 3 * it.node_a + 2);
+      F3 v0 = xf_point(X, load_vertex(H, it.slot_b + lane, 0));
+      F3 v1 = xf_point(X, load_vertex(H, it.slot_b + lane, 1));
+      F3 v2 = xf_point(X, load_vertex(H, it.slot_b + lane, 2));
+      float4 sp = tri_sphere(v0, v1, v2);
       S.sb[lane] = sp;
-      keep_b = sphere_near_triangle(sp, A0, A1, A2, ga0.w + thr);
+      keep_b = sphere_near_triangle(sp, {ga0.x, ga0.y, ga0.z}, {ga1.x, ga1.y, ga1.z},
+                                    {ga2.x, ga2.y, ga2.z}, ga0.w + thr);
     }
     unsigned ma = __ballot_sync(0xffffffffu, keep_a), mb = __ballot_sync(0xffffffffu, keep_b);
     if (keep_a) S.ka[__popc(ma & ((1u << lane) - 1u))] = (unsigned char)lane;
@@ -438,8 +427,6 @@ __global__ void __launch_bounds__(256, 3) k_tile(HierDev H, const PairXf* __rest
     __syncwarp();
     const int total = ka * kb;
     const float inv_kb = 1.0f / (float)(kb > 0 ? kb : 1);
-    // pass 1: bounding-sphere test of the kept products, survivors queued
-    int nq = 0;
     for (int f0 = 0; f0 < total; f0 += 32) {
       int f = f0 + lane;
       bool act = f < total;
@@ -451,45 +438,57 @@ __global__ void __launch_bounds__(256, 3) k_tile(HierDev H, const PairXf* __rest
       float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
       float lim = (p.w + q.w) + thr;
       bool keep = act && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
-      unsigned m = __ballot_sync(0xffffffffu, keep);
-      if (keep) S.q[nq + __popc(m & ((1u << lane) - 1u))] = (unsigned short)((i << 5) | j);
-      nq += __popc(m);
+      warp_append(keep, make_int4(it.pair, it.slot_a + i, it.slot_b + j, 0), fine, cnt + CNT_SWEEP,
+                  cap_fine, status + ST_REQ_SWEEP);
     }
     spheres.v += lane == 0 ? (unsigned)total : 0u;
-    __syncwarp();
-    // pass 2: penalty sweep + certificate on the queued pairs
-    for (int q0 = 0; q0 < nq; q0 += 32) {
-      int k = q0 + lane;
-      bool act = k < nq;
-      int code = act ? S.q[k] : 0;
-      int i = code >> 5, j = code & 31;
-      float4 a0 = S.a[0][i], a1 = S.a[1][i], a2 = S.a[2][i];
-      float4 b0 = S.b[0][j], b1 = S.b[1][j], b2 = S.b[2][j];
-      bool cv = true;
-      float gap;
-      if (sc.n_iter == 4)
-        gap = sweep_certificate<CONV, 4>({a0.x, a0.y, a0.z}, {a1.x, a1.y, a1.z}, {a2.x, a2.y, a2.z},
-                                         {b0.x, b0.y, b0.z}, {b1.x, b1.y, b1.z}, {b2.x, b2.y, b2.z},
-                                         sc, conv_tol2, &cv, nullptr);
-      else
-        gap = sweep_certificate<CONV, 0>({a0.x, a0.y, a0.z}, {a1.x, a1.y, a1.z}, {a2.x, a2.y, a2.z},
-                                         {b0.x, b0.y, b0.z}, {b1.x, b1.y, b1.z}, {b2.x, b2.y, b2.z},
-                                         sc, conv_tol2, &cv, nullptr);
-      bool s = act && !(gap > thr);
-      tests.add(act);
-      ncand.add(s);
-      if (CONV) nodot.add(s && !cv);
-      warp_append(s, make_int3(it.pair, it.slot_a + i, it.slot_b + j), cands, cnt + CNT_CANDS,
-                  cap_cands, status + ST_REQ_CANDS);
-    }
     __syncwarp();
   }
   if (lane == 0) {
     if (ntile) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_TILES, (unsigned long long)ntile);
     if (nfvs) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_FINE_SURROGATE, (unsigned long long)nfvs);
   }
-  tests.flush(cnt + CNT_STATS + MRDEM_STAT_FINE_TESTS);
   spheres.flush(cnt + CNT_STATS + MRDEM_STAT_SPHERE_TESTS);
+}
+
+// k_sweep_fine ----------------------------------------------------------------
+template <bool CONV>
+__global__ void __launch_bounds__(256) k_sweep_fine(HierDev H, const PairXf* __restrict__ xf,
+                                                    SweepConst sc, float conv_c,
+                                                    const int4* __restrict__ fine, int3* cands,
+                                                    unsigned long long* cnt,
+                                                    unsigned long long* status, int64_t cap_fine,
+                                                    int64_t cap_cands,
+                                                    const double* __restrict__ eps_d) {
+  int64_t n = (int64_t)cnt[CNT_SWEEP];
+  if (n > cap_fine) n = cap_fine;
+  WarpCount tests, ncand, nodot;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    int64_t k = base + threadIdx.x;
+    bool act = k < n, s = false, cv = true;
+    int4 e = act ? fine[k] : make_int4(0, 0, 0, 0);
+    if (act) {
+      PairXf X;
+      load_pairxf(xf, e.x, X);
+      float ce = conv_c * (float)__ldg(eps_d + e.x);
+      F3 p0 = load_vertex(H, e.y, 0), p1 = load_vertex(H, e.y, 1), p2 = load_vertex(H, e.y, 2);
+      F3 q0 = xf_point(X, load_vertex(H, e.z, 0)), q1 = xf_point(X, load_vertex(H, e.z, 1));
+      F3 q2 = xf_point(X, load_vertex(H, e.z, 2));
+      float gap;
+      if (sc.n_iter == 4)
+        gap = sweep_certificate<CONV, 4>(p0, p1, p2, q0, q1, q2, sc, ce * ce, &cv, nullptr);
+      else
+        gap = sweep_certificate<CONV, 0>(p0, p1, p2, q0, q1, q2, sc, ce * ce, &cv, nullptr);
+      s = !(gap > X.tau + X.margin);
+    }
+    tests.add(act);
+    ncand.add(s);
+    if (CONV) nodot.add(s && !cv);
+    warp_append(s, make_int3(e.x, e.y, e.z), cands, cnt + CNT_CANDS, cap_cands,
+                status + ST_REQ_CANDS);
+  }
+  tests.flush(cnt + CNT_STATS + MRDEM_STAT_FINE_TESTS);
   ncand.flush(cnt + CNT_STATS + MRDEM_STAT_CANDIDATES);
   if (CONV) nodot.flush(cnt + CNT_STATS + MRDEM_STAT_UNCONVERGED);
 }
@@ -801,28 +800,34 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
                                          c->cap_level, c->cap_tiles);
     }
     int steps = std::min(hier->h.max_depth - 1, kMaxLevels - 1);
+    constexpr int W = 8;
     for (int l = 0; l < steps; ++l) {
-      constexpr int W = 8;
-      int lb = one_wave(c, K_LEVEL, k_level<W>, W * 32, 0);
-      ProfScope ps(c, K_LEVEL, s);
-      k_level<W><<<lb, W * 32, 0, s>>>(H, c->xf, sc, c->level_list[l & 1], l,
-                                                  c->level_list[(l + 1) & 1], c->tiles,
-                                                  c->counters, c->status, c->cap_level,
-                                                  c->cap_tiles);
-    }
-    int tw = prm.tile_warps;
-    size_t smem = (size_t)tw * sizeof(TileSmem);
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaFuncSetAttribute(k_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * (int)sizeof(TileSmem));
-      attr_set = true;
+      {
+        int eb = one_wave(c, K_LEVEL, k_expand<W>, W * 32, 0);
+        ProfScope ps(c, K_LEVEL, s);
+        cudaMemsetAsync(c->counters + CNT_SWEEP, 0, sizeof(unsigned long long), s);
+        k_expand<W><<<eb, W * 32, 0, s>>>(H, c->xf, c->level_list[l & 1], l, c->sweep,
+                                          c->counters, c->status, c->cap_level, c->cap_sweep);
+      }
+      int nb = one_wave(c, K_SWEEP_NODES, k_sweep_nodes, 256, 0);
+      ProfScope ps(c, K_SWEEP_NODES, s);
+      k_sweep_nodes<<<nb, 256, 0, s>>>(H, c->xf, sc, c->sweep, l, c->level_list[(l + 1) & 1],
+                                       c->tiles, c->counters, c->status, c->cap_sweep,
+                                       c->cap_level, c->cap_tiles);
     }
     {
-    int tb = one_wave(c, K_TILE, k_tile<true>, tw * 32, smem);
-    ProfScope ps(c, K_TILE, s);
-    k_tile<true><<<tb, tw * 32, smem, s>>>(
-        H, c->xf, sc, prm.conv_c, c->tiles, c->cands, c->counters, c->status, c->cap_tiles,
-        c->cap_cands, eps);
+      int tb = one_wave(c, K_TILE, k_tile<W>, W * 32, 0);
+      ProfScope ps(c, K_TILE, s);
+      cudaMemsetAsync(c->counters + CNT_SWEEP, 0, sizeof(unsigned long long), s);
+      k_tile<W><<<tb, W * 32, 0, s>>>(H, c->xf, c->tiles, c->sweep, c->counters, c->status,
+                                      c->cap_tiles, c->cap_sweep);
+    }
+    {
+      int fb = one_wave(c, K_SWEEP_FINE, k_sweep_fine<true>, 256, 0);
+      ProfScope ps(c, K_SWEEP_FINE, s);
+      k_sweep_fine<true><<<fb, 256, 0, s>>>(H, c->xf, sc, prm.conv_c, c->sweep, c->cands,
+                                            c->counters, c->status, c->cap_sweep, c->cap_cands,
+                                            eps);
     }
     int et = prm.exact_threads;
     if (precision == MRDEM_PREC_FP64) {
@@ -834,11 +839,12 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
         ProfScope ps(c, K_EXACT, s);
         // the level lists are free once the tiles are done: reuse one as the fallback list
         k_exact32<<<c->n_sms * 8, et, 0, s>>>(H, c->xf64, c->cands, c->counters, c->status,
-                                               c->cap_cands, reinterpret_cast<int3*>(c->level_list[0]), c->cap_level, *out);
+                                               c->cap_cands, reinterpret_cast<int3*>(c->level_list[0]),
+                                               c->cap_level, *out);
       }
       ProfScope ps(c, K_EXACT64, s);
-      k_exact64<<<c->n_sms * 4, et, 0, s>>>(H, c->xf64, reinterpret_cast<const int3*>(c->level_list[0]), c->counters,
-                                             CNT_FALLBACK, c->cap_level, c->status,
+      k_exact64<<<c->n_sms * 4, et, 0, s>>>(H, c->xf64, reinterpret_cast<const int3*>(c->level_list[0]),
+                                             c->counters, CNT_FALLBACK, c->cap_level, c->status,
                                              MRDEM_STAT_FP64, *out);
     }
   }

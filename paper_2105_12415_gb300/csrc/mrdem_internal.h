@@ -34,6 +34,8 @@ struct HierHost {
 // Device view of a hierarchy, passed by value to kernels.
 struct HierDev {
   const float4* node_geo;  // [n_nodes*3]: (v0.xyz, delta) (v1.xyz, 0) (v2.xyz, 0)
+  const float4* node_sph;  // [n_nodes]: body-frame sphere (centre, radius + delta) holding
+                           // the node's surrogate eps-free environment
   const int2* node_child;  // [n_nodes]
   const float* tri;        // 9 planes: coordinate k of slot s at tri[k*stride + s]
   const int32_t* vid;      // 3 planes: global vertex index of corner k of slot s
@@ -78,6 +80,7 @@ enum Counter : int {
   CNT_TILES = CNT_FETCH + kMaxLevels + 2,
   CNT_CANDS,
   CNT_FALLBACK,                           // FP32 form: candidates left for the FP64 test
+  CNT_SWEEP,                              // entries in the sweep list
   CNT_STATS,                              // [MRDEM_STAT_COUNT] statistics
   CNT_TOTAL = CNT_STATS + MRDEM_STAT_COUNT
 };
@@ -89,6 +92,7 @@ enum Status : int {
   ST_REQ_TILES,
   ST_REQ_CANDS,
   ST_REQ_CONTACTS,
+  ST_REQ_SWEEP,
   ST_TOTAL = 8
 };
 
@@ -102,7 +106,7 @@ struct mrdem_hier {
 };
 
 namespace mrdem {
-enum KernelId : int { K_SETUP = 0, K_LEVEL, K_TILE, K_EXACT, K_EXACT64, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_COUNT };
+enum KernelId : int { K_SETUP = 0, K_LEVEL, K_SWEEP_NODES, K_TILE, K_SWEEP_FINE, K_EXACT, K_EXACT64, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_COUNT };
 struct ProfRec {
   int kernel;
   cudaEvent_t a, b;
@@ -116,7 +120,8 @@ struct mrdem_ctx {
   int4* level_list[2] = {nullptr, nullptr};
   mrdem::TileItem* tiles = nullptr;
   int3* cands = nullptr;
-  int64_t cap_level = 0, cap_tiles = 0, cap_cands = 0;
+  int4* sweep = nullptr;  // pairs waiting for the penalty sweep (node pairs, then fine pairs)
+  int64_t cap_level = 0, cap_tiles = 0, cap_cands = 0, cap_sweep = 0;
   mrdem::PairXf* xf = nullptr;
   mrdem::PairXf64* xf64 = nullptr;
   int64_t cap_pairs = 0;

@@ -125,7 +125,7 @@ def test_capacity_overflow_is_reported_and_recovered(orc):
     import ctypes as C
     import torch
     import paper_2105_12415_gb300 as m
-    ctx = m.Context(0, cap_level=8, cap_tiles=8, cap_candidates=8)
+    ctx = m.Context(0, cap_level=8, cap_tiles=8, cap_candidates=8, cap_sweep=8)
     s = scene_c1()
     hier = m.Hierarchy.from_scene(ctx, s)
     dev = torch.device("cuda:0")
@@ -136,9 +136,9 @@ def test_capacity_overflow_is_reported_and_recovered(orc):
     st = lib.mrdem_detect(ctx.handle, hier.handle, 1, t["pairs"].data_ptr(), t["eps"].data_ptr(),
                           t["poses"].data_ptr(), 1, C.byref(cs), None, None)
     assert st == 0
-    req = np.zeros(4, np.int64)
+    req = np.zeros(5, np.int64)
     assert lib.mrdem_check(ctx.handle, None, req.ctypes.data) == m._lib.MRDEM_ERR_CAPACITY
-    assert req[0] > 8 or req[1] > 8 or req[2] > 8
+    assert req[0] > 8 or req[1] > 8 or req[2] > 8 or req[4] > 8
     got, _ = m.detect(ctx, hier, t["pairs"], t["eps"], t["poses"], "fp64", contacts=contacts)
     compare_contacts(got.to_numpy(), orc.detect(s), s, "fp64")
 
