@@ -235,13 +235,13 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
   int64_t stride = (h.n_tri_pad + 31) / 32 * 32;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   size_t sz_geo = al(sizeof(float4) * 3 * h.n_nodes), sz_child = al(sizeof(int2) * h.n_nodes);
-  size_t sz_sph = al(sizeof(float4) * h.n_nodes);
+  size_t sz_sph = al(sizeof(float4) * h.n_nodes), sz_tsph = al(sizeof(float4) * stride);
   size_t sz_tri = al(sizeof(float) * 9 * stride), sz_vid = al(sizeof(int32_t) * 3 * stride);
   size_t sz_slot = al(sizeof(int32_t) * stride), sz_ts = al(sizeof(int32_t) * h.n_tri);
   size_t sz_off = al(sizeof(int64_t) * (h.n_particles + 1));
   size_t sz_root = al(sizeof(int32_t) * h.n_particles), sz_br = al(sizeof(float) * h.n_particles);
   size_t total = sz_geo + sz_child + sz_tri + sz_vid + sz_slot + sz_ts + sz_off + sz_root + sz_br +
-                 sz_sph;
+                 sz_sph + sz_tsph;
   char* base = nullptr;
   if (cudaMalloc(&base, total) != cudaSuccess) {
     cudaGetLastError();
@@ -253,6 +253,7 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     size_t o_geo = 0, o_child = o_geo + sz_geo, o_tri = o_child + sz_child, o_vid = o_tri + sz_tri;
     size_t o_slot = o_vid + sz_vid, o_ts = o_slot + sz_slot, o_off = o_ts + sz_ts;
     size_t o_root = o_off + sz_off, o_br = o_root + sz_root, o_sph = o_br + sz_br;
+    size_t o_tsph = o_sph + sz_sph;
     float4* geo = (float4*)(p + o_geo);
     for (int64_t n = 0; n < h.n_nodes; ++n) {
       const float* t = &h.node_tri[9 * n];
@@ -279,10 +280,24 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     std::memcpy(p + o_child, h.node_child.data(), sizeof(int32_t) * 2 * h.n_nodes);
     float* tri = (float*)(p + o_tri);
     int32_t* vid = (int32_t*)(p + o_vid);
+    float4* tsph = (float4*)(p + o_tsph);
     for (int64_t s = 0; s < h.n_tri_pad; ++s) {
       for (int k = 0; k < 9; ++k) tri[k * stride + s] = h.slot_xyz[9 * s + k];
       for (int k = 0; k < 3; ++k) vid[k * stride + s] = h.slot_vid[3 * s + k];
+      // bounding sphere of the triangle: centroid, largest vertex distance,
+      // in double and rounded up (padding slots get an empty sphere)
+      const float* t = &h.slot_xyz[9 * s];
+      double c[3], r2 = 0;
+      for (int k = 0; k < 3; ++k) c[k] = ((double)t[k] + (double)t[3 + k] + (double)t[6 + k]) / 3.0;
+      for (int v = 0; v < 3; ++v) {
+        double d2 = 0;
+        for (int k = 0; k < 3; ++k) d2 += ((double)t[3 * v + k] - c[k]) * ((double)t[3 * v + k] - c[k]);
+        r2 = std::max(r2, d2);
+      }
+      tsph[s] = make_float4((float)c[0], (float)c[1], (float)c[2],
+                            (float)(std::sqrt(r2) * (1.0 + 1e-6) + 1e-30));
     }
+    for (int64_t s = h.n_tri_pad; s < stride; ++s) tsph[s] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t s = h.n_tri_pad; s < stride; ++s)
       for (int k = 0; k < 3; ++k) vid[k * stride + s] = -1;
     int32_t* st = (int32_t*)(p + o_slot);
@@ -307,6 +322,7 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     d.root = (const int32_t*)(base + o_root);
     d.bound_r = (const float*)(base + o_br);
     d.node_sph = (const float4*)(base + o_sph);
+    d.tri_sph = (const float4*)(base + o_tsph);
     d.stride = stride;
     d.n_tri = h.n_tri;
     d.n_particles = h.n_particles;

@@ -71,6 +71,38 @@ __device__ __forceinline__ void warp_append(bool pred, const Item& item, Item* l
   }
 }
 
+// Per-warp output queue in shared memory: items are collected with a ballot
+// per round and written out in batches, one global atomic per batch instead
+// of one per round.  All calls must be made by all 32 lanes.
+template <typename Item, int CAP>
+struct WarpQueue {
+  Item* buf;  // shared memory, CAP items
+  int n = 0;  // warp-uniform fill level
+  __device__ __forceinline__ void flush(Item* list, unsigned long long* counter, int64_t cap,
+                                        unsigned long long* req) {
+    __syncwarp();
+    if (n == 0) return;
+    unsigned long long base = 0;
+    if (lane_id() == 0) base = atomicAdd(counter, (unsigned long long)n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int k = lane_id(); k < n; k += 32) {
+      unsigned long long idx = base + k;
+      if ((int64_t)idx < cap) list[idx] = buf[k];
+      else atomicMax(req, idx + 1);
+    }
+    n = 0;
+    __syncwarp();
+  }
+  __device__ __forceinline__ void push(bool pred, const Item& item, Item* list,
+                                       unsigned long long* counter, int64_t cap,
+                                       unsigned long long* req) {
+    unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (pred) buf[n + __popc(m & ((1u << lane_id()) - 1u))] = item;
+    n += __popc(m);
+    if (n > CAP - 32) flush(list, counter, cap, req);
+  }
+};
+
 __device__ __forceinline__ F3 xf_point(const PairXf& X, F3 v) {
   return {fmaf(X.R[0], v.x, fmaf(X.R[1], v.y, fmaf(X.R[2], v.z, X.t[0]))),
           fmaf(X.R[3], v.x, fmaf(X.R[4], v.y, fmaf(X.R[5], v.z, X.t[1]))),
@@ -239,11 +271,14 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
                                                        unsigned long long* status,
                                                        int64_t cap_level, int64_t cap_sweep) {
   __shared__ float4 ssph[WARPS][16];
+  __shared__ int4 sq[WARPS][128];
   const int w = threadIdx.x >> 5, lane = lane_id();
   int64_t n_in = (int64_t)cnt[CNT_LEVEL + level];
   if (n_in > cap_level) n_in = cap_level;
   const int slot_tests = MRDEM_STAT_TESTS + (level + 1 < MRDEM_STAT_LEVELS ? level + 1 : MRDEM_STAT_LEVELS - 1);
   WarpCount tests;
+  WarpQueue<int4, 128> outq;
+  outq.buf = sq[w];
   const int64_t step = (int64_t)gridDim.x * WARPS;
   int64_t item = (int64_t)blockIdx.x * WARPS + w;
   int4 nxt = item < n_in ? in[item] : make_int4(0, 0, 0, 0);
@@ -271,11 +306,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
       float lim = p.w + q.w;  // q.w carries 2 eps + margin
       bool keep = act && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
       tests.add(act);
-      warp_append(keep, make_int4(it.x, it.y + i, it.z + j, 0), sweep, cnt + CNT_SWEEP, cap_sweep,
-                  status + ST_REQ_SWEEP);
+      outq.push(keep, make_int4(it.x, it.y + i, it.z + j, 0), sweep, cnt + CNT_SWEEP, cap_sweep,
+                status + ST_REQ_SWEEP);
     }
     __syncwarp();
   }
+  outq.flush(sweep, cnt + CNT_SWEEP, cap_sweep, status + ST_REQ_SWEEP);
   tests.flush(cnt + CNT_STATS + slot_tests);
 }
 
@@ -290,6 +326,13 @@ __global__ void __launch_bounds__(256) k_sweep_nodes(HierDev H, const PairXf* __
   if (n > cap_sweep) n = cap_sweep;
   const int slot_surv = MRDEM_STAT_SURVIVORS + (level + 1 < MRDEM_STAT_LEVELS ? level + 1 : MRDEM_STAT_LEVELS - 1);
   WarpCount nsweep, surv;
+  __shared__ TileItem stq[8][64];
+  __shared__ int4 slq[8][64];
+  const int w = threadIdx.x >> 5;
+  WarpQueue<TileItem, 64> tq;
+  WarpQueue<int4, 64> lq;
+  tq.buf = stq[w];
+  lq.buf = slq[w];
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     int64_t k = base + threadIdx.x;
@@ -320,11 +363,13 @@ __global__ void __launch_bounds__(256) k_sweep_nodes(HierDev H, const PairXf* __
     bool leaves = ia.y < 0 && ib.y < 0;
     nsweep.add(act);
     surv.add(s);
-    warp_append(s && leaves, make_tile(e.x, e.y, e.z, ia, ib), tiles, cnt + CNT_TILES, cap_tiles,
-                status + ST_REQ_TILES);
-    warp_append(s && !leaves, make_level(e.x, e.y, e.z, ia, ib), out, cnt + CNT_LEVEL + level + 1,
-                cap_level, status + ST_REQ_LEVEL);
+    tq.push(s && leaves, make_tile(e.x, e.y, e.z, ia, ib), tiles, cnt + CNT_TILES, cap_tiles,
+            status + ST_REQ_TILES);
+    lq.push(s && !leaves, make_level(e.x, e.y, e.z, ia, ib), out, cnt + CNT_LEVEL + level + 1,
+            cap_level, status + ST_REQ_LEVEL);
   }
+  tq.flush(tiles, cnt + CNT_TILES, cap_tiles, status + ST_REQ_TILES);
+  lq.flush(out, cnt + CNT_LEVEL + level + 1, cap_level, status + ST_REQ_LEVEL);
   nsweep.flush(cnt + CNT_STATS + MRDEM_STAT_LEVEL_SWEEPS);
   surv.flush(cnt + CNT_STATS + slot_surv);
 }
@@ -378,8 +423,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_tile(HierDev H, const PairXf* __
                                                      unsigned long long* status, int64_t cap_tiles,
                                                      int64_t cap_fine) {
   __shared__ TileSmem smem[WARPS];
+  __shared__ int4 sq[WARPS][128];
   const int w = threadIdx.x >> 5, lane = lane_id();
   TileSmem& S = smem[w];
+  WarpQueue<int4, 128> q;
+  q.buf = sq[w];
   int64_t n_tiles = (int64_t)cnt[CNT_TILES];
   if (n_tiles > cap_tiles) n_tiles = cap_tiles;
   WarpCount spheres;
@@ -400,9 +448,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_tile(HierDev H, const PairXf* __
     if (lane < na) {
       float4 gb0 = __ldg(H.node_geo + 3 * it.node_b), gb1 = __ldg(H.node_geo + 3 * it.node_b + 1);
       float4 gb2 = __ldg(H.node_geo + 3 * it.node_b + 2);
-      F3 v0 = load_vertex(H, it.slot_a + lane, 0), v1 = load_vertex(H, it.slot_a + lane, 1);
-      F3 v2 = load_vertex(H, it.slot_a + lane, 2);
-      float4 sp = tri_sphere(v0, v1, v2);
+      float4 sp = __ldg(H.tri_sph + it.slot_a + lane);
       S.sa[lane] = sp;
       keep_a = sphere_near_triangle(sp, xf_point(X, {gb0.x, gb0.y, gb0.z}),
                                     xf_point(X, {gb1.x, gb1.y, gb1.z}),
@@ -411,10 +457,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_tile(HierDev H, const PairXf* __
     if (lane < nb) {
       float4 ga0 = __ldg(H.node_geo + 3 * it.node_a), ga1 = __ldg(H.node_geo + 3 * it.node_a + 1);
       float4 ga2 = __ldg(H.node_geo + 3 * it.node_a + 2);
-      F3 v0 = xf_point(X, load_vertex(H, it.slot_b + lane, 0));
-      F3 v1 = xf_point(X, load_vertex(H, it.slot_b + lane, 1));
-      F3 v2 = xf_point(X, load_vertex(H, it.slot_b + lane, 2));
-      float4 sp = tri_sphere(v0, v1, v2);
+      float4 sb = __ldg(H.tri_sph + it.slot_b + lane);
+      F3 c = xf_point(X, {sb.x, sb.y, sb.z});
+      float4 sp = make_float4(c.x, c.y, c.z, sb.w);
       S.sb[lane] = sp;
       keep_b = sphere_near_triangle(sp, {ga0.x, ga0.y, ga0.z}, {ga1.x, ga1.y, ga1.z},
                                     {ga2.x, ga2.y, ga2.z}, ga0.w + thr);
@@ -434,16 +479,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_tile(HierDev H, const PairXf* __
       int jj = f - ii * kb;
       if (!act) { ii = 0; jj = 0; }
       int i = S.ka[ii], j = S.kb[jj];
-      float4 p = S.sa[i], q = S.sb[j];
-      float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-      float lim = (p.w + q.w) + thr;
+      float4 p = S.sa[i], r = S.sb[j];
+      float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
+      float lim = (p.w + r.w) + thr;
       bool keep = act && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
-      warp_append(keep, make_int4(it.pair, it.slot_a + i, it.slot_b + j, 0), fine, cnt + CNT_SWEEP,
-                  cap_fine, status + ST_REQ_SWEEP);
+      q.push(keep, make_int4(it.pair, it.slot_a + i, it.slot_b + j, 0), fine, cnt + CNT_SWEEP,
+             cap_fine, status + ST_REQ_SWEEP);
     }
     spheres.v += lane == 0 ? (unsigned)total : 0u;
     __syncwarp();
   }
+  q.flush(fine, cnt + CNT_SWEEP, cap_fine, status + ST_REQ_SWEEP);
   if (lane == 0) {
     if (ntile) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_TILES, (unsigned long long)ntile);
     if (nfvs) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_FINE_SURROGATE, (unsigned long long)nfvs);

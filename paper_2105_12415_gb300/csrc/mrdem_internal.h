@@ -38,6 +38,7 @@ struct HierDev {
                            // the node's surrogate eps-free environment
   const int2* node_child;  // [n_nodes]
   const float* tri;        // 9 planes: coordinate k of slot s at tri[k*stride + s]
+  const float4* tri_sph;   // [stride]: body-frame bounding sphere of each fine triangle
   const int32_t* vid;      // 3 planes: global vertex index of corner k of slot s
   const int32_t* slot_tri; // [stride] local input triangle index (-1 pad)
   const int32_t* tri_slot; // [n_tri] global input triangle -> slot
