@@ -70,6 +70,10 @@ typedef struct CUstream_st* mrdem_stream; /* same type as cudaStream_t */
 #define MRDEM_STAT_SPHERE_TESTS 22 /* fine pairs given the bounding-sphere test */
 #define MRDEM_STAT_FINE_SURROGATE 23 /* fine triangles tested against the other leaf's surrogate */
 #define MRDEM_STAT_LEVEL_SWEEPS 24 /* surrogate pairs given the penalty sweep (all levels) */
+#define MRDEM_STAT_NOALLOC_OVERFLOW 25 /* mrdem_detect_noalloc only: largest size a fixed list or
+                                          the contact buffer needed beyond its limit, 0 if none */
+#define MRDEM_STAT_NOALLOC_INVALID 26  /* mrdem_detect_noalloc only: non-zero if a pose, eps or
+                                          particle index was invalid */
 #define MRDEM_STAT_COUNT 32
 
 typedef struct mrdem_params {
@@ -268,6 +272,40 @@ int mrdem_triangle_distance(mrdem_ctx* ctx, int64_t n, const double* P, const do
                             const double* eps, int32_t precision, double* dist, double* point_a,
                             double* point_b, int32_t* feature, float* sweep_x, float* sweep_gap,
                             int32_t* sweep_conv, mrdem_stream stream);
+
+/* Detection for callers that may not allocate device memory.  Some callers
+ * own every byte of device memory themselves: a simulation host that hands
+ * this library a fixed memory budget at start-up, or a real-time loop that
+ * must not call cudaMalloc/cudaFree after initialisation because those calls
+ * synchronise the device and can stall the loop.  They cannot use
+ * mrdem_detect, whose context allocates its work lists (and grows them on
+ * demand).  This call does the same work as mrdem_detect with the same
+ * kernels, but every work list lives in one fixed array in device memory that
+ * is part of the library image (about 7.2 MB; every GPU that loads the library
+ * holds it until the process exits).  It allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.  The method has no counterpart of
+ * this call in the paper; it is a deployment variant of mrdem_detect.
+ *
+ * Arguments: as mrdem_detect, without a context: hier must have been
+ * uploaded (its context supplies the device and the sweep constants); stats
+ * is required (device int64 [MRDEM_STAT_COUNT]).
+ * Limits: n_pairs <= 1024 (larger: MRDEM_ERR_INVALID, nothing enqueued); per
+ * call at most 65536 node-pair items per level, 65536 leaf-pair tiles, 131072
+ * pairs waiting for a sweep and 65536 fine candidates.  Work beyond a limit
+ * is dropped: after the stream completes, stats[MRDEM_STAT_NOALLOC_OVERFLOW]
+ * holds the size that would have been needed (0 when nothing overflowed; the
+ * contact buffer's overflow is reported there too) and the contact set is
+ * then incomplete; stats[MRDEM_STAT_NOALLOC_INVALID] is non-zero when an
+ * input was invalid.  These flags are not latched in the context.
+ * The first call on a device looks up the device address of the fixed array;
+ * make that first call before any stream capture.  Every call on a device
+ * shares the one array and clears its counters on entry, so calls that
+ * overlap on the GPU (concurrent streams, or host threads on one device)
+ * race and corrupt each other's results: serialise them.  Returns
+ * MRDEM_ERR_INVALID for bad arguments, MRDEM_ERR_CUDA if a launch failed. */
+int mrdem_detect_noalloc(const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
+                         const double* pair_eps, const double* poses, int32_t precision,
+                         const mrdem_contacts* out, int64_t* stats, mrdem_stream stream);
 
 /* Kernel timing for benchmarks (not part of the method).  While enabled, the
  * context records a CUDA event pair on the launch stream around every kernel

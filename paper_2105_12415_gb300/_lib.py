@@ -33,6 +33,8 @@ MRDEM_STAT_FP64 = 21
 MRDEM_STAT_SPHERE_TESTS = 22
 MRDEM_STAT_FINE_SURROGATE = 23
 MRDEM_STAT_LEVEL_SWEEPS = 24
+MRDEM_STAT_NOALLOC_OVERFLOW = 25
+MRDEM_STAT_NOALLOC_INVALID = 26
 MRDEM_STAT_COUNT = 32
 
 
@@ -92,6 +94,8 @@ SIGNATURES = {
                                           _P]),
     "mrdem_triangle_distance": (C.c_int, [_P, _I64, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P,
                                           _P]),
+    "mrdem_detect_noalloc": (C.c_int, [_P, _I64, _P, _P, _P, _I, C.POINTER(mrdem_contacts), _P,
+                                       _P]),
     "mrdem_profile": (C.c_int, [_P, _I]),
     "mrdem_profile_read": (C.c_int, [_P, _I, C.POINTER(C.c_char_p), _P, _P, C.POINTER(_I)]),
 }

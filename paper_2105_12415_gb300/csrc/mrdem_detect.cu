@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "mrdem_geometry.cuh"
@@ -952,3 +953,151 @@ int launch_triangle_distance(mrdem_ctx* c, int64_t n, const double* P, const dou
 }
 
 }  // namespace mrdem
+
+// ---------------------------------------------------------------------------
+// Detection without allocation.  All work lists of one call live in a fixed
+// file-scope device array, so the call needs no device memory beyond its
+// inputs and outputs.  Limits (each fixed list; the call reports an overflow
+// in its statistics and the result is then incomplete):
+namespace {
+constexpr int64_t kNaPairs = 1024;       // particle pairs per call
+constexpr int64_t kNaLevel = 1 << 16;    // node-pair items per level
+constexpr int64_t kNaTiles = 1 << 16;    // leaf-pair tiles
+constexpr int64_t kNaSweep = 1 << 17;    // pairs waiting for a sweep
+constexpr int64_t kNaCands = 1 << 16;    // fine candidates
+constexpr size_t na_align(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kNaOffCnt = 0;
+constexpr size_t kNaOffSt = na_align(kNaOffCnt + sizeof(unsigned long long) * mrdem::CNT_TOTAL);
+constexpr size_t kNaOffXf = na_align(kNaOffSt + sizeof(unsigned long long) * mrdem::ST_TOTAL);
+constexpr size_t kNaOffXf64 = na_align(kNaOffXf + sizeof(mrdem::PairXf) * kNaPairs);
+constexpr size_t kNaOffL0 = na_align(kNaOffXf64 + sizeof(mrdem::PairXf64) * kNaPairs);
+constexpr size_t kNaOffL1 = na_align(kNaOffL0 + sizeof(int4) * kNaLevel);
+constexpr size_t kNaOffTiles = na_align(kNaOffL1 + sizeof(int4) * kNaLevel);
+constexpr size_t kNaOffSweep = na_align(kNaOffTiles + sizeof(mrdem::TileItem) * kNaTiles);
+constexpr size_t kNaOffCands = na_align(kNaOffSweep + sizeof(int4) * kNaSweep);
+constexpr size_t kNaBytes = na_align(kNaOffCands + sizeof(int3) * kNaCands);  // about 7.2 MB
+}  // namespace
+
+// The scratch itself: every GPU that loads this library holds it until exit.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+namespace mrdem {
+namespace {
+
+// Device address of the scratch array, looked up once per device (host code
+// cannot use the symbol itself as a device pointer).
+std::mutex g_na_mutex;
+void* g_na_addr[256] = {nullptr};
+
+int noalloc_scratch(int device, unsigned char** out) {
+  if (device < 0 || device >= 256) return MRDEM_ERR_INVALID;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_addr[device]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return MRDEM_ERR_CUDA;
+    }
+    g_na_addr[device] = p;
+  }
+  *out = static_cast<unsigned char*>(g_na_addr[device]);
+  return MRDEM_OK;
+}
+
+// Copies the overflow and invalid-input flags of the call into its statistics.
+__global__ void k_noalloc_status(const unsigned long long* status, int64_t* stats) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    unsigned long long req = 0;
+    for (int k = ST_REQ_LEVEL; k <= ST_REQ_SWEEP; ++k) req = req > status[k] ? req : status[k];
+    stats[MRDEM_STAT_NOALLOC_OVERFLOW] = (int64_t)req;
+    stats[MRDEM_STAT_NOALLOC_INVALID] = (int64_t)status[ST_NONFINITE];
+  }
+}
+
+}  // namespace
+}  // namespace mrdem
+
+extern "C" int mrdem_detect_noalloc(const mrdem_hier* hier, int64_t n_pairs,
+                                    const int32_t* pair_ab, const double* pair_eps,
+                                    const double* poses, int32_t precision,
+                                    const mrdem_contacts* out, int64_t* stats,
+                                    mrdem_stream stream) {
+  using namespace mrdem;
+  if (!hier || !hier->d_mem || !hier->ctx || !out || !out->count || !stats) return MRDEM_ERR_INVALID;
+  if (n_pairs < 0 || n_pairs > kNaPairs) return MRDEM_ERR_INVALID;
+  if (n_pairs > 0 && (!pair_ab || !pair_eps || !poses)) return MRDEM_ERR_INVALID;
+  if (out->capacity < 0 ||
+      (out->capacity > 0 && (!out->pair || !out->tri_a || !out->tri_b || !out->dist ||
+                             !out->point_a || !out->point_b)))
+    return MRDEM_ERR_INVALID;
+  if (precision != MRDEM_PREC_FP32 && precision != MRDEM_PREC_FP64) return MRDEM_ERR_INVALID;
+  mrdem_ctx* c = hier->ctx;
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  if (cudaSetDevice(c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return MRDEM_ERR_CUDA;
+  }
+  unsigned char* base = nullptr;
+  int st = noalloc_scratch(c->device, &base);
+  if (st != MRDEM_OK) {
+    if (prev >= 0) cudaSetDevice(prev);
+    return st;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + kNaOffCnt);
+  unsigned long long* status = reinterpret_cast<unsigned long long*>(base + kNaOffSt);
+  PairXf* xf = reinterpret_cast<PairXf*>(base + kNaOffXf);
+  PairXf64* xf64 = reinterpret_cast<PairXf64*>(base + kNaOffXf64);
+  int4* lists[2] = {reinterpret_cast<int4*>(base + kNaOffL0), reinterpret_cast<int4*>(base + kNaOffL1)};
+  TileItem* tiles = reinterpret_cast<TileItem*>(base + kNaOffTiles);
+  int4* sweep = reinterpret_cast<int4*>(base + kNaOffSweep);
+  int3* cands = reinterpret_cast<int3*>(base + kNaOffCands);
+  const HierDev& H = hier->dev;
+  const mrdem_params& prm = c->params;
+  SweepConst sc = sweep_const(prm);
+  // the array keeps the previous call's contents: clear what starts at zero
+  cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * CNT_TOTAL, s);
+  cudaMemsetAsync(status, 0, sizeof(unsigned long long) * ST_TOTAL, s);
+  cudaMemsetAsync(out->count, 0, sizeof(int64_t), s);
+  if (n_pairs > 0) {
+    int threads = 256;
+    int blocks = (int)std::min<int64_t>((n_pairs + threads - 1) / threads, (int64_t)c->n_sms * 8);
+    k_setup<<<blocks, threads, 0, s>>>(H, (int)n_pairs, pair_ab, pair_eps, poses, xf, xf64, sc, 1,
+                                       lists[0], tiles, cnt, status, kNaLevel, kNaTiles);
+    int steps = std::min(hier->h.max_depth - 1, kMaxLevels - 1);
+    constexpr int W = 8;
+    for (int l = 0; l < steps; ++l) {
+      int eb = one_wave(c, K_LEVEL, k_expand<W>, W * 32, 0);
+      cudaMemsetAsync(cnt + CNT_SWEEP, 0, sizeof(unsigned long long), s);
+      k_expand<W><<<eb, W * 32, 0, s>>>(H, xf, lists[l & 1], l, sweep, cnt, status, kNaLevel,
+                                        kNaSweep);
+      int nb = one_wave(c, K_SWEEP_NODES, k_sweep_nodes, 256, 0);
+      k_sweep_nodes<<<nb, 256, 0, s>>>(H, xf, sc, sweep, l, lists[(l + 1) & 1], tiles, cnt,
+                                       status, kNaSweep, kNaLevel, kNaTiles);
+    }
+    int tb = one_wave(c, K_TILE, k_tile<W>, W * 32, 0);
+    cudaMemsetAsync(cnt + CNT_SWEEP, 0, sizeof(unsigned long long), s);
+    k_tile<W><<<tb, W * 32, 0, s>>>(H, xf, tiles, sweep, cnt, status, kNaTiles, kNaSweep);
+    int fb = one_wave(c, K_SWEEP_FINE, k_sweep_fine<true>, 256, 0);
+    k_sweep_fine<true><<<fb, 256, 0, s>>>(H, xf, sc, prm.conv_c, sweep, cands, cnt, status,
+                                          kNaSweep, kNaCands, pair_eps);
+    int et = prm.exact_threads;
+    if (precision == MRDEM_PREC_FP64) {
+      k_exact64<<<c->n_sms * 8, et, 0, s>>>(H, xf64, cands, cnt, CNT_CANDS, kNaCands, status,
+                                             MRDEM_STAT_FP64, *out);
+    } else {
+      // the first level list is free once the tiles are done: the fallback list
+      k_exact32<<<c->n_sms * 8, et, 0, s>>>(H, xf64, cands, cnt, status, kNaCands,
+                                             reinterpret_cast<int3*>(lists[0]), kNaLevel, *out);
+      k_exact64<<<c->n_sms * 4, et, 0, s>>>(H, xf64, reinterpret_cast<const int3*>(lists[0]), cnt,
+                                             CNT_FALLBACK, kNaLevel, status, MRDEM_STAT_FP64, *out);
+    }
+  }
+  cudaMemcpyAsync(stats, cnt + CNT_STATS, sizeof(int64_t) * MRDEM_STAT_COUNT,
+                  cudaMemcpyDeviceToDevice, s);
+  k_noalloc_status<<<1, 32, 0, s>>>(status, stats);
+  cudaError_t e = cudaGetLastError();
+  if (prev >= 0) cudaSetDevice(prev);
+  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
