@@ -596,8 +596,12 @@ __device__ __forceinline__ void write_contact(const HierDev& H, const mrdem_cont
   }
 }
 
-// FP32 form, first pass over the candidates.
-__global__ void __launch_bounds__(128) k_exact32(HierDev H, const PairXf64* __restrict__ xf64,
+// FP32 form, first pass over the candidates.  The float stage runs on float
+// coordinates (B moved by the float transform; its error is within the
+// pair's margin), so pairs it rejects never touch double arithmetic; the
+// others are finished in double from the double transform.
+__global__ void __launch_bounds__(128) k_exact32(HierDev H, const PairXf* __restrict__ xf,
+                                                 const PairXf64* __restrict__ xf64,
                                                  const int3* __restrict__ cands,
                                                  unsigned long long* cnt,
                                                  unsigned long long* status, int64_t cap_cands,
@@ -613,16 +617,28 @@ __global__ void __launch_bounds__(128) k_exact32(HierDev H, const PairXf64* __re
     int3 c = make_int3(0, 0, 0);
     double d = 0;
     D3 pa = {0, 0, 0}, pb = {0, 0, 0};
-    const PairXf64* X = nullptr;
+    unsigned mask = 0;
     if (k < n) {
       c = cands[k];
-      X = xf64 + c.x;
+      PairXf X;
+      load_pairxf(xf, c.x, X);
+      F3 a0 = load_vertex(H, c.y, 0), a1 = load_vertex(H, c.y, 1), a2 = load_vertex(H, c.y, 2);
+      F3 Pf[3] = {{0.f, 0.f, 0.f}, a1 - a0, a2 - a0};
+      F3 Qf[3] = {xf_point(X, load_vertex(H, c.z, 0)) - a0, xf_point(X, load_vertex(H, c.z, 1)) - a0,
+                  xf_point(X, load_vertex(H, c.z, 2)) - a0};
+      res = cand_float_stage(Pf, Qf, (double)X.tau, X.margin, &mask);
+    }
+    // finish the accepted pairs in double (only these lanes touch FP64)
+    if (res == 1) {
+      const PairXf64& X64 = xf64[c.x];
       CandGeom g;
-      cand_geom(H, *X, c, g);
-      res = cand_fp32(g, d, pa, pb);
-      if (res == 1) {
-        pa = xf_point64(X->RA, X->tA, pa + g.o);
-        pb = xf_point64(X->RA, X->tA, pb + g.o);
+      cand_geom(H, X64, c, g);
+      d = cand_double_stage(g, mask, pa, pb, nullptr, nullptr);
+      if (d <= g.tau) {
+        pa = xf_point64(X64.RA, X64.tA, pa + g.o);
+        pb = xf_point64(X64.RA, X64.tA, pb + g.o);
+      } else {
+        res = 0;
       }
     }
     ncon.add(res == 1);
@@ -885,7 +901,7 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
       {
         ProfScope ps(c, K_EXACT, s);
         // the level lists are free once the tiles are done: reuse one as the fallback list
-        k_exact32<<<c->n_sms * 8, et, 0, s>>>(H, c->xf64, c->cands, c->counters, c->status,
+        k_exact32<<<c->n_sms * 8, et, 0, s>>>(H, c->xf, c->xf64, c->cands, c->counters, c->status,
                                                c->cap_cands, reinterpret_cast<int3*>(c->level_list[0]),
                                                c->cap_level, *out);
       }
@@ -898,6 +914,20 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
   if (stats)
     cudaMemcpyAsync(stats, c->counters + CNT_STATS, sizeof(int64_t) * MRDEM_STAT_COUNT,
                     cudaMemcpyDeviceToDevice, s);
+  return finish(s);
+}
+
+// Per-pair transforms only (no root test), e.g. for the adjoint.
+int setup_pairs(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
+                const double* eps, const double* poses, cudaStream_t s) {
+  int st = ensure_pairs(c, n_pairs);
+  if (st) return st;
+  if (n_pairs == 0) return MRDEM_OK;
+  SweepConst sc = sweep_const(c->params);
+  int threads = 256;
+  int blocks = (int)std::min<int64_t>((n_pairs + threads - 1) / threads, (int64_t)c->n_sms * 8);
+  k_setup<<<blocks, threads, 0, s>>>(hier->dev, (int)n_pairs, ab, eps, poses, c->xf, c->xf64, sc, 0,
+                                     nullptr, nullptr, c->counters, c->status, 0, 0);
   return finish(s);
 }
 
@@ -1088,7 +1118,7 @@ extern "C" int mrdem_detect_noalloc(const mrdem_hier* hier, int64_t n_pairs,
                                              MRDEM_STAT_FP64, *out);
     } else {
       // the first level list is free once the tiles are done: the fallback list
-      k_exact32<<<c->n_sms * 8, et, 0, s>>>(H, xf64, cands, cnt, status, kNaCands,
+      k_exact32<<<c->n_sms * 8, et, 0, s>>>(H, xf, xf64, cands, cnt, status, kNaCands,
                                              reinterpret_cast<int3*>(lists[0]), kNaLevel, *out);
       k_exact64<<<c->n_sms * 4, et, 0, s>>>(H, xf64, reinterpret_cast<const int3*>(lists[0]), cnt,
                                              CNT_FALLBACK, kNaLevel, status, MRDEM_STAT_FP64, *out);

@@ -23,6 +23,47 @@ namespace mrdem {
 
 using D3 = V3<double>;
 
+// helpers (the same layout as the detection kernels use)
+__device__ __forceinline__ V3<float> load_vertex(const HierDev& H, int slot, int c) {
+  return {__ldg(H.tri + (3 * c + 0) * H.stride + slot), __ldg(H.tri + (3 * c + 1) * H.stride + slot),
+          __ldg(H.tri + (3 * c + 2) * H.stride + slot)};
+}
+__device__ __forceinline__ V3<float> xf_point(const PairXf& X, V3<float> v) {
+  return {fmaf(X.R[0], v.x, fmaf(X.R[1], v.y, fmaf(X.R[2], v.z, X.t[0]))),
+          fmaf(X.R[3], v.x, fmaf(X.R[4], v.y, fmaf(X.R[5], v.z, X.t[1]))),
+          fmaf(X.R[6], v.x, fmaf(X.R[7], v.y, fmaf(X.R[8], v.z, X.t[2])))};
+}
+__device__ __forceinline__ void load_pairxf(const PairXf* xf, int p, PairXf& X) {
+  const float4* q = reinterpret_cast<const float4*>(xf + p);
+  float4 a = __ldg(q), b = __ldg(q + 1), cc = __ldg(q + 2), d = __ldg(q + 3);
+  X.R[0] = a.x; X.R[1] = a.y; X.R[2] = a.z; X.R[3] = a.w;
+  X.R[4] = b.x; X.R[5] = b.y; X.R[6] = b.z; X.R[7] = b.w;
+  X.R[8] = cc.x; X.t[0] = cc.y; X.t[1] = cc.z; X.t[2] = cc.w;
+  X.tau = d.x; X.margin = d.y;
+  X.A = __float_as_int(d.z); X.B = __float_as_int(d.w);
+}
+// Both triangles of a candidate in A's frame, relative to A's first vertex
+// (double, from the double transform).
+__device__ __forceinline__ void cand_geom64(const HierDev& H, const PairXf64& X, int sa, int sb,
+                                            CandGeom& g) {
+  D3 Pb[3], Qb[3];
+  for (int q = 0; q < 3; ++q) {
+    Pb[q] = {(double)H.tri[(3 * q) * H.stride + sa], (double)H.tri[(3 * q + 1) * H.stride + sa],
+             (double)H.tri[(3 * q + 2) * H.stride + sa]};
+    Qb[q] = {(double)H.tri[(3 * q) * H.stride + sb], (double)H.tri[(3 * q + 1) * H.stride + sb],
+             (double)H.tri[(3 * q + 2) * H.stride + sb]};
+  }
+  g.o = Pb[0];
+  for (int q = 0; q < 3; ++q) {
+    g.P[q] = Pb[q] - g.o;
+    D3 y = {X.R[0] * Qb[q].x + X.R[1] * Qb[q].y + X.R[2] * Qb[q].z + X.t[0],
+            X.R[3] * Qb[q].x + X.R[4] * Qb[q].y + X.R[5] * Qb[q].z + X.t[1],
+            X.R[6] * Qb[q].x + X.R[7] * Qb[q].y + X.R[8] * Qb[q].z + X.t[2]};
+    g.Q[q] = y - g.o;
+  }
+  g.tau = 2.0 * X.eps;
+}
+
 namespace {
 
 __device__ __forceinline__ void pose_matrix(const double* p, double R[9]) {
@@ -118,14 +159,15 @@ __global__ void __launch_bounds__(256) k_forces(HierDev H, const int32_t* __rest
 }
 
 // Adjoint: one thread per contact.  Closest points and barycentric weights
-// are recomputed from the triangles in A's frame: float sub-tests select the
-// minimising sub-test(s), which are finished in double (the same scheme as
-// the detection's FP32 form); crossing or nearly touching pairs use the full
-// double test.  Gauss-Newton blocks of contacts that share a pair within a
-// warp are summed in shared memory before one set of atomics per pair.
+// are recomputed from the triangles in A's frame (per-pair transforms from the
+// setup pass): float sub-tests select the minimising sub-test(s), which are
+// finished in double (the detection's FP32 form); crossing or nearly touching
+// pairs use the full double test.  Gauss-Newton blocks of contacts that share
+// a pair within a warp are summed in shared memory before one set of atomics
+// per pair.
 constexpr int kGradThreads = 128;
-__global__ void __launch_bounds__(kGradThreads) k_grad(HierDev H, const int32_t* __restrict__ ab,
-                                                       const double* __restrict__ eps,
+__global__ void __launch_bounds__(kGradThreads) k_grad(HierDev H, const PairXf* __restrict__ xf,
+                                                       const PairXf64* __restrict__ xf64,
                                                        const double* __restrict__ poses,
                                                        mrdem_contacts c,
                                                        const double* __restrict__ mass, double k_s,
@@ -141,41 +183,29 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(HierDev H, const int32_t*
     int p = k < n ? c.pair[k] : -1;
     bool ok = p >= 0 && p < n_pairs;
     double J[12], h = 0.0;
+    if (ok) ok = xf64[p].valid != 0;
     if (ok) {
-      int A = ab[2 * p], B = ab[2 * p + 1];
-      double e = eps[p];
-      const double* pA = poses + 7 * (int64_t)A;
-      const double* pB = poses + 7 * (int64_t)B;
-      double RA[9], RB[9];
-      pose_matrix(pA, RA);
-      pose_matrix(pB, RB);
+      const PairXf64& X64 = xf64[p];
+      const int A = X64.A, B = X64.B;
+      const double e = X64.eps;
       int sa = H.tri_slot[H.tri_off[A] + c.tri_a[k]];
       int sb = H.tri_slot[H.tri_off[B] + c.tri_b[k]];
-      // both triangles in A's frame relative to A's first vertex
-      double Rab[9], tab[3];
-      for (int r = 0; r < 3; ++r) {
-        for (int q = 0; q < 3; ++q)
-          Rab[3 * r + q] = RA[r] * RB[q] + RA[3 + r] * RB[3 + q] + RA[6 + r] * RB[6 + q];
-        tab[r] = RA[r] * (pB[0] - pA[0]) + RA[3 + r] * (pB[1] - pA[1]) + RA[6 + r] * (pB[2] - pA[2]);
-      }
+      // float stage on float coordinates relative to A's first vertex
+      PairXf X;
+      load_pairxf(xf, p, X);
+      V3<float> a0 = load_vertex(H, sa, 0), a1 = load_vertex(H, sa, 1), a2 = load_vertex(H, sa, 2);
+      V3<float> Pf[3] = {{0.f, 0.f, 0.f}, a1 - a0, a2 - a0};
+      V3<float> Qf[3] = {xf_point(X, load_vertex(H, sb, 0)) - a0, xf_point(X, load_vertex(H, sb, 1)) - a0,
+                         xf_point(X, load_vertex(H, sb, 2)) - a0};
+      unsigned mask = 0;
+      int res = cand_float_stage(Pf, Qf, 1e300, X.margin, &mask);
       CandGeom g;
-      D3 Pb[3], Qb[3];
-      for (int q = 0; q < 3; ++q) {
-        Pb[q] = {(double)H.tri[(3 * q) * H.stride + sa], (double)H.tri[(3 * q + 1) * H.stride + sa],
-                 (double)H.tri[(3 * q + 2) * H.stride + sa]};
-        Qb[q] = {(double)H.tri[(3 * q) * H.stride + sb], (double)H.tri[(3 * q + 1) * H.stride + sb],
-                 (double)H.tri[(3 * q + 2) * H.stride + sb]};
-      }
-      g.o = Pb[0];
-      for (int q = 0; q < 3; ++q) {
-        g.P[q] = Pb[q] - g.o;
-        D3 y = mul(Rab, Qb[q]);
-        g.Q[q] = D3{y.x + tab[0], y.y + tab[1], y.z + tab[2]} - g.o;
-      }
-      g.tau = 1e300;
+      cand_geom64(H, X64, sa, sb, g);
       double d, wa[3], wb[3];
       D3 pa, pb;
-      if (cand_fp32(g, d, pa, pb, wa, wb) != 1) {
+      if (res == 1) {
+        d = cand_double_stage(g, mask, pa, pb, wa, wb);
+      } else {
         TriTriResult<double> r = tri_tri_distance(g.P, g.Q);
         d = r.d; pa = r.pa; pb = r.pb;
         for (int q = 0; q < 3; ++q) { wa[q] = r.wa[q]; wb[q] = r.wb[q]; }
@@ -184,34 +214,37 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(HierDev H, const int32_t*
       if (ok) {
         double mu = 1.0 / (1.0 / mass[A] + 1.0 / mass[B]);
         double ks = k_s * sqrt(mu);
-        // world frame: points, direction
-        D3 paw = mul(RA, pa + g.o), pbw = mul(RA, pb + g.o);
-        paw = {paw.x + pA[0], paw.y + pA[1], paw.z + pA[2]};
-        pbw = {pbw.x + pA[0], pbw.y + pA[1], pbw.z + pA[2]};
-        D3 u;
+        // direction in A's frame, then the world
+        D3 uA;
         if (d > 0.0) {
-          u = (1.0 / d) * (paw - pbw);
+          uA = (1.0 / d) * (pa - pb);
         } else {
-          D3 n = cross(g.P[1] - g.P[0], g.P[2] - g.P[0]);
-          u = (-1.0 / sqrt(dot(n, n))) * mul(RA, n);
+          D3 nn = cross(g.P[1] - g.P[0], g.P[2] - g.P[0]);
+          uA = (-1.0 / sqrt(dot(nn, nn))) * nn;
         }
+        D3 paw = mul(X64.RA, pa + g.o), pbw = mul(X64.RA, pb + g.o);
+        paw = {paw.x + X64.tA[0], paw.y + X64.tA[1], paw.z + X64.tA[2]};
+        pbw = {pbw.x + X64.tA[0], pbw.y + X64.tA[1], pbw.z + X64.tA[2]};
+        D3 u = mul(X64.RA, uA);
         double de = -ks * (1.0 - d / (2.0 * e)) * scale;
         D3 gv = de * u;
         if (dverts) {
+          // A's body frame: R_A^T g = de uA; B's body frame: R_rel^T of that
+          D3 gA = de * uA;
+          D3 gB = mul_t(X64.R, gA);
           for (int v = 0; v < 3; ++v) {
             int ia = H.vid[v * H.stride + sa], ib = H.vid[v * H.stride + sb];
-            D3 ga = mul_t(RA, wa[v] * gv);
-            D3 gb = mul_t(RB, (-wb[v]) * gv);
-            atomicAdd(dverts + 3 * (int64_t)ia, (float)ga.x);
-            atomicAdd(dverts + 3 * (int64_t)ia + 1, (float)ga.y);
-            atomicAdd(dverts + 3 * (int64_t)ia + 2, (float)ga.z);
-            atomicAdd(dverts + 3 * (int64_t)ib, (float)gb.x);
-            atomicAdd(dverts + 3 * (int64_t)ib + 1, (float)gb.y);
-            atomicAdd(dverts + 3 * (int64_t)ib + 2, (float)gb.z);
+            atomicAdd(dverts + 3 * (int64_t)ia, (float)(wa[v] * gA.x));
+            atomicAdd(dverts + 3 * (int64_t)ia + 1, (float)(wa[v] * gA.y));
+            atomicAdd(dverts + 3 * (int64_t)ia + 2, (float)(wa[v] * gA.z));
+            atomicAdd(dverts + 3 * (int64_t)ib, (float)(-wb[v] * gB.x));
+            atomicAdd(dverts + 3 * (int64_t)ib + 1, (float)(-wb[v] * gB.y));
+            atomicAdd(dverts + 3 * (int64_t)ib + 2, (float)(-wb[v] * gB.z));
           }
         }
-        D3 ra = paw - D3{pA[0], pA[1], pA[2]};
-        D3 rb = pbw - D3{pB[0], pB[1], pB[2]};
+        const double* tB = poses + 7 * (int64_t)B;
+        D3 ra = paw - D3{X64.tA[0], X64.tA[1], X64.tA[2]};
+        D3 rb = pbw - D3{tB[0], tB[1], tB[2]};
         if (dpose) {
           add3(dpose + 6 * (int64_t)A, gv);
           add3(dpose + 6 * (int64_t)A + 3, cross(ra, gv));
@@ -277,9 +310,13 @@ int launch_grad(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int
                 const double* mass, double k_s, double scale, float* dverts, double* dpose,
                 double* jac, cudaStream_t s) {
   if (!dverts && !dpose && !jac) return MRDEM_OK;
+  if (n_pairs == 0) return MRDEM_OK;
+  // per-pair transforms of this call's poses (no root test)
+  int st = setup_pairs(c, hier, n_pairs, ab, eps, poses, s);
+  if (st != MRDEM_OK) return st;
   ProfScope ps(c, K_GRAD, s);
-  k_grad<<<c->n_sms * 8, kGradThreads, 0, s>>>(hier->dev, ab, eps, poses, *con, mass, k_s, scale, dverts,
-                                       dpose, jac, n_pairs);
+  k_grad<<<c->n_sms * 8, kGradThreads, 0, s>>>(hier->dev, c->xf, c->xf64, poses, *con, mass, k_s,
+                                                scale, dverts, dpose, jac, n_pairs);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
 

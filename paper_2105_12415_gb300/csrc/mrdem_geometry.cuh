@@ -343,17 +343,18 @@ struct CandGeom {
 // float minimum is re-evaluated in double and the smallest value is the
 // distance (the true minimiser is always among them).
 // Returns 1 (contact, r filled), 0 (no contact) or -1 (needs the full FP64 test).
-// Returns 1 (distance <= 2 eps: d, pa, pb and the weights filled), 0 (beyond
-// 2 eps) or -1 (crossing or nearly touching: needs the full double test).
-// With tau = +inf every non-crossing pair is finished (used by the adjoint).
-MRDEM_HD int cand_fp32(const CandGeom& g, double& d, V3<double>& pa, V3<double>& pb,
-                       double* wa = nullptr, double* wb = nullptr) {
-  V3<float> Pf[3], Qf[3];
+// Float stage of the FP32 form: the fifteen sub-tests on float coordinates
+// relative to A's first vertex.  extra_err bounds the error of those
+// coordinates beyond their own rounding (e.g. a float rigid transform).
+// Returns 0 (beyond 2 eps for sure), -1 (crossing or nearly touching: needs
+// the full double test) or 1 (finish in double: the sub-tests whose bit is
+// set in *mask are within 2 err of the float minimum and contain the true
+// minimiser).
+MRDEM_HD int cand_float_stage(const V3<float> Pf[3], const V3<float> Qf[3], double tau,
+                              float extra_err, unsigned* mask) {
   float L = 0.f;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    Pf[k] = {(float)g.P[k].x, (float)g.P[k].y, (float)g.P[k].z};
-    Qf[k] = {(float)g.Q[k].x, (float)g.Q[k].y, (float)g.Q[k].z};
     L = fmaxf(L, fmaxf(fmaxf(fabsf(Pf[k].x), fabsf(Pf[k].y)), fabsf(Pf[k].z)));
     L = fmaxf(L, fmaxf(fmaxf(fabsf(Qf[k].x), fabsf(Qf[k].y)), fabsf(Qf[k].z)));
   }
@@ -362,15 +363,26 @@ MRDEM_HD int cand_fp32(const CandGeom& g, double& d, V3<double>& pa, V3<double>&
   float best2 = d2[0];
 #pragma unroll
   for (int k = 1; k < 15; ++k) best2 = fminf(best2, d2[k]);
-  float err = ldexpf(L, -15);
+  float err = ldexpf(L, -15) + extra_err;
   float d32 = sqrtf(best2);
   if (crossing || d32 <= 2.f * err) return -1;
-  if ((double)d32 > g.tau + (double)err) return 0;
+  if ((double)d32 > tau + (double)err) return 0;
   float lim = d32 + 2.f * err;
   float lim2 = lim * lim;
+  unsigned m = 0;
+#pragma unroll
+  for (int k = 0; k < 15; ++k) m |= (d2[k] <= lim2 ? 1u : 0u) << k;
+  *mask = m;
+  return 1;
+}
+
+// Double stage: the smallest of the masked sub-tests, with closest points
+// and barycentric weights.
+MRDEM_HD double cand_double_stage(const CandGeom& g, unsigned mask, V3<double>& pa,
+                                  V3<double>& pb, double* wa, double* wb) {
   double bd2 = 1e300;
   for (int k = 0; k < 15; ++k) {
-    if (d2[k] > lim2) continue;
+    if (!((mask >> k) & 1u)) continue;
     V3<double> a, b;
     double xa[3], xb[3];
     double v = eval_subtest(g.P, g.Q, k, &a, &b, xa, xb);
@@ -382,7 +394,24 @@ MRDEM_HD int cand_fp32(const CandGeom& g, double& d, V3<double>& pa, V3<double>&
       if (wb) { wb[0] = xb[0]; wb[1] = xb[1]; wb[2] = xb[2]; }
     }
   }
-  d = sqrt(bd2);
+  return sqrt(bd2);
+}
+
+// Returns 1 (distance <= 2 eps: d, pa, pb and the weights filled), 0 (beyond
+// 2 eps) or -1 (crossing or nearly touching: needs the full double test).
+// With tau = +inf every non-crossing pair is finished (used by the adjoint).
+MRDEM_HD int cand_fp32(const CandGeom& g, double& d, V3<double>& pa, V3<double>& pb,
+                       double* wa = nullptr, double* wb = nullptr) {
+  V3<float> Pf[3], Qf[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    Pf[k] = {(float)g.P[k].x, (float)g.P[k].y, (float)g.P[k].z};
+    Qf[k] = {(float)g.Q[k].x, (float)g.Q[k].y, (float)g.Q[k].z};
+  }
+  unsigned mask = 0;
+  int r = cand_float_stage(Pf, Qf, g.tau, 0.f, &mask);
+  if (r != 1) return r;
+  d = cand_double_stage(g, mask, pa, pb, wa, wb);
   return d <= g.tau ? 1 : 0;
 }
 

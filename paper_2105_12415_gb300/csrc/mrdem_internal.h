@@ -175,6 +175,8 @@ int launch_detect(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const
 int launch_plain(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
                  const double* pair_eps, const double* poses, const mrdem_contacts* out,
                  cudaStream_t s);
+int setup_pairs(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
+                const double* eps, const double* poses, cudaStream_t s);
 int launch_forces(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
                   const double* pair_eps, const double* poses, const mrdem_contacts* c,
                   const double* mass, const double* com, double k_s, double* ft, double* energy,
