@@ -527,7 +527,12 @@ __global__ void __launch_bounds__(256) k_sweep_fine(HierDev H, const PairXf* __r
         gap = sweep_certificate<CONV, 4>(p0, p1, p2, q0, q1, q2, sc, ce * ce, &cv, nullptr);
       else
         gap = sweep_certificate<CONV, 0>(p0, p1, p2, q0, q1, q2, sc, ce * ce, &cv, nullptr);
-      s = !(gap > X.tau + X.margin);
+      const float thr = X.tau + X.margin;
+      // a pair the sweep's direction cannot separate may still be separated
+      // along one of the face normals (nearly parallel triangles)
+      if (!(gap > thr)) gap = fmaxf(axis_gap(cross(p1 - p0, p2 - p0), p0, p1, p2, q0, q1, q2),
+                                    axis_gap(cross(q1 - q0, q2 - q0), p0, p1, p2, q0, q1, q2));
+      s = !(gap > thr);
     }
     tests.add(act);
     ncand.add(s);

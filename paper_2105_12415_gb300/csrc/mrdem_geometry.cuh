@@ -61,6 +61,25 @@ MRDEM_HD T my_sqrt(T v) { return sqrt(v); }
 template <>
 MRDEM_HD float my_sqrt<float>(float v) { return sqrtf(v); }
 
+// Quotient a / b.  In double on the device: a float reciprocal of b refined by
+// two Newton-Raphson steps r <- r (2 - b r) (each doubles the correct bits:
+// ~23 -> 46 -> 92) and one residual correction of the quotient; about one ulp,
+// far cheaper than the correctly rounded division, and exact enough for the
+// final distances; divisors outside [1e-30, 1e30] take the ordinary division.
+template <typename T>
+MRDEM_HD T qdiv(T a, T b) { return a / b; }
+#ifdef __CUDA_ARCH__
+template <>
+__device__ __forceinline__ double qdiv<double>(double a, double b) {
+  if (!(fabs(b) > 1e-30 && fabs(b) < 1e30)) return a / b;  // outside the float seed's range
+  double r = (double)__frcp_rn((float)b);
+  r = fma(r, fma(-b, r, 1.0), r);
+  r = fma(r, fma(-b, r, 1.0), r);
+  double q = a * r;
+  return fma(r, fma(-b, q, a), q);
+}
+#endif
+
 // Result of a closest-point query between two triangles P and Q.
 template <typename T>
 struct TriTriResult {
@@ -83,7 +102,7 @@ MRDEM_HD V3<T> closest_on_triangle(V3<T> p, V3<T> a, V3<T> b, V3<T> c, T w[3]) {
   if (d3 >= T(0) && d4 <= d3) { w[0] = 0; w[1] = 1; w[2] = 0; return b; }
   T vc = d1 * d4 - d3 * d2;
   if (vc <= T(0) && d1 >= T(0) && d3 <= T(0)) {
-    T s = d1 / (d1 - d3);
+    T s = qdiv(d1, d1 - d3);
     w[0] = T(1) - s; w[1] = s; w[2] = 0;
     return a + s * ab;
   }
@@ -92,18 +111,18 @@ MRDEM_HD V3<T> closest_on_triangle(V3<T> p, V3<T> a, V3<T> b, V3<T> c, T w[3]) {
   if (d6 >= T(0) && d5 <= d6) { w[0] = 0; w[1] = 0; w[2] = 1; return c; }
   T vb = d5 * d2 - d1 * d6;
   if (vb <= T(0) && d2 >= T(0) && d6 <= T(0)) {
-    T s = d2 / (d2 - d6);
+    T s = qdiv(d2, d2 - d6);
     w[0] = T(1) - s; w[1] = 0; w[2] = s;
     return a + s * ac;
   }
   T va = d3 * d6 - d5 * d4;
   T e43 = d4 - d3, e56 = d5 - d6;
   if (va <= T(0) && e43 >= T(0) && e56 >= T(0)) {
-    T s = e43 / (e43 + e56);
+    T s = qdiv(e43, e43 + e56);
     w[0] = 0; w[1] = T(1) - s; w[2] = s;
     return b + s * (c - b);
   }
-  T inv = T(1) / (va + vb + vc);
+  T inv = qdiv(T(1), va + vb + vc);
   T v = vb * inv, u = vc * inv;
   w[0] = T(1) - v - u; w[1] = v; w[2] = u;
   return a + v * ab + u * ac;
@@ -120,14 +139,14 @@ MRDEM_HD void closest_segments(V3<T> p1, V3<T> q1, V3<T> p2, V3<T> q2, T* s_out,
   T c = dot(d1, r), b = dot(d1, d2);
   T den = a * e - b * b;
   *near_parallel = den <= T(1e-6) * a * e;
-  T s = den > T(0) ? clamp01((b * f - c * e) / den) : T(0);
-  T t = (b * s + f) / e;
+  T s = den > T(0) ? clamp01(qdiv(b * f - c * e, den)) : T(0);
+  T t = qdiv(b * s + f, e);
   if (t < T(0)) {
     t = T(0);
-    s = clamp01(-c / a);
+    s = clamp01(qdiv(-c, a));
   } else if (t > T(1)) {
     t = T(1);
-    s = clamp01((b - c) / a);
+    s = clamp01(qdiv(b - c, a));
   }
   *s_out = s;
   *t_out = t;
@@ -513,6 +532,24 @@ MRDEM_HD float sweep_certificate(V3<float> p0, V3<float> p1, V3<float> p2, V3<fl
   float mp = fminf(dot(r, p0), fminf(dot(r, p1), dot(r, p2)));
   float mq = fmaxf(dot(r, q0), fmaxf(dot(r, q1), dot(r, q2)));
   return (mp - mq) * inv;
+}
+
+// Support gap of the two triangles along an axis n (any non-zero vector):
+// max over both orientations of (min over one triangle - max over the other),
+// divided by |n|.  Like the sweep's certificate it bounds the distance from
+// below; along the face normals it is tight for nearly parallel triangles.
+MRDEM_HD float axis_gap(V3<float> n, V3<float> p0, V3<float> p1, V3<float> p2, V3<float> q0,
+                        V3<float> q1, V3<float> q2) {
+  float a0 = dot(n, p0), a1 = dot(n, p1), a2 = dot(n, p2);
+  float b0 = dot(n, q0), b1 = dot(n, q1), b2 = dot(n, q2);
+  float amin = fminf(a0, fminf(a1, a2)), amax = fmaxf(a0, fmaxf(a1, a2));
+  float bmin = fminf(b0, fminf(b1, b2)), bmax = fmaxf(b0, fmaxf(b1, b2));
+#ifdef __CUDA_ARCH__
+  float inv = rsqrtf(dot(n, n));
+#else
+  float inv = 1.f / sqrtf(dot(n, n));
+#endif
+  return fmaxf(amin - bmax, bmin - amax) * inv;
 }
 
 }  // namespace mrdem
