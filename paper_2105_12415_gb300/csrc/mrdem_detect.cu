@@ -353,13 +353,16 @@ __global__ void __launch_bounds__(256) k_sweep_nodes(HierDev H, const PairXf* __
       F3 q2 = xf_point(X, {b2.x, b2.y, b2.z});
       bool cv;
       float gap;
+      F3 p0 = {a0.x, a0.y, a0.z}, p1 = {a1.x, a1.y, a1.z}, p2 = {a2.x, a2.y, a2.z};
       if (sc.n_iter == 4)
-        gap = sweep_certificate<false, 4>({a0.x, a0.y, a0.z}, {a1.x, a1.y, a1.z}, {a2.x, a2.y, a2.z},
-                                          q0, q1, q2, sc, 0.f, &cv, nullptr);
+        gap = sweep_certificate<false, 4>(p0, p1, p2, q0, q1, q2, sc, 0.f, &cv, nullptr);
       else
-        gap = sweep_certificate<false, 0>({a0.x, a0.y, a0.z}, {a1.x, a1.y, a1.z}, {a2.x, a2.y, a2.z},
-                                          q0, q1, q2, sc, 0.f, &cv, nullptr);
-      s = !(gap > a0.w + b0.w + X.tau + X.margin);
+        gap = sweep_certificate<false, 0>(p0, p1, p2, q0, q1, q2, sc, 0.f, &cv, nullptr);
+      const float thr = a0.w + b0.w + X.tau + X.margin;
+      // the surrogates' face normals as further separating axes
+      if (!(gap > thr)) gap = fmaxf(axis_gap(cross(p1 - p0, p2 - p0), p0, p1, p2, q0, q1, q2),
+                                    axis_gap(cross(q1 - q0, q2 - q0), p0, p1, p2, q0, q1, q2));
+      s = !(gap > thr);
     }
     bool leaves = ia.y < 0 && ib.y < 0;
     nsweep.add(act);
