@@ -18,9 +18,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 
-CU_SOURCES = ["mrdem_detect.cu", "mrdem_forces.cu"]
+CU_SOURCES = ["mrdem_detect.cu", "mrdem_forces.cu", "mrdem_closest.cu"]
 CPP_SOURCES = ["mrdem_api.cpp", "mrdem_hierarchy.cpp"]
-HEADERS = ["mrdem_geometry.cuh", "mrdem_internal.h"]
+HEADERS = ["mrdem_geometry.cuh", "mrdem_internal.h", "mrdem_device.cuh"]
 
 
 def _inputs():

@@ -33,6 +33,15 @@ void free_lists(mrdem_ctx* c) {
   cudaFree(c->cands);
   cudaFree(c->sweep);
   c->sweep = nullptr;
+  cudaFree(c->acc);
+  cudaFree(c->items_pt);
+  cudaFree(c->items_ee);
+  cudaFree(c->res_pt);
+  cudaFree(c->res_ee);
+  c->acc = nullptr;
+  c->items_pt = c->items_ee = nullptr;
+  c->res_pt = c->res_ee = nullptr;
+  c->cap_items = 0;
   c->level_list[0] = c->level_list[1] = nullptr;
   c->tiles = nullptr;
   c->cands = nullptr;
@@ -45,7 +54,12 @@ int alloc_lists(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca, int64_t sw) {
       cudaMalloc(&c->level_list[1], sizeof(int4) * lv) != cudaSuccess ||
       cudaMalloc(&c->tiles, sizeof(TileItem) * ti) != cudaSuccess ||
       cudaMalloc(&c->cands, sizeof(int3) * ca) != cudaSuccess ||
-      cudaMalloc(&c->sweep, sizeof(int4) * sw) != cudaSuccess) {
+      cudaMalloc(&c->sweep, sizeof(int4) * sw) != cudaSuccess ||
+      cudaMalloc(&c->acc, sizeof(AccRec) * ca) != cudaSuccess ||
+      cudaMalloc(&c->items_pt, sizeof(int) * 2 * ca) != cudaSuccess ||
+      cudaMalloc(&c->items_ee, sizeof(int) * 2 * ca) != cudaSuccess ||
+      cudaMalloc(&c->res_pt, sizeof(ItemRes) * 2 * ca) != cudaSuccess ||
+      cudaMalloc(&c->res_ee, sizeof(ItemRes) * 2 * ca) != cudaSuccess) {
     cudaGetLastError();
     free_lists(c);
     return MRDEM_ERR_OOM;
@@ -54,6 +68,7 @@ int alloc_lists(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca, int64_t sw) {
   c->cap_tiles = ti;
   c->cap_cands = ca;
   c->cap_sweep = sw;
+  c->cap_items = 2 * ca;
   return MRDEM_OK;
 }
 
@@ -90,7 +105,7 @@ void mrdem_default_params(mrdem_params* p) {
   p->kmeans_iters = 3;
   p->cap_level = (int64_t)1 << 24;
   p->cap_tiles = (int64_t)1 << 24;
-  p->cap_candidates = (int64_t)1 << 25;
+  p->cap_candidates = (int64_t)1 << 20;
   p->tile_warps = 8;
   p->tile_blocks_per_sm = 4;
   p->level_warps = 8;

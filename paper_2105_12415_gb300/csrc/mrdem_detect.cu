@@ -29,112 +29,12 @@
 #include <mutex>
 #include <vector>
 
-#include "mrdem_geometry.cuh"
-#include "mrdem_internal.h"
+#include "mrdem_device.cuh"
 
 namespace mrdem {
 
 using F3 = V3<float>;
 using D3 = V3<double>;
-
-// ---------------------------------------------------------------------------
-// helpers
-__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
-
-__device__ __forceinline__ void quat_matrix(double w, double x, double y, double z, double R[9]) {
-  double n = w * w + x * x + y * y + z * z;
-  double s = 2.0 / n;
-  double xx = s * x * x, yy = s * y * y, zz = s * z * z;
-  double xy = s * x * y, xz = s * x * z, yz = s * y * z;
-  double wx = s * w * x, wy = s * w * y, wz = s * w * z;
-  R[0] = 1.0 - (yy + zz); R[1] = xy - wz;         R[2] = xz + wy;
-  R[3] = xy + wz;         R[4] = 1.0 - (xx + zz); R[5] = yz - wx;
-  R[6] = xz - wy;         R[7] = yz + wx;         R[8] = 1.0 - (xx + yy);
-}
-
-// Append `item` for each lane with `pred` to `list` (capacity cap); one
-// atomic per warp.  Must be called by all 32 lanes.  Overflowing entries are
-// dropped and the needed size is latched in *req.
-template <typename Item>
-__device__ __forceinline__ void warp_append(bool pred, const Item& item, Item* list,
-                                            unsigned long long* counter, int64_t cap,
-                                            unsigned long long* req) {
-  unsigned m = __ballot_sync(0xffffffffu, pred);
-  if (!m) return;
-  int leader = __ffs(m) - 1;
-  unsigned long long base = 0;
-  if ((int)lane_id() == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (pred) {
-    unsigned long long idx = base + __popc(m & ((1u << lane_id()) - 1u));
-    if ((int64_t)idx < cap) list[idx] = item;
-    else atomicMax(req, idx + 1);
-  }
-}
-
-// Per-warp output queue in shared memory: items are collected with a ballot
-// per round and written out in batches, one global atomic per batch instead
-// of one per round.  All calls must be made by all 32 lanes.
-template <typename Item, int CAP>
-struct WarpQueue {
-  Item* buf;  // shared memory, CAP items
-  int n = 0;  // warp-uniform fill level
-  __device__ __forceinline__ void flush(Item* list, unsigned long long* counter, int64_t cap,
-                                        unsigned long long* req) {
-    __syncwarp();
-    if (n == 0) return;
-    unsigned long long base = 0;
-    if (lane_id() == 0) base = atomicAdd(counter, (unsigned long long)n);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    for (int k = lane_id(); k < n; k += 32) {
-      unsigned long long idx = base + k;
-      if ((int64_t)idx < cap) list[idx] = buf[k];
-      else atomicMax(req, idx + 1);
-    }
-    n = 0;
-    __syncwarp();
-  }
-  __device__ __forceinline__ void push(bool pred, const Item& item, Item* list,
-                                       unsigned long long* counter, int64_t cap,
-                                       unsigned long long* req) {
-    unsigned m = __ballot_sync(0xffffffffu, pred);
-    if (pred) buf[n + __popc(m & ((1u << lane_id()) - 1u))] = item;
-    n += __popc(m);
-    if (n > CAP - 32) flush(list, counter, cap, req);
-  }
-};
-
-__device__ __forceinline__ F3 xf_point(const PairXf& X, F3 v) {
-  return {fmaf(X.R[0], v.x, fmaf(X.R[1], v.y, fmaf(X.R[2], v.z, X.t[0]))),
-          fmaf(X.R[3], v.x, fmaf(X.R[4], v.y, fmaf(X.R[5], v.z, X.t[1]))),
-          fmaf(X.R[6], v.x, fmaf(X.R[7], v.y, fmaf(X.R[8], v.z, X.t[2])))};
-}
-__device__ __forceinline__ D3 xf_point64(const double* R, const double* t, D3 v) {
-  return {R[0] * v.x + R[1] * v.y + R[2] * v.z + t[0], R[3] * v.x + R[4] * v.y + R[5] * v.z + t[1],
-          R[6] * v.x + R[7] * v.y + R[8] * v.z + t[2]};
-}
-
-__device__ __forceinline__ void load_pairxf(const PairXf* xf, int p, PairXf& X) {
-  const float4* s = reinterpret_cast<const float4*>(xf + p);
-  float4 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2), d = __ldg(s + 3);
-  X.R[0] = a.x; X.R[1] = a.y; X.R[2] = a.z; X.R[3] = a.w;
-  X.R[4] = b.x; X.R[5] = b.y; X.R[6] = b.z; X.R[7] = b.w;
-  X.R[8] = c.x; X.t[0] = c.y; X.t[1] = c.z; X.t[2] = c.w;
-  X.tau = d.x; X.margin = d.y;
-  X.A = __float_as_int(d.z); X.B = __float_as_int(d.w);
-}
-
-// Warp-aggregated statistics: lane 0 keeps the warp's running totals.
-struct WarpCount {
-  unsigned v = 0;  // per-warp totals stay far below 2^32
-  __device__ __forceinline__ void add(bool pred) {
-    unsigned m = __ballot_sync(0xffffffffu, pred);
-    v += __popc(m);
-  }
-  __device__ __forceinline__ void flush(unsigned long long* dst) {
-    if (lane_id() == 0 && v) atomicAdd(dst, (unsigned long long)v);
-  }
-};
 
 __device__ __forceinline__ TileItem make_tile(int pair, int na_node, int nb_node, int2 ia, int2 ib) {
   TileItem t;
@@ -415,10 +315,6 @@ __device__ __forceinline__ TileItem load_tile(const TileItem* tiles, int64_t t) 
   return r;
 }
 
-__device__ __forceinline__ F3 load_vertex(const HierDev& H, int slot, int c) {
-  return {__ldg(H.tri + (3 * c + 0) * H.stride + slot), __ldg(H.tri + (3 * c + 1) * H.stride + slot),
-          __ldg(H.tri + (3 * c + 2) * H.stride + slot)};
-}
 
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_tile(HierDev H, const PairXf* __restrict__ xf,
@@ -559,51 +455,6 @@ __global__ void __launch_bounds__(256) k_sweep_fine(HierDev H, const PairXf* __r
 //   always among them, so this equals the double comparison-based result).
 //   Crossing or nearly touching pairs go to a fallback list that the FP64
 //   kernel finishes.
-__device__ __forceinline__ void load_tri64(const HierDev& H, int slot, D3 T[3]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    T[c].x = (double)__ldg(H.tri + (3 * c + 0) * H.stride + slot);
-    T[c].y = (double)__ldg(H.tri + (3 * c + 1) * H.stride + slot);
-    T[c].z = (double)__ldg(H.tri + (3 * c + 2) * H.stride + slot);
-  }
-}
-
-__device__ __forceinline__ void cand_geom(const HierDev& H, const PairXf64& X, int3 c, CandGeom& g) {
-  D3 Pb[3], Qb[3];
-  load_tri64(H, c.y, Pb);
-  load_tri64(H, c.z, Qb);
-  g.o = Pb[0];
-#pragma unroll
-  for (int v = 0; v < 3; ++v) {
-    g.P[v] = Pb[v] - g.o;
-    g.Q[v] = xf_point64(X.R, X.t, Qb[v]) - g.o;
-  }
-  g.tau = 2.0 * X.eps;
-}
-
-__device__ __forceinline__ void write_contact(const HierDev& H, const mrdem_contacts& out,
-                                              unsigned long long* status, bool hit, int pair,
-                                              int sa, int sb, double d, D3 pa, D3 pb) {
-  unsigned m = __ballot_sync(0xffffffffu, hit);
-  if (!m) return;
-  int leader = __ffs(m) - 1;
-  unsigned long long b = 0;
-  if ((int)lane_id() == leader) b = atomicAdd((unsigned long long*)out.count, (unsigned long long)__popc(m));
-  b = __shfl_sync(0xffffffffu, b, leader);
-  if (!hit) return;
-  unsigned long long idx = b + __popc(m & ((1u << lane_id()) - 1u));
-  if ((int64_t)idx < out.capacity) {
-    out.pair[idx] = pair;
-    out.tri_a[idx] = H.slot_tri[sa];
-    out.tri_b[idx] = H.slot_tri[sb];
-    out.dist[idx] = d;
-    out.point_a[3 * idx] = pa.x; out.point_a[3 * idx + 1] = pa.y; out.point_a[3 * idx + 2] = pa.z;
-    out.point_b[3 * idx] = pb.x; out.point_b[3 * idx + 1] = pb.y; out.point_b[3 * idx + 2] = pb.z;
-  } else {
-    atomicMax(status + ST_REQ_CONTACTS, idx + 1);
-  }
-}
-
 // FP32 form, first pass over the candidates.  The float stage runs on float
 // coordinates (B moved by the float transform; its error is within the
 // pair's margin), so pairs it rejects never touch double arithmetic; the
@@ -906,17 +757,8 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
       k_exact64<<<c->n_sms * 8, et, 0, s>>>(H, c->xf64, c->cands, c->counters, CNT_CANDS,
                                              c->cap_cands, c->status, MRDEM_STAT_FP64, *out);
     } else {
-      {
-        ProfScope ps(c, K_EXACT, s);
-        // the level lists are free once the tiles are done: reuse one as the fallback list
-        k_exact32<<<c->n_sms * 8, et, 0, s>>>(H, c->xf, c->xf64, c->cands, c->counters, c->status,
-                                               c->cap_cands, reinterpret_cast<int3*>(c->level_list[0]),
-                                               c->cap_level, *out);
-      }
-      ProfScope ps(c, K_EXACT64, s);
-      k_exact64<<<c->n_sms * 4, et, 0, s>>>(H, c->xf64, reinterpret_cast<const int3*>(c->level_list[0]),
-                                             c->counters, CNT_FALLBACK, c->cap_level, c->status,
-                                             MRDEM_STAT_FP64, *out);
+      int r = launch_exact_fp32(c, hier, out, s);
+      if (r) return r;
     }
   }
   if (stats)

@@ -16,53 +16,10 @@
 
 #include <algorithm>
 
-#include "mrdem_geometry.cuh"
-#include "mrdem_internal.h"
+#include "mrdem_device.cuh"
 
 namespace mrdem {
 
-using D3 = V3<double>;
-
-// helpers (the same layout as the detection kernels use)
-__device__ __forceinline__ V3<float> load_vertex(const HierDev& H, int slot, int c) {
-  return {__ldg(H.tri + (3 * c + 0) * H.stride + slot), __ldg(H.tri + (3 * c + 1) * H.stride + slot),
-          __ldg(H.tri + (3 * c + 2) * H.stride + slot)};
-}
-__device__ __forceinline__ V3<float> xf_point(const PairXf& X, V3<float> v) {
-  return {fmaf(X.R[0], v.x, fmaf(X.R[1], v.y, fmaf(X.R[2], v.z, X.t[0]))),
-          fmaf(X.R[3], v.x, fmaf(X.R[4], v.y, fmaf(X.R[5], v.z, X.t[1]))),
-          fmaf(X.R[6], v.x, fmaf(X.R[7], v.y, fmaf(X.R[8], v.z, X.t[2])))};
-}
-__device__ __forceinline__ void load_pairxf(const PairXf* xf, int p, PairXf& X) {
-  const float4* q = reinterpret_cast<const float4*>(xf + p);
-  float4 a = __ldg(q), b = __ldg(q + 1), cc = __ldg(q + 2), d = __ldg(q + 3);
-  X.R[0] = a.x; X.R[1] = a.y; X.R[2] = a.z; X.R[3] = a.w;
-  X.R[4] = b.x; X.R[5] = b.y; X.R[6] = b.z; X.R[7] = b.w;
-  X.R[8] = cc.x; X.t[0] = cc.y; X.t[1] = cc.z; X.t[2] = cc.w;
-  X.tau = d.x; X.margin = d.y;
-  X.A = __float_as_int(d.z); X.B = __float_as_int(d.w);
-}
-// Both triangles of a candidate in A's frame, relative to A's first vertex
-// (double, from the double transform).
-__device__ __forceinline__ void cand_geom64(const HierDev& H, const PairXf64& X, int sa, int sb,
-                                            CandGeom& g) {
-  D3 Pb[3], Qb[3];
-  for (int q = 0; q < 3; ++q) {
-    Pb[q] = {(double)H.tri[(3 * q) * H.stride + sa], (double)H.tri[(3 * q + 1) * H.stride + sa],
-             (double)H.tri[(3 * q + 2) * H.stride + sa]};
-    Qb[q] = {(double)H.tri[(3 * q) * H.stride + sb], (double)H.tri[(3 * q + 1) * H.stride + sb],
-             (double)H.tri[(3 * q + 2) * H.stride + sb]};
-  }
-  g.o = Pb[0];
-  for (int q = 0; q < 3; ++q) {
-    g.P[q] = Pb[q] - g.o;
-    D3 y = {X.R[0] * Qb[q].x + X.R[1] * Qb[q].y + X.R[2] * Qb[q].z + X.t[0],
-            X.R[3] * Qb[q].x + X.R[4] * Qb[q].y + X.R[5] * Qb[q].z + X.t[1],
-            X.R[6] * Qb[q].x + X.R[7] * Qb[q].y + X.R[8] * Qb[q].z + X.t[2]};
-    g.Q[q] = y - g.o;
-  }
-  g.tau = 2.0 * X.eps;
-}
 
 namespace {
 
@@ -76,10 +33,6 @@ __device__ __forceinline__ void pose_matrix(const double* p, double R[9]) {
 __device__ __forceinline__ D3 mul(const double R[9], D3 v) {
   return {R[0] * v.x + R[1] * v.y + R[2] * v.z, R[3] * v.x + R[4] * v.y + R[5] * v.z,
           R[6] * v.x + R[7] * v.y + R[8] * v.z};
-}
-__device__ __forceinline__ D3 mul_t(const double R[9], D3 v) {
-  return {R[0] * v.x + R[3] * v.y + R[6] * v.z, R[1] * v.x + R[4] * v.y + R[7] * v.z,
-          R[2] * v.x + R[5] * v.y + R[8] * v.z};
 }
 __device__ __forceinline__ void world_tri(const HierDev& H, int slot, const double R[9],
                                           const double* t, D3 T[3]) {
@@ -158,140 +111,6 @@ __global__ void __launch_bounds__(256) k_forces(HierDev H, const int32_t* __rest
   }
 }
 
-// Adjoint: one thread per contact.  Closest points and barycentric weights
-// are recomputed from the triangles in A's frame (per-pair transforms from the
-// setup pass): float sub-tests select the minimising sub-test(s), which are
-// finished in double (the detection's FP32 form); crossing or nearly touching
-// pairs use the full double test.  Gauss-Newton blocks of contacts that share
-// a pair within a warp are summed in shared memory before one set of atomics
-// per pair.
-constexpr int kGradThreads = 128;
-__global__ void __launch_bounds__(kGradThreads) k_grad(HierDev H, const PairXf* __restrict__ xf,
-                                                       const PairXf64* __restrict__ xf64,
-                                                       const double* __restrict__ poses,
-                                                       mrdem_contacts c,
-                                                       const double* __restrict__ mass, double k_s,
-                                                       double scale, float* dverts, double* dpose,
-                                                       double* jac, int64_t n_pairs) {
-  __shared__ double sJ[kGradThreads / 32][32][13];  // 12 Jacobian entries and the weight e''
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t n = *c.count;
-  if (n > c.capacity) n = c.capacity;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-    int64_t k = base + threadIdx.x;
-    int p = k < n ? c.pair[k] : -1;
-    bool ok = p >= 0 && p < n_pairs;
-    double J[12], h = 0.0;
-    if (ok) ok = xf64[p].valid != 0;
-    if (ok) {
-      const PairXf64& X64 = xf64[p];
-      const int A = X64.A, B = X64.B;
-      const double e = X64.eps;
-      int sa = H.tri_slot[H.tri_off[A] + c.tri_a[k]];
-      int sb = H.tri_slot[H.tri_off[B] + c.tri_b[k]];
-      // float stage on float coordinates relative to A's first vertex
-      PairXf X;
-      load_pairxf(xf, p, X);
-      V3<float> a0 = load_vertex(H, sa, 0), a1 = load_vertex(H, sa, 1), a2 = load_vertex(H, sa, 2);
-      V3<float> Pf[3] = {{0.f, 0.f, 0.f}, a1 - a0, a2 - a0};
-      V3<float> Qf[3] = {xf_point(X, load_vertex(H, sb, 0)) - a0, xf_point(X, load_vertex(H, sb, 1)) - a0,
-                         xf_point(X, load_vertex(H, sb, 2)) - a0};
-      unsigned mask = 0;
-      int res = cand_float_stage(Pf, Qf, 1e300, X.margin, &mask);
-      CandGeom g;
-      cand_geom64(H, X64, sa, sb, g);
-      double d, wa[3], wb[3];
-      D3 pa, pb;
-      if (res == 1) {
-        d = cand_double_stage(g, mask, pa, pb, wa, wb);
-      } else {
-        TriTriResult<double> r = tri_tri_distance(g.P, g.Q);
-        d = r.d; pa = r.pa; pb = r.pb;
-        for (int q = 0; q < 3; ++q) { wa[q] = r.wa[q]; wb[q] = r.wb[q]; }
-      }
-      ok = d <= 2.0 * e;
-      if (ok) {
-        double mu = 1.0 / (1.0 / mass[A] + 1.0 / mass[B]);
-        double ks = k_s * sqrt(mu);
-        // direction in A's frame, then the world
-        D3 uA;
-        if (d > 0.0) {
-          uA = (1.0 / d) * (pa - pb);
-        } else {
-          D3 nn = cross(g.P[1] - g.P[0], g.P[2] - g.P[0]);
-          uA = (-1.0 / sqrt(dot(nn, nn))) * nn;
-        }
-        D3 paw = mul(X64.RA, pa + g.o), pbw = mul(X64.RA, pb + g.o);
-        paw = {paw.x + X64.tA[0], paw.y + X64.tA[1], paw.z + X64.tA[2]};
-        pbw = {pbw.x + X64.tA[0], pbw.y + X64.tA[1], pbw.z + X64.tA[2]};
-        D3 u = mul(X64.RA, uA);
-        double de = -ks * (1.0 - d / (2.0 * e)) * scale;
-        D3 gv = de * u;
-        if (dverts) {
-          // A's body frame: R_A^T g = de uA; B's body frame: R_rel^T of that
-          D3 gA = de * uA;
-          D3 gB = mul_t(X64.R, gA);
-          for (int v = 0; v < 3; ++v) {
-            int ia = H.vid[v * H.stride + sa], ib = H.vid[v * H.stride + sb];
-            atomicAdd(dverts + 3 * (int64_t)ia, (float)(wa[v] * gA.x));
-            atomicAdd(dverts + 3 * (int64_t)ia + 1, (float)(wa[v] * gA.y));
-            atomicAdd(dverts + 3 * (int64_t)ia + 2, (float)(wa[v] * gA.z));
-            atomicAdd(dverts + 3 * (int64_t)ib, (float)(-wb[v] * gB.x));
-            atomicAdd(dverts + 3 * (int64_t)ib + 1, (float)(-wb[v] * gB.y));
-            atomicAdd(dverts + 3 * (int64_t)ib + 2, (float)(-wb[v] * gB.z));
-          }
-        }
-        const double* tB = poses + 7 * (int64_t)B;
-        D3 ra = paw - D3{X64.tA[0], X64.tA[1], X64.tA[2]};
-        D3 rb = pbw - D3{tB[0], tB[1], tB[2]};
-        if (dpose) {
-          add3(dpose + 6 * (int64_t)A, gv);
-          add3(dpose + 6 * (int64_t)A + 3, cross(ra, gv));
-          add3(dpose + 6 * (int64_t)B, -1.0 * gv);
-          add3(dpose + 6 * (int64_t)B + 3, cross(rb, -1.0 * gv));
-        }
-        D3 c1 = cross(ra, u), c2 = cross(rb, u);
-        J[0] = u.x; J[1] = u.y; J[2] = u.z; J[3] = c1.x; J[4] = c1.y; J[5] = c1.z;
-        J[6] = -u.x; J[7] = -u.y; J[8] = -u.z; J[9] = -c2.x; J[10] = -c2.y; J[11] = -c2.z;
-        h = ks / (2.0 * e) * scale;
-      }
-    }
-    if (jac) {
-      // group the warp's contacts by pair; each group's 78 distinct block
-      // entries are summed by the lanes in turn and added once
-      for (int q = 0; q < 12; ++q) sJ[w][lane][q] = ok ? J[q] : 0.0;
-      sJ[w][lane][12] = ok ? h : 0.0;
-      __syncwarp();
-      unsigned pending = __ballot_sync(0xffffffffu, ok);
-      int mykey = ok ? p : -1;
-      while (pending) {
-        int leader = __ffs(pending) - 1;
-        int key = __shfl_sync(0xffffffffu, mykey, leader);
-        unsigned grp = __ballot_sync(0xffffffffu, ok && mykey == key);
-        pending &= ~grp;
-        for (int e2 = lane; e2 < 78; e2 += 32) {
-          // e2 -> (r, q) with r <= q in the upper triangle of 12 x 12
-          int r = 0, rem = e2;
-          while (rem >= 12 - r) { rem -= 12 - r; ++r; }
-          int q = r + rem;
-          double acc = 0.0;
-          unsigned gm = grp;
-          while (gm) {
-            int l = __ffs(gm) - 1;
-            gm &= gm - 1;
-            acc += sJ[w][l][12] * sJ[w][l][r] * sJ[w][l][q];
-          }
-          double* o = jac + 144 * (int64_t)key;
-          atomicAdd(o + 12 * r + q, acc);
-          if (q != r) atomicAdd(o + 12 * q + r, acc);
-        }
-      }
-      __syncwarp();
-    }
-  }
-}
-
 }  // namespace
 
 int launch_forces(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
@@ -311,13 +130,12 @@ int launch_grad(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int
                 double* jac, cudaStream_t s) {
   if (!dverts && !dpose && !jac) return MRDEM_OK;
   if (n_pairs == 0) return MRDEM_OK;
-  // per-pair transforms of this call's poses (no root test)
+  // per-pair transforms of this call's poses (no root test), then the
+  // closest points of every contact and the scatter
   int st = setup_pairs(c, hier, n_pairs, ab, eps, poses, s);
   if (st != MRDEM_OK) return st;
-  ProfScope ps(c, K_GRAD, s);
-  k_grad<<<c->n_sms * 8, kGradThreads, 0, s>>>(hier->dev, c->xf, c->xf64, poses, *con, mass, k_s,
-                                                scale, dverts, dpose, jac, n_pairs);
-  return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+  return launch_grad_closest(c, hier, n_pairs, ab, poses, con, mass, k_s, scale, dverts, dpose,
+                             jac, s);
 }
 
 }  // namespace mrdem

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "mrdem.h"
+#include "mrdem_geometry.cuh"
 
 namespace mrdem {
 
@@ -74,6 +75,22 @@ struct alignas(16) TileItem {
   int slot_b, counts, pad0, pad1;  // counts = na | nb << 8
 };
 
+// A pair accepted by the float stage of the closest-point computation: its
+// double geometry and the ranges of its work items.
+struct AccRec {
+  CandGeom g;
+  int entry, pair;
+  int pt_begin, ee_begin;
+  int counts;  // point-triangle items | edge-edge items << 8
+  int pad;
+};
+// Result of one sub-test in double: squared distance, closest points and
+// barycentric weights (A's frame, relative to the pair's origin).
+struct ItemRes {
+  double d2;
+  double pa[3], pb[3], wa[3], wb[3];
+};
+
 // Device counters (one int64 array, zeroed at the start of every detect).
 enum Counter : int {
   CNT_LEVEL = 0,                          // [0..kMaxLevels] items in level list l
@@ -82,6 +99,9 @@ enum Counter : int {
   CNT_CANDS,
   CNT_FALLBACK,                           // FP32 form: candidates left for the FP64 test
   CNT_SWEEP,                              // entries in the sweep list
+  CNT_ACC,                                // pairs accepted by the float stage
+  CNT_PT,                                 // point-triangle work items
+  CNT_EE,                                 // edge-edge work items
   CNT_STATS,                              // [MRDEM_STAT_COUNT] statistics
   CNT_TOTAL = CNT_STATS + MRDEM_STAT_COUNT
 };
@@ -122,6 +142,12 @@ struct mrdem_ctx {
   mrdem::TileItem* tiles = nullptr;
   int3* cands = nullptr;
   int4* sweep = nullptr;  // pairs waiting for the penalty sweep (node pairs, then fine pairs)
+  mrdem::AccRec* acc = nullptr;     // [cap_cands] pairs accepted by the float stage
+  int* items_pt = nullptr;          // [cap_items] point-triangle work items
+  int* items_ee = nullptr;          // [cap_items] edge-edge work items
+  mrdem::ItemRes* res_pt = nullptr;  // [cap_items]
+  mrdem::ItemRes* res_ee = nullptr;  // [cap_items]
+  int64_t cap_items = 0;
   int64_t cap_level = 0, cap_tiles = 0, cap_cands = 0, cap_sweep = 0;
   mrdem::PairXf* xf = nullptr;
   mrdem::PairXf64* xf64 = nullptr;
@@ -177,6 +203,15 @@ int launch_plain(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const 
                  cudaStream_t s);
 int setup_pairs(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
                 const double* eps, const double* poses, cudaStream_t s);
+// closest-point pipeline (mrdem_closest.cu)
+int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts* out,
+                      cudaStream_t s);
+int launch_exact64_list(mrdem_ctx* c, const mrdem_hier* hier, const int* fallback,
+                        const mrdem_contacts* out, cudaStream_t s);
+int launch_grad_closest(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
+                        const double* poses, const mrdem_contacts* con, const double* mass,
+                        double k_s, double scale, float* dverts, double* dpose, double* jac,
+                        cudaStream_t s);
 int launch_forces(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
                   const double* pair_eps, const double* poses, const mrdem_contacts* c,
                   const double* mass, const double* com, double k_s, double* ft, double* energy,
