@@ -26,14 +26,16 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Floating-point operations in the finest-level kernel, counted from its source
-# as FADD + FMUL + 2 FFMA + MUFU (cross-checked with ncu's instruction
-# counters): one penalty sweep (4 iterations, convergence
-# check, certificate) and one bounding-sphere test of a fine pair.
-FLOPS_PER_SWEEP = 429           # sweep + convergence check + certificate
+# Floating-point operations per unit of work, counted from the kernels' source
+# as FADD + FMUL + 2 FFMA + MUFU (min/max and compares not counted):
+FLOPS_PER_SWEEP = 429           # one penalty sweep: 4 iterations, convergence check, certificate
 FLOPS_PER_XFORM = 54            # moving B's triangle into A's frame (27 FFMA)
+FLOPS_PER_AXIS = 108            # separating-axis test along both face normals
 FLOPS_PER_NODE_SWEEP = 398 + 54  # the surrogate sweep has no convergence check
-FLOPS_PER_SPHERE_TEST = 11
+FLOPS_PER_SPHERE_TEST = 11      # bounding-sphere test of a fine pair
+FLOPS_PER_FINE_VS_SURR = 18     # fine triangle's sphere vs a surrogate's plane and node sphere
+FLOPS_PER_TILE = 40             # per leaf pair: B's surrogate plane and sphere into A's frame
+FLOPS_PER_EXPAND_TEST = 29      # child-pair sphere test incl. moving B's centre (9 FFMA)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -143,25 +145,37 @@ class Clocks:
 
 
 def _source_hash():
+    """Hash of the library's CUDA/C++ sources (a traffic figure is valid only
+    for the source it was measured on)."""
     h = hashlib.sha256()
-    for f in ("mrdem_detect.cu", "mrdem_geometry.cuh"):
-        with open(os.path.join(ROOT, "paper_2105_12415_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    d = os.path.join(ROOT, "paper_2105_12415_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 
 def _traffic_per_launch():
-    """DRAM bytes per k_tile launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "k_tile_c2_traffic.json")
+    """DRAM bytes per launch of each kernel, from the table in the committed
+    ncu summary (rows `| kernel | bytes per full launch | source hash |`),
+    for rows measured on the current source; {} if none."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic_c2_batched.md")
+    out = {}
     try:
         with open(p) as f:
-            d = json.load(f)
+            lines = f.read().splitlines()
     except OSError:
-        return None
-    if d.get("source_hash") != _source_hash():
-        return None
-    return d.get("dram_bytes_per_full_launch")
+        return out
+    cur = _source_hash()
+    for ln in lines:
+        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cells) == 3 and cells[2] == cur:
+            try:
+                out[cells[0]] = float(cells[1])
+            except ValueError:
+                pass
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -333,7 +347,12 @@ def main():
     value = args.steps * P * world / (ms_max * 1e-3)
     st = stats.cpu().numpy()
     n_contacts = int(contacts.count.item())
-    launches_per_step = 1 + 2 * max(0, info["max_depth"] - 1) + 6
+    # our kernels per step: k_setup, (k_expand, k_sweep_nodes) per surrogate
+    # level below the roots, k_tile, k_sweep_fine, the exact pass (FP32 form:
+    # k_cp_float, 2 x k_cp_items, k_select_exact, k_exact64_idx; FP64 form:
+    # k_exact64), then k_frames + k_forces and k_frames + k_grad
+    exact_launches = 5 if args.precision == "fp32" else 1
+    launches_per_step = 1 + 2 * max(0, info["max_depth"] - 1) + 2 + exact_launches + 4
 
     # ---- per-kernel timing (same steps, outside the graph, events per kernel)
     ctx.profile(True)
@@ -344,17 +363,25 @@ def main():
     ctx.profile(False)
     prof = ctx.profile_read()
     fine_tests = int(st[m._lib.MRDEM_STAT_FINE_TESTS])
+    fine_sweeps = int(st[m._lib.MRDEM_STAT_FINE_SWEEPS])
     sphere_tests = int(st[m._lib.MRDEM_STAT_SPHERE_TESTS])
     level_sweeps = int(st[m._lib.MRDEM_STAT_LEVEL_SWEEPS])
+    tiles = int(st[m._lib.MRDEM_STAT_TILES])
+    fvs = int(st[m._lib.MRDEM_STAT_FINE_SURROGATE])
+    expand_tests = int(st[1:m._lib.MRDEM_STAT_LEVELS].sum())
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     total_prof = sum(v[0] for v in prof.values())
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                    "share": v[0] / total_prof} for k, v in prof.items()}
-    # algorithmic FP32 flops per step of the sweep kernels
-    flops = {"k_sweep_fine": fine_tests * (FLOPS_PER_SWEEP + FLOPS_PER_XFORM),
-             "k_sweep_nodes": level_sweeps * FLOPS_PER_NODE_SWEEP}
+    # algorithmic FP32 flops per step of the culling and sweep kernels
+    flops = {"k_sweep_fine": fine_tests * (FLOPS_PER_XFORM + FLOPS_PER_AXIS)
+             + fine_sweeps * FLOPS_PER_SWEEP,
+             "k_sweep_nodes": level_sweeps * FLOPS_PER_NODE_SWEEP,
+             "k_tile": tiles * FLOPS_PER_TILE + fvs * FLOPS_PER_FINE_VS_SURR
+             + sphere_tests * FLOPS_PER_SPHERE_TEST,
+             "k_expand": expand_tests * FLOPS_PER_EXPAND_TEST}
     rl = {}
     for k, f in flops.items():
         if k in prof:
@@ -362,9 +389,12 @@ def main():
             per_launch = f / (prof[k][1] / args.steps)
             ach = per_launch / avg_s / 1e12
             rl[k] = {"achieved": ach, "frac": ach / fp32_peak, "flops_per_launch": per_launch,
-                     "avg_ms": avg_s * 1e3}
+                     "avg_ms": avg_s * 1e3, "ms_per_step": prof[k][0] / args.steps}
+    # the headline is the modelled kernel with the largest time per step
+    top = max(rl, key=lambda k: rl[k]["ms_per_step"]) if rl else "k_tile"
     traffic = _traffic_per_launch()
-    fin = rl.get("k_sweep_fine", {"achieved": float("nan"), "frac": float("nan"), "avg_ms": float("nan")})
+    fin = rl.get(top, {"achieved": float("nan"), "frac": float("nan"), "avg_ms": float("nan"),
+                       "flops_per_launch": float("nan")})
 
     # ---- end to end through the public API (host inputs, host results)
     e2e = None
@@ -438,12 +468,10 @@ def main():
                    "replicas": world, "l2": "flushed between steps (256 MiB write)",
                    "step": "detect + forces + adjoint (verts, poses, 12x12 blocks)",
                    "graph": "one CUDA graph per step", "prep_s": round(prep_s, 1)},
-        "roofline": {"bound": "alu", "kernel": "k_sweep_fine", "achieved": fin["achieved"],
+        "roofline": {"bound": "alu", "kernel": top, "achieved": fin["achieved"],
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": fin["frac"],
-                     "traffic": traffic,
-                     "per_launch": {"sweeps": fine_tests,
-                                    "flops_per_sweep": FLOPS_PER_SWEEP + FLOPS_PER_XFORM,
-                                    "avg_ms": fin["avg_ms"]},
+                     "traffic": traffic.get(top),
+                     "per_launch": {"flops": fin["flops_per_launch"], "avg_ms": fin["avg_ms"]},
                      "peak_note": "152 SMs x 128 FP32 lanes x 2 x max SM clock (nominal)",
                      "all": rl},
         "clocks": clk.summary(),
@@ -453,8 +481,9 @@ def main():
                   "survivors_per_level": [int(x) for x in st[8:14]],
                   "leaf_tiles": int(st[16]), "sphere_tests": sphere_tests,
                   "level_sweeps": level_sweeps, "fine_vs_surrogate": int(st[23]),
-                  "fine_tests": fine_tests, "candidates": int(st[18]),
+                  "fine_tests": fine_tests, "fine_sweeps": fine_sweeps, "candidates": int(st[18]),
                   "unconverged": int(st[19]), "contacts": n_contacts, "fp64_refinements": int(st[21]),
+                  "fp64_items": [int(st[m._lib.MRDEM_STAT_ITEMS_PT]), int(st[m._lib.MRDEM_STAT_ITEMS_EE])],
                   "fine_tests_per_s": fine_tests * args.steps * world / (ms_max * 1e-3),
                   "brute_force_pairs_per_s": float(
                       (np.diff(scene.tri_off)[scene.pairs[:, 0]] *

@@ -27,7 +27,10 @@
  *   - stream-ordered calls (detect, forces, grad, triangle_distance) enqueue
  *     work on the given cudaStream_t (NULL = legacy default stream), never
  *     synchronise the host and can be captured into a CUDA graph, unless the
- *     call's comment says otherwise.  Their device-side failures (work-list
+ *     call's comment says otherwise.  They keep per-pair and per-particle
+ *     scratch in the context, which a call with more pairs or particles than
+ *     any earlier one on that context grows (cudaMalloc): make such a call
+ *     once before capturing.  Their device-side failures (work-list
  *     overflow, non-finite input) are latched in the context and reported by
  *     mrdem_check().
  */
@@ -62,7 +65,8 @@ typedef struct CUstream_st* mrdem_stream; /* same type as cudaStream_t */
 #define MRDEM_STAT_TESTS 0       /* [0..7]  surrogate pairs examined at unfold step l (0 = roots) */
 #define MRDEM_STAT_SURVIVORS 8   /* [8..15] of which not pruned (sphere test, then sweep) */
 #define MRDEM_STAT_TILES 16      /* leaf-pair tiles reaching the finest level */
-#define MRDEM_STAT_FINE_TESTS 17 /* fine triangle-pair sweeps (iterative tests) after the cull */
+#define MRDEM_STAT_FINE_TESTS 17 /* fine triangle pairs tested after the cull (face-normal
+                                    axes, then the iterative sweep) */
 #define MRDEM_STAT_CANDIDATES 18 /* fine pairs not pruned by the sweep's certificate */
 #define MRDEM_STAT_UNCONVERGED 19 /* candidates whose sweep had not converged (the paper's odot) */
 #define MRDEM_STAT_CONTACTS 20   /* contacts written (or that would have been written) */
@@ -74,6 +78,10 @@ typedef struct CUstream_st* mrdem_stream; /* same type as cudaStream_t */
                                           the contact buffer needed beyond its limit, 0 if none */
 #define MRDEM_STAT_NOALLOC_INVALID 26  /* mrdem_detect_noalloc only: non-zero if a pose, eps or
                                           particle index was invalid */
+#define MRDEM_STAT_FINE_SWEEPS 27 /* of the fine tests, those the face normals did not
+                                     separate, given the iterative sweep */
+#define MRDEM_STAT_ITEMS_PT 28   /* FP32 form: point-triangle sub-tests finished in FP64 */
+#define MRDEM_STAT_ITEMS_EE 29   /* FP32 form: edge-edge sub-tests finished in FP64 */
 #define MRDEM_STAT_COUNT 32
 
 typedef struct mrdem_params {
@@ -220,9 +228,11 @@ int mrdem_contact_forces(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs
                          double k_s, double* force_torque, double* energy, mrdem_stream stream);
 
 /* Adjoint of the contact energy E = sum_c e(d_c) (the energy of
- * mrdem_contact_forces), scaled by dE_scale (the upstream gradient).  The
- * closest points of each contact are recomputed in FP64 from the triangles;
- * nothing per pair is stored between detect and this call.  Outputs
+ * mrdem_contact_forces), scaled by dE_scale (the upstream gradient).  Like
+ * mrdem_contact_forces it takes each contact's dist, point_a and point_b as
+ * mrdem_detect wrote them, so `contacts` must come from a detection at these
+ * poses; the barycentric weights of the closest points (for dE_dverts) are
+ * recomputed in FP64 from the body-frame triangles.  Outputs
  * (accumulated, caller zeroes; each may be NULL):
  *   dE_dverts float [n_verts*3]  gradient w.r.t. body-frame vertex positions
  *                                (vertex numbering of the hierarchy's input)

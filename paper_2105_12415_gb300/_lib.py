@@ -35,6 +35,9 @@ MRDEM_STAT_FINE_SURROGATE = 23
 MRDEM_STAT_LEVEL_SWEEPS = 24
 MRDEM_STAT_NOALLOC_OVERFLOW = 25
 MRDEM_STAT_NOALLOC_INVALID = 26
+MRDEM_STAT_FINE_SWEEPS = 27
+MRDEM_STAT_ITEMS_PT = 28
+MRDEM_STAT_ITEMS_EE = 29
 MRDEM_STAT_COUNT = 32
 
 

@@ -169,6 +169,7 @@ int mrdem_destroy(mrdem_ctx* c) {
   free_lists(c);
   cudaFree(c->xf);
   cudaFree(c->xf64);
+  cudaFree(c->frames);
   cudaFree(c->counters);
   cudaFree(c->status);
   delete c;
@@ -250,13 +251,13 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
   int64_t stride = (h.n_tri_pad + 31) / 32 * 32;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   size_t sz_geo = al(sizeof(float4) * 3 * h.n_nodes), sz_child = al(sizeof(int2) * h.n_nodes);
-  size_t sz_sph = al(sizeof(float4) * h.n_nodes), sz_tsph = al(sizeof(float4) * stride);
+  size_t sz_sph = al(sizeof(float4) * h.n_nodes), sz_nrm = sz_sph, sz_tsph = al(sizeof(float4) * stride);
   size_t sz_tri = al(sizeof(float) * 9 * stride), sz_vid = al(sizeof(int32_t) * 3 * stride);
   size_t sz_slot = al(sizeof(int32_t) * stride), sz_ts = al(sizeof(int32_t) * h.n_tri);
   size_t sz_off = al(sizeof(int64_t) * (h.n_particles + 1));
   size_t sz_root = al(sizeof(int32_t) * h.n_particles), sz_br = al(sizeof(float) * h.n_particles);
   size_t total = sz_geo + sz_child + sz_tri + sz_vid + sz_slot + sz_ts + sz_off + sz_root + sz_br +
-                 sz_sph + sz_tsph;
+                 sz_sph + sz_nrm + sz_tsph;
   char* base = nullptr;
   if (cudaMalloc(&base, total) != cudaSuccess) {
     cudaGetLastError();
@@ -268,7 +269,7 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     size_t o_geo = 0, o_child = o_geo + sz_geo, o_tri = o_child + sz_child, o_vid = o_tri + sz_tri;
     size_t o_slot = o_vid + sz_vid, o_ts = o_slot + sz_slot, o_off = o_ts + sz_ts;
     size_t o_root = o_off + sz_off, o_br = o_root + sz_root, o_sph = o_br + sz_br;
-    size_t o_tsph = o_sph + sz_sph;
+    size_t o_nrm = o_sph + sz_sph, o_tsph = o_nrm + sz_nrm;
     float4* geo = (float4*)(p + o_geo);
     for (int64_t n = 0; n < h.n_nodes; ++n) {
       const float* t = &h.node_tri[9 * n];
@@ -291,6 +292,30 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
       }
       double r = (std::sqrt(r2) + (double)h.node_delta[n]) * (1.0 + 1e-6) + 1e-30;
       sph[n] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)r);
+    }
+    // surrogate planes: unit normal and offset in double, stored in float
+    // (a zero normal for a degenerate surrogate makes every plane test pass)
+    float4* nrm = (float4*)(p + o_nrm);
+    for (int64_t n = 0; n < h.n_nodes; ++n) {
+      const float* t = &h.node_tri[9 * n];
+      double e1[3], e2[3], nn[3];
+      for (int k = 0; k < 3; ++k) {
+        e1[k] = (double)t[3 + k] - (double)t[k];
+        e2[k] = (double)t[6 + k] - (double)t[k];
+      }
+      nn[0] = e1[1] * e2[2] - e1[2] * e2[1];
+      nn[1] = e1[2] * e2[0] - e1[0] * e2[2];
+      nn[2] = e1[0] * e2[1] - e1[1] * e2[0];
+      double l = std::sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+      double e = std::sqrt(std::max(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2],
+                                    e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]));
+      if (!(l > 1e-9 * e * e)) {
+        nrm[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      for (int k = 0; k < 3; ++k) nn[k] /= l;
+      nrm[n] = make_float4((float)nn[0], (float)nn[1], (float)nn[2],
+                           (float)(nn[0] * t[0] + nn[1] * t[1] + nn[2] * t[2]));
     }
     std::memcpy(p + o_child, h.node_child.data(), sizeof(int32_t) * 2 * h.n_nodes);
     float* tri = (float*)(p + o_tri);
@@ -337,6 +362,7 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     d.root = (const int32_t*)(base + o_root);
     d.bound_r = (const float*)(base + o_br);
     d.node_sph = (const float4*)(base + o_sph);
+    d.node_nrm = (const float4*)(base + o_nrm);
     d.tri_sph = (const float4*)(base + o_tsph);
     d.stride = stride;
     d.n_tri = h.n_tri;

@@ -146,10 +146,12 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
 // emit compact lists of surviving pairs (the buffered comparisons of
 // Sec. 5.4) and thread-per-pair sweep kernels that process those lists with
 // every lane busy:
-//   k_expand       one warp per level item: the child pairs of a surviving
-//                  node pair get a bounding-sphere test (node spheres
-//                  precomputed in the body frame, radius including delta);
-//                  survivors go to the sweep list;
+//   k_expand       the child pairs of surviving node pairs get a bounding-
+//                  sphere test (node spheres precomputed in the body frame,
+//                  radius including delta); a warp takes 32 level items and
+//                  deals their child pairs out to its lanes (near the leaves
+//                  an item often has only 2 or 4); survivors go to the sweep
+//                  list;
 //   k_sweep_nodes  one thread per listed node pair: penalty sweep + certificate
 //                  against delta_a + delta_b + 2 eps; survivors become the
 //                  next level's items, or leaf-pair tiles when both are leaves;
@@ -171,7 +173,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
                                                        int4* sweep, unsigned long long* cnt,
                                                        unsigned long long* status,
                                                        int64_t cap_level, int64_t cap_sweep) {
-  __shared__ float4 ssph[WARPS][16];
+  __shared__ int soff[WARPS][32];
+  __shared__ int4 sit[WARPS][32];
   __shared__ int4 sq[WARPS][128];
   const int w = threadIdx.x >> 5, lane = lane_id();
   int64_t n_in = (int64_t)cnt[CNT_LEVEL + level];
@@ -180,34 +183,46 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
   WarpCount tests;
   WarpQueue<int4, 128> outq;
   outq.buf = sq[w];
-  const int64_t step = (int64_t)gridDim.x * WARPS;
-  int64_t item = (int64_t)blockIdx.x * WARPS + w;
-  int4 nxt = item < n_in ? in[item] : make_int4(0, 0, 0, 0);
-  for (; item < n_in; item += step) {
+  const int64_t step = (int64_t)gridDim.x * WARPS * 32;
+  int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 32;
+  int4 nxt = base + lane < n_in ? in[base + lane] : make_int4(0, 0, 0, 0);
+  for (; base < n_in; base += step) {
+    // this warp's 32 items: child-pair counts, their offsets (exclusive scan)
     const int4 it = nxt;
-    if (item + step < n_in) nxt = in[item + step];
-    int na = it.w & 0xff, nb = (it.w >> 8) & 0xff;
-    if (lane < na) {
-      ssph[w][lane] = __ldg(H.node_sph + it.y + lane);
-    } else if (lane >= 8 && lane < 8 + nb) {
-      PairXf X;
-      load_pairxf(xf, it.x, X);
-      float4 sp = __ldg(H.node_sph + it.z + lane - 8);
-      F3 c = xf_point(X, {sp.x, sp.y, sp.z});
-      ssph[w][lane] = make_float4(c.x, c.y, c.z, sp.w + X.tau + X.margin);
-    }
+    const bool valid = base + lane < n_in;
+    if (base + step + lane < n_in) nxt = in[base + step + lane];
+    const int c = valid ? (it.w & 0xff) * ((it.w >> 8) & 0xff) : 0;
+    const int incl = warp_scan(c);
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    soff[w][lane] = incl - c;
+    sit[w][lane] = it;
     __syncwarp();
-    const int total = na * nb;
     for (int f0 = 0; f0 < total; f0 += 32) {
-      int f = f0 + lane;
-      bool act = f < total;
-      int i = act ? f / nb : 0, j = act ? f - (f / nb) * nb : 0;
-      float4 p = ssph[w][i], q = ssph[w][8 + j];
-      float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-      float lim = p.w + q.w;  // q.w carries 2 eps + margin
-      bool keep = act && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
+      const int f = f0 + lane;
+      const bool act = f < total;
+      // owner: the last item whose offset is <= f (items without child
+      // pairs share the next item's offset and are never picked)
+      int l = 0;
+#pragma unroll
+      for (int b = 16; b > 0; b >>= 1)
+        if (soff[w][l + b] <= f) l += b;
+      const int4 o = sit[w][l];
+      const int nb = (o.w >> 8) & 0xff;
+      const int r = act ? f - soff[w][l] : 0;
+      const int i = (int)(((float)r + 0.5f) * (1.0f / (float)(nb > 0 ? nb : 1)));
+      const int j = r - i * nb;
+      bool keep = false;
+      if (act) {
+        PairXf X;
+        load_pairxf(xf, o.x, X);
+        float4 p = __ldg(H.node_sph + o.y + i), q = __ldg(H.node_sph + o.z + j);
+        F3 cq = xf_point(X, {q.x, q.y, q.z});
+        float dx = p.x - cq.x, dy = p.y - cq.y, dz = p.z - cq.z;
+        float lim = p.w + q.w + X.tau + X.margin;
+        keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
+      }
       tests.add(act);
-      outq.push(keep, make_int4(it.x, it.y + i, it.z + j, 0), sweep, cnt + CNT_SWEEP, cap_sweep,
+      outq.push(keep, make_int4(o.x, o.y + i, o.z + j, 0), sweep, cnt + CNT_SWEEP, cap_sweep,
                 status + ST_REQ_SWEEP);
     }
     __syncwarp();
@@ -294,16 +309,26 @@ __device__ __forceinline__ float4 tri_sphere(F3 v0, F3 v1, F3 v2) {
   return make_float4(c.x, c.y, c.z, sqrtf(r2) * (1.f + 1e-6f));
 }
 
-// Is the sphere (c, r) within `lim` + r of the surrogate triangle (g0,g1,g2)?
-// The distance from the centre to the triangle minus r bounds the distance
-// of anything inside the sphere from below.
-__device__ __forceinline__ bool sphere_near_triangle(float4 s, F3 g0, F3 g1, F3 g2, float lim) {
-  float w[3];
-  F3 c = {s.x, s.y, s.z};
-  F3 q = closest_on_triangle(c, g0, g1, g2, w);
-  F3 d = c - q;
-  float l = lim + s.w;
-  return dot(d, d) <= l * l;
+
+// A leaf's surrogate as seen from the other particle (A's frame): the unit
+// normal and offset of its plane and its node sphere (centre, largest vertex
+// distance + delta).
+struct SurrogateBound {
+  F3 n;
+  float off;
+  float4 sph;
+};
+// Can a point of the sphere (c, r) come within delta + thr of the surrogate
+// triangle?  Two necessary conditions, both branch-free: within
+// delta + thr + r of its plane (the distance to a triangle is at least the
+// distance to its plane), and within the node radius + thr + r of the node
+// centre.  A NaN keeps the sphere.
+__device__ __forceinline__ bool sphere_near_surrogate(float4 s, const SurrogateBound& b,
+                                                      float delta, float thr) {
+  float pd = fabsf(fmaf(b.n.x, s.x, fmaf(b.n.y, s.y, fmaf(b.n.z, s.z, -b.off))));
+  float dx = s.x - b.sph.x, dy = s.y - b.sph.y, dz = s.z - b.sph.z;
+  float lim = b.sph.w + thr + s.w;
+  return !(pd > delta + thr + s.w) && !(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > lim * lim);
 }
 
 __device__ __forceinline__ TileItem load_tile(const TileItem* tiles, int64_t t) {
@@ -317,7 +342,7 @@ __device__ __forceinline__ TileItem load_tile(const TileItem* tiles, int64_t t) 
 
 
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_tile(HierDev H, const PairXf* __restrict__ xf,
+__global__ void __launch_bounds__(WARPS * 32, 4) k_tile(HierDev H, const PairXf* __restrict__ xf,
                                                      const TileItem* __restrict__ tiles,
                                                      int4* fine, unsigned long long* cnt,
                                                      unsigned long long* status, int64_t cap_tiles,
@@ -345,24 +370,32 @@ __global__ void __launch_bounds__(WARPS * 32) k_tile(HierDev H, const PairXf* __
     int na = it.counts & 0xff, nb = (it.counts >> 8) & 0xff;
     const float thr = X.tau + X.margin;
     bool keep_a = false, keep_b = false;
+    // the two leaves' surrogates as seen from the other side (A's frame)
+    const float da = __ldg(&H.node_geo[3 * it.node_a].w), db = __ldg(&H.node_geo[3 * it.node_b].w);
+    float4 nA = __ldg(H.node_nrm + it.node_a), nB = __ldg(H.node_nrm + it.node_b);
+    float4 sphA = __ldg(H.node_sph + it.node_a), sphB = __ldg(H.node_sph + it.node_b);
+    SurrogateBound bA = {{nA.x, nA.y, nA.z}, nA.w, sphA};
+    SurrogateBound bB;
+    {
+      F3 c = xf_point(X, {sphB.x, sphB.y, sphB.z});
+      bB.sph = make_float4(c.x, c.y, c.z, sphB.w);
+      // rotate the normal; the offset moves by n'.t
+      bB.n = {fmaf(X.R[0], nB.x, fmaf(X.R[1], nB.y, X.R[2] * nB.z)),
+              fmaf(X.R[3], nB.x, fmaf(X.R[4], nB.y, X.R[5] * nB.z)),
+              fmaf(X.R[6], nB.x, fmaf(X.R[7], nB.y, X.R[8] * nB.z))};
+      bB.off = nB.w + fmaf(bB.n.x, X.t[0], fmaf(bB.n.y, X.t[1], bB.n.z * X.t[2]));
+    }
     if (lane < na) {
-      float4 gb0 = __ldg(H.node_geo + 3 * it.node_b), gb1 = __ldg(H.node_geo + 3 * it.node_b + 1);
-      float4 gb2 = __ldg(H.node_geo + 3 * it.node_b + 2);
       float4 sp = __ldg(H.tri_sph + it.slot_a + lane);
       S.sa[lane] = sp;
-      keep_a = sphere_near_triangle(sp, xf_point(X, {gb0.x, gb0.y, gb0.z}),
-                                    xf_point(X, {gb1.x, gb1.y, gb1.z}),
-                                    xf_point(X, {gb2.x, gb2.y, gb2.z}), gb0.w + thr);
+      keep_a = sphere_near_surrogate(sp, bB, db, thr);
     }
     if (lane < nb) {
-      float4 ga0 = __ldg(H.node_geo + 3 * it.node_a), ga1 = __ldg(H.node_geo + 3 * it.node_a + 1);
-      float4 ga2 = __ldg(H.node_geo + 3 * it.node_a + 2);
       float4 sb = __ldg(H.tri_sph + it.slot_b + lane);
       F3 c = xf_point(X, {sb.x, sb.y, sb.z});
       float4 sp = make_float4(c.x, c.y, c.z, sb.w);
       S.sb[lane] = sp;
-      keep_b = sphere_near_triangle(sp, {ga0.x, ga0.y, ga0.z}, {ga1.x, ga1.y, ga1.z},
-                                    {ga2.x, ga2.y, ga2.z}, ga0.w + thr);
+      keep_b = sphere_near_surrogate(sp, bA, da, thr);
     }
     unsigned ma = __ballot_sync(0xffffffffu, keep_a), mb = __ballot_sync(0xffffffffu, keep_b);
     if (keep_a) S.ka[__popc(ma & ((1u << lane) - 1u))] = (unsigned char)lane;
@@ -398,48 +431,101 @@ __global__ void __launch_bounds__(WARPS * 32) k_tile(HierDev H, const PairXf* __
 }
 
 // k_sweep_fine ----------------------------------------------------------------
+// Fine pairs awaiting the sweep, per warp: A's triangle and B's (in A's
+// frame) as 18 floats, the pair entry and the thresholds.  At most 31 wait
+// between rounds and a round adds at most 32.
+constexpr int kFineWarps = 4;
+struct FineQueue {
+  float g[18][64];
+  int4 e[64];
+  float thr[64], ce2[64];
+};
+
 template <bool CONV>
-__global__ void __launch_bounds__(256) k_sweep_fine(HierDev H, const PairXf* __restrict__ xf,
-                                                    SweepConst sc, float conv_c,
-                                                    const int4* __restrict__ fine, int3* cands,
-                                                    unsigned long long* cnt,
-                                                    unsigned long long* status, int64_t cap_fine,
-                                                    int64_t cap_cands,
-                                                    const double* __restrict__ eps_d) {
+__global__ void __launch_bounds__(kFineWarps * 32) k_sweep_fine(
+    HierDev H, const PairXf* __restrict__ xf, SweepConst sc, float conv_c,
+    const int4* __restrict__ fine, int3* cands, unsigned long long* cnt, unsigned long long* status,
+    int64_t cap_fine, int64_t cap_cands, const double* __restrict__ eps_d) {
+  __shared__ FineQueue smem[kFineWarps];
+  __shared__ int3 scq[kFineWarps][64];
+  const int w = threadIdx.x >> 5, lane = lane_id();
+  FineQueue& Q = smem[w];
+  WarpQueue<int3, 64> cq;
+  cq.buf = scq[w];
   int64_t n = (int64_t)cnt[CNT_SWEEP];
   if (n > cap_fine) n = cap_fine;
-  WarpCount tests, ncand, nodot;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-    int64_t k = base + threadIdx.x;
-    bool act = k < n, s = false, cv = true;
-    int4 e = act ? fine[k] : make_int4(0, 0, 0, 0);
-    if (act) {
-      PairXf X;
-      load_pairxf(xf, e.x, X);
-      float ce = conv_c * (float)__ldg(eps_d + e.x);
-      F3 p0 = load_vertex(H, e.y, 0), p1 = load_vertex(H, e.y, 1), p2 = load_vertex(H, e.y, 2);
-      F3 q0 = xf_point(X, load_vertex(H, e.z, 0)), q1 = xf_point(X, load_vertex(H, e.z, 1));
-      F3 q2 = xf_point(X, load_vertex(H, e.z, 2));
+  WarpCount tests, nsweep, ncand, nodot;
+  int qn = 0;  // warp-uniform queue fill
+  // the sweep and its certificate for queue entry `slot` (-1: idle lane)
+  auto sweep_slot = [&](int slot) {
+    bool s = false, cv = true;
+    if (slot >= 0) {
+      F3 v[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) v[c] = {Q.g[3 * c][slot], Q.g[3 * c + 1][slot], Q.g[3 * c + 2][slot]};
       float gap;
       if (sc.n_iter == 4)
-        gap = sweep_certificate<CONV, 4>(p0, p1, p2, q0, q1, q2, sc, ce * ce, &cv, nullptr);
+        gap = sweep_certificate<CONV, 4>(v[0], v[1], v[2], v[3], v[4], v[5], sc, Q.ce2[slot], &cv, nullptr);
       else
-        gap = sweep_certificate<CONV, 0>(p0, p1, p2, q0, q1, q2, sc, ce * ce, &cv, nullptr);
-      const float thr = X.tau + X.margin;
-      // a pair the sweep's direction cannot separate may still be separated
-      // along one of the face normals (nearly parallel triangles)
-      if (!(gap > thr)) gap = fmaxf(axis_gap(cross(p1 - p0, p2 - p0), p0, p1, p2, q0, q1, q2),
-                                    axis_gap(cross(q1 - q0, q2 - q0), p0, p1, p2, q0, q1, q2));
-      s = !(gap > thr);
+        gap = sweep_certificate<CONV, 0>(v[0], v[1], v[2], v[3], v[4], v[5], sc, Q.ce2[slot], &cv, nullptr);
+      s = !(gap > Q.thr[slot]);
     }
-    tests.add(act);
+    nsweep.add(slot >= 0);
     ncand.add(s);
     if (CONV) nodot.add(s && !cv);
-    warp_append(s, make_int3(e.x, e.y, e.z), cands, cnt + CNT_CANDS, cap_cands,
-                status + ST_REQ_CANDS);
+    const int4 e = Q.e[slot >= 0 ? slot : 0];
+    cq.push(s, make_int3(e.x, e.y, e.z), cands, cnt + CNT_CANDS, cap_cands, status + ST_REQ_CANDS);
+  };
+  const int64_t step = (int64_t)gridDim.x * kFineWarps * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * kFineWarps + w) * 32; base < n; base += step) {
+    const int64_t k = base + lane;
+    const bool act = k < n;
+    bool need = false;
+    int4 e = make_int4(0, 0, 0, 0);
+    F3 p0, p1, p2, q0, q1, q2;
+    float thr = 0.f, ce = 0.f;
+    if (act) {
+      e = fine[k];
+      PairXf X;
+      load_pairxf(xf, e.x, X);
+      ce = conv_c * (float)__ldg(eps_d + e.x);
+      p0 = load_vertex(H, e.y, 0); p1 = load_vertex(H, e.y, 1); p2 = load_vertex(H, e.y, 2);
+      q0 = xf_point(X, load_vertex(H, e.z, 0)); q1 = xf_point(X, load_vertex(H, e.z, 1));
+      q2 = xf_point(X, load_vertex(H, e.z, 2));
+      thr = X.tau + X.margin;
+      // the face normals first: they separate most pairs at a tenth of the
+      // sweep's cost
+      float gap = fmaxf(axis_gap(cross(p1 - p0, p2 - p0), p0, p1, p2, q0, q1, q2),
+                        axis_gap(cross(q1 - q0, q2 - q0), p0, p1, p2, q0, q1, q2));
+      need = !(gap > thr);
+    }
+    tests.add(act);
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (need) {
+      const int slot = qn + __popc(m & ((1u << lane) - 1u));
+      const F3 v[6] = {p0, p1, p2, q0, q1, q2};
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        Q.g[3 * c][slot] = v[c].x;
+        Q.g[3 * c + 1][slot] = v[c].y;
+        Q.g[3 * c + 2][slot] = v[c].z;
+      }
+      Q.e[slot] = e;
+      Q.thr[slot] = thr;
+      Q.ce2[slot] = ce * ce;
+    }
+    qn += __popc(m);
+    __syncwarp();
+    if (qn >= 32) {
+      sweep_slot(qn - 32 + lane);
+      qn -= 32;
+      __syncwarp();
+    }
   }
+  if (qn > 0) sweep_slot(lane < qn ? lane : -1);
+  cq.flush(cands, cnt + CNT_CANDS, cap_cands, status + ST_REQ_CANDS);
   tests.flush(cnt + CNT_STATS + MRDEM_STAT_FINE_TESTS);
+  nsweep.flush(cnt + CNT_STATS + MRDEM_STAT_FINE_SWEEPS);
   ncand.flush(cnt + CNT_STATS + MRDEM_STAT_CANDIDATES);
   if (CONV) nodot.flush(cnt + CNT_STATS + MRDEM_STAT_UNCONVERGED);
 }
@@ -745,9 +831,9 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
                                       c->cap_tiles, c->cap_sweep);
     }
     {
-      int fb = one_wave(c, K_SWEEP_FINE, k_sweep_fine<true>, 256, 0);
+      int fb = one_wave(c, K_SWEEP_FINE, k_sweep_fine<true>, kFineWarps * 32, 0);
       ProfScope ps(c, K_SWEEP_FINE, s);
-      k_sweep_fine<true><<<fb, 256, 0, s>>>(H, c->xf, sc, prm.conv_c, c->sweep, c->cands,
+      k_sweep_fine<true><<<fb, kFineWarps * 32, 0, s>>>(H, c->xf, sc, prm.conv_c, c->sweep, c->cands,
                                             c->counters, c->status, c->cap_sweep, c->cap_cands,
                                             eps);
     }
@@ -764,20 +850,6 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
   if (stats)
     cudaMemcpyAsync(stats, c->counters + CNT_STATS, sizeof(int64_t) * MRDEM_STAT_COUNT,
                     cudaMemcpyDeviceToDevice, s);
-  return finish(s);
-}
-
-// Per-pair transforms only (no root test), e.g. for the adjoint.
-int setup_pairs(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
-                const double* eps, const double* poses, cudaStream_t s) {
-  int st = ensure_pairs(c, n_pairs);
-  if (st) return st;
-  if (n_pairs == 0) return MRDEM_OK;
-  SweepConst sc = sweep_const(c->params);
-  int threads = 256;
-  int blocks = (int)std::min<int64_t>((n_pairs + threads - 1) / threads, (int64_t)c->n_sms * 8);
-  k_setup<<<blocks, threads, 0, s>>>(hier->dev, (int)n_pairs, ab, eps, poses, c->xf, c->xf64, sc, 0,
-                                     nullptr, nullptr, c->counters, c->status, 0, 0);
   return finish(s);
 }
 
@@ -959,8 +1031,8 @@ extern "C" int mrdem_detect_noalloc(const mrdem_hier* hier, int64_t n_pairs,
     int tb = one_wave(c, K_TILE, k_tile<W>, W * 32, 0);
     cudaMemsetAsync(cnt + CNT_SWEEP, 0, sizeof(unsigned long long), s);
     k_tile<W><<<tb, W * 32, 0, s>>>(H, xf, tiles, sweep, cnt, status, kNaTiles, kNaSweep);
-    int fb = one_wave(c, K_SWEEP_FINE, k_sweep_fine<true>, 256, 0);
-    k_sweep_fine<true><<<fb, 256, 0, s>>>(H, xf, sc, prm.conv_c, sweep, cands, cnt, status,
+    int fb = one_wave(c, K_SWEEP_FINE, k_sweep_fine<true>, kFineWarps * 32, 0);
+    k_sweep_fine<true><<<fb, kFineWarps * 32, 0, s>>>(H, xf, sc, prm.conv_c, sweep, cands, cnt, status,
                                           kNaSweep, kNaCands, pair_eps);
     int et = prm.exact_threads;
     if (precision == MRDEM_PREC_FP64) {

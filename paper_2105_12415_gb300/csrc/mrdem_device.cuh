@@ -49,6 +49,16 @@ __device__ __forceinline__ void warp_append(bool pred, const Item& item, Item* l
   }
 }
 
+// Inclusive warp prefix sum.
+__device__ __forceinline__ int warp_scan(int v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, v, o);
+    if ((int)lane_id() >= o) v += y;
+  }
+  return v;
+}
+
 // Per-warp output queue in shared memory: items are collected with a ballot
 // per round and written out in batches, one global atomic per batch instead
 // of one per round.  All calls must be made by all 32 lanes.
@@ -112,6 +122,35 @@ struct WarpCount {
     if (lane_id() == 0 && v) atomicAdd(dst, (unsigned long long)v);
   }
 };
+
+// Per-key sums over a warp.  For every distinct key among the lanes with
+// `ok` set (the group of lanes holding that key), lane e (e < nq, in strides
+// of 32) forms term = val(e) and receives the group's sum of term(l) over its
+// lanes l through emit(key, e, sum); then, after a warp barrier, post(key)
+// runs on every lane.  Contacts of one particle pair sit mostly next to each
+// other in a contact list, so a warp holds few groups and a per-pair output
+// gets one atomic per group instead of one per contact.  Sums run in lane
+// order.
+template <typename Val, typename Emit, typename Post>
+__device__ __forceinline__ void warp_group_sums(bool ok, int key, int nq, Val val, Emit emit,
+                                                Post post) {
+  const int lane = lane_id();
+  unsigned pending = __ballot_sync(0xffffffffu, ok);
+  while (pending) {
+    const int k = __shfl_sync(0xffffffffu, key, __ffs(pending) - 1);
+    const unsigned grp = __ballot_sync(0xffffffffu, ok && key == k);
+    pending &= ~grp;
+    for (int e = lane; e < nq; e += 32) {
+      const auto term = val(e);
+      double acc = 0.0;
+      for (unsigned g = grp; g; g &= g - 1) acc += term(__ffs(g) - 1);
+      emit(k, e, acc);
+    }
+    __syncwarp();
+    post(k);
+    __syncwarp();
+  }
+}
 
 __device__ __forceinline__ F3 load_vertex(const HierDev& H, int slot, int c) {
   return {__ldg(H.tri + (3 * c + 0) * H.stride + slot), __ldg(H.tri + (3 * c + 1) * H.stride + slot),

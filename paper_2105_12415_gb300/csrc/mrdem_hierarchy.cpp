@@ -351,7 +351,8 @@ int build_particle(const mrdem_params& prm, const float* V, int nv, const int32_
       continue;
     }
     int k = prm.fanout;
-    if (n / prm.fanout < prm.leaf_min) k = std::max(2, (n + prm.leaf_max - 1) / prm.leaf_max);
+    if (n / prm.fanout < prm.leaf_min)
+      k = std::min(prm.fanout, std::max(2, (n + prm.leaf_max - 1) / prm.leaf_max));
     k = std::min(k, n);
     auto parts = balanced_kmeans(nodes[q].tris, cen, k, prm.kmeans_iters);
     int lvl = nodes[q].level;
@@ -400,7 +401,7 @@ int build_hierarchy_host(const mrdem_params& prm, int32_t n, const int64_t* vert
                          const float* verts, const int64_t* tri_off, const int32_t* tris,
                          HierHost* out) {
   if (n <= 0 || !vert_off || !verts || !tri_off || !tris) return MRDEM_ERR_INVALID;
-  if (prm.fanout < 2 || prm.leaf_max < 1 || prm.leaf_max > 32 || prm.leaf_min < 1)
+  if (prm.fanout < 2 || prm.fanout > 8 || prm.leaf_max < 1 || prm.leaf_max > 32 || prm.leaf_min < 1)
     return MRDEM_ERR_INVALID;
   if (vert_off[0] != 0 || tri_off[0] != 0) return MRDEM_ERR_INVALID;
   for (int i = 0; i < n; ++i)

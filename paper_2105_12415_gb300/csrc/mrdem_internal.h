@@ -37,6 +37,8 @@ struct HierDev {
   const float4* node_geo;  // [n_nodes*3]: (v0.xyz, delta) (v1.xyz, 0) (v2.xyz, 0)
   const float4* node_sph;  // [n_nodes]: body-frame sphere (centre, radius + delta) holding
                            // the node's surrogate eps-free environment
+  const float4* node_nrm;  // [n_nodes]: body-frame unit normal of the surrogate triangle and
+                           // its plane offset n.v0 (FP64 on the host; zero if degenerate)
   const int2* node_child;  // [n_nodes]
   const float* tri;        // 9 planes: coordinate k of slot s at tri[k*stride + s]
   const float4* tri_sph;   // [stride]: body-frame bounding sphere of each fine triangle
@@ -152,6 +154,8 @@ struct mrdem_ctx {
   mrdem::PairXf* xf = nullptr;
   mrdem::PairXf64* xf64 = nullptr;
   int64_t cap_pairs = 0;
+  double* frames = nullptr;  // [cap_frames * 16]: per particle R (9), t (3), world com (3)
+  int64_t cap_frames = 0;
   unsigned long long* counters = nullptr;  // [CNT_TOTAL]
   unsigned long long* status = nullptr;    // [ST_TOTAL]
   int occ[16] = {0};  // resident blocks per SM of each kernel (0 = not queried yet)
@@ -201,17 +205,11 @@ int launch_detect(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const
 int launch_plain(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
                  const double* pair_eps, const double* poses, const mrdem_contacts* out,
                  cudaStream_t s);
-int setup_pairs(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
-                const double* eps, const double* poses, cudaStream_t s);
 // closest-point pipeline (mrdem_closest.cu)
 int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts* out,
                       cudaStream_t s);
 int launch_exact64_list(mrdem_ctx* c, const mrdem_hier* hier, const int* fallback,
                         const mrdem_contacts* out, cudaStream_t s);
-int launch_grad_closest(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
-                        const double* poses, const mrdem_contacts* con, const double* mass,
-                        double k_s, double scale, float* dverts, double* dpose, double* jac,
-                        cudaStream_t s);
 int launch_forces(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
                   const double* pair_eps, const double* poses, const mrdem_contacts* c,
                   const double* mass, const double* com, double k_s, double* ft, double* energy,

@@ -134,3 +134,20 @@ def test_invalid_inputs():
         m.Hierarchy.build_host(s.vert_off, s.verts, s.tri_off, deg)
     with pytest.raises(m.MrdemError):
         m.Hierarchy.build_host(np.array([0]), s.verts, np.array([0]), s.tris)
+
+
+def test_fanout_bounds():
+    """A split has at most `fanout` children (<= 8) whatever leaf_min asks,
+    and a fanout above 8 is rejected."""
+    import paper_2105_12415_gb300 as m
+    s = scene_pairs([4], [2], [1.0], [0.4], [0.01], [0.0], 5, "fan")
+    with pytest.raises(m.MrdemError):
+        _host(s, fanout=9)
+    for fan, leaf_min in ((8, 64), (3, 32), (2, 1)):
+        ex = _host(s, fanout=fan, leaf_min=leaf_min).export()
+        ch = ex["node_child"]
+        inner = ch[:, 1] > 0
+        assert inner.any()
+        assert ch[inner, 1].max() <= fan
+        leaves = ch[:, 1] < 0
+        assert (-ch[leaves, 1]).max() <= 32
