@@ -3,24 +3,26 @@
 // Algorithm 5 of Noble & Weinzierl (arXiv 2105.12415) for a batch of particle
 // pairs, level-synchronous, as a fixed sequence of kernels (capturable in one
 // CUDA graph, no host synchronisation):
-//   k_setup  one thread per pair: B->A relative transform (FP64, and its
-//            float copy), then the root surrogate pair test;
-//   k_level  one warp per surviving node pair: tests all child pairs (<= 8x8)
-//            of the pair with the float penalty sweep + certificate against
-//            delta_a + delta_b + 2 eps (conservative surrogates, Definition
-//            "conservative"); survivors are compacted by warp ballot into the
-//            next level's list, or into the leaf-pair list once both sides are
-//            leaves (a side that is already a leaf stays while the other
-//            unfolds, Algorithm 5);
-//   k_tile   one warp per leaf pair, fetched dynamically: both leaves' fine
-//            triangles staged in shared memory (B transformed into A's frame),
-//            the la x lb products spread over the lanes, one fine pair per
-//            lane: the float sweep of Eq. 3/4 (fixed iteration count,
-//            Algorithm 4 top) and the certificate at 2 eps; survivors are the
-//            candidates;
-//   k_exact  one thread per candidate: the comparison-based distance of Sec. 3
-//            (Algorithm 4 bottom), FP64, or float with FP64 for the final
-//            value; contacts (d <= 2 eps) appended to the caller's buffers.
+//   k_setup        one thread per pair: B->A relative transform (FP64, and its
+//                  float copy), then the root surrogate pair test;
+//   k_expand       per surrogate level: child pairs of the surviving node
+//                  pairs, bounding-sphere cull, survivors to the sweep list;
+//   k_sweep_nodes  per surrogate level: penalty sweep + certificate against
+//                  delta_a + delta_b + 2 eps (conservative surrogates, Sec. 4);
+//                  survivors become the next level's items, or leaf-pair
+//                  tiles once both sides are leaves (a side that is already a
+//                  leaf stays while the other unfolds, Algorithm 5);
+//   k_tile         one warp per leaf pair: fine triangles against the other
+//                  leaf's surrogate, then sphere products; survivors to the
+//                  fine list;
+//   k_sweep_fine   one thread per fine pair: separation along the face
+//                  normals, then the float sweep of Eq. 3/4 (fixed iteration
+//                  count, Algorithm 4) and the certificate at 2 eps; survivors
+//                  are the candidates;
+//   exact          the comparison-based distance of Sec. 3 (Algorithm 4's
+//                  fallback) per candidate: FP64 (k_exact64), or float with
+//                  FP64 work items for the final value (mrdem_closest.cu);
+//                  contacts (d <= 2 eps) appended to the caller's buffers.
 // The pruning only discards pairs whose certified lower bound exceeds the
 // threshold, so the contact set equals the brute-force one (Lemma 1).
 #include <cuda_runtime.h>
