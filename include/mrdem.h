@@ -56,8 +56,11 @@ typedef struct CUstream_st* mrdem_stream; /* same type as cudaStream_t */
 #define MRDEM_ERR_NONFINITE (-5) /* a pose or eps was NaN/Inf, or eps <= 0 */
 
 /* arithmetic of the final distance of candidate triangle pairs */
-#define MRDEM_PREC_FP32 0 /* FP32 comparison-based distance; FP64 re-evaluation of pairs
-                             within a margin of 2 eps and of near-parallel edge pairs */
+#define MRDEM_PREC_FP32 0 /* FP32 comparison-based sub-tests with an error bound; the
+                             sub-tests within that bound of the float minimum (all of
+                             them, and the crossing tests, for crossing or nearly
+                             touching pairs) finished in double-float arithmetic (pairs
+                             of floats, about 48 significant bits) */
 #define MRDEM_PREC_FP64 1 /* FP64 comparison-based distance for every candidate */
 
 /* indices into the int64 statistics array filled by mrdem_detect */
@@ -70,7 +73,8 @@ typedef struct CUstream_st* mrdem_stream; /* same type as cudaStream_t */
 #define MRDEM_STAT_CANDIDATES 18 /* fine pairs not pruned by the sweep's certificate */
 #define MRDEM_STAT_UNCONVERGED 19 /* candidates whose sweep had not converged (the paper's odot) */
 #define MRDEM_STAT_CONTACTS 20   /* contacts written (or that would have been written) */
-#define MRDEM_STAT_FP64 21       /* candidates given the full FP64 comparison-based test */
+#define MRDEM_STAT_FP64 21       /* candidates given the full comparison-based test in extended
+                                    precision (FP32 form: crossing or nearly touching pairs) */
 #define MRDEM_STAT_SPHERE_TESTS 22 /* fine pairs given the bounding-sphere test */
 #define MRDEM_STAT_FINE_SURROGATE 23 /* fine triangles tested against the other leaf's surrogate */
 #define MRDEM_STAT_LEVEL_SWEEPS 24 /* surrogate pairs given the penalty sweep (all levels) */
@@ -80,8 +84,8 @@ typedef struct CUstream_st* mrdem_stream; /* same type as cudaStream_t */
                                           particle index was invalid */
 #define MRDEM_STAT_FINE_SWEEPS 27 /* of the fine tests, those the face normals did not
                                      separate, given the iterative sweep */
-#define MRDEM_STAT_ITEMS_PT 28   /* FP32 form: point-triangle sub-tests finished in FP64 */
-#define MRDEM_STAT_ITEMS_EE 29   /* FP32 form: edge-edge sub-tests finished in FP64 */
+#define MRDEM_STAT_ITEMS_PT 28   /* FP32 form: point-triangle sub-tests finished in double-float */
+#define MRDEM_STAT_ITEMS_EE 29   /* FP32 form: edge-edge sub-tests finished in double-float */
 #define MRDEM_STAT_COUNT 32
 
 typedef struct mrdem_params {
@@ -268,10 +272,10 @@ int mrdem_detect_plain_fp64(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pa
  *     relative to P's first vertex; FP64: as given).  feature codes: k (0..2)
  *     vertex k of P vs Q; 3+k vertex k of Q vs P; 6+3i+j edge i of P vs edge j
  *     of Q (edge i joins vertex i and i+1 mod 3); 100+i edge i of P crosses Q;
- *     103+j edge j of Q crosses P.  In the FP32 form the code is -1 for a
- *     pair decided to be within 2 eps by the float test (its value finished
- *     in double), and -2 for a pair the float test decided to be beyond
- *     2 eps (the reported distance is then the full double result).
+ *     103+j edge j of Q crosses P.  The FP32 form is the detection's: float
+ *     sub-tests, then double-float finishing; its feature code is -2 for a
+ *     pair it decides to be beyond 2 eps (the reported distance is then the
+ *     full double result).
  *   sweep_x [n*4], sweep_gap [n], sweep_conv [n]: the FP32 penalty sweep of
  *     Eq. 3/4 (ctx's constants) on the float-rounded triangles: final
  *     barycentric unknowns (a1, b1, a2, b2), the certified lower bound of the

@@ -20,7 +20,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 
 CU_SOURCES = ["mrdem_detect.cu", "mrdem_forces.cu", "mrdem_closest.cu"]
 CPP_SOURCES = ["mrdem_api.cpp", "mrdem_hierarchy.cpp"]
-HEADERS = ["mrdem_geometry.cuh", "mrdem_internal.h", "mrdem_device.cuh"]
+HEADERS = ["mrdem_geometry.cuh", "mrdem_internal.h", "mrdem_device.cuh", "mrdem_dd.cuh"]
 
 
 def _inputs():

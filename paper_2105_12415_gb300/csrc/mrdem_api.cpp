@@ -38,9 +38,11 @@ void free_lists(mrdem_ctx* c) {
   cudaFree(c->items_ee);
   cudaFree(c->res_pt);
   cudaFree(c->res_ee);
+  cudaFree(c->items_cx);
+  cudaFree(c->res_cx);
   c->acc = nullptr;
-  c->items_pt = c->items_ee = nullptr;
-  c->res_pt = c->res_ee = nullptr;
+  c->items_pt = c->items_ee = c->items_cx = nullptr;
+  c->res_pt = c->res_ee = c->res_cx = nullptr;
   c->cap_items = 0;
   c->level_list[0] = c->level_list[1] = nullptr;
   c->tiles = nullptr;
@@ -59,7 +61,9 @@ int alloc_lists(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca, int64_t sw) {
       cudaMalloc(&c->items_pt, sizeof(int) * 2 * ca) != cudaSuccess ||
       cudaMalloc(&c->items_ee, sizeof(int) * 2 * ca) != cudaSuccess ||
       cudaMalloc(&c->res_pt, sizeof(ItemRes) * 2 * ca) != cudaSuccess ||
-      cudaMalloc(&c->res_ee, sizeof(ItemRes) * 2 * ca) != cudaSuccess) {
+      cudaMalloc(&c->res_ee, sizeof(ItemRes) * 2 * ca) != cudaSuccess ||
+      cudaMalloc(&c->items_cx, sizeof(int) * 2 * ca) != cudaSuccess ||
+      cudaMalloc(&c->res_cx, sizeof(ItemRes) * 2 * ca) != cudaSuccess) {
     cudaGetLastError();
     free_lists(c);
     return MRDEM_ERR_OOM;
@@ -169,6 +173,7 @@ int mrdem_destroy(mrdem_ctx* c) {
   free_lists(c);
   cudaFree(c->xf);
   cudaFree(c->xf64);
+  cudaFree(c->xfdd);
   cudaFree(c->frames);
   cudaFree(c->counters);
   cudaFree(c->status);

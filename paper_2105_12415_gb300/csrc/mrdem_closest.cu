@@ -3,18 +3,21 @@
 //
 // Used by the FP32 form of the exact distance (Sec. 3, comparison-based
 // method, the final test of Algorithm 4).  Three steps:
-//   k_cp_float   one thread per pair: the fifteen sub-tests in float on
+//   k_cp_float   one thread per candidate: the fifteen sub-tests in float on
 //                coordinates relative to A's first vertex; a pair clearly
-//                beyond 2 eps is dropped, a crossing or nearly touching pair
-//                goes to a fallback list (full double test), and every other
-//                pair is accepted: its double geometry is stored and one work
-//                item per sub-test within 2 err of the float minimum is
-//                appended to the point-triangle or the edge-edge list;
-//   k_cp_items   one thread per work item, one list at a time, so the lanes
-//                of a warp run the same double routine;
-//   k_select_exact one thread per accepted pair: the smallest of its items
-//                is the distance (the true minimiser is always among them)
-//                and the pair's contact is written.
+//                beyond 2 eps is dropped; every other pair is accepted: its
+//                double-float geometry is stored and one work item per
+//                sub-test within 2 err of the float minimum is appended to the
+//                point-triangle or the edge-edge list; a crossing or nearly
+//                touching pair gets all fifteen sub-tests and the six
+//                edge-against-triangle crossing tests as items;
+//   k_cp_items   one thread per work item, one list (and one routine) per
+//                launch, so the lanes of a warp run the same code, in
+//                double-float arithmetic;
+//   k_select_exact one thread per accepted pair: the first crossing in the
+//                fixed order, else the smallest item, is the distance (the
+//                true minimiser is always among them); the contact is
+//                written.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,21 +45,23 @@ __device__ __forceinline__ int64_t warp_reserve(int n, unsigned long long* count
 
 __global__ void __launch_bounds__(128) k_cp_float(HierDev H, const PairXf* __restrict__ xf,
                                                   const PairXf64* __restrict__ xf64,
+                                                  const PairXfDD* __restrict__ xfdd,
                                                   const int3* __restrict__ cands,
                                                   AccRec* acc, int64_t cap_acc, int* items_pt,
-                                                  int* items_ee, int64_t cap_items,
-                                                  int* fallback, int64_t cap_fallback,
+                                                  int* items_ee, int* items_cx, int64_t cap_items,
                                                   unsigned long long* cnt,
                                                   unsigned long long* status) {
   int64_t n = (int64_t)cnt[CNT_CANDS];
   if (n > cap_acc) n = cap_acc;  // the accepted list has the candidate list's capacity
   unsigned n_pt = 0, n_ee = 0;
+  WarpCount nfull;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     int64_t k = base + threadIdx.x;
     int res = 0;
     unsigned mask = 0;
     int3 e = make_int3(0, 0, 0);
+    float L = 0.f;
     if (k < n) {
       e = cands[k];
       PairXf X;
@@ -66,9 +71,17 @@ __global__ void __launch_bounds__(128) k_cp_float(HierDev H, const PairXf* __res
       F3 Qf[3] = {xf_point(X, load_vertex(H, e.z, 0)) - a0, xf_point(X, load_vertex(H, e.z, 1)) - a0,
                   xf_point(X, load_vertex(H, e.z, 2)) - a0};
       res = cand_float_stage(Pf, Qf, (double)X.tau, X.margin, &mask);
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+        L = fmaxf(L, fmaxf(fmaxf(fabsf(Pf[v].x), fabsf(Pf[v].y)),
+                           fmaxf(fmaxf(fabsf(Pf[v].z), fabsf(Qf[v].x)), fmaxf(fabsf(Qf[v].y), fabsf(Qf[v].z)))));
     }
-    // accepted pairs: double geometry and work items
-    bool accept = res == 1;
+    // accepted pairs: double-float geometry and work items; a crossing or
+    // nearly touching pair (res < 0) takes every sub-test and the crossings
+    const bool full = res < 0;
+    if (full) mask = 0x7fffu;
+    nfull.add(full);
+    bool accept = res != 0;
     unsigned am = __ballot_sync(0xffffffffu, accept);
     unsigned long long abase = 0;
     if (am) {
@@ -83,22 +96,18 @@ __global__ void __launch_bounds__(128) k_cp_float(HierDev H, const PairXf* __res
     }
     int npt = accept ? __popc(mask & 0x3fu) : 0;
     int nee = accept ? __popc(mask >> 6) : 0;
+    int ncx = accept && full ? 6 : 0;
     int64_t pt0 = warp_reserve(npt, cnt + CNT_PT, cap_items, status + ST_REQ_CANDS);
     int64_t ee0 = warp_reserve(nee, cnt + CNT_EE, cap_items, status + ST_REQ_CANDS);
-    if (accept && (pt0 < 0 || ee0 < 0)) accept = false;
+    int64_t cx0 = warp_reserve(ncx, cnt + CNT_CX, cap_items, status + ST_REQ_CANDS);
+    if (accept && (pt0 < 0 || ee0 < 0 || cx0 < 0)) accept = false;
     n_pt += accept ? (unsigned)npt : 0u;
     n_ee += accept ? (unsigned)nee : 0u;
     if (accept) {
-      AccRec& r = acc[ai];
-      const PairXf64& X64 = xf64[e.x];
-      CandGeom g;
-      cand_geom(H, X64, e, g);
-      r.g = g;
-      r.entry = (int)k;
-      r.pair = e.x;
-      r.pt_begin = (int)pt0;
-      r.ee_begin = (int)ee0;
-      r.counts = npt | (nee << 8);
+      CandDD g;
+      cand_dd(H, xfdd[e.x], e, 2.0 * xf64[e.x].eps, L, g);
+      store_acc(acc + ai, g, (int)k, e.x, (int)pt0, (int)ee0, (int)cx0,
+                npt | (nee << 8) | (ncx << 16));
       int ip = (int)pt0, ie = (int)ee0;
       for (int f = 0; f < 15; ++f) {
         if (!((mask >> f) & 1u)) continue;
@@ -106,8 +115,8 @@ __global__ void __launch_bounds__(128) k_cp_float(HierDev H, const PairXf* __res
         if (f < 6) items_pt[ip++] = item;
         else items_ee[ie++] = item;
       }
+      for (int f = 0; f < ncx; ++f) items_cx[cx0 + f] = (int)(ai << 4) | f;
     }
-    warp_append(res < 0, (int)k, fallback, cnt + CNT_FALLBACK, cap_fallback, status + ST_REQ_CANDS);
   }
   n_pt = __reduce_add_sync(0xffffffffu, n_pt);
   n_ee = __reduce_add_sync(0xffffffffu, n_ee);
@@ -115,10 +124,13 @@ __global__ void __launch_bounds__(128) k_cp_float(HierDev H, const PairXf* __res
     if (n_pt) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_ITEMS_PT, (unsigned long long)n_pt);
     if (n_ee) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_ITEMS_EE, (unsigned long long)n_ee);
   }
+  nfull.flush(cnt + CNT_STATS + MRDEM_STAT_FP64);
 }
 
-// One sub-test in double per thread; the lanes of a warp run the same
-// routine (point-triangle or edge-edge list).
+// One work item per thread in double-float; KIND 0: point-triangle, 1:
+// edge-edge, 2: edge-against-triangle crossing (one list per launch, so the
+// lanes of a warp run one routine and the kernel holds only that code).
+template <int KIND>
 __global__ void __launch_bounds__(256) k_cp_items(const AccRec* __restrict__ acc,
                                                   const int* __restrict__ items, int count_slot,
                                                   int64_t cap_items, ItemRes* res,
@@ -128,24 +140,61 @@ __global__ void __launch_bounds__(256) k_cp_items(const AccRec* __restrict__ acc
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
     int it = items[k];
-    const CandGeom& g = acc[it >> 4].g;
-    CandGeom G = g;
-    D3 pa, pb;
-    double wa[3], wb[3];
-    double d2 = eval_subtest(G.P, G.Q, it & 15, &pa, &pb, wa, wb);
-    ItemRes& r = res[k];
-    r.d2 = d2;
-    r.pa[0] = pa.x; r.pa[1] = pa.y; r.pa[2] = pa.z;
-    r.pb[0] = pb.x; r.pb[1] = pb.y; r.pb[2] = pb.z;
-    for (int q = 0; q < 3; ++q) { r.wa[q] = wa[q]; r.wb[q] = wb[q]; }
+    V3<dd> P[3], Q[3];
+    load_cand_tris(acc + (it >> 4), P, Q);
+    const int f = it & 15;
+    V3<dd> pa, pb;
+    dd d2;
+    if (KIND == 2) {
+      // edge (i, i+1) of P through Q for f < 3, of Q through P otherwise
+      const int i = f < 3 ? f : f - 3, i1 = i == 2 ? 0 : i + 1;
+      V3<dd> s0 = f < 3 ? pick3(P, i) : pick3(Q, i), s1 = f < 3 ? pick3(P, i1) : pick3(Q, i1);
+      dd t, w[3];
+      bool cross = f < 3 ? segment_crosses(s0, s1, Q[0], Q[1], Q[2], &t, w)
+                         : segment_crosses(s0, s1, P[0], P[1], P[2], &t, w);
+      if (cross) {
+        pa = s0 + t * (s1 - s0);
+        d2 = dd(0.f, 0.f);
+      } else {
+        pa = s0;
+        d2 = dd(INFINITY);
+      }
+      pb = pa;
+    } else if (KIND == 0) {
+      // vertex f of P against Q, or vertex f - 3 of Q against P, without
+      // branches on the Voronoi region (the lanes of a warp stay together)
+      if (f < 3) {
+        pa = pick3(P, f);
+        pb = closest_on_triangle_flat(pa, Q[0], Q[1], Q[2]);
+      } else {
+        pb = pick3(Q, f - 3);
+        pa = closest_on_triangle_flat(pb, P[0], P[1], P[2]);
+      }
+      V3<dd> dv = pa - pb;
+      d2 = dot(dv, dv);
+    } else {
+      dd wa[3], wb[3];
+      d2 = eval_subtest(P, Q, f >= 6 ? f : 6, &pa, &pb, wa, wb);
+    }
+    float4* o = reinterpret_cast<float4*>(res + k);
+    o[0] = make_float4(d2.hi, d2.lo, pa.x.hi, pa.x.lo);
+    o[1] = make_float4(pa.y.hi, pa.y.lo, pa.z.hi, pa.z.lo);
+    o[2] = make_float4(pb.x.hi, pb.x.lo, pb.y.hi, pb.y.lo);
+    o[3] = make_float4(pb.z.hi, pb.z.lo, 0.f, 0.f);
   }
 }
 
-// The smallest item of an accepted pair.
+// The result of an accepted pair: its first crossing in the fixed order, else
+// the first smallest sub-test (point-triangle items before edge-edge items,
+// each in feature order), as in tri_tri_distance.
 __device__ __forceinline__ const ItemRes* best_item(const AccRec& r, const ItemRes* res_pt,
-                                                    const ItemRes* res_ee) {
+                                                    const ItemRes* res_ee, const ItemRes* res_cx) {
+  int npt = r.counts & 0xff, nee = (r.counts >> 8) & 0xff, ncx = (r.counts >> 16) & 0xff;
+  for (int q = 0; q < ncx; ++q) {
+    const ItemRes* x = res_cx + r.cx_begin + q;
+    if (x->d2.hi == 0.f) return x;
+  }
   const ItemRes* best = nullptr;
-  int npt = r.counts & 0xff, nee = (r.counts >> 8) & 0xff;
   for (int q = 0; q < npt; ++q) {
     const ItemRes* x = res_pt + r.pt_begin + q;
     if (!best || x->d2 < best->d2) best = x;
@@ -158,10 +207,11 @@ __device__ __forceinline__ const ItemRes* best_item(const AccRec& r, const ItemR
 }
 
 // Exact pass: contacts of the accepted candidates.
-__global__ void __launch_bounds__(128) k_select_exact(HierDev H, const PairXf64* __restrict__ xf64,
+__global__ void __launch_bounds__(128) k_select_exact(HierDev H, const PairXfDD* __restrict__ xfdd,
                                                       const AccRec* __restrict__ acc,
                                                       const ItemRes* __restrict__ res_pt,
                                                       const ItemRes* __restrict__ res_ee,
+                                                      const ItemRes* __restrict__ res_cx,
                                                       const int3* __restrict__ cands,
                                                       unsigned long long* cnt, int64_t cap_acc,
                                                       unsigned long long* status,
@@ -178,15 +228,15 @@ __global__ void __launch_bounds__(128) k_select_exact(HierDev H, const PairXf64*
     D3 pa = {0, 0, 0}, pb = {0, 0, 0};
     if (k < n) {
       const AccRec& r = acc[k];
-      const ItemRes* b = best_item(r, res_pt, res_ee);
+      const ItemRes* b = best_item(r, res_pt, res_ee, res_cx);
       if (b) {
-        d = sqrt(b->d2);
+        d = ldexp(to_double(dd_sqrt(b->d2)), r.g.k);
         hit = d <= r.g.tau;
         if (hit) {
           c = cands[r.entry];
-          const PairXf64& X = xf64[r.pair];
-          pa = xf_point64(X.RA, X.tA, D3{b->pa[0], b->pa[1], b->pa[2]} + r.g.o);
-          pb = xf_point64(X.RA, X.tA, D3{b->pb[0], b->pb[1], b->pb[2]} + r.g.o);
+          const PairXfDD& X = xfdd[r.pair];
+          pa = world_point(X, b->pa, r.g.k, r.g.o);
+          pb = world_point(X, b->pb, r.g.k, r.g.o);
         }
       }
     }
@@ -196,82 +246,27 @@ __global__ void __launch_bounds__(128) k_select_exact(HierDev H, const PairXf64*
   ncon.flush(cnt + CNT_STATS + MRDEM_STAT_CONTACTS);
 }
 
-// Full double test of the fallback entries (indices into the candidates).
-__global__ void __launch_bounds__(128) k_exact64_idx(HierDev H, const PairXf64* __restrict__ xf64,
-                                                     const int3* __restrict__ cands,
-                                                     const int* __restrict__ list,
-                                                     unsigned long long* cnt, int64_t cap,
-                                                     unsigned long long* status,
-                                                     mrdem_contacts out) {
-  int64_t n = (int64_t)cnt[CNT_FALLBACK];
-  if (n > cap) n = cap;
-  WarpCount ncon, nall;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-    int64_t k = base + threadIdx.x;
-    bool hit = false;
-    int3 c = make_int3(0, 0, 0);
-    double d = 0;
-    D3 pa = {0, 0, 0}, pb = {0, 0, 0};
-    if (k < n) {
-      c = cands[list[k]];
-      const PairXf64& X = xf64[c.x];
-      CandGeom g;
-      cand_geom(H, X, c, g);
-      TriTriResult<double> r = tri_tri_distance(g.P, g.Q);
-      hit = r.d <= g.tau;
-      d = r.d;
-      if (hit) {
-        pa = xf_point64(X.RA, X.tA, r.pa + g.o);
-        pb = xf_point64(X.RA, X.tA, r.pb + g.o);
-      }
-    }
-    ncon.add(hit);
-    nall.add(k < n);
-    write_contact(H, out, status, hit, c.x, c.y, c.z, d, pa, pb);
-  }
-  ncon.flush(cnt + CNT_STATS + MRDEM_STAT_CONTACTS);
-  nall.flush(cnt + CNT_STATS + MRDEM_STAT_FP64);
-}
-
 // ---------------------------------------------------------------------------
 // launchers
 
-// The float stage over the candidate list and the two double item lists.
-static int closest_float_stage(mrdem_ctx* c, const mrdem_hier* hier, int* fallback,
-                               int64_t cap_fallback, cudaStream_t s) {
-  cudaMemsetAsync(c->counters + CNT_ACC, 0, sizeof(unsigned long long) * 3, s);
-  cudaMemsetAsync(c->counters + CNT_FALLBACK, 0, sizeof(unsigned long long), s);
-  k_cp_float<<<c->n_sms * 8, 128, 0, s>>>(hier->dev, c->xf, c->xf64, c->cands, c->acc,
-                                          c->cap_cands, c->items_pt, c->items_ee, c->cap_items,
-                                          fallback, cap_fallback, c->counters, c->status);
-  int ib = c->n_sms * 8;
-  k_cp_items<<<ib, 256, 0, s>>>(c->acc, c->items_pt, CNT_PT, c->cap_items, c->res_pt, c->counters);
-  k_cp_items<<<ib, 256, 0, s>>>(c->acc, c->items_ee, CNT_EE, c->cap_items, c->res_ee, c->counters);
-  return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
-}
-
 int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts* out,
                       cudaStream_t s) {
-  int* fallback = reinterpret_cast<int*>(c->level_list[0]);  // free once the tiles are done
-  int st;
-  {
-    ProfScope ps(c, K_EXACT, s);
-    st = closest_float_stage(c, hier, fallback, c->cap_level, s);
-    if (st) return st;
-    k_select_exact<<<c->n_sms * 8, 128, 0, s>>>(hier->dev, c->xf64, c->acc, c->res_pt, c->res_ee,
-                                                 c->cands, c->counters, c->cap_cands, c->status,
-                                                 *out);
-  }
-  ProfScope ps(c, K_EXACT64, s);
-  launch_exact64_list(c, hier, fallback, out, s);
-  return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
-}
-
-int launch_exact64_list(mrdem_ctx* c, const mrdem_hier* hier, const int* fallback,
-                        const mrdem_contacts* out, cudaStream_t s) {
-  k_exact64_idx<<<c->n_sms * 4, 128, 0, s>>>(hier->dev, c->xf64, c->cands, fallback, c->counters,
-                                              c->cap_level, c->status, *out);
+  ProfScope ps(c, K_EXACT, s);
+  // accepted pairs and the three item lists start empty
+  cudaMemsetAsync(c->counters + CNT_ACC, 0, sizeof(unsigned long long) * 4, s);
+  k_cp_float<<<c->n_sms * 8, 128, 0, s>>>(hier->dev, c->xf, c->xf64, c->xfdd, c->cands, c->acc,
+                                          c->cap_cands, c->items_pt, c->items_ee, c->items_cx,
+                                          c->cap_items, c->counters, c->status);
+  int ib = c->n_sms * 8;
+  k_cp_items<0><<<ib, 256, 0, s>>>(c->acc, c->items_pt, CNT_PT, c->cap_items, c->res_pt,
+                                   c->counters);
+  k_cp_items<1><<<ib, 256, 0, s>>>(c->acc, c->items_ee, CNT_EE, c->cap_items, c->res_ee,
+                                   c->counters);
+  k_cp_items<2><<<ib, 256, 0, s>>>(c->acc, c->items_cx, CNT_CX, c->cap_items, c->res_cx,
+                                   c->counters);
+  k_select_exact<<<c->n_sms * 8, 128, 0, s>>>(hier->dev, c->xfdd, c->acc, c->res_pt, c->res_ee,
+                                               c->res_cx, c->cands, c->counters, c->cap_cands,
+                                               c->status, *out);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
 

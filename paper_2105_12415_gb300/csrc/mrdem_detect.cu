@@ -61,7 +61,8 @@ __device__ __forceinline__ int4 make_level(int pair, int node_a, int node_b, int
 // k_setup: per pair transforms + root test
 __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
                         const double* __restrict__ eps, const double* __restrict__ poses,
-                        PairXf* xf, PairXf64* xf64, SweepConst sc, int root_test, int4* list0,
+                        PairXf* xf, PairXf64* xf64, PairXfDD* xfdd, SweepConst sc,
+                        int root_test, int4* list0,
                         TileItem* tiles, unsigned long long* cnt, unsigned long long* status,
                         int64_t cap_level, int64_t cap_tiles) {
   WarpCount tests, surv;
@@ -129,6 +130,18 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
       }
       xf[p] = X;
       xf64[p] = X64;
+      if (xfdd) {
+        PairXfDD D;
+        for (int k = 0; k < 9; ++k) {
+          D.R[k] = dd(ok ? X64.R[k] : 0.0);
+          D.RA[k] = dd(ok ? X64.RA[k] : 0.0);
+        }
+        for (int k = 0; k < 3; ++k) {
+          D.t[k] = dd(ok ? X64.t[k] : 0.0);
+          D.tA[k] = dd(ok ? X64.tA[k] : 0.0);
+        }
+        xfdd[p] = D;
+      }
     }
     if (root_test) {
       tests.add(in && ok);
@@ -722,10 +735,55 @@ __global__ void k_tridist(int64_t n, const double* __restrict__ Pin, const doubl
       double d = 0;
       D3 a = {0, 0, 0}, b = {0, 0, 0};
       int f = -1;
-      int res = PREC == MRDEM_PREC_FP32 ? cand_fp32(g, d, a, b) : -1;
+      int res = -1;
+      if (PREC == MRDEM_PREC_FP32) {
+        // the detection's FP32 form: float stage, then double-float finishing
+        // of the sub-tests it keeps, or of the full test for a fallback pair
+        F3 Pf[3], Qf[3];
+        float L = 0.f;
+        for (int v = 0; v < 3; ++v) {
+          Pf[v] = {(float)g.P[v].x, (float)g.P[v].y, (float)g.P[v].z};
+          Qf[v] = {(float)g.Q[v].x, (float)g.Q[v].y, (float)g.Q[v].z};
+          L = fmaxf(L, fmaxf(fmaxf(fabsf(Pf[v].x), fabsf(Pf[v].y)),
+                             fmaxf(fmaxf(fabsf(Pf[v].z), fabsf(Qf[v].x)), fmaxf(fabsf(Qf[v].y), fabsf(Qf[v].z)))));
+        }
+        unsigned mask = 0;
+        res = cand_float_stage(Pf, Qf, g.tau, 0.f, &mask);
+        if (res != 0) {
+          const int ks = L > 0.f ? ilogbf(L) : 0;
+          const float sc2 = ldexpf(1.f, -ks);
+          V3<dd> P[3], Q[3];
+          for (int v = 0; v < 3; ++v) {
+            P[v] = scale_dd(to_dd(g.P[v]), sc2);
+            Q[v] = scale_dd(to_dd(g.Q[v]), sc2);
+          }
+          V3<dd> pa2, pb2;
+          dd best;
+          if (res == 1) {
+            best = dd(INFINITY);
+            for (int q = 0; q < 15; ++q) {
+              if (!((mask >> q) & 1u)) continue;
+              V3<dd> x, y;
+              dd wa[3], wb[3];
+              dd v2 = eval_subtest(P, Q, q, &x, &y, wa, wb);
+              if (v2 < best) { best = v2; pa2 = x; pb2 = y; f = q; }
+            }
+            d = ldexp(to_double(dd_sqrt(best)), ks);
+            if (!(d <= g.tau)) res = 0;
+          } else {
+            TriTriResult<dd> r = tri_tri_distance(P, Q);
+            d = ldexp(to_double(r.d), ks);
+            pa2 = r.pa; pb2 = r.pb; f = r.feature;
+            res = 1;
+          }
+          const float us = ldexpf(1.f, ks);
+          a = to_double(scale_dd(pa2, us));
+          b = to_double(scale_dd(pb2, us));
+        }
+      }
       if (res != 1) {
-        // FP64 form, fallback, or a pair the float test put beyond 2 eps:
-        // report the full double result (feature -2 marks the float rejection)
+        // FP64 form, or a pair the FP32 form puts beyond 2 eps: report the
+        // full double result (feature -2 marks the FP32 form's rejection)
         TriTriResult<double> r = tri_tri_distance(g.P, g.Q);
         d = r.d; a = r.pa; b = r.pb; f = res == 0 ? -2 : r.feature;
       }
@@ -747,14 +805,19 @@ static int ensure_pairs(mrdem_ctx* c, int64_t n) {
   while (cap < n) cap *= 2;
   cudaFree(c->xf);
   cudaFree(c->xf64);
+  cudaFree(c->xfdd);
   c->xf = nullptr;
   c->xf64 = nullptr;
+  c->xfdd = nullptr;
   c->cap_pairs = 0;
   if (cudaMalloc(&c->xf, sizeof(PairXf) * cap) != cudaSuccess ||
-      cudaMalloc(&c->xf64, sizeof(PairXf64) * cap) != cudaSuccess) {
+      cudaMalloc(&c->xf64, sizeof(PairXf64) * cap) != cudaSuccess ||
+      cudaMalloc(&c->xfdd, sizeof(PairXfDD) * cap) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(c->xf);
+    cudaFree(c->xf64);
     c->xf = nullptr;
+    c->xf64 = nullptr;
     return MRDEM_ERR_OOM;
   }
   c->cap_pairs = cap;
@@ -805,7 +868,8 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
     int blocks = (int)std::min<int64_t>((n_pairs + threads - 1) / threads, (int64_t)c->n_sms * 8);
     {
       ProfScope ps(c, K_SETUP, s);
-      k_setup<<<blocks, threads, 0, s>>>(H, (int)n_pairs, ab, eps, poses, c->xf, c->xf64, sc, 1,
+      k_setup<<<blocks, threads, 0, s>>>(H, (int)n_pairs, ab, eps, poses, c->xf, c->xf64, c->xfdd,
+                                         sc, 1,
                                          c->level_list[0], c->tiles, c->counters, c->status,
                                          c->cap_level, c->cap_tiles);
     }
@@ -866,7 +930,8 @@ int launch_plain(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const in
   if (n_pairs == 0) return finish(s);
   int threads = 256;
   int blocks = (int)((n_pairs + threads - 1) / threads);
-  k_setup<<<blocks, threads, 0, s>>>(H, (int)n_pairs, ab, eps, poses, c->xf, c->xf64, sc, 0,
+  k_setup<<<blocks, threads, 0, s>>>(H, (int)n_pairs, ab, eps, poses, c->xf, c->xf64, nullptr,
+                                     sc, 0,
                                      nullptr, nullptr, c->counters, c->status, 0, 0);
   std::vector<int32_t> hab(2 * n_pairs);
   if (cudaMemcpyAsync(hab.data(), ab, sizeof(int32_t) * 2 * n_pairs, cudaMemcpyDeviceToHost, s) !=
@@ -1017,7 +1082,8 @@ extern "C" int mrdem_detect_noalloc(const mrdem_hier* hier, int64_t n_pairs,
   if (n_pairs > 0) {
     int threads = 256;
     int blocks = (int)std::min<int64_t>((n_pairs + threads - 1) / threads, (int64_t)c->n_sms * 8);
-    k_setup<<<blocks, threads, 0, s>>>(H, (int)n_pairs, pair_ab, pair_eps, poses, xf, xf64, sc, 1,
+    k_setup<<<blocks, threads, 0, s>>>(H, (int)n_pairs, pair_ab, pair_eps, poses, xf, xf64, nullptr,
+                                       sc, 1,
                                        lists[0], tiles, cnt, status, kNaLevel, kNaTiles);
     int steps = std::min(hier->h.max_depth - 1, kMaxLevels - 1);
     constexpr int W = 8;

@@ -179,6 +179,88 @@ __device__ __forceinline__ void cand_geom(const HierDev& H, const PairXf64& X, i
   g.tau = 2.0 * X.eps;
 }
 
+// FP32 form: a candidate's geometry in double-float (see CandDD).  L is the
+// largest float coordinate magnitude relative to A's first vertex (from the
+// float stage), which fixes the power-of-two scale.
+__device__ __forceinline__ V3<dd> scale_dd(V3<dd> v, float s) {
+  // multiplying both words by a power of two is exact
+  return {dd(v.x.hi * s, v.x.lo * s), dd(v.y.hi * s, v.y.lo * s), dd(v.z.hi * s, v.z.lo * s)};
+}
+__device__ __forceinline__ void cand_dd(const HierDev& H, const PairXfDD& X, int3 c, double tau,
+                                        float L, CandDD& g) {
+  const int k = L > 0.f ? ilogbf(L) : 0;
+  const float s = ldexpf(1.f, -k);
+  F3 a[3] = {load_vertex(H, c.y, 0), load_vertex(H, c.y, 1), load_vertex(H, c.y, 2)};
+  g.o[0] = a[0].x; g.o[1] = a[0].y; g.o[2] = a[0].z;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    // differences of floats are exact as double-float
+    g.P[v] = scale_dd({two_sum(a[v].x, -a[0].x), two_sum(a[v].y, -a[0].y), two_sum(a[v].z, -a[0].z)}, s);
+    F3 b = load_vertex(H, c.z, v);
+    dd q[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      dd acc = X.t[r] - dd(g.o[r]);
+      acc = acc + mul_f(X.R[3 * r], b.x);
+      acc = acc + mul_f(X.R[3 * r + 1], b.y);
+      q[r] = acc + mul_f(X.R[3 * r + 2], b.z);
+    }
+    g.Q[v] = scale_dd({q[0], q[1], q[2]}, s);
+  }
+  g.k = k;
+  g.tau = tau;
+}
+// The two triangles of a candidate record as nine 16-B loads (P then Q, each
+// vertex x.hi x.lo y.hi y.lo z.hi z.lo).
+__device__ __forceinline__ void load_cand_tris(const AccRec* r, V3<dd> P[3], V3<dd> Q[3]) {
+  const float4* s = reinterpret_cast<const float4*>(r);
+  float f[36];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    float4 v = __ldg(s + q);
+    f[4 * q] = v.x; f[4 * q + 1] = v.y; f[4 * q + 2] = v.z; f[4 * q + 3] = v.w;
+  }
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    P[v] = {dd(f[6 * v], f[6 * v + 1]), dd(f[6 * v + 2], f[6 * v + 3]), dd(f[6 * v + 4], f[6 * v + 5])};
+    Q[v] = {dd(f[18 + 6 * v], f[18 + 6 * v + 1]), dd(f[18 + 6 * v + 2], f[18 + 6 * v + 3]),
+            dd(f[18 + 6 * v + 4], f[18 + 6 * v + 5])};
+  }
+}
+// Store a candidate record as twelve 16-B words.
+__device__ __forceinline__ void store_acc(AccRec* dst, const CandDD& g, int entry, int pair,
+                                          int pt_begin, int ee_begin, int cx_begin, int counts) {
+  float f[48];
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    const V3<dd>& p = g.P[v];
+    const V3<dd>& q = g.Q[v];
+    f[6 * v] = p.x.hi; f[6 * v + 1] = p.x.lo; f[6 * v + 2] = p.y.hi;
+    f[6 * v + 3] = p.y.lo; f[6 * v + 4] = p.z.hi; f[6 * v + 5] = p.z.lo;
+    f[18 + 6 * v] = q.x.hi; f[18 + 6 * v + 1] = q.x.lo; f[18 + 6 * v + 2] = q.y.hi;
+    f[18 + 6 * v + 3] = q.y.lo; f[18 + 6 * v + 4] = q.z.hi; f[18 + 6 * v + 5] = q.z.lo;
+  }
+  f[36] = g.o[0]; f[37] = g.o[1]; f[38] = g.o[2]; f[39] = __int_as_float(g.k);
+  f[40] = __int_as_float(__double2loint(g.tau)); f[41] = __int_as_float(__double2hiint(g.tau));
+  f[42] = __int_as_float(entry); f[43] = __int_as_float(pair);
+  f[44] = __int_as_float(pt_begin); f[45] = __int_as_float(ee_begin);
+  f[46] = __int_as_float(cx_begin); f[47] = __int_as_float(counts);
+  float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int q = 0; q < 12; ++q) d[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+}
+
+// World point of a candidate-frame point p (scaled by 2^-k, relative to o).
+__device__ __forceinline__ D3 world_point(const PairXfDD& X, V3<dd> p, int k, const float o[3]) {
+  V3<dd> b = scale_dd(p, ldexpf(1.f, k));
+  b = {b.x + dd(o[0]), b.y + dd(o[1]), b.z + dd(o[2])};
+  dd w[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    w[r] = X.tA[r] + X.RA[3 * r] * b.x + X.RA[3 * r + 1] * b.y + X.RA[3 * r + 2] * b.z;
+  return {to_double(w[0]), to_double(w[1]), to_double(w[2])};
+}
+
 __device__ __forceinline__ void write_contact(const HierDev& H, const mrdem_contacts& out,
                                               unsigned long long* status, bool hit, int pair,
                                               int sa, int sb, double d, D3 pa, D3 pb) {

@@ -128,6 +128,36 @@ MRDEM_HD V3<T> closest_on_triangle(V3<T> p, V3<T> a, V3<T> b, V3<T> c, T w[3]) {
   return a + v * ab + u * ac;
 }
 
+// The same closest point with the region chosen by the same tests in the same
+// order but without branches: every quantity is formed, the first region
+// whose test holds wins, and one quotient q = num / den gives the point
+// a + v ab + w ac (vertex regions: (0,0), (1,0), (0,1); edge ab: (q,0); edge
+// ac: (0,q); edge bc: (1-q,q); face: (vb q, vc q) with q = 1/(va+vb+vc)).
+// Used where the lanes of a warp evaluate different points.
+template <typename T>
+MRDEM_HD V3<T> closest_on_triangle_flat(V3<T> p, V3<T> a, V3<T> b, V3<T> c) {
+  V3<T> ab = b - a, ac = c - a, ap = p - a, bp = p - b, cp = p - c;
+  T d1 = dot(ab, ap), d2 = dot(ac, ap), d3 = dot(ab, bp), d4 = dot(ac, bp);
+  T d5 = dot(ab, cp), d6 = dot(ac, cp);
+  T vc = d1 * d4 - d3 * d2, vb = d5 * d2 - d1 * d6, va = d3 * d6 - d5 * d4;
+  T e43 = d4 - d3, e56 = d5 - d6;
+  const T zero(0), one(1);
+  int region = 6;
+  if (va <= zero && e43 >= zero && e56 >= zero) region = 5;
+  if (vb <= zero && d2 >= zero && d6 <= zero) region = 4;
+  if (d6 >= zero && d5 <= d6) region = 3;
+  if (vc <= zero && d1 >= zero && d3 <= zero) region = 2;
+  if (d3 >= zero && d4 <= d3) region = 1;
+  if (d1 <= zero && d2 <= zero) region = 0;
+  T num = region == 2 ? d1 : (region == 4 ? d2 : (region == 5 ? e43 : (region == 6 ? one : zero)));
+  T den = region == 2 ? d1 - d3
+        : (region == 4 ? d2 - d6 : (region == 5 ? e43 + e56 : (region == 6 ? va + vb + vc : one)));
+  T q = qdiv(num, den);
+  T v = region == 1 ? one : (region == 2 ? q : (region == 5 ? one - q : (region == 6 ? vb * q : zero)));
+  T w = region == 3 ? one : (region == 4 || region == 5 ? q : (region == 6 ? vc * q : zero));
+  return a + v * ab + w * ac;
+}
+
 // Closest points of segments [p1, q1] and [p2, q2]: minimise over s, then
 // clamp t and re-solve s if t left [0, 1].  Returns the parameters.
 // near_parallel is set when |d1 x d2|^2 <= 1e-6 |d1|^2 |d2|^2.

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "mrdem.h"
+#include "mrdem_dd.cuh"
 #include "mrdem_geometry.cuh"
 
 namespace mrdem {
@@ -79,18 +80,36 @@ struct alignas(16) TileItem {
 
 // A pair accepted by the float stage of the closest-point computation: its
 // double geometry and the ranges of its work items.
-struct AccRec {
-  CandGeom g;
-  int entry, pair;
-  int pt_begin, ee_begin;
-  int counts;  // point-triangle items | edge-edge items << 8
-  int pad;
+// The pair's transforms in double-float (FP32 form of the final values).
+struct alignas(16) PairXfDD {
+  dd R[9], t[3];    // B body -> A body
+  dd RA[9], tA[3];  // A body -> world
 };
-// Result of one sub-test in double: squared distance, closest points and
-// barycentric weights (A's frame, relative to the pair's origin).
-struct ItemRes {
-  double d2;
-  double pa[3], pb[3], wa[3], wb[3];
+// FP32 form: a candidate's two triangles in double-float, relative to A's
+// first vertex o (a float) and scaled by 2^-k (k from the largest
+// coordinate), so that every intermediate stays well inside the float range.
+struct CandDD {
+  V3<dd> P[3], Q[3];
+  float o[3];
+  int k;
+  double tau;  // 2 eps
+};
+// 192 B, moved as twelve 16-B words.
+struct alignas(16) AccRec {
+  CandDD g;
+  int entry, pair;
+  int pt_begin, ee_begin, cx_begin;
+  int counts;  // point-triangle items | edge-edge items << 8 | crossing items << 16
+};
+static_assert(sizeof(AccRec) == 192, "AccRec layout");
+// Result of one work item in double-float: squared distance (0 for a
+// crossing, +inf for an edge that does not cross) and closest points (A's
+// frame, relative to o, scaled like the candidate).  64 B, written as four
+// 16-B stores.
+struct alignas(16) ItemRes {
+  dd d2;
+  V3<dd> pa, pb;
+  float pad[2];
 };
 
 // Device counters (one int64 array, zeroed at the start of every detect).
@@ -99,11 +118,12 @@ enum Counter : int {
   CNT_FETCH = CNT_LEVEL + kMaxLevels + 1, // [kMaxLevels+1] dynamic work fetch per kernel
   CNT_TILES = CNT_FETCH + kMaxLevels + 2,
   CNT_CANDS,
-  CNT_FALLBACK,                           // FP32 form: candidates left for the FP64 test
+  CNT_FALLBACK,                           // one-kernel FP32 form: candidates for the full test
   CNT_SWEEP,                              // entries in the sweep list
   CNT_ACC,                                // pairs accepted by the float stage
   CNT_PT,                                 // point-triangle work items
   CNT_EE,                                 // edge-edge work items
+  CNT_CX,                                 // edge-against-triangle crossing work items
   CNT_STATS,                              // [MRDEM_STAT_COUNT] statistics
   CNT_TOTAL = CNT_STATS + MRDEM_STAT_COUNT
 };
@@ -149,10 +169,13 @@ struct mrdem_ctx {
   int* items_ee = nullptr;          // [cap_items] edge-edge work items
   mrdem::ItemRes* res_pt = nullptr;  // [cap_items]
   mrdem::ItemRes* res_ee = nullptr;  // [cap_items]
+  int* items_cx = nullptr;          // [cap_items] crossing work items
+  mrdem::ItemRes* res_cx = nullptr;  // [cap_items]
   int64_t cap_items = 0;
   int64_t cap_level = 0, cap_tiles = 0, cap_cands = 0, cap_sweep = 0;
   mrdem::PairXf* xf = nullptr;
   mrdem::PairXf64* xf64 = nullptr;
+  mrdem::PairXfDD* xfdd = nullptr;
   int64_t cap_pairs = 0;
   double* frames = nullptr;  // [cap_frames * 16]: per particle R (9), t (3), world com (3)
   int64_t cap_frames = 0;
@@ -208,8 +231,6 @@ int launch_plain(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const 
 // closest-point pipeline (mrdem_closest.cu)
 int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts* out,
                       cudaStream_t s);
-int launch_exact64_list(mrdem_ctx* c, const mrdem_hier* hier, const int* fallback,
-                        const mrdem_contacts* out, cudaStream_t s);
 int launch_forces(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
                   const double* pair_eps, const double* poses, const mrdem_contacts* c,
                   const double* mass, const double* com, double k_s, double* ft, double* energy,
