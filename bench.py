@@ -43,7 +43,7 @@ FP32_LANES_PER_SM = 128
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -91,7 +91,8 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling during the timed region: the sampler (10 ms period)
+    is running, confirmed by its first sample, before the region starts."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -100,27 +101,48 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.lines = []
+        self.t_start = None
+
+    def _read(self):
+        import time
+        for ln in self.proc.stdout:
+            if ln.strip():
+                self.raw.append((time.perf_counter(), ln))
 
     def __enter__(self):
+        import threading
+        import time
+        self.raw = []
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        t0 = time.perf_counter()
+        while not self.raw and time.perf_counter() - t0 < 10.0:
+            time.sleep(0.005)
+        self.t_start = time.perf_counter()
         return self
 
     def __exit__(self, *a):
-        self.lines = []
+        import time
+        t_end = time.perf_counter()
         if self.proc is not None:
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+                self.proc.wait()
+            self.thread.join(timeout=5)
+            # samples taken while the timed region ran
+            self.lines = [ln for t, ln in self.raw if self.t_start <= t <= t_end]
 
     def summary(self):
         sm, mx, reasons = [], None, set()

@@ -235,8 +235,9 @@ int mrdem_contact_forces(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs
  * mrdem_contact_forces), scaled by dE_scale (the upstream gradient).  Like
  * mrdem_contact_forces it takes each contact's dist, point_a and point_b as
  * mrdem_detect wrote them, so `contacts` must come from a detection at these
- * poses; the barycentric weights of the closest points (for dE_dverts) are
- * recomputed in FP64 from the body-frame triangles.  Outputs
+ * poses; the barycentric weights of the closest points (for the float
+ * output dE_dverts) are recomputed in float from the body-frame triangles and
+ * the world offsets (taken in FP64).  Outputs
  * (accumulated, caller zeroes; each may be NULL):
  *   dE_dverts float [n_verts*3]  gradient w.r.t. body-frame vertex positions
  *                                (vertex numbering of the hierarchy's input)

@@ -9,8 +9,8 @@
 // -e'(d) = |F|, so F = -dE/dt_A.  The adjoint takes each contact's distance
 // and world closest points as the detection wrote them (the forward pass
 // keeps what the backward pass needs), recomputes only the barycentric
-// weights of the closest points in FP64 from the body-frame triangles, and
-// scatters
+// weights of the closest points (in float: the vertex gradient is a float
+// output) from the body-frame triangles, and scatters
 //   dE/dv = R^T (w e'(d) (+-u))  for the six vertices,
 //   dE/dt = +-e'(d) u, dE/dtheta = (p - t) x (+-e'(d) u),
 //   jac  += e''(d) J J^T, J = [u, (pa - t_A) x u, -u, -(pb - t_B) x u].
@@ -43,29 +43,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__device__ __forceinline__ D3 mul_t(const double R[9], D3 v) {
-  return {R[0] * v.x + R[3] * v.y + R[6] * v.z, R[1] * v.x + R[4] * v.y + R[7] * v.z,
-          R[2] * v.x + R[5] * v.y + R[8] * v.z};
-}
 __device__ __forceinline__ D3 body_vertex(const HierDev& H, int slot, int c) {
   return {(double)H.tri[(3 * c) * H.stride + slot], (double)H.tri[(3 * c + 1) * H.stride + slot],
           (double)H.tri[(3 * c + 2) * H.stride + slot]};
-}
-// Barycentric weights of a point x of the triangle V (least squares in the
-// triangle's plane; a degenerate triangle puts all weight on V0).
-__device__ __forceinline__ void barycentric(const D3 V[3], D3 x, double w[3]) {
-  D3 e1 = V[1] - V[0], e2 = V[2] - V[0], r = x - V[0];
-  double d11 = dot(e1, e1), d12 = dot(e1, e2), d22 = dot(e2, e2);
-  double r1 = dot(r, e1), r2 = dot(r, e2);
-  double den = d11 * d22 - d12 * d12;
-  if (!(den > 0.0)) {
-    w[0] = 1.0; w[1] = 0.0; w[2] = 0.0;
-    return;
-  }
-  double inv = 1.0 / den;
-  w[1] = (d22 * r1 - d12 * r2) * inv;
-  w[2] = (d11 * r2 - d12 * r1) * inv;
-  w[0] = 1.0 - w[1] - w[2];
 }
 // Unit direction of a contact in the world frame: (pa - pb)/d, at d = 0
 // minus the outward unit normal of A's triangle.
@@ -77,23 +57,49 @@ __device__ __forceinline__ D3 contact_dir(const HierDev& H, double d, D3 pa, D3 
   return mul(RA, (-1.0 / sqrt(dot(n, n))) * n);
 }
 
-// Per-particle frames, once per call: R (row-major), t and the world centre
-// of mass (zero without com), 16 doubles per particle.  The contact kernels
-// read them instead of rebuilding both rotation matrices for every contact.
-constexpr int kFrame = 16;
-__global__ void __launch_bounds__(256) k_frames(int n, const double* __restrict__ poses,
-                                                const double* __restrict__ com, double* fr) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double* p = poses + 7 * (int64_t)i;
-  double R[9];
-  pose_matrix(p, R);
-  double* o = fr + kFrame * (int64_t)i;
-  for (int q = 0; q < 9; ++q) o[q] = R[q];
-  o[9] = p[0]; o[10] = p[1]; o[11] = p[2];
-  D3 c = com ? mul(R, {com[3 * i], com[3 * i + 1], com[3 * i + 2]}) : D3{0.0, 0.0, 0.0};
-  o[12] = c.x + p[0]; o[13] = c.y + p[1]; o[14] = c.z + p[2];
-  o[15] = 0.0;
+// Per-call tables built once by k_frames: per particle R (row-major), t and
+// the world centre of mass (zero without com), 16 doubles, and R again in
+// float (12 floats); per pair K_s sqrt(mu) and 1/(2 eps).  The contact
+// kernels read them instead of rebuilding rotations and dividing per contact.
+constexpr int kFrame = 16, kFrameF = 12;
+struct Tables {
+  double* fr;   // [n_particles * kFrame]
+  float* frf;   // [n_particles * kFrameF]
+  double2* pc;  // [n_pairs]
+};
+__global__ void __launch_bounds__(256) k_frames(int n, int64_t n_pairs,
+                                                const double* __restrict__ poses,
+                                                const double* __restrict__ com,
+                                                const int32_t* __restrict__ ab,
+                                                const double* __restrict__ eps,
+                                                const double* __restrict__ mass, double k_s,
+                                                Tables T) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double* p = poses + 7 * i;
+    double R[9];
+    pose_matrix(p, R);
+    double* o = T.fr + kFrame * i;
+    float* of = T.frf + kFrameF * i;
+    for (int q = 0; q < 9; ++q) {
+      o[q] = R[q];
+      of[q] = (float)R[q];
+    }
+    of[9] = of[10] = of[11] = 0.f;
+    o[9] = p[0]; o[10] = p[1]; o[11] = p[2];
+    D3 c = com ? mul(R, {com[3 * i], com[3 * i + 1], com[3 * i + 2]}) : D3{0.0, 0.0, 0.0};
+    o[12] = c.x + p[0]; o[13] = c.y + p[1]; o[14] = c.z + p[2];
+    o[15] = 0.0;
+  }
+  if (i < n_pairs) {
+    int A = ab[2 * i], B = ab[2 * i + 1];
+    double ks = 0.0;
+    if (A >= 0 && A < n && B >= 0 && B < n) {
+      const double mA = mass[A], mB = mass[B];
+      ks = k_s * sqrt(mA * mB / (mA + mB));
+    }
+    T.pc[i] = make_double2(ks, 0.5 / eps[i]);
+  }
 }
 __device__ __forceinline__ void frame_R(const double* fr, int i, double R[9]) {
   const double2* f = reinterpret_cast<const double2*>(fr + kFrame * (int64_t)i);
@@ -104,17 +110,45 @@ __device__ __forceinline__ void frame_R(const double* fr, int i, double R[9]) {
   }
   R[8] = __ldg(fr + kFrame * (int64_t)i + 8);
 }
+__device__ __forceinline__ void frame_Rf(const float* frf, int i, float R[9]) {
+  const float4* f = reinterpret_cast<const float4*>(frf + kFrameF * (int64_t)i);
+  float4 a = __ldg(f), b = __ldg(f + 1), c = __ldg(f + 2);
+  R[0] = a.x; R[1] = a.y; R[2] = a.z; R[3] = a.w; R[4] = b.x; R[5] = b.y; R[6] = b.z;
+  R[7] = b.w; R[8] = c.x;
+}
 __device__ __forceinline__ D3 frame_vec(const double* fr, int i, int at) {
   const double* f = fr + kFrame * (int64_t)i + at;
   return {__ldg(f), __ldg(f + 1), __ldg(f + 2)};
+}
+// float helpers of the vertex gradient (a float output)
+__device__ __forceinline__ F3 mul_tf(const float R[9], F3 v) {
+  return {fmaf(R[0], v.x, fmaf(R[3], v.y, R[6] * v.z)), fmaf(R[1], v.x, fmaf(R[4], v.y, R[7] * v.z)),
+          fmaf(R[2], v.x, fmaf(R[5], v.y, R[8] * v.z))};
+}
+__device__ __forceinline__ F3 to_f3(D3 v) { return {(float)v.x, (float)v.y, (float)v.z}; }
+// Barycentric weights of a point x of triangle V, in float: least squares in
+// the triangle's plane; a degenerate triangle puts all weight on V0.
+__device__ __forceinline__ void barycentric_f(const F3 V[3], F3 x, float w[3]) {
+  F3 e1 = V[1] - V[0], e2 = V[2] - V[0], r = x - V[0];
+  float d11 = dot(e1, e1), d12 = dot(e1, e2), d22 = dot(e2, e2);
+  float r1 = dot(r, e1), r2 = dot(r, e2);
+  float den = d11 * d22 - d12 * d12;
+  if (!(den > 0.f)) {
+    w[0] = 1.f; w[1] = 0.f; w[2] = 0.f;
+    return;
+  }
+  float inv = 1.f / den;
+  w[1] = (d22 * r1 - d12 * r2) * inv;
+  w[2] = (d11 * r2 - d12 * r1) * inv;
+  w[0] = 1.f - w[1] - w[2];
 }
 
 constexpr int kForceThreads = 128;
 
 __global__ void __launch_bounds__(kForceThreads) k_forces(
     HierDev H, const int32_t* __restrict__ ab, const double* __restrict__ eps, mrdem_contacts c,
-    const double* __restrict__ mass, const double* __restrict__ fr, double k_s, double* ft,
-    double* energy, int64_t n_pairs) {
+    const double2* __restrict__ pc, const double* __restrict__ fr, double* ft, double* energy,
+    int64_t n_pairs) {
   __shared__ double sF[kForceThreads / 32][32][9];  // F, (x - c_A) x F, (x - c_B) x (-F)
   double(*F9)[9] = sF[threadIdx.x >> 5];
   const int lane = lane_id();
@@ -129,8 +163,8 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(
     if (ok) {
       int A = ab[2 * p], B = ab[2 * p + 1];
       double e = eps[p], d = c.dist[k];
-      const double mA = mass[A], mB = mass[B];
-      double ks = k_s * sqrt(mA * mB / (mA + mB));
+      const double2 kc = __ldg(pc + p);  // K_s sqrt(mu), 1/(2 eps)
+      const double ks = kc.x;
       D3 pa = {c.point_a[3 * k], c.point_a[3 * k + 1], c.point_a[3 * k + 2]};
       D3 pb = {c.point_b[3 * k], c.point_b[3 * k + 1], c.point_b[3 * k + 2]};
       D3 u;
@@ -141,7 +175,7 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(
         frame_R(fr, A, RA);
         u = contact_dir(H, d, pa, pb, H.tri_slot[H.tri_off[A] + c.tri_a[k]], RA);
       }
-      double s = 1.0 - d / (2.0 * e);
+      double s = 1.0 - d * kc.y;
       D3 F = (ks * s) * u;
       e_k = ks * e * s * s;
       D3 xc = 0.5 * (pa + pb);
@@ -206,8 +240,8 @@ __device__ __forceinline__ void gram_pair(int e, int& i, int& j) {
 
 __global__ void __launch_bounds__(kGradThreads) k_grad(
     HierDev H, const int32_t* __restrict__ ab, const double* __restrict__ eps,
-    const double* __restrict__ fr, mrdem_contacts c, const double* __restrict__ mass,
-    double k_s, double scale, float* dverts, double* dpose, double* jac, int64_t n_pairs) {
+    const double* __restrict__ fr, const float* __restrict__ frf, const double2* __restrict__ pc,
+    mrdem_contacts c, double scale, float* dverts, double* dpose, double* jac, int64_t n_pairs) {
   __shared__ GradSmem smem[kGradThreads / 32];
   GradSmem& S = smem[threadIdx.x >> 5];
   const int lane = lane_id();
@@ -228,36 +262,44 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
     }
     if (ok) {
       int A = ab[2 * p], B = ab[2 * p + 1];
-      const double mA = mass[A], mB = mass[B];
-      const double ks = k_s * sqrt(mA * mB / (mA + mB));
-      const double inv2e = 0.5 / e;
+      const double2 kc = __ldg(pc + p);  // K_s sqrt(mu), 1/(2 eps)
+      const double ks = kc.x, inv2e = kc.y;
       D3 pa = {c.point_a[3 * k], c.point_a[3 * k + 1], c.point_a[3 * k + 2]};
       D3 pb = {c.point_b[3 * k], c.point_b[3 * k + 1], c.point_b[3 * k + 2]};
-      double RA[9], RB[9];
-      frame_R(fr, A, RA);
-      frame_R(fr, B, RB);
       int sa = H.tri_slot[H.tri_off[A] + c.tri_a[k]];
       int sb = H.tri_slot[H.tri_off[B] + c.tri_b[k]];
-      D3 u = contact_dir(H, d, pa, pb, sa, RA);
+      D3 u;
+      if (d > 0.0) {
+        u = (1.0 / d) * (pa - pb);
+      } else {
+        double RA[9];
+        frame_R(fr, A, RA);
+        u = contact_dir(H, d, pa, pb, sa, RA);
+      }
       D3 gv = (-ks * (1.0 - d * inv2e) * scale) * u;
       D3 ra = pa - frame_vec(fr, A, 9), rb = pb - frame_vec(fr, B, 9);
       if (dverts) {
-        // body-frame closest points and their weights; the gradient of a
-        // body-frame vertex is R^T of the world one
-        D3 VA[3] = {body_vertex(H, sa, 0), body_vertex(H, sa, 1), body_vertex(H, sa, 2)};
-        D3 VB[3] = {body_vertex(H, sb, 0), body_vertex(H, sb, 1), body_vertex(H, sb, 2)};
-        double wa[3], wb[3];
-        barycentric(VA, mul_t(RA, ra), wa);
-        barycentric(VB, mul_t(RB, rb), wb);
-        D3 gA = mul_t(RA, gv), gB = mul_t(RB, gv);
+        // a float output: body-frame closest points and their weights in
+        // float from the world offsets (differences taken in double); the
+        // gradient of a body-frame vertex is R^T of the world one
+        float RA[9], RB[9];
+        frame_Rf(frf, A, RA);
+        frame_Rf(frf, B, RB);
+        F3 VA[3] = {load_vertex(H, sa, 0), load_vertex(H, sa, 1), load_vertex(H, sa, 2)};
+        F3 VB[3] = {load_vertex(H, sb, 0), load_vertex(H, sb, 1), load_vertex(H, sb, 2)};
+        float wa[3], wb[3];
+        barycentric_f(VA, mul_tf(RA, to_f3(ra)), wa);
+        barycentric_f(VB, mul_tf(RB, to_f3(rb)), wb);
+        const F3 g = to_f3(gv);
+        const F3 gA = mul_tf(RA, g), gB = mul_tf(RB, g);
         for (int v = 0; v < 3; ++v) {
           int64_t ia = 3 * (int64_t)H.vid[v * H.stride + sa], ib = 3 * (int64_t)H.vid[v * H.stride + sb];
-          atomicAdd(dverts + ia, (float)(wa[v] * gA.x));
-          atomicAdd(dverts + ia + 1, (float)(wa[v] * gA.y));
-          atomicAdd(dverts + ia + 2, (float)(wa[v] * gA.z));
-          atomicAdd(dverts + ib, (float)(-wb[v] * gB.x));
-          atomicAdd(dverts + ib + 1, (float)(-wb[v] * gB.y));
-          atomicAdd(dverts + ib + 2, (float)(-wb[v] * gB.z));
+          atomicAdd(dverts + ia, wa[v] * gA.x);
+          atomicAdd(dverts + ia + 1, wa[v] * gA.y);
+          atomicAdd(dverts + ia + 2, wa[v] * gA.z);
+          atomicAdd(dverts + ib, -wb[v] * gB.x);
+          atomicAdd(dverts + ib + 1, -wb[v] * gB.y);
+          atomicAdd(dverts + ib + 2, -wb[v] * gB.z);
         }
       }
       D3 c1 = cross(ra, u), c2 = cross(rb, u);
@@ -319,25 +361,36 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
 
 }  // namespace
 
-static int ensure_frames(mrdem_ctx* c, int64_t n) {
-  if (n <= c->cap_frames) return MRDEM_OK;
-  cudaFree(c->frames);
-  c->frames = nullptr;
-  c->cap_frames = 0;
-  if (cudaMalloc(&c->frames, sizeof(double) * kFrame * n) != cudaSuccess) {
-    cudaGetLastError();
-    return MRDEM_ERR_OOM;
+static int ensure_tables(mrdem_ctx* c, int64_t n, int64_t n_pairs, Tables* T) {
+  // doubles: frames, then pair constants (2 each); floats after them
+  const int64_t nd = kFrame * n + 2 * n_pairs, nf = kFrameF * n;
+  const int64_t need = nd + (nf + 1) / 2;
+  if (need > c->cap_frames) {
+    cudaFree(c->frames);
+    c->frames = nullptr;
+    c->cap_frames = 0;
+    if (cudaMalloc(&c->frames, sizeof(double) * need) != cudaSuccess) {
+      cudaGetLastError();
+      return MRDEM_ERR_OOM;
+    }
+    c->cap_frames = need;
   }
-  c->cap_frames = n;
+  T->fr = c->frames;
+  T->pc = reinterpret_cast<double2*>(c->frames + kFrame * n);
+  T->frf = reinterpret_cast<float*>(c->frames + nd);
   return MRDEM_OK;
 }
 
-static int launch_frames(mrdem_ctx* c, const mrdem_hier* hier, const double* poses,
-                         const double* com, cudaStream_t s) {
+static int launch_tables(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
+                         const double* eps, const double* poses, const double* mass,
+                         const double* com, double k_s, Tables* T, cudaStream_t s) {
   int n = hier->dev.n_particles;
-  int st = ensure_frames(c, n);
+  int st = ensure_tables(c, n, n_pairs, T);
   if (st) return st;
-  if (n > 0) k_frames<<<(n + 255) / 256, 256, 0, s>>>(n, poses, com, c->frames);
+  int64_t m = std::max<int64_t>(n, n_pairs);
+  if (m > 0)
+    k_frames<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(n, n_pairs, poses, com, ab, eps, mass,
+                                                         k_s, *T);
   return MRDEM_OK;
 }
 
@@ -347,10 +400,11 @@ int launch_forces(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
                   cudaStream_t s) {
   if (!ft && !energy) return MRDEM_OK;
   ProfScope ps(c, K_FORCES, s);
-  int st = launch_frames(c, hier, poses, com, s);
+  Tables T;
+  int st = launch_tables(c, hier, n_pairs, ab, eps, poses, mass, com, k_s, &T, s);
   if (st) return st;
-  k_forces<<<c->n_sms * 16, kForceThreads, 0, s>>>(hier->dev, ab, eps, *con, mass, c->frames,
-                                                    k_s, ft, energy, n_pairs);
+  k_forces<<<c->n_sms * 16, kForceThreads, 0, s>>>(hier->dev, ab, eps, *con, T.pc, T.fr, ft,
+                                                    energy, n_pairs);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
 
@@ -361,9 +415,10 @@ int launch_grad(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int
   if (!dverts && !dpose && !jac) return MRDEM_OK;
   if (n_pairs == 0) return MRDEM_OK;
   ProfScope ps(c, K_GRAD, s);
-  int st = launch_frames(c, hier, poses, nullptr, s);
+  Tables T;
+  int st = launch_tables(c, hier, n_pairs, ab, eps, poses, mass, nullptr, k_s, &T, s);
   if (st) return st;
-  k_grad<<<c->n_sms * 16, kGradThreads, 0, s>>>(hier->dev, ab, eps, c->frames, *con, mass, k_s,
+  k_grad<<<c->n_sms * 16, kGradThreads, 0, s>>>(hier->dev, ab, eps, T.fr, T.frf, T.pc, *con,
                                                  scale, dverts, dpose, jac, n_pairs);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
