@@ -257,7 +257,7 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   size_t sz_geo = al(sizeof(float4) * 3 * h.n_nodes), sz_child = al(sizeof(int2) * h.n_nodes);
   size_t sz_sph = al(sizeof(float4) * h.n_nodes), sz_nrm = sz_sph, sz_tsph = al(sizeof(float4) * stride);
-  size_t sz_tri = al(sizeof(float) * 9 * stride), sz_vid = al(sizeof(int32_t) * 3 * stride);
+  size_t sz_tri = al(sizeof(float4) * 3 * stride), sz_vid = al(sizeof(int32_t) * 3 * stride);
   size_t sz_slot = al(sizeof(int32_t) * stride), sz_ts = al(sizeof(int32_t) * h.n_tri);
   size_t sz_off = al(sizeof(int64_t) * (h.n_particles + 1));
   size_t sz_root = al(sizeof(int32_t) * h.n_particles), sz_br = al(sizeof(float) * h.n_particles);
@@ -327,7 +327,8 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     int32_t* vid = (int32_t*)(p + o_vid);
     float4* tsph = (float4*)(p + o_tsph);
     for (int64_t s = 0; s < h.n_tri_pad; ++s) {
-      for (int k = 0; k < 9; ++k) tri[k * stride + s] = h.slot_xyz[9 * s + k];
+      for (int k = 0; k < 9; ++k) tri[12 * s + k] = h.slot_xyz[9 * s + k];
+      tri[12 * s + 9] = tri[12 * s + 10] = tri[12 * s + 11] = 0.f;
       for (int k = 0; k < 3; ++k) vid[k * stride + s] = h.slot_vid[3 * s + k];
       // bounding sphere of the triangle: centroid, largest vertex distance,
       // in double and rounded up (padding slots get an empty sphere)
@@ -359,7 +360,7 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     HierDev& d = hier->dev;
     d.node_geo = (const float4*)(base + o_geo);
     d.node_child = (const int2*)(base + o_child);
-    d.tri = (const float*)(base + o_tri);
+    d.tri = (const float4*)(base + o_tri);
     d.vid = (const int32_t*)(base + o_vid);
     d.slot_tri = (const int32_t*)(base + o_slot);
     d.tri_slot = (const int32_t*)(base + o_ts);

@@ -66,10 +66,11 @@ __global__ void __launch_bounds__(128) k_cp_float(HierDev H, const PairXf* __res
       e = cands[k];
       PairXf X;
       load_pairxf(xf, e.x, X);
-      F3 a0 = load_vertex(H, e.y, 0), a1 = load_vertex(H, e.y, 1), a2 = load_vertex(H, e.y, 2);
-      F3 Pf[3] = {{0.f, 0.f, 0.f}, a1 - a0, a2 - a0};
-      F3 Qf[3] = {xf_point(X, load_vertex(H, e.z, 0)) - a0, xf_point(X, load_vertex(H, e.z, 1)) - a0,
-                  xf_point(X, load_vertex(H, e.z, 2)) - a0};
+      F3 a[3], b[3];
+      load_tri(H, e.y, a);
+      load_tri(H, e.z, b);
+      F3 Pf[3] = {{0.f, 0.f, 0.f}, a[1] - a[0], a[2] - a[0]};
+      F3 Qf[3] = {xf_point(X, b[0]) - a[0], xf_point(X, b[1]) - a[0], xf_point(X, b[2]) - a[0]};
       res = cand_float_stage(Pf, Qf, (double)X.tau, X.margin, &mask);
 #pragma unroll
       for (int v = 0; v < 3; ++v)

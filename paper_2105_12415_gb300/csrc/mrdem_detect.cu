@@ -163,10 +163,11 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
 // every lane busy:
 //   k_expand       the child pairs of surviving node pairs get a bounding-
 //                  sphere test (node spheres precomputed in the body frame,
-//                  radius including delta); a warp takes 32 level items and
-//                  deals their child pairs out to its lanes (near the leaves
-//                  an item often has only 2 or 4); survivors go to the sweep
-//                  list;
+//                  radius including delta); a warp takes up to 32 level
+//                  items (fewer when the level is small, so that every
+//                  resident warp has work) and deals their child pairs out
+//                  to its lanes (near the leaves an item often has only 2 or
+//                  4); survivors go to the sweep list;
 //   k_sweep_nodes  one thread per listed node pair: penalty sweep + certificate
 //                  against delta_a + delta_b + 2 eps; survivors become the
 //                  next level's items, or leaf-pair tiles when both are leaves;
@@ -198,14 +199,19 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
   WarpCount tests;
   WarpQueue<int4, 128> outq;
   outq.buf = sq[w];
-  const int64_t step = (int64_t)gridDim.x * WARPS * 32;
-  int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 32;
-  int4 nxt = base + lane < n_in ? in[base + lane] : make_int4(0, 0, 0, 0);
+  // items per warp and pass: the smallest power of two that spreads the
+  // level over every resident warp (32 at most)
+  const int64_t warps = (int64_t)gridDim.x * WARPS;
+  int C = 32;
+  while (C > 1 && (int64_t)(C >> 1) * warps >= n_in) C >>= 1;
+  const int64_t step = warps * C;
+  int64_t base = ((int64_t)blockIdx.x * WARPS + w) * C;
+  int4 nxt = lane < C && base + lane < n_in ? in[base + lane] : make_int4(0, 0, 0, 0);
   for (; base < n_in; base += step) {
-    // this warp's 32 items: child-pair counts, their offsets (exclusive scan)
+    // this warp's C items: child-pair counts, their offsets (exclusive scan)
     const int4 it = nxt;
-    const bool valid = base + lane < n_in;
-    if (base + step + lane < n_in) nxt = in[base + step + lane];
+    const bool valid = lane < C && base + lane < n_in;
+    if (lane < C && base + step + lane < n_in) nxt = in[base + step + lane];
     const int c = valid ? (it.w & 0xff) * ((it.w >> 8) & 0xff) : 0;
     const int incl = warp_scan(c);
     const int total = __shfl_sync(0xffffffffu, incl, 31);
@@ -215,11 +221,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
     for (int f0 = 0; f0 < total; f0 += 32) {
       const int f = f0 + lane;
       const bool act = f < total;
-      // owner: the last item whose offset is <= f (items without child
-      // pairs share the next item's offset and are never picked)
+      // owner: the last of the C items whose offset is <= f (items without
+      // child pairs share the next item's offset and are never picked)
       int l = 0;
-#pragma unroll
-      for (int b = 16; b > 0; b >>= 1)
+      for (int b = C >> 1; b > 0; b >>= 1)
         if (soff[w][l + b] <= f) l += b;
       const int4 o = sit[w][l];
       const int nb = (o.w >> 8) & 0xff;
@@ -504,9 +509,11 @@ __global__ void __launch_bounds__(kFineWarps * 32) k_sweep_fine(
       PairXf X;
       load_pairxf(xf, e.x, X);
       ce = conv_c * (float)__ldg(eps_d + e.x);
-      p0 = load_vertex(H, e.y, 0); p1 = load_vertex(H, e.y, 1); p2 = load_vertex(H, e.y, 2);
-      q0 = xf_point(X, load_vertex(H, e.z, 0)); q1 = xf_point(X, load_vertex(H, e.z, 1));
-      q2 = xf_point(X, load_vertex(H, e.z, 2));
+      F3 a[3], b[3];
+      load_tri(H, e.y, a);
+      load_tri(H, e.z, b);
+      p0 = a[0]; p1 = a[1]; p2 = a[2];
+      q0 = xf_point(X, b[0]); q1 = xf_point(X, b[1]); q2 = xf_point(X, b[2]);
       thr = X.tau + X.margin;
       // the face normals first: they separate most pairs at a tenth of the
       // sweep's cost
@@ -582,10 +589,11 @@ __global__ void __launch_bounds__(128) k_exact32(HierDev H, const PairXf* __rest
       c = cands[k];
       PairXf X;
       load_pairxf(xf, c.x, X);
-      F3 a0 = load_vertex(H, c.y, 0), a1 = load_vertex(H, c.y, 1), a2 = load_vertex(H, c.y, 2);
-      F3 Pf[3] = {{0.f, 0.f, 0.f}, a1 - a0, a2 - a0};
-      F3 Qf[3] = {xf_point(X, load_vertex(H, c.z, 0)) - a0, xf_point(X, load_vertex(H, c.z, 1)) - a0,
-                  xf_point(X, load_vertex(H, c.z, 2)) - a0};
+      F3 a[3], b[3];
+      load_tri(H, c.y, a);
+      load_tri(H, c.z, b);
+      F3 Pf[3] = {{0.f, 0.f, 0.f}, a[1] - a[0], a[2] - a[0]};
+      F3 Qf[3] = {xf_point(X, b[0]) - a[0], xf_point(X, b[1]) - a[0], xf_point(X, b[2]) - a[0]};
       res = cand_float_stage(Pf, Qf, (double)X.tau, X.margin, &mask);
     }
     // finish the accepted pairs in double (only these lanes touch FP64)

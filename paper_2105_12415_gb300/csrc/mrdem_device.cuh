@@ -152,18 +152,20 @@ __device__ __forceinline__ void warp_group_sums(bool ok, int key, int nq, Val va
   }
 }
 
-__device__ __forceinline__ F3 load_vertex(const HierDev& H, int slot, int c) {
-  return {__ldg(H.tri + (3 * c + 0) * H.stride + slot), __ldg(H.tri + (3 * c + 1) * H.stride + slot),
-          __ldg(H.tri + (3 * c + 2) * H.stride + slot)};
+// A fine triangle's body-frame vertices: one 48-B record, three 16-B loads.
+__device__ __forceinline__ void load_tri(const HierDev& H, int slot, F3 v[3]) {
+  const float4* r = H.tri + 3 * (int64_t)slot;
+  float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+  v[0] = {a.x, a.y, a.z};
+  v[1] = {a.w, b.x, b.y};
+  v[2] = {b.z, b.w, c.x};
 }
 
 __device__ __forceinline__ void load_tri64(const HierDev& H, int slot, D3 T[3]) {
+  F3 v[3];
+  load_tri(H, slot, v);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    T[c].x = (double)__ldg(H.tri + (3 * c + 0) * H.stride + slot);
-    T[c].y = (double)__ldg(H.tri + (3 * c + 1) * H.stride + slot);
-    T[c].z = (double)__ldg(H.tri + (3 * c + 2) * H.stride + slot);
-  }
+  for (int c = 0; c < 3; ++c) T[c] = {(double)v[c].x, (double)v[c].y, (double)v[c].z};
 }
 
 __device__ __forceinline__ void cand_geom(const HierDev& H, const PairXf64& X, int3 c, CandGeom& g) {
@@ -190,13 +192,15 @@ __device__ __forceinline__ void cand_dd(const HierDev& H, const PairXfDD& X, int
                                         float L, CandDD& g) {
   const int k = L > 0.f ? ilogbf(L) : 0;
   const float s = ldexpf(1.f, -k);
-  F3 a[3] = {load_vertex(H, c.y, 0), load_vertex(H, c.y, 1), load_vertex(H, c.y, 2)};
+  F3 a[3], bq[3];
+  load_tri(H, c.y, a);
+  load_tri(H, c.z, bq);
   g.o[0] = a[0].x; g.o[1] = a[0].y; g.o[2] = a[0].z;
 #pragma unroll
   for (int v = 0; v < 3; ++v) {
     // differences of floats are exact as double-float
     g.P[v] = scale_dd({two_sum(a[v].x, -a[0].x), two_sum(a[v].y, -a[0].y), two_sum(a[v].z, -a[0].z)}, s);
-    F3 b = load_vertex(H, c.z, v);
+    const F3 b = bq[v];
     dd q[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {

@@ -43,16 +43,14 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__device__ __forceinline__ D3 body_vertex(const HierDev& H, int slot, int c) {
-  return {(double)H.tri[(3 * c) * H.stride + slot], (double)H.tri[(3 * c + 1) * H.stride + slot],
-          (double)H.tri[(3 * c + 2) * H.stride + slot]};
-}
+
 // Unit direction of a contact in the world frame: (pa - pb)/d, at d = 0
 // minus the outward unit normal of A's triangle.
 __device__ __forceinline__ D3 contact_dir(const HierDev& H, double d, D3 pa, D3 pb, int slot_a,
                                           const double RA[9]) {
   if (d > 0.0) return (1.0 / d) * (pa - pb);
-  D3 V[3] = {body_vertex(H, slot_a, 0), body_vertex(H, slot_a, 1), body_vertex(H, slot_a, 2)};
+  D3 V[3];
+  load_tri64(H, slot_a, V);
   D3 n = cross(V[1] - V[0], V[2] - V[0]);
   return mul(RA, (-1.0 / sqrt(dot(n, n))) * n);
 }
@@ -285,8 +283,9 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
         float RA[9], RB[9];
         frame_Rf(frf, A, RA);
         frame_Rf(frf, B, RB);
-        F3 VA[3] = {load_vertex(H, sa, 0), load_vertex(H, sa, 1), load_vertex(H, sa, 2)};
-        F3 VB[3] = {load_vertex(H, sb, 0), load_vertex(H, sb, 1), load_vertex(H, sb, 2)};
+        F3 VA[3], VB[3];
+        load_tri(H, sa, VA);
+        load_tri(H, sb, VB);
         float wa[3], wb[3];
         barycentric_f(VA, mul_tf(RA, to_f3(ra)), wa);
         barycentric_f(VB, mul_tf(RB, to_f3(rb)), wb);

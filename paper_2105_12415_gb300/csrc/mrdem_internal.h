@@ -41,7 +41,8 @@ struct HierDev {
   const float4* node_nrm;  // [n_nodes]: body-frame unit normal of the surrogate triangle and
                            // its plane offset n.v0 (FP64 on the host; zero if degenerate)
   const int2* node_child;  // [n_nodes]
-  const float* tri;        // 9 planes: coordinate k of slot s at tri[k*stride + s]
+  const float4* tri;       // [stride*3]: slot s's vertices as one 48-B record,
+                           // (v0.xyz v1.x) (v1.yz v2.xy) (v2.z 0 0 0)
   const float4* tri_sph;   // [stride]: body-frame bounding sphere of each fine triangle
   const int32_t* vid;      // 3 planes: global vertex index of corner k of slot s
   const int32_t* slot_tri; // [stride] local input triangle index (-1 pad)
