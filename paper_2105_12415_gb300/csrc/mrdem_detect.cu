@@ -872,8 +872,9 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
   cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * CNT_TOTAL, s);
   cudaMemsetAsync(out->count, 0, sizeof(int64_t), s);
   if (n_pairs > 0) {
-    int threads = 256;
-    int blocks = (int)std::min<int64_t>((n_pairs + threads - 1) / threads, (int64_t)c->n_sms * 8);
+    // one warp per block: the FP64 setup work spreads over every SM
+    int threads = 32;
+    int blocks = (int)std::min<int64_t>((n_pairs + threads - 1) / threads, (int64_t)c->n_sms * 64);
     {
       ProfScope ps(c, K_SETUP, s);
       k_setup<<<blocks, threads, 0, s>>>(H, (int)n_pairs, ab, eps, poses, c->xf, c->xf64, c->xfdd,
@@ -936,7 +937,7 @@ int launch_plain(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const in
   SweepConst sc = sweep_const(c->params);
   cudaMemsetAsync(out->count, 0, sizeof(int64_t), s);
   if (n_pairs == 0) return finish(s);
-  int threads = 256;
+  int threads = 32;
   int blocks = (int)((n_pairs + threads - 1) / threads);
   k_setup<<<blocks, threads, 0, s>>>(H, (int)n_pairs, ab, eps, poses, c->xf, c->xf64, nullptr,
                                      sc, 0,
@@ -954,9 +955,10 @@ int launch_plain(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const in
     if (A < 0 || B < 0 || A >= hier->h.n_particles || B >= hier->h.n_particles) continue;
     int64_t na = to[A + 1] - to[A], nb = to[B + 1] - to[B];
     int64_t total = na * nb;
-    int64_t blocks2 = std::min<int64_t>((total + threads - 1) / threads, (int64_t)c->n_sms * 64);
+    const int pt = 256;
+    int64_t blocks2 = std::min<int64_t>((total + pt - 1) / pt, (int64_t)c->n_sms * 64);
     ProfScope ps(c, K_PLAIN, s);
-    k_plain<<<(int)blocks2, threads, 0, s>>>(H, c->xf64, (int)p, na, nb, c->status, *out);
+    k_plain<<<(int)blocks2, pt, 0, s>>>(H, c->xf64, (int)p, na, nb, c->status, *out);
   }
   return finish(s);
 }
@@ -1088,8 +1090,8 @@ extern "C" int mrdem_detect_noalloc(const mrdem_hier* hier, int64_t n_pairs,
   cudaMemsetAsync(status, 0, sizeof(unsigned long long) * ST_TOTAL, s);
   cudaMemsetAsync(out->count, 0, sizeof(int64_t), s);
   if (n_pairs > 0) {
-    int threads = 256;
-    int blocks = (int)std::min<int64_t>((n_pairs + threads - 1) / threads, (int64_t)c->n_sms * 8);
+    int threads = 32;
+    int blocks = (int)std::min<int64_t>((n_pairs + threads - 1) / threads, (int64_t)c->n_sms * 64);
     k_setup<<<blocks, threads, 0, s>>>(H, (int)n_pairs, pair_ab, pair_eps, poses, xf, xf64, nullptr,
                                        sc, 1,
                                        lists[0], tiles, cnt, status, kNaLevel, kNaTiles);

@@ -65,7 +65,7 @@ struct Tables {
   float* frf;   // [n_particles * kFrameF]
   double2* pc;  // [n_pairs]
 };
-__global__ void __launch_bounds__(256) k_frames(int n, int64_t n_pairs,
+__global__ void __launch_bounds__(64) k_frames(int n, int64_t n_pairs,
                                                 const double* __restrict__ poses,
                                                 const double* __restrict__ com,
                                                 const int32_t* __restrict__ ab,
@@ -388,8 +388,8 @@ static int launch_tables(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, 
   if (st) return st;
   int64_t m = std::max<int64_t>(n, n_pairs);
   if (m > 0)
-    k_frames<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(n, n_pairs, poses, com, ab, eps, mass,
-                                                         k_s, *T);
+    k_frames<<<(unsigned)((m + 63) / 64), 64, 0, s>>>(n, n_pairs, poses, com, ab, eps, mass, k_s,
+                                                       *T);
   return MRDEM_OK;
 }
 
