@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
 }
 
 // k_sweep_nodes ---------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_sweep_nodes(HierDev H, const PairXf* __restrict__ xf,
+__global__ void __launch_bounds__(256, 4) k_sweep_nodes(HierDev H, const PairXf* __restrict__ xf,
                                                      SweepConst sc, const int4* __restrict__ sweep,
                                                      int level, int4* out, TileItem* tiles,
                                                      unsigned long long* cnt,
