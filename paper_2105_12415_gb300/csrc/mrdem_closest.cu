@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(128) k_cp_float(HierDev H, const PairXf* __res
                                                   int* items_ee, int* items_cx, int64_t cap_items,
                                                   unsigned long long* cnt,
                                                   unsigned long long* status) {
+  wait_prior_grid();
   int64_t n = (int64_t)cnt[CNT_CANDS];
   if (n > cap_acc) n = cap_acc;  // the accepted list has the candidate list's capacity
   unsigned n_pt = 0, n_ee = 0;
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(256) k_cp_items(const AccRec* __restrict__ acc
                                                   const int* __restrict__ items, int count_slot,
                                                   int64_t cap_items, ItemRes* res,
                                                   const unsigned long long* cnt) {
+  wait_prior_grid();
   int64_t n = (int64_t)cnt[count_slot];
   if (n > cap_items) n = cap_items;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -217,6 +219,7 @@ __global__ void __launch_bounds__(128) k_select_exact(HierDev H, const PairXfDD*
                                                       unsigned long long* cnt, int64_t cap_acc,
                                                       unsigned long long* status,
                                                       mrdem_contacts out) {
+  wait_prior_grid();
   int64_t n = (int64_t)cnt[CNT_ACC];
   if (n > cap_acc) n = cap_acc;
   WarpCount ncon;
@@ -253,21 +256,19 @@ __global__ void __launch_bounds__(128) k_select_exact(HierDev H, const PairXfDD*
 int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts* out,
                       cudaStream_t s) {
   ProfScope ps(c, K_EXACT, s);
-  // accepted pairs and the three item lists start empty
-  cudaMemsetAsync(c->counters + CNT_ACC, 0, sizeof(unsigned long long) * 4, s);
-  k_cp_float<<<c->n_sms * 8, 128, 0, s>>>(hier->dev, c->xf, c->xf64, c->xfdd, c->cands, c->acc,
-                                          c->cap_cands, c->items_pt, c->items_ee, c->items_cx,
-                                          c->cap_items, c->counters, c->status);
+  // the accepted pairs and the three item lists start empty (counters zeroed by detect)
+  launch_after(k_cp_float, c->n_sms * 8, 128, 0, s, hier->dev, c->xf, c->xf64, c->xfdd, c->cands,
+               c->acc, c->cap_cands, c->items_pt, c->items_ee, c->items_cx, c->cap_items,
+               c->counters, c->status);
   int ib = c->n_sms * 8;
-  k_cp_items<0><<<ib, 256, 0, s>>>(c->acc, c->items_pt, CNT_PT, c->cap_items, c->res_pt,
-                                   c->counters);
-  k_cp_items<1><<<ib, 256, 0, s>>>(c->acc, c->items_ee, CNT_EE, c->cap_items, c->res_ee,
-                                   c->counters);
-  k_cp_items<2><<<ib, 256, 0, s>>>(c->acc, c->items_cx, CNT_CX, c->cap_items, c->res_cx,
-                                   c->counters);
-  k_select_exact<<<c->n_sms * 8, 128, 0, s>>>(hier->dev, c->xfdd, c->acc, c->res_pt, c->res_ee,
-                                               c->res_cx, c->cands, c->counters, c->cap_cands,
-                                               c->status, *out);
+  launch_after(k_cp_items<0>, ib, 256, 0, s, c->acc, c->items_pt, (int)CNT_PT, c->cap_items,
+               c->res_pt, c->counters);
+  launch_after(k_cp_items<1>, ib, 256, 0, s, c->acc, c->items_ee, (int)CNT_EE, c->cap_items,
+               c->res_ee, c->counters);
+  launch_after(k_cp_items<2>, ib, 256, 0, s, c->acc, c->items_cx, (int)CNT_CX, c->cap_items,
+               c->res_cx, c->counters);
+  launch_after(k_select_exact, c->n_sms * 8, 128, 0, s, hier->dev, c->xfdd, c->acc, c->res_pt,
+               c->res_ee, c->res_cx, c->cands, c->counters, c->cap_cands, c->status, *out);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
 

@@ -65,6 +65,7 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
                         int root_test, int4* list0,
                         TileItem* tiles, unsigned long long* cnt, unsigned long long* status,
                         int64_t cap_level, int64_t cap_tiles) {
+  wait_prior_grid();
   WarpCount tests, surv;
   int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x; base < n_pairs; base += stride) {
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
                                                        int4* sweep, unsigned long long* cnt,
                                                        unsigned long long* status,
                                                        int64_t cap_level, int64_t cap_sweep) {
+  wait_prior_grid();
   __shared__ int soff[WARPS][32];
   __shared__ int4 sit[WARPS][32];
   __shared__ int4 sq[WARPS][128];
@@ -242,12 +244,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
         keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
       }
       tests.add(act);
-      outq.push(keep, make_int4(o.x, o.y + i, o.z + j, 0), sweep, cnt + CNT_SWEEP, cap_sweep,
+      outq.push(keep, make_int4(o.x, o.y + i, o.z + j, 0), sweep, cnt + CNT_SWEEP + level, cap_sweep,
                 status + ST_REQ_SWEEP);
     }
     __syncwarp();
   }
-  outq.flush(sweep, cnt + CNT_SWEEP, cap_sweep, status + ST_REQ_SWEEP);
+  outq.flush(sweep, cnt + CNT_SWEEP + level, cap_sweep, status + ST_REQ_SWEEP);
   tests.flush(cnt + CNT_STATS + slot_tests);
 }
 
@@ -258,7 +260,8 @@ __global__ void __launch_bounds__(256, 4) k_sweep_nodes(HierDev H, const PairXf*
                                                      unsigned long long* cnt,
                                                      unsigned long long* status, int64_t cap_sweep,
                                                      int64_t cap_level, int64_t cap_tiles) {
-  int64_t n = (int64_t)cnt[CNT_SWEEP];
+  wait_prior_grid();
+  int64_t n = (int64_t)cnt[CNT_SWEEP + level];
   if (n > cap_sweep) n = cap_sweep;
   const int slot_surv = MRDEM_STAT_SURVIVORS + (level + 1 < MRDEM_STAT_LEVELS ? level + 1 : MRDEM_STAT_LEVELS - 1);
   WarpCount nsweep, surv;
@@ -367,6 +370,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_tile(HierDev H, const PairXf*
                                                      int4* fine, unsigned long long* cnt,
                                                      unsigned long long* status, int64_t cap_tiles,
                                                      int64_t cap_fine) {
+  wait_prior_grid();
   __shared__ TileSmem smem[WARPS];
   __shared__ int4 sq[WARPS][128];
   const int w = threadIdx.x >> 5, lane = lane_id();
@@ -436,13 +440,13 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_tile(HierDev H, const PairXf*
       float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
       float lim = (p.w + r.w) + thr;
       bool keep = act && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
-      q.push(keep, make_int4(it.pair, it.slot_a + i, it.slot_b + j, 0), fine, cnt + CNT_SWEEP,
+      q.push(keep, make_int4(it.pair, it.slot_a + i, it.slot_b + j, 0), fine, cnt + CNT_FINE,
              cap_fine, status + ST_REQ_SWEEP);
     }
     spheres.v += lane == 0 ? (unsigned)total : 0u;
     __syncwarp();
   }
-  q.flush(fine, cnt + CNT_SWEEP, cap_fine, status + ST_REQ_SWEEP);
+  q.flush(fine, cnt + CNT_FINE, cap_fine, status + ST_REQ_SWEEP);
   if (lane == 0) {
     if (ntile) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_TILES, (unsigned long long)ntile);
     if (nfvs) atomicAdd(cnt + CNT_STATS + MRDEM_STAT_FINE_SURROGATE, (unsigned long long)nfvs);
@@ -466,13 +470,14 @@ __global__ void __launch_bounds__(kFineWarps * 32) k_sweep_fine(
     HierDev H, const PairXf* __restrict__ xf, SweepConst sc, float conv_c,
     const int4* __restrict__ fine, int3* cands, unsigned long long* cnt, unsigned long long* status,
     int64_t cap_fine, int64_t cap_cands, const double* __restrict__ eps_d) {
+  wait_prior_grid();
   __shared__ FineQueue smem[kFineWarps];
   __shared__ int3 scq[kFineWarps][64];
   const int w = threadIdx.x >> 5, lane = lane_id();
   FineQueue& Q = smem[w];
   WarpQueue<int3, 64> cq;
   cq.buf = scq[w];
-  int64_t n = (int64_t)cnt[CNT_SWEEP];
+  int64_t n = (int64_t)cnt[CNT_FINE];
   if (n > cap_fine) n = cap_fine;
   WarpCount tests, nsweep, ncand, nodot;
   int qn = 0;  // warp-uniform queue fill
@@ -623,6 +628,7 @@ __global__ void __launch_bounds__(128) k_exact64(HierDev H, const PairXf64* __re
                                                  unsigned long long* cnt, int count_slot,
                                                  int64_t cap, unsigned long long* status,
                                                  int stat_slot, mrdem_contacts out) {
+  wait_prior_grid();
   int64_t n = (int64_t)cnt[count_slot];
   if (n > cap) n = cap;
   WarpCount ncon, nall;
@@ -888,35 +894,32 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
       {
         int eb = one_wave(c, K_LEVEL, k_expand<W>, W * 32, 0);
         ProfScope ps(c, K_LEVEL, s);
-        cudaMemsetAsync(c->counters + CNT_SWEEP, 0, sizeof(unsigned long long), s);
-        k_expand<W><<<eb, W * 32, 0, s>>>(H, c->xf, c->level_list[l & 1], l, c->sweep,
-                                          c->counters, c->status, c->cap_level, c->cap_sweep);
+        launch_after(k_expand<W>, eb, W * 32, 0, s, H, c->xf, c->level_list[l & 1], l, c->sweep,
+                     c->counters, c->status, c->cap_level, c->cap_sweep);
       }
       int nb = one_wave(c, K_SWEEP_NODES, k_sweep_nodes, 256, 0);
       ProfScope ps(c, K_SWEEP_NODES, s);
-      k_sweep_nodes<<<nb, 256, 0, s>>>(H, c->xf, sc, c->sweep, l, c->level_list[(l + 1) & 1],
-                                       c->tiles, c->counters, c->status, c->cap_sweep,
-                                       c->cap_level, c->cap_tiles);
+      launch_after(k_sweep_nodes, nb, 256, 0, s, H, c->xf, sc, c->sweep, l,
+                   c->level_list[(l + 1) & 1], c->tiles, c->counters, c->status, c->cap_sweep,
+                   c->cap_level, c->cap_tiles);
     }
     {
       int tb = one_wave(c, K_TILE, k_tile<W>, W * 32, 0);
       ProfScope ps(c, K_TILE, s);
-      cudaMemsetAsync(c->counters + CNT_SWEEP, 0, sizeof(unsigned long long), s);
-      k_tile<W><<<tb, W * 32, 0, s>>>(H, c->xf, c->tiles, c->sweep, c->counters, c->status,
-                                      c->cap_tiles, c->cap_sweep);
+      launch_after(k_tile<W>, tb, W * 32, 0, s, H, c->xf, c->tiles, c->sweep, c->counters,
+                   c->status, c->cap_tiles, c->cap_sweep);
     }
     {
       int fb = one_wave(c, K_SWEEP_FINE, k_sweep_fine<true>, kFineWarps * 32, 0);
       ProfScope ps(c, K_SWEEP_FINE, s);
-      k_sweep_fine<true><<<fb, kFineWarps * 32, 0, s>>>(H, c->xf, sc, prm.conv_c, c->sweep, c->cands,
-                                            c->counters, c->status, c->cap_sweep, c->cap_cands,
-                                            eps);
+      launch_after(k_sweep_fine<true>, fb, kFineWarps * 32, 0, s, H, c->xf, sc, prm.conv_c,
+                   c->sweep, c->cands, c->counters, c->status, c->cap_sweep, c->cap_cands, eps);
     }
     int et = prm.exact_threads;
     if (precision == MRDEM_PREC_FP64) {
       ProfScope ps(c, K_EXACT, s);
-      k_exact64<<<c->n_sms * 8, et, 0, s>>>(H, c->xf64, c->cands, c->counters, CNT_CANDS,
-                                             c->cap_cands, c->status, MRDEM_STAT_FP64, *out);
+      launch_after(k_exact64, c->n_sms * 8, et, 0, s, H, c->xf64, c->cands, c->counters,
+                   (int)CNT_CANDS, c->cap_cands, c->status, (int)MRDEM_STAT_FP64, *out);
     } else {
       int r = launch_exact_fp32(c, hier, out, s);
       if (r) return r;
@@ -1099,7 +1102,6 @@ extern "C" int mrdem_detect_noalloc(const mrdem_hier* hier, int64_t n_pairs,
     constexpr int W = 8;
     for (int l = 0; l < steps; ++l) {
       int eb = one_wave(c, K_LEVEL, k_expand<W>, W * 32, 0);
-      cudaMemsetAsync(cnt + CNT_SWEEP, 0, sizeof(unsigned long long), s);
       k_expand<W><<<eb, W * 32, 0, s>>>(H, xf, lists[l & 1], l, sweep, cnt, status, kNaLevel,
                                         kNaSweep);
       int nb = one_wave(c, K_SWEEP_NODES, k_sweep_nodes, 256, 0);
@@ -1107,7 +1109,6 @@ extern "C" int mrdem_detect_noalloc(const mrdem_hier* hier, int64_t n_pairs,
                                        status, kNaSweep, kNaLevel, kNaTiles);
     }
     int tb = one_wave(c, K_TILE, k_tile<W>, W * 32, 0);
-    cudaMemsetAsync(cnt + CNT_SWEEP, 0, sizeof(unsigned long long), s);
     k_tile<W><<<tb, W * 32, 0, s>>>(H, xf, tiles, sweep, cnt, status, kNaTiles, kNaSweep);
     int fb = one_wave(c, K_SWEEP_FINE, k_sweep_fine<true>, kFineWarps * 32, 0);
     k_sweep_fine<true><<<fb, kFineWarps * 32, 0, s>>>(H, xf, sc, prm.conv_c, sweep, cands, cnt, status,

@@ -1,8 +1,10 @@
 // mrdem_device.cuh -- device helpers shared by the kernels: lane utilities,
 // warp-aggregated list appends and output queues, statistics counters, the
-// pair transforms and the loads of triangles from the structure-of-arrays
-// slots.
+// pair transforms, the loads of the fine triangles' 48-B records and the
+// double-float candidate geometry.
 #pragma once
+
+#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -47,6 +49,29 @@ __device__ __forceinline__ void warp_append(bool pred, const Item& item, Item* l
     if ((int64_t)idx < cap) list[idx] = item;
     else atomicMax(req, idx + 1);
   }
+}
+
+// Programmatic dependent launch: a kernel started with launch_after may be
+// scheduled while the previous kernel of the stream drains; it waits in
+// wait_prior_grid(), its first statement, until that kernel has completed
+// and its writes are visible, so the stream order of the work is kept and
+// only launch latency and the previous kernel's tail overlap.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... Exp, typename... Act>
+inline cudaError_t launch_after(void (*kernel)(Exp...), dim3 grid, dim3 block, size_t smem,
+                                cudaStream_t s, Act&&... args) {
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Act>(args)...);
 }
 
 // Inclusive warp prefix sum.

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(64) k_frames(int n, int64_t n_pairs,
                                                 const double* __restrict__ eps,
                                                 const double* __restrict__ mass, double k_s,
                                                 Tables T) {
+  wait_prior_grid();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     const double* p = poses + 7 * i;
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(
     HierDev H, const int32_t* __restrict__ ab, const double* __restrict__ eps, mrdem_contacts c,
     const double2* __restrict__ pc, const double* __restrict__ fr, double* ft, double* energy,
     int64_t n_pairs) {
+  wait_prior_grid();
   __shared__ double sF[kForceThreads / 32][32][9];  // F, (x - c_A) x F, (x - c_B) x (-F)
   double(*F9)[9] = sF[threadIdx.x >> 5];
   const int lane = lane_id();
@@ -240,6 +242,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
     HierDev H, const int32_t* __restrict__ ab, const double* __restrict__ eps,
     const double* __restrict__ fr, const float* __restrict__ frf, const double2* __restrict__ pc,
     mrdem_contacts c, double scale, float* dverts, double* dpose, double* jac, int64_t n_pairs) {
+  wait_prior_grid();
   __shared__ GradSmem smem[kGradThreads / 32];
   GradSmem& S = smem[threadIdx.x >> 5];
   const int lane = lane_id();
@@ -402,8 +405,8 @@ int launch_forces(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
   Tables T;
   int st = launch_tables(c, hier, n_pairs, ab, eps, poses, mass, com, k_s, &T, s);
   if (st) return st;
-  k_forces<<<c->n_sms * 16, kForceThreads, 0, s>>>(hier->dev, ab, eps, *con, T.pc, T.fr, ft,
-                                                    energy, n_pairs);
+  launch_after(k_forces, c->n_sms * 16, kForceThreads, 0, s, hier->dev, ab, eps, *con,
+               (const double2*)T.pc, (const double*)T.fr, ft, energy, n_pairs);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
 
@@ -417,8 +420,9 @@ int launch_grad(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int
   Tables T;
   int st = launch_tables(c, hier, n_pairs, ab, eps, poses, mass, nullptr, k_s, &T, s);
   if (st) return st;
-  k_grad<<<c->n_sms * 16, kGradThreads, 0, s>>>(hier->dev, ab, eps, T.fr, T.frf, T.pc, *con,
-                                                 scale, dverts, dpose, jac, n_pairs);
+  launch_after(k_grad, c->n_sms * 16, kGradThreads, 0, s, hier->dev, ab, eps, (const double*)T.fr,
+               (const float*)T.frf, (const double2*)T.pc, *con, scale, dverts, dpose, jac,
+               n_pairs);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
 

@@ -120,7 +120,9 @@ enum Counter : int {
   CNT_TILES = CNT_FETCH + kMaxLevels + 2,
   CNT_CANDS,
   CNT_FALLBACK,                           // one-kernel FP32 form: candidates for the full test
-  CNT_SWEEP,                              // entries in the sweep list
+  CNT_SWEEP,                              // [kMaxLevels] entries in level l's sweep list
+  CNT_FINE = CNT_SWEEP + kMaxLevels,      // entries in the fine list (all zeroed with the
+                                          // rest, so no reset between the kernels)
   CNT_ACC,                                // pairs accepted by the float stage
   CNT_PT,                                 // point-triangle work items
   CNT_EE,                                 // edge-edge work items

@@ -51,6 +51,29 @@ def test_tiny_and_mixed_scenes(gctx, orc, precision):
         compare_contacts(got, ref, s, precision)
 
 
+def _scaled(scene, k):
+    """The scene with geometry, positions and eps multiplied by k."""
+    import dataclasses
+    poses = scene.poses.copy()
+    poses[:, :3] *= k
+    return dataclasses.replace(scene, verts=(scene.verts * np.float32(k)).astype(np.float32),
+                               poses=poses, eps=scene.eps * k, radius=scene.radius * k,
+                               com=scene.com * k, name=f"{scene.name}-x{k:g}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("k", [1e-5, 1e5])
+def test_scaled_scenes(gctx, orc, precision, k):
+    """Scaling geometry, positions and eps by k scales every distance: the
+    contact set matches the oracle's at any scale (the FP32 form's
+    double-float finishing scales each candidate by a power of two)."""
+    s = _scaled(scene_tiny(n_pairs=16, levels=(1, 2)), k)
+    ref = orc.detect(s)
+    assert len(ref["d"]) > 0
+    got, _, _ = _run(gctx, s, precision)
+    compare_contacts(got, ref, s, precision)
+
+
 def test_plain_fp64_form_and_lemma1(gctx, orc):
     """The plain form (all pairs, FP64) equals the oracle, and the hierarchy's
     result equals the plain form's (Lemma 1)."""
