@@ -311,14 +311,16 @@ def main():
     def step():
         s = _stream(None)
         cs = contacts.struct()
-        m._lib.check(lib.mrdem_detect(ctx.handle, hier.handle, P, _p(prob.pairs), _p(prob.eps),
-                                      _p(prob.poses), m.api.PRECISION[args.precision],
-                                      C.byref(cs), _p(stats), s), "detect")
+        # the accumulated outputs are zeroed first, so that detect, forces and
+        # the adjoint follow each other directly in the stream
         ft.zero_()
         energy.zero_()
         gv.zero_()
         gp.zero_()
         jac.zero_()
+        m._lib.check(lib.mrdem_detect(ctx.handle, hier.handle, P, _p(prob.pairs), _p(prob.eps),
+                                      _p(prob.poses), m.api.PRECISION[args.precision],
+                                      C.byref(cs), _p(stats), s), "detect")
         m._lib.check(lib.mrdem_contact_forces(ctx.handle, hier.handle, P, _p(prob.pairs),
                                               _p(prob.eps), _p(prob.poses), C.byref(cs),
                                               _p(prob.mass), _p(prob.com), 1000.0, _p(ft),

@@ -391,8 +391,8 @@ static int launch_tables(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, 
   if (st) return st;
   int64_t m = std::max<int64_t>(n, n_pairs);
   if (m > 0)
-    k_frames<<<(unsigned)((m + 63) / 64), 64, 0, s>>>(n, n_pairs, poses, com, ab, eps, mass, k_s,
-                                                       *T);
+    launch_after(k_frames, (unsigned)((m + 63) / 64), 64, 0, s, n, n_pairs, poses, com, ab, eps,
+                 mass, k_s, *T);
   return MRDEM_OK;
 }
 
