@@ -440,13 +440,12 @@ def main():
             prob.poses.copy_(h_poses, non_blocking=True)
             prob.pairs.copy_(h_pairs, non_blocking=True)
             prob.eps.copy_(h_eps, non_blocking=True)
-            prob.detect(stats=stats)            # checked call: syncs and reads the status
-            f_, e_ = prob.forces()
-            _, gp_, _ = prob.grad(want_jac=True)
+            # one public call: detect + forces + adjoint, status checked once
+            c_, f_, e_, _, gp_, _, _ = prob.step(want_jac=True)
             h_ft.copy_(f_, non_blocking=True)
             h_gp.copy_(gp_, non_blocking=True)
             h_e.copy_(e_, non_blocking=True)
-            h_n.copy_(prob.contacts.count, non_blocking=True)
+            h_n.copy_(c_.count, non_blocking=True)
             b.record()
             b.synchronize()
             e_ms += a.elapsed_time(b)

@@ -358,6 +358,101 @@ class ContactProblem:
         return contact_grad(self.ctx, self.hier, self.pairs, self.eps, self.poses, self.contacts,
                             self.mass, self.k_s, scale, want_jac=want_jac, stream=stream)
 
+    # ---- one step of the batch: detection, forces and energy, adjoint
+    def _outputs(self, want_verts, want_pose, want_jac):
+        info = self.hier.info()
+        n, P, d = info["n_particles"], self.pairs.shape[0], self.pairs.device
+        o = getattr(self, "_out", None)
+        if o is None:
+            o = self._out = dict(
+                ft=torch.zeros((n, 6), dtype=torch.float64, device=d),
+                energy=torch.zeros(1, dtype=torch.float64, device=d),
+                gv=torch.zeros((info["n_verts"], 3), dtype=torch.float32, device=d),
+                gp=torch.zeros((n, 6), dtype=torch.float64, device=d),
+                jac=torch.zeros((P, 12, 12), dtype=torch.float64, device=d),
+                stats=torch.zeros(L.MRDEM_STAT_COUNT, dtype=torch.int64, device=d))
+        if self.contacts is None:
+            self.contacts = Contacts(max(1024, 64 * P), d)
+        return (o["ft"], o["energy"], o["gv"] if want_verts else None,
+                o["gp"] if want_pose else None, o["jac"] if want_jac else None, o["stats"])
+
+    def _enqueue(self, scale, want_verts, want_pose, want_jac):
+        lib = L.load()
+        ft, energy, gv, gp, jac, stats = self._outputs(want_verts, want_pose, want_jac)
+        for t in (ft, energy, gv, gp, jac):
+            if t is not None:
+                t.zero_()
+        P, s = self.pairs.shape[0], _stream(None)
+        prec = PRECISION[self.precision] if isinstance(self.precision, str) else int(self.precision)
+        cs = self.contacts.struct()
+        h, c = self.hier.handle, self.ctx.handle
+        L.check(lib.mrdem_detect(c, h, P, _p(self.pairs), _p(self.eps), _p(self.poses), prec,
+                                 C.byref(cs), _p(stats), s), "mrdem_detect")
+        L.check(lib.mrdem_contact_forces(c, h, P, _p(self.pairs), _p(self.eps), _p(self.poses),
+                                         C.byref(cs), _p(self.mass), _p(self.com), self.k_s,
+                                         _p(ft), _p(energy), s), "mrdem_contact_forces")
+        if gv is not None or gp is not None or jac is not None:
+            L.check(lib.mrdem_contact_grad(c, h, P, _p(self.pairs), _p(self.eps), _p(self.poses),
+                                           C.byref(cs), _p(self.mass), self.k_s, float(scale),
+                                           _p(gv), _p(gp), _p(jac), s), "mrdem_contact_grad")
+
+    def _check_and_grow(self):
+        """Status of the work just enqueued (synchronises the stream): True if
+        it completed, False after growing an overflowing list."""
+        lib = L.load()
+        req = np.zeros(5, np.int64)
+        st = lib.mrdem_check(self.ctx.handle, _stream(None), _np_ptr(req))
+        if st == L.MRDEM_OK:
+            return True
+        if st != L.MRDEM_ERR_CAPACITY:
+            L.check(st, "ContactProblem.step")
+        prm = self.ctx.params
+        grow = lambda need, cap: int(need * 1.25) + 1024 if need > cap else 0  # noqa: E731
+        lv, ti, ca = grow(req[0], prm.cap_level), grow(req[1], prm.cap_tiles), grow(req[2], prm.cap_candidates)
+        sw = grow(req[4], prm.cap_sweep)
+        if lv or ti or ca or sw:
+            self.ctx.reserve(lv, ti, ca, sw)
+        if req[3] > self.contacts.capacity:
+            self.contacts.resize(int(req[3] * 1.25) + 1024)
+        self._graph = None
+        return False
+
+    def step(self, scale=1.0, want_verts=True, want_pose=True, want_jac=False, graph=True,
+             max_retries=4):
+        """Detection, forces and energy, and the adjoint of the whole batch in
+        one call on the current stream.  The status is checked once, at the end
+        (one synchronisation); after a list overflow the lists grow and the
+        step runs again.  With graph=True the sequence is captured once into a
+        CUDA graph (captured again after a list grows or the flags change) and
+        replayed, so the inputs must be updated in place (pairs, eps, poses,
+        mass, com keep their storage).  Returns tensors owned by the problem,
+        overwritten by the next step: (contacts, force_torque, energy,
+        dE_dverts, dE_dpose, jac, stats)."""
+        key = (float(scale), bool(want_verts), bool(want_pose), bool(want_jac))
+        for _ in range(max_retries + 1):
+            g = getattr(self, "_graph", None)
+            if not graph:
+                self._enqueue(scale, want_verts, want_pose, want_jac)
+            elif g is not None and self._graph_key == key:
+                g.replay()
+            else:
+                # an uncaptured run first: it sizes the scratch the graph will use
+                self._enqueue(scale, want_verts, want_pose, want_jac)
+                if not self._check_and_grow():
+                    continue
+                g = torch.cuda.CUDAGraph()
+                side = torch.cuda.Stream()
+                side.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.graph(g, stream=side):
+                    self._enqueue(scale, want_verts, want_pose, want_jac)
+                torch.cuda.current_stream().wait_stream(side)
+                self._graph, self._graph_key = g, key
+                g.replay()
+            if self._check_and_grow():
+                ft, energy, gv, gp, jac, stats = self._outputs(want_verts, want_pose, want_jac)
+                return self.contacts, ft, energy, gv, gp, jac, stats
+        raise L.MrdemError(L.MRDEM_ERR_CAPACITY, "ContactProblem.step (retries exhausted)")
+
 
 class ContactEnergy(torch.autograd.Function):
     """E = sum over contacts of K_s sqrt(mu) eps (1 - d/(2 eps))^2.
