@@ -323,16 +323,6 @@ struct TileSmem {
   unsigned char ka[32], kb[32];  // triangles kept by the fine-vs-surrogate test
 };
 
-// Bounding sphere of a triangle: centroid and largest vertex distance
-// (rounded up).
-__device__ __forceinline__ float4 tri_sphere(F3 v0, F3 v1, F3 v2) {
-  F3 c = (1.f / 3.f) * ((v0 + v1) + v2);
-  F3 d0 = v0 - c, d1 = v1 - c, d2 = v2 - c;
-  float r2 = fmaxf(dot(d0, d0), fmaxf(dot(d1, d1), dot(d2, d2)));
-  return make_float4(c.x, c.y, c.z, sqrtf(r2) * (1.f + 1e-6f));
-}
-
-
 // A leaf's surrogate as seen from the other particle (A's frame): the unit
 // normal and offset of its plane and its node sphere (centre, largest vertex
 // distance + delta).

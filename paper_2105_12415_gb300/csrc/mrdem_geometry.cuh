@@ -293,10 +293,6 @@ template <typename T>
 MRDEM_HD TriTriResult<T> tri_tri_distance(const V3<T> P[3], const V3<T> Q[3]) {
   return tri_tri_distance_impl<T, false>(P, Q, nullptr);
 }
-template <typename T>
-MRDEM_HD TriTriResult<T> tri_tri_distance_ranked(const V3<T> P[3], const V3<T> Q[3], T* second2) {
-  return tri_tri_distance_impl<T, true>(P, Q, second2);
-}
 
 // All fifteen sub-tests of the comparison-based distance without early exit:
 // d2[k] is the squared distance of sub-test k (k = feature code 0..14).
@@ -389,9 +385,8 @@ struct CandGeom {
 // FP32 form of the final distance: the fifteen sub-tests in float on the
 // rounded coordinates with the error bound err = 2^-15 max|coordinate|; a
 // pair clearly beyond 2 eps is dropped; every sub-test within 2 err of the
-// float minimum is re-evaluated in double and the smallest value is the
-// distance (the true minimiser is always among them).
-// Returns 1 (contact, r filled), 0 (no contact) or -1 (needs the full FP64 test).
+// float minimum is finished in extended precision and the smallest value is
+// the distance (the true minimiser is always among them).
 // Float stage of the FP32 form: the fifteen sub-tests on float coordinates
 // relative to A's first vertex.  extra_err bounds the error of those
 // coordinates beyond their own rounding (e.g. a float rigid transform).
@@ -444,24 +439,6 @@ MRDEM_HD double cand_double_stage(const CandGeom& g, unsigned mask, V3<double>& 
     }
   }
   return sqrt(bd2);
-}
-
-// Returns 1 (distance <= 2 eps: d, pa, pb and the weights filled), 0 (beyond
-// 2 eps) or -1 (crossing or nearly touching: needs the full double test).
-// With tau = +inf every non-crossing pair is finished (used by the adjoint).
-MRDEM_HD int cand_fp32(const CandGeom& g, double& d, V3<double>& pa, V3<double>& pb,
-                       double* wa = nullptr, double* wb = nullptr) {
-  V3<float> Pf[3], Qf[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    Pf[k] = {(float)g.P[k].x, (float)g.P[k].y, (float)g.P[k].z};
-    Qf[k] = {(float)g.Q[k].x, (float)g.Q[k].y, (float)g.Q[k].z};
-  }
-  unsigned mask = 0;
-  int r = cand_float_stage(Pf, Qf, g.tau, 0.f, &mask);
-  if (r != 1) return r;
-  d = cand_double_stage(g, mask, pa, pb, wa, wb);
-  return d <= g.tau ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
