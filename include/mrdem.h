@@ -201,7 +201,10 @@ int mrdem_hier_export(const mrdem_hier* hier, float* node_tri, float* node_delta
  * int32 particle indices of hier (A, B; A != B not required), pair_eps
  * [n_pairs] eps of each pair (both particles), poses [n_particles*7].
  * `precision` is MRDEM_PREC_FP32 or MRDEM_PREC_FP64.  Writes the contact set
- * of every pair into *out (count overwritten).  stats: NULL or device int64
+ * of every pair into *out (count overwritten), grouped by pair with the pairs
+ * in increasing order (the order within a pair is not fixed); the context
+ * keeps a scratch contact list of out's capacity, grown on a call with a
+ * larger capacity than before.  stats: NULL or device int64
  * [MRDEM_STAT_COUNT], overwritten.  The result equals the brute-force contact
  * set over all fine triangle pairs (Lemma 1).  Errors returned directly:
  * INVALID (sizes, null pointers, hier not uploaded to ctx), CUDA. */

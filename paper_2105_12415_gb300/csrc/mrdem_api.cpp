@@ -174,6 +174,10 @@ int mrdem_destroy(mrdem_ctx* c) {
   cudaFree(c->xf);
   cudaFree(c->xf64);
   cudaFree(c->xfdd);
+  cudaFree(c->pair_cnt);
+  cudaFree(c->tmp_i);
+  cudaFree(c->tmp_d);
+  cudaFree(c->tmp_count);
   cudaFree(c->frames);
   cudaFree(c->counters);
   cudaFree(c->status);
@@ -523,7 +527,7 @@ int mrdem_triangle_distance(mrdem_ctx* c, int64_t n, const double* P, const doub
 
 static const char* kKernelNames[K_COUNT] = {
     "k_setup", "k_expand", "k_sweep_nodes", "k_tile",  "k_sweep_fine", "k_exact",
-    "k_exact64", "k_forces", "k_grad",       "k_plain", "k_tridist"};
+    "k_exact64", "k_forces", "k_grad",       "k_plain", "k_tridist", "k_sort"};
 
 int mrdem_profile(mrdem_ctx* c, int32_t enable) {
   if (!c) return MRDEM_ERR_INVALID;

@@ -810,18 +810,23 @@ static int ensure_pairs(mrdem_ctx* c, int64_t n) {
   cudaFree(c->xf);
   cudaFree(c->xf64);
   cudaFree(c->xfdd);
+  cudaFree(c->pair_cnt);
   c->xf = nullptr;
   c->xf64 = nullptr;
   c->xfdd = nullptr;
+  c->pair_cnt = nullptr;
   c->cap_pairs = 0;
   if (cudaMalloc(&c->xf, sizeof(PairXf) * cap) != cudaSuccess ||
       cudaMalloc(&c->xf64, sizeof(PairXf64) * cap) != cudaSuccess ||
-      cudaMalloc(&c->xfdd, sizeof(PairXfDD) * cap) != cudaSuccess) {
+      cudaMalloc(&c->xfdd, sizeof(PairXfDD) * cap) != cudaSuccess ||
+      cudaMalloc(&c->pair_cnt, sizeof(int32_t) * cap) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(c->xf);
     cudaFree(c->xf64);
+    cudaFree(c->xfdd);
     c->xf = nullptr;
     c->xf64 = nullptr;
+    c->xfdd = nullptr;
     return MRDEM_ERR_OOM;
   }
   c->cap_pairs = cap;
@@ -852,6 +857,101 @@ static SweepConst sweep_const(const mrdem_params& p) {
   return sc;
 }
 
+// ---------------------------------------------------------------------------
+// Contacts ordered by pair: detection writes its contacts to a scratch list
+// in whatever order the warps finish; a counting sort over the pair index
+// (count, exclusive scan, scatter) then writes them to the caller's buffers
+// grouped by pair, pairs in increasing order (within a pair the order is
+// not fixed).  The per-pair sums of forces and the adjoint then meet one or
+// two pairs per warp instead of several.
+__global__ void __launch_bounds__(256) k_sort_count(mrdem_contacts tmp, int32_t* pair_cnt) {
+  wait_prior_grid();
+  int64_t n = *tmp.count;
+  if (n > tmp.capacity) n = tmp.capacity;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(pair_cnt + tmp.pair[k], 1);
+}
+
+// Exclusive scan of the per-pair counts in place, one block.
+__global__ void __launch_bounds__(1024) k_sort_scan(int32_t* pair_cnt, int64_t n_pairs) {
+  wait_prior_grid();
+  __shared__ int64_t part[1024];
+  const int64_t per = (n_pairs + blockDim.x - 1) / blockDim.x;
+  const int64_t b = threadIdx.x * per, e = b + per < n_pairs ? b + per : n_pairs;
+  int64_t sum = 0;
+  for (int64_t i = b; i < e; ++i) sum += pair_cnt[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    int64_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t run = part[threadIdx.x] - sum;
+  for (int64_t i = b; i < e; ++i) {
+    int32_t c = pair_cnt[i];
+    pair_cnt[i] = (int32_t)run;
+    run += c;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_sort_scatter(mrdem_contacts tmp, int32_t* pair_cnt,
+                                                      mrdem_contacts out) {
+  wait_prior_grid();
+  int64_t n = *tmp.count;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *out.count = n;
+  if (n > tmp.capacity) n = tmp.capacity;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int p = tmp.pair[k];
+    const int64_t j = atomicAdd(pair_cnt + p, 1);
+    if (j >= out.capacity) continue;
+    out.pair[j] = p;
+    out.tri_a[j] = tmp.tri_a[k];
+    out.tri_b[j] = tmp.tri_b[k];
+    out.dist[j] = tmp.dist[k];
+    for (int q = 0; q < 3; ++q) {
+      out.point_a[3 * j + q] = tmp.point_a[3 * k + q];
+      out.point_b[3 * j + q] = tmp.point_b[3 * k + q];
+    }
+  }
+}
+
+// Scratch contact list with the caller's capacity.
+static int ensure_tmp(mrdem_ctx* c, int64_t cap, mrdem_contacts* tmp) {
+  if (cap > c->cap_tmp || !c->tmp_count) {
+    cudaFree(c->tmp_i);
+    cudaFree(c->tmp_d);
+    if (!c->tmp_count && cudaMalloc(&c->tmp_count, sizeof(int64_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return MRDEM_ERR_OOM;
+    }
+    c->tmp_i = nullptr;
+    c->tmp_d = nullptr;
+    c->cap_tmp = 0;
+    const int64_t n = cap > 0 ? cap : 1;
+    if (cudaMalloc(&c->tmp_i, sizeof(int32_t) * 3 * n) != cudaSuccess ||
+        cudaMalloc(&c->tmp_d, sizeof(double) * 7 * n) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(c->tmp_i);
+      c->tmp_i = nullptr;
+      return MRDEM_ERR_OOM;
+    }
+    c->cap_tmp = n;
+  }
+  tmp->capacity = cap;
+  tmp->count = c->tmp_count;
+  tmp->pair = c->tmp_i;
+  tmp->tri_a = c->tmp_i + c->cap_tmp;
+  tmp->tri_b = c->tmp_i + 2 * c->cap_tmp;
+  tmp->dist = c->tmp_d;
+  tmp->point_a = c->tmp_d + c->cap_tmp;
+  tmp->point_b = c->tmp_d + 4 * c->cap_tmp;
+  return MRDEM_OK;
+}
+
 static int finish(cudaStream_t) {
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
@@ -862,11 +962,16 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
                   int64_t* stats, cudaStream_t s) {
   int st = ensure_pairs(c, n_pairs);
   if (st) return st;
+  mrdem_contacts tmp;
+  st = ensure_tmp(c, out->capacity, &tmp);
+  if (st) return st;
   const HierDev& H = hier->dev;
   const mrdem_params& prm = c->params;
   SweepConst sc = sweep_const(prm);
   cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * CNT_TOTAL, s);
   cudaMemsetAsync(out->count, 0, sizeof(int64_t), s);
+  cudaMemsetAsync(tmp.count, 0, sizeof(int64_t), s);
+  if (n_pairs > 0) cudaMemsetAsync(c->pair_cnt, 0, sizeof(int32_t) * n_pairs, s);
   if (n_pairs > 0) {
     // one warp per block: the FP64 setup work spreads over every SM
     int threads = 32;
@@ -909,10 +1014,18 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
     if (precision == MRDEM_PREC_FP64) {
       ProfScope ps(c, K_EXACT, s);
       launch_after(k_exact64, c->n_sms * 8, et, 0, s, H, c->xf64, c->cands, c->counters,
-                   (int)CNT_CANDS, c->cap_cands, c->status, (int)MRDEM_STAT_FP64, *out);
+                   (int)CNT_CANDS, c->cap_cands, c->status, (int)MRDEM_STAT_FP64, tmp);
     } else {
-      int r = launch_exact_fp32(c, hier, out, s);
+      int r = launch_exact_fp32(c, hier, &tmp, s);
       if (r) return r;
+    }
+    // the contacts, grouped by pair, into the caller's buffers
+    {
+      ProfScope ps(c, K_SORT, s);
+      const int sb = c->n_sms * 4;
+      launch_after(k_sort_count, sb, 256, 0, s, tmp, c->pair_cnt);
+      launch_after(k_sort_scan, 1, 1024, 0, s, c->pair_cnt, n_pairs);
+      launch_after(k_sort_scatter, sb, 256, 0, s, tmp, c->pair_cnt, *out);
     }
   }
   if (stats)

@@ -152,7 +152,7 @@ struct mrdem_hier {
 };
 
 namespace mrdem {
-enum KernelId : int { K_SETUP = 0, K_LEVEL, K_SWEEP_NODES, K_TILE, K_SWEEP_FINE, K_EXACT, K_EXACT64, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_COUNT };
+enum KernelId : int { K_SETUP = 0, K_LEVEL, K_SWEEP_NODES, K_TILE, K_SWEEP_FINE, K_EXACT, K_EXACT64, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_SORT, K_COUNT };
 struct ProfRec {
   int kernel;
   cudaEvent_t a, b;
@@ -179,7 +179,14 @@ struct mrdem_ctx {
   mrdem::PairXf* xf = nullptr;
   mrdem::PairXf64* xf64 = nullptr;
   mrdem::PairXfDD* xfdd = nullptr;
+  int32_t* pair_cnt = nullptr;  // [cap_pairs]: contacts per pair, then write cursors
   int64_t cap_pairs = 0;
+  // detection's contacts before they are ordered by pair (same layout as the
+  // caller's buffers, capacity cap_tmp)
+  int32_t* tmp_i = nullptr;   // pair, tri_a, tri_b: three arrays of cap_tmp
+  double* tmp_d = nullptr;    // dist [cap_tmp], point_a [cap_tmp*3], point_b [cap_tmp*3]
+  int64_t* tmp_count = nullptr;
+  int64_t cap_tmp = 0;
   double* frames = nullptr;  // [cap_frames * 16]: per particle R (9), t (3), world com (3)
   int64_t cap_frames = 0;
   unsigned long long* counters = nullptr;  // [CNT_TOTAL]

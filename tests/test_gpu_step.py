@@ -72,3 +72,13 @@ def test_step_grows_lists_and_recaptures():
     small.poses.copy_(torch.as_tensor(moved, device="cuda:0"))
     prob.poses.copy_(torch.as_tensor(moved, device="cuda:0"))
     _same(_stepped(small, True), _separate(prob))
+
+
+def test_contacts_grouped_by_pair():
+    """Detection writes its contacts grouped by pair, pairs in increasing order."""
+    s = scene_c3(n_pairs=1024).subset(np.arange(0, 1024, 32))
+    prob = _problem(s)
+    c, _ = prob.detect()
+    pairs = c.to_numpy(sort=False)["pair"]
+    assert len(pairs) > 0
+    assert np.all(np.diff(pairs) >= 0)
