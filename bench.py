@@ -373,10 +373,11 @@ def main():
     n_contacts = int(contacts.count.item())
     # our kernels per step: k_setup, (k_expand, k_sweep_nodes) per surrogate
     # level below the roots, k_tile, k_sweep_fine, the exact pass (FP32 form:
-    # k_cp_float, 2 x k_cp_items, k_select_exact, k_exact64_idx; FP64 form:
-    # k_exact64), then k_frames + k_forces and k_frames + k_grad
+    # k_cp_float, 3 x k_cp_items, k_select_exact; FP64 form: k_exact64), the
+    # ordering by pair (k_sort_scan, k_sort_scatter), then k_frames + k_forces
+    # and k_frames + k_grad
     exact_launches = 5 if args.precision == "fp32" else 1
-    launches_per_step = 1 + 2 * max(0, info["max_depth"] - 1) + 2 + exact_launches + 4
+    launches_per_step = 1 + 2 * max(0, info["max_depth"] - 1) + 2 + exact_launches + 2 + 4
 
     # ---- per-kernel timing (same steps, outside the graph, events per kernel)
     ctx.profile(True)

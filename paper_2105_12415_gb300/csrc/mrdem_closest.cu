@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(128) k_select_exact(HierDev H, const PairXfDD*
                                                       const int3* __restrict__ cands,
                                                       unsigned long long* cnt, int64_t cap_acc,
                                                       unsigned long long* status,
-                                                      mrdem_contacts out) {
+                                                      mrdem_contacts out, int32_t* pair_cnt) {
   wait_prior_grid();
   int64_t n = (int64_t)cnt[CNT_ACC];
   if (n > cap_acc) n = cap_acc;
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(128) k_select_exact(HierDev H, const PairXfDD*
       }
     }
     ncon.add(hit);
-    write_contact(H, out, status, hit, c.x, c.y, c.z, d, pa, pb);
+    write_contact(H, out, status, hit, c.x, c.y, c.z, d, pa, pb, pair_cnt);
   }
   ncon.flush(cnt + CNT_STATS + MRDEM_STAT_CONTACTS);
 }
@@ -268,7 +268,8 @@ int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts
   launch_after(k_cp_items<2>, ib, 256, 0, s, c->acc, c->items_cx, (int)CNT_CX, c->cap_items,
                c->res_cx, c->counters);
   launch_after(k_select_exact, c->n_sms * 8, 128, 0, s, hier->dev, c->xfdd, c->acc, c->res_pt,
-               c->res_ee, c->res_cx, c->cands, c->counters, c->cap_cands, c->status, *out);
+               c->res_ee, c->res_cx, c->cands, c->counters, c->cap_cands, c->status, *out,
+               c->pair_cnt);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
 

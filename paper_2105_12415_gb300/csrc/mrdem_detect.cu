@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(128) k_exact64(HierDev H, const PairXf64* __re
                                                  const int3* __restrict__ list,
                                                  unsigned long long* cnt, int count_slot,
                                                  int64_t cap, unsigned long long* status,
-                                                 int stat_slot, mrdem_contacts out) {
+                                                 int stat_slot, mrdem_contacts out, int32_t* pair_cnt) {
   wait_prior_grid();
   int64_t n = (int64_t)cnt[count_slot];
   if (n > cap) n = cap;
@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(128) k_exact64(HierDev H, const PairXf64* __re
     }
     ncon.add(hit);
     nall.add(k < n);
-    write_contact(H, out, status, hit, c.x, c.y, c.z, d, pa, pb);
+    write_contact(H, out, status, hit, c.x, c.y, c.z, d, pa, pb, pair_cnt);
   }
   ncon.flush(cnt + CNT_STATS + MRDEM_STAT_CONTACTS);
   if (stat_slot >= 0) nall.flush(cnt + CNT_STATS + stat_slot);
@@ -859,20 +859,12 @@ static SweepConst sweep_const(const mrdem_params& p) {
 
 // ---------------------------------------------------------------------------
 // Contacts ordered by pair: detection writes its contacts to a scratch list
-// in whatever order the warps finish; a counting sort over the pair index
-// (count, exclusive scan, scatter) then writes them to the caller's buffers
+// in whatever order the warps finish, counting them per pair as it goes; a
+// counting sort over the pair index (exclusive scan, scatter) then writes
+// them to the caller's buffers
 // grouped by pair, pairs in increasing order (within a pair the order is
 // not fixed).  The per-pair sums of forces and the adjoint then meet one or
 // two pairs per warp instead of several.
-__global__ void __launch_bounds__(256) k_sort_count(mrdem_contacts tmp, int32_t* pair_cnt) {
-  wait_prior_grid();
-  int64_t n = *tmp.count;
-  if (n > tmp.capacity) n = tmp.capacity;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(pair_cnt + tmp.pair[k], 1);
-}
-
 // Exclusive scan of the per-pair counts in place, one block.
 __global__ void __launch_bounds__(1024) k_sort_scan(int32_t* pair_cnt, int64_t n_pairs) {
   wait_prior_grid();
@@ -1014,7 +1006,8 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
     if (precision == MRDEM_PREC_FP64) {
       ProfScope ps(c, K_EXACT, s);
       launch_after(k_exact64, c->n_sms * 8, et, 0, s, H, c->xf64, c->cands, c->counters,
-                   (int)CNT_CANDS, c->cap_cands, c->status, (int)MRDEM_STAT_FP64, tmp);
+                   (int)CNT_CANDS, c->cap_cands, c->status, (int)MRDEM_STAT_FP64, tmp,
+                   c->pair_cnt);
     } else {
       int r = launch_exact_fp32(c, hier, &tmp, s);
       if (r) return r;
@@ -1023,7 +1016,6 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
     {
       ProfScope ps(c, K_SORT, s);
       const int sb = c->n_sms * 4;
-      launch_after(k_sort_count, sb, 256, 0, s, tmp, c->pair_cnt);
       launch_after(k_sort_scan, 1, 1024, 0, s, c->pair_cnt, n_pairs);
       launch_after(k_sort_scatter, sb, 256, 0, s, tmp, c->pair_cnt, *out);
     }
@@ -1219,13 +1211,14 @@ extern "C" int mrdem_detect_noalloc(const mrdem_hier* hier, int64_t n_pairs,
     int et = prm.exact_threads;
     if (precision == MRDEM_PREC_FP64) {
       k_exact64<<<c->n_sms * 8, et, 0, s>>>(H, xf64, cands, cnt, CNT_CANDS, kNaCands, status,
-                                             MRDEM_STAT_FP64, *out);
+                                             MRDEM_STAT_FP64, *out, nullptr);
     } else {
       // the first level list is free once the tiles are done: the fallback list
       k_exact32<<<c->n_sms * 8, et, 0, s>>>(H, xf, xf64, cands, cnt, status, kNaCands,
                                              reinterpret_cast<int3*>(lists[0]), kNaLevel, *out);
       k_exact64<<<c->n_sms * 4, et, 0, s>>>(H, xf64, reinterpret_cast<const int3*>(lists[0]), cnt,
-                                             CNT_FALLBACK, kNaLevel, status, MRDEM_STAT_FP64, *out);
+                                             CNT_FALLBACK, kNaLevel, status, MRDEM_STAT_FP64, *out,
+                                             nullptr);
     }
   }
   cudaMemcpyAsync(stats, cnt + CNT_STATS, sizeof(int64_t) * MRDEM_STAT_COUNT,

@@ -290,9 +290,12 @@ __device__ __forceinline__ D3 world_point(const PairXfDD& X, V3<dd> p, int k, co
   return {to_double(w[0]), to_double(w[1]), to_double(w[2])};
 }
 
+// Append a contact (warp-collective).  pair_cnt, if given, counts the stored
+// contacts of each pair (for the ordering by pair that follows).
 __device__ __forceinline__ void write_contact(const HierDev& H, const mrdem_contacts& out,
                                               unsigned long long* status, bool hit, int pair,
-                                              int sa, int sb, double d, D3 pa, D3 pb) {
+                                              int sa, int sb, double d, D3 pa, D3 pb,
+                                              int32_t* pair_cnt = nullptr) {
   unsigned m = __ballot_sync(0xffffffffu, hit);
   if (!m) return;
   int leader = __ffs(m) - 1;
@@ -308,6 +311,7 @@ __device__ __forceinline__ void write_contact(const HierDev& H, const mrdem_cont
     out.dist[idx] = d;
     out.point_a[3 * idx] = pa.x; out.point_a[3 * idx + 1] = pa.y; out.point_a[3 * idx + 2] = pa.z;
     out.point_b[3 * idx] = pb.x; out.point_b[3 * idx + 1] = pb.y; out.point_b[3 * idx + 2] = pb.z;
+    if (pair_cnt) atomicAdd(pair_cnt + pair, 1);
   } else {
     atomicMax(status + ST_REQ_CONTACTS, idx + 1);
   }
