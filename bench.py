@@ -173,14 +173,20 @@ class Clocks:
 
 
 def _source_hash():
-    """Hash of the library's CUDA/C++ sources (a traffic figure is valid only
-    for the source it was measured on)."""
+    """Hash of the library's CUDA/C++ sources without their comments and
+    blank lines (a traffic figure is valid only for the code it was measured
+    on; comment edits do not change it)."""
+    import re
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2105_12415_gb300", "csrc")
     for f in sorted(os.listdir(d)):
         if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(f.encode() + b"\0" + fh.read())
+            with open(os.path.join(d, f), encoding="utf-8") as fh:
+                src = fh.read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", "", src)
+            lines = [ln.rstrip() for ln in src.splitlines() if ln.strip()]
+            h.update(f.encode() + b"\0" + "\n".join(lines).encode())
     return h.hexdigest()[:16]
 
 

@@ -549,16 +549,18 @@ __global__ void __launch_bounds__(kFineWarps * 32) k_sweep_fine(
 
 // ---------------------------------------------------------------------------
 // Final distance of the candidates.
-//   FP64 form: the comparison-based distance in double for every candidate.
-//   FP32 form: the fifteen sub-tests in float on coordinates relative to A's
-//   first vertex (rounded from double), with an a-priori error bound
-//   err = 2^-15 max|coordinate|.  Pairs clearly beyond 2 eps are dropped;
-//   every sub-test within 2 err of the float minimum is re-evaluated in
-//   double and the smallest value is the distance (the true minimiser is
-//   always among them, so this equals the double comparison-based result).
-//   Crossing or nearly touching pairs go to a fallback list that the FP64
-//   kernel finishes.
-// FP32 form, first pass over the candidates.  The float stage runs on float
+//   FP64 form: the comparison-based distance in double for every candidate
+//   (k_exact64).
+//   FP32 form of mrdem_detect: the float stage and double-float work items of
+//   mrdem_closest.cu.
+//   FP32 form of the allocation-free entry point, whose fixed scratch has no
+//   room for work-item lists: one kernel (k_exact32) with the same float
+//   stage (error bound err = 2^-15 max|coordinate| on coordinates relative to
+//   A's first vertex); every sub-test within 2 err of the float minimum is
+//   re-evaluated in double in the same thread and the smallest value is the
+//   distance (the true minimiser is always among them); crossing or nearly
+//   touching pairs go to a fallback list that k_exact64 finishes.
+// k_exact32, the one-kernel FP32 form.  The float stage runs on float
 // coordinates (B moved by the float transform; its error is within the
 // pair's margin), so pairs it rejects never touch double arithmetic; the
 // others are finished in double from the double transform.
@@ -612,7 +614,7 @@ __global__ void __launch_bounds__(128) k_exact32(HierDev H, const PairXf* __rest
 }
 
 // Full FP64 comparison-based distance for every entry of a list (the FP64
-// form's candidates, or the FP32 form's fallback list).
+// form's candidates, or the fallback list of the one-kernel FP32 form).
 __global__ void __launch_bounds__(128) k_exact64(HierDev H, const PairXf64* __restrict__ xf64,
                                                  const int3* __restrict__ list,
                                                  unsigned long long* cnt, int count_slot,
