@@ -210,3 +210,70 @@ def world_triangles(scene, i, poses=None):
     R = pose_matrix(poses[i])
     w = v.astype(np.float64) @ R.T + poses[i][:3]
     return w[t].reshape(-1, 9)
+
+
+def merge_contacts(contacts, eps):
+    """Redundant-contact filter of Sec. 2 (the implementation note on the
+    contact set C): close-by contact points of one particle pair are merged
+    into one average point.
+
+    Reading: within each pair p, two contacts are linked when their contact
+    points x = (pa + pb)/2 are closer than the pair's eps, evaluated in FP64
+    as ((dx*dx + dy*dy) + dz*dz) < eps*eps; every connected component of the
+    links (the transitive closure, so the result does not depend on the order
+    of C) becomes one contact with pa and pb the means of its members' (its
+    contact point is then the mean contact point and its normal the mean
+    normal), d = |pa - pb|, and ta, tb of the member with the smallest
+    (ta, tb).  Returns the merged list sorted by (pair, ta, tb) and, per
+    merged contact, the number of members ("members").
+    """
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+
+    pair = np.asarray(contacts["pair"], np.int64)
+    ta = np.asarray(contacts["ta"], np.int64)
+    tb = np.asarray(contacts["tb"], np.int64)
+    pa = np.asarray(contacts["pa"], np.float64).reshape(-1, 3)
+    pb = np.asarray(contacts["pb"], np.float64).reshape(-1, 3)
+    eps = np.asarray(eps, np.float64)
+    order = np.lexsort((tb, ta, pair))
+    starts = np.flatnonzero(np.r_[True, pair[order][1:] != pair[order][:-1]]) if len(order) else []
+    ends = list(starts[1:]) + [len(order)]
+    out = {k: [] for k in ("pair", "ta", "tb", "d", "pa", "pb", "members")}
+    for s, e in zip(starts, ends):
+        idx = order[s:e]
+        p = int(pair[idx[0]])
+        x = (pa[idx] + pb[idx]) * 0.5
+        lim = eps[p] * eps[p]
+        n = len(idx)
+        rows, cols = [], []
+        for r0 in range(0, n, 512):  # the squared distances, a block of rows at a time
+            xr = x[r0:r0 + 512]
+            dx = xr[:, None, 0] - x[None, :, 0]
+            dy = xr[:, None, 1] - x[None, :, 1]
+            dz = xr[:, None, 2] - x[None, :, 2]
+            i, j = np.nonzero((dx * dx + dy * dy) + dz * dz < lim)
+            rows.append(i + r0)
+            cols.append(j)
+        rows, cols = np.concatenate(rows), np.concatenate(cols)
+        adj = coo_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
+        _, lab = connected_components(adj, directed=False)
+        # components in the order of their first (smallest-key) member
+        first = {}
+        for k, c in enumerate(lab):
+            first.setdefault(int(c), k)
+        for c, k0 in sorted(first.items(), key=lambda t: t[1]):
+            m = idx[lab == c]
+            a, b = pa[m].mean(axis=0), pb[m].mean(axis=0)
+            out["pair"].append(p)
+            out["ta"].append(int(ta[idx[k0]]))
+            out["tb"].append(int(tb[idx[k0]]))
+            out["pa"].append(a)
+            out["pb"].append(b)
+            out["d"].append(float(np.sqrt(np.sum((a - b) ** 2))))
+            out["members"].append(len(m))
+    return dict(pair=np.array(out["pair"], np.int32), ta=np.array(out["ta"], np.int32),
+                tb=np.array(out["tb"], np.int32), d=np.array(out["d"], np.float64),
+                pa=np.array(out["pa"], np.float64).reshape(-1, 3),
+                pb=np.array(out["pb"], np.float64).reshape(-1, 3),
+                members=np.array(out["members"], np.int64))
