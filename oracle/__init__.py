@@ -22,13 +22,25 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (g++, OpenMP, no fast-math) if it is missing or stale."""
+    """Compile the oracle (g++, OpenMP, no fast-math) unless a build of the
+    same source (content hash, stored beside the library) is present."""
+    import hashlib
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-fno-fast-math",
+           "-ffp-contract=off"]
+    with open(_SRC, "rb") as f:
+        digest = hashlib.sha256(" ".join(cmd + [os.uname().machine]).encode() + f.read()).hexdigest()
+    try:
+        with open(_OUT + ".inputs") as f:
+            fresh = os.path.exists(_OUT) and f.read().strip() == digest
+    except OSError:
+        fresh = False
+    if force or not fresh:
         tmp = _OUT + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
-                               "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp])
+        subprocess.check_call(cmd + [_SRC, "-o", tmp])
         os.replace(tmp, _OUT)
+        with open(_OUT + ".inputs", "w") as f:
+            f.write(digest + "\n")
     return _OUT
 
 
@@ -221,10 +233,11 @@ def merge_contacts(contacts, eps):
     points x = (pa + pb)/2 are closer than the pair's eps, evaluated in FP64
     as ((dx*dx + dy*dy) + dz*dz) < eps*eps; every connected component of the
     links (the transitive closure, so the result does not depend on the order
-    of C) becomes one contact with pa and pb the means of its members' (its
-    contact point is then the mean contact point and its normal the mean
-    normal), d = |pa - pb|, and ta, tb of the member with the smallest
-    (ta, tb).  Returns the merged list sorted by (pair, ta, tb) and, per
+    of C) with two or more members becomes one contact with pa and pb the
+    means of its members' (its contact point is then the mean contact point
+    and its normal the mean normal), d = |pa - pb|, and ta, tb of the member
+    with the smallest (ta, tb); a contact with no other closer than eps stays
+    as it is (d included).  Returns the merged list sorted by (pair, ta, tb) and, per
     merged contact, the number of members ("members").
     """
     from scipy.sparse import coo_matrix
@@ -235,6 +248,7 @@ def merge_contacts(contacts, eps):
     tb = np.asarray(contacts["tb"], np.int64)
     pa = np.asarray(contacts["pa"], np.float64).reshape(-1, 3)
     pb = np.asarray(contacts["pb"], np.float64).reshape(-1, 3)
+    dist = np.asarray(contacts["d"], np.float64)
     eps = np.asarray(eps, np.float64)
     order = np.lexsort((tb, ta, pair))
     starts = np.flatnonzero(np.r_[True, pair[order][1:] != pair[order][:-1]]) if len(order) else []
@@ -264,13 +278,17 @@ def merge_contacts(contacts, eps):
             first.setdefault(int(c), k)
         for c, k0 in sorted(first.items(), key=lambda t: t[1]):
             m = idx[lab == c]
-            a, b = pa[m].mean(axis=0), pb[m].mean(axis=0)
+            if len(m) == 1:  # nothing close by: the contact stays as detected
+                a, b, d = pa[m[0]], pb[m[0]], float(dist[m[0]])
+            else:
+                a, b = pa[m].mean(axis=0), pb[m].mean(axis=0)
+                d = float(np.sqrt(np.sum((a - b) ** 2)))
             out["pair"].append(p)
             out["ta"].append(int(ta[idx[k0]]))
             out["tb"].append(int(tb[idx[k0]]))
             out["pa"].append(a)
             out["pb"].append(b)
-            out["d"].append(float(np.sqrt(np.sum((a - b) ** 2))))
+            out["d"].append(d)
             out["members"].append(len(m))
     return dict(pair=np.array(out["pair"], np.int32), ta=np.array(out["ta"], np.int32),
                 tb=np.array(out["tb"], np.int32), d=np.array(out["d"], np.float64),

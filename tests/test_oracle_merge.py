@@ -203,3 +203,19 @@ def test_a_dropped_link_would_split(orc):
         sel = list(keep)
         c = _contacts([0] * len(sel), sel, [0] * len(sel), x[sel], x[sel])
         assert len(orc.merge_contacts(c, [eps])["d"]) == want
+
+
+def test_lone_contact_stays_as_detected(orc):
+    """A contact with no other contact of its pair closer than eps is not
+    averaged with anything: it comes out as it went in, its distance included
+    (a crossing pair keeps d = 0 even where the two closest points differ in
+    the last bits)."""
+    pa = [[0.0, 0.0, 0.0], [5.0, 0.0, 0.0]]
+    pb = [[0.0, 0.0, 1e-17], [5.0, 0.0, 0.25]]
+    c = _contacts([0, 0], [1, 2], [3, 4], pa, pb)
+    c["d"] = np.array([0.0, 0.25])
+    m = orc.merge_contacts(c, [0.5])
+    assert list(m["members"]) == [1, 1]
+    np.testing.assert_array_equal(m["d"], [0.0, 0.25])
+    np.testing.assert_array_equal(m["pa"], np.asarray(pa))
+    np.testing.assert_array_equal(m["pb"], np.asarray(pb))
