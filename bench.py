@@ -51,6 +51,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--no-merge", action="store_true")
+    ap.add_argument("--merge-calls", type=int, default=50)
     return ap.parse_args()
 
 
@@ -437,6 +439,39 @@ def main():
     fin = rl.get(top, {"achieved": float("nan"), "frac": float("nan"), "avg_ms": float("nan"),
                        "flops_per_launch": float("nan")})
 
+    # ---- redundant-contact merge (Sec. 2) of the step's contact list, timed
+    # on its own (not part of the step): CUDA events around each call, L2
+    # flushed between calls
+    merge = None
+    if not args.no_merge:
+        merged, members = m.merge_contacts(ctx, prob.eps, contacts)  # sizes the output
+        for k in range(args.warmup):
+            flush.fill_(k & 0xFF)
+            m.merge_contacts(ctx, prob.eps, contacts, out=merged, members=members, check=False)
+        torch.cuda.synchronize()
+        mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.merge_calls)]
+        for k in range(args.merge_calls):
+            flush.fill_(k & 0xFF)
+            mev[k][0].record()
+            m.merge_contacts(ctx, prob.eps, contacts, out=merged, members=members, check=False)
+            mev[k][1].record()
+        torch.cuda.synchronize()
+        m._lib.check(lib.mrdem_check(ctx.handle, None, None), "merge check")
+        mms = sum(a.elapsed_time(b) for a, b in mev) / args.merge_calls
+        n_out = int(merged.count.item())
+        # compulsory bytes: read each contact once (pair, tri_a, tri_b, pa, pb:
+        # 60 B), write each merged contact once (68 B + member count 4 B),
+        # eps and two per-pair counts (16 B)
+        mbytes = 60 * n_contacts + 72 * n_out + 16 * P
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        merge = {"ms_per_call": mms, "contacts_in": n_contacts, "contacts_out": n_out,
+                 "launches_per_call": 7, "calls": args.merge_calls,
+                 "roofline": {"bound": "hbm", "achieved": mbytes / (mms * 1e-3) / 1e9,
+                              "peak": hbm, "unit": "GB/s",
+                              "frac": mbytes / (mms * 1e-3) / 1e9 / hbm,
+                              "bytes_per_call": mbytes, "traffic": None}}
+
     # ---- end to end through the public API (host inputs, host results)
     e2e = None
     if not args.no_e2e:
@@ -529,6 +564,7 @@ def main():
                       (np.diff(scene.tri_off)[scene.pairs[:, 0]] *
                        np.diff(scene.tri_off)[scene.pairs[:, 1]]).sum()) * args.steps * world / (ms_max * 1e-3)},
         "e2e": e2e,
+        "merge": merge,
         "plain_fp64_gpu": plain,
         "cpu_baseline": cpu,
     }

@@ -24,7 +24,7 @@
  *   - arrays are dense, row-major, little-endian, without padding;
  *   - a pose is 7 doubles (tx, ty, tz, qw, qx, qy, qz); the quaternion is
  *     normalised before use; world = R(q) * body + t;
- *   - stream-ordered calls (detect, forces, grad, triangle_distance) enqueue
+ *   - stream-ordered calls (detect, merge, forces, grad, triangle_distance) enqueue
  *     work on the given cudaStream_t (NULL = legacy default stream), never
  *     synchronise the host and can be captured into a CUDA graph, unless the
  *     call's comment says otherwise.  They keep per-pair and per-particle
@@ -258,6 +258,37 @@ int mrdem_contact_grad(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
                        const mrdem_contacts* contacts, const double* mass, double k_s,
                        double dE_scale, float* dE_dverts, double* dE_dpose, double* jac,
                        mrdem_stream stream);
+
+/* Redundant-contact merge (Sec. 2, the implementation note on the contact
+ * set: contact points closer than eps are merged into one average point
+ * before the set is used).  Within each pair p, contacts i and j are linked
+ * when their contact points x = (point_a + point_b)/2 lie closer than
+ * pair_eps[p], evaluated in FP64 as ((dx*dx + dy*dy) + dz*dz) < eps*eps with
+ * every operation rounded on its own (no fused multiply-add); each connected
+ * component of the links becomes one contact whose point_a and point_b are
+ * the means of its members' (so its contact point is their mean contact point
+ * and its normal their mean normal), dist = |point_a - point_b|, and tri_a,
+ * tri_b those of the member with the smallest (tri_a, tri_b).
+ * Device inputs: pair_eps [n_pairs]; `in`, any contact list (for example
+ * mrdem_detect's output, in any order; entries past min(*in->count,
+ * in->capacity) are ignored).  Device outputs: `out` (buffers distinct from
+ * in's; count overwritten with the number of merged contacts, which may
+ * exceed out->capacity), grouped by pair in increasing order and within a
+ * pair by increasing (tri_a, tri_b); members: NULL or int32
+ * [out->capacity], the number of contacts merged into each entry.  The result
+ * does not depend on the order of `in` (sums run in (tri_a, tri_b) order).
+ * The merged list serves mrdem_contact_forces; the adjoint
+ * (mrdem_contact_grad) is defined on the unmerged list.  Work per pair is
+ * quadratic in its number of contacts.  The context keeps about 132 bytes of
+ * scratch per entry of in's capacity and 8 per pair, grown on a larger call.
+ * Device-side failures latched for mrdem_check: a pair index outside
+ * [0, n_pairs) (the entry is dropped) or an eps that is not finite and
+ * positive: NONFINITE; more merged contacts than out->capacity: CAPACITY with
+ * required[3].  Errors returned directly: INVALID (null pointers,
+ * overlapping in/out buffers, n_pairs or a capacity >= 2^31), OOM, CUDA. */
+int mrdem_merge_contacts(mrdem_ctx* ctx, int64_t n_pairs, const double* pair_eps,
+                         const mrdem_contacts* in, const mrdem_contacts* out, int32_t* members,
+                         mrdem_stream stream);
 
 /* Plain GPU form (reported baseline): the contact set by FP64 comparison-based
  * distance over ALL fine triangle pairs of each pair (Algorithm 2), no

@@ -93,6 +93,8 @@ SIGNATURES = {
                                        _P, _D, _P, _P, _P]),
     "mrdem_contact_grad": (C.c_int, [_P, _P, _I64, _P, _P, _P, C.POINTER(mrdem_contacts), _P, _D,
                                      _D, _P, _P, _P, _P]),
+    "mrdem_merge_contacts": (C.c_int, [_P, _I64, _P, C.POINTER(mrdem_contacts),
+                                       C.POINTER(mrdem_contacts), _P, _P]),
     "mrdem_detect_plain_fp64": (C.c_int, [_P, _P, _I64, _P, _P, _P, C.POINTER(mrdem_contacts),
                                           _P]),
     "mrdem_triangle_distance": (C.c_int, [_P, _I64, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P,

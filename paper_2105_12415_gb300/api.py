@@ -269,6 +269,38 @@ def detect_plain_fp64(ctx, hier, pairs, eps, poses, contacts=None, stream=None):
     raise L.MrdemError(L.MRDEM_ERR_CAPACITY, "mrdem_detect_plain_fp64")
 
 
+def merge_contacts(ctx: Context, eps, contacts: Contacts, out: Contacts | None = None,
+                   members=None, check=True, stream=None, max_retries=4):
+    """Redundant-contact merge (Sec. 2): per pair, contacts whose contact
+    points lie closer than the pair's eps, taken transitively, become one
+    contact at their mean points.  Returns (merged contacts, members): the
+    list grouped by pair and ordered by the representatives' (tri_a, tri_b),
+    and per entry the number of contacts merged into it (int32).  With
+    check=True the call synchronises, grows an overflowing output and
+    repeats; with check=False it only enqueues work."""
+    P = eps.shape[0]
+    _need(eps, torch.float64, (P,), "eps")
+    if out is None:
+        out = Contacts(max(1024, contacts.capacity), contacts.device)
+    lib = L.load()
+    for _ in range(max_retries + 1):
+        if members is None or members.shape[0] < out.capacity:
+            members = torch.empty(out.capacity, dtype=torch.int32, device=out.device)
+        cin, cout = contacts.struct(), out.struct()
+        L.check(lib.mrdem_merge_contacts(ctx.handle, P, _p(eps), C.byref(cin), C.byref(cout),
+                                         _p(members), _stream(stream)), "mrdem_merge_contacts")
+        if not check:
+            return out, members
+        req = np.zeros(5, np.int64)
+        st = lib.mrdem_check(ctx.handle, _stream(stream), _np_ptr(req))
+        if st == L.MRDEM_OK:
+            return out, members
+        if st != L.MRDEM_ERR_CAPACITY:
+            L.check(st, "mrdem_merge_contacts")
+        out.resize(int(req[3] * 1.25) + 1024)
+    raise L.MrdemError(L.MRDEM_ERR_CAPACITY, "mrdem_merge_contacts (retries exhausted)")
+
+
 def contact_forces(ctx, hier, pairs, eps, poses, contacts, mass, com, k_s=1000.0, force_torque=None,
                    energy=None, stream=None):
     n = hier.info()["n_particles"]

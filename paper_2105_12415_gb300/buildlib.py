@@ -5,6 +5,7 @@ linked by nvcc (static CUDA runtime).  Translation units compile in parallel.
 """
 from __future__ import annotations
 
+import hashlib
 import os
 import subprocess
 import sys
@@ -18,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 
-CU_SOURCES = ["mrdem_detect.cu", "mrdem_forces.cu", "mrdem_closest.cu"]
+CU_SOURCES = ["mrdem_detect.cu", "mrdem_forces.cu", "mrdem_closest.cu", "mrdem_merge.cu"]
 CPP_SOURCES = ["mrdem_api.cpp", "mrdem_hierarchy.cpp"]
 HEADERS = ["mrdem_geometry.cuh", "mrdem_internal.h", "mrdem_device.cuh", "mrdem_dd.cuh"]
 
@@ -30,17 +31,31 @@ def _inputs():
     return files
 
 
-def _stale(target, deps):
-    if not os.path.exists(target):
+def _digest(deps, flags):
+    """Content hash of the inputs and the compiler flags.  A build is reused
+    only when this matches the hash stored beside it: file times are not
+    comparable between the machine that edits the sources and the one that
+    builds them."""
+    h = hashlib.sha256(" ".join(flags).encode())
+    for d in deps:
+        with open(d, "rb") as f:
+            h.update(os.path.basename(d).encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def _stale(target, digest):
+    try:
+        with open(target + ".inputs") as f:
+            return not os.path.exists(target) or f.read().strip() != digest
+    except OSError:
         return True
-    t = os.path.getmtime(target)
-    return any(os.path.getmtime(d) > t for d in deps)
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     deps = _inputs()
-    if not force and not _stale(LIB, deps):
+    digest = _digest(deps, ARCH + [NVCC, os.uname().machine])
+    if not force and not _stale(LIB, digest):
         return LIB
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     jobs = []
@@ -74,6 +89,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     subprocess.check_call([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fopenmp",
                            "-lgomp"])
     os.replace(tmp, LIB)
+    with open(LIB + ".inputs", "w") as f:
+        f.write(digest + "\n")
     return LIB
 
 

@@ -178,6 +178,8 @@ int mrdem_destroy(mrdem_ctx* c) {
   cudaFree(c->tmp_i);
   cudaFree(c->tmp_d);
   cudaFree(c->tmp_count);
+  cudaFree(c->merge_seg);
+  cudaFree(c->merge_mem);
   cudaFree(c->frames);
   cudaFree(c->counters);
   cudaFree(c->status);
@@ -525,9 +527,28 @@ int mrdem_triangle_distance(mrdem_ctx* c, int64_t n, const double* P, const doub
                                   sconv, (cudaStream_t)s);
 }
 
+int mrdem_merge_contacts(mrdem_ctx* c, int64_t n_pairs, const double* eps,
+                         const mrdem_contacts* in, const mrdem_contacts* out, int32_t* members,
+                         mrdem_stream s) {
+  if (!c || n_pairs < 0 || n_pairs >= (int64_t)1 << 31) return MRDEM_ERR_INVALID;
+  if (!contacts_ok(in) || !contacts_ok(out) || (n_pairs > 0 && !eps)) return MRDEM_ERR_INVALID;
+  if (in->capacity >= (int64_t)1 << 31 || out->capacity >= (int64_t)1 << 31)
+    return MRDEM_ERR_INVALID;
+  // the output buffers may not overlap the input's
+  const void* ip[] = {in->count, in->pair, in->tri_a, in->tri_b, in->dist, in->point_a, in->point_b};
+  const void* op[] = {out->count, out->pair, out->tri_a, out->tri_b, out->dist, out->point_a,
+                      out->point_b, members};
+  for (const void* a : ip)
+    for (const void* b : op)
+      if (a && a == b) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_merge(c, n_pairs, eps, in, out, members, (cudaStream_t)s);
+}
+
 static const char* kKernelNames[K_COUNT] = {
     "k_setup", "k_expand", "k_sweep_nodes", "k_tile",  "k_sweep_fine", "k_exact",
-    "k_exact64", "k_forces", "k_grad",       "k_plain", "k_tridist", "k_sort"};
+    "k_exact64", "k_forces", "k_grad",       "k_plain", "k_tridist", "k_sort",
+    "k_merge"};
 
 int mrdem_profile(mrdem_ctx* c, int32_t enable) {
   if (!c) return MRDEM_ERR_INVALID;

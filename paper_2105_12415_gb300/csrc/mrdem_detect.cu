@@ -870,25 +870,7 @@ static SweepConst sweep_const(const mrdem_params& p) {
 // Exclusive scan of the per-pair counts in place, one block.
 __global__ void __launch_bounds__(1024) k_sort_scan(int32_t* pair_cnt, int64_t n_pairs) {
   wait_prior_grid();
-  __shared__ int64_t part[1024];
-  const int64_t per = (n_pairs + blockDim.x - 1) / blockDim.x;
-  const int64_t b = threadIdx.x * per, e = b + per < n_pairs ? b + per : n_pairs;
-  int64_t sum = 0;
-  for (int64_t i = b; i < e; ++i) sum += pair_cnt[i];
-  part[threadIdx.x] = sum;
-  __syncthreads();
-  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-    int64_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  int64_t run = part[threadIdx.x] - sum;
-  for (int64_t i = b; i < e; ++i) {
-    int32_t c = pair_cnt[i];
-    pair_cnt[i] = (int32_t)run;
-    run += c;
-  }
+  block_exclusive_scan(pair_cnt, n_pairs, nullptr);
 }
 
 __global__ void __launch_bounds__(256) k_sort_scatter(mrdem_contacts tmp, int32_t* pair_cnt,

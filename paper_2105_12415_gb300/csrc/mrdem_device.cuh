@@ -148,6 +148,32 @@ struct WarpCount {
   }
 };
 
+// Exclusive prefix sum of n int32 counts in place by one block of up to 1024
+// threads, each taking a contiguous run of the counts; the sum of all counts
+// goes to *total when total is not null.
+__device__ __forceinline__ void block_exclusive_scan(int32_t* cnt, int64_t n, int64_t* total) {
+  __shared__ int64_t part[1024];
+  const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t b = threadIdx.x * per, e = b + per < n ? b + per : n;
+  int64_t sum = 0;
+  for (int64_t i = b; i < e; ++i) sum += cnt[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    int64_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t run = part[threadIdx.x] - sum;
+  for (int64_t i = b; i < e; ++i) {
+    int32_t c = cnt[i];
+    cnt[i] = (int32_t)run;
+    run += c;
+  }
+  if (total && threadIdx.x == blockDim.x - 1) *total = part[threadIdx.x];
+}
+
 // Per-key sums over a warp.  For every distinct key among the lanes with
 // `ok` set (the group of lanes holding that key), lane e (e < nq, in strides
 // of 32) forms term = val(e) and receives the group's sum of term(l) over its

@@ -152,7 +152,7 @@ struct mrdem_hier {
 };
 
 namespace mrdem {
-enum KernelId : int { K_SETUP = 0, K_LEVEL, K_SWEEP_NODES, K_TILE, K_SWEEP_FINE, K_EXACT, K_EXACT64, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_SORT, K_COUNT };
+enum KernelId : int { K_SETUP = 0, K_LEVEL, K_SWEEP_NODES, K_TILE, K_SWEEP_FINE, K_EXACT, K_EXACT64, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_SORT, K_MERGE, K_COUNT };
 struct ProfRec {
   int kernel;
   cudaEvent_t a, b;
@@ -187,6 +187,14 @@ struct mrdem_ctx {
   double* tmp_d = nullptr;    // dist [cap_tmp], point_a [cap_tmp*3], point_b [cap_tmp*3]
   int64_t* tmp_count = nullptr;
   int64_t cap_tmp = 0;
+  // redundant-contact merge: per pair, segment cursors and merged counts
+  // (2 * cap_merge_pairs int32); per input entry, working arrays and the
+  // merged contacts (cap_merge entries)
+  int32_t* merge_seg = nullptr;
+  int64_t cap_merge_pairs = 0;
+  void* merge_mem = nullptr;
+  int64_t cap_merge = 0;
+  bool merge_smem_set = false;
   double* frames = nullptr;  // [cap_frames * 16]: per particle R (9), t (3), world com (3)
   int64_t cap_frames = 0;
   unsigned long long* counters = nullptr;  // [CNT_TOTAL]
@@ -249,6 +257,9 @@ int launch_grad(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const i
                 const double* pair_eps, const double* poses, const mrdem_contacts* c,
                 const double* mass, double k_s, double scale, float* dverts, double* dpose,
                 double* jac, cudaStream_t s);
+// redundant-contact merge (mrdem_merge.cu)
+int launch_merge(mrdem_ctx* ctx, int64_t n_pairs, const double* pair_eps, const mrdem_contacts* in,
+                 const mrdem_contacts* out, int32_t* members, cudaStream_t s);
 int launch_triangle_distance(mrdem_ctx* ctx, int64_t n, const double* P, const double* Q,
                              const double* eps, int precision, double* dist, double* pa,
                              double* pb, int32_t* feature, float* sx, float* sgap, int32_t* sconv,
