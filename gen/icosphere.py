@@ -287,3 +287,42 @@ def scene_regular_pair(level: int, radius: float, centre_dist: float, qA, qB, ep
     pA = np.concatenate([[0.0, 0.0, 0.0], qA])
     pB = np.concatenate([[centre_dist, 0.0, 0.0], qB])
     return _assemble([m, m], [pA, pB], [radius, radius], [(0, 1)], [eps], "regular-pair")
+
+
+def scene_particle_on_plane(levels=(3, 3, 4, 5), gaps=(-0.5, 0.3, 1.5, 2.5), eps: float = 0.01,
+                            radius: float = 1.0, plane_inradius: float = 3.0, seed: int = 6,
+                            amp: float = 0.05, spread: float = 50.0):
+    """The particle-on-plane setup of Sec. 6: a bumped sphere-like particle
+    over a tilted plane made of one large triangle (the paper notes that the
+    plane's triangulation does not matter while its triangles are large next
+    to the particle).  Pair k: particle 2k (subdivision levels[k], radius
+    `radius`, random rotation) and plane 2k+1, an equilateral triangle of
+    inradius `plane_inradius` (a body-frame triangle in the z = 0 plane,
+    counter-clockwise seen from +z) with a random orientation whose +z side
+    faces the particle.  The plane is placed gaps[k] * eps below the
+    particle's lowest vertex along its normal, so for gaps >= 0 the meshes'
+    distance is gaps[k] * eps; the particle's centre projects onto the
+    triangle's centre.  eps is per pair (the paper uses 1e-2 relative to the
+    particle diameter)."""
+    rng = np.random.default_rng([BASE_SEED, seed, 13])
+    a = 2.0 * plane_inradius  # circumradius
+    tri_v = np.array([[a * np.cos(t), a * np.sin(t), 0.0]
+                      for t in (np.pi / 2, np.pi / 2 + 2 * np.pi / 3, np.pi / 2 + 4 * np.pi / 3)])
+    plane = (tri_v.astype(np.float32), np.array([[0, 1, 2]], np.int32))
+    meshes, poses, radii, pairs, eps_l = [], [], [], [], []
+    for k, (lv, g) in enumerate(zip(levels, gaps)):
+        m = bumped_icosphere(int(lv), radius, rng, amp)
+        qA = random_quaternion(rng)
+        qP = random_quaternion(rng)
+        RA, RP = quat_to_matrix_f64(qA), quat_to_matrix_f64(qP)
+        n = RP[:, 2]  # the plane's normal in the world frame
+        c = rng.uniform(-spread, spread, size=3)
+        w = m[0].astype(np.float64) @ RA.T  # particle vertices relative to its centre
+        h_min = float((w @ n).min())
+        t_plane = c + (h_min - float(g) * eps) * n
+        meshes += [m, plane]
+        poses += [np.concatenate([c, qA]), np.concatenate([t_plane, qP])]
+        radii += [radius, plane_inradius]
+        pairs.append((2 * k, 2 * k + 1))
+        eps_l.append(eps)
+    return _assemble(meshes, poses, radii, pairs, eps_l, "particle-on-plane")

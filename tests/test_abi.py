@@ -50,5 +50,6 @@ def test_null_arguments_are_rejected():
     assert lib.mrdem_create(None, 0, None) == m._lib.MRDEM_ERR_INVALID
     assert lib.mrdem_detect(None, None, 0, None, None, None, 0, None, None, None) == -1
     assert lib.mrdem_check(None, None, None) == -1
+    assert lib.mrdem_merge_contacts(None, 0, None, None, None, None, None) == -1
     assert lib.mrdem_hier_get_info(None, None) == -1
     assert lib.mrdem_destroy(None) == 0

@@ -5,7 +5,7 @@ sampled pairs, and the edge cases."""
 import numpy as np
 import pytest
 
-from gen import scene_c1, scene_c2, scene_pairs, scene_tiny
+from gen import scene_c1, scene_c2, scene_pairs, scene_particle_on_plane, scene_tiny
 from tests.gpu_common import compare_contacts, gpu_scene_tensors
 
 pytestmark = pytest.mark.gpu
@@ -72,6 +72,18 @@ def test_scaled_scenes(gctx, orc, precision, k):
     assert len(ref["d"]) > 0
     got, _, _ = _run(gctx, s, precision)
     compare_contacts(got, ref, s, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_particle_on_plane(gctx, orc, precision):
+    """Particle-on-plane (Sec. 6): particles of 1280 to 20480 triangles over
+    a one-triangle plane (the |T| : 1 extreme), penetrating, touching and
+    apart; contact set and distances as the oracle's."""
+    s = scene_particle_on_plane()
+    ref = orc.detect(s)
+    got, stats, _ = _run(gctx, s, precision)
+    compare_contacts(got, ref, s, precision)
+    assert np.bincount(got["pair"], minlength=s.n_pairs)[3] == 0
 
 
 def test_plain_fp64_form_and_lemma1(gctx, orc):

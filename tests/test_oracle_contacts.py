@@ -161,3 +161,33 @@ def test_swap_and_rigid_motion_invariance(orc):
     assert sorted(zip(c3["pair"], c3["ta"], c3["tb"])) == sorted(zip(c["pair"], c["ta"], c["tb"]))
     for p, i, j, d in zip(c3["pair"], c3["ta"], c3["tb"], c3["d"]):
         assert abs(m1[(p, i, j)] - d) < 1e-11
+
+
+def test_particle_on_plane_closed_form(orc):
+    """Particle-on-plane (Sec. 6): against one large plane triangle, a
+    particle triangle's distance is a closed form of its vertices' heights h
+    over the plane: 0 if they change sign, else min |h| (the nearest vertex
+    projects inside the plane triangle).  The contact set and distances of
+    the oracle match it; the gap-2.5 eps pair has no contacts."""
+    from gen import scene_particle_on_plane
+    s = scene_particle_on_plane()
+    c = orc.detect(s)
+    for k in range(s.n_pairs):
+        A, B = s.pairs[k]
+        WA = orc.world_triangles(s, A).reshape(-1, 3, 3)
+        WP = orc.world_triangles(s, B).reshape(3, 3)
+        nrm = np.cross(WP[1] - WP[0], WP[2] - WP[0])
+        nrm /= np.linalg.norm(nrm)
+        h = (WA - WP[0]) @ nrm
+        d = np.where((h.min(1) <= 0) & (h.max(1) >= 0), 0.0, np.abs(h).min(1))
+        want = np.flatnonzero(d <= 2 * s.eps[k])
+        sel = c["pair"] == k
+        got = np.sort(c["ta"][sel])
+        band = np.flatnonzero(np.abs(d - 2 * s.eps[k]) <= 1e-9)
+        assert set(got) ^ set(want) <= set(band), k
+        dd = dict(zip(c["ta"][sel].tolist(), c["d"][sel].tolist()))
+        for t in set(got) & set(want):
+            assert abs(dd[t] - d[t]) <= 1e-12 * (1 + np.abs(WA).max()), (k, t, dd[t], d[t])
+        assert (c["tb"][sel] == 0).all()
+    counts = np.bincount(c["pair"], minlength=s.n_pairs)
+    assert counts[3] == 0 and counts[:3].min() > 0
