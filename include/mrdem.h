@@ -278,8 +278,9 @@ int mrdem_contact_grad(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
  * [out->capacity], the number of contacts merged into each entry.  The result
  * does not depend on the order of `in` (sums run in (tri_a, tri_b) order).
  * The merged list serves mrdem_contact_forces; the adjoint
- * (mrdem_contact_grad) is defined on the unmerged list.  Work per pair is
- * quadratic in its number of contacts.  The context keeps about 132 bytes of
+ * (mrdem_contact_grad) is defined on the unmerged list.  Work per pair grows
+ * with the number of its contacts within eps of each other along x
+ * (quadratic at worst, for a dense patch).  The context keeps 244 bytes of
  * scratch per entry of in's capacity and 8 per pair, grown on a larger call.
  * Device-side failures latched for mrdem_check: a pair index outside
  * [0, n_pairs) (the entry is dropped) or an eps that is not finite and

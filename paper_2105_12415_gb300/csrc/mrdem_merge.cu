@@ -8,9 +8,10 @@
 // a pair, contacts i and j are linked when their contact points
 // x = (pa + pb)/2 satisfy ((dx*dx + dy*dy) + dz*dz) < eps*eps in FP64
 // (explicitly rounded operations, no fused multiply-add); every connected
-// component of the links becomes one contact with the members' mean pa and pb
-// (so the mean contact point and the mean normal), dist = |pa - pb|, and the
-// triangle indices of the member with the smallest (tri_a, tri_b).
+// component of two or more contacts becomes one contact with the members'
+// mean pa and pb (so the mean contact point and the mean normal),
+// dist = |pa - pb|, and the triangle indices of the member with the smallest
+// (tri_a, tri_b); a lone contact is kept as detected.
 //
 // Pipeline (one stream, programmatic launches):
 //   k_merge_count    contacts per pair;
@@ -22,12 +23,11 @@
 //                    kLargeCap contacts, the context's scratch beyond):
 //                    bitonic sort by (tri_a, tri_b), a second one along x,
 //                    links by a sweep along x (a float test with an error
-//                    bound decides all but the pairs near eps, which take the
-//                    FP64 test), lock-free union-find with links to the
-//                    smaller index (the root of a component is its smallest
-//                    key), component means (a thread per small component,
-//                    a warp per large one; a lone contact is kept as it
-//                    is); each pair
+//                    bound decides all but the pairs near eps, which take
+//                    the FP64 test), lock-free union-find with links to the
+//                    smaller index and path halving (the root of a component
+//                    is its smallest key), component means (a thread per
+//                    small component, a warp per large one); each pair
 //                    writes its merged contacts at the start of its segment
 //                    of a scratch list;
 //   k_merge_scan     exclusive scan of the merged counts -> output offsets
