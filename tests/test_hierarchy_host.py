@@ -151,3 +151,55 @@ def test_fanout_bounds():
         assert ch[inner, 1].max() <= fan
         leaves = ch[:, 1] < 0
         assert (-ch[leaves, 1]).max() <= 32
+
+
+def _parents(ex):
+    par = -np.ones(len(ex["node_delta"]), np.int64)
+    for k, (b, c) in enumerate(ex["node_child"]):
+        if c > 0:
+            par[b:b + c] = k
+    return par
+
+
+@pytest.mark.parametrize("levels", [(3, 3), (2, 4)])
+def test_ancestors_of_every_contact_pass_the_surrogate_test(orc, levels):
+    """Lemma 1's premise on the built trees: for every oracle contact (fine
+    pair within 2 eps), each pair of ancestors that Algorithm 5 examines on
+    the way down (both sides unfold together; a side that reached its leaf
+    stays there) has surrogates within delta_a + delta_b + 2 eps in FP64, so
+    no certified prune can drop it."""
+    s = scene_pairs([levels[0]], [levels[1]], [1.0], [1.0], [0.02], [-0.2], 9, "anc")
+    c = orc.detect(s)
+    assert len(c["d"]) > 50
+    ex = _host(s).export()
+    par = _parents(ex)
+    # input triangle -> leaf node, per particle
+    leaf_of = {}
+    for k, (b, cnt) in enumerate(ex["node_child"]):
+        if cnt < 0:
+            for slot in range(b, b - cnt):
+                if ex["slot_tri"][slot] >= 0:
+                    leaf_of[(int(ex["slot_particle"][slot]), int(ex["slot_tri"][slot]))] = k
+    R = [orc.pose_matrix(s.poses[i]) for i in range(2)]
+
+    def world(node, i):
+        T = ex["node_tri"][node].reshape(3, 3).astype(np.float64)
+        return (T @ R[i].T + s.poses[i][:3]).ravel()
+
+    def chain(leaf):
+        out = [leaf]
+        while par[out[-1]] >= 0:
+            out.append(int(par[out[-1]]))
+        return out[::-1]  # root first
+
+    P, Q, lim = [], [], []
+    for ta, tb in zip(c["ta"], c["tb"]):
+        ca, cb = chain(leaf_of[(0, int(ta))]), chain(leaf_of[(1, int(tb))])
+        for lvl in range(max(len(ca), len(cb))):
+            na, nb = ca[min(lvl, len(ca) - 1)], cb[min(lvl, len(cb) - 1)]
+            P.append(world(na, 0))
+            Q.append(world(nb, 1))
+            lim.append(float(ex["node_delta"][na]) + float(ex["node_delta"][nb]) + 2 * s.eps[0])
+    d = orc.tri_tri(np.array(P), np.array(Q))[0]
+    lim = np.array(lim)
+    assert np.all(d <= lim * (1 + 1e-12)), (d - lim).max()

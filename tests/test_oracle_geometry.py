@@ -144,3 +144,40 @@ def test_symmetry_and_rigid_motion(orc):
     # scale covariance
     d4, _, _, _ = orc.tri_tri(2.5 * P, 2.5 * Q)
     assert np.allclose(d4, 2.5 * d, rtol=1e-13, atol=1e-13)
+
+
+def _near_parallel(rng, P):
+    """Q = P turned by a tiny angle about its centroid, moved along P's normal
+    by U[-0.1, 0.3] and sideways (vectorised form of the family above)."""
+    n = len(P)
+    T = P.reshape(n, 3, 3)
+    ax = rng.normal(size=(n, 3))
+    ax /= np.linalg.norm(ax, axis=1, keepdims=True)
+    ang = rng.uniform(0, 1e-3, n)
+    K = np.zeros((n, 3, 3))
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 2] = -ax[:, 2], ax[:, 1], -ax[:, 0]
+    K[:, 1, 0], K[:, 2, 0], K[:, 2, 1] = ax[:, 2], -ax[:, 1], ax[:, 0]
+    R = np.eye(3) + np.sin(ang)[:, None, None] * K + (1 - np.cos(ang))[:, None, None] * (K @ K)
+    c = T.mean(1, keepdims=True)
+    nrm = np.cross(T[:, 1] - T[:, 0], T[:, 2] - T[:, 0])
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    off = rng.uniform(-0.1, 0.3, (n, 1)) * nrm + rng.normal(scale=0.3, size=(n, 3))
+    return (np.einsum("nij,nkj->nki", R, T - c) + c + off[:, None, :]).reshape(n, 9)
+
+
+def test_kkt_enumeration_million(orc):
+    """One million seeded random triangle pairs (15 chunks of separated,
+    touching and crossing pairs, 5 of near-parallel ones) against the
+    independent KKT enumeration, in chunks of 50 000."""
+    rng = np.random.default_rng(2105)
+    worst = 0.0
+    for chunk in range(20):
+        n = 50_000
+        P = _rand_tris(rng, n, spread=1.5)
+        Q = _near_parallel(rng, P) if chunk >= 15 else _rand_tris(rng, n, spread=1.5)
+        d = orc.tri_tri(P, Q)[0]
+        dk = kkt_distance(P, Q)
+        err = np.abs(d - dk) / np.maximum(1.0, dk)
+        worst = max(worst, float(err.max()))
+        assert err.max() <= 1e-9, (chunk, err.max())
+    assert worst < 1e-9
