@@ -250,6 +250,22 @@ def cpu_oracle_baseline(scene, budget_s, n_threads=0):
                       f"triangle pairs), FP64 brute force, {dt:.1f} s"}
 
 
+def merge_oracle_baseline(contacts, eps, gpu_members):
+    """The oracle's merge (numpy, one host thread) on the same contact list
+    as the GPU call, timed once; its partition must equal the GPU's (the
+    merged count and the members of each merged contact, in output order)."""
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    ref = oracle.merge_contacts(contacts, eps)
+    dt = time.perf_counter() - t0
+    same = (len(ref["members"]) == len(gpu_members)
+            and bool(np.array_equal(ref["members"], np.asarray(gpu_members))))
+    return {"ms_per_call": dt * 1e3, "contacts_out": int(len(ref["members"])), "cores": 1,
+            "kind": "oracle", "partition_equal": same}
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores (the reference arm)."""
     rank, world, _ = _dist_init(args.gpus)
@@ -471,6 +487,9 @@ def main():
                               "peak": hbm, "unit": "GB/s",
                               "frac": mbytes / (mms * 1e-3) / 1e9 / hbm,
                               "bytes_per_call": mbytes, "traffic": None}}
+        if rank == 0 and not args.no_baselines:
+            merge["oracle"] = merge_oracle_baseline(contacts.to_numpy(sort=False),
+                                                    scene.eps, members[:n_out].cpu().numpy())
 
     # ---- end to end through the public API (host inputs, host results)
     e2e = None

@@ -90,3 +90,16 @@ def test_traffic_rows_follow_the_source(tmp_path):
     assert b._source_hash() == h and b._traffic_per_launch() == {"k_tile": 1234.0}
     (csrc / "k.cu").write_text("__global__ void k() { int x = 0; }\n")
     assert b._source_hash() != h and b._traffic_per_launch() == {}
+
+
+def test_merge_oracle_baseline_reports_partition_parity():
+    """The bench's timed oracle merge compares its partition with the GPU's
+    member counts (here a hand-made list and the counts it must give)."""
+    import numpy as np
+    b = _bench()
+    pa = np.array([[0.0, 0, 0], [0.001, 0, 0], [5.0, 0, 0]])
+    c = dict(pair=np.array([0, 0, 0]), ta=np.array([1, 2, 3]), tb=np.zeros(3, int), pa=pa,
+             pb=pa + [0, 0, 0.01], d=np.full(3, 0.01))
+    r = b.merge_oracle_baseline(c, np.array([0.01]), np.array([2, 1]))
+    assert r["partition_equal"] and r["contacts_out"] == 2 and r["kind"] == "oracle"
+    assert not b.merge_oracle_baseline(c, np.array([0.01]), np.array([1, 1, 1]))["partition_equal"]
