@@ -326,3 +326,65 @@ def scene_particle_on_plane(levels=(3, 3, 4, 5), gaps=(-0.5, 0.3, 1.5, 2.5), eps
         pairs.append((2 * k, 2 * k + 1))
         eps_l.append(eps)
     return _assemble(meshes, poses, radii, pairs, eps_l, "particle-on-plane")
+
+
+def scene_packing(n: int = 64, fraction: float = 0.3, levels=(2, 3, 4), r_min: float = 1.0,
+                  r_max: float = 10.0, eps_rel: float = 0.01, overlap: float = 0.3,
+                  seed: int = 10, amp: float = 0.05, tries_per_particle: int = 200):
+    """Many-particle packing (the implicit-step workload): n bumped
+    sphere-like particles, subdivision uniform in `levels`, radius log-uniform
+    in [r_min, r_max], placed by random sequential addition, largest first,
+    in a cube sized for the requested volume fraction of the nominal spheres
+    (a particle's bounding radius 1.05 r may not overlap an earlier
+    particle's).  Random sequential addition jams well below dense packings:
+    when a particle finds no place in `tries_per_particle` attempts the cube
+    grows by 1 % and the placement goes on, so every particle is placed and
+    the achieved fraction is returned.  A share `overlap` of the particles is
+    then moved towards its nearest neighbour until their bounding spheres
+    overlap by eps / 2, so that contacts exist.  eps of a pair =
+    eps_rel * min(diameters).  The scene's pair list is empty (pairs come
+    from a broad phase).  Returns (scene, achieved fraction, velocities
+    [n, 6] = (v, omega), zero)."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng([BASE_SEED, seed, 17])
+    radius = np.sort(np.exp(rng.uniform(np.log(r_min), np.log(r_max), size=n)))[::-1]
+    R = 1.05 * radius
+    side = ((4.0 / 3.0) * np.pi * (radius ** 3).sum() / fraction) ** (1.0 / 3.0)
+    centres = np.zeros((n, 3))
+    tree, in_tree = None, 0
+    i = 0
+    while i < n:
+        ok = False
+        for _ in range(tries_per_particle):
+            c = rng.uniform(R[i], side - R[i], size=3)
+            near = list(range(in_tree, i))
+            if tree is not None:
+                near += tree.query_ball_point(c, R[i] + R[0])
+            if not near or (np.linalg.norm(centres[near] - c, axis=1) >= R[near] + R[i]).all():
+                ok = True
+                break
+        if not ok:
+            side *= 1.01
+            continue
+        centres[i] = c
+        i += 1
+        if i - in_tree >= 64:
+            tree, in_tree = cKDTree(centres[:i]), i
+    meshes, poses = [], []
+    for k in range(n):
+        meshes.append(bumped_icosphere(int(rng.choice(levels)), float(radius[k]), rng, amp))
+        poses.append(np.concatenate([centres[k], random_quaternion(rng)]))
+    poses = np.array(poses)
+    # bring some particles into contact with their nearest neighbour
+    movers = rng.choice(n, size=int(overlap * n), replace=False) if n > 1 else []
+    for k in movers:
+        d = np.linalg.norm(poses[:, :3] - poses[k, :3], axis=1)
+        d[k] = np.inf
+        j = int(np.argmin(d))
+        e = eps_rel * 2.0 * min(radius[k], radius[j])
+        shift = d[j] - (R[k] + R[j] - 0.5 * e)
+        if shift > 0:
+            poses[k, :3] += shift * (poses[j, :3] - poses[k, :3]) / d[j]
+    achieved = (4.0 / 3.0) * np.pi * (radius ** 3).sum() / side ** 3
+    s = _assemble(meshes, poses, radius, np.zeros((0, 2), np.int32), np.zeros(0), "packing")
+    return s, float(achieved), np.zeros((n, 6))

@@ -1,0 +1,129 @@
+"""FP64 CPU oracle of the implicit time step (test infrastructure only: the
+tests and bench.py's CPU-baseline leg use it; the product path never does).
+
+Broad phase: the particle pairs whose bounding spheres, each widened by the
+pair's eps, overlap, by brute force over all pairs.
+
+Implicit Euler step (Algorithm 3, with the force law of Sec. 2): the paper's
+Picard iteration.  Starting from the current velocities, repeat: find the
+contacts of every candidate pair at the guessed geometry, compute the
+contact forces and torques there, set the guessed velocities to
+v + dt (F / m + g) and omega + dt tau / I, and move the guessed geometry from
+the step's start by dt times the guessed velocities (translation of the
+centre of mass; rotation by the rotation vector dt omega, applied in the
+world frame); stop when the guessed velocities no longer change.  The
+fixed point is the implicit Euler solution; damping or acceleration of the
+iteration (Sec. 6) change the path to it, not the point, and are left out.
+
+Readings (the paper leaves them open): the particles' inertia is that of a
+solid sphere of the particle's radius, I = 2/5 m r^2 (isotropic, so no
+gyroscopic term); gravity g = (0, 0, -9.81); the contact forces are those of
+the unmerged contact set (the energy's, whose derivatives a Newton step
+uses); the particles' centres of mass are their body-frame origins.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import detect, forces
+
+G_DEFAULT = np.array([0.0, 0.0, -9.81])
+
+
+def bounding_radius(scene):
+    """Largest body-frame vertex distance from the origin, per particle."""
+    out = np.empty(scene.n_particles)
+    for i in range(scene.n_particles):
+        v, _ = scene.particle(i)
+        out[i] = np.sqrt((v.astype(np.float64) ** 2).sum(1)).max()
+    return out
+
+
+def pair_eps(radius, i, j, eps_rel=0.01):
+    """eps of a pair: eps_rel times the smaller diameter (Sec. 6 states eps
+    relative to the particle diameter)."""
+    return eps_rel * 2.0 * np.minimum(radius[i], radius[j])
+
+
+def broad_phase(centres, bound, radius, eps_rel=0.01, chunk=2048):
+    """All pairs i < j with |c_i - c_j| <= bound_i + bound_j + 2 eps_ij, by
+    brute force over all pairs; sorted by (i, j)."""
+    centres = np.asarray(centres, np.float64)
+    n = len(centres)
+    out_i, out_j = [], []
+    for a in range(0, n, chunk):
+        c = centres[a:a + chunk]
+        d = np.sqrt(((c[:, None, :] - centres[None, :, :]) ** 2).sum(-1))
+        ii = np.arange(a, a + len(c))[:, None]
+        jj = np.arange(n)[None, :]
+        lim = bound[ii] + bound[jj] + 2.0 * pair_eps(radius, ii, jj, eps_rel)
+        sel = (jj > ii) & (d <= lim)
+        i, j = np.nonzero(sel)
+        out_i.append(i + a)
+        out_j.append(j)
+    i = np.concatenate(out_i) if out_i else np.zeros(0, np.int64)
+    j = np.concatenate(out_j) if out_j else np.zeros(0, np.int64)
+    o = np.lexsort((j, i))
+    return np.stack([i[o], j[o]], 1).astype(np.int32)
+
+
+def _quat_mul(a, b):
+    w1, x1, y1, z1 = a
+    w2, x2, y2, z2 = b
+    return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2,
+                     w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2,
+                     w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+
+
+def rotvec_quat(r):
+    """Unit quaternion of the rotation by the rotation vector r."""
+    th = float(np.linalg.norm(r))
+    if th == 0.0:
+        return np.array([1.0, 0.0, 0.0, 0.0])
+    return np.concatenate([[np.cos(th / 2)], np.sin(th / 2) * np.asarray(r) / th])
+
+
+def moved_poses(poses, vel, dt):
+    """The step's geometry update: centre + dt v, orientation turned by
+    dt omega in the world frame."""
+    out = np.array(poses, np.float64, copy=True)
+    for i in range(len(out)):
+        out[i, :3] = poses[i, :3] + dt * vel[i, :3]
+        q = _quat_mul(rotvec_quat(dt * vel[i, 3:]), poses[i, 3:] / np.linalg.norm(poses[i, 3:]))
+        out[i, 3:] = q / np.linalg.norm(q)
+    return out
+
+
+def implicit_euler_step(scene, vel, pairs, eps, dt, g=G_DEFAULT, k_s=1000.0, tol=1e-13,
+                        max_iter=200):
+    """One implicit Euler step by Picard iteration (Algorithm 3).  scene:
+    meshes, poses (step start), masses; vel [n, 6] (v, omega) at the start;
+    pairs / eps: the candidate pairs and their eps.  Returns (poses, vel,
+    iterations, history of the velocity change per iteration)."""
+    import dataclasses
+    n = scene.n_particles
+    m = np.asarray(scene.mass, np.float64)
+    inertia = 0.4 * m * np.asarray(scene.radius, np.float64) ** 2
+    base = dataclasses.replace(scene, pairs=np.asarray(pairs, np.int32).reshape(-1, 2),
+                               eps=np.asarray(eps, np.float64), com=np.zeros((n, 3)))
+    v0 = np.asarray(vel, np.float64)
+    guess = v0.copy()
+    hist = []
+    for it in range(1, max_iter + 1):
+        poses = moved_poses(scene.poses, guess, dt)
+        if base.n_pairs:
+            c = detect(base, poses=poses)
+            ft, _ = forces(base, c, k_s=k_s, poses=poses)
+        else:
+            ft = np.zeros((n, 6))
+        new = np.empty_like(guess)
+        new[:, :3] = v0[:, :3] + dt * (ft[:, :3] / m[:, None] + g)
+        new[:, 3:] = v0[:, 3:] + dt * ft[:, 3:] / inertia[:, None]
+        change = float(np.abs(new - guess).max())
+        scale = float(np.abs(new).max()) + 1e-300
+        hist.append(change / scale)
+        guess = new
+        if change <= tol * scale:
+            break
+    return moved_poses(scene.poses, guess, dt), guess, it, hist

@@ -1,0 +1,188 @@
+"""Pins of the implicit-step oracle (Algorithm 3 with the force law of
+Sec. 2) and of its broad phase, against closed forms, an independent
+library search and invariants."""
+import numpy as np
+import pytest
+
+from gen import quat_to_matrix_f64, scene_packing
+
+
+@pytest.fixture(scope="module")
+def imp():
+    import oracle
+    oracle.build()
+    from oracle import implicit
+    return implicit
+
+
+def test_broad_phase_matches_kdtree(imp):
+    from scipy.spatial import cKDTree
+    s, _, _ = scene_packing(300, 0.3, seed=21)
+    c = s.poses[:, :3]
+    bound = imp.bounding_radius(s)
+    got = imp.broad_phase(c, bound, s.radius)
+    lim_max = 2 * bound.max() + 2 * 0.02 * s.radius.max()
+    cand = np.array(sorted(cKDTree(c).query_pairs(lim_max)))
+    i, j = cand[:, 0], cand[:, 1]
+    d = np.linalg.norm(c[i] - c[j], axis=1)
+    keep = d <= bound[i] + bound[j] + 2 * imp.pair_eps(s.radius, i, j)
+    want = cand[keep]
+    assert len(got) > 0
+    np.testing.assert_array_equal(got, want[np.lexsort((want[:, 1], want[:, 0]))])
+
+
+def test_broad_phase_lattice_closed_form(imp):
+    """Unit spheres on a k x k x k cubic lattice of spacing 2 + eps: each
+    pair of face neighbours touches within 2 eps, diagonal neighbours do not;
+    3 k^2 (k - 1) pairs."""
+    k = 5
+    g = np.arange(k) * 2.015
+    c = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    ones = np.ones(len(c))
+    got = imp.broad_phase(c, ones, ones)   # eps = 0.02 per pair
+    assert len(got) == 3 * k * k * (k - 1)
+    assert np.allclose(np.linalg.norm(c[got[:, 0]] - c[got[:, 1]], axis=1), 2.015)
+
+
+def _single(levels=2, radius=1.0):
+    s, _, _ = scene_packing(1, 0.1, levels=(levels,), r_min=radius, r_max=radius, seed=3)
+    return s
+
+
+def test_free_flight_closed_form(imp):
+    """No contacts: v' = v + dt g, c' = c + dt v', q' = exp(dt omega) q; the
+    first update is the fixed point (the second iteration only confirms
+    it)."""
+    s = _single()
+    vel = np.array([[0.3, -0.2, 1.0, 0.5, -1.5, 2.0]])
+    dt = 1e-3
+    poses, v, it, _ = imp.implicit_euler_step(s, vel, np.zeros((0, 2)), np.zeros(0), dt)
+    assert it == 2
+    v_want = vel[0, :3] + dt * imp.G_DEFAULT
+    np.testing.assert_allclose(v[0, :3], v_want, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(v[0, 3:], vel[0, 3:], rtol=0, atol=0)
+    np.testing.assert_allclose(poses[0, :3], s.poses[0, :3] + dt * v_want, rtol=0, atol=1e-13)
+    # orientation: rotation by dt omega about the world axis omega/|omega|
+    w = vel[0, 3:]
+    th = dt * np.linalg.norm(w)
+    ax = w / np.linalg.norm(w)
+    K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+    Rw = np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K
+    R0 = quat_to_matrix_f64(s.poses[0, 3:])
+    np.testing.assert_allclose(quat_to_matrix_f64(poses[0, 3:]), Rw @ R0, rtol=0, atol=1e-14)
+
+
+def _colliding_pair(imp, seed=4):
+    """Two particles whose meshes are within 2 eps of each other (placed by
+    the pair generator at gap 0.5 eps), approaching each other."""
+    from gen import scene_pairs
+    e = 0.02 * 1.0
+    s = scene_pairs([2], [2], [1.0], [1.2], [e], [0.5 * e], seed, "colliding", spread=5.0)
+    bound = imp.bounding_radius(s)
+    pairs = imp.broad_phase(s.poses[:, :3], bound, s.radius)
+    assert pairs.tolist() == [[0, 1]]
+    eps = imp.pair_eps(s.radius, pairs[:, 0], pairs[:, 1])
+    assert np.allclose(eps, e)
+    u = s.poses[1, :3] - s.poses[0, :3]
+    u /= np.linalg.norm(u)
+    vel = np.zeros((2, 6))
+    vel[0, :3] = 0.2 * u
+    vel[1, :3] = -0.1 * u
+    vel[:, 3:] = [[0.0, 0.3, -0.2], [0.1, 0.0, 0.4]]
+    return s, vel, pairs, eps
+
+
+def test_momentum_balance_and_convergence(imp):
+    """Contact forces are equal and opposite: the total momentum changes by
+    dt * sum(m) g exactly (rounding aside), and the Picard iteration
+    contracts to a fixed point."""
+    s, vel, pairs, eps = _colliding_pair(imp)
+    import oracle
+    c = oracle.detect(s.__class__(**{**s.__dict__, "pairs": pairs, "eps": eps}))
+    assert len(c["d"]) > 0   # the pair is in contact at the start
+    dt = 2e-4
+    _, v, it, hist = imp.implicit_euler_step(s, vel, pairs, eps, dt)
+    assert 1 < it < 200 and hist[-1] <= 1e-13
+    m = s.mass
+    p0 = (m[:, None] * vel[:, :3]).sum(0) + dt * m.sum() * imp.G_DEFAULT
+    p1 = (m[:, None] * v[:, :3]).sum(0)
+    assert np.abs(p1 - p0).max() <= 1e-12 * np.abs(m[:, None] * vel[:, :3]).sum()
+    # the contact pushed them apart: the approach speed dropped
+    u = s.poses[1, :3] - s.poses[0, :3]
+    assert (v[0, :3] - v[1, :3]) @ u < (vel[0, :3] - vel[1, :3]) @ u
+
+
+def test_galilean_and_rotation_invariance(imp):
+    """A uniform extra velocity adds to every result velocity; rotating the
+    scene, its velocities and gravity rotates the result."""
+    s, vel, pairs, eps = _colliding_pair(imp, seed=6)
+    dt = 2e-4
+    P, V, _, _ = imp.implicit_euler_step(s, vel, pairs, eps, dt)
+    w = np.array([0.05, -0.02, 0.01])
+    vel2 = vel.copy()
+    vel2[:, :3] += w
+    P2, V2, _, _ = imp.implicit_euler_step(s, vel2, pairs, eps, dt)
+    np.testing.assert_allclose(V2[:, :3] - w, V[:, :3], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(V2[:, 3:], V[:, 3:], rtol=0, atol=1e-9)
+    # rotation of everything
+    th = 0.7
+    Q = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1.0]])
+    Q = Q @ quat_to_matrix_f64(np.array([0.9, 0.1, -0.3, 0.2]) / np.linalg.norm([0.9, 0.1, -0.3, 0.2]))
+    qQ = _quat_of(Q)
+    s3 = s.__class__(**s.__dict__)
+    s3.poses = s.poses.copy()
+    for i in range(s.n_particles):
+        s3.poses[i, :3] = Q @ s.poses[i, :3]
+        s3.poses[i, 3:] = _qmul(qQ, s.poses[i, 3:])
+    vel3 = np.concatenate([vel[:, :3] @ Q.T, vel[:, 3:] @ Q.T], 1)
+    P3, V3, _, _ = imp.implicit_euler_step(s3, vel3, pairs, eps, dt, g=Q @ imp.G_DEFAULT)
+    np.testing.assert_allclose(V3[:, :3], V[:, :3] @ Q.T, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(V3[:, 3:], V[:, 3:] @ Q.T, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(P3[:, :3], P[:, :3] @ Q.T, rtol=0, atol=1e-9)
+
+
+def _quat_of(R):
+    w = np.sqrt(max(0.0, 1 + R[0, 0] + R[1, 1] + R[2, 2])) / 2
+    x = np.copysign(np.sqrt(max(0.0, 1 + R[0, 0] - R[1, 1] - R[2, 2])) / 2, R[2, 1] - R[1, 2])
+    y = np.copysign(np.sqrt(max(0.0, 1 - R[0, 0] + R[1, 1] - R[2, 2])) / 2, R[0, 2] - R[2, 0])
+    z = np.copysign(np.sqrt(max(0.0, 1 - R[0, 0] - R[1, 1] + R[2, 2])) / 2, R[1, 0] - R[0, 1])
+    q = np.array([w, x, y, z])
+    return q / np.linalg.norm(q)
+
+
+def _qmul(a, b):
+    w1, x1, y1, z1 = a
+    w2, x2, y2, z2 = b
+    return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+
+
+def test_angular_momentum_identity(imp):
+    """Each contact applies +F and -F at one point, so over an implicit Euler
+    step the total angular momentum about the origin,
+    L = sum c_i x m_i v_i + I_i omega_i, obeys
+    L' = L + dt sum c_i x m_i g - dt^2 sum v'_i x F_i
+    (F_i the total contact force on i at the end of the step): exact up to
+    rounding, so it pins the torques, the inertia and the rotation update."""
+    import dataclasses
+
+    import oracle
+    s, vel, pairs, eps = _colliding_pair(imp, seed=8)
+    dt = 5e-4
+    P, V, it, _ = imp.implicit_euler_step(s, vel, pairs, eps, dt, tol=1e-15)
+    m = s.mass
+    inertia = 0.4 * m * s.radius ** 2
+    base = dataclasses.replace(s, pairs=pairs, eps=eps, com=np.zeros((2, 3)))
+    c = oracle.detect(base, poses=P)
+    assert len(c["d"]) > 0
+    ft, _ = oracle.forces(base, c, poses=P)
+    F = ft[:, :3]
+    c0 = s.poses[:, :3]
+    L0 = (np.cross(c0, m[:, None] * vel[:, :3]) + inertia[:, None] * vel[:, 3:]).sum(0)
+    L1 = (np.cross(P[:, :3], m[:, None] * V[:, :3]) + inertia[:, None] * V[:, 3:]).sum(0)
+    want = L0 + dt * np.cross(c0, m[:, None] * imp.G_DEFAULT).sum(0) - dt ** 2 * np.cross(V[:, :3], F).sum(0)
+    scale = np.abs(np.cross(c0, m[:, None] * vel[:, :3])).sum() + np.abs(inertia[:, None] * vel[:, 3:]).sum()
+    assert np.abs(L1 - want).max() <= 1e-11 * scale, (L1 - want, scale)
+    # a wrong inertia would break it
+    L1_bad = (np.cross(P[:, :3], m[:, None] * V[:, :3]) + 1.1 * inertia[:, None] * V[:, 3:]).sum(0)
+    assert np.abs(L1_bad - want).max() > 1e-6 * scale
