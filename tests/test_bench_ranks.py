@@ -103,3 +103,14 @@ def test_merge_oracle_baseline_reports_partition_parity():
     r = b.merge_oracle_baseline(c, np.array([0.01]), np.array([2, 1]))
     assert r["partition_equal"] and r["contacts_out"] == 2 and r["kind"] == "oracle"
     assert not b.merge_oracle_baseline(c, np.array([0.01]), np.array([1, 1, 1]))["partition_equal"]
+
+
+def test_cpu_baseline_single_thread_and_model():
+    """The oracle baseline runs on a bounded sample with one thread as well as
+    all cores, and names the host CPU."""
+    from gen import scene_tiny
+    b = _bench()
+    s = scene_tiny(n_pairs=16)
+    one = b.cpu_oracle_baseline(s, 0.5, n_threads=1)
+    assert one["cores"] == 1 and one["value"] > 0 and one["kind"] == "oracle"
+    assert isinstance(b._cpu_model(), str) and b._cpu_model()
