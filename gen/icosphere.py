@@ -388,3 +388,31 @@ def scene_packing(n: int = 64, fraction: float = 0.3, levels=(2, 3, 4), r_min: f
     achieved = (4.0 / 3.0) * np.pi * (radius ** 3).sum() / side ** 3
     s = _assemble(meshes, poses, radius, np.zeros((0, 2), np.int32), np.zeros(0), "packing")
     return s, float(achieved), np.zeros((n, 6))
+
+
+def scene_disparity(n_pairs: int = 64, level_big: int = 6, level_small: int = 3,
+                    ratio: float = 20.0, eps_rel: float = 0.01, seed: int = 12, amp: float = 0.05):
+    """Size-disparity pairs (the scale study of Sec. 6 and the many-particle
+    scale workload): pair k holds a big particle (subdivision level_big,
+    radius `ratio`) and a small one (subdivision level_small, radius 1), both
+    bumped, random orientations, eps = eps_rel times the small diameter, gap
+    U[-0.5 eps, 3 eps] between the two closest aligned extreme vertices."""
+    rng = np.random.default_rng([BASE_SEED, seed, 19])
+    eps = np.full(n_pairs, eps_rel * 2.0)
+    gaps = rng.uniform(-0.5, 3.0, size=n_pairs) * eps
+    return scene_pairs(np.full(n_pairs, level_big), np.full(n_pairs, level_small),
+                       np.full(n_pairs, ratio), np.ones(n_pairs), eps, gaps, seed,
+                       f"disparity-{n_pairs}-pairs-x{ratio:g}", amp=amp)
+
+
+def scene_regular_disparate_pair(level_a: int, radius_a: float, level_b: int, radius_b: float,
+                                 centre_dist: float, qA, qB, eps: float):
+    """Two unbumped icospheres of different sizes and subdivisions at a given
+    centre distance along +x; for closed-form distances."""
+    va, fa = icosphere(level_a)
+    vb, fb = icosphere(level_b)
+    mA = ((va * radius_a).astype(np.float32), fa)
+    mB = ((vb * radius_b).astype(np.float32), fb)
+    pA = np.concatenate([[0.0, 0.0, 0.0], qA])
+    pB = np.concatenate([[centre_dist, 0.0, 0.0], qB])
+    return _assemble([mA, mB], [pA, pB], [radius_a, radius_b], [(0, 1)], [eps], "regular-disparate")

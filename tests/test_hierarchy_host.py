@@ -203,3 +203,14 @@ def test_ancestors_of_every_contact_pass_the_surrogate_test(orc, levels):
     d = orc.tri_tri(np.array(P), np.array(Q))[0]
     lim = np.array(lim)
     assert np.all(d <= lim * (1 + 1e-12)), (d - lim).max()
+
+
+def test_conservative_on_large_disparate_particles(orc):
+    """An 81,920-triangle particle (subdivision 6, radius 20) beside a small
+    one: depth 5 with leaves of 20, every surrogate conservative."""
+    from gen import scene_disparity
+    s = scene_disparity(1)
+    h = _host(s)
+    info = h.info()
+    assert info["n_tri"] == 81920 + 1280 and info["max_depth"] == 5
+    _check_conservative(orc, s, h.export())

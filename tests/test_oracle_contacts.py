@@ -191,3 +191,32 @@ def test_particle_on_plane_closed_form(orc):
         assert (c["tb"][sel] == 0).all()
     counts = np.bincount(c["pair"], minlength=s.n_pairs)
     assert counts[3] == 0 and counts[:3].min() > 0
+
+
+@pytest.mark.parametrize("la,ra,lb,rb", [(4, 20.0, 1, 1.0), (3, 8.0, 0, 1.0), (1, 1.0, 3, 4.0)])
+def test_size_disparity_vertex_aligned(orc, la, ra, lb, rb):
+    """Size disparity (Sec. 6, Tables 7 and 8): a vertex of a large regular
+    icosphere facing a vertex of a small one along x: the distance is the
+    distance of the two vertices; the brute force finds exactly that."""
+    from gen import scene_regular_disparate_pair
+    va, _ = icosphere(la)
+    vb, _ = icosphere(lb)
+    xa0 = (va[0] * ra).astype(np.float32).astype(np.float64)
+    xb0 = (vb[5] * rb).astype(np.float32).astype(np.float64)
+    qA = _quat_from_matrix(_rotation_taking(xa0, np.array([1.0, 0, 0])))
+    qB = _quat_from_matrix(_rotation_taking(xb0, np.array([-1.0, 0, 0])))
+    D = ra + rb + 0.3
+    s = scene_regular_disparate_pair(la, ra, lb, rb, D, qA, qB, eps=0.5)
+    xa = quat_to_matrix_f64(qA) @ xa0
+    xb = quat_to_matrix_f64(qB) @ xb0 + np.array([D, 0, 0])
+    expected = np.linalg.norm(xb - xa)
+    c = orc.detect(s)
+    assert len(c["d"]) > 0
+    assert abs(c["d"].min() - expected) < 1e-12 * max(1.0, ra)
+    # a vertex against a vertex: the minimum is attained by the triangle
+    # pairs around the two axis vertices only
+    fa = icosphere(la)[1]
+    fb = icosphere(lb)[1]
+    at_min = np.abs(c["d"] - expected) < 1e-9
+    assert set(c["ta"][at_min]) <= set(np.flatnonzero((fa == 0).any(1)))
+    assert set(c["tb"][at_min]) <= set(np.flatnonzero((fb == 5).any(1)))
