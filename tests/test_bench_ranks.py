@@ -114,3 +114,16 @@ def test_cpu_baseline_single_thread_and_model():
     one = b.cpu_oracle_baseline(s, 0.5, n_threads=1)
     assert one["cores"] == 1 and one["value"] > 0 and one["kind"] == "oracle"
     assert isinstance(b._cpu_model(), str) and b._cpu_model()
+
+
+def test_clock_summary_reads_samples():
+    """The clock record taken during the timed region: median SM clock, the
+    maximum, and the throttle reasons that were active."""
+    b = _bench()
+    c = b.Clocks(0)
+    c.lines = ["0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 2040, 2070, 950.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 910.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    r = c.summary()
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert b.Clocks(0).summary()["samples"] == 0
