@@ -53,3 +53,26 @@ def test_null_arguments_are_rejected():
     assert lib.mrdem_merge_contacts(None, 0, None, None, None, None, None) == -1
     assert lib.mrdem_hier_get_info(None, None) == -1
     assert lib.mrdem_destroy(None) == 0
+
+
+def test_plain_c_caller(tmp_path):
+    """The boundary is a C ABI: a C program that includes only
+    include/mrdem.h and links libmrdem.so builds trees on the host, has bad
+    input rejected with a status, and (without a GPU) gets MRDEM_ERR_CUDA from
+    mrdem_create."""
+    import subprocess
+
+    import torch
+    import paper_2105_12415_gb300 as m
+    lib = m._lib.library_path()
+    m.load()
+    exe = tmp_path / "c_abi_example"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "c_abi_example.c"), "-o", str(exe),
+                           "-L", os.path.dirname(lib), "-lmrdem",
+                           "-Wl,-rpath," + os.path.dirname(lib)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "trees: 2 particles" in r.stdout
+    if not torch.cuda.is_available():
+        assert "no GPU here" in r.stdout
