@@ -196,6 +196,15 @@ int mrdem_hier_export(const mrdem_hier* hier, float* node_tri, float* node_delta
                       int32_t* node_child, int32_t* node_level, int32_t* root,
                       int32_t* slot_tri, int32_t* slot_particle);
 
+/* Copy the oriented box of every node into node_box (host float
+ * [n_nodes*16]): centre xyz, three axes (rows, unit length up to float
+ * rounding), half extents along them, 0.  The box holds every fine vertex
+ * below the node: for each vertex v, |u_k . (v - c)| <= half_k in FP64 with
+ * the stored values.  Principal axes of the vertices' covariance.  A further
+ * conservative bound of a node's fine geometry beside surrogate + delta; the
+ * device does not use it yet.  Errors: INVALID (null pointers). */
+int mrdem_hier_export_boxes(const mrdem_hier* hier, float* node_box);
+
 /* Multiresolution contact detection (Algorithm 5 with the hybrid test of
  * Algorithm 4) for n_pairs particle pairs.  Device inputs: pair_ab [n_pairs*2]
  * int32 particle indices of hier (A, B; A != B not required), pair_eps

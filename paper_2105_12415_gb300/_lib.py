@@ -87,6 +87,7 @@ SIGNATURES = {
     "mrdem_hier_destroy": (C.c_int, [_P]),
     "mrdem_hier_get_info": (C.c_int, [_P, C.POINTER(mrdem_hier_info)]),
     "mrdem_hier_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "mrdem_hier_export_boxes": (C.c_int, [_P, _P]),
     "mrdem_detect": (C.c_int, [_P, _P, _I64, _P, _P, _P, _I, C.POINTER(mrdem_contacts), _P, _P]),
     "mrdem_check": (C.c_int, [_P, _P, _P]),
     "mrdem_contact_forces": (C.c_int, [_P, _P, _I64, _P, _P, _P, C.POINTER(mrdem_contacts), _P,

@@ -151,6 +151,9 @@ class Hierarchy:
         L.check(L.load().mrdem_hier_export(self.handle, *[_np_ptr(out[k]) for k in (
             "node_tri", "node_delta", "node_child", "node_level", "root", "slot_tri",
             "slot_particle")]), "mrdem_hier_export")
+        out["node_box"] = np.empty((nn, 16), np.float32)
+        L.check(L.load().mrdem_hier_export_boxes(self.handle, _np_ptr(out["node_box"])),
+                "mrdem_hier_export_boxes")
         return out
 
     def close(self):

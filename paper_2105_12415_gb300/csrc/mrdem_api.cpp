@@ -438,6 +438,12 @@ int mrdem_hier_export(const mrdem_hier* hier, float* node_tri, float* node_delta
   return MRDEM_OK;
 }
 
+int mrdem_hier_export_boxes(const mrdem_hier* hier, float* node_box) {
+  if (!hier || !node_box) return MRDEM_ERR_INVALID;
+  std::copy(hier->h.node_box.begin(), hier->h.node_box.end(), node_box);
+  return MRDEM_OK;
+}
+
 static int check_pair_args(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
                            const double* eps, const double* poses) {
   if (!c || !h || n_pairs < 0 || n_pairs >= (int64_t)1 << 31) return MRDEM_ERR_INVALID;

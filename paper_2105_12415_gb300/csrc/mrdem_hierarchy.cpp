@@ -313,6 +313,97 @@ float round_up_f32(double x) {
   return f;
 }
 
+// Eigenvectors of a symmetric 3x3 matrix by cyclic Jacobi rotations: each
+// rotation zeroes one off-diagonal entry; the sweeps stop when the
+// off-diagonal part is negligible.  Rows of U are the eigenvectors.
+void sym3_eigenvectors(double A[3][3], double U[3][3]) {
+  double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    const double diag = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off <= 1e-30 * diag || off == 0.0) break;
+    for (int p = 0; p < 2; ++p) {
+      for (int q = p + 1; q < 3; ++q) {
+        if (A[p][q] == 0.0) continue;
+        // the rotation angle that annihilates A[p][q]
+        const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < 3; ++k) {  // A <- A J (columns p, q)
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - sn * akq;
+          A[k][q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < 3; ++k) {  // A <- J^T A (rows p, q)
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - sn * aqk;
+          A[q][k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < 3; ++k) {  // V <- V J
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - sn * vkq;
+          V[k][q] = sn * vkp + c * vkq;
+        }
+      }
+    }
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int k = 0; k < 3; ++k) U[r][k] = V[k][r];
+}
+
+// Oriented box around a node's fine vertices: the principal axes of their
+// covariance, stored in float, the centre of their extents along those axes
+// in float, and half extents that are the largest FP64 projections
+// |u_k . (v - c)| of the vertices on the stored axes about the stored centre,
+// rounded up: the stored box contains every vertex when evaluated in FP64.
+// Layout: centre xyz, axes u0 u1 u2 (rows), half extents xyz, 0.
+void fit_box(const std::vector<D3>& pts, float box[16]) {
+  D3 m{0, 0, 0};
+  for (const D3& p : pts) m = m + p;
+  m = (1.0 / (double)pts.size()) * m;
+  double C[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (const D3& p : pts) {
+    const double d[3] = {p.x - m.x, p.y - m.y, p.z - m.z};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) C[a][b] += d[a] * d[b];
+  }
+  double U[3][3];
+  sym3_eigenvectors(C, U);
+  // orthonormalise (Gram-Schmidt) and round the axes to float
+  D3 u[3] = {{U[0][0], U[0][1], U[0][2]}, {U[1][0], U[1][1], U[1][2]}, {0, 0, 0}};
+  u[0] = (1.0 / std::sqrt(dot(u[0], u[0]))) * u[0];
+  u[1] = u[1] - dot(u[1], u[0]) * u[0];
+  u[1] = (1.0 / std::sqrt(dot(u[1], u[1]))) * u[1];
+  u[2] = cross(u[0], u[1]);
+  D3 uf[3];
+  for (int k = 0; k < 3; ++k) uf[k] = {(double)(float)u[k].x, (double)(float)u[k].y, (double)(float)u[k].z};
+  double lo[3], hi[3];
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = INFINITY;
+    hi[k] = -INFINITY;
+  }
+  for (const D3& p : pts)
+    for (int k = 0; k < 3; ++k) {
+      const double t = dot(uf[k], p - m);
+      lo[k] = std::min(lo[k], t);
+      hi[k] = std::max(hi[k], t);
+    }
+  D3 c = m;
+  for (int k = 0; k < 3; ++k) c = c + (0.5 * (lo[k] + hi[k])) * uf[k];
+  const D3 cf{(double)(float)c.x, (double)(float)c.y, (double)(float)c.z};
+  double half[3] = {0, 0, 0};
+  for (const D3& p : pts)
+    for (int k = 0; k < 3; ++k) half[k] = std::max(half[k], std::fabs(dot(uf[k], p - cf)));
+  box[0] = (float)cf.x; box[1] = (float)cf.y; box[2] = (float)cf.z;
+  for (int k = 0; k < 3; ++k) {
+    box[3 + 3 * k] = (float)uf[k].x;
+    box[4 + 3 * k] = (float)uf[k].y;
+    box[5 + 3 * k] = (float)uf[k].z;
+    box[12 + k] = round_up_f32(half[k] * (1.0 + 1e-12));
+  }
+  box[15] = 0.f;
+}
+
 struct Node {
   std::vector<int32_t> tris;  // local triangle indices below the node
   int level = 1;
@@ -320,6 +411,7 @@ struct Node {
   bool leaf = false;
   float tri[9];
   float delta = 0;
+  float box[16];  // oriented box around the fine vertices below (fit_box)
 };
 
 // Build one particle's tree (nodes in breadth-first order).
@@ -391,6 +483,7 @@ int build_particle(const mrdem_params& prm, const float* V, int nv, const int32_
       return MRDEM_ERR_INVALID;
     // exact slack of the stored triangle over every vertex below the node
     nd.delta = round_up_f32(max_dist(pts, Sf) * (1.0 + 1e-12));
+    fit_box(pts, nd.box);
   }
   return MRDEM_OK;
 }
@@ -437,6 +530,7 @@ int build_hierarchy_host(const mrdem_params& prm, int32_t n, const int64_t* vert
   if (h.n_nodes >= (int64_t)1 << 31 || h.n_tri_pad >= (int64_t)1 << 31) return MRDEM_ERR_INVALID;
   h.node_tri.resize(h.n_nodes * 9);
   h.node_delta.resize(h.n_nodes);
+  h.node_box.resize(h.n_nodes * 16);
   h.node_child.resize(h.n_nodes * 2);
   h.node_level.resize(h.n_nodes);
   h.root.resize(n);
@@ -464,6 +558,7 @@ int build_hierarchy_host(const mrdem_params& prm, int32_t n, const int64_t* vert
       auto& nd = nodes[q];
       std::memcpy(&h.node_tri[g * 9], nd.tri, sizeof(nd.tri));
       h.node_delta[g] = nd.delta;
+      std::memcpy(&h.node_box[g * 16], nd.box, sizeof(nd.box));
       h.node_level[g] = nd.level;
       depth = std::max(depth, nd.level);
       if (nd.leaf) {

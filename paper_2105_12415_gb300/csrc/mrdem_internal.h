@@ -20,6 +20,7 @@ struct HierHost {
   int64_t n_nodes = 0, n_tri = 0, n_tri_pad = 0, n_verts = 0;
   std::vector<float> node_tri;      // [n_nodes * 9]
   std::vector<float> node_delta;    // [n_nodes]
+  std::vector<float> node_box;      // [n_nodes * 16] oriented box (host only so far)
   std::vector<int32_t> node_child;  // [n_nodes * 2] (begin, count); count < 0: leaf slots
   std::vector<int32_t> node_level;  // [n_nodes]
   std::vector<int32_t> root;        // [n_particles]

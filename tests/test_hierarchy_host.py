@@ -214,3 +214,103 @@ def test_conservative_on_large_disparate_particles(orc):
     info = h.info()
     assert info["n_tri"] == 81920 + 1280 and info["max_depth"] == 5
     _check_conservative(orc, s, h.export())
+
+
+def _box_contains_all(ex, scene, node, box):
+    slots = _fine_tris_below(ex, node)
+    part = int(ex["slot_particle"][slots[0]])
+    v, t = scene.particle(part)
+    V = v[np.unique(t[ex["slot_tri"][slots]].ravel())].astype(np.float64)
+    c = box[0:3].astype(np.float64)
+    U = box[3:12].reshape(3, 3).astype(np.float64)
+    half = box[12:15].astype(np.float64)
+    proj = np.abs((V - c) @ U.T)
+    return bool((proj <= half).all()), U, half, V
+
+
+@pytest.mark.parametrize("which", ["c1", "disparity"])
+def test_node_boxes_contain_their_fine_vertices(which):
+    """Every node's oriented box holds every fine vertex below it, exactly
+    in FP64 with the stored float values; the axes are orthonormal to float
+    rounding; no half extent exceeds the node's vertex spread."""
+    from gen import scene_disparity
+    s = scene_c1() if which == "c1" else scene_disparity(1)
+    ex = _host(s).export()
+    boxes = ex["node_box"]
+    assert boxes.shape == (len(ex["node_delta"]), 16)
+    step = 1 if which == "c1" else 7
+    for node in range(0, len(boxes), step):
+        ok, U, half, V = _box_contains_all(ex, s, node, boxes[node])
+        assert ok, node
+        assert np.abs(U @ U.T - np.eye(3)).max() < 1e-6
+        spread = np.linalg.norm(V.max(0) - V.min(0))
+        assert half.max() <= spread
+
+
+def test_box_of_a_cuboid_is_the_cuboid():
+    """A cuboid with sides 4 > 2 > 1, turned and moved: the principal axes of
+    its 8 corners are its edges, so its box is the cuboid itself (half
+    extents 2, 1, 0.5, centre its centre)."""
+    from gen.icosphere import _assemble
+    rng = np.random.default_rng(5)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    corners = np.array([[x, y, z] for x in (-2, 2) for y in (-1, 1) for z in (-0.5, 0.5)], float)
+    c0 = np.array([0.25, -0.5, 0.125])
+    verts = (corners @ Q.T + c0).astype(np.float32)
+    faces = np.array([[0, 1, 3], [0, 3, 2], [4, 6, 7], [4, 7, 5], [0, 4, 5], [0, 5, 1],
+                      [2, 3, 7], [2, 7, 6], [0, 2, 6], [0, 6, 4], [1, 5, 7], [1, 7, 3]], np.int32)
+    s = _assemble([(verts, faces)], [[0, 0, 0, 1, 0, 0, 0]], [2.3], np.zeros((0, 2)), [], "cuboid")
+    ex = _host(s).export()
+    box = ex["node_box"][ex["root"][0]]
+    np.testing.assert_allclose(np.sort(box[12:15]), [0.5, 1.0, 2.0], rtol=1e-6)
+    np.testing.assert_allclose(box[0:3], c0, atol=1e-6)
+    U = box[3:12].reshape(3, 3)
+    # each axis is parallel to one cuboid edge direction
+    assert np.allclose(np.sort(np.abs(U @ Q).max(1)), 1.0, atol=1e-6)
+
+
+def test_boxes_prune_leaf_pairs_the_surrogates_keep(orc):
+    """The purpose of the boxes: on the one-pair workload, of the leaf pairs
+    that pass the exact surrogate test (delta_a + delta_b + 2 eps), the
+    six face axes of the two boxes separate a good share by more than 2 eps,
+    and never one that holds a fine pair within 2 eps."""
+    s = scene_c1()
+    ex = _host(s).export()
+    boxes = ex["node_box"]
+    c = orc.detect(s)
+    R = [orc.pose_matrix(s.poses[i]) for i in range(2)]
+
+    def world_box(i, k):
+        b = boxes[k].astype(np.float64)
+        return (R[i] @ b[0:3] + s.poses[i][:3], b[3:12].reshape(3, 3) @ R[i].T, b[12:15])
+
+    def separated(A, B, gap):
+        for ax in list(A[1]) + list(B[1]):
+            ra = np.abs(A[1] @ ax) @ A[2]
+            rb = np.abs(B[1] @ ax) @ B[2]
+            if abs((B[0] - A[0]) @ ax) > ra + rb + gap:
+                return True
+        return False
+
+    leaves = [[k for k in range(len(boxes)) if ex["node_child"][k, 1] < 0 and
+               ex["slot_particle"][ex["node_child"][k, 0]] == i] for i in range(2)]
+    slot_leaf = {}
+    for i in range(2):
+        for k in leaves[i]:
+            b, n = ex["node_child"][k]
+            for sl in range(b, b - n):
+                slot_leaf[(i, int(ex["slot_tri"][sl]))] = k
+    contact_leaves = {(slot_leaf[(0, int(a))], slot_leaf[(1, int(b))]) for a, b in zip(c["ta"], c["tb"])}
+    P, Q, lim, keys = [], [], [], []
+    for ka in leaves[0]:
+        for kb in leaves[1]:
+            P.append((ex["node_tri"][ka].reshape(3, 3).astype(np.float64) @ R[0].T + s.poses[0][:3]).ravel())
+            Q.append((ex["node_tri"][kb].reshape(3, 3).astype(np.float64) @ R[1].T + s.poses[1][:3]).ravel())
+            lim.append(ex["node_delta"][ka] + ex["node_delta"][kb] + 2 * s.eps[0])
+            keys.append((ka, kb))
+    d = orc.tri_tri(np.array(P), np.array(Q))[0]
+    passing = [keys[i] for i in np.flatnonzero(d <= np.array(lim))]
+    cut = [k for k in passing if separated(world_box(0, k[0]), world_box(1, k[1]), 2 * s.eps[0])]
+    assert contact_leaves <= set(passing)
+    assert not (set(cut) & contact_leaves)
+    assert len(cut) >= 0.2 * len(passing), (len(cut), len(passing))
