@@ -1,0 +1,136 @@
+"""Precision report: the largest error of each GPU output against the FP64
+oracle, for the FP32 and FP64 forms, on the parity workloads.
+
+Run on a GPU host (not collected by pytest):
+
+    python tests/precision_report.py profiles/precision_report.md
+
+Outputs and how their errors are measured (the same quantities the parity
+tests bound):
+  contact set      contacts missing / extra against the oracle, and how many
+                   of those lie within 1e-6 eps of the threshold 2 eps;
+  distance         max |d - d_ref| / max(d_ref, eps) over the common contacts;
+  closest points   max |p_a - p_a,ref| / eps over common contacts with d > 0;
+  force, torque    per particle max |F - F_ref| / sum_c |F_c| (torque: over
+                   sum_c |F_c| times the largest lever);
+  energy           |E - E_ref| / E_ref;
+  pose gradient    max |g - g_ref| / max |g_ref| (the differentiation
+                   workload, which has no touching pairs);
+  Jacobian blocks  max |J - J_ref| / max |J_ref|;
+  vertex gradient  max |g - g_ref| / max |g_ref| (a float output).
+"""
+from __future__ import annotations
+
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+
+def _workloads():
+    from gen import scene_c1, scene_c2, scene_c3, scene_disparity, scene_particle_on_plane
+    c2 = scene_c2()
+    ntri = np.diff(c2.tri_off)
+    small = [k for k in range(0, c2.n_pairs, 8)
+             if ntri[c2.pairs[k, 0]] * ntri[c2.pairs[k, 1]] <= 1280 * 5120][:48]
+    return [("one pair, 1280 triangles", scene_c1(), False),
+            ("batched workload, 48 sampled pairs", c2.subset(small), False),
+            ("differentiation, 8 pairs of 5120", scene_c3().subset(np.arange(0, 1024, 128)), True),
+            ("particle on plane", scene_particle_on_plane(), False),
+            ("size disparity 20:1, 2 pairs", scene_disparity(2), False)]
+
+
+def _contact_errors(got, ref, scene):
+    key = lambda c: list(zip(c["pair"].tolist(), c["ta"].tolist(), c["tb"].tolist()))  # noqa: E731
+    kg, kr = key(got), key(ref)
+    sg, sr = set(kg), set(kr)
+    dref = dict(zip(kr, ref["d"].tolist()))
+    dgot = dict(zip(kg, got["d"].tolist()))
+    eps = scene.eps
+    near = lambda k, d: abs(d - 2 * eps[k[0]]) <= 1e-6 * eps[k[0]]  # noqa: E731
+    missing = sr - sg
+    extra = sg - sr
+    common = sorted(sg & sr)
+    gi = {k: i for i, k in enumerate(kg)}
+    ri = {k: i for i, k in enumerate(kr)}
+    derr = perr = 0.0
+    for k in common:
+        e = eps[k[0]]
+        derr = max(derr, abs(dgot[k] - dref[k]) / max(dref[k], e))
+        if dref[k] > 0:
+            perr = max(perr, float(np.linalg.norm(got["pa"][gi[k]] - ref["pa"][ri[k]])) / e)
+    return {"missing": len(missing), "missing_in_band": sum(near(k, dref[k]) for k in missing),
+            "extra": len(extra), "extra_in_band": sum(near(k, dgot[k]) for k in extra),
+            "distance": derr, "points": perr, "common": len(common)}
+
+
+def _force_errors(ft, e, ft_ref, e_ref, ref, scene):
+    mu = 1 / (1 / scene.mass[scene.pairs[:, 0]] + 1 / scene.mass[scene.pairs[:, 1]])
+    mag = 1000 * np.sqrt(mu[ref["pair"]]) * (1 - ref["d"] / (2 * scene.eps[ref["pair"]]))
+    tot = np.zeros(scene.n_particles)
+    for col in (0, 1):
+        np.add.at(tot, scene.pairs[ref["pair"], col], mag)
+    lever = 2 * (scene.radius.max() + np.abs(scene.poses[:, :3]).max())
+    has = tot > 0
+    f = np.abs(ft[:, :3] - ft_ref[:, :3]).max(1)[has] / tot[has] if has.any() else np.zeros(1)
+    t = np.abs(ft[:, 3:] - ft_ref[:, 3:]).max(1)[has] / (tot[has] * lever) if has.any() else np.zeros(1)
+    return {"force": float(f.max()), "torque": float(t.max()),
+            "energy": abs(e - e_ref) / max(e_ref, 1e-300)}
+
+
+def main(out_path=None):
+    import torch
+
+    import oracle
+    import paper_2105_12415_gb300 as m
+    if not torch.cuda.is_available():
+        raise SystemExit("needs a GPU")
+    m.build()
+    oracle.build()
+    ctx = m.Context(0)
+    dev = torch.device("cuda:0")
+    rows = []
+    for name, s, grads in _workloads():
+        ref = oracle.detect(s)
+        ft_ref, e_ref = oracle.forces(s, ref)
+        gref = oracle.grad(s, ref) if grads else None
+        hier = m.Hierarchy.from_scene(ctx, s)
+        for form in ("fp32", "fp64"):
+            prob = m.ContactProblem.from_scene(ctx, hier, s, dev, precision=form)
+            c, _ = prob.detect()
+            got = c.to_numpy()
+            row = {"workload": name, "form": form, "contacts": len(ref["d"])}
+            row.update(_contact_errors(got, ref, s))
+            ft, e = prob.forces()
+            row.update(_force_errors(ft.cpu().numpy(), float(e.item()), ft_ref, e_ref, ref, s))
+            if grads:
+                gv, gp, jac = prob.grad(want_jac=True)
+                gv_ref, gp_ref, jac_ref = gref
+                row["pose_grad"] = float(np.abs(gp.cpu().numpy() - gp_ref).max() / np.abs(gp_ref).max())
+                row["jacobian"] = float(np.abs(jac.cpu().numpy().reshape(jac_ref.shape) - jac_ref).max()
+                                        / np.abs(jac_ref).max())
+                row["vertex_grad"] = float(np.abs(gv.cpu().numpy() - gv_ref).max() / np.abs(gv_ref).max())
+            rows.append(row)
+            print(row, flush=True)
+    cols = ["workload", "form", "contacts", "missing", "missing_in_band", "extra", "extra_in_band",
+            "distance", "points", "force", "torque", "energy", "pose_grad", "jacobian", "vertex_grad"]
+    fmt = lambda v: (f"{v:.2e}" if isinstance(v, float) else str(v))  # noqa: E731
+    lines = ["| " + " | ".join(cols) + " |", "|" + "---|" * len(cols)]
+    for r in rows:
+        lines.append("| " + " | ".join(fmt(r.get(k, "")) for k in cols) + " |")
+    text = "\n".join(lines) + "\n"
+    print(text)
+    if out_path:
+        how = __doc__[__doc__.index("Outputs and how"):].strip()
+        with open(out_path, "w") as f:
+            f.write("# Precision report: GPU outputs against the FP64 oracle\n\n"
+                    f"Command: `python tests/precision_report.py {out_path}`\n\n"
+                    f"{how}\n\n{text}")
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else None)
