@@ -37,6 +37,7 @@ FLOPS_PER_SPHERE_TEST = 11      # bounding-sphere test of a fine pair
 FLOPS_PER_FINE_VS_SURR = 18     # fine triangle's sphere vs a surrogate's plane and node sphere
 FLOPS_PER_TILE = 40             # per leaf pair: B's surrogate plane and sphere into A's frame
 FLOPS_PER_EXPAND_TEST = 29      # child-pair sphere test incl. moving B's centre (9 FFMA)
+FLOPS_PER_BOX_TEST = 360        # oriented-box test: B's box into A's frame (63) + six axes (297)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -460,6 +461,9 @@ def main():
     tiles = int(st[m._lib.MRDEM_STAT_TILES])
     fvs = int(st[m._lib.MRDEM_STAT_FINE_SURROGATE])
     expand_tests = int(st[1:m._lib.MRDEM_STAT_LEVELS].sum())
+    # every child pair that passed the sphere test got the box test: those
+    # it pruned and those that went on to the sweep
+    box_tests = int(st[m._lib.MRDEM_STAT_BOX_PRUNED]) + level_sweeps
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -472,7 +476,7 @@ def main():
              "k_sweep_nodes": level_sweeps * FLOPS_PER_NODE_SWEEP,
              "k_tile": tiles * FLOPS_PER_TILE + fvs * FLOPS_PER_FINE_VS_SURR
              + sphere_tests * FLOPS_PER_SPHERE_TEST,
-             "k_expand": expand_tests * FLOPS_PER_EXPAND_TEST}
+             "k_expand": expand_tests * FLOPS_PER_EXPAND_TEST + box_tests * FLOPS_PER_BOX_TEST}
     rl = {}
     for k, f in flops.items():
         if k in prof:
@@ -611,7 +615,8 @@ def main():
         "stats": {"tests_per_level": [int(x) for x in st[0:6]],
                   "survivors_per_level": [int(x) for x in st[8:14]],
                   "leaf_tiles": int(st[16]), "sphere_tests": sphere_tests,
-                  "level_sweeps": level_sweeps, "fine_vs_surrogate": int(st[23]),
+                  "level_sweeps": level_sweeps, "box_pruned": int(st[m._lib.MRDEM_STAT_BOX_PRUNED]),
+                  "fine_vs_surrogate": int(st[23]),
                   "fine_tests": fine_tests, "fine_sweeps": fine_sweeps, "candidates": int(st[18]),
                   "unconverged": int(st[19]), "contacts": n_contacts, "fp64_refinements": int(st[21]),
                   "fp64_items": [int(st[m._lib.MRDEM_STAT_ITEMS_PT]), int(st[m._lib.MRDEM_STAT_ITEMS_EE])],

@@ -86,6 +86,8 @@ typedef struct CUstream_st* mrdem_stream; /* same type as cudaStream_t */
                                      separate, given the iterative sweep */
 #define MRDEM_STAT_ITEMS_PT 28   /* FP32 form: point-triangle sub-tests finished in double-float */
 #define MRDEM_STAT_ITEMS_EE 29   /* FP32 form: edge-edge sub-tests finished in double-float */
+#define MRDEM_STAT_BOX_PRUNED 30 /* child node pairs that passed the sphere test and were pruned
+                                    by the oriented boxes around their fine vertices */
 #define MRDEM_STAT_COUNT 32
 
 typedef struct mrdem_params {
@@ -201,8 +203,10 @@ int mrdem_hier_export(const mrdem_hier* hier, float* node_tri, float* node_delta
  * rounding), half extents along them, 0.  The box holds every fine vertex
  * below the node: for each vertex v, |u_k . (v - c)| <= half_k in FP64 with
  * the stored values.  Principal axes of the vertices' covariance.  A further
- * conservative bound of a node's fine geometry beside surrogate + delta; the
- * device does not use it yet.  Errors: INVALID (null pointers). */
+ * conservative bound of a node's fine geometry beside surrogate + delta: the
+ * detection prunes child node pairs whose boxes a face axis separates by more
+ * than 2 eps (plus the pair's rounding margin).  Errors: INVALID (null
+ * pointers). */
 int mrdem_hier_export_boxes(const mrdem_hier* hier, float* node_box);
 
 /* Multiresolution contact detection (Algorithm 5 with the hybrid test of

@@ -38,6 +38,7 @@ MRDEM_STAT_NOALLOC_INVALID = 26
 MRDEM_STAT_FINE_SWEEPS = 27
 MRDEM_STAT_ITEMS_PT = 28
 MRDEM_STAT_ITEMS_EE = 29
+MRDEM_STAT_BOX_PRUNED = 30
 MRDEM_STAT_COUNT = 32
 
 

@@ -267,8 +267,9 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
   size_t sz_slot = al(sizeof(int32_t) * stride), sz_ts = al(sizeof(int32_t) * h.n_tri);
   size_t sz_off = al(sizeof(int64_t) * (h.n_particles + 1));
   size_t sz_root = al(sizeof(int32_t) * h.n_particles), sz_br = al(sizeof(float) * h.n_particles);
+  size_t sz_box = al(sizeof(float4) * 4 * h.n_nodes);
   size_t total = sz_geo + sz_child + sz_tri + sz_vid + sz_slot + sz_ts + sz_off + sz_root + sz_br +
-                 sz_sph + sz_nrm + sz_tsph;
+                 sz_sph + sz_nrm + sz_tsph + sz_box;
   char* base = nullptr;
   if (cudaMalloc(&base, total) != cudaSuccess) {
     cudaGetLastError();
@@ -280,7 +281,7 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     size_t o_geo = 0, o_child = o_geo + sz_geo, o_tri = o_child + sz_child, o_vid = o_tri + sz_tri;
     size_t o_slot = o_vid + sz_vid, o_ts = o_slot + sz_slot, o_off = o_ts + sz_ts;
     size_t o_root = o_off + sz_off, o_br = o_root + sz_root, o_sph = o_br + sz_br;
-    size_t o_nrm = o_sph + sz_sph, o_tsph = o_nrm + sz_nrm;
+    size_t o_nrm = o_sph + sz_sph, o_tsph = o_nrm + sz_nrm, o_box = o_tsph + sz_tsph;
     float4* geo = (float4*)(p + o_geo);
     for (int64_t n = 0; n < h.n_nodes; ++n) {
       const float* t = &h.node_tri[9 * n];
@@ -327,6 +328,15 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
       for (int k = 0; k < 3; ++k) nn[k] /= l;
       nrm[n] = make_float4((float)nn[0], (float)nn[1], (float)nn[2],
                            (float)(nn[0] * t[0] + nn[1] * t[1] + nn[2] * t[2]));
+    }
+    // oriented boxes: (c.xyz, h0) (u0.xyz, h1) (u1.xyz, h2) (u2.xyz, 0)
+    float4* box = (float4*)(p + o_box);
+    for (int64_t n = 0; n < h.n_nodes; ++n) {
+      const float* b = &h.node_box[16 * n];
+      box[4 * n + 0] = make_float4(b[0], b[1], b[2], b[12]);
+      box[4 * n + 1] = make_float4(b[3], b[4], b[5], b[13]);
+      box[4 * n + 2] = make_float4(b[6], b[7], b[8], b[14]);
+      box[4 * n + 3] = make_float4(b[9], b[10], b[11], 0.f);
     }
     std::memcpy(p + o_child, h.node_child.data(), sizeof(int32_t) * 2 * h.n_nodes);
     float* tri = (float*)(p + o_tri);
@@ -376,6 +386,7 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     d.node_sph = (const float4*)(base + o_sph);
     d.node_nrm = (const float4*)(base + o_nrm);
     d.tri_sph = (const float4*)(base + o_tsph);
+    d.node_box = (const float4*)(base + o_box);
     d.stride = stride;
     d.n_tri = h.n_tri;
     d.n_particles = h.n_particles;

@@ -164,7 +164,8 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
 // every lane busy:
 //   k_expand       the child pairs of surviving node pairs get a bounding-
 //                  sphere test (node spheres precomputed in the body frame,
-//                  radius including delta); a warp takes up to 32 level
+//                  radius including delta), then a separating-axis test of
+//                  oriented boxes around their fine vertices; a warp takes up to 32 level
 //                  items (fewer when the level is small, so that every
 //                  resident warp has work) and deals their child pairs out
 //                  to its lanes (near the leaves an item often has only 2 or
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
   int64_t n_in = (int64_t)cnt[CNT_LEVEL + level];
   if (n_in > cap_level) n_in = cap_level;
   const int slot_tests = MRDEM_STAT_TESTS + (level + 1 < MRDEM_STAT_LEVELS ? level + 1 : MRDEM_STAT_LEVELS - 1);
-  WarpCount tests;
+  WarpCount tests, boxcut;
   WarpQueue<int4, 128> outq;
   outq.buf = sq[w];
   // items per warp and pass: the smallest power of two that spreads the
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
       const int r = act ? f - soff[w][l] : 0;
       const int i = (int)(((float)r + 0.5f) * (1.0f / (float)(nb > 0 ? nb : 1)));
       const int j = r - i * nb;
-      bool keep = false;
+      bool keep = false, boxed = false;
       if (act) {
         PairXf X;
         load_pairxf(xf, o.x, X);
@@ -242,8 +243,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
         float dx = p.x - cq.x, dy = p.y - cq.y, dz = p.z - cq.z;
         float lim = p.w + q.w + X.tau + X.margin;
         keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
+        // the oriented boxes of the two children's fine geometry, 2 eps
+        // apart (plus the pair's rounding margin): no fine pair below them
+        // can be a contact
+        if (keep) {
+          boxed = boxes_apart(load_box(H, o.y + i), move_box(X, load_box(H, o.z + j)),
+                              X.tau + X.margin);
+          keep = !boxed;
+        }
       }
       tests.add(act);
+      boxcut.add(boxed);
       outq.push(keep, make_int4(o.x, o.y + i, o.z + j, 0), sweep, cnt + CNT_SWEEP + level, cap_sweep,
                 status + ST_REQ_SWEEP);
     }
@@ -251,6 +261,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
   }
   outq.flush(sweep, cnt + CNT_SWEEP + level, cap_sweep, status + ST_REQ_SWEEP);
   tests.flush(cnt + CNT_STATS + slot_tests);
+  boxcut.flush(cnt + CNT_STATS + MRDEM_STAT_BOX_PRUNED);
 }
 
 // k_sweep_nodes ---------------------------------------------------------------

@@ -121,6 +121,62 @@ __device__ __forceinline__ F3 xf_point(const PairXf& X, F3 v) {
           fmaf(X.R[3], v.x, fmaf(X.R[4], v.y, fmaf(X.R[5], v.z, X.t[1]))),
           fmaf(X.R[6], v.x, fmaf(X.R[7], v.y, fmaf(X.R[8], v.z, X.t[2])))};
 }
+// A node's oriented box (body frame): centre, unit axes (rows), half
+// extents; it holds every fine vertex below the node (built on the host).
+struct NodeBox {
+  F3 c;
+  F3 u[3];
+  float h[3];
+};
+__device__ __forceinline__ NodeBox load_box(const HierDev& H, int node) {
+  const float4* b = H.node_box + 4 * (int64_t)node;
+  const float4 a = __ldg(b), x = __ldg(b + 1), y = __ldg(b + 2), z = __ldg(b + 3);
+  NodeBox o;
+  o.c = {a.x, a.y, a.z};
+  o.u[0] = {x.x, x.y, x.z};
+  o.u[1] = {y.x, y.y, y.z};
+  o.u[2] = {z.x, z.y, z.z};
+  o.h[0] = a.w;
+  o.h[1] = x.w;
+  o.h[2] = y.w;
+  return o;
+}
+// B's box moved into A's frame: centre by the pair transform, axes rotated.
+__device__ __forceinline__ NodeBox move_box(const PairXf& X, const NodeBox& b) {
+  NodeBox o;
+  o.c = xf_point(X, b.c);
+  for (int k = 0; k < 3; ++k) {
+    const F3 v = b.u[k];
+    o.u[k] = {fmaf(X.R[0], v.x, fmaf(X.R[1], v.y, X.R[2] * v.z)),
+              fmaf(X.R[3], v.x, fmaf(X.R[4], v.y, X.R[5] * v.z)),
+              fmaf(X.R[6], v.x, fmaf(X.R[7], v.y, X.R[8] * v.z))};
+    o.h[k] = b.h[k];
+  }
+  return o;
+}
+// Half width of a box along an axis a: sum_k h_k |a . u_k|.
+__device__ __forceinline__ float box_half_width(const NodeBox& b, F3 a) {
+  float r = 0.f;
+  for (int k = 0; k < 3; ++k)
+    r = fmaf(b.h[k], fabsf(fmaf(a.x, b.u[k].x, fmaf(a.y, b.u[k].y, a.z * b.u[k].z))), r);
+  return r;
+}
+// True when one of the six face axes separates the two boxes (same frame)
+// by more than gap: along that axis the centres are farther apart than the
+// two half widths plus gap, so no point of one box comes within gap of the
+// other (a separating-axis test; conservative for any choice of axes).
+__device__ __forceinline__ bool boxes_apart(const NodeBox& A, const NodeBox& B, float gap) {
+  const F3 d = {B.c.x - A.c.x, B.c.y - A.c.y, B.c.z - A.c.z};
+  bool apart = false;
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    const F3 a = s < 3 ? A.u[s] : B.u[s - 3];
+    const float dist = fabsf(fmaf(a.x, d.x, fmaf(a.y, d.y, a.z * d.z)));
+    apart = apart || dist > box_half_width(A, a) + box_half_width(B, a) + gap;
+  }
+  return apart;
+}
+
 __device__ __forceinline__ D3 xf_point64(const double* R, const double* t, D3 v) {
   return {R[0] * v.x + R[1] * v.y + R[2] * v.z + t[0], R[3] * v.x + R[4] * v.y + R[5] * v.z + t[1],
           R[6] * v.x + R[7] * v.y + R[8] * v.z + t[2]};

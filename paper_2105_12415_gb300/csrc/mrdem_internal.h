@@ -20,7 +20,7 @@ struct HierHost {
   int64_t n_nodes = 0, n_tri = 0, n_tri_pad = 0, n_verts = 0;
   std::vector<float> node_tri;      // [n_nodes * 9]
   std::vector<float> node_delta;    // [n_nodes]
-  std::vector<float> node_box;      // [n_nodes * 16] oriented box (host only so far)
+  std::vector<float> node_box;      // [n_nodes * 16] oriented box: c, u0, u1, u2, h, 0
   std::vector<int32_t> node_child;  // [n_nodes * 2] (begin, count); count < 0: leaf slots
   std::vector<int32_t> node_level;  // [n_nodes]
   std::vector<int32_t> root;        // [n_particles]
@@ -45,6 +45,8 @@ struct HierDev {
   const float4* tri;       // [stride*3]: slot s's vertices as one 48-B record,
                            // (v0.xyz v1.x) (v1.yz v2.xy) (v2.z 0 0 0)
   const float4* tri_sph;   // [stride]: body-frame bounding sphere of each fine triangle
+  const float4* node_box;  // [n_nodes*4]: oriented box around the node's fine vertices,
+                           // (c.xyz, h0) (u0.xyz, h1) (u1.xyz, h2) (u2.xyz, 0)
   const int32_t* vid;      // 3 planes: global vertex index of corner k of slot s
   const int32_t* slot_tri; // [stride] local input triangle index (-1 pad)
   const int32_t* tri_slot; // [n_tri] global input triangle -> slot

@@ -39,6 +39,8 @@ def test_c1_one_pair_full_parity(gctx, orc, precision):
     assert stats[20] == len(got["d"])
     # the hierarchy pruned: far fewer fine tests than 1280^2
     assert 0 < stats[17] < 0.1 * 1280 * 1280
+    # the oriented boxes pruned child pairs the spheres let through
+    assert stats[30] > 0
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
