@@ -186,3 +186,21 @@ def test_angular_momentum_identity(imp):
     # a wrong inertia would break it
     L1_bad = (np.cross(P[:, :3], m[:, None] * V[:, :3]) + 1.1 * inertia[:, None] * V[:, 3:]).sum(0)
     assert np.abs(L1_bad - want).max() > 1e-6 * scale
+
+
+@pytest.mark.parametrize("seed", [4, 6, 8])
+def test_newton_and_picard_reach_the_same_step(imp, seed):
+    """Two different solvers of the implicit Euler equations, the paper's
+    Picard iteration and Newton's method with the Gauss-Newton contact
+    stiffness, converge to the same velocities and poses.  (Both converge
+    linearly here: the Gauss-Newton blocks leave out the negative tangential
+    stiffness e'(d) Hess(d) of vertex and edge contacts.)"""
+    s, vel, pairs, eps = _colliding_pair(imp, seed=seed)
+    dt = 5e-4
+    # Picard stops at its rounding floor (about 5e-14 change per iteration)
+    P1, V1, it1, hist = imp.implicit_euler_step(s, vel, pairs, eps, dt, tol=2e-13, max_iter=1000)
+    P2, V2, it2 = imp.implicit_euler_step_newton(s, vel, pairs, eps, dt, tol=1e-12, max_iter=1000)
+    assert it1 < 1000 and it2 < 1000, (it1, it2)
+    scale = np.abs(V1).max()
+    assert np.abs(V1 - V2).max() <= 1e-10 * scale, (np.abs(V1 - V2).max(), scale, it1, it2)
+    np.testing.assert_allclose(P2[:, :3], P1[:, :3], rtol=0, atol=1e-12)
