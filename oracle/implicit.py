@@ -130,7 +130,7 @@ def implicit_euler_step(scene, vel, pairs, eps, dt, g=G_DEFAULT, k_s=1000.0, tol
 
 
 def implicit_euler_step_newton(scene, vel, pairs, eps, dt, g=G_DEFAULT, k_s=1000.0, tol=1e-13,
-                               max_iter=100):
+                               max_iter=100, stiffness="gauss-newton"):
     """The same implicit Euler step solved by Newton's method in the
     velocities instead of Picard: residual
       r_i = M_i (V_i - V0_i) / dt - (F_i, tau_i)(geometry moved by dt V) - (m_i g, 0)
@@ -138,7 +138,9 @@ def implicit_euler_step_newton(scene, vel, pairs, eps, dt, g=G_DEFAULT, k_s=1000
     the pairs' Gauss-Newton blocks sum e''(d) J J^T (the contact stiffness in
     the pose unknowns, barycentrics frozen).  The residual is exact, so the
     converged velocities are the implicit Euler solution; an approximate
-    Jacobian only slows the convergence.  Returns (poses, vel, iterations)."""
+    Jacobian only slows the convergence.  stiffness="hessian" uses the full
+    pose Hessian (`pose_hessian`, closest points free) instead of the blocks.
+    Returns (poses, vel, iterations)."""
     import dataclasses
 
     from . import grad
@@ -159,10 +161,13 @@ def implicit_euler_step_newton(scene, vel, pairs, eps, dt, g=G_DEFAULT, k_s=1000
         if base.n_pairs:
             c = detect(base, poses=poses)
             ft, _ = forces(base, c, k_s=k_s, poses=poses)
-            _, _, jac = grad(base, c, k_s=k_s, poses=poses)
-            for p, (a, b) in enumerate(pairs):
-                idx = np.r_[6 * a:6 * a + 6, 6 * b:6 * b + 6]
-                K[np.ix_(idx, idx)] += jac[p]
+            if stiffness == "hessian":
+                K = pose_hessian(scene, poses, pairs, eps, k_s=k_s)
+            else:
+                _, _, jac = grad(base, c, k_s=k_s, poses=poses)
+                for p, (a, b) in enumerate(pairs):
+                    idx = np.r_[6 * a:6 * a + 6, 6 * b:6 * b + 6]
+                    K[np.ix_(idx, idx)] += jac[p]
         else:
             ft = np.zeros((n, 6))
         r = (Mdiag * (V - v0).ravel()) / dt - ft.ravel() - gext.ravel()
@@ -172,3 +177,45 @@ def implicit_euler_step_newton(scene, vel, pairs, eps, dt, g=G_DEFAULT, k_s=1000
         dV = np.linalg.solve(np.diag(Mdiag / dt) + dt * K, -r)
         V = V + dV.reshape(n, 6)
     return moved_poses(scene.poses, V, dt), V, it
+
+
+def twisted_pose(pose, k, h):
+    """A pose moved by h along twist coordinate k: a world translation
+    (k < 3) or a left rotation about the particle origin (k >= 3)."""
+    p = np.array(pose, np.float64, copy=True)
+    if k < 3:
+        p[k] += h
+        return p
+    ax = np.zeros(3)
+    ax[k - 3] = 1.0
+    q = _quat_mul(rotvec_quat(h * ax), p[3:] / np.linalg.norm(p[3:]))
+    p[3:] = q / np.linalg.norm(q)
+    return p
+
+
+def pose_hessian(scene, poses, pairs, eps, k_s=1000.0, h=1e-6):
+    """Second derivatives of the contact energy in the particles' pose twists
+    (translation, left rotation about the origin), [6n, 6n]: central
+    differences of the analytic gradient dE/dpose (the oracle's `grad`), so
+    the closest points are free to move (unlike the Gauss-Newton blocks,
+    whose barycentrics are frozen).  Accurate to O(h^2) where the contact
+    set and the closest features do not change within h."""
+    import dataclasses
+
+    from . import grad
+    n = scene.n_particles
+    base = dataclasses.replace(scene, pairs=np.asarray(pairs, np.int32).reshape(-1, 2),
+                               eps=np.asarray(eps, np.float64), com=np.zeros((n, 3)))
+
+    def gradient(P):
+        c = detect(base, poses=P)
+        return grad(base, c, k_s=k_s, poses=P)[1].ravel()
+
+    H = np.zeros((6 * n, 6 * n))
+    for i in range(n):
+        for k in range(6):
+            Pp, Pm = np.array(poses, copy=True), np.array(poses, copy=True)
+            Pp[i] = twisted_pose(poses[i], k, h)
+            Pm[i] = twisted_pose(poses[i], k, -h)
+            H[:, 6 * i + k] = (gradient(Pp) - gradient(Pm)) / (2 * h)
+    return H

@@ -204,3 +204,44 @@ def test_newton_and_picard_reach_the_same_step(imp, seed):
     scale = np.abs(V1).max()
     assert np.abs(V1 - V2).max() <= 1e-10 * scale, (np.abs(V1 - V2).max(), scale, it1, it2)
     np.testing.assert_allclose(P2[:, :3], P1[:, :3], rtol=0, atol=1e-12)
+
+
+def test_pose_hessian_vertex_against_vertex_closed_form(imp):
+    """Two regular icosahedra tip to tip (every contact between the triangles
+    around the two tips has the tips as closest points): the translation
+    block of the energy's Hessian is 25 (e'' u u^T + e' (I - u u^T) / d),
+    e' = -K_s sqrt(mu) (1 - d/(2 eps)), e'' = K_s sqrt(mu) / (2 eps); the
+    Gauss-Newton block has only the first term."""
+    import oracle
+    from gen import icosphere, scene_regular_pair
+    from tests.test_oracle_contacts import _quat_from_matrix, _rotation_taking
+    v, f = icosphere(0)
+    qA = _quat_from_matrix(_rotation_taking(v[0], np.array([1.0, 0, 0])))
+    qB = _quat_from_matrix(_rotation_taking(v[3], np.array([-1.0, 0, 0])))
+    s = scene_regular_pair(0, 1.0, 2.06, qA, qB, 0.05)
+    c = oracle.detect(s)
+    assert len(c["d"]) == 25
+    H = imp.pose_hessian(s, s.poses, s.pairs, s.eps)
+    d = float(c["d"][0])
+    u = (c["pa"][0] - c["pb"][0]) / d
+    ks = 1000.0 * np.sqrt(1 / (1 / s.mass[0] + 1 / s.mass[1]))
+    e1 = -ks * (1 - d / (2 * s.eps[0]))
+    e2 = ks / (2 * s.eps[0])
+    want = 25 * (e2 * np.outer(u, u) + e1 * (np.eye(3) - np.outer(u, u)) / d)
+    np.testing.assert_allclose(H[0:3, 0:3], want, rtol=0, atol=1e-5 * np.abs(want).max())
+    np.testing.assert_allclose(H[6:9, 6:9], want, rtol=0, atol=1e-5 * np.abs(want).max())
+    np.testing.assert_allclose(H[0:3, 6:9], -want, rtol=0, atol=1e-5 * np.abs(want).max())
+    _, _, jac = oracle.grad(s, c)
+    np.testing.assert_allclose(jac[0][0:3, 0:3], 25 * e2 * np.outer(u, u), rtol=1e-9, atol=1e-9)
+
+
+def test_newton_with_the_full_hessian_converges_fast(imp):
+    """With the full pose Hessian as stiffness, Newton's method converges in
+    a handful of iterations to the Picard fixed point."""
+    s, vel, pairs, eps = _colliding_pair(imp, seed=8)
+    dt = 5e-4
+    _, V1, it1, _ = imp.implicit_euler_step(s, vel, pairs, eps, dt, tol=2e-13, max_iter=1000)
+    _, V2, it2 = imp.implicit_euler_step_newton(s, vel, pairs, eps, dt, tol=1e-12, max_iter=50,
+                                                stiffness="hessian")
+    assert it2 <= 8, it2
+    assert np.abs(V1 - V2).max() <= 1e-9 * np.abs(V1).max()
