@@ -188,7 +188,7 @@ def _assemble(meshes, poses, radius, pairs, eps, name):
     to = np.zeros(len(meshes) + 1, np.int64)
     vo[1:] = np.cumsum([len(v) for v in vs])
     to[1:] = np.cumsum([len(t) for t in ts])
-    radius = np.asarray(radius, np.float64)
+    radius = np.ascontiguousarray(radius, np.float64)
     return Scene(np.ascontiguousarray(np.concatenate(vs), dtype=np.float32), vo,
                  np.ascontiguousarray(np.concatenate(ts), dtype=np.int32), to,
                  np.asarray(poses, np.float64), (4.0 / 3.0) * np.pi * radius ** 3,
