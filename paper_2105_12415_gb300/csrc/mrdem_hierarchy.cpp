@@ -15,7 +15,11 @@
 //   * each surrogate gets the smallest slack delta that keeps it conservative:
 //     the largest FP64 distance from a fine vertex below it to the stored
 //     float32 triangle (distance to a triangle is convex, so its maximum over
-//     a fine triangle is at a vertex), rounded up to float32.
+//     a fine triangle is at a vertex), rounded up to float32;
+//   * beyond the paper, every node also gets an oriented box around the fine
+//     vertices below it (principal axes of their covariance; the box is
+//     convex, so it holds the node's fine triangles too), a further
+//     conservative bound that the detection tests after the node spheres.
 // Layout: nodes of a particle in breadth-first order, children contiguous;
 // fine triangles reordered so that each leaf owns a contiguous run of slots,
 // padded to a multiple of 4 slots.
