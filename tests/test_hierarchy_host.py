@@ -228,13 +228,15 @@ def _box_contains_all(ex, scene, node, box):
     return bool((proj <= half).all()), U, half, V
 
 
-@pytest.mark.parametrize("which", ["c1", "disparity"])
+@pytest.mark.parametrize("which", ["c1", "disparity", "plane"])
 def test_node_boxes_contain_their_fine_vertices(which):
     """Every node's oriented box holds every fine vertex below it, exactly
     in FP64 with the stored float values; the axes are orthonormal to float
-    rounding; no half extent exceeds the node's vertex spread."""
-    from gen import scene_disparity
-    s = scene_c1() if which == "c1" else scene_disparity(1)
+    rounding; no half extent exceeds the node's vertex spread.  The plane
+    particles (one triangle) get a flat box."""
+    from gen import scene_disparity, scene_particle_on_plane
+    s = {"c1": scene_c1, "disparity": lambda: scene_disparity(1),
+         "plane": scene_particle_on_plane}[which]()
     ex = _host(s).export()
     boxes = ex["node_box"]
     assert boxes.shape == (len(ex["node_delta"]), 16)
@@ -245,6 +247,8 @@ def test_node_boxes_contain_their_fine_vertices(which):
         assert np.abs(U @ U.T - np.eye(3)).max() < 1e-6
         spread = np.linalg.norm(V.max(0) - V.min(0))
         assert half.max() <= spread
+        if len(V) == 3:  # a single triangle: its box has no thickness
+            assert half.min() <= 1e-6 * half.max()
 
 
 def test_box_of_a_cuboid_is_the_cuboid():
