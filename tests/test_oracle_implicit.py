@@ -245,3 +245,30 @@ def test_newton_with_the_full_hessian_converges_fast(imp):
                                                 stiffness="hessian")
     assert it2 <= 8, it2
     assert np.abs(V1 - V2).max() <= 1e-9 * np.abs(V1).max()
+
+
+def test_packing_generator():
+    """Every requested particle is placed; the achieved volume fraction is
+    stated (random sequential addition jams below dense packings); the
+    particles moved towards a neighbour give overlapping bounding spheres;
+    the same seed gives the same scene."""
+    s, frac, vel = scene_packing(400, 0.5, seed=31)
+    assert s.n_particles == 400 and vel.shape == (400, 6)
+    r = s.radius
+    vol = (4.0 / 3.0) * np.pi * (r ** 3).sum()
+    c = s.poses[:, :3]
+    side_est = (vol / frac) ** (1 / 3)
+    assert 0 < frac <= 0.5 and np.ptp(c, axis=0).max() <= side_est * 1.0001
+    d = np.linalg.norm(c[:, None] - c[None], axis=-1) + np.eye(400) * 1e9
+    overlap = (d < 1.05 * (r[:, None] + r[None])).any(1)
+    assert overlap.sum() >= 0.2 * 400 * 0.5
+    s2, frac2, _ = scene_packing(400, 0.5, seed=31)
+    assert frac2 == frac and np.array_equal(s2.poses, s.poses) and np.array_equal(s2.verts, s.verts)
+
+
+def test_disparity_generator():
+    from gen import scene_disparity
+    s = scene_disparity(3)
+    nt = np.diff(s.tri_off)
+    assert list(nt) == [81920, 1280] * 3
+    assert np.allclose(s.radius, [20.0, 1.0] * 3) and np.allclose(s.eps, 0.02)
