@@ -272,3 +272,62 @@ def test_disparity_generator():
     nt = np.diff(s.tri_off)
     assert list(nt) == [81920, 1280] * 3
     assert np.allclose(s.radius, [20.0, 1.0] * 3) and np.allclose(s.eps, 0.02)
+
+
+def _chain(k, seed):
+    """k bumped particles in a chain: each placed along a random direction
+    so that its extreme vertex lies 0.5 eps from the previous particle's
+    extreme vertex (the pair generator's support-plane placement), so every
+    consecutive pair is in contact."""
+    from gen import bumped_icosphere, quat_to_matrix_f64, random_quaternion
+    from gen.icosphere import _assemble
+    rng = np.random.default_rng([2105124150, seed])
+    meshes = [bumped_icosphere(2, float(rng.uniform(1.0, 1.5)), rng) for _ in range(k)]
+    poses = [np.concatenate([[0.0, 0.0, 0.0], random_quaternion(rng)])]
+    for i in range(1, k):
+        e = 0.02 * min(np.abs(meshes[i - 1][0]).max(), np.abs(meshes[i][0]).max())
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        Rp = quat_to_matrix_f64(poses[-1][3:])
+        wp = meshes[i - 1][0].astype(np.float64) @ Rp.T + poses[-1][:3]
+        q = random_quaternion(rng)
+        wc = meshes[i][0].astype(np.float64) @ quat_to_matrix_f64(q).T
+        t = wp[np.argmax(wp @ u)] + 0.5 * e * u - wc[np.argmax(wc @ -u)]
+        poses.append(np.concatenate([t, q]))
+    radius = [float(np.linalg.norm(m[0], axis=1).mean()) for m in meshes]
+    return _assemble(meshes, poses, radius, np.zeros((0, 2), np.int32), np.zeros(0), "chain")
+
+
+def test_many_particles_momentum_identities(imp):
+    """A small packing with several contacting pairs (one particle may touch
+    several others): the momentum balance and the angular-momentum identity
+    of the implicit Euler step hold for the whole system."""
+    import dataclasses
+
+    import oracle
+    s = _chain(4, seed=41)
+    bound = imp.bounding_radius(s)
+    pairs = imp.broad_phase(s.poses[:, :3], bound, s.radius)
+    eps = imp.pair_eps(s.radius, pairs[:, 0], pairs[:, 1])
+    base = dataclasses.replace(s, pairs=pairs, eps=eps, com=np.zeros((s.n_particles, 3)))
+    c0 = oracle.detect(base)
+    assert len(np.unique(c0["pair"])) >= 3   # the chain's pairs are in contact
+    rng = np.random.default_rng(2)
+    vel = rng.normal(scale=0.1, size=(s.n_particles, 6))
+    dt = 2e-4
+    P, V, it, hist = imp.implicit_euler_step(s, vel, pairs, eps, dt, tol=2e-13, max_iter=2000)
+    assert it < 2000
+    m = s.mass
+    inertia = 0.4 * m * s.radius ** 2
+    p0 = (m[:, None] * vel[:, :3]).sum(0) + dt * m.sum() * imp.G_DEFAULT
+    p1 = (m[:, None] * V[:, :3]).sum(0)
+    assert np.abs(p1 - p0).max() <= 1e-11 * (np.abs(m[:, None] * vel[:, :3]).sum() + dt * m.sum() * 9.81)
+    c = oracle.detect(base, poses=P)
+    ft, _ = oracle.forces(base, c, poses=P)
+    x0 = s.poses[:, :3]
+    L0 = (np.cross(x0, m[:, None] * vel[:, :3]) + inertia[:, None] * vel[:, 3:]).sum(0)
+    L1 = (np.cross(P[:, :3], m[:, None] * V[:, :3]) + inertia[:, None] * V[:, 3:]).sum(0)
+    want = L0 + dt * np.cross(x0, m[:, None] * imp.G_DEFAULT).sum(0) - dt ** 2 * np.cross(V[:, :3], ft[:, :3]).sum(0)
+    scale = np.abs(np.cross(x0, m[:, None] * vel[:, :3])).sum() + np.abs(inertia[:, None] * vel[:, 3:]).sum() \
+        + dt * np.abs(np.cross(x0, m[:, None] * imp.G_DEFAULT)).sum()
+    assert np.abs(L1 - want).max() <= 1e-10 * scale, (np.abs(L1 - want).max(), scale)
