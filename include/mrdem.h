@@ -304,6 +304,68 @@ int mrdem_merge_contacts(mrdem_ctx* ctx, int64_t n_pairs, const double* pair_eps
                          const mrdem_contacts* in, const mrdem_contacts* out, int32_t* members,
                          mrdem_stream stream);
 
+/* ---- implicit time step (Algorithm 3, Sec. 6 many-particle setup)
+ *
+ * Broad phase: every particle pair i < j whose bounding spheres, widened by
+ * the pair's eps, overlap: |c_i - c_j| <= R_i + R_j + 2 eps_ij with
+ * eps_ij = eps_rel * 2 * min(r_i, r_j) (eps relative to the smaller
+ * particle diameter, Sec. 6).
+ *   poses   device double [n*7] (centre xyz, quaternion wxyz); only the
+ *           centres are read;
+ *   bound   device double [n]: bounding radius R_i of particle i about its
+ *           centre (the largest distance of a vertex from the body origin);
+ *   radius  device double [n]: the radius r_i that scales eps;
+ *   pairs   device int32 [cap*2] and pair_eps device double [cap]: the
+ *           candidates ordered by (i, j) and their eps_ij (the inputs
+ *           mrdem_detect takes);
+ *   count   device int64: the number of candidates.  When it exceeds cap
+ *           nothing is written to pairs / pair_eps: grow to count and call
+ *           again.
+ * The decision |c_i - c_j| <= ... is taken in FP64 without fused
+ * multiply-adds ((dx^2 + dy^2) + dz^2, sqrt; (R_i + R_j) + 2 eps_ij), so the
+ * list is a deterministic function of the inputs.  Uniform grid of cells no
+ * smaller than the largest R_i + R_j + 2 eps_ij, hashed into 2^k >= 2n
+ * buckets; the context keeps about 28 n + 4 * 2^k bytes of scratch, grown on
+ * a larger call.  Device-side failure latched for mrdem_check: a centre,
+ * bound or radius that is not finite, or a negative bound or radius:
+ * NONFINITE (count is then 0).  Errors returned directly: INVALID (null
+ * pointers, n > 2^26, cap >= 2^31, eps_rel negative or not finite), OOM,
+ * CUDA.  Stream-ordered, no host synchronisation. */
+int mrdem_broad_phase(mrdem_ctx* ctx, int32_t n, const double* poses, const double* bound,
+                      const double* radius, double eps_rel, int32_t* pairs, double* pair_eps,
+                      int64_t cap, int64_t* count, mrdem_stream stream);
+
+/* Rigid-body pose update of the implicit Euler step: for each particle,
+ * centre' = centre + dt v and orientation' = quat(dt omega) * orientation
+ * (the rotation vector dt omega applied in the world frame), renormalised.
+ *   poses0  device double [n*7] (centre xyz, quaternion wxyz, any norm > 0);
+ *   vel     device double [n*6]: (v xyz, omega xyz) in the world frame;
+ *   poses   device double [n*7] output; may be poses0 itself, not vel.
+ * Errors: INVALID (null pointers, dt not finite, vel == poses), CUDA. */
+int mrdem_move_poses(mrdem_ctx* ctx, int32_t n, const double* poses0, const double* vel,
+                     double dt, double* poses, mrdem_stream stream);
+
+/* One Picard update of the implicit Euler step (Algorithm 3): from the
+ * contact forces and torques at the geometry moved by the guessed
+ * velocities, new velocities
+ *   v' = v0 + dt (F / m + g),   omega' = omega0 + dt tau / I
+ * (isotropic inertia I per particle; torques about the centre of mass).
+ *   vel0          device double [n*6]: velocities at the start of the step;
+ *   force_torque  device double [n*6]: (F, tau) at the guessed geometry
+ *                 (mrdem_contact_forces' output);
+ *   mass, inertia device double [n];
+ *   gravity       HOST double [3];
+ *   vel           device double [n*6]: in, the guess; out, the update;
+ *   norms         device double [2]: out, (max |v' - guess|, max |v'|) over
+ *                 all components, the iteration's convergence measure (NaN
+ *                 if any update is NaN).
+ * Errors: INVALID (null pointers, dt or gravity not finite, vel aliasing
+ * vel0 or force_torque), CUDA. */
+int mrdem_picard_update(mrdem_ctx* ctx, int32_t n, const double* vel0,
+                        const double* force_torque, const double* mass, const double* inertia,
+                        const double* gravity, double dt, double* vel, double* norms,
+                        mrdem_stream stream);
+
 /* Plain GPU form (reported baseline): the contact set by FP64 comparison-based
  * distance over ALL fine triangle pairs of each pair (Algorithm 2), no
  * hierarchy, one kernel launch per particle pair.  Same inputs and outputs as

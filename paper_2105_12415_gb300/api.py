@@ -363,6 +363,113 @@ def triangle_distance(ctx, P, Q, eps, precision="fp64", sweep=True, stream=None)
     return out
 
 
+# ---- implicit time step (Algorithm 3)
+
+G_DEFAULT = (0.0, 0.0, -9.81)
+
+
+def broad_phase(ctx: Context, poses, bound, radius, eps_rel=0.01, cap=None, stream=None,
+                max_retries=4):
+    """Candidate particle pairs of a many-particle scene (uniform-grid broad
+    phase): every i < j with |c_i - c_j| <= R_i + R_j + 2 eps_ij,
+    eps_ij = eps_rel * 2 * min(r_i, r_j).  poses [n, 7], bound R [n] and
+    radius r [n]: float64 on the device.  Returns (pairs int32 [P, 2] ordered
+    by (i, j), eps float64 [P]).  Synchronises to read the count; grows the
+    output and repeats when it overflows."""
+    n = poses.shape[0]
+    _need(poses, torch.float64, (n, 7), "poses")
+    _need(bound, torch.float64, (n,), "bound")
+    _need(radius, torch.float64, (n,), "radius")
+    dev = poses.device
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    cap = int(cap) if cap is not None else max(1024, 16 * n)
+    lib = L.load()
+    for _ in range(max_retries + 1):
+        pairs = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+        eps = torch.empty(cap, dtype=torch.float64, device=dev)
+        L.check(lib.mrdem_broad_phase(ctx.handle, n, _p(poses), _p(bound), _p(radius),
+                                      float(eps_rel), _p(pairs), _p(eps), cap, _p(count),
+                                      _stream(stream)), "mrdem_broad_phase")
+        L.check(lib.mrdem_check(ctx.handle, _stream(stream), None), "mrdem_broad_phase")
+        total = int(count.item())
+        if total <= cap:
+            return pairs[:total], eps[:total]
+        cap = total
+    raise L.MrdemError(L.MRDEM_ERR_CAPACITY, "mrdem_broad_phase (retries exhausted)")
+
+
+def move_poses(ctx: Context, poses0, vel, dt, out=None, stream=None):
+    """Poses after a step dt at velocities vel [n, 6] (v, omega; world
+    frame): centre + dt v, orientation turned by the rotation vector
+    dt omega (left multiplication)."""
+    n = poses0.shape[0]
+    _need(poses0, torch.float64, (n, 7), "poses0")
+    _need(vel, torch.float64, (n, 6), "vel")
+    if out is None:
+        out = torch.empty_like(poses0)
+    _need(out, torch.float64, (n, 7), "out")
+    L.check(L.load().mrdem_move_poses(ctx.handle, n, _p(poses0), _p(vel), float(dt), _p(out),
+                                      _stream(stream)), "mrdem_move_poses")
+    return out
+
+
+def picard_update(ctx: Context, vel0, force_torque, mass, inertia, dt, vel, norms=None,
+                  gravity=G_DEFAULT, stream=None):
+    """One Picard update in place: vel <- (v0 + dt (F / m + g),
+    omega0 + dt tau / I).  Returns norms (device float64 [2]):
+    (max |new - old|, max |new|)."""
+    n = vel0.shape[0]
+    for t, name in ((vel0, "vel0"), (force_torque, "force_torque"), (vel, "vel")):
+        _need(t, torch.float64, (n, 6), name)
+    _need(mass, torch.float64, (n,), "mass")
+    _need(inertia, torch.float64, (n,), "inertia")
+    if norms is None:
+        norms = torch.empty(2, dtype=torch.float64, device=vel0.device)
+    g = (C.c_double * 3)(*[float(x) for x in gravity])
+    L.check(L.load().mrdem_picard_update(ctx.handle, n, _p(vel0), _p(force_torque), _p(mass),
+                                         _p(inertia), C.cast(g, C.c_void_p), float(dt), _p(vel),
+                                         _p(norms), _stream(stream)), "mrdem_picard_update")
+    return norms
+
+
+def implicit_euler_step(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inertia, pairs, eps,
+                        dt, gravity=G_DEFAULT, k_s=1000.0, precision="fp32", tol=1e-13,
+                        max_iter=200, contacts=None):
+    """One implicit Euler step by Picard iteration (Algorithm 3): starting
+    from vel0, repeat: move the particles from poses0 by dt times the guessed
+    velocities, detect the contacts of the candidate pairs there, compute the
+    contact forces and torques (about the body origins), and update the
+    guess; stop when max |new - guess| <= tol * max |new|.  All arithmetic
+    runs in the library's kernels; the loop reads two numbers per iteration.
+    Returns (poses, vel, iterations, history of the relative change)."""
+    n = poses0.shape[0]
+    dev = poses0.device
+    P = pairs.shape[0]
+    vel = vel0.clone()
+    poses = torch.empty_like(poses0)
+    com = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    ft = torch.zeros((n, 6), dtype=torch.float64, device=dev)
+    energy = torch.zeros(1, dtype=torch.float64, device=dev)
+    norms = torch.empty(2, dtype=torch.float64, device=dev)
+    hist = []
+    it = 0
+    for it in range(1, max_iter + 1):
+        move_poses(ctx, poses0, vel, dt, out=poses)
+        ft.zero_()
+        if P:
+            contacts, _ = detect(ctx, hier, pairs, eps, poses, precision, contacts=contacts)
+            contact_forces(ctx, hier, pairs, eps, poses, contacts, mass, com, k_s,
+                           force_torque=ft, energy=energy)
+        picard_update(ctx, vel0, ft, mass, inertia, dt, vel, norms, gravity)
+        change, scale = norms.tolist()
+        scale += 1e-300
+        hist.append(change / scale)
+        if change <= tol * scale:
+            break
+    move_poses(ctx, poses0, vel, dt, out=poses)
+    return poses, vel, it, hist
+
+
 class ContactProblem:
     """Everything the energy of a particle batch depends on, resident on the device."""
 

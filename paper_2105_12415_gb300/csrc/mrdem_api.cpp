@@ -180,6 +180,7 @@ int mrdem_destroy(mrdem_ctx* c) {
   cudaFree(c->tmp_count);
   cudaFree(c->merge_seg);
   cudaFree(c->merge_mem);
+  cudaFree(c->broad_mem);
   cudaFree(c->frames);
   cudaFree(c->counters);
   cudaFree(c->status);
@@ -562,10 +563,45 @@ int mrdem_merge_contacts(mrdem_ctx* c, int64_t n_pairs, const double* eps,
   return launch_merge(c, n_pairs, eps, in, out, members, (cudaStream_t)s);
 }
 
+int mrdem_broad_phase(mrdem_ctx* c, int32_t n, const double* poses, const double* bound,
+                      const double* radius, double eps_rel, int32_t* pairs, double* pair_eps,
+                      int64_t cap, int64_t* count, mrdem_stream s) {
+  if (!c || n < 0 || n > ((int32_t)1 << 26) || !count || cap < 0 || cap >= (int64_t)1 << 31)
+    return MRDEM_ERR_INVALID;
+  if (!(eps_rel >= 0.0) || !std::isfinite(eps_rel)) return MRDEM_ERR_INVALID;
+  if (n > 0 && (!poses || !bound || !radius)) return MRDEM_ERR_INVALID;
+  if (cap > 0 && (!pairs || !pair_eps)) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_broad_phase(c, n, poses, bound, radius, eps_rel, pairs, pair_eps, cap, count,
+                            (cudaStream_t)s);
+}
+
+int mrdem_move_poses(mrdem_ctx* c, int32_t n, const double* poses0, const double* vel, double dt,
+                     double* poses, mrdem_stream s) {
+  if (!c || n < 0 || !std::isfinite(dt)) return MRDEM_ERR_INVALID;
+  if (n > 0 && (!poses0 || !vel || !poses)) return MRDEM_ERR_INVALID;
+  if (n > 0 && (const void*)vel == (const void*)poses) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_move_poses(c, n, poses0, vel, dt, poses, (cudaStream_t)s);
+}
+
+int mrdem_picard_update(mrdem_ctx* c, int32_t n, const double* vel0, const double* force_torque,
+                        const double* mass, const double* inertia, const double* gravity,
+                        double dt, double* vel, double* norms, mrdem_stream s) {
+  if (!c || n < 0 || !gravity || !norms || !std::isfinite(dt)) return MRDEM_ERR_INVALID;
+  if (n > 0 && (!vel0 || !force_torque || !mass || !inertia || !vel)) return MRDEM_ERR_INVALID;
+  if (n > 0 && (vel == vel0 || vel == force_torque)) return MRDEM_ERR_INVALID;
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(gravity[k])) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_picard_update(c, n, vel0, force_torque, mass, inertia, gravity, dt, vel, norms,
+                              (cudaStream_t)s);
+}
+
 static const char* kKernelNames[K_COUNT] = {
     "k_setup", "k_expand", "k_sweep_nodes", "k_tile",  "k_sweep_fine", "k_exact",
     "k_exact64", "k_forces", "k_grad",       "k_plain", "k_tridist", "k_sort",
-    "k_merge"};
+    "k_merge", "k_broad", "k_step"};
 
 int mrdem_profile(mrdem_ctx* c, int32_t enable) {
   if (!c) return MRDEM_ERR_INVALID;

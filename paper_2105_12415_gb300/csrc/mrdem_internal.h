@@ -155,7 +155,7 @@ struct mrdem_hier {
 };
 
 namespace mrdem {
-enum KernelId : int { K_SETUP = 0, K_LEVEL, K_SWEEP_NODES, K_TILE, K_SWEEP_FINE, K_EXACT, K_EXACT64, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_SORT, K_MERGE, K_COUNT };
+enum KernelId : int { K_SETUP = 0, K_LEVEL, K_SWEEP_NODES, K_TILE, K_SWEEP_FINE, K_EXACT, K_EXACT64, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_SORT, K_MERGE, K_BROAD, K_STEP, K_COUNT };
 struct ProfRec {
   int kernel;
   cudaEvent_t a, b;
@@ -198,6 +198,10 @@ struct mrdem_ctx {
   void* merge_mem = nullptr;
   int64_t cap_merge = 0;
   bool merge_smem_set = false;
+  // broad phase of the implicit step: grid record, per-particle cells, order
+  // and counts, bucket ends (cap_broad bytes)
+  void* broad_mem = nullptr;
+  size_t cap_broad = 0;
   double* frames = nullptr;  // [cap_frames * 16]: per particle R (9), t (3), world com (3)
   int64_t cap_frames = 0;
   unsigned long long* counters = nullptr;  // [CNT_TOTAL]
@@ -263,6 +267,15 @@ int launch_grad(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const i
 // redundant-contact merge (mrdem_merge.cu)
 int launch_merge(mrdem_ctx* ctx, int64_t n_pairs, const double* pair_eps, const mrdem_contacts* in,
                  const mrdem_contacts* out, int32_t* members, cudaStream_t s);
+// implicit time step (mrdem_step.cu)
+int launch_broad_phase(mrdem_ctx* ctx, int32_t n, const double* poses, const double* bound,
+                       const double* radius, double eps_rel, int32_t* pairs, double* pair_eps,
+                       int64_t cap, int64_t* count, cudaStream_t s);
+int launch_move_poses(mrdem_ctx* ctx, int32_t n, const double* poses0, const double* vel,
+                      double dt, double* poses, cudaStream_t s);
+int launch_picard_update(mrdem_ctx* ctx, int32_t n, const double* vel0, const double* ft,
+                         const double* mass, const double* inertia, const double* gravity,
+                         double dt, double* vel, double* norms, cudaStream_t s);
 int launch_triangle_distance(mrdem_ctx* ctx, int64_t n, const double* P, const double* Q,
                              const double* eps, int precision, double* dist, double* pa,
                              double* pb, int32_t* feature, float* sx, float* sgap, int32_t* sconv,

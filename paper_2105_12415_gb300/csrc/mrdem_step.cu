@@ -1,0 +1,317 @@
+// mrdem_step.cu -- kernels of the implicit time step (Algorithm 3) around the
+// contact detection and forces: the uniform-grid broad phase that lists the
+// candidate particle pairs, the rigid-body pose update, and the Picard update
+// of the velocities with its convergence measure.
+//
+// Broad phase, one call:
+//   k_bp_bounds   one block: smallest centre per axis, largest bounding radius
+//                 and radius -> cell side; flags non-finite input;
+//   k_bp_cells    cell and bucket of every particle, bucket sizes;
+//   k_bp_scan     exclusive scan of the bucket sizes -> bucket starts;
+//   k_bp_scatter  particles grouped by bucket (the starts end as the ends);
+//   k_bp_count    a thread per particle: its candidates j > i in the 27 cells;
+//   k_bp_scan     exclusive scan of the counts -> output offsets and the total;
+//   k_bp_write    if the total fits: each particle writes its candidates at its
+//                 offset and sorts them by j, so the list is ordered by (i, j)
+//                 whatever order the atomics grouped the buckets in.
+// The particles' own FP64 arithmetic lives in mrdem_step.cuh.
+#include <cuda_runtime.h>
+
+#include "mrdem_device.cuh"
+#include "mrdem_step.cuh"
+
+namespace mrdem {
+
+namespace {
+
+constexpr int kBoundsThreads = 1024;
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double dmax_nan(double a, double b) {
+  if (a != a) return a;
+  if (b != b) return b;
+  return a > b ? a : b;
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = dmax_nan(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void __launch_bounds__(kBoundsThreads) k_bp_bounds(BroadIn in, BroadGrid* grid,
+                                                              unsigned long long* status) {
+  wait_prior_grid();
+  __shared__ double part[5][32];
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, rb = 0.0, rr = 0.0;
+  bool bad = false;
+  for (int32_t i = threadIdx.x; i < in.n; i += blockDim.x) {
+    const double* c = in.poses + (int64_t)7 * i;
+    for (int k = 0; k < 3; ++k) {
+      const double x = c[k];
+      if (!isfinite(x)) bad = true;
+      lo[k] = fmin(lo[k], x);
+    }
+    const double R = in.bound[i], r = in.radius[i];
+    if (!(R >= 0.0) || !isfinite(R) || !(r >= 0.0) || !isfinite(r)) bad = true;
+    rb = fmax(rb, R);
+    rr = fmax(rr, r);
+  }
+  double v[5] = {warp_min(lo[0]), warp_min(lo[1]), warp_min(lo[2]), warp_max(rb), warp_max(rr)};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0)
+    for (int k = 0; k < 5; ++k) part[k][warp] = v[k];
+  bad = __syncthreads_or(bad) != 0;
+  if (warp == 0) {
+    for (int k = 0; k < 5; ++k) {
+      double x = lane < nw ? part[k][lane] : (k < 3 ? INFINITY : 0.0);
+      v[k] = k < 3 ? warp_min(x) : warp_max(x);
+    }
+    if (lane == 0) {
+      BroadGrid g;
+      g.lo[0] = v[0];
+      g.lo[1] = v[1];
+      g.lo[2] = v[2];
+      g.h = bp_cell_side(v[3], v[4], in.eps_rel);
+      g.inv_h = 1.0 / g.h;
+      g.bad = (bad || !isfinite(g.h)) ? 1 : 0;
+      g.pad = 0;
+      *grid = g;
+      if (g.bad) atomicExch(status + ST_NONFINITE, 1ull);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_bp_cells(BroadIn in, const BroadGrid* grid,
+                                                       BroadWork w) {
+  wait_prior_grid();
+  const BroadGrid g = *grid;
+  if (g.bad) return;
+  const int32_t step = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += step) {
+    const double* c = in.poses + (int64_t)7 * i;
+    BroadCell cl;
+    cl.x = bp_cell(c[0], g.lo[0], g.inv_h);
+    cl.y = bp_cell(c[1], g.lo[1], g.inv_h);
+    cl.z = bp_cell(c[2], g.lo[2], g.inv_h);
+    cl.b = bp_bucket(cl.x, cl.y, cl.z, w.log2_t);
+    w.cell[i] = cl;
+    atomicAdd(w.bucket_end + cl.b, 1);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_bp_scan(int32_t* cnt, int64_t n, int64_t* total) {
+  wait_prior_grid();
+  block_exclusive_scan(cnt, n, total);
+}
+
+__global__ void __launch_bounds__(kThreads) k_bp_scatter(BroadIn in, const BroadGrid* grid,
+                                                         BroadWork w) {
+  wait_prior_grid();
+  if (grid->bad) return;
+  const int32_t step = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += step)
+    w.order[atomicAdd(w.bucket_end + w.cell[i].b, 1)] = i;
+}
+
+__global__ void __launch_bounds__(kThreads) k_bp_count(BroadIn in, const BroadGrid* grid,
+                                                       BroadWork w, int32_t* cnt) {
+  wait_prior_grid();
+  const bool bad = grid->bad != 0;
+  const int32_t step = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += step)
+    cnt[i] = bad ? 0 : bp_visit(in, w, i, [](int32_t, double) {});
+}
+
+__global__ void __launch_bounds__(kThreads) k_bp_write(BroadIn in, const BroadGrid* grid,
+                                                       BroadWork w, const int32_t* off,
+                                                       const int64_t* count, int64_t cap,
+                                                       int32_t* pairs, double* pair_eps) {
+  wait_prior_grid();
+  const int64_t total = *count;
+  if (grid->bad || total > cap) return;
+  const int32_t step = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += step) {
+    const int64_t o = off[i];
+    const int64_t m = (i + 1 < in.n ? (int64_t)off[i + 1] : total) - o;
+    int64_t k = 0;
+    bp_visit(in, w, i, [&](int32_t j, double e) {
+      if (k < m) {
+        pairs[2 * (o + k) + 1] = j;
+        pair_eps[o + k] = e;
+      }
+      ++k;
+    });
+    const int64_t got = k < m ? k : m;
+    // insertion sort of the particle's candidates by j (a few dozen at most
+    // in a packing)
+    for (int64_t a = o + 1; a < o + got; ++a) {
+      const int32_t j = pairs[2 * a + 1];
+      const double e = pair_eps[a];
+      int64_t b = a - 1;
+      while (b >= o && pairs[2 * b + 1] > j) {
+        pairs[2 * (b + 1) + 1] = pairs[2 * b + 1];
+        pair_eps[b + 1] = pair_eps[b];
+        --b;
+      }
+      pairs[2 * (b + 1) + 1] = j;
+      pair_eps[b + 1] = e;
+    }
+    for (int64_t a = o; a < o + got; ++a) pairs[2 * a] = i;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_move_poses(int32_t n, const double* poses0,
+                                                         const double* vel, double dt,
+                                                         double* poses) {
+  wait_prior_grid();
+  const int32_t step = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+    double p0[7], v[6], out[7];
+    for (int k = 0; k < 7; ++k) p0[k] = poses0[(int64_t)7 * i + k];
+    for (int k = 0; k < 6; ++k) v[k] = vel[(int64_t)6 * i + k];
+    move_pose(p0, v, dt, out);
+    for (int k = 0; k < 7; ++k) poses[(int64_t)7 * i + k] = out[k];
+  }
+}
+
+struct Gravity {
+  double g[3];
+};
+
+__global__ void __launch_bounds__(kThreads) k_picard(int32_t n, const double* vel0,
+                                                     const double* ft, const double* mass,
+                                                     const double* inertia, Gravity grav,
+                                                     double dt, double* vel,
+                                                     unsigned long long* norms) {
+  wait_prior_grid();
+  double cmax = 0.0, smax = 0.0;
+  const int32_t step = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+    double v0[6], f[6], guess[6], out[6], c, s;
+    for (int k = 0; k < 6; ++k) {
+      v0[k] = vel0[(int64_t)6 * i + k];
+      f[k] = ft[(int64_t)6 * i + k];
+      guess[k] = vel[(int64_t)6 * i + k];
+    }
+    picard_velocity(v0, f, mass[i], inertia[i], grav.g, dt, guess, out, &c, &s);
+    for (int k = 0; k < 6; ++k) vel[(int64_t)6 * i + k] = out[k];
+    cmax = dmax_nan(cmax, c);
+    smax = dmax_nan(smax, s);
+  }
+  cmax = warp_max(cmax);
+  smax = warp_max(smax);
+  if ((threadIdx.x & 31) == 0) {
+    // non-negative doubles (and NaN, with its sign cleared) order like their bits
+    atomicMax(norms, (unsigned long long)__double_as_longlong(fabs(cmax)));
+    atomicMax(norms + 1, (unsigned long long)__double_as_longlong(fabs(smax)));
+  }
+}
+
+int ceil_log2(int64_t v) {
+  int k = 0;
+  while (((int64_t)1 << k) < v) ++k;
+  return k;
+}
+
+int blocks_for(const mrdem_ctx* c, int64_t n) {
+  const int64_t b = (n + kThreads - 1) / kThreads;
+  const int64_t lim = (int64_t)c->n_sms * 8;
+  return (int)(b < 1 ? 1 : (b < lim ? b : lim));
+}
+
+}  // namespace
+
+// Broad-phase scratch: the grid record, then cell [n], order [n], counts /
+// offsets [n], bucket ends [2^log2_t].
+static int ensure_broad(mrdem_ctx* c, int32_t n, BroadWork* w, BroadGrid** grid,
+                        int32_t** cnt) {
+  const int log2_t = ceil_log2(2 * (int64_t)n) < 6 ? 6 : ceil_log2(2 * (int64_t)n);
+  const int64_t t = (int64_t)1 << log2_t;
+  const size_t bytes = 256 + sizeof(BroadCell) * (size_t)n + sizeof(int32_t) * (size_t)n * 2 +
+                       sizeof(int32_t) * (size_t)t + 64;
+  if (bytes > c->cap_broad) {
+    cudaFree(c->broad_mem);
+    c->broad_mem = nullptr;
+    c->cap_broad = 0;
+    if (cudaMalloc(&c->broad_mem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->broad_mem = nullptr;
+      return MRDEM_ERR_OOM;
+    }
+    c->cap_broad = bytes;
+  }
+  unsigned char* p = static_cast<unsigned char*>(c->broad_mem);
+  *grid = reinterpret_cast<BroadGrid*>(p);
+  p += 256;
+  w->cell = reinterpret_cast<BroadCell*>(p);
+  p += sizeof(BroadCell) * (size_t)n;
+  w->order = reinterpret_cast<int32_t*>(p);
+  p += sizeof(int32_t) * (size_t)n;
+  *cnt = reinterpret_cast<int32_t*>(p);
+  p += sizeof(int32_t) * (size_t)n;
+  w->bucket_end = reinterpret_cast<int32_t*>(p);
+  w->log2_t = log2_t;
+  return MRDEM_OK;
+}
+
+int launch_broad_phase(mrdem_ctx* c, int32_t n, const double* poses, const double* bound,
+                       const double* radius, double eps_rel, int32_t* pairs, double* pair_eps,
+                       int64_t cap, int64_t* count, cudaStream_t s) {
+  if (n == 0) {
+    cudaMemsetAsync(count, 0, sizeof(int64_t), s);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+  }
+  BroadWork w;
+  BroadGrid* grid = nullptr;
+  int32_t* cnt = nullptr;
+  int st = ensure_broad(c, n, &w, &grid, &cnt);
+  if (st) return st;
+  const BroadIn in{poses, bound, radius, eps_rel, n};
+  const int64_t t = (int64_t)1 << w.log2_t;
+  const int nb = blocks_for(c, n);
+  ProfScope ps(c, K_BROAD, s);
+  cudaMemsetAsync(w.bucket_end, 0, sizeof(int32_t) * (size_t)t, s);
+  launch_after(k_bp_bounds, 1, kBoundsThreads, 0, s, in, grid, c->status);
+  launch_after(k_bp_cells, nb, kThreads, 0, s, in, (const BroadGrid*)grid, w);
+  launch_after(k_bp_scan, 1, 1024, 0, s, w.bucket_end, t, (int64_t*)nullptr);
+  launch_after(k_bp_scatter, nb, kThreads, 0, s, in, (const BroadGrid*)grid, w);
+  launch_after(k_bp_count, nb, kThreads, 0, s, in, (const BroadGrid*)grid, w, cnt);
+  launch_after(k_bp_scan, 1, 1024, 0, s, cnt, (int64_t)n, count);
+  launch_after(k_bp_write, nb, kThreads, 0, s, in, (const BroadGrid*)grid, w,
+               (const int32_t*)cnt, (const int64_t*)count, cap, pairs, pair_eps);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
+
+int launch_move_poses(mrdem_ctx* c, int32_t n, const double* poses0, const double* vel, double dt,
+                      double* poses, cudaStream_t s) {
+  if (n == 0) return MRDEM_OK;
+  ProfScope ps(c, K_STEP, s);
+  launch_after(k_move_poses, blocks_for(c, n), kThreads, 0, s, n, poses0, vel, dt, poses);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
+
+int launch_picard_update(mrdem_ctx* c, int32_t n, const double* vel0, const double* ft,
+                         const double* mass, const double* inertia, const double* gravity,
+                         double dt, double* vel, double* norms, cudaStream_t s) {
+  cudaMemsetAsync(norms, 0, 2 * sizeof(double), s);
+  if (n > 0) {
+    ProfScope ps(c, K_STEP, s);
+    Gravity g{{gravity[0], gravity[1], gravity[2]}};
+    launch_after(k_picard, blocks_for(c, n), kThreads, 0, s, n, vel0, ft, mass, inertia, g, dt,
+                 vel, reinterpret_cast<unsigned long long*>(norms));
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
+
+}  // namespace mrdem

@@ -1,0 +1,217 @@
+// mrdem_step.cuh -- per-particle arithmetic of the implicit time step
+// (Algorithm 3): the broad phase that lists the candidate particle pairs, the
+// rigid-body pose update and the Picard update of the velocities.  Host and
+// device functions, so the kernels in mrdem_step.cu are thin loops around them.
+//
+// Broad phase.  Particle i has centre c_i (the translation of its pose),
+// bounding radius R_i about it and radius r_i; pair eps_ij = eps_rel 2 min(r_i, r_j)
+// (eps relative to the smaller particle diameter, Sec. 6).  A pair i < j is a
+// candidate when the bounding spheres widened by eps_ij overlap:
+//   |c_i - c_j| <= R_i + R_j + 2 eps_ij.
+// Cells of side h >= max (R_i + R_j + 2 eps_ij) put every candidate of i in one
+// of the 27 cells around i's cell.  Cells are hashed into a power-of-two table
+// (the spatial hash of Teschner et al. 2003, "Optimized spatial hashing for
+// collision detection of deformable objects"); a bucket can hold several cells,
+// so a particle found in a bucket counts only if its own cell is the one being
+// visited, which also keeps a particle from being seen twice when two of the 27
+// cells share a bucket.  The distance test runs in FP64 without fused
+// multiply-adds, term by term ((dx^2 + dy^2) + dz^2, then sqrt), so its
+// decisions do not depend on the compiler.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include "mrdem_geometry.cuh"
+
+namespace mrdem {
+
+// Grid of the broad phase, written by the bounds kernel: lo = the smallest
+// centre coordinate per axis, h = the cell side, inv_h = 1 / h.
+struct BroadGrid {
+  double lo[3];
+  double h, inv_h;
+  int32_t bad;  // a centre, bound or radius was not finite (or negative)
+  int32_t pad;
+};
+
+// Cell sides are widened by this relative slack so that rounding in
+// (x - lo) * inv_h (up to a few ulp of cell coordinates below 2^30) cannot
+// put two candidates two cells apart.
+constexpr double kCellSlack = 1.0 + 1.0 / 65536.0;
+constexpr double kCellMax = 1073741824.0;  // cell coordinates are clamped to [0, 2^30]
+
+MRDEM_HD double bp_mul(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+
+MRDEM_HD double bp_add(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+
+// Cell side from the largest bounding radius and radius: every candidate pair
+// has R_i + R_j + 2 eps_ij <= 2 R_max + 4 eps_rel r_max.
+MRDEM_HD double bp_cell_side(double r_bound_max, double r_max, double eps_rel) {
+  const double h = (2.0 * r_bound_max + 4.0 * eps_rel * r_max) * kCellSlack;
+  return h > 0.0 ? h : 1.0;  // all zero: candidates coincide, any side will do
+}
+
+// Cell coordinate along one axis; monotone in x, clamped to [0, 2^30].
+MRDEM_HD int32_t bp_cell(double x, double lo, double inv_h) {
+  const double q = (x - lo) * inv_h;
+  if (!(q > 0.0)) return 0;
+  if (q >= kCellMax) return (int32_t)kCellMax;
+  return (int32_t)q;  // truncation = floor for q > 0
+}
+
+// Bucket of cell (x, y, z) in a table of 2^log2_t buckets.
+MRDEM_HD uint32_t bp_bucket(int32_t x, int32_t y, int32_t z, int log2_t) {
+  const uint32_t hsh = ((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349663u) ^
+                       ((uint32_t)z * 83492791u);
+  return hsh & ((1u << log2_t) - 1u);
+}
+
+// eps of pair (i, j): eps_rel * 2 * min(r_i, r_j), in that order of operations.
+MRDEM_HD double bp_pair_eps(double r_i, double r_j, double eps_rel) {
+  return bp_mul(eps_rel * 2.0, r_i < r_j ? r_i : r_j);
+}
+
+// The candidate test |c_i - c_j| <= R_i + R_j + 2 eps_ij.
+MRDEM_HD bool bp_candidate(const double* ci, const double* cj, double Ri, double Rj, double eij) {
+  const double dx = ci[0] - cj[0], dy = ci[1] - cj[1], dz = ci[2] - cj[2];
+  double s = bp_mul(dx, dx);
+  s = bp_add(s, bp_mul(dy, dy));
+  s = bp_add(s, bp_mul(dz, dz));
+  const double lim = bp_add(bp_add(Ri, Rj), bp_mul(2.0, eij));
+  return sqrt(s) <= lim;
+}
+
+// Input arrays of the broad phase (device pointers in the kernels).
+struct BroadIn {
+  const double* poses;   // [n*7]: centre xyz, quaternion wxyz
+  const double* bound;   // [n] bounding radius about the centre
+  const double* radius;  // [n]
+  double eps_rel;
+  int32_t n;
+};
+
+// Cell of a particle: coordinates and bucket.
+struct alignas(16) BroadCell {
+  int32_t x, y, z;
+  uint32_t b;
+};
+
+// Working arrays: cell[i] = (cx, cy, cz, bucket) of particle i; order = the
+// particles grouped by bucket; bucket_end[b] = one past the last entry of
+// bucket b in order (bucket b starts at bucket_end[b - 1], or 0).
+struct BroadWork {
+  BroadCell* cell;
+  int32_t* order;
+  int32_t* bucket_end;
+  int log2_t;
+};
+
+// Visits the candidates j > i of particle i in bucket order; calls f(j, eps_ij)
+// for each and returns how many there were.
+template <typename F>
+MRDEM_HD int32_t bp_visit(const BroadIn& in, const BroadWork& w, int32_t i, F f) {
+  const double* ci = in.poses + (int64_t)7 * i;
+  const double Ri = in.bound[i], ri = in.radius[i];
+  const BroadCell me = w.cell[i];
+  int32_t found = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int32_t x = me.x + dx, y = me.y + dy, z = me.z + dz;
+        if (x < 0 || y < 0 || z < 0 || x > (int32_t)kCellMax || y > (int32_t)kCellMax ||
+            z > (int32_t)kCellMax)
+          continue;  // no particle lives there
+        const uint32_t b = bp_bucket(x, y, z, w.log2_t);
+        const int32_t beg = b ? w.bucket_end[b - 1] : 0, end = w.bucket_end[b];
+        for (int32_t k = beg; k < end; ++k) {
+          const int32_t j = w.order[k];
+          if (j <= i) continue;
+          const BroadCell cj = w.cell[j];
+          if (cj.x != x || cj.y != y || cj.z != z) continue;
+          const double eij = bp_pair_eps(ri, in.radius[j], in.eps_rel);
+          if (!bp_candidate(ci, in.poses + (int64_t)7 * j, Ri, in.bound[j], eij)) continue;
+          f(j, eij);
+          ++found;
+        }
+      }
+  return found;
+}
+
+// ---- rigid-body update and Picard iteration (Algorithm 3)
+
+// Unit quaternion (w, x, y, z) of the rotation by rotation vector r.
+MRDEM_HD void rotvec_to_quat(const double r[3], double q[4]) {
+  const double th = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  if (th == 0.0) {
+    q[0] = 1.0;
+    q[1] = q[2] = q[3] = 0.0;
+    return;
+  }
+  const double s = sin(0.5 * th) / th;
+  q[0] = cos(0.5 * th);
+  q[1] = s * r[0];
+  q[2] = s * r[1];
+  q[3] = s * r[2];
+}
+
+// Hamilton product a * b.
+MRDEM_HD void quat_mul(const double a[4], const double b[4], double out[4]) {
+  out[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+  out[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+  out[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+  out[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+// Pose after a step dt with velocity (v, omega): centre c + dt v, orientation
+// turned by the rotation vector dt omega in the world frame (left
+// multiplication), renormalised.
+MRDEM_HD void move_pose(const double* pose0, const double* vel, double dt, double* out) {
+  for (int k = 0; k < 3; ++k) out[k] = pose0[k] + dt * vel[k];
+  const double r[3] = {dt * vel[3], dt * vel[4], dt * vel[5]};
+  double dq[4], q0[4], q[4];
+  rotvec_to_quat(r, dq);
+  const double n0 = sqrt(pose0[3] * pose0[3] + pose0[4] * pose0[4] + pose0[5] * pose0[5] +
+                         pose0[6] * pose0[6]);
+  for (int k = 0; k < 4; ++k) q0[k] = pose0[3 + k] / n0;
+  quat_mul(dq, q0, q);
+  const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int k = 0; k < 4; ++k) out[3 + k] = q[k] / n;
+}
+
+// One Picard update of particle i's velocities: new = (v0 + dt (F / m + g),
+// omega0 + dt tau / I) from the forces at the guessed geometry.  Returns
+// max_k |new_k - guess_k| and max_k |new_k| through *change and *scale.
+MRDEM_HD void picard_velocity(const double* vel0, const double* ft, double m, double inertia,
+                              const double g[3], double dt, const double* guess, double* out,
+                              double* change, double* scale) {
+  double c = 0.0, s = 0.0;
+  for (int k = 0; k < 6; ++k) {
+    // no contraction into fused multiply-adds: the rounding is that of the
+    // plain formula, operation by operation
+    const double v = k < 3 ? bp_add(vel0[k], bp_mul(dt, bp_add(ft[k] / m, g[k])))
+                           : bp_add(vel0[k], bp_mul(dt, ft[k]) / inertia);
+    const double d = fabs(v - guess[k]), a = fabs(v);
+    c = d > c ? d : c;
+    s = a > s ? a : s;
+    if (d != d) c = d;  // NaN propagates
+    if (a != a) s = a;
+    out[k] = v;
+  }
+  *change = c;
+  *scale = s;
+}
+
+}  // namespace mrdem

@@ -274,30 +274,6 @@ def test_disparity_generator():
     assert np.allclose(s.radius, [20.0, 1.0] * 3) and np.allclose(s.eps, 0.02)
 
 
-def _chain(k, seed):
-    """k bumped particles in a chain: each placed along a random direction
-    so that its extreme vertex lies 0.5 eps from the previous particle's
-    extreme vertex (the pair generator's support-plane placement), so every
-    consecutive pair is in contact."""
-    from gen import bumped_icosphere, quat_to_matrix_f64, random_quaternion
-    from gen.icosphere import _assemble
-    rng = np.random.default_rng([2105124150, seed])
-    meshes = [bumped_icosphere(2, float(rng.uniform(1.0, 1.5)), rng) for _ in range(k)]
-    poses = [np.concatenate([[0.0, 0.0, 0.0], random_quaternion(rng)])]
-    for i in range(1, k):
-        e = 0.02 * min(np.abs(meshes[i - 1][0]).max(), np.abs(meshes[i][0]).max())
-        u = rng.normal(size=3)
-        u /= np.linalg.norm(u)
-        Rp = quat_to_matrix_f64(poses[-1][3:])
-        wp = meshes[i - 1][0].astype(np.float64) @ Rp.T + poses[-1][:3]
-        q = random_quaternion(rng)
-        wc = meshes[i][0].astype(np.float64) @ quat_to_matrix_f64(q).T
-        t = wp[np.argmax(wp @ u)] + 0.5 * e * u - wc[np.argmax(wc @ -u)]
-        poses.append(np.concatenate([t, q]))
-    radius = [float(np.linalg.norm(m[0], axis=1).mean()) for m in meshes]
-    return _assemble(meshes, poses, radius, np.zeros((0, 2), np.int32), np.zeros(0), "chain")
-
-
 def test_many_particles_momentum_identities(imp):
     """A small packing with several contacting pairs (one particle may touch
     several others): the momentum balance and the angular-momentum identity
@@ -305,7 +281,8 @@ def test_many_particles_momentum_identities(imp):
     import dataclasses
 
     import oracle
-    s = _chain(4, seed=41)
+    from gen import scene_chain
+    s = scene_chain(4, seed=41)
     bound = imp.bounding_radius(s)
     pairs = imp.broad_phase(s.poses[:, :3], bound, s.radius)
     eps = imp.pair_eps(s.radius, pairs[:, 0], pairs[:, 1])

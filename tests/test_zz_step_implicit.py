@@ -1,0 +1,242 @@
+"""The implicit time step on the GPU (Algorithm 3) against the FP64 oracle:
+the uniform-grid broad phase (bit-exact pair list and eps), the rigid-body
+pose update, the Picard velocity update, and whole Picard steps whose fixed
+point is compared with the oracle's.
+
+Tolerances.  The broad phase takes the same FP64 decisions as the oracle, so
+its list must be identical.  Pose updates agree to a few ulps (sin / cos of
+the rotation angle).  A Picard step's fixed point V solves
+V = v0 + dt M^-1 F(V); the contact forces of the two sides differ by at most
+tol_F sum_c |F_c| per particle (tol_F = 1e-9 for the FP64 form, 1e-5 for
+FP32, the bounds of the force parity tests), so the fixed points differ by
+at most about tol_F dt sum_c |F_c| max(1/m, R/I) times 1 / (1 - rho), rho the
+contraction of the iteration (about 0.2 on the chain); the tests allow ten
+times tol_F dt sum_c |F_c| max(1/m, R/I), taken over particles.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from gen import scene_chain, scene_packing
+
+pytestmark = pytest.mark.gpu
+
+TOL_F = {"fp64": 1e-9, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def m():
+    import paper_2105_12415_gb300 as m
+    m.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def imp(orc):
+    import oracle.implicit as imp
+    return imp
+
+
+@pytest.fixture(scope="module")
+def ctx(m):
+    return m.Context(0)
+
+
+def _t(a, dtype="float64"):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=getattr(torch, dtype), device="cuda:0")
+
+
+def _bound(scene):
+    """Largest vertex distance from the body origin, per particle (FP64 of
+    the float vertices)."""
+    return np.array([np.sqrt((scene.particle(i)[0].astype(np.float64) ** 2).sum(1)).max()
+                     for i in range(scene.n_particles)])
+
+
+@pytest.mark.parametrize("n,fraction,levels,seed", [(300, 0.35, (1, 2), 1), (2000, 0.5, (1,), 2),
+                                                    (50, 0.55, (1, 2), 3)])
+def test_broad_phase_equals_oracle(m, ctx, imp, n, fraction, levels, seed):
+    s, _, _ = scene_packing(n, fraction, levels=levels, r_min=1.0, r_max=10.0, seed=seed)
+    bound = _bound(s)
+    ref = imp.broad_phase(s.poses[:, :3], bound, s.radius)
+    ref_eps = imp.pair_eps(s.radius, ref[:, 0], ref[:, 1])
+    assert len(ref) > n // 10
+    pairs, eps = m.broad_phase(ctx, _t(s.poses), _t(bound), _t(s.radius))
+    assert np.array_equal(pairs.cpu().numpy(), ref)
+    assert np.array_equal(eps.cpu().numpy(), ref_eps)
+
+
+def test_broad_phase_grows_and_repeats(m, ctx, imp):
+    s, _, _ = scene_packing(300, 0.35, levels=(1, 2), r_min=1.0, r_max=10.0, seed=1)
+    bound = _bound(s)
+    ref = imp.broad_phase(s.poses[:, :3], bound, s.radius)
+    pairs, _ = m.broad_phase(ctx, _t(s.poses), _t(bound), _t(s.radius), cap=3)
+    assert np.array_equal(pairs.cpu().numpy(), ref)
+
+
+def test_broad_phase_edge_cases(m, ctx, imp):
+    # no particle, one particle
+    for n in (0, 1):
+        P = np.zeros((n, 7))
+        P[:, 3] = 1.0
+        pairs, eps = m.broad_phase(ctx, _t(P), _t(np.ones(n)), _t(np.ones(n)))
+        assert pairs.shape == (0, 2) and eps.shape == (0,)
+    # coincident points of zero size: every pair, in (i, j) order
+    P = np.zeros((5, 7))
+    P[:, 3] = 1.0
+    pairs, eps = m.broad_phase(ctx, _t(P), _t(np.zeros(5)), _t(np.zeros(5)))
+    assert pairs.cpu().numpy().tolist() == [[i, j] for i in range(5) for j in range(i + 1, 5)]
+    assert (eps.cpu().numpy() == 0).all()
+    # two clusters 1e12 apart (cell coordinates clamped) and touching spheres
+    # exactly at the limit distance
+    rng = np.random.default_rng(0)
+    P = np.zeros((42, 7))
+    P[:, 3] = 1.0
+    P[:20, :3] = rng.normal(size=(20, 3))
+    P[20:40, :3] = 1e12 + rng.normal(size=(20, 3))
+    P[40, :3] = (5.0, 5.0, 5.0)
+    P[41, :3] = (5.0, 5.0, 6.02)  # at the limit 0.5 + 0.5 + 2 * 0.01, up to rounding
+    b = np.full(42, 0.5)
+    r = np.full(42, 0.5)
+    ref = imp.broad_phase(P[:, :3], b, r)
+    pairs, _ = m.broad_phase(ctx, _t(P), _t(b), _t(r))
+    assert np.array_equal(pairs.cpu().numpy(), ref)
+
+
+def test_broad_phase_rejects_nonfinite(m, ctx):
+    P = np.zeros((4, 7))
+    P[:, 3] = 1.0
+    P[:, 0] = np.arange(4)
+    P[2, 1] = np.nan
+    with pytest.raises(m.MrdemError):
+        m.broad_phase(ctx, _t(P), _t(np.ones(4)), _t(np.ones(4)))
+    # the context stays usable
+    P[2, 1] = 0.0
+    pairs, _ = m.broad_phase(ctx, _t(P), _t(np.ones(4)), _t(np.ones(4)))
+    assert pairs.shape[0] == 6
+
+
+def test_move_poses_equals_oracle(m, ctx, imp):
+    s, _, _ = scene_packing(200, 0.3, levels=(1,), seed=5)
+    rng = np.random.default_rng(7)
+    V = rng.normal(size=(200, 6)) * 3.0
+    V[0, 3:] = 0.0  # no rotation
+    for dt in (1e-3, 0.5):
+        got = m.move_poses(ctx, _t(s.poses), _t(V), dt).cpu().numpy()
+        ref = imp.moved_poses(s.poses, V, dt)
+        assert np.abs(got - ref).max() <= 1e-14 * (1.0 + np.abs(ref).max())
+        assert np.abs(np.linalg.norm(got[:, 3:], axis=1) - 1.0).max() <= 1e-15
+    # in place
+    P = _t(s.poses)
+    m.move_poses(ctx, P, _t(V), 1e-3, out=P)
+    assert np.abs(P.cpu().numpy() - imp.moved_poses(s.poses, V, 1e-3)).max() <= 1e-14 * (1.0 + np.abs(s.poses).max())
+
+
+def test_picard_update_closed_form(m, ctx):
+    rng = np.random.default_rng(8)
+    n = 1000
+    v0 = rng.normal(size=(n, 6))
+    guess = rng.normal(size=(n, 6))
+    ft = rng.normal(size=(n, 6)) * 100.0
+    mass = rng.uniform(0.5, 2.0, n)
+    inertia = rng.uniform(0.1, 1.0, n)
+    g = (0.5, -1.0, -9.81)
+    dt = 1e-3
+    vel = _t(guess)
+    norms = m.picard_update(ctx, _t(v0), _t(ft), _t(mass), _t(inertia), dt, vel, gravity=g)
+    want = np.empty((n, 6))
+    want[:, :3] = v0[:, :3] + dt * (ft[:, :3] / mass[:, None] + np.array(g))
+    want[:, 3:] = v0[:, 3:] + dt * ft[:, 3:] / inertia[:, None]
+    # the kernel rounds operation by operation in the formula's order
+    assert np.array_equal(vel.cpu().numpy(), want)
+    c, sc = norms.cpu().numpy()
+    assert c == np.abs(want - guess).max()
+    assert sc == np.abs(want).max()
+
+
+def _chain_problem(imp):
+    s = scene_chain(4, seed=41)
+    bound = _bound(s)
+    pairs = imp.broad_phase(s.poses[:, :3], bound, s.radius)
+    eps = imp.pair_eps(s.radius, pairs[:, 0], pairs[:, 1])
+    rng = np.random.default_rng(2)
+    vel = rng.normal(scale=0.1, size=(s.n_particles, 6))
+    return s, bound, pairs, eps, vel
+
+
+def _fixed_point_bound(orc, s, pairs, eps, P, dt, precision):
+    """ten times tol_F dt sum_c |F_c| max(1/m, R/I), the largest over
+    particles, at the oracle's final geometry"""
+    base = dataclasses.replace(s, pairs=pairs, eps=eps, com=np.zeros((s.n_particles, 3)))
+    c = orc.detect(base, poses=P)
+    mu = 1 / (1 / s.mass[pairs[:, 0]] + 1 / s.mass[pairs[:, 1]])
+    mag = 1000.0 * np.sqrt(mu[c["pair"]]) * (1 - c["d"] / (2 * eps[c["pair"]]))
+    tot = np.zeros(s.n_particles)
+    for col in (0, 1):
+        np.add.at(tot, pairs[c["pair"], col], mag)
+    inertia = 0.4 * s.mass * s.radius ** 2
+    lever = _bound(s)
+    return 10.0 * TOL_F[precision] * dt * (tot * np.maximum(1 / s.mass, lever / inertia)).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_picard_map_at_oracle_fixed_point(m, ctx, orc, imp, precision):
+    """One GPU Picard iteration started from the oracle's fixed point returns
+    it, within the force tolerance."""
+    s, _, pairs, eps, vel = _chain_problem(imp)
+    dt = 2e-4
+    P, V, it, _ = imp.implicit_euler_step(s, vel, pairs, eps, dt, tol=2e-13, max_iter=2000)
+    assert it < 2000
+    hier = m.Hierarchy.from_scene(ctx, s)
+    inertia = 0.4 * s.mass * s.radius ** 2
+    poses = m.move_poses(ctx, _t(s.poses), _t(V), dt)
+    assert np.abs(poses.cpu().numpy() - P).max() <= 1e-14 * (1.0 + np.abs(P).max())
+    tp, te = _t(pairs, "int32"), _t(eps)
+    contacts, _ = m.detect(ctx, hier, tp, te, poses, precision)
+    ft, _ = m.contact_forces(ctx, hier, tp, te, poses, contacts, _t(s.mass),
+                             _t(np.zeros((s.n_particles, 3))))
+    V1 = _t(V)
+    m.picard_update(ctx, _t(vel), ft, _t(s.mass), _t(inertia), dt, V1)
+    bound = _fixed_point_bound(orc, s, pairs, eps, P, dt, precision) / 10.0
+    assert np.abs(V1.cpu().numpy() - V).max() <= bound + 1e-12 * np.abs(V).max()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_implicit_step_equals_oracle(m, ctx, orc, imp, precision, tol):
+    s, bound, pairs, eps, vel = _chain_problem(imp)
+    dt = 2e-4
+    P, V, it_ref, _ = imp.implicit_euler_step(s, vel, pairs, eps, dt, tol=2e-13, max_iter=2000)
+    hier = m.Hierarchy.from_scene(ctx, s)
+    inertia = 0.4 * s.mass * s.radius ** 2
+    # pairs from the GPU broad phase, as a user would run it
+    gp, ge = m.broad_phase(ctx, _t(s.poses), _t(bound), _t(s.radius))
+    assert np.array_equal(gp.cpu().numpy(), pairs)
+    poses, Vg, it, hist = m.implicit_euler_step(ctx, hier, _t(s.poses), _t(vel), _t(s.mass),
+                                                _t(inertia), gp, ge, dt, precision=precision,
+                                                tol=tol, max_iter=200)
+    assert it < 200, hist[-5:]
+    lim = _fixed_point_bound(orc, s, pairs, eps, P, dt, precision) + tol * np.abs(V).max() * 10
+    assert np.abs(Vg.cpu().numpy() - V).max() <= lim
+    assert np.abs(poses.cpu().numpy() - P).max() <= dt * lim + 1e-14 * (1.0 + np.abs(P).max())
+    if precision == "fp64":
+        assert it <= it_ref + 2  # a looser tolerance than the oracle's stops no later
+
+
+def test_free_flight_is_exact(m, ctx, imp):
+    """No candidate pairs: one iteration gives v0 + dt g exactly."""
+    s, _, _ = scene_packing(30, 0.05, levels=(1,), seed=9)
+    rng = np.random.default_rng(3)
+    vel = rng.normal(size=(s.n_particles, 6))
+    dt = 1e-3
+    hier = m.Hierarchy.from_scene(ctx, s)
+    inertia = 0.4 * s.mass * s.radius ** 2
+    empty_p = _t(np.zeros((0, 2)), "int32")
+    empty_e = _t(np.zeros(0))
+    poses, V, it, _ = m.implicit_euler_step(ctx, hier, _t(s.poses), _t(vel), _t(s.mass),
+                                            _t(inertia), empty_p, empty_e, dt)
+    Pr, Vr, _, _ = imp.implicit_euler_step(s, vel, np.zeros((0, 2), np.int32), np.zeros(0), dt)
+    assert it == 2
+    assert np.array_equal(V.cpu().numpy(), Vr)
+    assert np.abs(poses.cpu().numpy() - Pr).max() <= 1e-14 * (1.0 + np.abs(Pr).max())
