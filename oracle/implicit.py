@@ -15,6 +15,11 @@ world frame); stop when the guessed velocities no longer change.  The
 fixed point is the implicit Euler solution; damping or acceleration of the
 iteration (Sec. 6) change the path to it, not the point, and are left out.
 
+Contact Hessian (`contact_hessian`): the second derivatives of the contact
+energy in the pose twists with the closest points free, in closed form per
+contact (the closest-point parameters eliminated by the implicit function
+theorem), for Newton's method on the same equations.
+
 Readings (the paper leaves them open): the particles' inertia is that of a
 solid sphere of the particle's radius, I = 2/5 m r^2 (isotropic, so no
 gyroscopic term); gravity g = (0, 0, -9.81); the contact forces are those of
@@ -139,7 +144,8 @@ def implicit_euler_step_newton(scene, vel, pairs, eps, dt, g=G_DEFAULT, k_s=1000
     the pose unknowns, barycentrics frozen).  The residual is exact, so the
     converged velocities are the implicit Euler solution; an approximate
     Jacobian only slows the convergence.  stiffness="hessian" uses the full
-    pose Hessian (`pose_hessian`, closest points free) instead of the blocks.
+    pose Hessian (`pose_hessian`, closest points free) instead of the blocks,
+    stiffness="analytic" the same Hessian in closed form (`contact_hessian`).
     Returns (poses, vel, iterations)."""
     import dataclasses
 
@@ -163,6 +169,9 @@ def implicit_euler_step_newton(scene, vel, pairs, eps, dt, g=G_DEFAULT, k_s=1000
             ft, _ = forces(base, c, k_s=k_s, poses=poses)
             if stiffness == "hessian":
                 K = pose_hessian(scene, poses, pairs, eps, k_s=k_s)
+            elif stiffness == "analytic":
+                _, gp, _ = grad(base, c, k_s=k_s, poses=poses)
+                K = twist_hessian_fd_form(contact_hessian(base, c, poses=poses, k_s=k_s), gp)
             else:
                 _, _, jac = grad(base, c, k_s=k_s, poses=poses)
                 for p, (a, b) in enumerate(pairs):
@@ -219,3 +228,125 @@ def pose_hessian(scene, poses, pairs, eps, k_s=1000.0, h=1e-6):
             Pm[i] = twisted_pose(poses[i], k, -h)
             H[:, 6 * i + k] = (gradient(Pp) - gradient(Pm)) / (2 * h)
     return H
+
+
+def _barycentric(p, T):
+    """Barycentric coordinates of p in triangle T [3, 3] (least squares in
+    the triangle's plane)."""
+    A = np.stack([T[1] - T[0], T[2] - T[0]], 1)
+    s = np.linalg.lstsq(A, p - T[0], rcond=None)[0]
+    return np.array([1.0 - s[0] - s[1], s[0], s[1]])
+
+
+def _skew(r):
+    return np.array([[0.0, -r[2], r[1]], [r[2], 0.0, -r[0]], [-r[1], r[0], 0.0]])
+
+
+def contact_hessian(scene, contacts, poses=None, k_s=1000.0, active_tol=1e-9):
+    """Second derivatives of the contact energy E = sum_c e(d_c) (Sec. 2 force
+    law, e(d) = K_s sqrt(mu) eps (1 - d/(2 eps))^2) in the particles' pose
+    twists (world translation; world rotation increment theta about the
+    particle's origin, applied on the left of R), [6n, 6n], symmetric, with
+    the closest points free to move.
+
+    Per contact with d > 0, from its closest points and their triangles:
+      * the active features: the triangle corners with a barycentric weight
+        of the closest point above active_tol (a vertex, an edge or the face
+        of each triangle);
+      * phi(X, s) = |P(s) - Q(s)|^2 / 2, X the six world corners, s the free
+        barycentric parameters of the active features (none for a vertex,
+        one for an edge, two for a face), P and Q linear in s and X; at the
+        optimum grad_s phi = 0, so g(X) = min_s phi has grad g = phi_X and
+        Hess g = phi_XX - phi_Xs phi_ss^-1 phi_sX (implicit function
+        theorem); d = sqrt(2 g) gives grad d = grad g / d and
+        Hess d = Hess g / d - grad g grad g^T / d^3;
+      * Hess_X e = e''(d) grad d grad d^T + e'(d) Hess d, e' = -K_s sqrt(mu)
+        (1 - d/(2 eps)), e'' = K_s sqrt(mu) / (2 eps);
+      * to the twists: X_v(delta) = exp([theta]x)(X_v - t) + t + delta_t, so
+        dX_v = [I, -[X_v - t]x] and the rotation block gains
+        sum_v sym(g_v r_v^T) - (g_v . r_v) I with g_v = dE/dX_v and
+        r_v = X_v - t (the second-order term of the exponential).
+    Contacts at d = 0 (crossing triangles) are skipped: d is not
+    differentiable there.  The central differences of the analytic gradient
+    in `pose_hessian` move the rotation of the perturbed pose, which adds
+    -1/2 [dE/dtheta]x to each particle's rotation block (the commutator of
+    two rotations); `twist_hessian_fd_form` adds it."""
+    from . import world_triangles
+    poses = scene.poses if poses is None else poses
+    n = scene.n_particles
+    H = np.zeros((6 * n, 6 * n))
+    tri_cache = {}
+
+    def tris(i):
+        if i not in tri_cache:
+            tri_cache[i] = world_triangles(scene, i, poses)
+        return tri_cache[i]
+
+    for k in range(len(contacts["d"])):
+        d = float(contacts["d"][k])
+        if not d > 0.0:
+            continue
+        p = int(contacts["pair"][k])
+        A, B = int(scene.pairs[p, 0]), int(scene.pairs[p, 1])
+        eps = float(scene.eps[p])
+        ks = k_s * np.sqrt(1.0 / (1.0 / scene.mass[A] + 1.0 / scene.mass[B]))
+        TA = tris(A)[contacts["ta"][k]].reshape(3, 3)
+        TB = tris(B)[contacts["tb"][k]].reshape(3, 3)
+        X = np.concatenate([TA, TB])                       # [6, 3]
+        wa = _barycentric(contacts["pa"][k], TA)
+        wb = _barycentric(contacts["pb"][k], TB)
+        SA = [i for i in range(3) if wa[i] > active_tol]
+        SB = [i for i in range(3) if wb[i] > active_tol]
+        sig = np.zeros(6)
+        sig[SA] = wa[SA] / wa[SA].sum()
+        sig[[3 + i for i in SB]] = -wb[SB] / wb[SB].sum()
+        r = sig @ X                                         # P - Q
+        # d sigma / d s for the free parameters
+        dsig = []
+        for j in SA[1:]:
+            col = np.zeros(6)
+            col[j], col[SA[0]] = 1.0, -1.0
+            dsig.append(col)
+        for j in SB[1:]:
+            col = np.zeros(6)
+            col[3 + j], col[3 + SB[0]] = -1.0, 1.0
+            dsig.append(col)
+        gg = np.kron(sig, r)                                # grad g, [18]
+        Hg = np.kron(np.outer(sig, sig), np.eye(3))         # phi_XX
+        if dsig:
+            D = np.array(dsig)                              # [q, 6]
+            G = D @ X                                       # [q, 3]: dr/ds
+            M = np.zeros((18, len(dsig)))
+            for q in range(len(dsig)):
+                M[:, q] = np.kron(D[q], r) + np.kron(sig, G[q])
+            Hg = Hg - M @ np.linalg.solve(G @ G.T, M.T)
+        dd = gg / d
+        Hd = Hg / d - np.outer(gg, gg) / d ** 3
+        e1 = -ks * (1.0 - d / (2.0 * eps))
+        e2 = ks / (2.0 * eps)
+        HX = e2 * np.outer(dd, dd) + e1 * Hd
+        gX = (e1 * dd).reshape(6, 3)
+        # chain rule to the two particles' twists
+        J = np.zeros((18, 12))
+        R2 = np.zeros((12, 12))
+        for v in range(6):
+            blk, t = (0, poses[A, :3]) if v < 3 else (6, poses[B, :3])
+            rv = X[v] - t
+            J[3 * v:3 * v + 3, blk:blk + 3] = np.eye(3)
+            J[3 * v:3 * v + 3, blk + 3:blk + 6] = -_skew(rv)
+            gr = np.outer(gX[v], rv)
+            R2[blk + 3:blk + 6, blk + 3:blk + 6] += 0.5 * (gr + gr.T) - (gX[v] @ rv) * np.eye(3)
+        H12 = J.T @ HX @ J + R2
+        idx = np.r_[6 * A:6 * A + 6, 6 * B:6 * B + 6]
+        H[np.ix_(idx, idx)] += H12
+    return H
+
+
+def twist_hessian_fd_form(H, grad_pose):
+    """The Hessian as `pose_hessian`'s central differences see it: each
+    particle's rotation block plus -1/2 [dE/dtheta]x (differentiating the
+    twist gradient while the pose itself rotates)."""
+    out = np.array(H, copy=True)
+    for i in range(len(grad_pose)):
+        out[6 * i + 3:6 * i + 6, 6 * i + 3:6 * i + 6] -= 0.5 * _skew(grad_pose[i, 3:])
+    return out

@@ -308,3 +308,147 @@ def test_many_particles_momentum_identities(imp):
     scale = np.abs(np.cross(x0, m[:, None] * vel[:, :3])).sum() + np.abs(inertia[:, None] * vel[:, 3:]).sum() \
         + dt * np.abs(np.cross(x0, m[:, None] * imp.G_DEFAULT)).sum()
     assert np.abs(L1 - want).max() <= 1e-10 * scale, (np.abs(L1 - want).max(), scale)
+
+
+def _one_contact(c, k):
+    return {key: v[k:k + 1] for key, v in c.items()}
+
+
+def _icosahedra_facing(kind_a, kind_b, angle=0.7, gap=1.0, eps=0.05):
+    """Two regular icosahedra along x, A's vertex / edge / face ('v', 'e',
+    'f') facing B's, B turned by `angle` about x (so facing edges cross), the
+    facing features gap * eps apart."""
+    from gen import icosphere, scene_regular_pair
+    from tests.test_oracle_contacts import _quat_from_matrix, _rotation_taking
+    v, f = icosphere(0)
+
+    def direction(kind):
+        return {"v": v[0], "e": v[f[0][0]] + v[f[0][1]], "f": v[f[0]].sum(0)}[kind]
+
+    ca, sa = np.cos(angle), np.sin(angle)
+    Rx = np.array([[1.0, 0, 0], [0, ca, -sa], [0, sa, ca]])
+    RA = _rotation_taking(direction(kind_a), np.array([1.0, 0, 0]))
+    RB = Rx @ _rotation_taking(direction(kind_b), np.array([-1.0, 0, 0]))
+    w = v.astype(np.float32).astype(np.float64)
+    D = (w @ RA.T)[:, 0].max() - (w @ RB.T)[:, 0].min() + gap * eps
+    return scene_regular_pair(0, 1.0, D, _quat_from_matrix(RA), _quat_from_matrix(RB), eps)
+
+
+FACING = [("v", "f"), ("f", "v"), ("e", "e"), ("v", "e"), ("e", "v"), ("v", "v")]
+
+
+@pytest.mark.parametrize("case", [4, 8] + FACING)
+def test_contact_hessian_matches_finite_differences(imp, case):
+    """The closed-form contact Hessian equals the central differences of the
+    analytic pose gradient (closest points free to move), once the
+    commutator of two rotations, -1/2 [dE/dtheta]x, is added to each
+    rotation block; the antisymmetric part of the differences is exactly
+    that term."""
+    import dataclasses
+
+    import oracle
+    if isinstance(case, int):
+        s, _, pairs, eps = _colliding_pair(imp, seed=case)
+    else:
+        s = _icosahedra_facing(*case)
+        pairs, eps = s.pairs, s.eps
+    base = dataclasses.replace(s, pairs=pairs, eps=eps, com=np.zeros((2, 3)))
+    c = oracle.detect(base)
+    assert len(c["d"]) >= 1 and (c["d"] > 0).all()
+    Ha = imp.contact_hessian(base, c)
+    Hf = imp.pose_hessian(s, s.poses, pairs, eps)
+    _, gp, _ = oracle.grad(base, c)
+    scale = np.abs(Hf).max()
+    assert np.abs(Ha - Ha.T).max() <= 1e-12 * scale
+    assert np.abs(imp.twist_hessian_fd_form(Ha, gp) - Hf).max() <= 1e-6 * scale
+    anti = 0.5 * (Hf - Hf.T)
+    for i in range(2):
+        want = -0.5 * imp._skew(gp[i, 3:])
+        assert np.abs(anti[6 * i + 3:6 * i + 6, 6 * i + 3:6 * i + 6] - want).max() <= 1e-6 * scale
+        if isinstance(case, int):   # off-centre contacts: the term is far above the tolerance
+            assert np.abs(gp[i, 3:]).max() >= 1e-4 * scale
+
+
+def test_contact_hessian_translation_block_closed_form(imp):
+    """Per contact, translating B moves the closest points along with it, so
+    the distance's translation Hessian is (I - u u^T - Pi) / d, Pi the
+    projector onto the directions of the active features (the span of the
+    edges of a closest edge or face of either triangle): zero for a vertex
+    against a face or two crossing edges, (I - u u^T - f f^T)/d for a vertex
+    against an edge f, (I - u u^T)/d for two vertices.  The block is then
+    e'' u u^T + e' (I - u u^T - Pi)/d, the same for A and B, and minus it
+    between them."""
+    import dataclasses
+
+    import oracle
+    kinds = set()
+    scenes = [_icosahedra_facing(a, b) for a, b in FACING]
+    for seed in (4, 8):
+        s, _, pairs, eps = _colliding_pair(imp, seed=seed)
+        scenes.append(dataclasses.replace(s, pairs=pairs, eps=eps, com=np.zeros((2, 3))))
+    for base in scenes:
+        s, eps = base, base.eps
+        c = oracle.detect(base)
+        assert len(c["d"]) > 0
+        TA = oracle.world_triangles(base, 0)
+        TB = oracle.world_triangles(base, 1)
+        ks = 1000.0 * np.sqrt(1 / (1 / s.mass[0] + 1 / s.mass[1]))
+        for k in range(len(c["d"])):
+            d = float(c["d"][k])
+            u = (c["pa"][k] - c["pb"][k]) / d
+            dirs, kind = [], []
+            for T, pt in ((TA[c["ta"][k]].reshape(3, 3), c["pa"][k]), (TB[c["tb"][k]].reshape(3, 3), c["pb"][k])):
+                w = imp._barycentric(pt, T)
+                S = [i for i in range(3) if w[i] > 1e-9]
+                dirs += [T[j] - T[S[0]] for j in S[1:]]
+                kind.append(len(S))
+            kinds.add(tuple(kind))
+            Pi = np.zeros((3, 3))
+            if dirs:
+                Q, sv, _ = np.linalg.svd(np.array(dirs).T)
+                for col in range(int((sv > 1e-12 * sv.max()).sum())):
+                    q = Q[:, col] - (Q[:, col] @ u) * u
+                    Pi += np.outer(q, q) / (q @ q)
+            e1 = -ks * (1 - d / (2 * eps[0]))
+            e2 = ks / (2 * eps[0])
+            want = e2 * np.outer(u, u) + e1 * (np.eye(3) - np.outer(u, u) - Pi) / d
+            H = imp.contact_hessian(base, _one_contact(c, k))
+            tol = 1e-9 * (abs(e2) + abs(e1) / d)
+            assert np.abs(H[0:3, 0:3] - want).max() <= tol, (k, H[0:3, 0:3], want)
+            assert np.abs(H[6:9, 6:9] - want).max() <= tol
+            assert np.abs(H[0:3, 6:9] + want).max() <= tol
+    assert kinds == {(1, 3), (3, 1), (2, 2), (1, 2), (2, 1), (1, 1)}   # every generic feature pair
+
+
+def test_contact_hessian_vertex_against_vertex_closed_form(imp):
+    """The tip-to-tip icosahedra of the finite-difference pin: the closed form
+    gives 25 (e'' u u^T + e' (I - u u^T) / d) directly."""
+    import oracle
+    from gen import icosphere, scene_regular_pair
+    from tests.test_oracle_contacts import _quat_from_matrix, _rotation_taking
+    v, f = icosphere(0)
+    qA = _quat_from_matrix(_rotation_taking(v[0], np.array([1.0, 0, 0])))
+    qB = _quat_from_matrix(_rotation_taking(v[3], np.array([-1.0, 0, 0])))
+    s = scene_regular_pair(0, 1.0, 2.06, qA, qB, 0.05)
+    c = oracle.detect(s)
+    H = imp.contact_hessian(s, c)
+    d = float(c["d"][0])
+    u = (c["pa"][0] - c["pb"][0]) / d
+    ks = 1000.0 * np.sqrt(1 / (1 / s.mass[0] + 1 / s.mass[1]))
+    e1 = -ks * (1 - d / (2 * s.eps[0]))
+    e2 = ks / (2 * s.eps[0])
+    want = 25 * (e2 * np.outer(u, u) + e1 * (np.eye(3) - np.outer(u, u)) / d)
+    np.testing.assert_allclose(H[0:3, 0:3], want, rtol=0, atol=1e-9 * np.abs(want).max())
+    np.testing.assert_allclose(H[0:3, 6:9], -want, rtol=0, atol=1e-9 * np.abs(want).max())
+
+
+def test_newton_with_the_analytic_hessian(imp):
+    """Newton's method with the closed-form Hessian as stiffness converges as
+    fast as with the finite-difference one, to the Picard fixed point."""
+    s, vel, pairs, eps = _colliding_pair(imp, seed=8)
+    dt = 5e-4
+    _, V1, _, _ = imp.implicit_euler_step(s, vel, pairs, eps, dt, tol=2e-13, max_iter=1000)
+    _, V2, it2 = imp.implicit_euler_step_newton(s, vel, pairs, eps, dt, tol=1e-12, max_iter=50,
+                                                stiffness="analytic")
+    assert it2 <= 8, it2
+    assert np.abs(V1 - V2).max() <= 1e-9 * np.abs(V1).max()
