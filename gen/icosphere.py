@@ -422,18 +422,25 @@ def scene_chain(k: int = 4, seed: int = 41, level: int = 2):
     """k bumped icospheres (radius U[1, 1.5]) in a chain: particle i sits
     along a random direction from particle i - 1 so that their extreme
     vertices along it are 0.5 eps apart (eps = 0.02 times the smaller largest
-    coordinate), so every consecutive pair touches.  No pairs listed (a broad
+    coordinate), so every consecutive pair touches; the direction is drawn
+    again while the new particle's bounding sphere comes within 4 eps of a
+    particle other than its predecessor, so the consecutive pairs are the
+    only contacts and no two meshes intersect.  No pairs listed (a broad
     phase supplies them)."""
     rng = np.random.default_rng([BASE_SEED, seed])
     meshes = [bumped_icosphere(level, float(rng.uniform(1.0, 1.5)), rng) for _ in range(k)]
+    bound = [float(np.sqrt((m[0].astype(np.float64) ** 2).sum(1)).max()) for m in meshes]
     poses = [np.concatenate([[0.0, 0.0, 0.0], random_quaternion(rng)])]
     for i in range(1, k):
         e = 0.02 * min(np.abs(meshes[i - 1][0]).max(), np.abs(meshes[i][0]).max())
-        u = _unit(rng)
         wp = meshes[i - 1][0].astype(np.float64) @ quat_to_matrix_f64(poses[-1][3:]).T + poses[-1][:3]
-        q = random_quaternion(rng)
-        wc = meshes[i][0].astype(np.float64) @ quat_to_matrix_f64(q).T
-        t = wp[np.argmax(wp @ u)] + 0.5 * e * u - wc[np.argmax(wc @ -u)]
+        while True:
+            u = _unit(rng)
+            q = random_quaternion(rng)
+            wc = meshes[i][0].astype(np.float64) @ quat_to_matrix_f64(q).T
+            t = wp[np.argmax(wp @ u)] + 0.5 * e * u - wc[np.argmax(wc @ -u)]
+            if all(np.linalg.norm(t - poses[j][:3]) > bound[i] + bound[j] + 4 * e for j in range(i - 1)):
+                break
         poses.append(np.concatenate([t, q]))
     radius = [float(np.linalg.norm(m[0], axis=1).mean()) for m in meshes]
     return _assemble(meshes, poses, radius, np.zeros((0, 2), np.int32), np.zeros(0), "chain")

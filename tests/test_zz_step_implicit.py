@@ -11,7 +11,9 @@ tol_F sum_c |F_c| per particle (tol_F = 1e-9 for the FP64 form, 1e-5 for
 FP32, the bounds of the force parity tests), so the fixed points differ by
 at most about tol_F dt sum_c |F_c| max(1/m, R/I) times 1 / (1 - rho), rho the
 contraction of the iteration (about 0.2 on the chain); the tests allow ten
-times tol_F dt sum_c |F_c| max(1/m, R/I), taken over particles.
+times tol_F dt sum_c |F_c| max(1/m, R/I), taken over particles.  The chain
+has no crossing triangles (d > 0.5 eps throughout the step), where the
+force direction would be a convention.
 """
 import dataclasses
 
