@@ -366,6 +366,25 @@ int mrdem_picard_update(mrdem_ctx* ctx, int32_t n, const double* vel0,
                         const double* gravity, double dt, double* vel, double* norms,
                         mrdem_stream stream);
 
+/* Contact Hessian for Newton's method on the implicit Euler equations: for
+ * every contact of the list with 0 < d <= 2 eps, the second derivatives of
+ * its energy e(d) = K_s sqrt(mu) eps (1 - d/(2 eps))^2 (Sec. 2 force law) in
+ * the pair's two pose twists, with the closest points free to move, added to
+ * blocks[p] of its pair p (device double [n_pairs*144], row-major 12x12, rows
+ * and columns (t_A, theta_A, t_B, theta_B); t a world translation, theta a
+ * world rotation increment about the particle origin applied on the left of
+ * R; accumulated, the caller zeroes).  The closest points and their features
+ * are recomputed in FP64 from the world triangles (the contact list only
+ * names the triangle pairs), so the blocks do not depend on the precision
+ * form of the detection.  Skipped: crossing triangles (d = 0, where d is not
+ * differentiable) and contacts between parallel features (an edge on a face,
+ * two faces), counted in *skipped (device int64, accumulated, nullable).
+ * Errors: INVALID (null pointers, k_s negative or not finite), CUDA. */
+int mrdem_contact_hessian(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
+                          const int32_t* pair_ab, const double* pair_eps, const double* poses,
+                          const mrdem_contacts* contacts, const double* mass, double k_s,
+                          double* blocks, int64_t* skipped, mrdem_stream stream);
+
 /* Plain GPU form (reported baseline): the contact set by FP64 comparison-based
  * distance over ALL fine triangle pairs of each pair (Algorithm 2), no
  * hierarchy, one kernel launch per particle pair.  Same inputs and outputs as

@@ -267,7 +267,9 @@ def contact_hessian(scene, contacts, poses=None, k_s=1000.0, active_tol=1e-9):
         sum_v sym(g_v r_v^T) - (g_v . r_v) I with g_v = dE/dX_v and
         r_v = X_v - t (the second-order term of the exponential).
     Contacts at d = 0 (crossing triangles) are skipped: d is not
-    differentiable there.  The central differences of the analytic gradient
+    differentiable there; so are contacts between parallel features (more
+    than two free parameters: an edge lying on a face, two faces), where the
+    closest points are not unique.  The central differences of the analytic gradient
     in `pose_hessian` move the rotation of the perturbed pose, which adds
     -1/2 [dE/dtheta]x to each particle's rotation block (the commutator of
     two rotations); `twist_hessian_fd_form` adds it."""
@@ -311,6 +313,8 @@ def contact_hessian(scene, contacts, poses=None, k_s=1000.0, active_tol=1e-9):
             col = np.zeros(6)
             col[3 + j], col[3 + SB[0]] = -1.0, 1.0
             dsig.append(col)
+        if len(dsig) > 2:
+            continue   # parallel features (an edge on a face, two faces): not twice differentiable
         gg = np.kron(sig, r)                                # grad g, [18]
         Hg = np.kron(np.outer(sig, sig), np.eye(3))         # phi_XX
         if dsig:

@@ -363,6 +363,27 @@ def triangle_distance(ctx, P, Q, eps, precision="fp64", sweep=True, stream=None)
     return out
 
 
+def contact_hessian(ctx, hier, pairs, eps, poses, contacts, mass, k_s=1000.0, blocks=None,
+                    stream=None):
+    """Per pair, the 12x12 second derivatives of its contacts' energy in the
+    two pose twists (closest points free).  Returns (blocks float64
+    [P, 12, 12], skipped: device int64 count of contacts between parallel
+    features)."""
+    n = hier.info()["n_particles"]
+    P = _pair_args(hier, pairs, eps, poses, n)
+    _need(mass, torch.float64, (n,), "mass")
+    if blocks is None:
+        blocks = torch.zeros((P, 12, 12), dtype=torch.float64, device=pairs.device)
+    _need(blocks, torch.float64, (P, 12, 12), "blocks")
+    skipped = torch.zeros(1, dtype=torch.int64, device=pairs.device)
+    cs = contacts.struct()
+    L.check(L.load().mrdem_contact_hessian(ctx.handle, hier.handle, P, _p(pairs), _p(eps),
+                                           _p(poses), C.byref(cs), _p(mass), float(k_s),
+                                           _p(blocks), _p(skipped), _stream(stream)),
+            "mrdem_contact_hessian")
+    return blocks, skipped
+
+
 # ---- implicit time step (Algorithm 3)
 
 G_DEFAULT = (0.0, 0.0, -9.81)

@@ -598,6 +598,19 @@ int mrdem_picard_update(mrdem_ctx* c, int32_t n, const double* vel0, const doubl
                               (cudaStream_t)s);
 }
 
+int mrdem_contact_hessian(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
+                          const double* eps, const double* poses, const mrdem_contacts* con,
+                          const double* mass, double k_s, double* blocks, int64_t* skipped,
+                          mrdem_stream s) {
+  int st = check_pair_args(c, h, n_pairs, ab, eps, poses);
+  if (st) return st;
+  if (!contacts_ok(con) || !mass || !(k_s >= 0) || !std::isfinite(k_s)) return MRDEM_ERR_INVALID;
+  if (n_pairs > 0 && !blocks) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_contact_hessian(c, h, n_pairs, ab, eps, poses, con, mass, k_s, blocks, skipped,
+                                (cudaStream_t)s);
+}
+
 static const char* kKernelNames[K_COUNT] = {
     "k_setup", "k_expand", "k_sweep_nodes", "k_tile",  "k_sweep_fine", "k_exact",
     "k_exact64", "k_forces", "k_grad",       "k_plain", "k_tridist", "k_sort",

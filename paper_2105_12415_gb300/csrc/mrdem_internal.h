@@ -276,6 +276,10 @@ int launch_move_poses(mrdem_ctx* ctx, int32_t n, const double* poses0, const dou
 int launch_picard_update(mrdem_ctx* ctx, int32_t n, const double* vel0, const double* ft,
                          const double* mass, const double* inertia, const double* gravity,
                          double dt, double* vel, double* norms, cudaStream_t s);
+int launch_contact_hessian(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
+                           const int32_t* pair_ab, const double* pair_eps, const double* poses,
+                           const mrdem_contacts* c, const double* mass, double k_s,
+                           double* blocks, int64_t* skipped, cudaStream_t s);
 int launch_triangle_distance(mrdem_ctx* ctx, int64_t n, const double* P, const double* Q,
                              const double* eps, int precision, double* dist, double* pa,
                              double* pb, int32_t* feature, float* sx, float* sgap, int32_t* sconv,

@@ -214,6 +214,70 @@ __global__ void __launch_bounds__(kThreads) k_picard(int32_t n, const double* ve
   }
 }
 
+// Rotation matrix (row-major) of a pose's quaternion w, x, y, z (any norm).
+__device__ __forceinline__ void quat_matrix(const double* q, double R[9]) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  const double s = 2.0 / (w * w + x * x + y * y + z * z);
+  R[0] = 1.0 - s * (y * y + z * z); R[1] = s * (x * y - w * z);       R[2] = s * (x * z + w * y);
+  R[3] = s * (x * y + w * z);       R[4] = 1.0 - s * (x * x + z * z); R[5] = s * (y * z - w * x);
+  R[6] = s * (x * z - w * y);       R[7] = s * (y * z + w * x);       R[8] = 1.0 - s * (x * x + y * y);
+}
+
+// World FP64 corners of fine triangle `tri` of particle i.
+__device__ __forceinline__ bool world_triangle(const HierDev& H, const double* poses, int i,
+                                               int tri, V3<double> T[3], V3<double>* t) {
+  if (tri < 0 || tri >= H.tri_off[i + 1] - H.tri_off[i]) return false;
+  const int slot = H.tri_slot[H.tri_off[i] + tri];
+  V3<double> V[3];
+  load_tri64(H, slot, V);
+  const double* p = poses + (int64_t)7 * i;
+  double R[9];
+  quat_matrix(p + 3, R);
+  *t = {p[0], p[1], p[2]};
+  for (int k = 0; k < 3; ++k)
+    T[k] = {R[0] * V[k].x + R[1] * V[k].y + R[2] * V[k].z + p[0],
+            R[3] * V[k].x + R[4] * V[k].y + R[5] * V[k].z + p[1],
+            R[6] * V[k].x + R[7] * V[k].y + R[8] * V[k].z + p[2]};
+  return true;
+}
+
+// A thread per contact: its 12x12 Hessian block (mrdem_step.cuh), added to
+// the pair's block with one atomic per entry.
+__global__ void __launch_bounds__(kThreads) k_hessian(HierDev H, const int32_t* ab,
+                                                      const double* eps, const double* poses,
+                                                      const double* mass, double k_s,
+                                                      mrdem_contacts c, int64_t n_pairs,
+                                                      double* blocks,
+                                                      unsigned long long* skipped) {
+  wait_prior_grid();
+  int64_t n = *c.count;
+  if (n > c.capacity) n = c.capacity;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long parallel = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += step) {
+    const int p = c.pair[k];
+    if (p < 0 || p >= n_pairs) continue;
+    const int A = ab[2 * p], B = ab[2 * p + 1];
+    if (A < 0 || A >= H.n_particles || B < 0 || B >= H.n_particles) continue;
+    V3<double> TA[3], TB[3], tA, tB;
+    if (!world_triangle(H, poses, A, c.tri_a[k], TA, &tA) ||
+        !world_triangle(H, poses, B, c.tri_b[k], TB, &tB))
+      continue;
+    const double mA = mass[A], mB = mass[B];
+    const double ks = k_s * sqrt(mA * mB / (mA + mB));
+    double h[144];
+    for (int q = 0; q < 144; ++q) h[q] = 0.0;
+    const int st = contact_hessian_block(TA, TB, tA, tB, ks, eps[p], h);
+    if (st == 0) {
+      double* o = blocks + 144 * (int64_t)p;
+      for (int q = 0; q < 144; ++q) atomicAdd(o + q, h[q]);
+    } else if (st == 2) {
+      ++parallel;
+    }
+  }
+  if (skipped && parallel) atomicAdd(skipped, parallel);
+}
+
 int ceil_log2(int64_t v) {
   int k = 0;
   while (((int64_t)1 << k) < v) ++k;
@@ -310,6 +374,21 @@ int launch_picard_update(mrdem_ctx* c, int32_t n, const double* vel0, const doub
     launch_after(k_picard, blocks_for(c, n), kThreads, 0, s, n, vel0, ft, mass, inertia, g, dt,
                  vel, reinterpret_cast<unsigned long long*>(norms));
   }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
+
+int launch_contact_hessian(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
+                           const double* eps, const double* poses, const mrdem_contacts* con,
+                           const double* mass, double k_s, double* blocks, int64_t* skipped,
+                           cudaStream_t s) {
+  if (n_pairs == 0 || con->capacity == 0) return MRDEM_OK;
+  ProfScope ps(c, K_STEP, s);
+  const int64_t nb64 = (con->capacity + kThreads - 1) / kThreads;
+  const int64_t lim = (int64_t)c->n_sms * 8;
+  const int nb = (int)(nb64 < lim ? nb64 : lim);
+  launch_after(k_hessian, nb, kThreads, 0, s, h->dev, ab, eps, poses, mass, k_s, *con, n_pairs,
+               blocks, reinterpret_cast<unsigned long long*>(skipped));
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }

@@ -215,3 +215,121 @@ MRDEM_HD void picard_velocity(const double* vel0, const double* ft, double m, do
 }
 
 }  // namespace mrdem
+
+namespace mrdem {
+
+// ---- contact Hessian for Newton's method on the implicit Euler equations
+//
+// Second derivatives of one contact's energy e(d) (Sec. 2 force law,
+// e = K_s sqrt(mu) eps (1 - d/(2 eps))^2) in the two particles' pose twists
+// (world translation; world rotation increment about the particle origin t,
+// on the left of R), with the closest points free to move.  Let the closest
+// points be pa = sum_v s_v X_v on A's active feature and pb on B's (active =
+// barycentric weight above kActiveTol: a vertex, an edge or the face), r =
+// pa - pb = d u, rho_A = pa - t_A, rho_B = -(pb - t_B), and
+//   Z = [I; [rho_A]x; -I; [rho_B]x]   (12 x 3),
+// the twist Jacobian of a point moving rigidly with A minus one moving with
+// B.  The free barycentric parameters q of the active features (at most two
+// for a contact between non-parallel features) have directions G_q (an edge
+// of A's feature, or minus an edge of B's), and
+//   N_q = Z G_q + (G_q x r in the rotation rows of the particle owning q).
+// Eliminating q by the implicit function theorem (the closest points are
+// optimal) gives
+//   H = Z [(e'' - e'/d) u u^T + (e'/d) I] Z^T - (e'/d) N (G G^T)^-1 N^T + R,
+// R the second-order term of the exponential map in each rotation block,
+// sym(g rho^T) - (g . rho) I with g = e' u.  For a vertex against a vertex
+// (no q) the translation block is e'' u u^T + e' (I - u u^T)/d.
+constexpr double kActiveTol = 1e-9;
+
+// Adds the 12x12 block of the contact between world triangles TA (on A) and
+// TB (on B) to out (row-major).  Returns 0 when added, 1 when the
+// triangles are more than 2 eps apart or cross (d = 0: not differentiable),
+// 2 when the active features are parallel (more than two free parameters or
+// a singular G G^T).
+MRDEM_HD int contact_hessian_block(const V3<double> TA[3], const V3<double> TB[3],
+                                   const V3<double>& tA, const V3<double>& tB, double ks,
+                                   double eps, double* out) {
+  typedef V3<double> D;
+  const TriTriResult<double> t = tri_tri_distance<double>(TA, TB);
+  if (!(t.d > 0.0) || t.d > 2.0 * eps) return 1;
+  int SA[3], SB[3], na = 0, nb = 0;
+  double sa = 0.0, sb = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    if (t.wa[i] > kActiveTol) { SA[na++] = i; sa += t.wa[i]; }
+    if (t.wb[i] > kActiveTol) { SB[nb++] = i; sb += t.wb[i]; }
+  }
+  if (na == 0 || nb == 0) return 2;
+  const int nq = (na - 1) + (nb - 1);
+  if (nq > 2) return 2;
+  D pa = {0.0, 0.0, 0.0}, pb = {0.0, 0.0, 0.0};
+  for (int k = 0; k < na; ++k) pa = pa + (t.wa[SA[k]] / sa) * TA[SA[k]];
+  for (int k = 0; k < nb; ++k) pb = pb + (t.wb[SB[k]] / sb) * TB[SB[k]];
+  const D r = pa - pb;
+  const double d = sqrt(dot(r, r));
+  if (!(d > 0.0)) return 1;
+  const D u = (1.0 / d) * r;
+  const double e1 = -ks * (1.0 - d / (2.0 * eps)), e2 = ks / (2.0 * eps);
+  const D rA = pa - tA, rB = -1.0 * (pb - tB);
+  // directions of the free parameters and the particle (0: A, 1: B) of each
+  D G[2];
+  int own[2];
+  int q = 0;
+  for (int k = 1; k < na; ++k, ++q) { G[q] = TA[SA[k]] - TA[SA[0]]; own[q] = 0; }
+  for (int k = 1; k < nb; ++k, ++q) { G[q] = -1.0 * (TB[SB[k]] - TB[SB[0]]); own[q] = 1; }
+  // (G G^T)^-1
+  double K[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  if (nq == 1) {
+    const double g11 = dot(G[0], G[0]);
+    if (!(g11 > 0.0)) return 2;
+    K[0][0] = 1.0 / g11;
+  } else if (nq == 2) {
+    const double g11 = dot(G[0], G[0]), g12 = dot(G[0], G[1]), g22 = dot(G[1], G[1]);
+    const double det = g11 * g22 - g12 * g12;
+    if (!(det > 1e-12 * g11 * g22)) return 2;
+    K[0][0] = g22 / det;
+    K[0][1] = K[1][0] = -g12 / det;
+    K[1][1] = g11 / det;
+  }
+  // Z x for a 3-vector x: a 12-vector
+  auto zmul = [&](const D& x, double* o) {
+    const D a = cross(rA, x), b = cross(rB, x);
+    o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = a.x; o[4] = a.y; o[5] = a.z;
+    o[6] = -x.x; o[7] = -x.y; o[8] = -x.z; o[9] = b.x; o[10] = b.y; o[11] = b.z;
+  };
+  double N[2][12];
+  for (int k = 0; k < nq; ++k) {
+    zmul(G[k], N[k]);
+    const D c = cross(G[k], r);
+    const int o = own[k] ? 9 : 3;
+    N[k][o] += c.x; N[k][o + 1] += c.y; N[k][o + 2] += c.z;
+  }
+  // Z [(e'' - e'/d) u u^T + (e'/d) I] Z^T = a (Zu)(Zu)^T + b sum_c (Z e_c)(Z e_c)^T
+  double zu[12], ze[3][12];
+  zmul(u, zu);
+  zmul(D{1.0, 0.0, 0.0}, ze[0]);
+  zmul(D{0.0, 1.0, 0.0}, ze[1]);
+  zmul(D{0.0, 0.0, 1.0}, ze[2]);
+  const double a = e2 - e1 / d, b = e1 / d;
+  const D g = e1 * u;
+  for (int i = 0; i < 12; ++i)
+    for (int j = 0; j < 12; ++j) {
+      double h = a * zu[i] * zu[j] + b * (ze[0][i] * ze[0][j] + ze[1][i] * ze[1][j] +
+                                          ze[2][i] * ze[2][j]);
+      for (int k = 0; k < nq; ++k)
+        for (int l = 0; l < nq; ++l) h -= b * N[k][i] * K[k][l] * N[l][j];
+      out[12 * i + j] += h;
+    }
+  // second-order term of the exponential map in the rotation blocks
+  const D rho[2] = {rA, rB};
+  for (int p = 0; p < 2; ++p) {
+    const int o = p ? 9 : 3;
+    const double gr[3] = {g.x, g.y, g.z}, rr[3] = {rho[p].x, rho[p].y, rho[p].z};
+    const double gdr = dot(g, rho[p]);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        out[12 * (o + i) + o + j] += 0.5 * (gr[i] * rr[j] + gr[j] * rr[i]) - (i == j ? gdr : 0.0);
+  }
+  return 0;
+}
+
+}  // namespace mrdem

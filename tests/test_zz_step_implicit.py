@@ -242,3 +242,40 @@ def test_free_flight_is_exact(m, ctx, imp):
     assert it == 2
     assert np.array_equal(V.cpu().numpy(), Vr)
     assert np.abs(poses.cpu().numpy() - Pr).max() <= 1e-14 * (1.0 + np.abs(Pr).max())
+
+
+def _hessian_scenes(imp):
+    from tests.test_oracle_implicit import FACING, _colliding_pair, _icosahedra_facing
+    out = [_icosahedra_facing(a, b) for a, b in FACING]
+    for seed in (4, 8):
+        s, _, pairs, eps = _colliding_pair(imp, seed=seed)
+        out.append(dataclasses.replace(s, pairs=pairs, eps=eps))
+    s, _, pairs, eps, _ = _chain_problem(imp)
+    out.append(dataclasses.replace(s, pairs=pairs, eps=eps))
+    return [dataclasses.replace(s, com=np.zeros((s.n_particles, 3))) for s in out]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_contact_hessian_equals_oracle(m, ctx, orc, imp, precision):
+    """The per-pair 12x12 contact Hessian blocks, assembled, equal the
+    oracle's closed-form Hessian (an independent implementation: the general
+    elimination over the six corners) to 1e-10 of its largest entry; every
+    feature pair occurs (vertex-face, crossing edges, vertex-edge,
+    vertex-vertex).  The closest points are recomputed in FP64, so the
+    FP32-form detection gives the same blocks (no contact lies within 1e-3
+    eps of the threshold 2 eps, where the contact sets may differ)."""
+    for s in _hessian_scenes(imp):
+        ref_c = orc.detect(s)
+        assert (np.abs(ref_c["d"] - 2 * s.eps[ref_c["pair"]]) > 1e-3 * s.eps[ref_c["pair"]]).all()
+        Href = imp.contact_hessian(s, ref_c)
+        hier = m.Hierarchy.from_scene(ctx, s)
+        tp, te, tposes, tmass = _t(s.pairs, "int32"), _t(s.eps), _t(s.poses), _t(s.mass)
+        contacts, _ = m.detect(ctx, hier, tp, te, tposes, precision)
+        assert contacts.n() == len(ref_c["d"])
+        blocks, skipped = m.contact_hessian(ctx, hier, tp, te, tposes, contacts, tmass)
+        assert int(skipped.item()) == 0
+        H = np.zeros_like(Href)
+        for p, (a, b) in enumerate(s.pairs):
+            idx = np.r_[6 * a:6 * a + 6, 6 * b:6 * b + 6]
+            H[np.ix_(idx, idx)] += blocks[p].cpu().numpy()
+        assert np.abs(H - Href).max() <= 1e-10 * np.abs(Href).max()
