@@ -145,8 +145,10 @@ def implicit_euler_step_newton(scene, vel, pairs, eps, dt, g=G_DEFAULT, k_s=1000
     converged velocities are the implicit Euler solution; an approximate
     Jacobian only slows the convergence.  stiffness="hessian" uses the full
     pose Hessian (`pose_hessian`, closest points free) instead of the blocks,
-    stiffness="analytic" the same Hessian in closed form (`contact_hessian`).
-    Returns (poses, vel, iterations)."""
+    stiffness="analytic" the same Hessian in closed form (`contact_hessian`,
+    in the form the differences see), "analytic-sym" its symmetric form.
+    Each step is halved until the residual's largest entry drops
+    (backtracking line search).  Returns (poses, vel, iterations)."""
     import dataclasses
 
     from . import grad
@@ -161,30 +163,49 @@ def implicit_euler_step_newton(scene, vel, pairs, eps, dt, g=G_DEFAULT, k_s=1000
     V = v0.copy()
     gext = np.zeros((n, 6))
     gext[:, :3] = m[:, None] * g
-    for it in range(1, max_iter + 1):
+
+    def residual(V):
         poses = moved_poses(scene.poses, V, dt)
-        K = np.zeros((6 * n, 6 * n))
+        c, ft = None, np.zeros((n, 6))
         if base.n_pairs:
             c = detect(base, poses=poses)
             ft, _ = forces(base, c, k_s=k_s, poses=poses)
-            if stiffness == "hessian":
-                K = pose_hessian(scene, poses, pairs, eps, k_s=k_s)
-            elif stiffness == "analytic":
-                _, gp, _ = grad(base, c, k_s=k_s, poses=poses)
-                K = twist_hessian_fd_form(contact_hessian(base, c, poses=poses, k_s=k_s), gp)
-            else:
-                _, _, jac = grad(base, c, k_s=k_s, poses=poses)
-                for p, (a, b) in enumerate(pairs):
-                    idx = np.r_[6 * a:6 * a + 6, 6 * b:6 * b + 6]
-                    K[np.ix_(idx, idx)] += jac[p]
-        else:
-            ft = np.zeros((n, 6))
-        r = (Mdiag * (V - v0).ravel()) / dt - ft.ravel() - gext.ravel()
+        return (Mdiag * (V - v0).ravel()) / dt - ft.ravel() - gext.ravel(), poses, c
+
+    def stiffness_matrix(poses, c):
+        K = np.zeros((6 * n, 6 * n))
+        if not base.n_pairs:
+            return K
+        if stiffness == "hessian":
+            return pose_hessian(scene, poses, pairs, eps, k_s=k_s)
+        if stiffness == "analytic-sym":
+            return contact_hessian(base, c, poses=poses, k_s=k_s)
+        if stiffness == "analytic":
+            _, gp, _ = grad(base, c, k_s=k_s, poses=poses)
+            return twist_hessian_fd_form(contact_hessian(base, c, poses=poses, k_s=k_s), gp)
+        _, _, jac = grad(base, c, k_s=k_s, poses=poses)
+        for p, (a, b) in enumerate(pairs):
+            idx = np.r_[6 * a:6 * a + 6, 6 * b:6 * b + 6]
+            K[np.ix_(idx, idx)] += jac[p]
+        return K
+
+    r, poses, c = residual(V)
+    for it in range(1, max_iter + 1):
         scale = float(np.abs(Mdiag * V.ravel()).max()) / dt + 1e-300
-        if float(np.abs(r).max()) <= tol * scale:
+        rn = float(np.abs(r).max())
+        if rn <= tol * scale:
             break
-        dV = np.linalg.solve(np.diag(Mdiag / dt) + dt * K, -r)
-        V = V + dV.reshape(n, 6)
+        dV = np.linalg.solve(np.diag(Mdiag / dt) + dt * stiffness_matrix(poses, c), -r).reshape(n, 6)
+        # backtracking: halve the step until the residual's largest entry
+        # drops (the contact set and the closest features change between
+        # iterates, so a full step can overshoot)
+        lam = 1.0
+        while True:
+            rt, pt, ct = residual(V + lam * dV)
+            if float(np.abs(rt).max()) < rn or lam < 2.0 ** -30:
+                break
+            lam *= 0.5
+        V, r, poses, c = V + lam * dV, rt, pt, ct
     return moved_poses(scene.poses, V, dt), V, it
 
 
