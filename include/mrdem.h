@@ -385,6 +385,45 @@ int mrdem_contact_hessian(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pair
                           const mrdem_contacts* contacts, const double* mass, double k_s,
                           double* blocks, int64_t* skipped, mrdem_stream stream);
 
+/* Residual of the implicit Euler equations at velocities vel (Newton's
+ * method on Algorithm 3's fixed point):
+ *   res = M (vel - vel0) / dt - force_torque - (m g, 0),
+ * M = diag(m, m, m, I, I, I), force_torque the contact forces and torques at
+ * the geometry moved by dt vel (mrdem_move_poses, mrdem_detect,
+ * mrdem_contact_forces).  Device double [n*6] each; mass, inertia [n];
+ * gravity HOST double [3].  norms (device double [2]) receives
+ * (max |res|, max |M vel| / dt), the convergence test's two sides.  Rounded
+ * operation by operation in the order written.  Errors: INVALID (null
+ * pointers, dt not positive and finite, gravity not finite), CUDA. */
+int mrdem_newton_residual(mrdem_ctx* ctx, int32_t n, const double* vel0, const double* vel,
+                          const double* force_torque, const double* mass, const double* inertia,
+                          const double* gravity, double dt, double* res, double* norms,
+                          mrdem_stream stream);
+
+/* Newton step of the implicit Euler equations: solves
+ *   (M/dt + dt K) x = rhs,   K = sum over pairs of the pair's 12x12 block
+ * (mrdem_contact_hessian's layout) placed at its two particles' twists,
+ * by conjugate gradients with the diagonal as preconditioner (an entry that
+ * is not positive uses M/dt instead), from x = 0, stopping when
+ * |r| <= rel_tol |rhs| or after max_iter iterations; every iteration is
+ * enqueued (no host synchronisation; iterations after convergence do no
+ * work).  pair_ab int32 [n_pairs*2], blocks double [n_pairs*144], mass and
+ * inertia [n], rhs and x [n*6]: device.  info (device double [4]) receives
+ * (iterations, |r|/|rhs|, 1 if p.Ap <= 0 stopped it (K not positive
+ * definite enough; x is then the last iterate, or, when the first
+ * direction p already has p.Ap < 0, the step (r.z / |p.Ap|) p), |rhs|).  The context keeps 240 n + 24 max_iter bytes of
+ * scratch.  Errors: INVALID (null pointers, rhs == x, n > 2^26,
+ * max_iter outside [0, 100000], rel_tol negative), OOM, CUDA. */
+int mrdem_newton_solve(mrdem_ctx* ctx, int32_t n, int64_t n_pairs, const int32_t* pair_ab,
+                       const double* blocks, const double* mass, const double* inertia,
+                       double dt, const double* rhs, double* x, int32_t max_iter, double rel_tol,
+                       double* info, mrdem_stream stream);
+
+/* out = y + a x over m doubles (device; out may be y or x): the trial
+ * velocities of a line search along a Newton step.  Errors: INVALID, CUDA. */
+int mrdem_vel_axpy(mrdem_ctx* ctx, int64_t m, double a, const double* x, const double* y,
+                   double* out, mrdem_stream stream);
+
 /* Plain GPU form (reported baseline): the contact set by FP64 comparison-based
  * distance over ALL fine triangle pairs of each pair (Algorithm 2), no
  * hierarchy, one kernel launch per particle pair.  Same inputs and outputs as

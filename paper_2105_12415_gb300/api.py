@@ -491,6 +491,115 @@ def implicit_euler_step(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inert
     return poses, vel, it, hist
 
 
+def newton_residual(ctx, vel0, vel, force_torque, mass, inertia, dt, res=None, norms=None,
+                    gravity=G_DEFAULT, stream=None):
+    """Residual M (vel - vel0)/dt - (F, tau) - (m g, 0) of the implicit Euler
+    equations; returns (res [n, 6], norms (max |res|, max |M vel|/dt))."""
+    n = vel0.shape[0]
+    for t, name in ((vel0, "vel0"), (vel, "vel"), (force_torque, "force_torque")):
+        _need(t, torch.float64, (n, 6), name)
+    _need(mass, torch.float64, (n,), "mass")
+    _need(inertia, torch.float64, (n,), "inertia")
+    if res is None:
+        res = torch.empty_like(vel0)
+    if norms is None:
+        norms = torch.empty(2, dtype=torch.float64, device=vel0.device)
+    g = (C.c_double * 3)(*[float(x) for x in gravity])
+    L.check(L.load().mrdem_newton_residual(ctx.handle, n, _p(vel0), _p(vel), _p(force_torque),
+                                           _p(mass), _p(inertia), C.cast(g, C.c_void_p),
+                                           float(dt), _p(res), _p(norms), _stream(stream)),
+            "mrdem_newton_residual")
+    return res, norms
+
+
+def newton_solve(ctx, pairs, blocks, mass, inertia, dt, rhs, x=None, max_iter=200, rel_tol=1e-12,
+                 info=None, stream=None):
+    """x with (M/dt + dt K) x = rhs by preconditioned conjugate gradients (K
+    the pair blocks); returns (x [n, 6], info (iterations, relative
+    residual, breakdown flag, |rhs|))."""
+    n = rhs.shape[0]
+    P = pairs.shape[0]
+    _need(rhs, torch.float64, (n, 6), "rhs")
+    _need(blocks, torch.float64, (P, 12, 12), "blocks")
+    if x is None:
+        x = torch.empty_like(rhs)
+    if info is None:
+        info = torch.empty(4, dtype=torch.float64, device=rhs.device)
+    L.check(L.load().mrdem_newton_solve(ctx.handle, n, P, _p(pairs), _p(blocks), _p(mass),
+                                        _p(inertia), float(dt), _p(rhs), _p(x), int(max_iter),
+                                        float(rel_tol), _p(info), _stream(stream)),
+            "mrdem_newton_solve")
+    return x, info
+
+
+def implicit_euler_step_newton(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inertia, pairs,
+                               eps, dt, gravity=G_DEFAULT, k_s=1000.0, precision="fp32",
+                               tol=1e-13, max_iter=50, cg_iter=200, cg_tol=1e-12, contacts=None):
+    """One implicit Euler step by Newton's method in the velocities, on the
+    same equations as the Picard iteration: residual
+    r = M (V - V0)/dt - (F, tau)(moved geometry) - (m g, 0), Jacobian
+    M/dt + dt K with K the contact Hessian blocks (closest points free), the
+    linear system solved by conjugate gradients, each step halved until
+    max |r| drops (backtracking).  Stops when max |r| <= tol max |M V|/dt.
+    Returns (poses, vel, iterations, stats: CG iterations and line-search
+    halvings per Newton iteration)."""
+    lib = L.load()
+    n = poses0.shape[0]
+    dev = poses0.device
+    P = pairs.shape[0]
+    V = vel0.clone()
+    Vt = torch.empty_like(V)
+    poses = torch.empty_like(poses0)
+    com = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    ft = torch.zeros((n, 6), dtype=torch.float64, device=dev)
+    energy = torch.zeros(1, dtype=torch.float64, device=dev)
+    res = torch.empty((n, 6), dtype=torch.float64, device=dev)
+    norms = torch.empty(2, dtype=torch.float64, device=dev)
+    blocks = torch.zeros((P, 12, 12), dtype=torch.float64, device=dev)
+    x = torch.empty((n, 6), dtype=torch.float64, device=dev)
+    info = torch.empty(4, dtype=torch.float64, device=dev)
+    state = {"contacts": contacts}
+
+    def residual(Vc):
+        move_poses(ctx, poses0, Vc, dt, out=poses)
+        ft.zero_()
+        if P:
+            state["contacts"], _ = detect(ctx, hier, pairs, eps, poses, precision,
+                                          contacts=state["contacts"])
+            contact_forces(ctx, hier, pairs, eps, poses, state["contacts"], mass, com, k_s,
+                           force_torque=ft, energy=energy)
+        newton_residual(ctx, vel0, Vc, ft, mass, inertia, dt, res, norms, gravity)
+        return norms.tolist()
+
+    rn, sc = residual(V)
+    stats = []
+    it = 0
+    for it in range(1, max_iter + 1):
+        if rn <= tol * (sc + 1e-300):
+            break
+        if P:
+            blocks.zero_()
+            contact_hessian(ctx, hier, pairs, eps, poses, state["contacts"], mass, k_s,
+                            blocks=blocks)
+        newton_solve(ctx, pairs, blocks, mass, inertia, dt, res, x, cg_iter, cg_tol, info)
+        cg = info.tolist()
+        lam, halvings = 1.0, 0
+        while True:
+            L.check(lib.mrdem_vel_axpy(ctx.handle, 6 * n, -lam, _p(x), _p(V), _p(Vt), None),
+                    "mrdem_vel_axpy")
+            rt, st = residual(Vt)
+            if rt < rn or lam < 2.0 ** -30:
+                break
+            lam *= 0.5
+            halvings += 1
+        V, Vt = Vt, V
+        rn, sc = rt, st
+        stats.append({"cg_iterations": int(cg[0]), "cg_residual": cg[1], "cg_breakdown": cg[2] != 0,
+                      "halvings": halvings})
+    move_poses(ctx, poses0, V, dt, out=poses)
+    return poses, V, it, stats
+
+
 class ContactProblem:
     """Everything the energy of a particle batch depends on, resident on the device."""
 

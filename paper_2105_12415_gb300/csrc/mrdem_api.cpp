@@ -181,6 +181,7 @@ int mrdem_destroy(mrdem_ctx* c) {
   cudaFree(c->merge_seg);
   cudaFree(c->merge_mem);
   cudaFree(c->broad_mem);
+  cudaFree(c->cg_mem);
   cudaFree(c->frames);
   cudaFree(c->counters);
   cudaFree(c->status);
@@ -609,6 +610,45 @@ int mrdem_contact_hessian(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, co
   DeviceGuard g(c->device);
   return launch_contact_hessian(c, h, n_pairs, ab, eps, poses, con, mass, k_s, blocks, skipped,
                                 (cudaStream_t)s);
+}
+
+int mrdem_newton_residual(mrdem_ctx* c, int32_t n, const double* vel0, const double* vel,
+                          const double* force_torque, const double* mass, const double* inertia,
+                          const double* gravity, double dt, double* res, double* norms,
+                          mrdem_stream s) {
+  if (!c || n < 0 || !gravity || !norms || !(dt > 0.0) || !std::isfinite(dt))
+    return MRDEM_ERR_INVALID;
+  if (n > 0 && (!vel0 || !vel || !force_torque || !mass || !inertia || !res))
+    return MRDEM_ERR_INVALID;
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(gravity[k])) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_newton_residual(c, n, vel0, vel, force_torque, mass, inertia, gravity, dt, res,
+                                norms, (cudaStream_t)s);
+}
+
+int mrdem_newton_solve(mrdem_ctx* c, int32_t n, int64_t n_pairs, const int32_t* ab,
+                       const double* blocks, const double* mass, const double* inertia, double dt,
+                       const double* rhs, double* x, int32_t max_iter, double rel_tol,
+                       double* info, mrdem_stream s) {
+  if (!c || n < 0 || n > ((int32_t)1 << 26) || n_pairs < 0 || n_pairs >= (int64_t)1 << 31 ||
+      !info || !(dt > 0.0) || !std::isfinite(dt) || max_iter < 0 || max_iter > 100000 ||
+      !(rel_tol >= 0.0) || !std::isfinite(rel_tol))
+    return MRDEM_ERR_INVALID;
+  if (n > 0 && (!mass || !inertia || !rhs || !x)) return MRDEM_ERR_INVALID;
+  if (n_pairs > 0 && (!ab || !blocks)) return MRDEM_ERR_INVALID;
+  if (n > 0 && (const void*)rhs == (const void*)x) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_newton_solve(c, n, n_pairs, ab, blocks, mass, inertia, dt, rhs, x, max_iter,
+                             rel_tol, info, (cudaStream_t)s);
+}
+
+int mrdem_vel_axpy(mrdem_ctx* c, int64_t m, double a, const double* x, const double* y,
+                   double* out, mrdem_stream s) {
+  if (!c || m < 0 || !std::isfinite(a)) return MRDEM_ERR_INVALID;
+  if (m > 0 && (!x || !y || !out)) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_vel_axpy(c, m, a, x, y, out, (cudaStream_t)s);
 }
 
 static const char* kKernelNames[K_COUNT] = {

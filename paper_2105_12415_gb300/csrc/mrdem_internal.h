@@ -202,6 +202,9 @@ struct mrdem_ctx {
   // and counts, bucket ends (cap_broad bytes)
   void* broad_mem = nullptr;
   size_t cap_broad = 0;
+  // conjugate-gradient solve of the Newton step: state, scalars, vectors
+  void* cg_mem = nullptr;
+  size_t cap_cg = 0;
   double* frames = nullptr;  // [cap_frames * 16]: per particle R (9), t (3), world com (3)
   int64_t cap_frames = 0;
   unsigned long long* counters = nullptr;  // [CNT_TOTAL]
@@ -280,6 +283,16 @@ int launch_contact_hessian(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pai
                            const int32_t* pair_ab, const double* pair_eps, const double* poses,
                            const mrdem_contacts* c, const double* mass, double k_s,
                            double* blocks, int64_t* skipped, cudaStream_t s);
+int launch_newton_residual(mrdem_ctx* ctx, int32_t n, const double* vel0, const double* vel,
+                           const double* ft, const double* mass, const double* inertia,
+                           const double* gravity, double dt, double* res, double* norms,
+                           cudaStream_t s);
+int launch_vel_axpy(mrdem_ctx* ctx, int64_t m, double a, const double* x, const double* y,
+                    double* out, cudaStream_t s);
+int launch_newton_solve(mrdem_ctx* ctx, int32_t n, int64_t n_pairs, const int32_t* pair_ab,
+                        const double* blocks, const double* mass, const double* inertia,
+                        double dt, const double* rhs, double* x, int32_t max_iter, double rel_tol,
+                        double* info, cudaStream_t s);
 int launch_triangle_distance(mrdem_ctx* ctx, int64_t n, const double* P, const double* Q,
                              const double* eps, int precision, double* dist, double* pa,
                              double* pb, int32_t* feature, float* sx, float* sgap, int32_t* sconv,

@@ -278,6 +278,232 @@ __global__ void __launch_bounds__(kThreads) k_hessian(HierDev H, const int32_t* 
   if (skipped && parallel) atomicAdd(skipped, parallel);
 }
 
+// ---- Newton's method: residual, and a Jacobi-preconditioned conjugate
+// gradient solve of (M/dt + dt K) x = b with K the pair blocks
+
+__global__ void __launch_bounds__(kThreads) k_residual(int32_t n, const double* vel0,
+                                                       const double* vel, const double* ft,
+                                                       const double* mass,
+                                                       const double* inertia, Gravity grav,
+                                                       double dt, double* res,
+                                                       unsigned long long* norms) {
+  wait_prior_grid();
+  double rmax = 0.0, smax = 0.0;
+  const int32_t step = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+    double v0[6], v[6], f[6], out[6], a, b;
+    for (int k = 0; k < 6; ++k) {
+      v0[k] = vel0[(int64_t)6 * i + k];
+      v[k] = vel[(int64_t)6 * i + k];
+      f[k] = ft[(int64_t)6 * i + k];
+    }
+    newton_residual(v0, v, f, mass[i], inertia[i], grav.g, dt, out, &a, &b);
+    for (int k = 0; k < 6; ++k) res[(int64_t)6 * i + k] = out[k];
+    rmax = dmax_nan(rmax, a);
+    smax = dmax_nan(smax, b);
+  }
+  rmax = warp_max(rmax);
+  smax = warp_max(smax);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(norms, (unsigned long long)__double_as_longlong(fabs(rmax)));
+    atomicMax(norms + 1, (unsigned long long)__double_as_longlong(fabs(smax)));
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_vel_axpy(int64_t m, double a, const double* x,
+                                                       const double* y, double* out) {
+  wait_prior_grid();
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step)
+    out[i] = y[i] + a * x[i];
+}
+
+struct CgState {
+  int32_t done, iters, breakdown, pad;
+};
+
+// Conjugate-gradient working set: vectors of 6n unknowns (x is the caller's
+// output), and per iteration k the scalars rz[k] = r.z, pap[k] = p.Ap and
+// rr[k] = r.r, summed with atomics.
+struct CgView {
+  double *x, *r, *z, *p, *ap, *diag;
+  double *rz, *pap, *rr;
+  CgState* st;
+  const double* mass;
+  const double* inertia;
+  double dt;
+  int32_t n;
+};
+
+__device__ __forceinline__ double cg_mdt(const CgView& v, int64_t i) {
+  const int32_t part = (int32_t)(i / 6);
+  return (i % 6 < 3 ? v.mass[part] : v.inertia[part]) / v.dt;
+}
+
+__device__ __forceinline__ double warp_sum_d(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_init(CgView v, const double* rhs) {
+  wait_prior_grid();
+  const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step) {
+    v.x[i] = 0.0;
+    v.r[i] = rhs[i];
+    v.diag[i] = cg_mdt(v, i);
+  }
+}
+
+// diagonal of the pair blocks into the preconditioner
+__global__ void __launch_bounds__(kThreads) k_cg_diag_pairs(CgView v, int64_t n_pairs,
+                                                            const int32_t* ab,
+                                                            const double* blocks) {
+  wait_prior_grid();
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_pairs; q += step) {
+    const int A = ab[2 * q], B = ab[2 * q + 1];
+    if (A < 0 || A >= v.n || B < 0 || B >= v.n) continue;
+    const double* Bq = blocks + 144 * q;
+    for (int k = 0; k < 6; ++k) {
+      atomicAdd(v.diag + (int64_t)6 * A + k, v.dt * Bq[13 * k]);
+      atomicAdd(v.diag + (int64_t)6 * B + k, v.dt * Bq[13 * (6 + k)]);
+    }
+  }
+}
+
+__device__ __forceinline__ double cg_precond(const CgView& v, int64_t i) {
+  const double d = v.diag[i];
+  return d > 0.0 ? d : cg_mdt(v, i);  // an indefinite diagonal falls back to M/dt
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_init2(CgView v) {
+  wait_prior_grid();
+  const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step) {
+    const double r = v.r[i], z = r / cg_precond(v, i);
+    v.z[i] = z;
+    v.p[i] = z;
+    rz += r * z;
+    rr += r * r;
+  }
+  rz = warp_sum_d(rz);
+  rr = warp_sum_d(rr);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(v.rz, rz);
+    atomicAdd(v.rr, rr);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_ap_diag(CgView v) {
+  wait_prior_grid();
+  if (v.st->done) return;
+  const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step)
+    v.ap[i] = cg_mdt(v, i) * v.p[i];
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_ap_pairs(CgView v, int64_t n_pairs,
+                                                          const int32_t* ab,
+                                                          const double* blocks) {
+  wait_prior_grid();
+  if (v.st->done) return;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_pairs; q += step) {
+    const int A = ab[2 * q], B = ab[2 * q + 1];
+    if (A < 0 || A >= v.n || B < 0 || B >= v.n) continue;
+    double y[12];
+    block_mul(blocks + 144 * q, v.p + (int64_t)6 * A, v.p + (int64_t)6 * B, y);
+    for (int k = 0; k < 6; ++k) {
+      atomicAdd(v.ap + (int64_t)6 * A + k, v.dt * y[k]);
+      atomicAdd(v.ap + (int64_t)6 * B + k, v.dt * y[6 + k]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_pap(CgView v, int k) {
+  wait_prior_grid();
+  if (v.st->done) return;
+  const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step)
+    s += v.p[i] * v.ap[i];
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) atomicAdd(v.pap + k, s);
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_step(CgView v, int k) {
+  wait_prior_grid();
+  if (v.st->done) return;
+  const double pap = v.pap[k];
+  const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
+  if (!(pap > 0.0)) {
+    // breakdown (flagged by k_cg_check): negative curvature along the first
+    // direction still gives a step along it, so that x is not left at zero
+    if (k == 0 && pap < 0.0) {
+      const double a = v.rz[0] / -pap;
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step)
+        v.x[i] += a * v.p[i];
+    }
+    return;
+  }
+  const double alpha = v.rz[k] / pap;
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step) {
+    v.x[i] += alpha * v.p[i];
+    const double r = v.r[i] - alpha * v.ap[i];
+    const double z = r / cg_precond(v, i);
+    v.r[i] = r;
+    v.z[i] = z;
+    rz += r * z;
+    rr += r * r;
+  }
+  rz = warp_sum_d(rz);
+  rr = warp_sum_d(rr);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(v.rz + k + 1, rz);
+    atomicAdd(v.rr + k + 1, rr);
+  }
+}
+
+// one thread: stop on convergence (|r|^2 <= tol2 |r0|^2) or breakdown
+// (p.Ap <= 0: the matrix is not positive definite along p)
+__global__ void k_cg_check(CgView v, int k, double tol2) {
+  wait_prior_grid();
+  CgState s = *v.st;
+  if (s.done) return;
+  if (k >= 0 && !(v.pap[k] > 0.0)) {
+    s.done = 1;
+    s.breakdown = 1;
+    s.iters = k;
+  } else if (v.rr[k + 1] <= tol2 * v.rr[0]) {
+    s.done = 1;
+    s.iters = k + 1;
+  }
+  *v.st = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_dir(CgView v, int k) {
+  wait_prior_grid();
+  if (v.st->done) return;
+  const double beta = v.rz[k + 1] / v.rz[k];
+  const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step)
+    v.p[i] = v.z[i] + beta * v.p[i];
+}
+
+__global__ void k_cg_finish(CgView v, int max_iter, double* info) {
+  wait_prior_grid();
+  const CgState s = *v.st;
+  const int it = s.done ? s.iters : max_iter;
+  info[0] = (double)it;
+  info[1] = v.rr[0] > 0.0 ? sqrt(v.rr[it] / v.rr[0]) : 0.0;
+  info[2] = (double)s.breakdown;
+  info[3] = sqrt(v.rr[0]);
+}
+
 int ceil_log2(int64_t v) {
   int k = 0;
   while (((int64_t)1 << k) < v) ++k;
@@ -389,6 +615,97 @@ int launch_contact_hessian(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, c
   const int nb = (int)(nb64 < lim ? nb64 : lim);
   launch_after(k_hessian, nb, kThreads, 0, s, h->dev, ab, eps, poses, mass, k_s, *con, n_pairs,
                blocks, reinterpret_cast<unsigned long long*>(skipped));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
+
+int launch_newton_residual(mrdem_ctx* c, int32_t n, const double* vel0, const double* vel,
+                           const double* ft, const double* mass, const double* inertia,
+                           const double* gravity, double dt, double* res, double* norms,
+                           cudaStream_t s) {
+  cudaMemsetAsync(norms, 0, 2 * sizeof(double), s);
+  if (n > 0) {
+    ProfScope ps(c, K_STEP, s);
+    Gravity g{{gravity[0], gravity[1], gravity[2]}};
+    launch_after(k_residual, blocks_for(c, n), kThreads, 0, s, n, vel0, vel, ft, mass, inertia, g,
+                 dt, res, reinterpret_cast<unsigned long long*>(norms));
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
+
+int launch_vel_axpy(mrdem_ctx* c, int64_t m, double a, const double* x, const double* y,
+                    double* out, cudaStream_t s) {
+  if (m > 0) {
+    ProfScope ps(c, K_STEP, s);
+    launch_after(k_vel_axpy, blocks_for(c, m), kThreads, 0, s, m, a, x, y, out);
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
+
+// Conjugate-gradient scratch: five vectors of 6n doubles, 3 (max_iter + 1)
+// scalars and the state record.
+static int ensure_cg(mrdem_ctx* c, int32_t n, int32_t max_iter, CgView* v) {
+  const size_t m = (size_t)6 * n, ns = 3 * ((size_t)max_iter + 1);
+  const size_t bytes = sizeof(double) * (5 * m + ns) + 64;
+  if (bytes > c->cap_cg) {
+    cudaFree(c->cg_mem);
+    c->cg_mem = nullptr;
+    c->cap_cg = 0;
+    if (cudaMalloc(&c->cg_mem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->cg_mem = nullptr;
+      return MRDEM_ERR_OOM;
+    }
+    c->cap_cg = bytes;
+  }
+  unsigned char* p = static_cast<unsigned char*>(c->cg_mem);
+  v->st = reinterpret_cast<CgState*>(p);
+  double* d = reinterpret_cast<double*>(p + 64);
+  v->rz = d;
+  v->pap = d + (max_iter + 1);
+  v->rr = d + 2 * ((size_t)max_iter + 1);
+  d += ns;
+  v->r = d;
+  v->z = d + m;
+  v->p = d + 2 * m;
+  v->ap = d + 3 * m;
+  v->diag = d + 4 * m;
+  return MRDEM_OK;
+}
+
+int launch_newton_solve(mrdem_ctx* c, int32_t n, int64_t n_pairs, const int32_t* ab,
+                        const double* blocks, const double* mass, const double* inertia,
+                        double dt, const double* rhs, double* x, int32_t max_iter, double rel_tol,
+                        double* info, cudaStream_t s) {
+  CgView v;
+  int st = ensure_cg(c, n, max_iter, &v);
+  if (st) return st;
+  v.x = x;
+  v.mass = mass;
+  v.inertia = inertia;
+  v.dt = dt;
+  v.n = n;
+  const size_t ns = 3 * ((size_t)max_iter + 1);
+  ProfScope ps(c, K_STEP, s);
+  cudaMemsetAsync(c->cg_mem, 0, 64 + sizeof(double) * ns, s);
+  const int64_t m = (int64_t)6 * n;
+  const int nd = blocks_for(c, m > 0 ? m : 1), np = blocks_for(c, n_pairs > 0 ? n_pairs : 1);
+  const double tol2 = rel_tol * rel_tol;
+  launch_after(k_cg_init, nd, kThreads, 0, s, v, rhs);
+  if (n_pairs > 0) launch_after(k_cg_diag_pairs, np, kThreads, 0, s, v, n_pairs, ab, blocks);
+  launch_after(k_cg_init2, nd, kThreads, 0, s, v);
+  launch_after(k_cg_check, 1, 1, 0, s, v, -1, tol2);
+  for (int k = 0; k < max_iter; ++k) {
+    launch_after(k_cg_ap_diag, nd, kThreads, 0, s, v);
+    if (n_pairs > 0) launch_after(k_cg_ap_pairs, np, kThreads, 0, s, v, n_pairs, ab, blocks);
+    launch_after(k_cg_pap, nd, kThreads, 0, s, v, k);
+    launch_after(k_cg_step, nd, kThreads, 0, s, v, k);
+    launch_after(k_cg_check, 1, 1, 0, s, v, k, tol2);
+    launch_after(k_cg_dir, nd, kThreads, 0, s, v, k);
+  }
+  launch_after(k_cg_finish, 1, 1, 0, s, v, max_iter, info);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }

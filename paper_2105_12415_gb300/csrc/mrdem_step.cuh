@@ -333,3 +333,39 @@ MRDEM_HD int contact_hessian_block(const V3<double> TA[3], const V3<double> TB[3
 }
 
 }  // namespace mrdem
+
+namespace mrdem {
+
+// Residual of the implicit Euler equations at velocities V (Newton's
+// method): r = M (V - V0) / dt - (F, tau)(geometry moved by dt V) - (m g, 0),
+// M = diag(m, m, m, I, I, I), rounded operation by operation in that order.
+// Returns max_k |r_k| and max_k |M_k V_k| / dt (the scale of the
+// convergence test) through *rmax and *smax.
+MRDEM_HD void newton_residual(const double* vel0, const double* vel, const double* ft, double m,
+                              double inertia, const double g[3], double dt, double* out,
+                              double* rmax, double* smax) {
+  double a = 0.0, s = 0.0;
+  for (int k = 0; k < 6; ++k) {
+    const double mk = k < 3 ? m : inertia;
+    double r = bp_add(bp_mul(mk, vel[k] - vel0[k]) / dt, -ft[k]);
+    if (k < 3) r = bp_add(r, -bp_mul(m, g[k]));
+    const double sv = fabs(bp_mul(mk, vel[k])) / dt;
+    out[k] = r;
+    a = (fabs(r) > a || r != r) ? fabs(r) : a;
+    s = (sv > s || sv != sv) ? sv : s;
+  }
+  *rmax = a;
+  *smax = s;
+}
+
+// 12x12 block times the 12-vector (x_A, x_B), row-major block.
+MRDEM_HD void block_mul(const double* B, const double* xa, const double* xb, double* y) {
+  for (int i = 0; i < 12; ++i) {
+    double acc = 0.0;
+    for (int j = 0; j < 6; ++j) acc += B[12 * i + j] * xa[j];
+    for (int j = 0; j < 6; ++j) acc += B[12 * i + 6 + j] * xb[j];
+    y[i] = acc;
+  }
+}
+
+}  // namespace mrdem

@@ -279,3 +279,117 @@ def test_contact_hessian_equals_oracle(m, ctx, orc, imp, precision):
             idx = np.r_[6 * a:6 * a + 6, 6 * b:6 * b + 6]
             H[np.ix_(idx, idx)] += blocks[p].cpu().numpy()
         assert np.abs(H - Href).max() <= 1e-10 * np.abs(Href).max()
+
+
+def test_newton_residual_closed_form(m, ctx):
+    rng = np.random.default_rng(11)
+    n = 500
+    v0, v, ft = rng.normal(size=(n, 6)), rng.normal(size=(n, 6)), rng.normal(size=(n, 6)) * 50
+    mass, inertia = rng.uniform(0.5, 2.0, n), rng.uniform(0.1, 1.0, n)
+    dt, g = 1e-3, (0.3, 0.0, -9.81)
+    res, norms = m.newton_residual(ctx, _t(v0), _t(v), _t(ft), _t(mass), _t(inertia), dt, gravity=g)
+    Md = np.concatenate([np.repeat(mass[:, None], 3, 1), np.repeat(inertia[:, None], 3, 1)], 1)
+    gext = np.zeros((n, 6))
+    gext[:, :3] = mass[:, None] * np.array(g)
+    want = (Md * (v - v0)) / dt - ft - gext
+    assert np.array_equal(res.cpu().numpy(), want)
+    rn, sc = norms.cpu().numpy()
+    assert rn == np.abs(want).max() and sc == np.abs(Md * v).max() / dt
+
+
+def _system(rng, n, pairs, spd=True):
+    P = len(pairs)
+    Q = rng.normal(size=(P, 12, 12))
+    blocks = Q @ Q.transpose(0, 2, 1) if spd else -50.0 * np.repeat(np.eye(12)[None], P, 0)
+    mass, inertia = rng.uniform(0.5, 2.0, n), rng.uniform(0.1, 1.0, n)
+    return blocks, mass, inertia
+
+
+def _assemble(n, pairs, blocks, mass, inertia, dt):
+    Md = np.concatenate([np.repeat(mass[:, None], 3, 1), np.repeat(inertia[:, None], 3, 1)], 1).ravel()
+    A = np.diag(Md / dt)
+    for p, (a, b) in enumerate(pairs):
+        idx = np.r_[6 * a:6 * a + 6, 6 * b:6 * b + 6]
+        A[np.ix_(idx, idx)] += dt * blocks[p]
+    return A, Md
+
+
+def test_newton_solve_conjugate_gradients(m, ctx):
+    """The preconditioned conjugate-gradient solve of (M/dt + dt K) x = b
+    equals a dense solve of the assembled matrix (K positive semi-definite
+    pair blocks on a random pair graph, particles sharing several pairs)."""
+    rng = np.random.default_rng(12)
+    n = 40
+    pairs = np.array(sorted({tuple(sorted(rng.choice(n, 2, replace=False))) for _ in range(90)}),
+                     np.int32)
+    blocks, mass, inertia = _system(rng, n, pairs)
+    dt = 0.05
+    A, _ = _assemble(n, pairs, blocks, mass, inertia, dt)
+    b = rng.normal(size=(n, 6))
+    x, info = m.newton_solve(ctx, _t(pairs, "int32"), _t(blocks), _t(mass), _t(inertia), dt, _t(b),
+                             max_iter=400, rel_tol=1e-13)
+    want = np.linalg.solve(A, b.ravel()).reshape(n, 6)
+    it, rel, brk, bn = info.cpu().numpy()
+    assert brk == 0 and 0 < it < 400 and rel <= 1e-13
+    assert abs(bn - np.linalg.norm(b)) <= 1e-12 * bn
+    assert np.abs(x.cpu().numpy() - want).max() <= 1e-10 * np.abs(want).max()
+    # no pairs: x = b dt / M exactly up to rounding, in one iteration
+    x0, info0 = m.newton_solve(ctx, _t(np.zeros((0, 2)), "int32"), _t(np.zeros((0, 12, 12))),
+                               _t(mass), _t(inertia), dt, _t(b), max_iter=10, rel_tol=1e-14)
+    Md = np.concatenate([np.repeat(mass[:, None], 3, 1), np.repeat(inertia[:, None], 3, 1)], 1)
+    assert np.abs(x0.cpu().numpy() - b * dt / Md).max() <= 1e-14 * np.abs(b * dt / Md).max()
+    assert info0.cpu().numpy()[0] == 1
+    # zero right-hand side: x = 0, no iteration
+    xz, infoz = m.newton_solve(ctx, _t(pairs, "int32"), _t(blocks), _t(mass), _t(inertia), dt,
+                               _t(np.zeros((n, 6))), max_iter=10)
+    assert (xz.cpu().numpy() == 0).all() and infoz.cpu().numpy()[0] == 0
+
+
+def test_newton_solve_reports_negative_curvature(m, ctx):
+    """Blocks that make the matrix indefinite along the first direction stop
+    the solve at once with the breakdown flag and a step along that
+    direction, (r.z / |p.Ap|) p with p = z = b / diag (an entry of the
+    diagonal that is not positive uses M/dt)."""
+    rng = np.random.default_rng(13)
+    n = 6
+    pairs = np.array([[0, 1], [2, 3], [4, 5]], np.int32)
+    blocks, mass, inertia = _system(rng, n, pairs, spd=False)
+    dt = 0.5
+    A, Md = _assemble(n, pairs, blocks, mass, inertia, dt)
+    b = rng.normal(size=(n, 6))
+    x, info = m.newton_solve(ctx, _t(pairs, "int32"), _t(blocks), _t(mass), _t(inertia), dt, _t(b),
+                             max_iter=10)
+    d = np.diag(A)
+    d = np.where(d > 0, d, Md / dt)
+    z = b.ravel() / d
+    pap = z @ A @ z
+    assert pap < 0
+    it, _, brk, _ = info.cpu().numpy()
+    assert brk == 1 and it == 0
+    want = (b.ravel() @ z) / -pap * z
+    assert np.abs(x.cpu().numpy().ravel() - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("case", [4, 8, "chain"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_newton_step_reaches_the_picard_fixed_point(m, ctx, orc, imp, case, precision, tol):
+    """Newton's method on the GPU (contact Hessian blocks, conjugate
+    gradients, backtracking) reaches the oracle's Picard fixed point in a
+    handful of iterations (the oracle's Newton needs 5 to 10 here, Picard
+    18 to 149), within the fixed-point bound of the Picard test."""
+    from tests.test_oracle_implicit import _colliding_pair
+    if case == "chain":
+        s, _, pairs, eps, vel = _chain_problem(imp)
+        dt = 2e-4
+    else:
+        s, vel, pairs, eps = _colliding_pair(imp, seed=case)
+        dt = 5e-4
+    P, V, _, _ = imp.implicit_euler_step(s, vel, pairs, eps, dt, tol=2e-13, max_iter=2000)
+    hier = m.Hierarchy.from_scene(ctx, s)
+    inertia = 0.4 * s.mass * s.radius ** 2
+    poses, Vg, it, stats = m.implicit_euler_step_newton(
+        ctx, hier, _t(s.poses), _t(vel), _t(s.mass), _t(inertia), _t(pairs, "int32"), _t(eps), dt,
+        precision=precision, tol=tol, max_iter=30)
+    assert it < (16 if precision == "fp64" else 30), stats
+    lim = _fixed_point_bound(orc, s, pairs, eps, P, dt, precision) + 10 * tol * np.abs(V).max()
+    assert np.abs(Vg.cpu().numpy() - V).max() <= lim, (np.abs(Vg.cpu().numpy() - V).max(), lim)
