@@ -1,0 +1,121 @@
+// Host build of the implicit step's device functions (mrdem_step.cuh) for the
+// CPU tests: the broad phase driven through the same sequence of steps as its
+// kernels (bounds, cells, bucket scan, scatter, count, scan, write and sort),
+// the pose update, and the per-contact Hessian block.  Test infrastructure:
+// the library itself runs these functions only in its CUDA kernels.
+#include <cmath>
+#include <vector>
+
+#include "mrdem_step.cuh"
+
+using namespace mrdem;
+
+extern "C" long long hs_broad_phase(int n, const double* poses, const double* bound,
+                                    const double* radius, double eps_rel, int* pairs,
+                                    double* pair_eps, long long cap, unsigned shuffle) {
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, rb = 0.0, rr = 0.0;
+  for (int i = 0; i < n; ++i) {
+    for (int k = 0; k < 3; ++k) lo[k] = fmin(lo[k], poses[7 * i + k]);
+    rb = fmax(rb, bound[i]);
+    rr = fmax(rr, radius[i]);
+  }
+  const double h = bp_cell_side(rb, rr, eps_rel), inv_h = 1.0 / h;
+  int log2_t = 6;
+  while ((1LL << log2_t) < 2LL * n) ++log2_t;
+  const long long t = 1LL << log2_t;
+  std::vector<BroadCell> cell(n);
+  std::vector<int32_t> order(n), bucket_end(t, 0), cnt(n);
+  BroadWork w{cell.data(), order.data(), bucket_end.data(), log2_t};
+  for (int i = 0; i < n; ++i) {
+    BroadCell c;
+    c.x = bp_cell(poses[7 * i], lo[0], inv_h);
+    c.y = bp_cell(poses[7 * i + 1], lo[1], inv_h);
+    c.z = bp_cell(poses[7 * i + 2], lo[2], inv_h);
+    c.b = bp_bucket(c.x, c.y, c.z, log2_t);
+    cell[i] = c;
+    ++bucket_end[c.b];
+  }
+  long long run = 0;
+  for (long long b = 0; b < t; ++b) {
+    const int c = bucket_end[b];
+    bucket_end[b] = (int32_t)run;
+    run += c;
+  }
+  // the kernel's atomics group a bucket's particles in any order: scatter
+  // them in a shuffled order
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  unsigned s = shuffle;
+  for (int i = n - 1; i > 0 && shuffle; --i) {
+    s = s * 1103515245u + 12345u;
+    const int j = (int)(s % (unsigned)(i + 1));
+    const int tmp = idx[i];
+    idx[i] = idx[j];
+    idx[j] = tmp;
+  }
+  for (int q = 0; q < n; ++q) order[bucket_end[cell[idx[q]].b]++] = idx[q];
+  const BroadIn in{poses, bound, radius, eps_rel, n};
+  for (int i = 0; i < n; ++i) cnt[i] = bp_visit(in, w, i, [](int32_t, double) {});
+  long long total = 0;
+  for (int i = 0; i < n; ++i) {
+    const int c = cnt[i];
+    cnt[i] = (int32_t)total;
+    total += c;
+  }
+  if (total > cap) return total;
+  for (int i = 0; i < n; ++i) {
+    const long long o = cnt[i], m = (i + 1 < n ? cnt[i + 1] : total) - o;
+    long long k = 0;
+    bp_visit(in, w, i, [&](int32_t j, double e) {
+      if (k < m) {
+        pairs[2 * (o + k) + 1] = j;
+        pair_eps[o + k] = e;
+      }
+      ++k;
+    });
+    for (long long a = o + 1; a < o + m; ++a) {
+      const int j = pairs[2 * a + 1];
+      const double e = pair_eps[a];
+      long long b = a - 1;
+      while (b >= o && pairs[2 * b + 1] > j) {
+        pairs[2 * (b + 1) + 1] = pairs[2 * b + 1];
+        pair_eps[b + 1] = pair_eps[b];
+        --b;
+      }
+      pairs[2 * (b + 1) + 1] = j;
+      pair_eps[b + 1] = e;
+    }
+    for (long long a = o; a < o + m; ++a) pairs[2 * a] = i;
+  }
+  return total;
+}
+
+extern "C" void hs_move_poses(int n, const double* poses0, const double* vel, double dt,
+                              double* out) {
+  for (int i = 0; i < n; ++i) move_pose(poses0 + 7 * i, vel + 6 * i, dt, out + 7 * i);
+}
+
+extern "C" int hs_contact_hessian(const double* A, const double* B, const double* tA,
+                                  const double* tB, double ks, double eps, double* out) {
+  V3<double> TA[3], TB[3];
+  for (int k = 0; k < 3; ++k) {
+    TA[k] = {A[3 * k], A[3 * k + 1], A[3 * k + 2]};
+    TB[k] = {B[3 * k], B[3 * k + 1], B[3 * k + 2]};
+  }
+  return contact_hessian_block(TA, TB, V3<double>{tA[0], tA[1], tA[2]},
+                               V3<double>{tB[0], tB[1], tB[2]}, ks, eps, out);
+}
+
+extern "C" void hs_picard(int n, const double* vel0, const double* ft, const double* mass,
+                          const double* inertia, const double* g, double dt, double* vel,
+                          double* norms) {
+  norms[0] = norms[1] = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double out[6], c, s;
+    picard_velocity(vel0 + 6 * i, ft + 6 * i, mass[i], inertia[i], g, dt, vel + 6 * i, out, &c,
+                    &s);
+    for (int k = 0; k < 6; ++k) vel[6 * i + k] = out[k];
+    norms[0] = c > norms[0] ? c : norms[0];
+    norms[1] = s > norms[1] ? s : norms[1];
+  }
+}
