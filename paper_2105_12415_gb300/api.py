@@ -455,33 +455,69 @@ def picard_update(ctx: Context, vel0, force_torque, mass, inertia, dt, vel, norm
 
 def implicit_euler_step(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inertia, pairs, eps,
                         dt, gravity=G_DEFAULT, k_s=1000.0, precision="fp32", tol=1e-13,
-                        max_iter=200, contacts=None):
+                        max_iter=200, contacts=None, graph=False):
     """One implicit Euler step by Picard iteration (Algorithm 3): starting
     from vel0, repeat: move the particles from poses0 by dt times the guessed
     velocities, detect the contacts of the candidate pairs there, compute the
     contact forces and torques (about the body origins), and update the
     guess; stop when max |new - guess| <= tol * max |new|.  All arithmetic
     runs in the library's kernels; the loop reads two numbers per iteration.
+    With graph=True the iteration (pose update, detection, forces, velocity
+    update) is captured once into a CUDA graph after a first checked
+    iteration and replayed; a work-list overflow found by the per-iteration
+    status check restores the velocities, runs that iteration again through
+    the checked path (which grows the lists) and captures anew.
     Returns (poses, vel, iterations, history of the relative change)."""
+    lib = L.load()
     n = poses0.shape[0]
     dev = poses0.device
     P = pairs.shape[0]
     vel = vel0.clone()
+    prev = torch.empty_like(vel)
     poses = torch.empty_like(poses0)
     com = torch.zeros((n, 3), dtype=torch.float64, device=dev)
     ft = torch.zeros((n, 6), dtype=torch.float64, device=dev)
     energy = torch.zeros(1, dtype=torch.float64, device=dev)
     norms = torch.empty(2, dtype=torch.float64, device=dev)
-    hist = []
-    it = 0
-    for it in range(1, max_iter + 1):
+    stats = torch.zeros(L.MRDEM_STAT_COUNT, dtype=torch.int64, device=dev)
+    state = {"contacts": contacts, "graph": None}
+
+    def body(checked):
         move_poses(ctx, poses0, vel, dt, out=poses)
         ft.zero_()
         if P:
-            contacts, _ = detect(ctx, hier, pairs, eps, poses, precision, contacts=contacts)
-            contact_forces(ctx, hier, pairs, eps, poses, contacts, mass, com, k_s,
+            state["contacts"], _ = detect(ctx, hier, pairs, eps, poses, precision,
+                                          contacts=state["contacts"], stats=stats,
+                                          check=checked)
+            contact_forces(ctx, hier, pairs, eps, poses, state["contacts"], mass, com, k_s,
                            force_torque=ft, energy=energy)
         picard_update(ctx, vel0, ft, mass, inertia, dt, vel, norms, gravity)
+
+    hist = []
+    it = 0
+    for it in range(1, max_iter + 1):
+        if not graph or it == 1:
+            body(True)
+        else:
+            if state["graph"] is None:
+                g = torch.cuda.CUDAGraph()
+                side = torch.cuda.Stream()
+                side.wait_stream(torch.cuda.current_stream())
+                prev.copy_(vel)
+                with torch.cuda.graph(g, stream=side):
+                    body(False)
+                torch.cuda.current_stream().wait_stream(side)
+                vel.copy_(prev)   # capturing does not run the work
+                state["graph"] = g
+            prev.copy_(vel)
+            state["graph"].replay()
+            st = lib.mrdem_check(ctx.handle, _stream(None), None)
+            if st == L.MRDEM_ERR_CAPACITY:
+                vel.copy_(prev)
+                body(True)
+                state["graph"] = None
+            elif st != L.MRDEM_OK:
+                L.check(st, "implicit_euler_step")
         change, scale = norms.tolist()
         scale += 1e-300
         hist.append(change / scale)

@@ -393,3 +393,29 @@ def test_newton_step_reaches_the_picard_fixed_point(m, ctx, orc, imp, case, prec
     assert it < (16 if precision == "fp64" else 30), stats
     lim = _fixed_point_bound(orc, s, pairs, eps, P, dt, precision) + 10 * tol * np.abs(V).max()
     assert np.abs(Vg.cpu().numpy() - V).max() <= lim, (np.abs(Vg.cpu().numpy() - V).max(), lim)
+
+
+def test_picard_iterations_replayed_from_a_cuda_graph(m, ctx, imp):
+    """The Picard iteration captured once into a CUDA graph and replayed
+    gives the uncaptured loop's result (the force sums' atomics may order
+    additions differently, so to 1e-12) in as many iterations, give or take
+    one; a context with tiny work lists grows them in the first, checked
+    iteration and then replays as well."""
+    s, _, pairs, eps, vel = _chain_problem(imp)
+    dt = 2e-4
+    inertia = 0.4 * s.mass * s.radius ** 2
+    hier = m.Hierarchy.from_scene(ctx, s)
+    args = (_t(s.poses), _t(vel), _t(s.mass), _t(inertia), _t(pairs, "int32"), _t(eps), dt)
+    P1, V1, it1, _ = m.implicit_euler_step(ctx, hier, *args, precision="fp64", tol=1e-11)
+    P2, V2, it2, _ = m.implicit_euler_step(ctx, hier, *args, precision="fp64", tol=1e-11,
+                                           graph=True)
+    assert abs(it1 - it2) <= 1
+    scale = V1.abs().max().item()
+    assert (V1 - V2).abs().max().item() <= 1e-12 * scale
+    assert (P1 - P2).abs().max().item() <= 1e-12 * (1.0 + P1.abs().max().item())
+    small = m.Context(0, cap_level=64, cap_tiles=64, cap_candidates=64, cap_sweep=64)
+    hs = m.Hierarchy.from_scene(small, s)
+    _, V3, it3, _ = m.implicit_euler_step(small, hs, *args, precision="fp64", tol=1e-11,
+                                          graph=True)
+    assert abs(it1 - it3) <= 1
+    assert (V1 - V3).abs().max().item() <= 1e-12 * scale
