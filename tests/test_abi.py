@@ -25,6 +25,32 @@ def test_library_exports_every_declared_symbol():
     assert set(names) == set(m._lib.SIGNATURES)
 
 
+def test_binding_signatures_match_the_header():
+    """Every ctypes signature of the binding takes as many arguments as the
+    header's prototype (a mismatch would pass garbage through the ABI)."""
+    import paper_2105_12415_gb300 as m
+    txt = open(os.path.join(ROOT, "include", "mrdem.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    protos = dict(re.findall(r"\b(mrdem_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S))
+    assert set(protos) == set(m._lib.SIGNATURES)
+    scalar = {"int64_t": C.c_int64, "int32_t": C.c_int32, "int": C.c_int, "double": C.c_double}
+    for name, params in protos.items():
+        params = params.strip()
+        plist = [] if params in ("", "void") else [x.strip() for x in params.split(",")]
+        args = m._lib.SIGNATURES[name][1]
+        assert len(args) == len(plist), (name, len(plist))
+        for decl, ct in zip(plist, args):
+            if "*" in decl or decl.startswith("mrdem_stream"):
+                # pointers (and the stream handle) travel as pointers
+                assert ct in (C.c_void_p, C.c_char_p) or issubclass(ct, C._Pointer) or \
+                    hasattr(ct, "contents"), (name, decl)
+            else:
+                base = decl.split()[0]
+                assert base in scalar, (name, decl)
+                assert C.sizeof(ct) == C.sizeof(scalar[base]) and \
+                    (ct is C.c_double) == (base == "double"), (name, decl, ct)
+
+
 def test_status_strings_and_defaults():
     import paper_2105_12415_gb300 as m
     lib = m.load()
@@ -52,6 +78,18 @@ def test_null_arguments_are_rejected():
     assert lib.mrdem_check(None, None, None) == -1
     assert lib.mrdem_merge_contacts(None, 0, None, None, None, None, None) == -1
     assert lib.mrdem_hier_get_info(None, None) == -1
+    assert lib.mrdem_broad_phase(None, 0, None, None, None, 0.01, None, None, 0, None, None) == -1
+    assert lib.mrdem_move_poses(None, 0, None, None, 1e-3, None, None) == -1
+    g = (C.c_double * 3)(0.0, 0.0, -9.81)
+    assert lib.mrdem_picard_update(None, 0, None, None, None, None, C.cast(g, C.c_void_p), 1e-3,
+                                   None, None, None) == -1
+    assert lib.mrdem_contact_hessian(None, None, 0, None, None, None, None, None, 1000.0, None,
+                                     None, None) == -1
+    assert lib.mrdem_newton_residual(None, 0, None, None, None, None, None,
+                                     C.cast(g, C.c_void_p), 1e-3, None, None, None) == -1
+    assert lib.mrdem_newton_solve(None, 0, 0, None, None, None, None, 1e-3, None, None, 10, 1e-10,
+                                  None, None) == -1
+    assert lib.mrdem_vel_axpy(None, 0, 1.0, None, None, None, None) == -1
     assert lib.mrdem_destroy(None) == 0
 
 
