@@ -424,6 +424,35 @@ int mrdem_newton_solve(mrdem_ctx* ctx, int32_t n, int64_t n_pairs, const int32_t
 int mrdem_vel_axpy(mrdem_ctx* ctx, int64_t m, double a, const double* x, const double* y,
                    double* out, mrdem_stream stream);
 
+/* Contacts of a cached candidate list (the active set kept across the
+ * iterations of one implicit step): for every listed triangle pair of
+ * `candidates` (pair, tri_a, tri_b; its other fields are not read), the
+ * exact FP64 comparison-based distance of the two world triangles at
+ * `poses`; pairs with d <= 2 eps (pair_eps) are written to `out` in the
+ * list's order (pair, triangles, d, closest points in the world frame, as
+ * mrdem_detect writes them), out->count = their number.  With candidates
+ * from mrdem_detect at eps + w at reference poses, the result equals
+ * mrdem_detect at eps at any poses whose points moved by at most w from
+ * the reference ones (triangle distances change by at most the sum of the
+ * two particles' displacements; see mrdem_motion_bound).  The context keeps
+ * 60 bytes per entry of the candidates' capacity.  Device-side failure
+ * latched for mrdem_check: more contacts than out->capacity: CAPACITY with
+ * required[3].  Errors: INVALID (null pointers, overlapping buffers,
+ * capacities >= 2^31), OOM, CUDA. */
+int mrdem_refine_contacts(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
+                          const int32_t* pair_ab, const double* pair_eps, const double* poses,
+                          const mrdem_contacts* candidates, const mrdem_contacts* out,
+                          mrdem_stream stream);
+
+/* Largest displacement of any point of any particle between poses_ref and
+ * poses (device double [n*7] each): |t - t_ref| + theta * bound, theta the
+ * angle of the rotation taking the reference orientation to the current
+ * one, bound (device double [n]) the particle's largest vertex distance
+ * from its origin; written to *out (device double).  Errors: INVALID,
+ * CUDA. */
+int mrdem_motion_bound(mrdem_ctx* ctx, int32_t n, const double* poses_ref, const double* poses,
+                       const double* bound, double* out, mrdem_stream stream);
+
 /* Plain GPU form (reported baseline): the contact set by FP64 comparison-based
  * distance over ALL fine triangle pairs of each pair (Algorithm 2), no
  * hierarchy, one kernel launch per particle pair.  Same inputs and outputs as

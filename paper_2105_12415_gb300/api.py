@@ -453,9 +453,49 @@ def picard_update(ctx: Context, vel0, force_torque, mass, inertia, dt, vel, norm
     return norms
 
 
+def refine_contacts(ctx, hier, pairs, eps, poses, candidates, out=None, stream=None,
+                    max_retries=4):
+    """Contacts (d <= 2 eps, exact FP64 distance) among the triangle pairs
+    listed in `candidates`, at `poses`, in the list's order.  Synchronises to
+    check the output's capacity; grows it and repeats on overflow."""
+    n = hier.info()["n_particles"]
+    P = _pair_args(hier, pairs, eps, poses, n)
+    if out is None:
+        out = Contacts(max(1024, candidates.capacity), pairs.device)
+    lib = L.load()
+    for _ in range(max_retries + 1):
+        cin, cout = candidates.struct(), out.struct()
+        L.check(lib.mrdem_refine_contacts(ctx.handle, hier.handle, P, _p(pairs), _p(eps),
+                                          _p(poses), C.byref(cin), C.byref(cout),
+                                          _stream(stream)), "mrdem_refine_contacts")
+        req = np.zeros(5, np.int64)
+        st = lib.mrdem_check(ctx.handle, _stream(stream), _np_ptr(req))
+        if st == L.MRDEM_OK:
+            return out
+        if st != L.MRDEM_ERR_CAPACITY:
+            L.check(st, "mrdem_refine_contacts")
+        out.resize(int(req[3] * 1.25) + 1024)
+    raise L.MrdemError(L.MRDEM_ERR_CAPACITY, "mrdem_refine_contacts (retries exhausted)")
+
+
+def motion_bound(ctx, poses_ref, poses, bound, out=None, stream=None):
+    """Largest displacement of any particle point between two poses (device
+    float64 [1]): |t - t_ref| + rotation angle * bound."""
+    n = poses.shape[0]
+    _need(poses_ref, torch.float64, (n, 7), "poses_ref")
+    _need(poses, torch.float64, (n, 7), "poses")
+    _need(bound, torch.float64, (n,), "bound")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=poses.device)
+    L.check(L.load().mrdem_motion_bound(ctx.handle, n, _p(poses_ref), _p(poses), _p(bound),
+                                        _p(out), _stream(stream)), "mrdem_motion_bound")
+    return out
+
+
 def implicit_euler_step(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inertia, pairs, eps,
                         dt, gravity=G_DEFAULT, k_s=1000.0, precision="fp32", tol=1e-13,
-                        max_iter=200, contacts=None, graph=False):
+                        max_iter=200, contacts=None, graph=False, cache_margin=None,
+                        bound=None):
     """One implicit Euler step by Picard iteration (Algorithm 3): starting
     from vel0, repeat: move the particles from poses0 by dt times the guessed
     velocities, detect the contacts of the candidate pairs there, compute the
@@ -467,6 +507,13 @@ def implicit_euler_step(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inert
     iteration and replayed; a work-list overflow found by the per-iteration
     status check restores the velocities, runs that iteration again through
     the checked path (which grows the lists) and captures anew.
+    With cache_margin = w (and bound, the particles' bounding radii) the
+    candidate triangle pairs are detected once at eps + w and kept; each
+    iteration checks that no point moved more than w from where the
+    candidates were detected (detecting again if one did) and takes its
+    contacts from the kept list by exact FP64 distances (the active set
+    kept across iterations, Alg. 6's idea, with the same contact set);
+    graph is then not used.
     Returns (poses, vel, iterations, history of the relative change)."""
     lib = L.load()
     n = poses0.shape[0]
@@ -482,6 +529,30 @@ def implicit_euler_step(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inert
     stats = torch.zeros(L.MRDEM_STAT_COUNT, dtype=torch.int64, device=dev)
     state = {"contacts": contacts, "graph": None}
 
+    cache = {"cand": None, "ref": torch.empty_like(poses0), "motion": None, "rebuilds": 0}
+    if cache_margin is not None:
+        _need(bound, torch.float64, (n,), "bound")
+        eps_w = eps + float(cache_margin)
+
+    def body_cached():
+        move_poses(ctx, poses0, vel, dt, out=poses)
+        ft.zero_()
+        if P:
+            fresh = cache["cand"] is None
+            if not fresh:
+                cache["motion"] = motion_bound(ctx, cache["ref"], poses, bound, out=cache["motion"])
+                fresh = cache["motion"].item() > float(cache_margin)
+            if fresh:
+                cache["cand"], _ = detect(ctx, hier, pairs, eps_w, poses, precision,
+                                          contacts=cache["cand"], stats=stats)
+                cache["ref"].copy_(poses)
+                cache["rebuilds"] += 1
+            state["contacts"] = refine_contacts(ctx, hier, pairs, eps, poses, cache["cand"],
+                                                out=state["contacts"])
+            contact_forces(ctx, hier, pairs, eps, poses, state["contacts"], mass, com, k_s,
+                           force_torque=ft, energy=energy)
+        picard_update(ctx, vel0, ft, mass, inertia, dt, vel, norms, gravity)
+
     def body(checked):
         move_poses(ctx, poses0, vel, dt, out=poses)
         ft.zero_()
@@ -496,7 +567,9 @@ def implicit_euler_step(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inert
     hist = []
     it = 0
     for it in range(1, max_iter + 1):
-        if not graph or it == 1:
+        if cache_margin is not None:
+            body_cached()
+        elif not graph or it == 1:
             body(True)
         else:
             if state["graph"] is None:

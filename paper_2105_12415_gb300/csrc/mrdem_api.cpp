@@ -182,6 +182,7 @@ int mrdem_destroy(mrdem_ctx* c) {
   cudaFree(c->merge_mem);
   cudaFree(c->broad_mem);
   cudaFree(c->cg_mem);
+  cudaFree(c->refine_mem);
   cudaFree(c->frames);
   cudaFree(c->counters);
   cudaFree(c->status);
@@ -649,6 +650,33 @@ int mrdem_vel_axpy(mrdem_ctx* c, int64_t m, double a, const double* x, const dou
   if (m > 0 && (!x || !y || !out)) return MRDEM_ERR_INVALID;
   DeviceGuard g(c->device);
   return launch_vel_axpy(c, m, a, x, y, out, (cudaStream_t)s);
+}
+
+int mrdem_refine_contacts(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
+                          const double* eps, const double* poses, const mrdem_contacts* cand,
+                          const mrdem_contacts* out, mrdem_stream s) {
+  int st = check_pair_args(c, h, n_pairs, ab, eps, poses);
+  if (st) return st;
+  if (!contacts_ok(cand) || !contacts_ok(out)) return MRDEM_ERR_INVALID;
+  if (cand->capacity >= (int64_t)1 << 31 || out->capacity >= (int64_t)1 << 31)
+    return MRDEM_ERR_INVALID;
+  const void* ip[] = {cand->count, cand->pair, cand->tri_a, cand->tri_b, cand->dist,
+                      cand->point_a, cand->point_b};
+  const void* op[] = {out->count, out->pair, out->tri_a, out->tri_b, out->dist, out->point_a,
+                      out->point_b};
+  for (const void* a : ip)
+    for (const void* b : op)
+      if (a && a == b) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_refine_contacts(c, h, n_pairs, ab, eps, poses, cand, out, (cudaStream_t)s);
+}
+
+int mrdem_motion_bound(mrdem_ctx* c, int32_t n, const double* poses_ref, const double* poses,
+                       const double* bound, double* out, mrdem_stream s) {
+  if (!c || n < 0 || !out) return MRDEM_ERR_INVALID;
+  if (n > 0 && (!poses_ref || !poses || !bound)) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_motion_bound(c, n, poses_ref, poses, bound, out, (cudaStream_t)s);
 }
 
 static const char* kKernelNames[K_COUNT] = {

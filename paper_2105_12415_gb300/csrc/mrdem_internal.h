@@ -205,6 +205,10 @@ struct mrdem_ctx {
   // conjugate-gradient solve of the Newton step: state, scalars, vectors
   void* cg_mem = nullptr;
   size_t cap_cg = 0;
+  // refinement of a cached candidate list: per candidate its FP64 result
+  // and a keep flag
+  void* refine_mem = nullptr;
+  size_t cap_refine = 0;
   double* frames = nullptr;  // [cap_frames * 16]: per particle R (9), t (3), world com (3)
   int64_t cap_frames = 0;
   unsigned long long* counters = nullptr;  // [CNT_TOTAL]
@@ -293,6 +297,11 @@ int launch_newton_solve(mrdem_ctx* ctx, int32_t n, int64_t n_pairs, const int32_
                         const double* blocks, const double* mass, const double* inertia,
                         double dt, const double* rhs, double* x, int32_t max_iter, double rel_tol,
                         double* info, cudaStream_t s);
+int launch_refine_contacts(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
+                           const int32_t* pair_ab, const double* pair_eps, const double* poses,
+                           const mrdem_contacts* cand, const mrdem_contacts* out, cudaStream_t s);
+int launch_motion_bound(mrdem_ctx* ctx, int32_t n, const double* ref, const double* poses,
+                        const double* bound, double* out, cudaStream_t s);
 int launch_triangle_distance(mrdem_ctx* ctx, int64_t n, const double* P, const double* Q,
                              const double* eps, int precision, double* dist, double* pa,
                              double* pb, int32_t* feature, float* sx, float* sgap, int32_t* sconv,

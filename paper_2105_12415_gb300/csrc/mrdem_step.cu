@@ -504,6 +504,112 @@ __global__ void k_cg_finish(CgView v, int max_iter, double* info) {
   info[3] = sqrt(v.rr[0]);
 }
 
+// ---- contacts of a cached candidate list (the active set kept across the
+// iterations of one step): exact FP64 distance of each listed triangle pair
+// at the current poses, kept when d <= 2 eps; two passes around a scan so the
+// output keeps the list's order.
+
+struct RefineRec {
+  double d, pa[3], pb[3];
+};
+
+__global__ void __launch_bounds__(kThreads) k_refine(HierDev H, const int32_t* ab,
+                                                     const double* eps, const double* poses,
+                                                     mrdem_contacts cand, int64_t n_pairs,
+                                                     RefineRec* rec, int32_t* keep) {
+  wait_prior_grid();
+  int64_t n = *cand.count;
+  if (n > cand.capacity) n = cand.capacity;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += step) {
+    int32_t ok = 0;
+    const int p = cand.pair[k];
+    if (p >= 0 && p < n_pairs) {
+      const int A = ab[2 * p], B = ab[2 * p + 1];
+      V3<double> TA[3], TB[3], tA, tB;
+      if (A >= 0 && A < H.n_particles && B >= 0 && B < H.n_particles &&
+          world_triangle(H, poses, A, cand.tri_a[k], TA, &tA) &&
+          world_triangle(H, poses, B, cand.tri_b[k], TB, &tB)) {
+        const TriTriResult<double> t = tri_tri_distance<double>(TA, TB);
+        if (t.d <= 2.0 * eps[p]) {
+          ok = 1;
+          RefineRec r;
+          r.d = t.d;
+          r.pa[0] = t.pa.x; r.pa[1] = t.pa.y; r.pa[2] = t.pa.z;
+          r.pb[0] = t.pb.x; r.pb[1] = t.pb.y; r.pb[2] = t.pb.z;
+          rec[k] = r;
+        }
+      }
+    }
+    keep[k] = ok;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_refine_scan(int32_t* keep, const mrdem_contacts cand,
+                                                      int64_t* total) {
+  wait_prior_grid();
+  int64_t n = *cand.count;
+  if (n > cand.capacity) n = cand.capacity;
+  block_exclusive_scan(keep, n, total);
+}
+
+// keep[] now holds exclusive offsets; entry k is kept when the next offset
+// (or the total) is larger
+__global__ void __launch_bounds__(kThreads) k_refine_write(mrdem_contacts cand,
+                                                           const RefineRec* rec,
+                                                           const int32_t* off, mrdem_contacts out,
+                                                           unsigned long long* status) {
+  wait_prior_grid();
+  int64_t n = *cand.count;
+  if (n > cand.capacity) n = cand.capacity;
+  const int64_t total = *out.count;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && total > out.capacity)
+    atomicMax(status + ST_REQ_CONTACTS, (unsigned long long)total);
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += step) {
+    const int64_t o = off[k], next = k + 1 < n ? (int64_t)off[k + 1] : total;
+    if (next == o || o >= out.capacity) continue;
+    const RefineRec r = rec[k];
+    out.pair[o] = cand.pair[k];
+    out.tri_a[o] = cand.tri_a[k];
+    out.tri_b[o] = cand.tri_b[k];
+    out.dist[o] = r.d;
+    for (int c = 0; c < 3; ++c) {
+      out.point_a[3 * o + c] = r.pa[c];
+      out.point_b[3 * o + c] = r.pb[c];
+    }
+  }
+}
+
+// Largest displacement of any point of a particle between two poses: the
+// centre's plus the rotation angle times the bounding radius.
+__global__ void __launch_bounds__(kThreads) k_motion(int32_t n, const double* ref,
+                                                     const double* poses, const double* bound,
+                                                     unsigned long long* out) {
+  wait_prior_grid();
+  double m = 0.0;
+  const int32_t step = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+    const double* a = ref + (int64_t)7 * i;
+    const double* b = poses + (int64_t)7 * i;
+    const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+    // relative rotation q_b q_a^-1 (unit quaternions up to their norms)
+    const double na = sqrt(a[3] * a[3] + a[4] * a[4] + a[5] * a[5] + a[6] * a[6]);
+    const double nb = sqrt(b[3] * b[3] + b[4] * b[4] + b[5] * b[5] + b[6] * b[6]);
+    const double qa[4] = {a[3] / na, -a[4] / na, -a[5] / na, -a[6] / na};
+    const double qb[4] = {b[3] / nb, b[4] / nb, b[5] / nb, b[6] / nb};
+    double q[4];
+    quat_mul(qb, qa, q);
+    const double vn = sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const double ang = 2.0 * atan2(vn, fabs(q[0]));
+    const double d = sqrt(dx * dx + dy * dy + dz * dz) + ang * bound[i];
+    m = dmax_nan(m, d);
+  }
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0)
+    atomicMax(out, (unsigned long long)__double_as_longlong(fabs(m)));
+}
+
 int ceil_log2(int64_t v) {
   int k = 0;
   while (((int64_t)1 << k) < v) ++k;
@@ -706,6 +812,47 @@ int launch_newton_solve(mrdem_ctx* c, int32_t n, int64_t n_pairs, const int32_t*
     launch_after(k_cg_dir, nd, kThreads, 0, s, v, k);
   }
   launch_after(k_cg_finish, 1, 1, 0, s, v, max_iter, info);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
+
+int launch_refine_contacts(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
+                           const double* eps, const double* poses, const mrdem_contacts* cand,
+                           const mrdem_contacts* out, cudaStream_t s) {
+  const int64_t cap = cand->capacity > 0 ? cand->capacity : 1;
+  const size_t bytes = (sizeof(RefineRec) + sizeof(int32_t)) * (size_t)cap;
+  if (bytes > c->cap_refine) {
+    cudaFree(c->refine_mem);
+    c->refine_mem = nullptr;
+    c->cap_refine = 0;
+    if (cudaMalloc(&c->refine_mem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->refine_mem = nullptr;
+      return MRDEM_ERR_OOM;
+    }
+    c->cap_refine = bytes;
+  }
+  RefineRec* rec = static_cast<RefineRec*>(c->refine_mem);
+  int32_t* keep = reinterpret_cast<int32_t*>(rec + cap);
+  ProfScope ps(c, K_STEP, s);
+  cudaMemsetAsync(out->count, 0, sizeof(int64_t), s);
+  const int nb = blocks_for(c, cap);
+  launch_after(k_refine, nb, kThreads, 0, s, h->dev, ab, eps, poses, *cand, n_pairs, rec, keep);
+  launch_after(k_refine_scan, 1, 1024, 0, s, keep, *cand, out->count);
+  launch_after(k_refine_write, nb, kThreads, 0, s, *cand, (const RefineRec*)rec,
+               (const int32_t*)keep, *out, c->status);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
+
+int launch_motion_bound(mrdem_ctx* c, int32_t n, const double* ref, const double* poses,
+                        const double* bound, double* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (n > 0) {
+    ProfScope ps(c, K_STEP, s);
+    launch_after(k_motion, blocks_for(c, n), kThreads, 0, s, n, ref, poses, bound,
+                 reinterpret_cast<unsigned long long*>(out));
+  }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }

@@ -431,3 +431,82 @@ def test_picard_iterations_replayed_from_a_cuda_graph(m, ctx, imp):
                                           graph=True)
     assert abs(it1 - it3) <= 1
     assert (V1 - V3).abs().max().item() <= 1e-12 * scale
+
+
+def test_motion_bound_closed_form(m, ctx):
+    """A translation moves every point by its length; a rotation by angle a
+    about the origin moves a point at distance R by at most a R; the bound
+    is the largest over the particles."""
+    def one(t, axis, a, R):
+        P0 = np.array([[0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0]])
+        P1 = P0.copy()
+        P1[0, :3] = t
+        P1[0, 3:] = np.concatenate([[np.cos(a / 2)], np.sin(a / 2) * np.asarray(axis)])
+        return m.motion_bound(ctx, _t(P0), _t(P1), _t(np.array([R]))).item()
+    assert abs(one((0.3, -0.4, 0.0), (0, 0, 1), 0.0, 2.0) - 0.5) <= 1e-15
+    assert abs(one((0.0, 0.0, 0.0), (0, 0, 1), 0.2, 5.0) - 1.0) <= 1e-14
+    assert abs(one((0.0, 0.0, 0.1), (1, 0, 0), 0.1, 3.0) - 0.4) <= 1e-14
+    assert abs(one((0.0, 0.0, 0.0), (0, 1, 0), -0.3, 1.0) - 0.3) <= 1e-14
+    P0 = np.zeros((3, 7))
+    P0[:, 3] = 1.0
+    P1 = P0.copy()
+    P1[0, :3] = (0.3, -0.4, 0.0)
+    P1[1, 3:] = (np.cos(0.1), 0.0, 0.0, np.sin(0.1))
+    got = m.motion_bound(ctx, _t(P0), _t(P1), _t(np.array([1.0, 5.0, 3.0]))).item()
+    assert abs(got - 1.0) <= 1e-14
+    assert m.motion_bound(ctx, _t(P0), _t(P0), _t(np.ones(3))).item() == 0.0
+
+
+def _perturbed(poses, rng, step):
+    """Poses moved by a translation of length step * (1 + |rng|) and a
+    rotation by an angle of at most step about a random axis."""
+    out = np.array(poses, copy=True)
+    for i in range(len(out)):
+        u = rng.normal(size=3)
+        out[i, :3] += step * u / np.linalg.norm(u)
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        a = step * rng.uniform(0.5, 1.0)
+        w, v = np.cos(a / 2), np.sin(a / 2) * ax
+        q = out[i, 3:]
+        qn = np.concatenate([[w * q[0] - v @ q[1:]], w * q[1:] + q[0] * v + np.cross(v, q[1:])])
+        out[i, 3:] = qn / np.linalg.norm(qn)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_refined_candidates_equal_detection(m, ctx, orc, imp, precision):
+    """Candidates detected at eps + w at reference poses, refined at poses
+    whose points moved by at most w, give the contact set of a detection at
+    those poses (the oracle's), with FP64 distances."""
+    from tests.gpu_common import compare_contacts
+    s, bound, pairs, eps, _ = _chain_problem(imp)
+    hier = m.Hierarchy.from_scene(ctx, s)
+    w = 0.25 * eps.min()
+    rng = np.random.default_rng(21)
+    moved = _perturbed(s.poses, rng, 0.4 * w / (1.0 + bound.max()))   # points move by < w / 2
+    tp, te = _t(pairs, "int32"), _t(eps)
+    mb = m.motion_bound(ctx, _t(s.poses), _t(moved), _t(bound)).item()
+    assert 0 < mb <= w
+    cand, _ = m.detect(ctx, hier, tp, _t(eps + w), _t(s.poses), precision)
+    got = m.refine_contacts(ctx, hier, tp, te, _t(moved), cand).to_numpy()
+    base = dataclasses.replace(s, pairs=pairs, eps=eps, com=np.zeros((s.n_particles, 3)))
+    ref = orc.detect(base, poses=moved)
+    assert len(ref["d"]) > 50 and cand.n() >= len(ref["d"])
+    compare_contacts(got, ref, base, "fp64")
+
+
+def test_picard_with_kept_candidates(m, ctx, imp):
+    """The Picard step taking each iteration's contacts from candidates kept
+    across the step (detected once at eps + w) gives the step of the full
+    detection (FP64 form) to 1e-12 in as many iterations."""
+    s, bound, pairs, eps, vel = _chain_problem(imp)
+    dt = 2e-4
+    inertia = 0.4 * s.mass * s.radius ** 2
+    hier = m.Hierarchy.from_scene(ctx, s)
+    args = (_t(s.poses), _t(vel), _t(s.mass), _t(inertia), _t(pairs, "int32"), _t(eps), dt)
+    P1, V1, it1, _ = m.implicit_euler_step(ctx, hier, *args, precision="fp64", tol=1e-11)
+    P2, V2, it2, _ = m.implicit_euler_step(ctx, hier, *args, precision="fp64", tol=1e-11,
+                                           cache_margin=0.25 * eps.min(), bound=_t(bound))
+    assert abs(it1 - it2) <= 1
+    assert (V1 - V2).abs().max().item() <= 1e-12 * V1.abs().max().item()
