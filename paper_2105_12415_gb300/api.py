@@ -492,6 +492,37 @@ def motion_bound(ctx, poses_ref, poses, bound, out=None, stream=None):
     return out
 
 
+class KeptCandidates:
+    """Contacts at a sequence of nearby poses from one candidate list: the
+    triangle pairs within 2 (eps + w) at the poses of the last detection,
+    refined by exact FP64 distances at the poses asked for, and detected
+    again when a point has moved more than w since (mrdem_motion_bound);
+    the contact set equals a detection at eps at every call."""
+
+    def __init__(self, ctx, hier, pairs, eps, margin, bound, precision="fp32"):
+        n = hier.info()["n_particles"]
+        _need(bound, torch.float64, (n,), "bound")
+        self.ctx, self.hier, self.pairs, self.eps, self.bound = ctx, hier, pairs, eps, bound
+        self.margin, self.precision = float(margin), precision
+        self.eps_w = eps + self.margin
+        self.cand = self.ref = self.motion = None
+        self.stats = torch.zeros(L.MRDEM_STAT_COUNT, dtype=torch.int64, device=pairs.device)
+        self.detections = 0
+
+    def contacts(self, poses, out=None):
+        fresh = self.cand is None
+        if not fresh:
+            self.motion = motion_bound(self.ctx, self.ref, poses, self.bound, out=self.motion)
+            fresh = self.motion.item() > self.margin
+        if fresh:
+            self.cand, _ = detect(self.ctx, self.hier, self.pairs, self.eps_w, poses,
+                                  self.precision, contacts=self.cand, stats=self.stats)
+            self.ref = poses.clone()
+            self.detections += 1
+        return refine_contacts(self.ctx, self.hier, self.pairs, self.eps, poses, self.cand,
+                               out=out)
+
+
 def implicit_euler_step(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inertia, pairs, eps,
                         dt, gravity=G_DEFAULT, k_s=1000.0, precision="fp32", tol=1e-13,
                         max_iter=200, contacts=None, graph=False, cache_margin=None,
@@ -529,26 +560,14 @@ def implicit_euler_step(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inert
     stats = torch.zeros(L.MRDEM_STAT_COUNT, dtype=torch.int64, device=dev)
     state = {"contacts": contacts, "graph": None}
 
-    cache = {"cand": None, "ref": torch.empty_like(poses0), "motion": None, "rebuilds": 0}
-    if cache_margin is not None:
-        _need(bound, torch.float64, (n,), "bound")
-        eps_w = eps + float(cache_margin)
+    kept = (KeptCandidates(ctx, hier, pairs, eps, cache_margin, bound, precision)
+            if cache_margin is not None else None)
 
     def body_cached():
         move_poses(ctx, poses0, vel, dt, out=poses)
         ft.zero_()
         if P:
-            fresh = cache["cand"] is None
-            if not fresh:
-                cache["motion"] = motion_bound(ctx, cache["ref"], poses, bound, out=cache["motion"])
-                fresh = cache["motion"].item() > float(cache_margin)
-            if fresh:
-                cache["cand"], _ = detect(ctx, hier, pairs, eps_w, poses, precision,
-                                          contacts=cache["cand"], stats=stats)
-                cache["ref"].copy_(poses)
-                cache["rebuilds"] += 1
-            state["contacts"] = refine_contacts(ctx, hier, pairs, eps, poses, cache["cand"],
-                                                out=state["contacts"])
+            state["contacts"] = kept.contacts(poses, out=state["contacts"])
             contact_forces(ctx, hier, pairs, eps, poses, state["contacts"], mass, com, k_s,
                            force_torque=ft, energy=energy)
         picard_update(ctx, vel0, ft, mass, inertia, dt, vel, norms, gravity)
@@ -643,13 +662,16 @@ def newton_solve(ctx, pairs, blocks, mass, inertia, dt, rhs, x=None, max_iter=20
 
 def implicit_euler_step_newton(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inertia, pairs,
                                eps, dt, gravity=G_DEFAULT, k_s=1000.0, precision="fp32",
-                               tol=1e-13, max_iter=50, cg_iter=200, cg_tol=1e-12, contacts=None):
+                               tol=1e-13, max_iter=50, cg_iter=200, cg_tol=1e-12, contacts=None,
+                               cache_margin=None, bound=None):
     """One implicit Euler step by Newton's method in the velocities, on the
     same equations as the Picard iteration: residual
     r = M (V - V0)/dt - (F, tau)(moved geometry) - (m g, 0), Jacobian
     M/dt + dt K with K the contact Hessian blocks (closest points free), the
     linear system solved by conjugate gradients, each step halved until
     max |r| drops (backtracking).  Stops when max |r| <= tol max |M V|/dt.
+    With cache_margin = w (and bound) the residuals take their contacts from
+    candidates kept across the step (KeptCandidates).
     Returns (poses, vel, iterations, stats: CG iterations and line-search
     halvings per Newton iteration)."""
     lib = L.load()
@@ -668,13 +690,18 @@ def implicit_euler_step_newton(ctx: Context, hier: Hierarchy, poses0, vel0, mass
     x = torch.empty((n, 6), dtype=torch.float64, device=dev)
     info = torch.empty(4, dtype=torch.float64, device=dev)
     state = {"contacts": contacts}
+    kept = (KeptCandidates(ctx, hier, pairs, eps, cache_margin, bound, precision)
+            if cache_margin is not None else None)
 
     def residual(Vc):
         move_poses(ctx, poses0, Vc, dt, out=poses)
         ft.zero_()
         if P:
-            state["contacts"], _ = detect(ctx, hier, pairs, eps, poses, precision,
-                                          contacts=state["contacts"])
+            if kept is not None:
+                state["contacts"] = kept.contacts(poses, out=state["contacts"])
+            else:
+                state["contacts"], _ = detect(ctx, hier, pairs, eps, poses, precision,
+                                              contacts=state["contacts"])
             contact_forces(ctx, hier, pairs, eps, poses, state["contacts"], mass, com, k_s,
                            force_torque=ft, energy=energy)
         newton_residual(ctx, vel0, Vc, ft, mass, inertia, dt, res, norms, gravity)

@@ -510,3 +510,35 @@ def test_picard_with_kept_candidates(m, ctx, imp):
                                            cache_margin=0.25 * eps.min(), bound=_t(bound))
     assert abs(it1 - it2) <= 1
     assert (V1 - V2).abs().max().item() <= 1e-12 * V1.abs().max().item()
+
+
+def test_kept_candidates_detect_again_only_beyond_the_margin(m, ctx, orc, imp):
+    """Poses within w of the last detection reuse its candidates; poses
+    beyond w trigger a new detection; every call returns the oracle's
+    contact set at its poses."""
+    from tests.gpu_common import compare_contacts
+    s, bound, pairs, eps, _ = _chain_problem(imp)
+    base = dataclasses.replace(s, pairs=pairs, eps=eps, com=np.zeros((s.n_particles, 3)))
+    hier = m.Hierarchy.from_scene(ctx, s)
+    w = 0.25 * eps.min()
+    kept = m.KeptCandidates(ctx, hier, _t(pairs, "int32"), _t(eps), w, _t(bound), "fp64")
+    rng = np.random.default_rng(22)
+    near = _perturbed(s.poses, rng, 0.4 * w / (1.0 + bound.max()))
+    far = _perturbed(s.poses, rng, 3.0 * w / (1.0 + bound.max()))
+    for poses, detections in ((s.poses, 1), (near, 1), (far, 2), (s.poses, 3)):
+        got = kept.contacts(_t(poses)).to_numpy()
+        assert kept.detections == detections
+        compare_contacts(got, orc.detect(base, poses=poses), base, "fp64")
+
+
+def test_newton_with_kept_candidates(m, ctx, imp):
+    s, bound, pairs, eps, vel = _chain_problem(imp)
+    dt = 2e-4
+    inertia = 0.4 * s.mass * s.radius ** 2
+    hier = m.Hierarchy.from_scene(ctx, s)
+    args = (_t(s.poses), _t(vel), _t(s.mass), _t(inertia), _t(pairs, "int32"), _t(eps), dt)
+    _, V1, it1, _ = m.implicit_euler_step_newton(ctx, hier, *args, precision="fp64", tol=1e-12)
+    _, V2, it2, _ = m.implicit_euler_step_newton(ctx, hier, *args, precision="fp64", tol=1e-12,
+                                                 cache_margin=0.25 * eps.min(), bound=_t(bound))
+    assert abs(it1 - it2) <= 1
+    assert (V1 - V2).abs().max().item() <= 1e-10 * V1.abs().max().item()
