@@ -589,22 +589,8 @@ __global__ void __launch_bounds__(kThreads) k_motion(int32_t n, const double* re
   wait_prior_grid();
   double m = 0.0;
   const int32_t step = gridDim.x * blockDim.x;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
-    const double* a = ref + (int64_t)7 * i;
-    const double* b = poses + (int64_t)7 * i;
-    const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
-    // relative rotation q_b q_a^-1 (unit quaternions up to their norms)
-    const double na = sqrt(a[3] * a[3] + a[4] * a[4] + a[5] * a[5] + a[6] * a[6]);
-    const double nb = sqrt(b[3] * b[3] + b[4] * b[4] + b[5] * b[5] + b[6] * b[6]);
-    const double qa[4] = {a[3] / na, -a[4] / na, -a[5] / na, -a[6] / na};
-    const double qb[4] = {b[3] / nb, b[4] / nb, b[5] / nb, b[6] / nb};
-    double q[4];
-    quat_mul(qb, qa, q);
-    const double vn = sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    const double ang = 2.0 * atan2(vn, fabs(q[0]));
-    const double d = sqrt(dx * dx + dy * dy + dz * dz) + ang * bound[i];
-    m = dmax_nan(m, d);
-  }
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step)
+    m = dmax_nan(m, particle_motion(ref + (int64_t)7 * i, poses + (int64_t)7 * i, bound[i]));
   m = warp_max(m);
   if ((threadIdx.x & 31) == 0)
     atomicMax(out, (unsigned long long)__double_as_longlong(fabs(m)));

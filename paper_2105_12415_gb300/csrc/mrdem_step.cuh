@@ -358,6 +358,24 @@ MRDEM_HD void newton_residual(const double* vel0, const double* vel, const doubl
   *smax = s;
 }
 
+// Largest displacement of a point of a particle between pose a and pose b
+// (centre xyz, quaternion wxyz, any norm): |t_b - t_a| + theta R, theta the
+// angle of the rotation q_b q_a^-1 and R the particle's bounding radius (a
+// rotation by theta about the origin moves a point at distance r by
+// 2 r sin(theta/2) <= theta r).
+MRDEM_HD double particle_motion(const double* a, const double* b, double R) {
+  const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+  const double na = sqrt(a[3] * a[3] + a[4] * a[4] + a[5] * a[5] + a[6] * a[6]);
+  const double nb = sqrt(b[3] * b[3] + b[4] * b[4] + b[5] * b[5] + b[6] * b[6]);
+  const double qa[4] = {a[3] / na, -a[4] / na, -a[5] / na, -a[6] / na};
+  const double qb[4] = {b[3] / nb, b[4] / nb, b[5] / nb, b[6] / nb};
+  double q[4];
+  quat_mul(qb, qa, q);
+  const double vn = sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const double ang = 2.0 * atan2(vn, fabs(q[0]));
+  return sqrt(dx * dx + dy * dy + dz * dz) + ang * R;
+}
+
 // 12x12 block times the 12-vector (x_A, x_B), row-major block.
 MRDEM_HD void block_mul(const double* B, const double* xa, const double* xb, double* y) {
   for (int i = 0; i < 12; ++i) {

@@ -119,3 +119,20 @@ extern "C" void hs_picard(int n, const double* vel0, const double* ft, const dou
     norms[1] = s > norms[1] ? s : norms[1];
   }
 }
+
+extern "C" double hs_particle_motion(const double* a, const double* b, double R) {
+  return particle_motion(a, b, R);
+}
+
+extern "C" void hs_newton_residual(int n, const double* vel0, const double* vel, const double* ft,
+                                   const double* mass, const double* inertia, const double* g,
+                                   double dt, double* res, double* norms) {
+  norms[0] = norms[1] = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double a, b;
+    newton_residual(vel0 + 6 * i, vel + 6 * i, ft + 6 * i, mass[i], inertia[i], g, dt,
+                    res + 6 * i, &a, &b);
+    norms[0] = a > norms[0] ? a : norms[0];
+    norms[1] = b > norms[1] ? b : norms[1];
+  }
+}

@@ -34,6 +34,9 @@ def hs(tmp_path_factory):
     lib.hs_move_poses.argtypes = [C.c_int, DP, DP, C.c_double, DP]
     lib.hs_contact_hessian.argtypes = [DP, DP, DP, DP, C.c_double, C.c_double, DP]
     lib.hs_picard.argtypes = [C.c_int, DP, DP, DP, DP, DP, C.c_double, DP, DP]
+    lib.hs_particle_motion.restype = C.c_double
+    lib.hs_particle_motion.argtypes = [DP, DP, C.c_double]
+    lib.hs_newton_residual.argtypes = [C.c_int, DP, DP, DP, DP, DP, DP, C.c_double, DP, DP]
     return lib
 
 
@@ -160,3 +163,52 @@ def test_hessian_block_function_equals_oracle(hs, imp, orc):
                                  _d(z).ctypes.data_as(DP), _d(z).ctypes.data_as(DP), 1.0, 0.1,
                                  out.ctypes.data_as(DP)) == 1
     assert (out == 0).all()
+
+
+def test_newton_residual_function_rounds_like_the_formula(hs):
+    rng = np.random.default_rng(11)
+    n = 500
+    v0, v, ft = rng.normal(size=(n, 6)), rng.normal(size=(n, 6)), rng.normal(size=(n, 6)) * 50
+    mass, inertia = rng.uniform(0.5, 2.0, n), rng.uniform(0.1, 1.0, n)
+    g, dt = np.array([0.3, 0.0, -9.81]), 1e-3
+    res, norms = np.zeros((n, 6)), np.zeros(2)
+    hs.hs_newton_residual(n, *[_d(a).ctypes.data_as(DP) for a in (v0, v, ft, mass, inertia, g)], dt,
+                          res.ctypes.data_as(DP), norms.ctypes.data_as(DP))
+    Md = np.concatenate([np.repeat(mass[:, None], 3, 1), np.repeat(inertia[:, None], 3, 1)], 1)
+    gext = np.zeros((n, 6))
+    gext[:, :3] = mass[:, None] * g
+    want = (Md * (v - v0)) / dt - ft - gext
+    assert np.array_equal(res, want)
+    assert norms[0] == np.abs(want).max() and norms[1] == np.abs(Md * v).max() / dt
+
+
+def test_particle_motion_function(hs, imp):
+    """|dt| + angle R, with the angle of the relative rotation, against the
+    largest displacement of sampled points of the bounding sphere (which it
+    bounds, and nearly reaches for the farthest point)."""
+    rng = np.random.default_rng(14)
+    for _ in range(200):
+        a = np.concatenate([rng.normal(size=3), rng.normal(size=4)])
+        b = a.copy()
+        b[:3] += rng.normal(size=3) * rng.uniform(0, 0.1)
+        r = rng.normal(size=3) * rng.uniform(0, 0.5)
+        b[3:] = imp._quat_mul(imp.rotvec_quat(r), a[3:] / np.linalg.norm(a[3:])) * rng.uniform(0.5, 2)
+        R = rng.uniform(0.1, 3.0)
+        got = hs.hs_particle_motion(_d(a).ctypes.data_as(DP), _d(b).ctypes.data_as(DP), R)
+        want = np.linalg.norm(b[:3] - a[:3]) + np.linalg.norm(r) * R
+        assert abs(got - want) <= 1e-12 * (1 + want)
+        # it bounds every point's displacement
+        x = rng.normal(size=(64, 3))
+        x = R * x / np.linalg.norm(x, axis=1, keepdims=True)
+        Ra = orc_matrix(a[3:])
+        Rb = orc_matrix(b[3:])
+        disp = np.linalg.norm((x @ Rb.T + b[:3]) - (x @ Ra.T + a[:3]), axis=1).max()
+        assert disp <= got * (1 + 1e-12)
+
+
+def orc_matrix(q):
+    q = np.asarray(q, np.float64) / np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
