@@ -55,9 +55,12 @@ def _args():
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--no-merge", action="store_true")
     ap.add_argument("--merge-calls", type=int, default=50)
-    ap.add_argument("--workload", default="batched", choices=["batched", "packing"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "packing", "scale"],
                     help="batched: the batched particle-pair step (default); packing: the "
-                         "implicit Euler step of a many-particle packing")
+                         "implicit Euler step of a many-particle packing; scale: detection and "
+                         "forces of the 136 M-triangle scale workload")
+    ap.add_argument("--chunk", type=int, default=65536,
+                    help="scale workload: particle pairs per detection call")
     ap.add_argument("--particles", type=int, default=10000)
     return ap.parse_args()
 
@@ -518,12 +521,102 @@ def run_packing(args):
     return 0
 
 
+def run_scale(args):
+    """The scale workload (100 000 particles of 1 280 triangles and 100 of
+    81 920 at 20 times the radius, 136 M triangles): broad phase, then per
+    step the detection and forces of every candidate pair, in chunks of
+    --chunk pairs per call (the work lists stay near their default size),
+    enqueued without host synchronisation and timed with CUDA events.  One
+    JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_2105_12415_gb300 as m
+    from gen.icosphere import scene_scale
+    from paper_2105_12415_gb300.api import _p, _stream
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    m.build()
+    lib = m.load()
+    t0 = time.perf_counter()
+    s, achieved = scene_scale()
+    n = s.n_particles
+    bound = np.array([np.sqrt((s.particle(i)[0].astype(np.float64) ** 2).sum(1)).max()
+                      for i in range(n)])
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx = m.Context(0)
+    hier = m.Hierarchy.from_scene(ctx, s)
+    build_s = time.perf_counter() - t0
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    poses, mass, com = t(s.poses), t(s.mass), t(np.zeros((n, 3)))
+    pairs, eps = m.broad_phase(ctx, poses, t(bound), t(s.radius))
+    P = pairs.shape[0]
+    chunks = [(a, min(a + args.chunk, P)) for a in range(0, P, args.chunk)]
+    contacts = None
+    stats = torch.zeros(m._lib.MRDEM_STAT_COUNT, dtype=torch.int64, device=dev)
+    ft = torch.zeros((n, 6), dtype=torch.float64, device=dev)
+    energy = torch.zeros(1, dtype=torch.float64, device=dev)
+    n_contacts = 0
+    for a, b in chunks:   # checked pass: sizes the lists and the contact buffer
+        contacts, _ = m.detect(ctx, hier, pairs[a:b], eps[a:b], poses, args.precision,
+                               contacts=contacts, stats=stats)
+        n_contacts += contacts.n()
+    import ctypes as C
+
+    def step():
+        ft.zero_()
+        energy.zero_()
+        for a, b in chunks:
+            cs = contacts.struct()
+            m._lib.check(lib.mrdem_detect(ctx.handle, hier.handle, b - a, _p(pairs[a:b]),
+                                          _p(eps[a:b]), _p(poses),
+                                          m.api.PRECISION[args.precision], C.byref(cs),
+                                          _p(stats), _stream(None)), "detect")
+            m._lib.check(lib.mrdem_contact_forces(ctx.handle, hier.handle, b - a, _p(pairs[a:b]),
+                                                  _p(eps[a:b]), _p(poses), C.byref(cs), _p(mass),
+                                                  _p(com), 1000.0, _p(ft), _p(energy),
+                                                  _stream(None)), "forces")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    m._lib.check(lib.mrdem_check(ctx.handle, None, None), "warm-up check")
+    K = max(1, min(args.steps, 20))
+    a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        a_ev.record()
+        for _ in range(K):
+            step()
+        b_ev.record()
+        torch.cuda.synchronize()
+    m._lib.check(lib.mrdem_check(ctx.handle, None, None), "timed steps")
+    ms = a_ev.elapsed_time(b_ev) / K
+    print(json.dumps({
+        "metric": "particle-pair detections/s, scale workload (detection and forces per step)",
+        "value": round(P / (ms * 1e-3), 1), "unit": "pairs/s", "higher_is_better": True,
+        "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "workload": "scale",
+        "config": {"workload": f"{n - 100} particles of 1280 triangles and 100 of 81920 at 20x "
+                               f"the radius, {achieved:.3f} volume fraction",
+                   "particles": n, "triangles": int(np.diff(s.tri_off).sum()), "pairs": P,
+                   "contacts": n_contacts, "chunk": args.chunk, "precision": args.precision},
+        "prep_s": {"generate": round(gen_s, 1), "trees": round(build_s, 1)},
+        "clocks": clk.summary(),
+    }), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "packing":
         return run_packing(args)
+    if args.workload == "scale":
+        return run_scale(args)
     import numpy as np
     import torch
 

@@ -445,3 +445,76 @@ def scene_chain(k: int = 4, seed: int = 41, level: int = 2):
     radius = [float(np.linalg.norm(m[0], axis=1).mean()) for m in meshes]
     return _assemble(meshes, poses, radius, np.zeros((0, 2), np.int32), np.zeros(0), "chain")
 
+
+
+def scene_scale(n_small: int = 100000, n_big: int = 100, level_small: int = 3,
+                level_big: int = 6, ratio: float = 20.0, fraction: float = 0.3,
+                eps_rel: float = 0.01, overlap: float = 0.3, seed: int = 23,
+                amp: float = 0.05, tries_per_particle: int = 200):
+    """Scale workload (the many-particle scale study of Sec. 6): n_big bumped
+    icospheres of subdivision level_big and radius `ratio` among n_small of
+    subdivision level_small and radius 1, random orientations, placed by
+    random sequential addition (the big ones first) in a cube sized for the
+    requested volume fraction, growing by 1 % when a particle finds no place
+    (bounding radius 1.05 r); then a share `overlap` of the particles moves
+    towards its nearest neighbour until their bounding spheres overlap by
+    eps / 2, eps = eps_rel * min(diameters).  No pairs listed (a broad phase
+    supplies them).  Returns (scene, achieved fraction)."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng([BASE_SEED, seed, 29])
+    n = n_big + n_small
+    radius = np.concatenate([np.full(n_big, float(ratio)), np.ones(n_small)])
+    R = 1.05 * radius
+    side = ((4.0 / 3.0) * np.pi * (radius ** 3).sum() / fraction) ** (1.0 / 3.0)
+    centres = np.zeros((n, 3))
+
+    def place(lo, hi, reach):
+        """Places particles lo..hi-1 (equal radius) avoiding the ones before."""
+        nonlocal side
+        big_tree = cKDTree(centres[:n_big]) if lo >= n_big and n_big else None
+        tree, in_tree = None, lo
+        i = lo
+        while i < hi:
+            ok = False
+            for _ in range(tries_per_particle):
+                c = rng.uniform(R[i], side - R[i], size=3)
+                near = list(range(in_tree, i))
+                if tree is not None:
+                    near += [lo + k for k in tree.query_ball_point(c, 2 * R[i])]
+                if big_tree is not None:
+                    near += big_tree.query_ball_point(c, R[i] + R[0])
+                if lo < n_big:
+                    near = list(range(lo, i))
+                if not near or (np.linalg.norm(centres[near] - c, axis=1) >= R[near] + R[i]).all():
+                    ok = True
+                    break
+            if not ok:
+                side *= 1.01
+                continue
+            centres[i] = c
+            i += 1
+            if i - in_tree >= 256:
+                tree, in_tree = cKDTree(centres[lo:i]), i
+        return reach
+
+    place(0, n_big, R[0])
+    place(n_big, n, R[n_big])
+    meshes = [bumped_icosphere(level_big if k < n_big else level_small, float(radius[k]), rng, amp)
+              for k in range(n)]
+    quats = random_quaternion(rng, n)
+    poses = np.concatenate([centres, quats], 1)
+    # bring some particles into contact with their nearest neighbour
+    tree = cKDTree(centres)
+    movers = rng.choice(n, size=int(overlap * n), replace=False) if n > 1 else []
+    for k in movers:
+        dist, idx = tree.query(poses[k, :3], k=2)
+        j = int(idx[1])
+        d = float(np.linalg.norm(poses[j, :3] - poses[k, :3]))
+        e = eps_rel * 2.0 * min(radius[k], radius[j])
+        shift = d - (R[k] + R[j] - 0.5 * e)
+        if shift > 0 and d > 0:
+            poses[k, :3] += shift * (poses[j, :3] - poses[k, :3]) / d
+    achieved = (4.0 / 3.0) * np.pi * (radius ** 3).sum() / side ** 3
+    s = _assemble(meshes, list(poses), list(radius), np.zeros((0, 2), np.int32), np.zeros(0),
+                  "scale")
+    return s, float(achieved)

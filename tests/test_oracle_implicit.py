@@ -464,3 +464,23 @@ def test_newton_with_the_analytic_hessian(imp, case, stiffness):
                                                 stiffness=stiffness)
     assert it2 <= 12, it2
     assert np.abs(V1 - V2).max() <= 1e-9 * np.abs(V1).max()
+
+
+def test_scale_generator():
+    """The scale workload's generator at a reduced size: the big particles
+    first with their subdivision and radius, then the small ones; the same
+    seed gives the same scene; some particles overlap a neighbour's bounding
+    sphere (so the broad phase finds pairs), the rest keep apart."""
+    from gen.icosphere import scene_scale
+    s, frac = scene_scale(n_small=1500, n_big=3, fraction=0.2)
+    nt = np.diff(s.tri_off)
+    assert s.n_particles == 1503 and list(nt[:3]) == [81920] * 3 and (nt[3:] == 1280).all()
+    assert np.allclose(s.radius[:3], 20.0) and np.allclose(s.radius[3:], 1.0)
+    assert 0 < frac <= 0.2
+    c = s.poses[:, :3]
+    from scipy.spatial import cKDTree
+    d, _ = cKDTree(c).query(c, k=2)
+    near = d[:, 1] < 1.05 * 2.0 * 1.0
+    assert near.sum() >= 100
+    s2, frac2 = scene_scale(n_small=1500, n_big=3, fraction=0.2)
+    assert frac2 == frac and np.array_equal(s2.poses, s.poses)
