@@ -405,19 +405,22 @@ int mrdem_newton_residual(mrdem_ctx* ctx, int32_t n, const double* vel0, const d
  * (mrdem_contact_hessian's layout) placed at its two particles' twists,
  * by conjugate gradients with the diagonal as preconditioner (an entry that
  * is not positive uses M/dt instead), from x = 0, stopping when
- * |r| <= rel_tol |rhs| or after max_iter iterations; every iteration is
- * enqueued (no host synchronisation; iterations after convergence do no
- * work).  pair_ab int32 [n_pairs*2], blocks double [n_pairs*144], mass and
+ * |r| <= rel_tol |rhs| or after max_iter iterations.  With check_every = 0
+ * every iteration is enqueued (no host synchronisation, capturable;
+ * iterations after convergence do no work); with check_every = k > 0 the
+ * call synchronises the stream every k iterations and stops enqueueing
+ * once the solve has finished.  pair_ab int32 [n_pairs*2], blocks double [n_pairs*144], mass and
  * inertia [n], rhs and x [n*6]: device.  info (device double [4]) receives
  * (iterations, |r|/|rhs|, 1 if p.Ap <= 0 stopped it (K not positive
  * definite enough; x is then the last iterate, or, when the first
  * direction p already has p.Ap < 0, the step (r.z / |p.Ap|) p), |rhs|).  The context keeps 240 n + 24 max_iter bytes of
  * scratch.  Errors: INVALID (null pointers, rhs == x, n > 2^26,
- * max_iter outside [0, 100000], rel_tol negative), OOM, CUDA. */
+ * max_iter outside [0, 100000], rel_tol or check_every negative), OOM,
+ * CUDA. */
 int mrdem_newton_solve(mrdem_ctx* ctx, int32_t n, int64_t n_pairs, const int32_t* pair_ab,
                        const double* blocks, const double* mass, const double* inertia,
                        double dt, const double* rhs, double* x, int32_t max_iter, double rel_tol,
-                       double* info, mrdem_stream stream);
+                       int32_t check_every, double* info, mrdem_stream stream);
 
 /* out = y + a x over m doubles (device; out may be y or x): the trial
  * velocities of a line search along a Newton step.  Errors: INVALID, CUDA. */

@@ -100,7 +100,8 @@ SIGNATURES = {
     "mrdem_contact_hessian": (C.c_int, [_P, _P, _I64, _P, _P, _P, C.POINTER(mrdem_contacts), _P,
                                         _D, _P, _P, _P]),
     "mrdem_newton_residual": (C.c_int, [_P, _I, _P, _P, _P, _P, _P, _P, _D, _P, _P, _P]),
-    "mrdem_newton_solve": (C.c_int, [_P, _I, _I64, _P, _P, _P, _P, _D, _P, _P, _I, _D, _P, _P]),
+    "mrdem_newton_solve": (C.c_int, [_P, _I, _I64, _P, _P, _P, _P, _D, _P, _P, _I, _D, _I, _P,
+                                     _P]),
     "mrdem_vel_axpy": (C.c_int, [_P, _I64, _D, _P, _P, _P, _P]),
     "mrdem_refine_contacts": (C.c_int, [_P, _P, _I64, _P, _P, _P, C.POINTER(mrdem_contacts),
                                         C.POINTER(mrdem_contacts), _P]),

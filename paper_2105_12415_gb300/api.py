@@ -641,7 +641,7 @@ def newton_residual(ctx, vel0, vel, force_torque, mass, inertia, dt, res=None, n
 
 
 def newton_solve(ctx, pairs, blocks, mass, inertia, dt, rhs, x=None, max_iter=200, rel_tol=1e-12,
-                 info=None, stream=None):
+                 info=None, stream=None, check_every=0):
     """x with (M/dt + dt K) x = rhs by preconditioned conjugate gradients (K
     the pair blocks); returns (x [n, 6], info (iterations, relative
     residual, breakdown flag, |rhs|))."""
@@ -655,7 +655,8 @@ def newton_solve(ctx, pairs, blocks, mass, inertia, dt, rhs, x=None, max_iter=20
         info = torch.empty(4, dtype=torch.float64, device=rhs.device)
     L.check(L.load().mrdem_newton_solve(ctx.handle, n, P, _p(pairs), _p(blocks), _p(mass),
                                         _p(inertia), float(dt), _p(rhs), _p(x), int(max_iter),
-                                        float(rel_tol), _p(info), _stream(stream)),
+                                        float(rel_tol), int(check_every), _p(info),
+                                        _stream(stream)),
             "mrdem_newton_solve")
     return x, info
 
@@ -717,7 +718,8 @@ def implicit_euler_step_newton(ctx: Context, hier: Hierarchy, poses0, vel0, mass
             blocks.zero_()
             contact_hessian(ctx, hier, pairs, eps, poses, state["contacts"], mass, k_s,
                             blocks=blocks)
-        newton_solve(ctx, pairs, blocks, mass, inertia, dt, res, x, cg_iter, cg_tol, info)
+        newton_solve(ctx, pairs, blocks, mass, inertia, dt, res, x, cg_iter, cg_tol, info,
+                     check_every=16)
         cg = info.tolist()
         lam, halvings = 1.0, 0
         while True:

@@ -631,17 +631,17 @@ int mrdem_newton_residual(mrdem_ctx* c, int32_t n, const double* vel0, const dou
 int mrdem_newton_solve(mrdem_ctx* c, int32_t n, int64_t n_pairs, const int32_t* ab,
                        const double* blocks, const double* mass, const double* inertia, double dt,
                        const double* rhs, double* x, int32_t max_iter, double rel_tol,
-                       double* info, mrdem_stream s) {
+                       int32_t check_every, double* info, mrdem_stream s) {
   if (!c || n < 0 || n > ((int32_t)1 << 26) || n_pairs < 0 || n_pairs >= (int64_t)1 << 31 ||
       !info || !(dt > 0.0) || !std::isfinite(dt) || max_iter < 0 || max_iter > 100000 ||
-      !(rel_tol >= 0.0) || !std::isfinite(rel_tol))
+      !(rel_tol >= 0.0) || !std::isfinite(rel_tol) || check_every < 0)
     return MRDEM_ERR_INVALID;
   if (n > 0 && (!mass || !inertia || !rhs || !x)) return MRDEM_ERR_INVALID;
   if (n_pairs > 0 && (!ab || !blocks)) return MRDEM_ERR_INVALID;
   if (n > 0 && (const void*)rhs == (const void*)x) return MRDEM_ERR_INVALID;
   DeviceGuard g(c->device);
   return launch_newton_solve(c, n, n_pairs, ab, blocks, mass, inertia, dt, rhs, x, max_iter,
-                             rel_tol, info, (cudaStream_t)s);
+                             rel_tol, check_every, info, (cudaStream_t)s);
 }
 
 int mrdem_vel_axpy(mrdem_ctx* c, int64_t m, double a, const double* x, const double* y,

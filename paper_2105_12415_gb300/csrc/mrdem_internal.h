@@ -296,7 +296,7 @@ int launch_vel_axpy(mrdem_ctx* ctx, int64_t m, double a, const double* x, const 
 int launch_newton_solve(mrdem_ctx* ctx, int32_t n, int64_t n_pairs, const int32_t* pair_ab,
                         const double* blocks, const double* mass, const double* inertia,
                         double dt, const double* rhs, double* x, int32_t max_iter, double rel_tol,
-                        double* info, cudaStream_t s);
+                        int32_t check_every, double* info, cudaStream_t s);
 int launch_refine_contacts(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
                            const int32_t* pair_ab, const double* pair_eps, const double* poses,
                            const mrdem_contacts* cand, const mrdem_contacts* out, cudaStream_t s);

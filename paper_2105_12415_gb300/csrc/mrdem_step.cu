@@ -770,7 +770,7 @@ static int ensure_cg(mrdem_ctx* c, int32_t n, int32_t max_iter, CgView* v) {
 int launch_newton_solve(mrdem_ctx* c, int32_t n, int64_t n_pairs, const int32_t* ab,
                         const double* blocks, const double* mass, const double* inertia,
                         double dt, const double* rhs, double* x, int32_t max_iter, double rel_tol,
-                        double* info, cudaStream_t s) {
+                        int32_t check_every, double* info, cudaStream_t s) {
   CgView v;
   int st = ensure_cg(c, n, max_iter, &v);
   if (st) return st;
@@ -790,6 +790,16 @@ int launch_newton_solve(mrdem_ctx* c, int32_t n, int64_t n_pairs, const int32_t*
   launch_after(k_cg_init2, nd, kThreads, 0, s, v);
   launch_after(k_cg_check, 1, 1, 0, s, v, -1, tol2);
   for (int k = 0; k < max_iter; ++k) {
+    if (check_every > 0 && k > 0 && k % check_every == 0) {
+      // stop enqueueing once the solve has finished (synchronises the stream)
+      CgState st;
+      if (cudaMemcpyAsync(&st, v.st, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return MRDEM_ERR_CUDA;
+      }
+      if (st.done) break;
+    }
     launch_after(k_cg_ap_diag, nd, kThreads, 0, s, v);
     if (n_pairs > 0) launch_after(k_cg_ap_pairs, np, kThreads, 0, s, v, n_pairs, ab, blocks);
     launch_after(k_cg_pap, nd, kThreads, 0, s, v, k);

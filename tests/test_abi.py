@@ -88,7 +88,7 @@ def test_null_arguments_are_rejected():
     assert lib.mrdem_newton_residual(None, 0, None, None, None, None, None,
                                      C.cast(g, C.c_void_p), 1e-3, None, None, None) == -1
     assert lib.mrdem_newton_solve(None, 0, 0, None, None, None, None, 1e-3, None, None, 10, 1e-10,
-                                  None, None) == -1
+                                  0, None, None) == -1
     assert lib.mrdem_vel_axpy(None, 0, 1.0, None, None, None, None) == -1
     assert lib.mrdem_destroy(None) == 0
 

@@ -345,6 +345,11 @@ def test_newton_solve_conjugate_gradients(m, ctx):
     assert brk == 0 and 0 < it < 400 and rel <= 1e-13
     assert abs(bn - np.linalg.norm(b)) <= 1e-12 * bn
     assert np.abs(x.cpu().numpy() - want).max() <= 1e-10 * np.abs(want).max()
+    # the same solve, stopped from the host every 4 iterations
+    x4, info4 = m.newton_solve(ctx, _t(pairs, "int32"), _t(blocks), _t(mass), _t(inertia), dt,
+                               _t(b), max_iter=400, rel_tol=1e-13, check_every=4)
+    assert info4.cpu().numpy()[2] == 0 and info4.cpu().numpy()[1] <= 1e-13
+    assert np.abs(x4.cpu().numpy() - want).max() <= 1e-10 * np.abs(want).max()
     # no pairs: x = b dt / M exactly up to rounding, in one iteration
     x0, info0 = m.newton_solve(ctx, _t(np.zeros((0, 2)), "int32"), _t(np.zeros((0, 12, 12))),
                                _t(mass), _t(inertia), dt, _t(b), max_iter=10, rel_tol=1e-14)
