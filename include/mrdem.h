@@ -323,10 +323,14 @@ int mrdem_merge_contacts(mrdem_ctx* ctx, int64_t n_pairs, const double* pair_eps
  *           again.
  * The decision |c_i - c_j| <= ... is taken in FP64 without fused
  * multiply-adds ((dx^2 + dy^2) + dz^2, sqrt; (R_i + R_j) + 2 eps_ij), so the
- * list is a deterministic function of the inputs.  Uniform grid of cells no
- * smaller than the largest R_i + R_j + 2 eps_ij, hashed into 2^k >= 2n
- * buckets; the context keeps about 28 n + 4 * 2^k bytes of scratch, grown on
- * a larger call.  Device-side failure latched for mrdem_check: a centre,
+ * list is a deterministic function of the inputs.  Particles are sorted into
+ * up to 8 size classes by R (class k: R in (R_max/2^(k+1), R_max/2^k]), each
+ * with a uniform grid of cells of side 2 R_max/2^k, all hashed into 2^k >= 2n
+ * buckets; a particle searches each class's cells within R_i + R_max/2^k +
+ * 4 eps_rel r_i of its centre (or that class's particles, when fewer), so
+ * big particles among small ones do not coarsen the small ones' cells.  The
+ * context keeps about 36 n + 4 * 2^k bytes of scratch, grown on a larger
+ * call.  Device-side failure latched for mrdem_check: a centre,
  * bound or radius that is not finite, or a negative bound or radius:
  * NONFINITE (count is then 0).  Errors returned directly: INVALID (null
  * pointers, n > 2^26, cap >= 2^31, eps_rel negative or not finite), OOM,

@@ -4,12 +4,17 @@
 // of the velocities with its convergence measure.
 //
 // Broad phase, one call:
-//   k_bp_bounds   one block: smallest centre per axis, largest bounding radius
-//                 and radius -> cell side; flags non-finite input;
-//   k_bp_cells    cell and bucket of every particle, bucket sizes;
-//   k_bp_scan     exclusive scan of the bucket sizes -> bucket starts;
-//   k_bp_scatter  particles grouped by bucket (the starts end as the ends);
-//   k_bp_count    a thread per particle: its candidates j > i in the 27 cells;
+//   k_bp_bounds   one block: smallest centre per axis, largest and smallest
+//                 bounding radius -> size classes and their cell sides;
+//                 flags non-finite input;
+//   k_bp_cells    class, cell and bucket of every particle; bucket and
+//                 class sizes;
+//   k_bp_scan     exclusive scans of the bucket and class sizes -> starts;
+//   k_bp_scatter  particles grouped by bucket and by class (the starts end
+//                 as the ends);
+//   k_bp_count    a thread per particle: its candidates j > i, class by
+//                 class, in the cells of that class's grid that its search
+//                 box meets (or the class's particles, when fewer);
 //   k_bp_scan     exclusive scan of the counts -> output offsets and the total;
 //   k_bp_write    if the total fits: each particle writes its candidates at its
 //                 offset and sorts them by j, so the list is ordered by (i, j)
@@ -49,7 +54,7 @@ __global__ void __launch_bounds__(kBoundsThreads) k_bp_bounds(BroadIn in, BroadG
                                                               unsigned long long* status) {
   wait_prior_grid();
   __shared__ double part[5][32];
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, rb = 0.0, rr = 0.0;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, rb = 0.0, rmin = INFINITY;
   bool bad = false;
   for (int32_t i = threadIdx.x; i < in.n; i += blockDim.x) {
     const double* c = in.poses + (int64_t)7 * i;
@@ -61,27 +66,34 @@ __global__ void __launch_bounds__(kBoundsThreads) k_bp_bounds(BroadIn in, BroadG
     const double R = in.bound[i], r = in.radius[i];
     if (!(R >= 0.0) || !isfinite(R) || !(r >= 0.0) || !isfinite(r)) bad = true;
     rb = fmax(rb, R);
-    rr = fmax(rr, r);
+    rmin = fmin(rmin, R);
   }
-  double v[5] = {warp_min(lo[0]), warp_min(lo[1]), warp_min(lo[2]), warp_max(rb), warp_max(rr)};
+  // mins of the three coordinates and of R, max of R
+  double v[5] = {warp_min(lo[0]), warp_min(lo[1]), warp_min(lo[2]), warp_max(rb), warp_min(rmin)};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (lane == 0)
     for (int k = 0; k < 5; ++k) part[k][warp] = v[k];
   bad = __syncthreads_or(bad) != 0;
   if (warp == 0) {
     for (int k = 0; k < 5; ++k) {
-      double x = lane < nw ? part[k][lane] : (k < 3 ? INFINITY : 0.0);
-      v[k] = k < 3 ? warp_min(x) : warp_max(x);
+      const bool is_max = k == 3;
+      double x = lane < nw ? part[k][lane] : (is_max ? 0.0 : INFINITY);
+      v[k] = is_max ? warp_max(x) : warp_min(x);
     }
     if (lane == 0) {
       BroadGrid g;
       g.lo[0] = v[0];
       g.lo[1] = v[1];
       g.lo[2] = v[2];
-      g.h = bp_cell_side(v[3], v[4], in.eps_rel);
-      g.inv_h = 1.0 / g.h;
-      g.bad = (bad || !isfinite(g.h)) ? 1 : 0;
-      g.pad = 0;
+      g.r_max = v[3];
+      g.classes = bp_classes(v[3], v[4]);
+      bool ok = !bad && isfinite(g.r_max);
+      for (int k = 0; k < kMaxClasses; ++k) {
+        g.h[k] = bp_cell_side(g.r_max, k);
+        g.inv_h[k] = 1.0 / g.h[k];
+        ok = ok && isfinite(g.h[k]) && g.h[k] > 0.0;
+      }
+      g.bad = ok ? 0 : 1;
       *grid = g;
       if (g.bad) atomicExch(status + ST_NONFINITE, 1ull);
     }
@@ -95,14 +107,10 @@ __global__ void __launch_bounds__(kThreads) k_bp_cells(BroadIn in, const BroadGr
   if (g.bad) return;
   const int32_t step = gridDim.x * blockDim.x;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += step) {
-    const double* c = in.poses + (int64_t)7 * i;
-    BroadCell cl;
-    cl.x = bp_cell(c[0], g.lo[0], g.inv_h);
-    cl.y = bp_cell(c[1], g.lo[1], g.inv_h);
-    cl.z = bp_cell(c[2], g.lo[2], g.inv_h);
-    cl.b = bp_bucket(cl.x, cl.y, cl.z, w.log2_t);
+    const BroadCell cl = bp_cell_of(in, g, i, w.log2_t);
     w.cell[i] = cl;
     atomicAdd(w.bucket_end + cl.b, 1);
+    atomicAdd(w.class_end + cl.k, 1);
   }
 }
 
@@ -116,17 +124,20 @@ __global__ void __launch_bounds__(kThreads) k_bp_scatter(BroadIn in, const Broad
   wait_prior_grid();
   if (grid->bad) return;
   const int32_t step = gridDim.x * blockDim.x;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += step)
-    w.order[atomicAdd(w.bucket_end + w.cell[i].b, 1)] = i;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += step) {
+    const BroadCell cl = w.cell[i];
+    w.order[atomicAdd(w.bucket_end + cl.b, 1)] = i;
+    w.class_order[atomicAdd(w.class_end + cl.k, 1)] = i;
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) k_bp_count(BroadIn in, const BroadGrid* grid,
                                                        BroadWork w, int32_t* cnt) {
   wait_prior_grid();
-  const bool bad = grid->bad != 0;
+  const BroadGrid g = *grid;
   const int32_t step = gridDim.x * blockDim.x;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += step)
-    cnt[i] = bad ? 0 : bp_visit(in, w, i, [](int32_t, double) {});
+    cnt[i] = g.bad ? 0 : bp_visit(in, g, w, i, [](int32_t, double) {});
 }
 
 __global__ void __launch_bounds__(kThreads) k_bp_write(BroadIn in, const BroadGrid* grid,
@@ -135,13 +146,14 @@ __global__ void __launch_bounds__(kThreads) k_bp_write(BroadIn in, const BroadGr
                                                        int32_t* pairs, double* pair_eps) {
   wait_prior_grid();
   const int64_t total = *count;
-  if (grid->bad || total > cap) return;
+  const BroadGrid g = *grid;
+  if (g.bad || total > cap) return;
   const int32_t step = gridDim.x * blockDim.x;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += step) {
     const int64_t o = off[i];
     const int64_t m = (i + 1 < in.n ? (int64_t)off[i + 1] : total) - o;
     int64_t k = 0;
-    bp_visit(in, w, i, [&](int32_t j, double e) {
+    bp_visit(in, g, w, i, [&](int32_t j, double e) {
       if (k < m) {
         pairs[2 * (o + k) + 1] = j;
         pair_eps[o + k] = e;
@@ -610,14 +622,15 @@ int blocks_for(const mrdem_ctx* c, int64_t n) {
 
 }  // namespace
 
-// Broad-phase scratch: the grid record, then cell [n], order [n], counts /
-// offsets [n], bucket ends [2^log2_t].
+// Broad-phase scratch: the grid record, then cell [n], order [n], class
+// order [n], counts / offsets [n], bucket ends [2^log2_t], class ends.
 static int ensure_broad(mrdem_ctx* c, int32_t n, BroadWork* w, BroadGrid** grid,
                         int32_t** cnt) {
   const int log2_t = ceil_log2(2 * (int64_t)n) < 6 ? 6 : ceil_log2(2 * (int64_t)n);
   const int64_t t = (int64_t)1 << log2_t;
-  const size_t bytes = 256 + sizeof(BroadCell) * (size_t)n + sizeof(int32_t) * (size_t)n * 2 +
-                       sizeof(int32_t) * (size_t)t + 64;
+  static_assert(sizeof(BroadGrid) <= 512, "grid record");
+  const size_t bytes = 512 + sizeof(BroadCell) * (size_t)n + sizeof(int32_t) * (size_t)n * 3 +
+                       sizeof(int32_t) * ((size_t)t + kMaxClasses) + 64;
   if (bytes > c->cap_broad) {
     cudaFree(c->broad_mem);
     c->broad_mem = nullptr;
@@ -631,14 +644,18 @@ static int ensure_broad(mrdem_ctx* c, int32_t n, BroadWork* w, BroadGrid** grid,
   }
   unsigned char* p = static_cast<unsigned char*>(c->broad_mem);
   *grid = reinterpret_cast<BroadGrid*>(p);
-  p += 256;
+  p += 512;
   w->cell = reinterpret_cast<BroadCell*>(p);
   p += sizeof(BroadCell) * (size_t)n;
   w->order = reinterpret_cast<int32_t*>(p);
   p += sizeof(int32_t) * (size_t)n;
+  w->class_order = reinterpret_cast<int32_t*>(p);
+  p += sizeof(int32_t) * (size_t)n;
   *cnt = reinterpret_cast<int32_t*>(p);
   p += sizeof(int32_t) * (size_t)n;
   w->bucket_end = reinterpret_cast<int32_t*>(p);
+  p += sizeof(int32_t) * (size_t)t;
+  w->class_end = reinterpret_cast<int32_t*>(p);
   w->log2_t = log2_t;
   return MRDEM_OK;
 }
@@ -660,10 +677,12 @@ int launch_broad_phase(mrdem_ctx* c, int32_t n, const double* poses, const doubl
   const int64_t t = (int64_t)1 << w.log2_t;
   const int nb = blocks_for(c, n);
   ProfScope ps(c, K_BROAD, s);
-  cudaMemsetAsync(w.bucket_end, 0, sizeof(int32_t) * (size_t)t, s);
+  // bucket ends and class ends are contiguous
+  cudaMemsetAsync(w.bucket_end, 0, sizeof(int32_t) * ((size_t)t + kMaxClasses), s);
   launch_after(k_bp_bounds, 1, kBoundsThreads, 0, s, in, grid, c->status);
   launch_after(k_bp_cells, nb, kThreads, 0, s, in, (const BroadGrid*)grid, w);
   launch_after(k_bp_scan, 1, 1024, 0, s, w.bucket_end, t, (int64_t*)nullptr);
+  launch_after(k_bp_scan, 1, 1024, 0, s, w.class_end, (int64_t)kMaxClasses, (int64_t*)nullptr);
   launch_after(k_bp_scatter, nb, kThreads, 0, s, in, (const BroadGrid*)grid, w);
   launch_after(k_bp_count, nb, kThreads, 0, s, in, (const BroadGrid*)grid, w, cnt);
   launch_after(k_bp_scan, 1, 1024, 0, s, cnt, (int64_t)n, count);

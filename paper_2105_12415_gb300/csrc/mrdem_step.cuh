@@ -8,15 +8,16 @@
 // (eps relative to the smaller particle diameter, Sec. 6).  A pair i < j is a
 // candidate when the bounding spheres widened by eps_ij overlap:
 //   |c_i - c_j| <= R_i + R_j + 2 eps_ij.
-// Cells of side h >= max (R_i + R_j + 2 eps_ij) put every candidate of i in one
-// of the 27 cells around i's cell.  Cells are hashed into a power-of-two table
-// (the spatial hash of Teschner et al. 2003, "Optimized spatial hashing for
-// collision detection of deformable objects"); a bucket can hold several cells,
-// so a particle found in a bucket counts only if its own cell is the one being
-// visited, which also keeps a particle from being seen twice when two of the 27
-// cells share a bucket.  The distance test runs in FP64 without fused
-// multiply-adds, term by term ((dx^2 + dy^2) + dz^2, then sqrt), so its
-// decisions do not depend on the compiler.
+// Particles are sorted into size classes by R, each class with a grid of its
+// own (cells hashed into one power-of-two table with the spatial hash of
+// Teschner et al. 2003, "Optimized spatial hashing for collision detection of
+// deformable objects", the class mixed into the hash); a bucket can hold
+// several cells, so a particle found in a bucket counts only if its own cell
+// and class are the ones being visited, which also keeps a particle from
+// being seen twice when two visited cells share a bucket.  The distance test
+// runs in FP64 without fused multiply-adds, term by term
+// ((dx^2 + dy^2) + dz^2, then sqrt), so its decisions do not depend on the
+// compiler.
 #pragma once
 
 #include <math.h>
@@ -26,18 +27,31 @@
 
 namespace mrdem {
 
-// Grid of the broad phase, written by the bounds kernel: lo = the smallest
-// centre coordinate per axis, h = the cell side, inv_h = 1 / h.
+// Size classes: class k holds the bounding radii R in (R_max/2^(k+1),
+// R_max/2^k], the last class everything smaller; each class has its own grid
+// of cells of side 2 R_max/2^k, hashed into one shared table.  Particle i
+// finds its candidates of class b in the cells of b's grid that meet the box
+// of half-width R_i + R_max/2^b + 4 eps_rel r_i around c_i (every candidate
+// j of class b lies in it: R_j <= R_max/2^b and 2 eps_ij <= 4 eps_rel r_i),
+// or, when that box holds more cells than class b has particles, by running
+// through class b's particles.  So a few big particles among many small
+// ones cost the small ones nothing: cells are sized per class, not by the
+// largest particle.
+constexpr int kMaxClasses = 8;
+
+// Grid of the broad phase, written by the bounds kernel.
 struct BroadGrid {
-  double lo[3];
-  double h, inv_h;
-  int32_t bad;  // a centre, bound or radius was not finite (or negative)
-  int32_t pad;
+  double lo[3];                 // smallest centre coordinate per axis
+  double r_max;                 // largest bounding radius
+  double h[kMaxClasses];        // cell side of class k
+  double inv_h[kMaxClasses];
+  int32_t classes;              // number of classes K
+  int32_t bad;                  // a centre, bound or radius was not finite (or negative)
 };
 
-// Cell sides are widened by this relative slack so that rounding in
-// (x - lo) * inv_h (up to a few ulp of cell coordinates below 2^30) cannot
-// put two candidates two cells apart.
+// Cell sides and search radii are widened by this relative slack, and the
+// search box by a few ulps of the coordinates, so that rounding in
+// (x - lo) * inv_h cannot leave a candidate outside the cells visited.
 constexpr double kCellSlack = 1.0 + 1.0 / 65536.0;
 constexpr double kCellMax = 1073741824.0;  // cell coordinates are clamped to [0, 2^30]
 
@@ -57,10 +71,27 @@ MRDEM_HD double bp_add(double a, double b) {
 #endif
 }
 
-// Cell side from the largest bounding radius and radius: every candidate pair
-// has R_i + R_j + 2 eps_ij <= 2 R_max + 4 eps_rel r_max.
-MRDEM_HD double bp_cell_side(double r_bound_max, double r_max, double eps_rel) {
-  const double h = (2.0 * r_bound_max + 4.0 * eps_rel * r_max) * kCellSlack;
+// Upper end R_max / 2^k of class k (exact: a power-of-two scaling).
+MRDEM_HD double bp_class_top(double r_max, int k) { return ldexp(r_max, -k); }
+
+// Number of classes for radii in [r_min, r_max]: enough that the smallest
+// radius falls in the last one, at most kMaxClasses.
+MRDEM_HD int bp_classes(double r_max, double r_min) {
+  int K = 1;
+  while (K < kMaxClasses && r_min <= bp_class_top(r_max, K)) ++K;
+  return K;
+}
+
+// Class of bounding radius R.
+MRDEM_HD int bp_class(double R, double r_max, int K) {
+  int k = 0;
+  while (k < K - 1 && R <= bp_class_top(r_max, k + 1)) ++k;
+  return k;
+}
+
+// Cell side of class k.
+MRDEM_HD double bp_cell_side(double r_max, int k) {
+  const double h = 2.0 * bp_class_top(r_max, k) * kCellSlack;
   return h > 0.0 ? h : 1.0;  // all zero: candidates coincide, any side will do
 }
 
@@ -72,10 +103,10 @@ MRDEM_HD int32_t bp_cell(double x, double lo, double inv_h) {
   return (int32_t)q;  // truncation = floor for q > 0
 }
 
-// Bucket of cell (x, y, z) in a table of 2^log2_t buckets.
-MRDEM_HD uint32_t bp_bucket(int32_t x, int32_t y, int32_t z, int log2_t) {
+// Bucket of cell (x, y, z) of class k in a table of 2^log2_t buckets.
+MRDEM_HD uint32_t bp_bucket(int32_t x, int32_t y, int32_t z, int32_t k, int log2_t) {
   const uint32_t hsh = ((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349663u) ^
-                       ((uint32_t)z * 83492791u);
+                       ((uint32_t)z * 83492791u) ^ ((uint32_t)k * 1566083941u);
   return hsh & ((1u << log2_t) - 1u);
 }
 
@@ -103,50 +134,82 @@ struct BroadIn {
   int32_t n;
 };
 
-// Cell of a particle: coordinates and bucket.
-struct alignas(16) BroadCell {
-  int32_t x, y, z;
+// Cell of a particle: coordinates in its class's grid, class, bucket.
+struct alignas(8) BroadCell {
+  int32_t x, y, z, k;
   uint32_t b;
+  int32_t pad;
 };
 
-// Working arrays: cell[i] = (cx, cy, cz, bucket) of particle i; order = the
-// particles grouped by bucket; bucket_end[b] = one past the last entry of
-// bucket b in order (bucket b starts at bucket_end[b - 1], or 0).
+// Working arrays: cell[i] of particle i; order = the particles grouped by
+// bucket, bucket_end[b] = one past the last entry of bucket b in order
+// (bucket b starts at bucket_end[b - 1], or 0); class_order = the particles
+// grouped by class, class_end[k] likewise.
 struct BroadWork {
   BroadCell* cell;
   int32_t* order;
   int32_t* bucket_end;
+  int32_t* class_order;
+  int32_t* class_end;
   int log2_t;
 };
 
-// Visits the candidates j > i of particle i in bucket order; calls f(j, eps_ij)
+// Cell of particle i from its centre and bounding radius.
+MRDEM_HD BroadCell bp_cell_of(const BroadIn& in, const BroadGrid& g, int32_t i, int log2_t) {
+  const double* c = in.poses + (int64_t)7 * i;
+  BroadCell cl;
+  cl.k = bp_class(in.bound[i], g.r_max, g.classes);
+  cl.x = bp_cell(c[0], g.lo[0], g.inv_h[cl.k]);
+  cl.y = bp_cell(c[1], g.lo[1], g.inv_h[cl.k]);
+  cl.z = bp_cell(c[2], g.lo[2], g.inv_h[cl.k]);
+  cl.b = bp_bucket(cl.x, cl.y, cl.z, cl.k, log2_t);
+  cl.pad = 0;
+  return cl;
+}
+
+// Visits the candidates j > i of particle i, class by class; calls f(j, eps_ij)
 // for each and returns how many there were.
 template <typename F>
-MRDEM_HD int32_t bp_visit(const BroadIn& in, const BroadWork& w, int32_t i, F f) {
+MRDEM_HD int32_t bp_visit(const BroadIn& in, const BroadGrid& g, const BroadWork& w, int32_t i,
+                          F f) {
   const double* ci = in.poses + (int64_t)7 * i;
   const double Ri = in.bound[i], ri = in.radius[i];
-  const BroadCell me = w.cell[i];
   int32_t found = 0;
-  for (int dz = -1; dz <= 1; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int32_t x = me.x + dx, y = me.y + dy, z = me.z + dz;
-        if (x < 0 || y < 0 || z < 0 || x > (int32_t)kCellMax || y > (int32_t)kCellMax ||
-            z > (int32_t)kCellMax)
-          continue;  // no particle lives there
-        const uint32_t b = bp_bucket(x, y, z, w.log2_t);
-        const int32_t beg = b ? w.bucket_end[b - 1] : 0, end = w.bucket_end[b];
-        for (int32_t k = beg; k < end; ++k) {
-          const int32_t j = w.order[k];
-          if (j <= i) continue;
-          const BroadCell cj = w.cell[j];
-          if (cj.x != x || cj.y != y || cj.z != z) continue;
-          const double eij = bp_pair_eps(ri, in.radius[j], in.eps_rel);
-          if (!bp_candidate(ci, in.poses + (int64_t)7 * j, Ri, in.bound[j], eij)) continue;
-          f(j, eij);
-          ++found;
+  auto test = [&](int32_t j) {
+    if (j <= i) return;
+    const double eij = bp_pair_eps(ri, in.radius[j], in.eps_rel);
+    if (!bp_candidate(ci, in.poses + (int64_t)7 * j, Ri, in.bound[j], eij)) return;
+    f(j, eij);
+    ++found;
+  };
+  for (int b = 0; b < g.classes; ++b) {
+    const int32_t beg = b ? w.class_end[b - 1] : 0, end = w.class_end[b];
+    if (end <= beg) continue;
+    const double rho = (Ri + bp_class_top(g.r_max, b) + 4.0 * in.eps_rel * ri) * kCellSlack;
+    int32_t lo[3], hi[3];
+    double ncells = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      const double pad = (fabs(ci[a]) + fabs(g.lo[a]) + rho) * 0x1p-48;
+      lo[a] = bp_cell(ci[a] - rho - pad, g.lo[a], g.inv_h[b]);
+      hi[a] = bp_cell(ci[a] + rho + pad, g.lo[a], g.inv_h[b]);
+      ncells *= (double)(hi[a] - lo[a] + 1);
+    }
+    if (ncells > (double)(end - beg)) {
+      for (int32_t q = beg; q < end; ++q) test(w.class_order[q]);
+      continue;
+    }
+    for (int32_t z = lo[2]; z <= hi[2]; ++z)
+      for (int32_t y = lo[1]; y <= hi[1]; ++y)
+        for (int32_t x = lo[0]; x <= hi[0]; ++x) {
+          const uint32_t bk = bp_bucket(x, y, z, b, w.log2_t);
+          const int32_t kb = bk ? w.bucket_end[bk - 1] : 0, ke = w.bucket_end[bk];
+          for (int32_t q = kb; q < ke; ++q) {
+            const int32_t j = w.order[q];
+            const BroadCell cj = w.cell[j];
+            if (cj.k == b && cj.x == x && cj.y == y && cj.z == z) test(j);
+          }
         }
-      }
+  }
   return found;
 }
 

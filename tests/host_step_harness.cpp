@@ -13,36 +13,52 @@ using namespace mrdem;
 extern "C" long long hs_broad_phase(int n, const double* poses, const double* bound,
                                     const double* radius, double eps_rel, int* pairs,
                                     double* pair_eps, long long cap, unsigned shuffle) {
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, rb = 0.0, rr = 0.0;
+  // k_bp_bounds
+  BroadGrid g;
+  g.lo[0] = g.lo[1] = g.lo[2] = INFINITY;
+  double rb = 0.0, rmin = INFINITY;
   for (int i = 0; i < n; ++i) {
-    for (int k = 0; k < 3; ++k) lo[k] = fmin(lo[k], poses[7 * i + k]);
+    for (int k = 0; k < 3; ++k) g.lo[k] = fmin(g.lo[k], poses[7 * i + k]);
     rb = fmax(rb, bound[i]);
-    rr = fmax(rr, radius[i]);
+    rmin = fmin(rmin, bound[i]);
   }
-  const double h = bp_cell_side(rb, rr, eps_rel), inv_h = 1.0 / h;
+  g.r_max = rb;
+  g.classes = bp_classes(rb, rmin);
+  for (int k = 0; k < kMaxClasses; ++k) {
+    g.h[k] = bp_cell_side(rb, k);
+    g.inv_h[k] = 1.0 / g.h[k];
+  }
+  g.bad = 0;
   int log2_t = 6;
   while ((1LL << log2_t) < 2LL * n) ++log2_t;
   const long long t = 1LL << log2_t;
   std::vector<BroadCell> cell(n);
-  std::vector<int32_t> order(n), bucket_end(t, 0), cnt(n);
-  BroadWork w{cell.data(), order.data(), bucket_end.data(), log2_t};
+  std::vector<int32_t> order(n), class_order(n), bucket_end(t, 0), class_end(kMaxClasses, 0),
+      cnt(n);
+  BroadWork w{cell.data(), order.data(), bucket_end.data(), class_order.data(), class_end.data(),
+              log2_t};
+  const BroadIn in{poses, bound, radius, eps_rel, n};
+  // k_bp_cells
   for (int i = 0; i < n; ++i) {
-    BroadCell c;
-    c.x = bp_cell(poses[7 * i], lo[0], inv_h);
-    c.y = bp_cell(poses[7 * i + 1], lo[1], inv_h);
-    c.z = bp_cell(poses[7 * i + 2], lo[2], inv_h);
-    c.b = bp_bucket(c.x, c.y, c.z, log2_t);
-    cell[i] = c;
-    ++bucket_end[c.b];
+    cell[i] = bp_cell_of(in, g, i, log2_t);
+    ++bucket_end[cell[i].b];
+    ++class_end[cell[i].k];
   }
+  // k_bp_scan (buckets, classes)
   long long run = 0;
   for (long long b = 0; b < t; ++b) {
     const int c = bucket_end[b];
     bucket_end[b] = (int32_t)run;
     run += c;
   }
-  // the kernel's atomics group a bucket's particles in any order: scatter
-  // them in a shuffled order
+  run = 0;
+  for (int k = 0; k < kMaxClasses; ++k) {
+    const int c = class_end[k];
+    class_end[k] = (int32_t)run;
+    run += c;
+  }
+  // k_bp_scatter: the kernel's atomics group a bucket's (and a class's)
+  // particles in any order; scatter them in a shuffled order
   std::vector<int> idx(n);
   for (int i = 0; i < n; ++i) idx[i] = i;
   unsigned s = shuffle;
@@ -53,9 +69,13 @@ extern "C" long long hs_broad_phase(int n, const double* poses, const double* bo
     idx[i] = idx[j];
     idx[j] = tmp;
   }
-  for (int q = 0; q < n; ++q) order[bucket_end[cell[idx[q]].b]++] = idx[q];
-  const BroadIn in{poses, bound, radius, eps_rel, n};
-  for (int i = 0; i < n; ++i) cnt[i] = bp_visit(in, w, i, [](int32_t, double) {});
+  for (int q = 0; q < n; ++q) {
+    const int i = idx[q];
+    order[bucket_end[cell[i].b]++] = i;
+    class_order[class_end[cell[i].k]++] = i;
+  }
+  // k_bp_count, k_bp_scan
+  for (int i = 0; i < n; ++i) cnt[i] = bp_visit(in, g, w, i, [](int32_t, double) {});
   long long total = 0;
   for (int i = 0; i < n; ++i) {
     const int c = cnt[i];
@@ -63,10 +83,11 @@ extern "C" long long hs_broad_phase(int n, const double* poses, const double* bo
     total += c;
   }
   if (total > cap) return total;
+  // k_bp_write
   for (int i = 0; i < n; ++i) {
     const long long o = cnt[i], m = (i + 1 < n ? cnt[i + 1] : total) - o;
     long long k = 0;
-    bp_visit(in, w, i, [&](int32_t j, double e) {
+    bp_visit(in, g, w, i, [&](int32_t j, double e) {
       if (k < m) {
         pairs[2 * (o + k) + 1] = j;
         pair_eps[o + k] = e;

@@ -212,3 +212,17 @@ def orc_matrix(q):
     return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
                      [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def test_broad_phase_functions_with_size_disparity(hs, imp):
+    """Big particles (radius 20) among small ones (radius 1): the size
+    classes give the oracle's list bit for bit."""
+    from gen.icosphere import scene_scale
+    s, _ = scene_scale(n_small=3000, n_big=4, fraction=0.2)
+    bound = _bound(s)
+    ref = imp.broad_phase(s.poses[:, :3], bound, s.radius)
+    assert (ref[:, 0] < 4).sum() >= 3 and (ref[:, 0] >= 4).sum() > 100   # big-small and small-small
+    for shuffle in (0, 5):
+        pairs, eps = _broad(hs, s.poses, bound, s.radius, shuffle)
+        assert np.array_equal(pairs, ref)
+        assert np.array_equal(eps, imp.pair_eps(s.radius, ref[:, 0], ref[:, 1]))
