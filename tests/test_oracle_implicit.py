@@ -484,3 +484,40 @@ def test_scale_generator():
     assert near.sum() >= 100
     s2, frac2 = scene_scale(n_small=1500, n_big=3, fraction=0.2)
     assert frac2 == frac and np.array_equal(s2.poses, s.poses)
+
+
+def test_kept_candidates_premise(orc, imp):
+    """The premise of keeping candidates across iterations: when every point
+    of A moves by at most m_A (centre shift plus rotation angle times the
+    bounding radius) and of B by at most m_B, every triangle distance
+    changes by at most m_A + m_B; so the pairs within 2 eps at the moved
+    poses are among those within 2 (eps + w) at the reference poses when
+    m_A + m_B <= 2 w.  Checked on the chain's triangle pairs under random
+    rigid motions."""
+    import dataclasses
+    from gen import scene_chain
+    s = scene_chain(4, seed=41)
+    pairs = imp.broad_phase(s.poses[:, :3], imp.bounding_radius(s), s.radius)
+    eps = imp.pair_eps(s.radius, pairs[:, 0], pairs[:, 1])
+    base = dataclasses.replace(s, pairs=pairs, eps=eps, com=np.zeros((4, 3)))
+    bound = imp.bounding_radius(s)
+    rng = np.random.default_rng(31)
+    w = 0.25 * eps.min()
+    wide = orc.detect(dataclasses.replace(base, eps=eps + w))
+    keys_wide = set(zip(wide["pair"].tolist(), wide["ta"].tolist(), wide["tb"].tolist()))
+    for _ in range(5):
+        vel = rng.normal(size=(4, 6))
+        motion = np.abs(vel[:, :3]).sum(1) + np.linalg.norm(vel[:, 3:], axis=1) * bound
+        dt = w / motion.max()       # every point moves by at most w
+        moved = imp.moved_poses(s.poses, vel, dt)
+        c = orc.detect(base, poses=moved)
+        keys = set(zip(c["pair"].tolist(), c["ta"].tolist(), c["tb"].tolist()))
+        assert keys <= keys_wide
+        # distances of the kept pairs move by at most the two motions
+        P0 = [orc.world_triangles(base, i) for i in range(4)]
+        P1 = [orc.world_triangles(base, i, poses=moved) for i in range(4)]
+        for p, ta, tb in list(keys_wide)[:200]:
+            a, b = pairs[p]
+            d0 = orc.tri_tri(P0[a][ta], P0[b][tb])[0][0]
+            d1 = orc.tri_tri(P1[a][ta], P1[b][tb])[0][0]
+            assert abs(d1 - d0) <= dt * (motion[a] + motion[b]) * (1 + 1e-9) + 1e-12
