@@ -347,9 +347,8 @@ struct CgView {
   int32_t n;
 };
 
-__device__ __forceinline__ double cg_mdt(const CgView& v, int64_t i) {
-  const int32_t part = (int32_t)(i / 6);
-  return (i % 6 < 3 ? v.mass[part] : v.inertia[part]) / v.dt;
+__device__ __forceinline__ double view_mdt(const CgView& v, int64_t i) {
+  return cg_mdt(v.mass, v.inertia, v.dt, i);
 }
 
 __device__ __forceinline__ double warp_sum_d(double x) {
@@ -364,7 +363,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(CgView v, const double* rh
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step) {
     v.x[i] = 0.0;
     v.r[i] = rhs[i];
-    v.diag[i] = cg_mdt(v, i);
+    v.diag[i] = view_mdt(v, i);
   }
 }
 
@@ -377,17 +376,17 @@ __global__ void __launch_bounds__(kThreads) k_cg_diag_pairs(CgView v, int64_t n_
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_pairs; q += step) {
     const int A = ab[2 * q], B = ab[2 * q + 1];
     if (A < 0 || A >= v.n || B < 0 || B >= v.n) continue;
-    const double* Bq = blocks + 144 * q;
+    double da[6], db[6];
+    cg_pair_diag(blocks + 144 * q, v.dt, da, db);
     for (int k = 0; k < 6; ++k) {
-      atomicAdd(v.diag + (int64_t)6 * A + k, v.dt * Bq[13 * k]);
-      atomicAdd(v.diag + (int64_t)6 * B + k, v.dt * Bq[13 * (6 + k)]);
+      atomicAdd(v.diag + (int64_t)6 * A + k, da[k]);
+      atomicAdd(v.diag + (int64_t)6 * B + k, db[k]);
     }
   }
 }
 
-__device__ __forceinline__ double cg_precond(const CgView& v, int64_t i) {
-  const double d = v.diag[i];
-  return d > 0.0 ? d : cg_mdt(v, i);  // an indefinite diagonal falls back to M/dt
+__device__ __forceinline__ double view_precond(const CgView& v, int64_t i) {
+  return cg_precond(v.diag[i], view_mdt(v, i));  // an indefinite diagonal falls back to M/dt
 }
 
 __global__ void __launch_bounds__(kThreads) k_cg_init2(CgView v) {
@@ -395,7 +394,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_init2(CgView v) {
   const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
   double rz = 0.0, rr = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step) {
-    const double r = v.r[i], z = r / cg_precond(v, i);
+    const double r = v.r[i], z = r / view_precond(v, i);
     v.z[i] = z;
     v.p[i] = z;
     rz += r * z;
@@ -414,7 +413,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_ap_diag(CgView v) {
   if (v.st->done) return;
   const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step)
-    v.ap[i] = cg_mdt(v, i) * v.p[i];
+    v.ap[i] = view_mdt(v, i) * v.p[i];
 }
 
 __global__ void __launch_bounds__(kThreads) k_cg_ap_pairs(CgView v, int64_t n_pairs,
@@ -426,11 +425,11 @@ __global__ void __launch_bounds__(kThreads) k_cg_ap_pairs(CgView v, int64_t n_pa
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_pairs; q += step) {
     const int A = ab[2 * q], B = ab[2 * q + 1];
     if (A < 0 || A >= v.n || B < 0 || B >= v.n) continue;
-    double y[12];
-    block_mul(blocks + 144 * q, v.p + (int64_t)6 * A, v.p + (int64_t)6 * B, y);
+    double ya[6], yb[6];
+    cg_pair_apply(blocks + 144 * q, v.p + (int64_t)6 * A, v.p + (int64_t)6 * B, v.dt, ya, yb);
     for (int k = 0; k < 6; ++k) {
-      atomicAdd(v.ap + (int64_t)6 * A + k, v.dt * y[k]);
-      atomicAdd(v.ap + (int64_t)6 * B + k, v.dt * y[6 + k]);
+      atomicAdd(v.ap + (int64_t)6 * A + k, ya[k]);
+      atomicAdd(v.ap + (int64_t)6 * B + k, yb[k]);
     }
   }
 }
@@ -466,7 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_step(CgView v, int k) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step) {
     v.x[i] += alpha * v.p[i];
     const double r = v.r[i] - alpha * v.ap[i];
-    const double z = r / cg_precond(v, i);
+    const double z = r / view_precond(v, i);
     v.r[i] = r;
     v.z[i] = z;
     rz += r * z;

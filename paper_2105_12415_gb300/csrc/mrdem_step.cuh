@@ -449,4 +449,36 @@ MRDEM_HD void block_mul(const double* B, const double* xa, const double* xb, dou
   }
 }
 
+// A pair's share of (dt K) p: dt times its block applied to (p_A, p_B),
+// split into A's six rows and B's six rows.
+MRDEM_HD void cg_pair_apply(const double* B, const double* pa, const double* pb, double dt,
+                            double ya[6], double yb[6]) {
+  double y[12];
+  block_mul(B, pa, pb, y);
+  for (int k = 0; k < 6; ++k) {
+    ya[k] = dt * y[k];
+    yb[k] = dt * y[6 + k];
+  }
+}
+
+// A pair's share of the diagonal of dt K: dt times the block's diagonal,
+// A's six entries and B's six.
+MRDEM_HD void cg_pair_diag(const double* B, double dt, double da[6], double db[6]) {
+  for (int k = 0; k < 6; ++k) {
+    da[k] = dt * B[13 * k];
+    db[k] = dt * B[13 * (6 + k)];
+  }
+}
+
+// Entry i (= 6 particle + component) of M / dt: mass for the three
+// translations, the moment of inertia for the three rotations.
+MRDEM_HD double cg_mdt(const double* mass, const double* inertia, double dt, int64_t i) {
+  const int64_t part = i / 6;
+  return (i % 6 < 3 ? mass[part] : inertia[part]) / dt;
+}
+
+// The preconditioner's entry: the matrix's diagonal, or M / dt where that
+// is not positive.
+MRDEM_HD double cg_precond(double diag, double mdt) { return diag > 0.0 ? diag : mdt; }
+
 }  // namespace mrdem

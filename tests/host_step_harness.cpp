@@ -157,3 +157,73 @@ extern "C" void hs_newton_residual(int n, const double* vel0, const double* vel,
     norms[1] = b > norms[1] ? b : norms[1];
   }
 }
+
+// (M/dt + dt K) p through the conjugate-gradient kernels' per-element
+// functions, and their preconditioner diagonal
+extern "C" void hs_cg_matvec(int n, long long n_pairs, const int* ab, const double* blocks,
+                             const double* mass, const double* inertia, double dt,
+                             const double* p, double* ap, double* diag) {
+  for (long long i = 0; i < 6LL * n; ++i) {
+    ap[i] = cg_mdt(mass, inertia, dt, i) * p[i];
+    diag[i] = cg_mdt(mass, inertia, dt, i);
+  }
+  for (long long q = 0; q < n_pairs; ++q) {
+    const int A = ab[2 * q], B = ab[2 * q + 1];
+    double ya[6], yb[6], da[6], db[6];
+    cg_pair_apply(blocks + 144 * q, p + 6 * A, p + 6 * B, dt, ya, yb);
+    cg_pair_diag(blocks + 144 * q, dt, da, db);
+    for (int k = 0; k < 6; ++k) {
+      ap[6 * A + k] += ya[k];
+      ap[6 * B + k] += yb[k];
+      diag[6 * A + k] += da[k];
+      diag[6 * B + k] += db[k];
+    }
+  }
+}
+
+// The conjugate-gradient sequence of the kernels (init, check, then per
+// iteration A p, p.Ap, the step or the negative-curvature step, check,
+// direction), serially; returns the iterations, *breakdown the flag.
+extern "C" int hs_cg_solve(int n, long long n_pairs, const int* ab, const double* blocks,
+                           const double* mass, const double* inertia, double dt,
+                           const double* rhs, double* x, int max_iter, double rel_tol,
+                           int* breakdown) {
+  const long long m = 6LL * n;
+  std::vector<double> r(rhs, rhs + m), z(m), p(m), ap(m), diag(m), zero(m, 0.0);
+  hs_cg_matvec(n, n_pairs, ab, blocks, mass, inertia, dt, zero.data(), ap.data(), diag.data());
+  double rz = 0.0, rr0 = 0.0;
+  for (long long i = 0; i < m; ++i) {
+    x[i] = 0.0;
+    z[i] = r[i] / cg_precond(diag[i], cg_mdt(mass, inertia, dt, i));
+    p[i] = z[i];
+    rz += r[i] * z[i];
+    rr0 += r[i] * r[i];
+  }
+  *breakdown = 0;
+  if (rr0 <= rel_tol * rel_tol * rr0) return 0;
+  for (int k = 0; k < max_iter; ++k) {
+    hs_cg_matvec(n, n_pairs, ab, blocks, mass, inertia, dt, p.data(), ap.data(), diag.data());
+    double pap = 0.0;
+    for (long long i = 0; i < m; ++i) pap += p[i] * ap[i];
+    if (!(pap > 0.0)) {
+      if (k == 0 && pap < 0.0)
+        for (long long i = 0; i < m; ++i) x[i] += rz / -pap * p[i];
+      *breakdown = 1;
+      return k;
+    }
+    const double alpha = rz / pap;
+    double rz1 = 0.0, rr = 0.0;
+    for (long long i = 0; i < m; ++i) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * ap[i];
+      z[i] = r[i] / cg_precond(diag[i], cg_mdt(mass, inertia, dt, i));
+      rz1 += r[i] * z[i];
+      rr += r[i] * r[i];
+    }
+    if (rr <= rel_tol * rel_tol * rr0) return k + 1;
+    const double beta = rz1 / rz;
+    for (long long i = 0; i < m; ++i) p[i] = z[i] + beta * p[i];
+    rz = rz1;
+  }
+  return max_iter;
+}

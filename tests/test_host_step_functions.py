@@ -226,3 +226,72 @@ def test_broad_phase_functions_with_size_disparity(hs, imp):
         pairs, eps = _broad(hs, s.poses, bound, s.radius, shuffle)
         assert np.array_equal(pairs, ref)
         assert np.array_equal(eps, imp.pair_eps(s.radius, ref[:, 0], ref[:, 1]))
+
+
+def _cg_system(rng, n, n_edges, spd=True):
+    pairs = np.array(sorted({tuple(sorted(rng.choice(n, 2, replace=False))) for _ in range(n_edges)}),
+                     np.int32)
+    Q = rng.normal(size=(len(pairs), 12, 12))
+    blocks = Q @ Q.transpose(0, 2, 1) if spd else -50.0 * np.repeat(np.eye(12)[None], len(pairs), 0)
+    mass, inertia = rng.uniform(0.5, 2.0, n), rng.uniform(0.1, 1.0, n)
+    return pairs, np.ascontiguousarray(blocks), mass, inertia
+
+
+def _dense(n, pairs, blocks, mass, inertia, dt):
+    Md = np.concatenate([np.repeat(mass[:, None], 3, 1), np.repeat(inertia[:, None], 3, 1)], 1).ravel()
+    A = np.diag(Md / dt)
+    for p, (a, b) in enumerate(pairs):
+        idx = np.r_[6 * a:6 * a + 6, 6 * b:6 * b + 6]
+        A[np.ix_(idx, idx)] += dt * blocks[p]
+    return A, Md
+
+
+def test_cg_functions_assemble_the_newton_matrix(hs):
+    """The solve's per-element functions apply M/dt + dt K (pair blocks in
+    row-major 12x12, A's twist first) and its diagonal exactly as the
+    assembled dense matrix; the serial sequence of the solve's kernels
+    reaches its solution, and stops at negative curvature with the flagged
+    step."""
+    hs.hs_cg_matvec.argtypes = [C.c_int, C.c_longlong, C.POINTER(C.c_int), DP, DP, DP, C.c_double,
+                                DP, DP, DP]
+    hs.hs_cg_solve.restype = C.c_int
+    hs.hs_cg_solve.argtypes = [C.c_int, C.c_longlong, C.POINTER(C.c_int), DP, DP, DP, C.c_double, DP,
+                               DP, C.c_int, C.c_double, C.POINTER(C.c_int)]
+    rng = np.random.default_rng(12)
+    n, dt = 40, 0.05
+    pairs, blocks, mass, inertia = _cg_system(rng, n, 90)
+    A, Md = _dense(n, pairs, blocks, mass, inertia, dt)
+    ip = lambda a: np.ascontiguousarray(a, np.int32).ctypes.data_as(C.POINTER(C.c_int))  # noqa: E731
+    p = rng.normal(size=6 * n)
+    ap, diag = np.zeros(6 * n), np.zeros(6 * n)
+    hs.hs_cg_matvec(n, len(pairs), ip(pairs), blocks.ctypes.data_as(DP), _d(mass).ctypes.data_as(DP),
+                    _d(inertia).ctypes.data_as(DP), dt, p.ctypes.data_as(DP), ap.ctypes.data_as(DP),
+                    diag.ctypes.data_as(DP))
+    assert np.abs(ap - A @ p).max() <= 1e-12 * np.abs(A @ p).max()
+    assert np.abs(diag - np.diag(A)).max() <= 1e-12 * np.abs(np.diag(A)).max()
+    b = rng.normal(size=6 * n)
+    x = np.zeros(6 * n)
+    brk = C.c_int()
+    it = hs.hs_cg_solve(n, len(pairs), ip(pairs), blocks.ctypes.data_as(DP), _d(mass).ctypes.data_as(DP),
+                        _d(inertia).ctypes.data_as(DP), dt, b.ctypes.data_as(DP), x.ctypes.data_as(DP),
+                        400, 1e-13, C.byref(brk))
+    assert brk.value == 0 and 0 < it < 400
+    want = np.linalg.solve(A, b)
+    assert np.abs(x - want).max() <= 1e-10 * np.abs(want).max()
+    # negative curvature along the first direction
+    n = 6
+    pairs = np.array([[0, 1], [2, 3], [4, 5]], np.int32)
+    blocks = np.ascontiguousarray(-50.0 * np.repeat(np.eye(12)[None], 3, 0))
+    mass, inertia = rng.uniform(0.5, 2.0, n), rng.uniform(0.1, 1.0, n)
+    dt = 0.5
+    A, Md = _dense(n, pairs, blocks, mass, inertia, dt)
+    b = rng.normal(size=6 * n)
+    x = np.zeros(6 * n)
+    it = hs.hs_cg_solve(n, 3, ip(pairs), blocks.ctypes.data_as(DP), _d(mass).ctypes.data_as(DP),
+                        _d(inertia).ctypes.data_as(DP), dt, b.ctypes.data_as(DP), x.ctypes.data_as(DP),
+                        10, 1e-10, C.byref(brk))
+    d = np.where(np.diag(A) > 0, np.diag(A), Md / dt)
+    z = b / d
+    pap = z @ A @ z
+    assert pap < 0 and it == 0 and brk.value == 1
+    assert np.abs(x - (b @ z) / -pap * z).max() <= 1e-12 * np.abs(x).max()
