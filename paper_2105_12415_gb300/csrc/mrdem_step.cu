@@ -226,15 +226,6 @@ __global__ void __launch_bounds__(kThreads) k_picard(int32_t n, const double* ve
   }
 }
 
-// Rotation matrix (row-major) of a pose's quaternion w, x, y, z (any norm).
-__device__ __forceinline__ void quat_matrix(const double* q, double R[9]) {
-  const double w = q[0], x = q[1], y = q[2], z = q[3];
-  const double s = 2.0 / (w * w + x * x + y * y + z * z);
-  R[0] = 1.0 - s * (y * y + z * z); R[1] = s * (x * y - w * z);       R[2] = s * (x * z + w * y);
-  R[3] = s * (x * y + w * z);       R[4] = 1.0 - s * (x * x + z * z); R[5] = s * (y * z - w * x);
-  R[6] = s * (x * z - w * y);       R[7] = s * (y * z + w * x);       R[8] = 1.0 - s * (x * x + y * y);
-}
-
 // World FP64 corners of fine triangle `tri` of particle i.
 __device__ __forceinline__ bool world_triangle(const HierDev& H, const double* poses, int i,
                                                int tri, V3<double> T[3], V3<double>* t) {
@@ -246,10 +237,7 @@ __device__ __forceinline__ bool world_triangle(const HierDev& H, const double* p
   double R[9];
   quat_matrix(p + 3, R);
   *t = {p[0], p[1], p[2]};
-  for (int k = 0; k < 3; ++k)
-    T[k] = {R[0] * V[k].x + R[1] * V[k].y + R[2] * V[k].z + p[0],
-            R[3] * V[k].x + R[4] * V[k].y + R[5] * V[k].z + p[1],
-            R[6] * V[k].x + R[7] * V[k].y + R[8] * V[k].z + p[2]};
+  for (int k = 0; k < 3; ++k) T[k] = pose_point(R, p, V[k]);
   return true;
 }
 

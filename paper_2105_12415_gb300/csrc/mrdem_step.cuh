@@ -238,6 +238,21 @@ MRDEM_HD void quat_mul(const double a[4], const double b[4], double out[4]) {
   out[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
 }
 
+// Rotation matrix (row-major) of quaternion q = (w, x, y, z) of any norm.
+MRDEM_HD void quat_matrix(const double* q, double R[9]) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  const double s = 2.0 / (w * w + x * x + y * y + z * z);
+  R[0] = 1.0 - s * (y * y + z * z); R[1] = s * (x * y - w * z);       R[2] = s * (x * z + w * y);
+  R[3] = s * (x * y + w * z);       R[4] = 1.0 - s * (x * x + z * z); R[5] = s * (y * z - w * x);
+  R[6] = s * (x * z - w * y);       R[7] = s * (y * z + w * x);       R[8] = 1.0 - s * (x * x + y * y);
+}
+
+// World position R v + t of body-frame point v under pose (t, q).
+MRDEM_HD V3<double> pose_point(const double R[9], const double* t, const V3<double>& v) {
+  return {R[0] * v.x + R[1] * v.y + R[2] * v.z + t[0], R[3] * v.x + R[4] * v.y + R[5] * v.z + t[1],
+          R[6] * v.x + R[7] * v.y + R[8] * v.z + t[2]};
+}
+
 // Pose after a step dt with velocity (v, omega): centre c + dt v, orientation
 // turned by the rotation vector dt omega in the world frame (left
 // multiplication), renormalised.

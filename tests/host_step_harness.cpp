@@ -227,3 +227,14 @@ extern "C" int hs_cg_solve(int n, long long n_pairs, const int* ab, const double
   }
   return max_iter;
 }
+
+extern "C" void hs_pose_points(const double* pose, int n, const double* v, double* out) {
+  double R[9];
+  quat_matrix(pose + 3, R);
+  for (int i = 0; i < n; ++i) {
+    const V3<double> w = pose_point(R, pose, V3<double>{v[3 * i], v[3 * i + 1], v[3 * i + 2]});
+    out[3 * i] = w.x;
+    out[3 * i + 1] = w.y;
+    out[3 * i + 2] = w.z;
+  }
+}

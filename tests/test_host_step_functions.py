@@ -295,3 +295,19 @@ def test_cg_functions_assemble_the_newton_matrix(hs):
     pap = z @ A @ z
     assert pap < 0 and it == 0 and brk.value == 1
     assert np.abs(x - (b @ z) / -pap * z).max() <= 1e-12 * np.abs(x).max()
+
+
+def test_pose_point_function_equals_oracle(hs, orc):
+    """World points R v + t of the kernels that build world triangles
+    (Hessian blocks, candidate refinement) against the oracle's pose matrix,
+    for unit and unnormalised quaternions."""
+    hs.hs_pose_points.argtypes = [DP, C.c_int, DP, DP]
+    rng = np.random.default_rng(15)
+    v = rng.normal(size=(50, 3))
+    for _ in range(20):
+        pose = np.concatenate([rng.normal(size=3) * 10, rng.normal(size=4) * rng.uniform(0.5, 2)])
+        out = np.zeros((50, 3))
+        hs.hs_pose_points(_d(pose).ctypes.data_as(DP), 50, _d(v).ctypes.data_as(DP),
+                          out.ctypes.data_as(DP))
+        want = v @ orc.pose_matrix(pose).T + pose[:3]
+        assert np.abs(out - want).max() <= 1e-13 * (1 + np.abs(want).max())
