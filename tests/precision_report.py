@@ -82,6 +82,55 @@ def _force_errors(ft, e, ft_ref, e_ref, ref, scene):
             "energy": abs(e - e_ref) / max(e_ref, 1e-300)}
 
 
+def _implicit_rows(m, ctx, orc):
+    """The implicit step on the four-particle chain against the oracle's
+    Picard fixed point: broad phase (exact equality), Picard and Newton steps
+    in both forms (largest velocity error relative to the largest velocity),
+    and the contact Hessian blocks (relative to the largest entry)."""
+    import dataclasses
+
+    import torch
+
+    import oracle.implicit as imp
+    from gen import scene_chain
+    dev = torch.device("cuda:0")
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    s = scene_chain(4, seed=41)
+    bound = imp.bounding_radius(s)
+    pairs = imp.broad_phase(s.poses[:, :3], bound, s.radius)
+    eps = imp.pair_eps(s.radius, pairs[:, 0], pairs[:, 1])
+    vel = np.random.default_rng(2).normal(scale=0.1, size=(s.n_particles, 6))
+    dt = 2e-4
+    P, V, it, _ = imp.implicit_euler_step(s, vel, pairs, eps, dt, tol=2e-13, max_iter=2000)
+    hier = m.Hierarchy.from_scene(ctx, s)
+    inertia = 0.4 * s.mass * s.radius ** 2
+    gp, _ = m.broad_phase(ctx, t(s.poses), t(bound), t(s.radius))
+    rows = [{"workload": "chain: broad phase", "form": "fp64",
+             "error": 0.0 if np.array_equal(gp.cpu().numpy(), pairs) else float("inf")}]
+    args = (t(s.poses), t(vel), t(s.mass), t(inertia), t(pairs, torch.int32), t(eps), dt)
+    for form, tol in (("fp64", 1e-11), ("fp32", 1e-5)):
+        _, Vp, itp, _ = m.implicit_euler_step(ctx, hier, *args, precision=form, tol=tol)
+        _, Vn, itn, _ = m.implicit_euler_step_newton(ctx, hier, *args, precision=form, tol=tol)
+        scale = np.abs(V).max()
+        rows.append({"workload": f"chain: Picard step ({itp} iterations, oracle {it})", "form": form,
+                     "error": float(np.abs(Vp.cpu().numpy() - V).max() / scale)})
+        rows.append({"workload": f"chain: Newton step ({itn} iterations)", "form": form,
+                     "error": float(np.abs(Vn.cpu().numpy() - V).max() / scale)})
+    base = dataclasses.replace(s, pairs=pairs, eps=eps, com=np.zeros((s.n_particles, 3)))
+    c = orc.detect(base)
+    Href = imp.contact_hessian(base, c)
+    tp = t(pairs, torch.int32)
+    cont, _ = m.detect(ctx, hier, tp, t(eps), t(s.poses), "fp64")
+    blocks, _ = m.contact_hessian(ctx, hier, tp, t(eps), t(s.poses), cont, t(s.mass))
+    H = np.zeros_like(Href)
+    for p, (a, b) in enumerate(pairs):
+        idx = np.r_[6 * a:6 * a + 6, 6 * b:6 * b + 6]
+        H[np.ix_(idx, idx)] += blocks[p].cpu().numpy()
+    rows.append({"workload": "chain: contact Hessian blocks", "form": "fp64",
+                 "error": float(np.abs(H - Href).max() / np.abs(Href).max())})
+    return rows
+
+
 def main(out_path=None):
     import torch
 
@@ -123,6 +172,11 @@ def main(out_path=None):
     for r in rows:
         lines.append("| " + " | ".join(fmt(r.get(k, "")) for k in cols) + " |")
     text = "\n".join(lines) + "\n"
+    irows = _implicit_rows(m, ctx, oracle)
+    text += "\nImplicit step (row f1), largest error relative to the largest value:\n\n"
+    text += "| quantity | form | error |\n|---|---|---|\n"
+    for r in irows:
+        text += f"| {r['workload']} | {r['form']} | {r['error']:.2e} |\n"
     print(text)
     if out_path:
         how = __doc__[__doc__.index("Outputs and how"):].strip()
