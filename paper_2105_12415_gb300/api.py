@@ -664,7 +664,7 @@ def newton_solve(ctx, pairs, blocks, mass, inertia, dt, rhs, x=None, max_iter=20
 def implicit_euler_step_newton(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inertia, pairs,
                                eps, dt, gravity=G_DEFAULT, k_s=1000.0, precision="fp32",
                                tol=1e-13, max_iter=50, cg_iter=200, cg_tol=1e-12, contacts=None,
-                               cache_margin=None, bound=None):
+                               cache_margin=None, bound=None, stiffness="hessian"):
     """One implicit Euler step by Newton's method in the velocities, on the
     same equations as the Picard iteration: residual
     r = M (V - V0)/dt - (F, tau)(moved geometry) - (m g, 0), Jacobian
@@ -672,7 +672,11 @@ def implicit_euler_step_newton(ctx: Context, hier: Hierarchy, poses0, vel0, mass
     linear system solved by conjugate gradients, each step halved until
     max |r| drops (backtracking).  Stops when max |r| <= tol max |M V|/dt.
     With cache_margin = w (and bound) the residuals take their contacts from
-    candidates kept across the step (KeptCandidates).
+    candidates kept across the step (KeptCandidates).  stiffness="gauss-newton"
+    uses the adjoint's 12x12 Gauss-Newton blocks e''(d) J J^T (closest points
+    frozen; positive semi-definite, so the solve never meets negative
+    curvature, but the iteration converges only linearly) instead of the
+    contact Hessian.
     Returns (poses, vel, iterations, stats: CG iterations and line-search
     halvings per Newton iteration)."""
     lib = L.load()
@@ -714,7 +718,11 @@ def implicit_euler_step_newton(ctx: Context, hier: Hierarchy, poses0, vel0, mass
     for it in range(1, max_iter + 1):
         if rn <= tol * (sc + 1e-300):
             break
-        if P:
+        if P and stiffness == "gauss-newton":
+            _, _, jac = contact_grad(ctx, hier, pairs, eps, poses, state["contacts"], mass, k_s,
+                                     want_verts=False, want_pose=False, want_jac=True)
+            blocks.copy_(jac)
+        elif P:
             blocks.zero_()
             contact_hessian(ctx, hier, pairs, eps, poses, state["contacts"], mass, k_s,
                             blocks=blocks)

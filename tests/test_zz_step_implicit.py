@@ -550,3 +550,20 @@ def test_newton_with_kept_candidates(m, ctx, imp):
                                                  cache_margin=0.25 * eps.min(), bound=_t(bound))
     assert abs(it1 - it2) <= 1
     assert (V1 - V2).abs().max().item() <= 1e-10 * V1.abs().max().item()
+
+
+def test_newton_with_gauss_newton_blocks(m, ctx, imp):
+    """Newton's method with the adjoint's Gauss-Newton blocks (closest points
+    frozen) as stiffness reaches the same fixed point as with the contact
+    Hessian, in more iterations (it converges linearly)."""
+    s, bound, pairs, eps, vel = _chain_problem(imp)
+    dt = 2e-4
+    inertia = 0.4 * s.mass * s.radius ** 2
+    hier = m.Hierarchy.from_scene(ctx, s)
+    args = (_t(s.poses), _t(vel), _t(s.mass), _t(inertia), _t(pairs, "int32"), _t(eps), dt)
+    _, V1, it1, _ = m.implicit_euler_step_newton(ctx, hier, *args, precision="fp64", tol=1e-12)
+    _, V2, it2, st2 = m.implicit_euler_step_newton(ctx, hier, *args, precision="fp64", tol=1e-12,
+                                                   max_iter=200, stiffness="gauss-newton")
+    assert it2 < 200 and it2 >= it1
+    assert not any(st["cg_breakdown"] for st in st2)
+    assert (V1 - V2).abs().max().item() <= 1e-10 * V1.abs().max().item()
