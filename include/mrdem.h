@@ -101,7 +101,7 @@ typedef struct mrdem_params {
   int32_t kmeans_iters;
   int64_t cap_level;      /* capacity (items) of each per-level work list */
   int64_t cap_tiles;      /* capacity of the leaf-pair tile list */
-  int64_t cap_candidates; /* capacity of the fine candidate list */
+  int64_t cap_candidates; /* capacity of the fine candidate list (< 2^27) */
   int32_t tile_warps;     /* warps per block of the finest-level kernel (autotuned) */
   int32_t tile_blocks_per_sm;
   int32_t level_warps;

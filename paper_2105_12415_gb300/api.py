@@ -678,7 +678,11 @@ def implicit_euler_step_newton(ctx: Context, hier: Hierarchy, poses0, vel0, mass
     curvature, but the iteration converges only linearly) instead of the
     contact Hessian.
     Returns (poses, vel, iterations, stats: CG iterations and line-search
-    halvings per Newton iteration)."""
+    halvings per Newton iteration).  A step that no halving makes descend
+    (30 halvings without a lower max |r|) is not taken: the iteration stops
+    at the previous V and that iteration's stats say line_search_failed."""
+    if stiffness not in ("hessian", "gauss-newton"):
+        raise ValueError(f"stiffness must be 'hessian' or 'gauss-newton', not {stiffness!r}")
     lib = L.load()
     n = poses0.shape[0]
     dev = poses0.device
@@ -729,19 +733,27 @@ def implicit_euler_step_newton(ctx: Context, hier: Hierarchy, poses0, vel0, mass
         newton_solve(ctx, pairs, blocks, mass, inertia, dt, res, x, cg_iter, cg_tol, info,
                      check_every=16)
         cg = info.tolist()
-        lam, halvings = 1.0, 0
+        lam, halvings, descended = 1.0, 0, False
         while True:
             L.check(lib.mrdem_vel_axpy(ctx.handle, 6 * n, -lam, _p(x), _p(V), _p(Vt), None),
                     "mrdem_vel_axpy")
             rt, st = residual(Vt)
-            if rt < rn or lam < 2.0 ** -30:
+            if rt < rn:
+                descended = True
+                break
+            if lam < 2.0 ** -30:
                 break
             lam *= 0.5
             halvings += 1
+        stats.append({"cg_iterations": int(cg[0]), "cg_residual": cg[1], "cg_breakdown": cg[2] != 0,
+                      "halvings": halvings, "line_search_failed": not descended})
+        if not descended:
+            # keep V; the contacts of the last trial are stale, so the
+            # residual is evaluated at V once more before returning
+            residual(V)
+            break
         V, Vt = Vt, V
         rn, sc = rt, st
-        stats.append({"cg_iterations": int(cg[0]), "cg_residual": cg[1], "cg_breakdown": cg[2] != 0,
-                      "halvings": halvings})
     move_poses(ctx, poses0, V, dt, out=poses)
     return poses, V, it, stats
 

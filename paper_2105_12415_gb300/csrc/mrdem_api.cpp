@@ -14,12 +14,16 @@ using namespace mrdem;
 
 namespace {
 
+// The FP32 exact pass packs a candidate's index and a sub-test number (4
+// bits) into one int32 work item.
+constexpr int64_t kMaxCandidates = (int64_t)1 << 27;
+
 bool params_ok(const mrdem_params& p) {
   return p.n_iter >= 1 && p.n_iter <= 64 && p.rho_reg > 0.f && p.rho_iter > 0.f && p.conv_c > 0.f &&
          p.fanout >= 2 && p.fanout <= 8 && p.leaf_max >= 1 && p.leaf_max <= 32 && p.leaf_min >= 1 &&
          p.kmeans_iters >= 0 && p.cap_level > 0 && p.cap_tiles > 0 && p.cap_candidates > 0 &&
          p.cap_level < (int64_t)1 << 31 && p.cap_tiles < (int64_t)1 << 31 &&
-         p.cap_candidates < (int64_t)1 << 31 && p.cap_sweep > 0 && p.cap_sweep < (int64_t)1 << 31 &&
+         p.cap_candidates < kMaxCandidates && p.cap_sweep > 0 && p.cap_sweep < (int64_t)1 << 31 &&
          p.tile_warps >= 1 && p.tile_warps <= 8 &&
          p.tile_blocks_per_sm >= 1 && p.tile_blocks_per_sm <= 64 && p.level_warps >= 1 &&
          p.level_warps <= 32 && p.exact_threads >= 32 && p.exact_threads <= 1024 &&
@@ -216,7 +220,7 @@ int mrdem_reserve(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca, int64_t sw) 
   ti = ti ? ti : c->cap_tiles;
   ca = ca ? ca : c->cap_cands;
   sw = sw ? sw : c->cap_sweep;
-  if (lv >= (int64_t)1 << 31 || ti >= (int64_t)1 << 31 || ca >= (int64_t)1 << 31 ||
+  if (lv >= (int64_t)1 << 31 || ti >= (int64_t)1 << 31 || ca >= kMaxCandidates ||
       sw >= (int64_t)1 << 31)
     return MRDEM_ERR_INVALID;
   if (cudaDeviceSynchronize() != cudaSuccess) return MRDEM_ERR_CUDA;

@@ -27,9 +27,11 @@
 namespace mrdem {
 
 // Reserve `n` consecutive slots per lane in a list; returns this lane's
-// first slot (or -1 on overflow, latched in *req).
-__device__ __forceinline__ int64_t warp_reserve(int n, unsigned long long* counter, int64_t cap,
-                                                unsigned long long* req) {
+// first slot, or -1 on overflow (latched in *req); the slots of a range that
+// crosses the capacity that do lie below it get the empty item -1, so that
+// every slot the readers see is written.
+__device__ __forceinline__ int64_t warp_reserve(int n, int* list, unsigned long long* counter,
+                                                int64_t cap, unsigned long long* req) {
   int incl = warp_scan(n);
   int total = __shfl_sync(0xffffffffu, incl, 31);
   unsigned long long base = 0;
@@ -38,6 +40,7 @@ __device__ __forceinline__ int64_t warp_reserve(int n, unsigned long long* count
   int64_t first = (int64_t)base + incl - n;
   if (n && first + n > cap) {
     atomicMax(req, (unsigned long long)(first + n));
+    for (int64_t q = first; q < cap; ++q) list[q] = -1;
     return -1;
   }
   return first;
@@ -99,10 +102,21 @@ __global__ void __launch_bounds__(128) k_cp_float(HierDev H, const PairXf* __res
     int npt = accept ? __popc(mask & 0x3fu) : 0;
     int nee = accept ? __popc(mask >> 6) : 0;
     int ncx = accept && full ? 6 : 0;
-    int64_t pt0 = warp_reserve(npt, cnt + CNT_PT, cap_items, status + ST_REQ_CANDS);
-    int64_t ee0 = warp_reserve(nee, cnt + CNT_EE, cap_items, status + ST_REQ_CANDS);
-    int64_t cx0 = warp_reserve(ncx, cnt + CNT_CX, cap_items, status + ST_REQ_CANDS);
-    if (accept && (pt0 < 0 || ee0 < 0 || cx0 < 0)) accept = false;
+    int64_t pt0 = warp_reserve(npt, items_pt, cnt + CNT_PT, cap_items, status + ST_REQ_CANDS);
+    int64_t ee0 = warp_reserve(nee, items_ee, cnt + CNT_EE, cap_items, status + ST_REQ_CANDS);
+    int64_t cx0 = warp_reserve(ncx, items_cx, cnt + CNT_CX, cap_items, status + ST_REQ_CANDS);
+    // Every slot below a list's capacity that a lane reserved is written,
+    // since the next kernels read each of them: when one of the three lists
+    // overflows (latched above; the call reports ERR_CAPACITY), the record
+    // keeps no items and the slots reserved in the other lists get the
+    // empty item -1.
+    const bool items_ok = pt0 >= 0 && ee0 >= 0 && cx0 >= 0;
+    if (accept && !items_ok) {
+      if (pt0 >= 0) for (int q = 0; q < npt; ++q) items_pt[pt0 + q] = -1;
+      if (ee0 >= 0) for (int q = 0; q < nee; ++q) items_ee[ee0 + q] = -1;
+      if (cx0 >= 0) for (int q = 0; q < ncx; ++q) items_cx[cx0 + q] = -1;
+      npt = nee = ncx = 0;
+    }
     n_pt += accept ? (unsigned)npt : 0u;
     n_ee += accept ? (unsigned)nee : 0u;
     if (accept) {
@@ -110,14 +124,16 @@ __global__ void __launch_bounds__(128) k_cp_float(HierDev H, const PairXf* __res
       cand_dd(H, xfdd[e.x], e, 2.0 * xf64[e.x].eps, L, g);
       store_acc(acc + ai, g, (int)k, e.x, (int)pt0, (int)ee0, (int)cx0,
                 npt | (nee << 8) | (ncx << 16));
-      int ip = (int)pt0, ie = (int)ee0;
-      for (int f = 0; f < 15; ++f) {
-        if (!((mask >> f) & 1u)) continue;
-        int item = (int)(ai << 4) | f;
-        if (f < 6) items_pt[ip++] = item;
-        else items_ee[ie++] = item;
+      if (items_ok) {
+        int ip = (int)pt0, ie = (int)ee0;
+        for (int f = 0; f < 15; ++f) {
+          if (!((mask >> f) & 1u)) continue;
+          int item = (int)(ai << 4) | f;
+          if (f < 6) items_pt[ip++] = item;
+          else items_ee[ie++] = item;
+        }
+        for (int f = 0; f < ncx; ++f) items_cx[cx0 + f] = (int)(ai << 4) | f;
       }
-      for (int f = 0; f < ncx; ++f) items_cx[cx0 + f] = (int)(ai << 4) | f;
     }
   }
   n_pt = __reduce_add_sync(0xffffffffu, n_pt);
@@ -143,6 +159,7 @@ __global__ void __launch_bounds__(256) k_cp_items(const AccRec* __restrict__ acc
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
     int it = items[k];
+    if (it < 0) continue;  // an empty slot left by an overflow
     V3<dd> P[3], Q[3];
     load_cand_tris(acc + (it >> 4), P, Q);
     const int f = it & 15;

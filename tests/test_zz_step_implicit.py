@@ -107,7 +107,7 @@ def test_broad_phase_edge_cases(m, ctx, imp):
     assert np.array_equal(pairs.cpu().numpy(), ref)
 
 
-def test_broad_phase_rejects_nonfinite(m, ctx):
+def test_broad_phase_rejects_nonfinite(m, ctx, imp):
     P = np.zeros((4, 7))
     P[:, 3] = 1.0
     P[:, 0] = np.arange(4)
@@ -117,7 +117,10 @@ def test_broad_phase_rejects_nonfinite(m, ctx):
     # the context stays usable
     P[2, 1] = 0.0
     pairs, _ = m.broad_phase(ctx, _t(P), _t(np.ones(4)), _t(np.ones(4)))
-    assert pairs.shape[0] == 6
+    # unit spheres at x = 0..3: five pairs lie within 2 + 2 eps, (0, 3) does not
+    ref = imp.broad_phase(P[:, :3], np.ones(4), np.ones(4))
+    assert len(ref) == 5
+    assert np.array_equal(pairs.cpu().numpy(), ref)
 
 
 def test_move_poses_equals_oracle(m, ctx, imp):

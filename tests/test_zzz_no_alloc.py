@@ -5,8 +5,11 @@ start-up, or a real-time loop that must not call cudaMalloc after
 initialisation) use this call instead of mrdem_detect: its work lists live in
 a fixed array inside the library.  The test calls it through the C ABI twice
 in a row and checks both results against mrdem_detect, with the tolerance of
-the other GPU tests.  It builds everything it needs, so it also passes alone
-in a fresh process (its first call then does the one-time set-up).
+the other GPU tests, and against the FP64 oracle directly, in both
+precisions on the one-pair scene (the FP32 form finishes in its own kernel,
+k_exact32).  It builds everything it needs, so it also passes alone in a
+fresh process (its first call then does the one-time set-up).  The file is
+named so that pytest collects it after every other test file.
 """
 import ctypes as C
 
@@ -27,8 +30,9 @@ def _noalloc(m, hier, t, contacts, stats, precision):
     return st
 
 
-@pytest.mark.parametrize("scene_fn,precision", [(scene_c1, 1), (lambda: scene_tiny(n_pairs=16, levels=(1, 2)), 0)])
-def test_noalloc_matches_detect_twice(scene_fn, precision):
+@pytest.mark.parametrize("scene_fn,precision", [(scene_c1, 1), (scene_c1, 0),
+                                                (lambda: scene_tiny(n_pairs=16, levels=(1, 2)), 0)])
+def test_noalloc_matches_detect_twice(orc, scene_fn, precision):
     import torch
     import paper_2105_12415_gb300 as m
     m.build()
@@ -41,6 +45,7 @@ def test_noalloc_matches_detect_twice(scene_fn, precision):
     ref, _ = m.detect(ctx, hier, t["pairs"], t["eps"], t["poses"], pname)
     ref = ref.to_numpy()
     assert len(ref["d"]) > 0
+    oref = orc.detect(s)
     for _ in range(2):  # the array keeps the previous call's contents
         contacts = m.Contacts(4 * len(ref["d"]) + 64, dev)
         stats = torch.full((m._lib.MRDEM_STAT_COUNT,), -1, dtype=torch.int64, device=dev)
@@ -52,6 +57,7 @@ def test_noalloc_matches_detect_twice(scene_fn, precision):
         got = contacts.to_numpy()
         assert len(got["d"]) == len(ref["d"]) == st[m._lib.MRDEM_STAT_CONTACTS]
         compare_contacts(got, ref, s, pname)
+        compare_contacts(got, oref, s, pname)
 
 
 def test_noalloc_rejects_too_many_pairs():
