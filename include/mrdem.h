@@ -102,11 +102,16 @@ typedef struct mrdem_params {
   int64_t cap_level;      /* capacity (items) of each per-level work list */
   int64_t cap_tiles;      /* capacity of the leaf-pair tile list */
   int64_t cap_candidates; /* capacity of the fine candidate list (< 2^27) */
-  int32_t tile_warps;     /* warps per block of the finest-level kernel (autotuned) */
-  int32_t tile_blocks_per_sm;
-  int32_t level_warps;
-  int32_t exact_threads;
+  /* Launch shapes of the detection kernels (mrdem_autotune picks them per
+   * device and workload size; these are the shapes used where it has not
+   * run).  Each must be one of the listed values. */
+  int32_t tile_warps;     /* k_tile, one warp per leaf-pair tile: warps per block (2, 4, 8) */
+  int32_t sweep_warps;    /* k_sweep_fine: warps per block (2, 4, 8) */
+  int32_t level_warps;    /* k_expand: warps per block (2, 4, 8) */
+  int32_t exact_threads;  /* exact-distance kernels: threads per block (64, 128, 256) */
   int64_t cap_sweep;      /* capacity of the list of pairs waiting for the penalty sweep */
+  int32_t expand_items;   /* k_expand: level items a warp takes per pass, at most (8, 16, 32) */
+  int32_t node_threads;   /* k_sweep_nodes: threads per block (128, 256) */
 } mrdem_params;
 
 /* Contact output.  All arrays are caller-owned device memory of `capacity`
@@ -180,6 +185,25 @@ int mrdem_hier_upload(mrdem_ctx* ctx, mrdem_hier* hier);
 int mrdem_build_hierarchy(mrdem_ctx* ctx, int32_t n_particles, const int64_t* vert_off,
                           const float* verts, const int64_t* tri_off, const int32_t* tris,
                           mrdem_hier** out);
+
+/* Build the surrogate trees on the GPU (Sec. 4, Algorithm 7, Appendix A) and
+ * keep them on ctx's device: the same tree shape as the host builder (node
+ * sizes follow from the counts), clusters from the recursive median split
+ * along the principal axis of the triangle centroids (the host builder's
+ * k-means seeding; its Lloyd refinement, kmeans_iters, is not run), one
+ * surrogate per node fitted on the device, its slack delta the largest FP64
+ * distance from a fine vertex below the node to the stored float triangle,
+ * rounded up (so every node is conservative), and the oriented boxes.
+ * Inputs: vert_off [n+1] and tri_off [n+1] host int64 offsets; verts
+ * (device float32 [vert_off[n]*3], body frame) and tris (device int32
+ * [tri_off[n]*3], local vertex indices) stay owned by the caller.
+ * Synchronous.  build_ms: NULL or host double, the device part's time.
+ * *out also holds the host copy (mrdem_hier_export works).  Errors: INVALID
+ * (offsets, index out of range, non-finite or degenerate input, degenerate
+ * fitted surrogate), OOM, CUDA. */
+int mrdem_build_hierarchy_device(mrdem_ctx* ctx, int32_t n_particles, const int64_t* vert_off,
+                                 const float* verts, const int64_t* tri_off, const int32_t* tris,
+                                 mrdem_hier** out, double* build_ms);
 int mrdem_hier_destroy(mrdem_hier* hier);
 int mrdem_hier_get_info(const mrdem_hier* hier, mrdem_hier_info* out);
 /* Copy the host arrays of a hierarchy into caller host buffers (any may be
@@ -224,6 +248,27 @@ int mrdem_hier_export_boxes(const mrdem_hier* hier, float* node_box);
 int mrdem_detect(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
                  const double* pair_eps, const double* poses, int32_t precision,
                  const mrdem_contacts* out, int64_t* stats, mrdem_stream stream);
+
+/* Launch-shape autotuner for mrdem_detect (no counterpart in the paper: it
+ * picks block sizes and items per warp for this GPU).  Runs the detection of
+ * the given batch (same arguments as mrdem_detect; n_pairs >= 1) under nine
+ * candidate shapes, reps + 1 times each, times every kernel with CUDA
+ * events, and stores for the batch's size class (n_pairs < 256, < 4096,
+ * < 65536, larger) the fastest value of each shape parameter: k_expand warps
+ * per block and items per warp, k_sweep_nodes threads, k_tile warps,
+ * k_sweep_fine warps, exact-pass threads.  Later mrdem_detect and
+ * mrdem_detect_noalloc calls of that size class use them; mrdem_set_params
+ * clears the table.  Synchronises the device (do not call during stream
+ * capture).  The results of every shape are the same contact set; *out holds
+ * the last run's.  chosen: NULL or host int32 [6] (the six values in that
+ * order); ms: NULL or host double [2], the time of one detection with the
+ * params' shapes and with the chosen ones.  Errors: INVALID, CUDA, CAPACITY
+ * or NONFINITE when a run overflowed a list or met a bad input (status left
+ * latched for mrdem_check; grow the lists and call again). */
+int mrdem_autotune(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
+                   const int32_t* pair_ab, const double* pair_eps, const double* poses,
+                   int32_t precision, const mrdem_contacts* out, int32_t reps, int32_t* chosen,
+                   double* ms);
 
 /* Synchronise `stream` and report the latched device-side status of ctx since
  * the last check: CAPACITY (a work list or a contact buffer overflowed; the

@@ -74,6 +74,7 @@ def _declare(L):
     L.orc_sweep.argtypes = [_I64, _P, _P, C.c_int, C.c_double, C.c_double, C.c_double, _P, _P,
                             _P, _P, _P]
     L.orc_vertex_surrogate_distance.argtypes = [_I64, _P, _P, _P]
+    L.orc_tri_pairs.argtypes = [_P, _P, _P, _P, _P, _I64, _P, _P, _P, _P, _P, C.c_int]
 
 
 def _c(a, dtype):
@@ -173,6 +174,22 @@ def detect(scene, poses=None, pairs=None, eps=None, n_threads=0, verts=None):
         if n <= cap:
             return {k: a[:n] for k, a in out.items()}
         cap = int(n)
+
+
+def tri_pairs(scene, abt, poses=None, n_threads=0):
+    """Distances of listed fine triangle pairs: abt [n, 4] = (particle A,
+    local triangle of A, particle B, local triangle of B).  The same world
+    triangles and exact distance as detect, so a listed pair gets the values
+    detect reports for it.  Returns d, pa, pb, feature."""
+    vo, v, to, t = _mesh(scene)
+    poses = _c(scene.poses if poses is None else poses, np.float64)
+    abt = _c(abt, np.int32).reshape(-1, 4)
+    n = len(abt)
+    d, pa, pb = np.empty(n), np.empty((n, 3)), np.empty((n, 3))
+    f = np.empty(n, np.int32)
+    lib().orc_tri_pairs(_ptr(vo), _ptr(v), _ptr(to), _ptr(t), _ptr(poses), n, _ptr(abt), _ptr(d),
+                        _ptr(pa), _ptr(pb), _ptr(f), n_threads)
+    return d, pa, pb, f
 
 
 def forces(scene, contacts, k_s=1000.0, poses=None):

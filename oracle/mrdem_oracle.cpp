@@ -367,6 +367,29 @@ int64_t orc_detect(const int64_t* vert_off, const double* verts, const int64_t* 
   return n;
 }
 
+// Distances of listed fine triangle pairs (particle A's triangle ta against
+// particle B's triangle tb), with the world triangles and the exact distance
+// of orc_detect: the same values orc_detect reports for a pair it lists.
+void orc_tri_pairs(const int64_t* vert_off, const double* verts, const int64_t* tri_off,
+                   const int32_t* tris, const double* poses, int64_t n, const int32_t* abt,
+                   double* d, double* pa, double* pb, int32_t* feature, int n_threads) {
+  Mesh m{vert_off, verts, tri_off, tris};
+  int threads = resolve_threads(n_threads);
+#pragma omp parallel for num_threads(threads) schedule(static)
+  for (int64_t k = 0; k < n; ++k) {
+    const int32_t* q = abt + 4 * k;  // A, ta, B, tb
+    Pose PA = make_pose(poses + 7 * q[0]), PB = make_pose(poses + 7 * q[2]);
+    V3 P[3], Q[3], a, b;
+    world_triangle(m, PA, q[0], q[1], P);
+    world_triangle(m, PB, q[2], q[3], Q);
+    int f;
+    d[k] = tri_tri(P, Q, &a, &b, &f);
+    put(pa + 3 * k, a);
+    put(pb + 3 * k, b);
+    feature[k] = f;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Penalty forces (Sec. 2, F(c)) of a contact list (as returned by orc_detect).
 // force_torque[6*i..]: world force (3) and torque about the world centre of

@@ -10,6 +10,6 @@ from .api import (  # noqa: F401
     Context, Contacts, ContactEnergy, ContactProblem, Hierarchy, contact_energy, contact_forces,
     contact_grad, detect, detect_plain_fp64, merge_contacts, triangle_distance, broad_phase,
     move_poses, picard_update, implicit_euler_step, contact_hessian, newton_residual, newton_solve,
-    implicit_euler_step_newton, refine_contacts, motion_bound, KeptCandidates,
+    implicit_euler_step_newton, refine_contacts, motion_bound, KeptCandidates, autotune,
 )
 from .buildlib import build  # noqa: F401

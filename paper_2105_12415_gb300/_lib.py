@@ -48,8 +48,9 @@ class mrdem_params(C.Structure):
         ("conv_c", C.c_float), ("fanout", C.c_int32), ("leaf_max", C.c_int32),
         ("leaf_min", C.c_int32), ("kmeans_iters", C.c_int32), ("cap_level", C.c_int64),
         ("cap_tiles", C.c_int64), ("cap_candidates", C.c_int64), ("tile_warps", C.c_int32),
-        ("tile_blocks_per_sm", C.c_int32), ("level_warps", C.c_int32),
-        ("exact_threads", C.c_int32), ("cap_sweep", C.c_int64),
+        ("sweep_warps", C.c_int32), ("level_warps", C.c_int32),
+        ("exact_threads", C.c_int32), ("cap_sweep", C.c_int64), ("expand_items", C.c_int32),
+        ("node_threads", C.c_int32),
     ]
 
 
@@ -115,6 +116,9 @@ SIGNATURES = {
                                           _P]),
     "mrdem_detect_noalloc": (C.c_int, [_P, _I64, _P, _P, _P, _I, C.POINTER(mrdem_contacts), _P,
                                        _P]),
+    "mrdem_autotune": (C.c_int, [_P, _P, _I64, _P, _P, _P, _I, C.POINTER(mrdem_contacts), _I,
+                                 _P, _P]),
+    "mrdem_build_hierarchy_device": (C.c_int, [_P, _I, _P, _P, _P, _P, C.POINTER(_P), _P]),
     "mrdem_profile": (C.c_int, [_P, _I]),
     "mrdem_profile_read": (C.c_int, [_P, _I, C.POINTER(C.c_char_p), _P, _P, C.POINTER(_I)]),
 }

@@ -127,6 +127,33 @@ class Hierarchy:
         return cls(h, keep=ctx)
 
     @classmethod
+    def build_device(cls, ctx: Context, vert_off, verts, tri_off, tris):
+        """Trees built on ctx's GPU (mrdem_build_hierarchy_device).  verts
+        (float32 [nv, 3]) and tris (int32 [nt, 3], local indices) are device
+        tensors; the offsets are host arrays.  Returns the hierarchy; its
+        build_ms attribute is the device part's time."""
+        vo = np.ascontiguousarray(vert_off, np.int64)
+        to = np.ascontiguousarray(tri_off, np.int64)
+        _need(verts, torch.float32, (int(vo[-1]), 3), "verts")
+        _need(tris, torch.int32, (int(to[-1]), 3), "tris")
+        h = C.c_void_p()
+        ms = C.c_double()
+        L.check(L.load().mrdem_build_hierarchy_device(ctx.handle, len(vo) - 1, _np_ptr(vo), _p(verts),
+                                                     _np_ptr(to), _p(tris), C.byref(h),
+                                                     C.byref(ms)),
+                "mrdem_build_hierarchy_device")
+        out = cls(h, keep=ctx)
+        out.build_ms = ms.value
+        return out
+
+    @classmethod
+    def from_scene_device(cls, ctx: Context, scene):
+        dev = torch.device("cuda", ctx.device)
+        verts = torch.as_tensor(np.ascontiguousarray(scene.verts, np.float32), device=dev)
+        tris = torch.as_tensor(np.ascontiguousarray(scene.tris, np.int32), device=dev)
+        return cls.build_device(ctx, scene.vert_off, verts, scene.tri_off, tris)
+
+    @classmethod
     def from_scene(cls, ctx: Context | None, scene, params=None):
         if ctx is None:
             return cls.build_host(scene.vert_off, scene.verts, scene.tri_off, scene.tris, params)
@@ -248,6 +275,29 @@ def detect(ctx: Context, hier: Hierarchy, pairs, eps, poses, precision="fp32", c
         if req[3] > contacts.capacity:
             contacts.resize(int(req[3] * 1.25) + 1024)
     raise L.MrdemError(L.MRDEM_ERR_CAPACITY, "mrdem_detect (retries exhausted)")
+
+
+TUNED_FIELDS = ("level_warps", "expand_items", "node_threads", "tile_warps", "sweep_warps",
+                "exact_threads")
+
+
+def autotune(ctx: Context, hier: Hierarchy, pairs, eps, poses, precision="fp32", contacts=None,
+             reps=3):
+    """Pick the detection kernels' launch shapes for this GPU and this batch's
+    size class (mrdem_autotune); later detections of that size class use
+    them.  A checked detection runs first, so the lists are large enough.
+    Returns {"chosen": {field: value}, "ms_default": t0, "ms_tuned": t1}."""
+    contacts, _ = detect(ctx, hier, pairs, eps, poses, precision, contacts=contacts)
+    P = _pair_args(hier, pairs, eps, poses, hier.info()["n_particles"])
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    chosen = np.zeros(6, np.int32)
+    ms = np.zeros(2)
+    cs = contacts.struct()
+    L.check(L.load().mrdem_autotune(ctx.handle, hier.handle, P, _p(pairs), _p(eps), _p(poses), prec,
+                                    C.byref(cs), int(reps), _np_ptr(chosen), _np_ptr(ms)),
+            "mrdem_autotune")
+    return {"chosen": dict(zip(TUNED_FIELDS, (int(v) for v in chosen))),
+            "ms_default": float(ms[0]), "ms_tuned": float(ms[1])}
 
 
 def detect_plain_fp64(ctx, hier, pairs, eps, poses, contacts=None, stream=None):

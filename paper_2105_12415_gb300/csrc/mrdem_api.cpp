@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 
 #include "mrdem_internal.h"
@@ -18,16 +19,21 @@ namespace {
 // bits) into one int32 work item.
 constexpr int64_t kMaxCandidates = (int64_t)1 << 27;
 
+bool one_of(int32_t v, std::initializer_list<int32_t> allowed) {
+  for (int32_t a : allowed)
+    if (v == a) return true;
+  return false;
+}
+
 bool params_ok(const mrdem_params& p) {
   return p.n_iter >= 1 && p.n_iter <= 64 && p.rho_reg > 0.f && p.rho_iter > 0.f && p.conv_c > 0.f &&
          p.fanout >= 2 && p.fanout <= 8 && p.leaf_max >= 1 && p.leaf_max <= 32 && p.leaf_min >= 1 &&
          p.kmeans_iters >= 0 && p.cap_level > 0 && p.cap_tiles > 0 && p.cap_candidates > 0 &&
          p.cap_level < (int64_t)1 << 31 && p.cap_tiles < (int64_t)1 << 31 &&
          p.cap_candidates < kMaxCandidates && p.cap_sweep > 0 && p.cap_sweep < (int64_t)1 << 31 &&
-         p.tile_warps >= 1 && p.tile_warps <= 8 &&
-         p.tile_blocks_per_sm >= 1 && p.tile_blocks_per_sm <= 64 && p.level_warps >= 1 &&
-         p.level_warps <= 32 && p.exact_threads >= 32 && p.exact_threads <= 1024 &&
-         p.exact_threads % 32 == 0;
+         one_of(p.tile_warps, {2, 4, 8}) && one_of(p.sweep_warps, {2, 4, 8}) &&
+         one_of(p.level_warps, {2, 4, 8}) && one_of(p.exact_threads, {64, 128, 256}) &&
+         one_of(p.expand_items, {8, 16, 32}) && one_of(p.node_threads, {128, 256});
 }
 
 void free_lists(mrdem_ctx* c) {
@@ -115,9 +121,11 @@ void mrdem_default_params(mrdem_params* p) {
   p->cap_tiles = (int64_t)1 << 24;
   p->cap_candidates = (int64_t)1 << 20;
   p->tile_warps = 8;
-  p->tile_blocks_per_sm = 4;
+  p->sweep_warps = 4;
   p->level_warps = 8;
   p->exact_threads = 128;
+  p->expand_items = 32;
+  p->node_threads = 256;
   p->cap_sweep = (int64_t)1 << 25;
 }
 
@@ -209,7 +217,8 @@ int mrdem_set_params(mrdem_ctx* c, const mrdem_params* p) {
   n.cap_sweep = c->params.cap_sweep;
   if (!params_ok(n)) return MRDEM_ERR_INVALID;
   c->params = n;
-  for (int& o : c->occ) o = 0;  // launch shapes may have changed
+  c->n_occ = 0;  // launch shapes may have changed
+  for (bool& t : c->tuned_ok) t = false;  // tuned shapes belong to the old parameters
   return MRDEM_OK;
 }
 
@@ -419,6 +428,24 @@ int mrdem_build_hierarchy(mrdem_ctx* c, int32_t n, const int64_t* vert_off, cons
   return st;
 }
 
+int mrdem_build_hierarchy_device(mrdem_ctx* c, int32_t n, const int64_t* vert_off,
+                                 const float* verts, const int64_t* tri_off, const int32_t* tris,
+                                 mrdem_hier** out, double* build_ms) {
+  if (!c || !out) return MRDEM_ERR_INVALID;
+  *out = nullptr;
+  DeviceGuard g(c->device);
+  mrdem_hier* hh = new (std::nothrow) mrdem_hier();
+  if (!hh) return MRDEM_ERR_OOM;
+  int st = build_hierarchy_device(c->params, n, vert_off, verts, tri_off, tris, &hh->h, build_ms);
+  if (st == MRDEM_OK) st = mrdem_hier_upload(c, hh);
+  if (st != MRDEM_OK) {
+    mrdem_hier_destroy(hh);
+    return st;
+  }
+  *out = hh;
+  return MRDEM_OK;
+}
+
 int mrdem_hier_destroy(mrdem_hier* h) {
   if (!h) return MRDEM_OK;
   if (h->d_mem) {
@@ -479,6 +506,18 @@ int mrdem_detect(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32
     return MRDEM_ERR_INVALID;
   DeviceGuard g(c->device);
   return launch_detect(c, h, n_pairs, ab, eps, poses, precision, out, stats, (cudaStream_t)s);
+}
+
+int mrdem_autotune(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
+                   const double* eps, const double* poses, int32_t precision,
+                   const mrdem_contacts* out, int32_t reps, int32_t* chosen, double* ms) {
+  int st = check_pair_args(c, h, n_pairs, ab, eps, poses);
+  if (st) return st;
+  if (!contacts_ok(out) || (precision != MRDEM_PREC_FP32 && precision != MRDEM_PREC_FP64) ||
+      reps < 1 || reps > 1000 || n_pairs < 1)
+    return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return autotune(c, h, n_pairs, ab, eps, poses, precision, out, reps, chosen, ms);
 }
 
 int mrdem_check(mrdem_ctx* c, mrdem_stream s, int64_t* required) {

@@ -46,7 +46,7 @@ __device__ __forceinline__ int64_t warp_reserve(int n, int* list, unsigned long 
   return first;
 }
 
-__global__ void __launch_bounds__(128) k_cp_float(HierDev H, const PairXf* __restrict__ xf,
+__global__ void __launch_bounds__(256) k_cp_float(HierDev H, const PairXf* __restrict__ xf,
                                                   const PairXf64* __restrict__ xf64,
                                                   const PairXfDD* __restrict__ xfdd,
                                                   const int3* __restrict__ cands,
@@ -227,7 +227,7 @@ __device__ __forceinline__ const ItemRes* best_item(const AccRec& r, const ItemR
 }
 
 // Exact pass: contacts of the accepted candidates.
-__global__ void __launch_bounds__(128) k_select_exact(HierDev H, const PairXfDD* __restrict__ xfdd,
+__global__ void __launch_bounds__(256) k_select_exact(HierDev H, const PairXfDD* __restrict__ xfdd,
                                                       const AccRec* __restrict__ acc,
                                                       const ItemRes* __restrict__ res_pt,
                                                       const ItemRes* __restrict__ res_ee,
@@ -271,10 +271,12 @@ __global__ void __launch_bounds__(128) k_select_exact(HierDev H, const PairXfDD*
 // launchers
 
 int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts* out,
-                      cudaStream_t s) {
+                      int threads, cudaStream_t s) {
   ProfScope ps(c, K_EXACT, s);
+  // blocks: 8 per SM at 128 threads, the same threads per SM otherwise
+  const int eb = c->n_sms * 8 * 128 / threads;
   // the accepted pairs and the three item lists start empty (counters zeroed by detect)
-  launch_after(k_cp_float, c->n_sms * 8, 128, 0, s, hier->dev, c->xf, c->xf64, c->xfdd, c->cands,
+  launch_after(k_cp_float, eb, threads, 0, s, hier->dev, c->xf, c->xf64, c->xfdd, c->cands,
                c->acc, c->cap_cands, c->items_pt, c->items_ee, c->items_cx, c->cap_items,
                c->counters, c->status);
   int ib = c->n_sms * 8;
@@ -284,7 +286,7 @@ int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts
                c->res_ee, c->counters);
   launch_after(k_cp_items<2>, ib, 256, 0, s, c->acc, c->items_cx, (int)CNT_CX, c->cap_items,
                c->res_cx, c->counters);
-  launch_after(k_select_exact, c->n_sms * 8, 128, 0, s, hier->dev, c->xfdd, c->acc, c->res_pt,
+  launch_after(k_select_exact, eb, threads, 0, s, hier->dev, c->xfdd, c->acc, c->res_pt,
                c->res_ee, c->res_cx, c->cands, c->counters, c->cap_cands, c->status, *out,
                c->pair_cnt);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;

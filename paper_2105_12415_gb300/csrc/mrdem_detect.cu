@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
                                                        const int4* __restrict__ in, int level,
                                                        int4* sweep, unsigned long long* cnt,
                                                        unsigned long long* status,
-                                                       int64_t cap_level, int64_t cap_sweep) {
+                                                       int64_t cap_level, int64_t cap_sweep,
+                                                       int max_items) {
   wait_prior_grid();
   __shared__ int soff[WARPS][32];
   __shared__ int4 sit[WARPS][32];
@@ -203,9 +204,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
   WarpQueue<int4, 128> outq;
   outq.buf = sq[w];
   // items per warp and pass: the smallest power of two that spreads the
-  // level over every resident warp (32 at most)
+  // level over every resident warp, max_items at most (a power of two <= 32)
   const int64_t warps = (int64_t)gridDim.x * WARPS;
-  int C = 32;
+  int C = max_items;
   while (C > 1 && (int64_t)(C >> 1) * warps >= n_in) C >>= 1;
   const int64_t step = warps * C;
   int64_t base = ((int64_t)blockIdx.x * WARPS + w) * C;
@@ -459,21 +460,20 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_tile(HierDev H, const PairXf*
 // Fine pairs awaiting the sweep, per warp: A's triangle and B's (in A's
 // frame) as 18 floats, the pair entry and the thresholds.  At most 31 wait
 // between rounds and a round adds at most 32.
-constexpr int kFineWarps = 4;
 struct FineQueue {
   float g[18][64];
   int4 e[64];
   float thr[64], ce2[64];
 };
 
-template <bool CONV>
-__global__ void __launch_bounds__(kFineWarps * 32) k_sweep_fine(
+template <int WARPS, bool CONV>
+__global__ void __launch_bounds__(WARPS * 32) k_sweep_fine(
     HierDev H, const PairXf* __restrict__ xf, SweepConst sc, float conv_c,
     const int4* __restrict__ fine, int3* cands, unsigned long long* cnt, unsigned long long* status,
     int64_t cap_fine, int64_t cap_cands, const double* __restrict__ eps_d) {
   wait_prior_grid();
-  __shared__ FineQueue smem[kFineWarps];
-  __shared__ int3 scq[kFineWarps][64];
+  __shared__ FineQueue smem[WARPS];
+  __shared__ int3 scq[WARPS][64];
   const int w = threadIdx.x >> 5, lane = lane_id();
   FineQueue& Q = smem[w];
   WarpQueue<int3, 64> cq;
@@ -502,8 +502,8 @@ __global__ void __launch_bounds__(kFineWarps * 32) k_sweep_fine(
     const int4 e = Q.e[slot >= 0 ? slot : 0];
     cq.push(s, make_int3(e.x, e.y, e.z), cands, cnt + CNT_CANDS, cap_cands, status + ST_REQ_CANDS);
   };
-  const int64_t step = (int64_t)gridDim.x * kFineWarps * 32;
-  for (int64_t base = ((int64_t)blockIdx.x * kFineWarps + w) * 32; base < n; base += step) {
+  const int64_t step = (int64_t)gridDim.x * WARPS * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 32; base < n; base += step) {
     const int64_t k = base + lane;
     const bool act = k < n;
     bool need = false;
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(kFineWarps * 32) k_sweep_fine(
 // coordinates (B moved by the float transform; its error is within the
 // pair's margin), so pairs it rejects never touch double arithmetic; the
 // others are finished in double from the double transform.
-__global__ void __launch_bounds__(128) k_exact32(HierDev H, const PairXf* __restrict__ xf,
+__global__ void __launch_bounds__(256) k_exact32(HierDev H, const PairXf* __restrict__ xf,
                                                  const PairXf64* __restrict__ xf64,
                                                  const int3* __restrict__ cands,
                                                  unsigned long long* cnt,
@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(128) k_exact32(HierDev H, const PairXf* __rest
 
 // Full FP64 comparison-based distance for every entry of a list (the FP64
 // form's candidates, or the fallback list of the one-kernel FP32 form).
-__global__ void __launch_bounds__(128) k_exact64(HierDev H, const PairXf64* __restrict__ xf64,
+__global__ void __launch_bounds__(256) k_exact64(HierDev H, const PairXf64* __restrict__ xf64,
                                                  const int3* __restrict__ list,
                                                  unsigned long long* cnt, int count_slot,
                                                  int64_t cap, unsigned long long* status,
@@ -850,16 +850,99 @@ static int ensure_pairs(mrdem_ctx* c, int64_t n) {
 // once (SMs x resident blocks per SM), so that interleaved work assignment
 // has no second wave.
 template <typename K>
-static int one_wave(mrdem_ctx* c, int id, K kernel, int threads, size_t smem) {
-  if (c->occ[id] <= 0) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess || b <= 0) {
-      cudaGetLastError();
-      b = 1;
-    }
-    c->occ[id] = b;
+static int one_wave(mrdem_ctx* c, K kernel, int threads, size_t smem) {
+  const void* k = reinterpret_cast<const void*>(kernel);
+  for (int i = 0; i < c->n_occ; ++i)
+    if (c->occ[i].kernel == k && c->occ[i].threads == threads && c->occ[i].smem == smem)
+      return c->occ[i].blocks * c->n_sms;
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess || b <= 0) {
+    cudaGetLastError();
+    b = 1;
   }
-  return c->occ[id] * c->n_sms;
+  if (c->n_occ < (int)(sizeof(c->occ) / sizeof(c->occ[0]))) c->occ[c->n_occ++] = {k, threads, smem, b};
+  return b * c->n_sms;
+}
+
+// Launch shapes: the autotuned entry of the call's size class, else the
+// context's parameters.
+Shape shape_for(const mrdem_ctx* c, int64_t n_pairs) {
+  if (c->force_shape) return *c->force_shape;
+  const int k = size_class(n_pairs);
+  if (c->tuned_ok[k]) return c->tuned[k];
+  const mrdem_params& p = c->params;
+  return {p.level_warps, p.expand_items, p.node_threads, p.tile_warps, p.sweep_warps,
+          p.exact_threads};
+}
+
+// Launch helpers over the kernels' block shapes (one template instance per
+// shape; `pdl` chains the launch to the previous kernel of the stream).
+template <typename... Exp, typename... Act>
+static void launch_pdl(bool pdl, void (*kernel)(Exp...), int grid, int block, cudaStream_t s,
+                       Act&&... args) {
+  if (pdl) launch_after(kernel, grid, block, 0, s, std::forward<Act>(args)...);
+  else kernel<<<grid, block, 0, s>>>(std::forward<Act>(args)...);
+}
+template <int W>
+static void expand_w(mrdem_ctx* c, bool pdl, cudaStream_t s, const HierDev& H, const PairXf* xf,
+                     const int4* in, int level, int4* sweep, unsigned long long* cnt,
+                     unsigned long long* status, int64_t cap_level, int64_t cap_sweep, int items) {
+  launch_pdl(pdl, k_expand<W>, one_wave(c, k_expand<W>, W * 32, 0), W * 32, s, H, xf, in, level,
+             sweep, cnt, status, cap_level, cap_sweep, items);
+}
+static void launch_expand(mrdem_ctx* c, const Shape& sh, bool pdl, cudaStream_t s, const HierDev& H,
+                          const PairXf* xf, const int4* in, int level, int4* sweep,
+                          unsigned long long* cnt, unsigned long long* status, int64_t cap_level,
+                          int64_t cap_sweep) {
+  if (sh.level_warps == 2) expand_w<2>(c, pdl, s, H, xf, in, level, sweep, cnt, status, cap_level, cap_sweep, sh.expand_items);
+  else if (sh.level_warps == 4) expand_w<4>(c, pdl, s, H, xf, in, level, sweep, cnt, status, cap_level, cap_sweep, sh.expand_items);
+  else expand_w<8>(c, pdl, s, H, xf, in, level, sweep, cnt, status, cap_level, cap_sweep, sh.expand_items);
+}
+template <int W>
+static void tile_w(mrdem_ctx* c, bool pdl, cudaStream_t s, const HierDev& H, const PairXf* xf,
+                   const TileItem* tiles, int4* fine, unsigned long long* cnt,
+                   unsigned long long* status, int64_t cap_tiles, int64_t cap_fine) {
+  launch_pdl(pdl, k_tile<W>, one_wave(c, k_tile<W>, W * 32, 0), W * 32, s, H, xf, tiles, fine, cnt,
+             status, cap_tiles, cap_fine);
+}
+static void launch_tile(mrdem_ctx* c, const Shape& sh, bool pdl, cudaStream_t s, const HierDev& H,
+                        const PairXf* xf, const TileItem* tiles, int4* fine,
+                        unsigned long long* cnt, unsigned long long* status, int64_t cap_tiles,
+                        int64_t cap_fine) {
+  if (sh.tile_warps == 2) tile_w<2>(c, pdl, s, H, xf, tiles, fine, cnt, status, cap_tiles, cap_fine);
+  else if (sh.tile_warps == 4) tile_w<4>(c, pdl, s, H, xf, tiles, fine, cnt, status, cap_tiles, cap_fine);
+  else tile_w<8>(c, pdl, s, H, xf, tiles, fine, cnt, status, cap_tiles, cap_fine);
+}
+template <int W>
+static void sweep_fine_w(mrdem_ctx* c, bool pdl, cudaStream_t s, const HierDev& H,
+                         const PairXf* xf, SweepConst sc, float conv_c, const int4* fine,
+                         int3* cands, unsigned long long* cnt, unsigned long long* status,
+                         int64_t cap_fine, int64_t cap_cands, const double* eps) {
+  launch_pdl(pdl, k_sweep_fine<W, true>, one_wave(c, k_sweep_fine<W, true>, W * 32, 0), W * 32, s,
+             H, xf, sc, conv_c, fine, cands, cnt, status, cap_fine, cap_cands, eps);
+}
+static void launch_sweep_fine(mrdem_ctx* c, const Shape& sh, bool pdl, cudaStream_t s,
+                              const HierDev& H, const PairXf* xf, SweepConst sc, float conv_c,
+                              const int4* fine, int3* cands, unsigned long long* cnt,
+                              unsigned long long* status, int64_t cap_fine, int64_t cap_cands,
+                              const double* eps) {
+  if (sh.sweep_warps == 2) sweep_fine_w<2>(c, pdl, s, H, xf, sc, conv_c, fine, cands, cnt, status, cap_fine, cap_cands, eps);
+  else if (sh.sweep_warps == 8) sweep_fine_w<8>(c, pdl, s, H, xf, sc, conv_c, fine, cands, cnt, status, cap_fine, cap_cands, eps);
+  else sweep_fine_w<4>(c, pdl, s, H, xf, sc, conv_c, fine, cands, cnt, status, cap_fine, cap_cands, eps);
+}
+static void launch_sweep_nodes(mrdem_ctx* c, const Shape& sh, bool pdl, cudaStream_t s,
+                               const HierDev& H, const PairXf* xf, SweepConst sc, const int4* sweep,
+                               int level, int4* out, TileItem* tiles, unsigned long long* cnt,
+                               unsigned long long* status, int64_t cap_sweep, int64_t cap_level,
+                               int64_t cap_tiles) {
+  const int t = sh.node_threads;
+  launch_pdl(pdl, k_sweep_nodes, one_wave(c, k_sweep_nodes, t, 0), t, s, H, xf, sc, sweep, level,
+             out, tiles, cnt, status, cap_sweep, cap_level, cap_tiles);
+}
+// k_exact64 grid: 8 blocks per SM at 128 threads, the same threads per SM
+// otherwise.
+static int exact_blocks(const mrdem_ctx* c, int threads, int per_sm_128) {
+  return c->n_sms * per_sm_128 * 128 / threads;
 }
 
 static SweepConst sweep_const(const mrdem_params& p) {
@@ -971,40 +1054,36 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
                                          c->cap_level, c->cap_tiles);
     }
     int steps = std::min(hier->h.max_depth - 1, kMaxLevels - 1);
-    constexpr int W = 8;
+    const Shape sh = shape_for(c, n_pairs);
     for (int l = 0; l < steps; ++l) {
       {
-        int eb = one_wave(c, K_LEVEL, k_expand<W>, W * 32, 0);
         ProfScope ps(c, K_LEVEL, s);
-        launch_after(k_expand<W>, eb, W * 32, 0, s, H, c->xf, c->level_list[l & 1], l, c->sweep,
-                     c->counters, c->status, c->cap_level, c->cap_sweep);
+        launch_expand(c, sh, true, s, H, c->xf, c->level_list[l & 1], l, c->sweep, c->counters,
+                      c->status, c->cap_level, c->cap_sweep);
       }
-      int nb = one_wave(c, K_SWEEP_NODES, k_sweep_nodes, 256, 0);
       ProfScope ps(c, K_SWEEP_NODES, s);
-      launch_after(k_sweep_nodes, nb, 256, 0, s, H, c->xf, sc, c->sweep, l,
-                   c->level_list[(l + 1) & 1], c->tiles, c->counters, c->status, c->cap_sweep,
-                   c->cap_level, c->cap_tiles);
+      launch_sweep_nodes(c, sh, true, s, H, c->xf, sc, c->sweep, l, c->level_list[(l + 1) & 1],
+                         c->tiles, c->counters, c->status, c->cap_sweep, c->cap_level,
+                         c->cap_tiles);
     }
     {
-      int tb = one_wave(c, K_TILE, k_tile<W>, W * 32, 0);
       ProfScope ps(c, K_TILE, s);
-      launch_after(k_tile<W>, tb, W * 32, 0, s, H, c->xf, c->tiles, c->sweep, c->counters,
-                   c->status, c->cap_tiles, c->cap_sweep);
+      launch_tile(c, sh, true, s, H, c->xf, c->tiles, c->sweep, c->counters, c->status,
+                  c->cap_tiles, c->cap_sweep);
     }
     {
-      int fb = one_wave(c, K_SWEEP_FINE, k_sweep_fine<true>, kFineWarps * 32, 0);
       ProfScope ps(c, K_SWEEP_FINE, s);
-      launch_after(k_sweep_fine<true>, fb, kFineWarps * 32, 0, s, H, c->xf, sc, prm.conv_c,
-                   c->sweep, c->cands, c->counters, c->status, c->cap_sweep, c->cap_cands, eps);
+      launch_sweep_fine(c, sh, true, s, H, c->xf, sc, prm.conv_c, c->sweep, c->cands, c->counters,
+                        c->status, c->cap_sweep, c->cap_cands, eps);
     }
-    int et = prm.exact_threads;
+    const int et = sh.exact_threads;
     if (precision == MRDEM_PREC_FP64) {
       ProfScope ps(c, K_EXACT, s);
-      launch_after(k_exact64, c->n_sms * 8, et, 0, s, H, c->xf64, c->cands, c->counters,
+      launch_after(k_exact64, exact_blocks(c, et, 8), et, 0, s, H, c->xf64, c->cands, c->counters,
                    (int)CNT_CANDS, c->cap_cands, c->status, (int)MRDEM_STAT_FP64, tmp,
                    c->pair_cnt);
     } else {
-      int r = launch_exact_fp32(c, hier, &tmp, s);
+      int r = launch_exact_fp32(c, hier, &tmp, et, s);
       if (r) return r;
     }
     // the contacts, grouped by pair, into the caller's buffers
@@ -1019,6 +1098,138 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
     cudaMemcpyAsync(stats, c->counters + CNT_STATS, sizeof(int64_t) * MRDEM_STAT_COUNT,
                     cudaMemcpyDeviceToDevice, s);
   return finish(s);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times the detection kernels under candidate launch shapes on the
+// caller's workload and keeps the fastest shape of each kernel for the call's
+// size class.  Nine shapes are run: every (k_expand warps, items per warp)
+// combination once, and the other kernels' values spread over the nine so
+// that each value is timed three or more times (the kernels run one after
+// another on lists of the same content whatever the shapes, so each kernel's
+// time depends on its own shape only).  Each shape runs reps + 1 times, the
+// first untimed; kernels are timed by the context's event pairs.
+int autotune(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
+             const double* eps, const double* poses, int precision, const mrdem_contacts* out,
+             int reps, int32_t* chosen, double* ms) {
+  static const int LW[3] = {2, 4, 8}, EI[3] = {8, 16, 32}, NT[2] = {128, 256};
+  static const int TW[3] = {2, 4, 8}, SW[3] = {2, 4, 8}, ET[3] = {64, 128, 256};
+  if (cudaDeviceSynchronize() != cudaSuccess) return MRDEM_ERR_CUDA;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return MRDEM_ERR_CUDA;
+  }
+  const mrdem_params& p = c->params;
+  const Shape base = {p.level_warps, p.expand_items, p.node_threads, p.tile_warps, p.sweep_warps,
+                      p.exact_threads};
+  double t_exp[3][3] = {}, t_nodes[2] = {}, t_tile[3] = {}, t_sweep[3] = {}, t_exact[3] = {};
+  int n_exp[3][3] = {}, n_nodes[2] = {}, n_tile[3] = {}, n_sweep[3] = {}, n_exact[3] = {};
+  const bool prof_was = c->prof;
+  std::vector<ProfRec> saved;
+  saved.swap(c->prof_recs);
+  int st = MRDEM_OK;
+  // one timed run of `reps` detections under shape sh: per-kernel sums
+  auto run = [&](const Shape& sh, double* per_kernel, double* total) -> int {
+    c->force_shape = &sh;
+    int r = launch_detect(c, hier, n_pairs, ab, eps, poses, precision, out, nullptr, s);  // untimed
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (r == MRDEM_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
+      r = MRDEM_ERR_CUDA;
+    c->prof = per_kernel != nullptr;
+    if (r == MRDEM_OK) cudaEventRecord(a, s);
+    for (int k = 0; k < reps && r == MRDEM_OK; ++k)
+      r = launch_detect(c, hier, n_pairs, ab, eps, poses, precision, out, nullptr, s);
+    if (r == MRDEM_OK) cudaEventRecord(b, s);
+    c->prof = false;
+    c->force_shape = nullptr;
+    if (cudaStreamSynchronize(s) != cudaSuccess) r = MRDEM_ERR_CUDA;
+    if (r == MRDEM_OK) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, a, b);
+      *total = t / reps;
+    }
+    for (auto& rec : c->prof_recs) {
+      float t = 0.f;
+      if (r == MRDEM_OK && cudaEventElapsedTime(&t, rec.a, rec.b) == cudaSuccess && per_kernel)
+        per_kernel[rec.kernel] += t / reps;
+      c->ev_pool.push_back(rec.a);
+      c->ev_pool.push_back(rec.b);
+    }
+    c->prof_recs.clear();
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    // a list that overflowed makes the timings meaningless: report it (the
+    // status stays latched for mrdem_check)
+    unsigned long long h[ST_TOTAL] = {};
+    if (r == MRDEM_OK &&
+        cudaMemcpy(h, c->status, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      for (int k = ST_REQ_LEVEL; k < ST_TOTAL; ++k)
+        if (h[k]) r = MRDEM_ERR_CAPACITY;
+      if (h[ST_NONFINITE]) r = MRDEM_ERR_NONFINITE;
+    }
+    if (cudaGetLastError() != cudaSuccess && r == MRDEM_OK) r = MRDEM_ERR_CUDA;
+    return r;
+  };
+  for (int i = 0; i < 9 && st == MRDEM_OK; ++i) {
+    const int e = i % 3, f = i / 3, g = (i + 1) % 3, q = (i + 2) % 3, x = (i + i / 3) % 3;
+    const Shape sh = {LW[e], EI[f], NT[i % 2], TW[g], SW[q], ET[x]};
+    double kt[K_COUNT] = {}, tot = 0.0;
+    st = run(sh, kt, &tot);
+    if (st != MRDEM_OK) break;
+    t_exp[e][f] += kt[K_LEVEL];
+    ++n_exp[e][f];
+    t_nodes[i % 2] += kt[K_SWEEP_NODES];
+    ++n_nodes[i % 2];
+    t_tile[g] += kt[K_TILE];
+    ++n_tile[g];
+    t_sweep[q] += kt[K_SWEEP_FINE];
+    ++n_sweep[q];
+    t_exact[x] += kt[K_EXACT];
+    ++n_exact[x];
+  }
+  Shape best = base;
+  if (st == MRDEM_OK) {
+    auto argmin = [](const double* t, const int* n, int m) {
+      int k = 0;
+      for (int j = 1; j < m; ++j)
+        if (n[j] && (!n[k] || t[j] / n[j] < t[k] / n[k])) k = j;
+      return k;
+    };
+    int be = 0, bf = 0;
+    for (int e = 0; e < 3; ++e)
+      for (int f = 0; f < 3; ++f)
+        if (n_exp[e][f] && t_exp[e][f] / n_exp[e][f] < t_exp[be][bf] / n_exp[be][bf]) {
+          be = e;
+          bf = f;
+        }
+    best = {LW[be], EI[bf], NT[argmin(t_nodes, n_nodes, 2)], TW[argmin(t_tile, n_tile, 3)],
+            SW[argmin(t_sweep, n_sweep, 3)], ET[argmin(t_exact, n_exact, 3)]};
+    double t_base = 0.0, t_best = 0.0;
+    st = run(base, nullptr, &t_base);
+    if (st == MRDEM_OK) st = run(best, nullptr, &t_best);
+    if (st == MRDEM_OK) {
+      const int k = size_class(n_pairs);
+      c->tuned[k] = best;
+      c->tuned_ok[k] = true;
+      if (ms) {
+        ms[0] = t_base;
+        ms[1] = t_best;
+      }
+      if (chosen) {
+        chosen[0] = best.level_warps;
+        chosen[1] = best.expand_items;
+        chosen[2] = best.node_threads;
+        chosen[3] = best.tile_warps;
+        chosen[4] = best.sweep_warps;
+        chosen[5] = best.exact_threads;
+      }
+    }
+  }
+  c->prof = prof_was;
+  c->prof_recs.swap(saved);
+  cudaStreamDestroy(s);
+  return st;
 }
 
 int launch_plain(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
@@ -1189,31 +1400,28 @@ extern "C" int mrdem_detect_noalloc(const mrdem_hier* hier, int64_t n_pairs,
                                        sc, 1,
                                        lists[0], tiles, cnt, status, kNaLevel, kNaTiles);
     int steps = std::min(hier->h.max_depth - 1, kMaxLevels - 1);
-    constexpr int W = 8;
+    const Shape sh = shape_for(c, n_pairs);
     for (int l = 0; l < steps; ++l) {
-      int eb = one_wave(c, K_LEVEL, k_expand<W>, W * 32, 0);
-      k_expand<W><<<eb, W * 32, 0, s>>>(H, xf, lists[l & 1], l, sweep, cnt, status, kNaLevel,
-                                        kNaSweep);
-      int nb = one_wave(c, K_SWEEP_NODES, k_sweep_nodes, 256, 0);
-      k_sweep_nodes<<<nb, 256, 0, s>>>(H, xf, sc, sweep, l, lists[(l + 1) & 1], tiles, cnt,
-                                       status, kNaSweep, kNaLevel, kNaTiles);
+      launch_expand(c, sh, false, s, H, xf, lists[l & 1], l, sweep, cnt, status, kNaLevel, kNaSweep);
+      launch_sweep_nodes(c, sh, false, s, H, xf, sc, sweep, l, lists[(l + 1) & 1], tiles, cnt,
+                         status, kNaSweep, kNaLevel, kNaTiles);
     }
-    int tb = one_wave(c, K_TILE, k_tile<W>, W * 32, 0);
-    k_tile<W><<<tb, W * 32, 0, s>>>(H, xf, tiles, sweep, cnt, status, kNaTiles, kNaSweep);
-    int fb = one_wave(c, K_SWEEP_FINE, k_sweep_fine<true>, kFineWarps * 32, 0);
-    k_sweep_fine<true><<<fb, kFineWarps * 32, 0, s>>>(H, xf, sc, prm.conv_c, sweep, cands, cnt, status,
-                                          kNaSweep, kNaCands, pair_eps);
-    int et = prm.exact_threads;
+    launch_tile(c, sh, false, s, H, xf, tiles, sweep, cnt, status, kNaTiles, kNaSweep);
+    launch_sweep_fine(c, sh, false, s, H, xf, sc, prm.conv_c, sweep, cands, cnt, status, kNaSweep,
+                      kNaCands, pair_eps);
+    const int et = sh.exact_threads;
     if (precision == MRDEM_PREC_FP64) {
-      k_exact64<<<c->n_sms * 8, et, 0, s>>>(H, xf64, cands, cnt, CNT_CANDS, kNaCands, status,
-                                             MRDEM_STAT_FP64, *out, nullptr);
+      k_exact64<<<exact_blocks(c, et, 8), et, 0, s>>>(H, xf64, cands, cnt, CNT_CANDS, kNaCands,
+                                                       status, MRDEM_STAT_FP64, *out, nullptr);
     } else {
       // the first level list is free once the tiles are done: the fallback list
-      k_exact32<<<c->n_sms * 8, et, 0, s>>>(H, xf, xf64, cands, cnt, status, kNaCands,
-                                             reinterpret_cast<int3*>(lists[0]), kNaLevel, *out);
-      k_exact64<<<c->n_sms * 4, et, 0, s>>>(H, xf64, reinterpret_cast<const int3*>(lists[0]), cnt,
-                                             CNT_FALLBACK, kNaLevel, status, MRDEM_STAT_FP64, *out,
-                                             nullptr);
+      k_exact32<<<exact_blocks(c, et, 8), et, 0, s>>>(H, xf, xf64, cands, cnt, status, kNaCands,
+                                                       reinterpret_cast<int3*>(lists[0]), kNaLevel,
+                                                       *out);
+      k_exact64<<<exact_blocks(c, et, 4), et, 0, s>>>(H, xf64,
+                                                       reinterpret_cast<const int3*>(lists[0]), cnt,
+                                                       CNT_FALLBACK, kNaLevel, status,
+                                                       MRDEM_STAT_FP64, *out, nullptr);
     }
   }
   cudaMemcpyAsync(stats, cnt + CNT_STATS, sizeof(int64_t) * MRDEM_STAT_COUNT,

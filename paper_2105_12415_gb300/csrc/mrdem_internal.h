@@ -155,6 +155,19 @@ struct mrdem_hier {
 };
 
 namespace mrdem {
+// Launch shapes of the detection kernels (the tunable part of the params).
+struct Shape {
+  int level_warps;    // k_expand: warps per block (2, 4, 8)
+  int expand_items;   // k_expand: level items per warp and pass, at most (8, 16, 32)
+  int node_threads;   // k_sweep_nodes: threads per block (128, 256)
+  int tile_warps;     // k_tile: warps per block (2, 4, 8)
+  int sweep_warps;    // k_sweep_fine: warps per block (2, 4, 8)
+  int exact_threads;  // exact pass: threads per block (64, 128, 256)
+};
+constexpr int kSizeClasses = 4;  // particle pairs per call: < 256, < 4096, < 65536, more
+inline int size_class(int64_t n_pairs) {
+  return n_pairs < 256 ? 0 : n_pairs < 4096 ? 1 : n_pairs < 65536 ? 2 : 3;
+}
 enum KernelId : int { K_SETUP = 0, K_LEVEL, K_SWEEP_NODES, K_TILE, K_SWEEP_FINE, K_EXACT, K_EXACT64, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_SORT, K_MERGE, K_BROAD, K_STEP, K_COUNT };
 struct ProfRec {
   int kernel;
@@ -213,7 +226,20 @@ struct mrdem_ctx {
   int64_t cap_frames = 0;
   unsigned long long* counters = nullptr;  // [CNT_TOTAL]
   unsigned long long* status = nullptr;    // [ST_TOTAL]
-  int occ[16] = {0};  // resident blocks per SM of each kernel (0 = not queried yet)
+  // resident blocks per SM of each kernel instance and block shape, filled
+  // on first use (a fixed table: a launch never allocates host memory)
+  struct Occ {
+    const void* kernel;
+    int threads;
+    size_t smem;
+    int blocks;
+  };
+  Occ occ[64] = {};
+  int n_occ = 0;
+  // launch shapes chosen by mrdem_autotune per size class (else the params')
+  mrdem::Shape tuned[mrdem::kSizeClasses] = {};
+  bool tuned_ok[mrdem::kSizeClasses] = {false, false, false, false};
+  const mrdem::Shape* force_shape = nullptr;  // set while the autotuner times a shape
   bool prof = false;
   std::vector<mrdem::ProfRec> prof_recs;
   std::vector<cudaEvent_t> ev_pool;
@@ -262,7 +288,12 @@ int launch_plain(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const 
                  cudaStream_t s);
 // closest-point pipeline (mrdem_closest.cu)
 int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts* out,
-                      cudaStream_t s);
+                      int threads, cudaStream_t s);
+// launch shapes (mrdem_detect.cu)
+Shape shape_for(const mrdem_ctx* c, int64_t n_pairs);
+int autotune(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
+             const double* eps, const double* poses, int precision, const mrdem_contacts* out,
+             int reps, int32_t* chosen, double* ms);
 int launch_forces(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
                   const double* pair_eps, const double* poses, const mrdem_contacts* c,
                   const double* mass, const double* com, double k_s, double* ft, double* energy,
@@ -306,6 +337,10 @@ int launch_triangle_distance(mrdem_ctx* ctx, int64_t n, const double* P, const d
                              const double* eps, int precision, double* dist, double* pa,
                              double* pb, int32_t* feature, float* sx, float* sgap, int32_t* sconv,
                              cudaStream_t s);
+// device hierarchy builder (mrdem_build.cu): fills *out like the host builder
+int build_hierarchy_device(const mrdem_params& p, int32_t n, const int64_t* vert_off,
+                           const float* d_verts, const int64_t* tri_off, const int32_t* d_tris,
+                           HierHost* out, double* ms);
 // host hierarchy builder (mrdem_hierarchy.cpp)
 int build_hierarchy_host(const mrdem_params& p, int32_t n, const int64_t* vert_off,
                          const float* verts, const int64_t* tri_off, const int32_t* tris,

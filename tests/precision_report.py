@@ -10,7 +10,12 @@ tests bound):
   contact set      contacts missing / extra against the oracle, and how many
                    of those lie within 1e-6 eps of the threshold 2 eps;
   distance         max |d - d_ref| / max(d_ref, eps) over the common contacts;
+  distance_uS      max |d - d_ref| in units of u S (u = 2^-53, S = |t_A| +
+                   |t_B| + r_A + r_B: the world coordinates' magnitude), the
+                   rounding floor of the distance tolerance;
   closest points   max |p_a - p_a,ref| / eps over common contacts with d > 0;
+  points_uS        largest distance of p_a from A's triangle (p_b from B's),
+                   in units of u S (the closest-point floor of the tests);
   force, torque    per particle max |F - F_ref| / sum_c |F_c| (torque: over
                    sum_c |F_c| times the largest lever);
   energy           |E - E_ref| / E_ref;
@@ -57,15 +62,39 @@ def _contact_errors(got, ref, scene):
     common = sorted(sg & sr)
     gi = {k: i for i, k in enumerate(kg)}
     ri = {k: i for i, k in enumerate(kr)}
-    derr = perr = 0.0
+    from tests.gpu_common import U, world_scale
+    uS = U * world_scale(scene)
+    derr = perr = duS = 0.0
     for k in common:
         e = eps[k[0]]
         derr = max(derr, abs(dgot[k] - dref[k]) / max(dref[k], e))
+        duS = max(duS, abs(dgot[k] - dref[k]) / uS[k[0]])
         if dref[k] > 0:
             perr = max(perr, float(np.linalg.norm(got["pa"][gi[k]] - ref["pa"][ri[k]])) / e)
+    # closest points: largest distance of p_a (p_b) from A's (B's) world
+    # triangle, in units of u S
+    pts = 0.0
+    if common:
+        import oracle
+        ig = np.array([gi[k] for k in common])
+        A = scene.pairs[[k[0] for k in common], 0]
+        B = scene.pairs[[k[0] for k in common], 1]
+        TA = np.empty((len(common), 9))
+        TB = np.empty((len(common), 9))
+        ta = np.array([k[1] for k in common])
+        tb = np.array([k[2] for k in common])
+        for i in np.unique(np.concatenate([A, B])):
+            W = oracle.world_triangles(scene, i)
+            TA[A == i] = W[ta[A == i]]
+            TB[B == i] = W[tb[B == i]]
+        da, _ = oracle.point_triangle(got["pa"][ig], TA)
+        db, _ = oracle.point_triangle(got["pb"][ig], TB)
+        us = np.array([uS[k[0]] for k in common])
+        pts = float((np.maximum(da, db) / us).max())
     return {"missing": len(missing), "missing_in_band": sum(near(k, dref[k]) for k in missing),
             "extra": len(extra), "extra_in_band": sum(near(k, dgot[k]) for k in extra),
-            "distance": derr, "points": perr, "common": len(common)}
+            "distance": derr, "distance_uS": duS, "points": perr, "points_uS": pts,
+            "common": len(common)}
 
 
 def _force_errors(ft, e, ft_ref, e_ref, ref, scene):
@@ -166,7 +195,7 @@ def main(out_path=None):
             rows.append(row)
             print(row, flush=True)
     cols = ["workload", "form", "contacts", "missing", "missing_in_band", "extra", "extra_in_band",
-            "distance", "points", "force", "torque", "energy", "pose_grad", "jacobian", "vertex_grad"]
+            "distance", "distance_uS", "points", "points_uS", "force", "torque", "energy", "pose_grad", "jacobian", "vertex_grad"]
     fmt = lambda v: (f"{v:.2e}" if isinstance(v, float) else str(v))  # noqa: E731
     lines = ["| " + " | ".join(cols) + " |", "|" + "---|" * len(cols)]
     for r in rows:

@@ -5,7 +5,7 @@ sampled pairs, and the edge cases."""
 import numpy as np
 import pytest
 
-from gen import scene_c1, scene_c2, scene_pairs, scene_particle_on_plane, scene_tiny
+from gen import scene_c1, scene_c2, scene_c3, scene_pairs, scene_particle_on_plane, scene_tiny
 from tests.gpu_common import compare_contacts, gpu_scene_tensors
 
 pytestmark = pytest.mark.gpu
@@ -180,14 +180,26 @@ def test_capacity_overflow_is_reported_and_recovered(orc):
     compare_contacts(got.to_numpy(), orc.detect(s), s, "fp64")
 
 
-@pytest.mark.parametrize("precision", ["fp32"])
-def test_batched_full_size_sampled(gctx, orc, precision):
+@pytest.fixture(scope="module")
+def c2_oracle_subset(orc):
+    """The oracle's contacts of the batched workload's pairs with id = 0 mod 8
+    (512 pairs), through the sphere-filtered brute force."""
+    from tests import oracle_filtered
+    s = scene_c2()
+    ids = np.arange(0, s.n_pairs, 8)
+    return s, ids, oracle_filtered.contacts(orc, s, ids)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batched_full_size_sampled(gctx, orc, c2_oracle_subset, precision):
     """The 4096-pair batched workload in one launch sequence (as timed by the
-    benchmark); sampled pairs checked against the oracle pair by pair, and
+    benchmark): the pairs with id = 0 mod 8 (512 pairs) checked against the
+    oracle contact by contact, the deepest interpenetration too, and
     properties that hold at any size checked on all pairs."""
     import torch
     import paper_2105_12415_gb300 as m
-    s = scene_c2()
+    from tests import oracle_filtered
+    s, ids, ref_sub = c2_oracle_subset
     hier = m.Hierarchy.from_scene(gctx, s)
     dev = torch.device("cuda:0")
     t = gpu_scene_tensors(s, dev)
@@ -204,19 +216,41 @@ def test_batched_full_size_sampled(gctx, orc, precision):
     assert len(np.unique(keys)) == n
     ntri = np.diff(s.tri_off)
     assert np.all(got["ta"] < ntri[s.pairs[got["pair"], 0]]) and np.all(got["tb"] < ntri[s.pairs[got["pair"], 1]])
-    # sampled pairs: one of every size class combination present, and the
-    # deepest interpenetration
-    rng = np.random.default_rng(0)
-    sample = list(rng.choice(s.n_pairs, size=10, replace=False))
-    sample.append(int(np.argmax(ntri[s.pairs[:, 0]] * ntri[s.pairs[:, 1]] *
-                               (np.bincount(got["pair"], minlength=s.n_pairs) > 0))))
-    sample = [int(x) for x in dict.fromkeys(int(v) for v in sample)]
-    sub = s.subset(sample)
-    ref = orc.detect(sub)
-    sel = np.isin(got["pair"], sample)
-    remap = {p: i for i, p in enumerate(sample)}
+    # the 512-pair subset, contact by contact
+    sel = np.isin(got["pair"], ids)
     g2 = {k: v[sel] for k, v in got.items()}
-    g2["pair"] = np.array([remap[p] for p in g2["pair"]], np.int32)
-    o = np.lexsort((g2["tb"], g2["ta"], g2["pair"]))
-    g2 = {k: v[o] for k, v in g2.items()}
-    compare_contacts(g2, ref, sub, precision)
+    assert len(ref_sub["d"]) > 1000
+    compare_contacts(g2, ref_sub, s, precision)
+    # the pair with the most contacts (deepest interpenetration) as well
+    deep = int(np.argmax(np.bincount(got["pair"], minlength=s.n_pairs)))
+    ref_d = oracle_filtered.contacts(orc, s, [deep])
+    g3 = {k: v[got["pair"] == deep] for k, v in got.items()}
+    compare_contacts(g3, ref_d, s, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_autotune_keeps_results(orc, precision):
+    """The launch-shape autotuner picks allowed values for the batch's size
+    class, and detection with the chosen shapes returns the oracle's contact
+    set as before; set_params clears the choice."""
+    import torch
+    import paper_2105_12415_gb300 as m
+    from tests import oracle_filtered
+    s = scene_c3(n_pairs=1024).subset(np.arange(0, 1024, 32))
+    ctx = m.Context(0)
+    hier = m.Hierarchy.from_scene(ctx, s)
+    t = gpu_scene_tensors(s, torch.device("cuda:0"))
+    ref = oracle_filtered.contacts(orc, s)
+    before, _ = m.detect(ctx, hier, t["pairs"], t["eps"], t["poses"], precision)
+    compare_contacts(before.to_numpy(), ref, s, precision)
+    r = m.autotune(ctx, hier, t["pairs"], t["eps"], t["poses"], precision, reps=2)
+    allowed = {"level_warps": {2, 4, 8}, "expand_items": {8, 16, 32}, "node_threads": {128, 256},
+               "tile_warps": {2, 4, 8}, "sweep_warps": {2, 4, 8}, "exact_threads": {64, 128, 256}}
+    for k, v in r["chosen"].items():
+        assert v in allowed[k], (k, v)
+    assert r["ms_default"] > 0 and r["ms_tuned"] > 0
+    after, _ = m.detect(ctx, hier, t["pairs"], t["eps"], t["poses"], precision)
+    compare_contacts(after.to_numpy(), ref, s, precision)
+    ctx.set_params(n_iter=4)
+    again, _ = m.detect(ctx, hier, t["pairs"], t["eps"], t["poses"], precision)
+    compare_contacts(again.to_numpy(), ref, s, precision)

@@ -504,7 +504,7 @@ def test_refined_candidates_equal_detection(m, ctx, orc, imp, precision):
     base = dataclasses.replace(s, pairs=pairs, eps=eps, com=np.zeros((s.n_particles, 3)))
     ref = orc.detect(base, poses=moved)
     assert len(ref["d"]) > 50 and cand.n() >= len(ref["d"])
-    compare_contacts(got, ref, base, "fp64")
+    compare_contacts(got, ref, base, "fp64", poses=moved)
 
 
 def test_picard_with_kept_candidates(m, ctx, imp):
@@ -539,7 +539,7 @@ def test_kept_candidates_detect_again_only_beyond_the_margin(m, ctx, orc, imp):
     for poses, detections in ((s.poses, 1), (near, 1), (far, 2), (s.poses, 3)):
         got = kept.contacts(_t(poses)).to_numpy()
         assert kept.detections == detections
-        compare_contacts(got, orc.detect(base, poses=poses), base, "fp64")
+        compare_contacts(got, orc.detect(base, poses=poses), base, "fp64", poses=poses)
 
 
 def test_newton_with_kept_candidates(m, ctx, imp):
