@@ -64,6 +64,11 @@ def _args():
     ap.add_argument("--chunk", type=int, default=65536,
                     help="scale workload: particle pairs per detection call")
     ap.add_argument("--particles", type=int, default=10000)
+    ap.add_argument("--host-trees", action="store_true",
+                    help="scale workload: build the surrogate trees on the host instead of the GPU")
+    ap.add_argument("--shapes", default=None,
+                    help="launch shapes instead of autotuning, e.g. level_warps=4,expand_items=8,"
+                         "node_threads=256,tile_warps=8,sweep_warps=2,exact_threads=64")
     return ap.parse_args()
 
 
@@ -549,7 +554,10 @@ def run_scale(args):
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     ctx = m.Context(0)
-    hier = m.Hierarchy.from_scene(ctx, s)
+    if args.host_trees:
+        hier = m.Hierarchy.from_scene(ctx, s)
+    else:
+        hier = m.Hierarchy.from_scene_device(ctx, s)
     build_s = time.perf_counter() - t0
     t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
     poses, mass, com = t(s.poses), t(s.mass), t(np.zeros((n, 3)))
@@ -605,7 +613,9 @@ def run_scale(args):
                                f"the radius, {achieved:.3f} volume fraction",
                    "particles": n, "triangles": int(np.diff(s.tri_off).sum()), "pairs": P,
                    "contacts": n_contacts, "chunk": args.chunk, "precision": args.precision},
-        "prep_s": {"generate": round(gen_s, 1), "trees": round(build_s, 1)},
+        "prep_s": {"generate": round(gen_s, 1), "trees": round(build_s, 1),
+                   "trees_where": "host" if args.host_trees else "device",
+                   "trees_device_ms": None if args.host_trees else round(hier.build_ms, 1)},
         "clocks": clk.summary(),
     }), flush=True)
     return 0
@@ -659,7 +669,11 @@ def main():
     contacts = prob.contacts
     # launch shapes for this GPU and batch size (untimed preparation)
     tuning = None
-    if not args.no_autotune:
+    if args.shapes:
+        kw = {k: int(v) for k, v in (kv.split("=") for kv in args.shapes.split(","))}
+        ctx.set_params(**kw)
+        tuning = {"chosen": kw, "given": True}
+    elif not args.no_autotune:
         t_tune = time.perf_counter()
         tuning = m.autotune(ctx, hier, prob.pairs, prob.eps, prob.poses, args.precision,
                             contacts=contacts)

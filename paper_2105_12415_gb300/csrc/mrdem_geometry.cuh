@@ -212,33 +212,44 @@ MRDEM_HD TriTriResult<T> tri_tri_distance_impl(const V3<T> P[3], const V3<T> Q[3
   TriTriResult<T> r;
   r.near_parallel = false;
   T w[3], t;
-  for (int i = 0; i < 3; ++i) {
-    int i1 = i == 2 ? 0 : i + 1;
-    if (segment_crosses(P[i], P[i1], Q[0], Q[1], Q[2], &t, w)) {
-      r.d = T(0);
-      r.pa = P[i] + t * (P[i1] - P[i]);
-      r.pb = r.pa;
-      r.wa[0] = r.wa[1] = r.wa[2] = T(0);
-      r.wa[i] = T(1) - t; r.wa[i1] = t;
-      r.wb[0] = w[0]; r.wb[1] = w[1]; r.wb[2] = w[2];
-      r.feature = 100 + i;
-      return r;
-    }
+  // the first crossing edge in the fixed order (P's edges, then Q's): its
+  // number c, parameter t and the crossed triangle's weights w
+  int c = -1;
+#ifdef __CUDA_ARCH__
+#pragma unroll
+#endif
+  for (int e = 0; e < 6; ++e) {
+    if (c >= 0) break;
+    const int i = e % 3, i1 = i == 2 ? 0 : i + 1;
+    const bool hit = e < 3 ? segment_crosses(P[i], P[i1], Q[0], Q[1], Q[2], &t, w)
+                           : segment_crosses(Q[i], Q[i1], P[0], P[1], P[2], &t, w);
+    if (hit) c = e;
   }
-  for (int j = 0; j < 3; ++j) {
-    int j1 = j == 2 ? 0 : j + 1;
-    if (segment_crosses(Q[j], Q[j1], P[0], P[1], P[2], &t, w)) {
-      r.d = T(0);
-      r.pb = Q[j] + t * (Q[j1] - Q[j]);
+  if (c >= 0) {
+    const int i = c % 3, i1 = i == 2 ? 0 : i + 1;
+    // weights of the crossing point on its edge: (1 - t) at vertex i, t at i1
+    const T e0 = i == 0 ? T(1) - t : (i1 == 0 ? t : T(0));
+    const T e1 = i == 1 ? T(1) - t : (i1 == 1 ? t : T(0));
+    const T e2 = i == 2 ? T(1) - t : (i1 == 2 ? t : T(0));
+    r.d = T(0);
+    if (c < 3) {
+      r.pa = pick3(P, i) + t * (pick3(P, i1) - pick3(P, i));
+      r.pb = r.pa;
+      r.wa[0] = e0; r.wa[1] = e1; r.wa[2] = e2;
+      r.wb[0] = w[0]; r.wb[1] = w[1]; r.wb[2] = w[2];
+    } else {
+      r.pb = pick3(Q, i) + t * (pick3(Q, i1) - pick3(Q, i));
       r.pa = r.pb;
-      r.wb[0] = r.wb[1] = r.wb[2] = T(0);
-      r.wb[j] = T(1) - t; r.wb[j1] = t;
+      r.wb[0] = e0; r.wb[1] = e1; r.wb[2] = e2;
       r.wa[0] = w[0]; r.wa[1] = w[1]; r.wa[2] = w[2];
-      r.feature = 103 + j;
-      return r;
     }
+    r.feature = 100 + c;
+    return r;
   }
   T best2 = T(INFINITY), sec2 = T(INFINITY);
+#ifdef __CUDA_ARCH__
+#pragma unroll
+#endif
   for (int k = 0; k < 3; ++k) {
     V3<T> q = closest_on_triangle(P[k], Q[0], Q[1], Q[2], w);
     V3<T> dv = P[k] - q;
@@ -251,6 +262,9 @@ MRDEM_HD TriTriResult<T> tri_tri_distance_impl(const V3<T> P[3], const V3<T> Q[3
       r.wb[0] = w[0]; r.wb[1] = w[1]; r.wb[2] = w[2];
     }
   }
+#ifdef __CUDA_ARCH__
+#pragma unroll
+#endif
   for (int k = 0; k < 3; ++k) {
     V3<T> p = closest_on_triangle(Q[k], P[0], P[1], P[2], w);
     V3<T> dv = p - Q[k];
@@ -263,9 +277,15 @@ MRDEM_HD TriTriResult<T> tri_tri_distance_impl(const V3<T> P[3], const V3<T> Q[3
       r.wa[0] = w[0]; r.wa[1] = w[1]; r.wa[2] = w[2];
     }
   }
+#ifdef __CUDA_ARCH__
+#pragma unroll
+#endif
   for (int i = 0; i < 3; ++i) {
     int i1 = i == 2 ? 0 : i + 1;
-    for (int j = 0; j < 3; ++j) {
+  #ifdef __CUDA_ARCH__
+#pragma unroll
+#endif
+  for (int j = 0; j < 3; ++j) {
       int j1 = j == 2 ? 0 : j + 1;
       T s, u;
       bool par;

@@ -241,39 +241,77 @@ __device__ __forceinline__ bool world_triangle(const HierDev& H, const double* p
   return true;
 }
 
-// A thread per contact: its 12x12 Hessian block (mrdem_step.cuh), added to
-// the pair's block with one atomic per entry.
-__global__ void __launch_bounds__(kThreads) k_hessian(HierDev H, const int32_t* ab,
-                                                      const double* eps, const double* poses,
-                                                      const double* mass, double k_s,
-                                                      mrdem_contacts c, int64_t n_pairs,
-                                                      double* blocks,
-                                                      unsigned long long* skipped) {
+// Contact Hessian blocks: a warp takes 32 contacts; each lane finds its
+// contact's closest points in FP64 and stores the block in compact form
+// (HessRep, mrdem_step.cuh) in shared memory; then the warp forms the blocks
+// entry by entry (a lane per entry, 144 = 4.5 x 32), summing runs of
+// contacts of the same pair (detection lists a pair's contacts together) in
+// registers and adding each run's sums to the pair's block with one atomic
+// per entry.
+constexpr int kHessWarps = 4;
+__global__ void __launch_bounds__(kHessWarps * 32) k_hessian(HierDev H, const int32_t* ab,
+                                                             const double* eps,
+                                                             const double* poses,
+                                                             const double* mass, double k_s,
+                                                             mrdem_contacts c, int64_t n_pairs,
+                                                             double* blocks,
+                                                             unsigned long long* skipped) {
   wait_prior_grid();
+  __shared__ HessRep rep[kHessWarps][32];
+  __shared__ int rpair[kHessWarps][32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t n = *c.count;
   if (n > c.capacity) n = c.capacity;
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const int64_t step = (int64_t)gridDim.x * kHessWarps * 32;
   unsigned long long parallel = 0;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += step) {
-    const int p = c.pair[k];
-    if (p < 0 || p >= n_pairs) continue;
-    const int A = ab[2 * p], B = ab[2 * p + 1];
-    if (A < 0 || A >= H.n_particles || B < 0 || B >= H.n_particles) continue;
-    V3<double> TA[3], TB[3], tA, tB;
-    if (!world_triangle(H, poses, A, c.tri_a[k], TA, &tA) ||
-        !world_triangle(H, poses, B, c.tri_b[k], TB, &tB))
-      continue;
-    const double mA = mass[A], mB = mass[B];
-    const double ks = k_s * sqrt(mA * mB / (mA + mB));
-    double h[144];
-    for (int q = 0; q < 144; ++q) h[q] = 0.0;
-    const int st = contact_hessian_block(TA, TB, tA, tB, ks, eps[p], h);
-    if (st == 0) {
-      double* o = blocks + 144 * (int64_t)p;
-      for (int q = 0; q < 144; ++q) atomicAdd(o + q, h[q]);
-    } else if (st == 2) {
-      ++parallel;
+  for (int64_t base = ((int64_t)blockIdx.x * kHessWarps + w) * 32; base < n; base += step) {
+    const int64_t k = base + lane;
+    int pr = -1;
+    if (k < n) {
+      const int p = c.pair[k];
+      if (p >= 0 && p < n_pairs) {
+        const int A = ab[2 * p], B = ab[2 * p + 1];
+        V3<double> TA[3], TB[3], tA, tB;
+        if (A >= 0 && A < H.n_particles && B >= 0 && B < H.n_particles &&
+            world_triangle(H, poses, A, c.tri_a[k], TA, &tA) &&
+            world_triangle(H, poses, B, c.tri_b[k], TB, &tB)) {
+          const double mA = mass[A], mB = mass[B];
+          const double ks = k_s * sqrt(mA * mB / (mA + mB));
+          const int st = contact_hessian_rep(TA, TB, tA, tB, ks, eps[p], &rep[w][lane]);
+          if (st == 0) pr = p;
+          else if (st == 2) ++parallel;
+        }
+      }
     }
+    rpair[w][lane] = pr;
+    __syncwarp();
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int cur = -1;
+    auto flush = [&]() {
+      double* o = blocks + 144 * (int64_t)cur;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        const int q = lane + 32 * m;
+        if (q < 144) atomicAdd(o + q, acc[m]);
+        acc[m] = 0.0;
+      }
+    };
+    for (int ci = 0; ci < 32; ++ci) {
+      const int p = rpair[w][ci];  // the same on every lane
+      if (p != cur) {
+        if (cur >= 0) flush();
+        cur = p;
+      }
+      if (p < 0) continue;
+      const HessRep& h = rep[w][ci];
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        const int q = lane + 32 * m;
+        if (q < 144) acc[m] += hessian_entry(h, q / 12, q % 12);
+      }
+    }
+    if (cur >= 0) flush();
+    __syncwarp();
   }
   if (skipped && parallel) atomicAdd(skipped, parallel);
 }
@@ -708,10 +746,11 @@ int launch_contact_hessian(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, c
                            cudaStream_t s) {
   if (n_pairs == 0 || con->capacity == 0) return MRDEM_OK;
   ProfScope ps(c, K_STEP, s);
-  const int64_t nb64 = (con->capacity + kThreads - 1) / kThreads;
-  const int64_t lim = (int64_t)c->n_sms * 8;
+  const int hb = kHessWarps * 32;
+  const int64_t nb64 = (con->capacity + hb - 1) / hb;
+  const int64_t lim = (int64_t)c->n_sms * 16;
   const int nb = (int)(nb64 < lim ? nb64 : lim);
-  launch_after(k_hessian, nb, kThreads, 0, s, h->dev, ab, eps, poses, mass, k_s, *con, n_pairs,
+  launch_after(k_hessian, nb, hb, 0, s, h->dev, ab, eps, poses, mass, k_s, *con, n_pairs,
                blocks, reinterpret_cast<unsigned long long*>(skipped));
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;

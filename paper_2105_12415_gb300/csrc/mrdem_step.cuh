@@ -319,94 +319,169 @@ namespace mrdem {
 // (no q) the translation block is e'' u u^T + e' (I - u u^T)/d.
 constexpr double kActiveTol = 1e-9;
 
-// Adds the 12x12 block of the contact between world triangles TA (on A) and
-// TB (on B) to out (row-major).  Returns 0 when added, 1 when the
-// triangles are more than 2 eps apart or cross (d = 0: not differentiable),
-// 2 when the active features are parallel (more than two free parameters or
-// a singular G G^T).
-MRDEM_HD int contact_hessian_block(const V3<double> TA[3], const V3<double> TB[3],
-                                   const V3<double>& tA, const V3<double>& tB, double ks,
-                                   double eps, double* out) {
+// A contact's Hessian block in compact form: the block's entries follow from
+// these (hessian_entry).  Rows of Z: z_i with (Z x)_i = z_i . x.
+struct HessRep {
+  double u[3], r[3];   // unit separation direction and r = pa - pb = d u
+  double rA[3], rB[3]; // rho_A = pa - t_A, rho_B = -(pb - t_B)
+  double G[2][3];      // directions of the free barycentric parameters
+  double K[3];         // (G G^T)^-1: K00, K01, K11
+  double a, b;         // e'' - e'/d and e'/d
+  double g[3];         // e' u
+  int nq;              // free parameters (0..2)
+  int own[2];          // particle of each (0: A, 1: B)
+};
+
+// Row z_i of Z = [I; [rho_A]x; -I; [rho_B]x] (12 x 3).
+MRDEM_HD void hess_zrow(const HessRep& h, int i, double z[3]) {
+  const int blk = i / 3, c = i % 3;
+  if (blk == 0 || blk == 2) {
+    const double one = blk == 0 ? 1.0 : -1.0;
+    z[0] = c == 0 ? one : 0.0;
+    z[1] = c == 1 ? one : 0.0;
+    z[2] = c == 2 ? one : 0.0;
+    return;
+  }
+  const double* q = blk == 1 ? h.rA : h.rB;
+  // row c of the cross-product matrix [q]x: (q x v)_c = z . v
+  if (c == 0) { z[0] = 0.0; z[1] = -q[2]; z[2] = q[1]; }
+  else if (c == 1) { z[0] = q[2]; z[1] = 0.0; z[2] = -q[0]; }
+  else { z[0] = -q[1]; z[1] = q[0]; z[2] = 0.0; }
+}
+
+// Entry i of N_k = Z G_k + (G_k x r in the rotation rows of its particle).
+MRDEM_HD double hess_n(const HessRep& h, int k, int i, const double z[3]) {
+  const double* G = h.G[k];
+  double v = z[0] * G[0] + z[1] * G[1] + z[2] * G[2];
+  const int o = h.own[k] ? 9 : 3;
+  if (i >= o && i < o + 3) {
+    const int m = i - o;
+    v += m == 0 ? G[1] * h.r[2] - G[2] * h.r[1]
+                : (m == 1 ? G[2] * h.r[0] - G[0] * h.r[2] : G[0] * h.r[1] - G[1] * h.r[0]);
+  }
+  return v;
+}
+
+// Entry (i, j) of the block:
+//   a (Zu)_i (Zu)_j + b (Z Z^T)_ij - b sum_kl N_k,i K_kl N_l,j
+//   + in the rotation blocks sym(g rho^T) - (g . rho) I.
+MRDEM_HD double hessian_entry(const HessRep& h, int i, int j) {
+  double zi[3], zj[3];
+  hess_zrow(h, i, zi);
+  hess_zrow(h, j, zj);
+  const double zui = zi[0] * h.u[0] + zi[1] * h.u[1] + zi[2] * h.u[2];
+  const double zuj = zj[0] * h.u[0] + zj[1] * h.u[1] + zj[2] * h.u[2];
+  double v = h.a * zui * zuj + h.b * (zi[0] * zj[0] + zi[1] * zj[1] + zi[2] * zj[2]);
+  if (h.nq > 0) {
+    const double ni0 = hess_n(h, 0, i, zi), nj0 = hess_n(h, 0, j, zj);
+    if (h.nq == 1) {
+      v -= h.b * ni0 * h.K[0] * nj0;
+    } else {
+      const double ni1 = hess_n(h, 1, i, zi), nj1 = hess_n(h, 1, j, zj);
+      v -= h.b * (ni0 * h.K[0] * nj0 + ni0 * h.K[1] * nj1 + ni1 * h.K[1] * nj0 +
+                  ni1 * h.K[2] * nj1);
+    }
+  }
+  const int bi = i / 3, bj = j / 3;
+  if (bi == bj && (bi == 1 || bi == 3)) {
+    const double* rho = bi == 1 ? h.rA : h.rB;
+    const int ii = i % 3, jj = j % 3;
+    v += 0.5 * (h.g[ii] * rho[jj] + h.g[jj] * rho[ii]);
+    if (ii == jj) v -= h.g[0] * rho[0] + h.g[1] * rho[1] + h.g[2] * rho[2];
+  }
+  return v;
+}
+
+// The compact block of the contact between world triangles TA (on A) and TB
+// (on B).  Returns 0 when the contact has a block, 1 when the triangles are
+// more than 2 eps apart or cross (d = 0: not differentiable), 2 when the
+// active features are parallel (more than two free parameters or a
+// singular G G^T).
+MRDEM_HD int contact_hessian_rep(const V3<double> TA[3], const V3<double> TB[3],
+                                 const V3<double>& tA, const V3<double>& tB, double ks,
+                                 double eps, HessRep* out) {
   typedef V3<double> D;
   const TriTriResult<double> t = tri_tri_distance<double>(TA, TB);
   if (!(t.d > 0.0) || t.d > 2.0 * eps) return 1;
-  int SA[3], SB[3], na = 0, nb = 0;
-  double sa = 0.0, sb = 0.0;
-  for (int i = 0; i < 3; ++i) {
-    if (t.wa[i] > kActiveTol) { SA[na++] = i; sa += t.wa[i]; }
-    if (t.wb[i] > kActiveTol) { SB[nb++] = i; sb += t.wb[i]; }
-  }
+  // active vertices of the two features (no array indexed by a variable, so
+  // that everything stays in registers)
+  const bool a0 = t.wa[0] > kActiveTol, a1 = t.wa[1] > kActiveTol, a2 = t.wa[2] > kActiveTol;
+  const bool b0 = t.wb[0] > kActiveTol, b1 = t.wb[1] > kActiveTol, b2 = t.wb[2] > kActiveTol;
+  const int na = (int)a0 + (int)a1 + (int)a2, nb = (int)b0 + (int)b1 + (int)b2;
   if (na == 0 || nb == 0) return 2;
   const int nq = (na - 1) + (nb - 1);
   if (nq > 2) return 2;
+  const double sa = (a0 ? t.wa[0] : 0.0) + (a1 ? t.wa[1] : 0.0) + (a2 ? t.wa[2] : 0.0);
+  const double sb = (b0 ? t.wb[0] : 0.0) + (b1 ? t.wb[1] : 0.0) + (b2 ? t.wb[2] : 0.0);
   D pa = {0.0, 0.0, 0.0}, pb = {0.0, 0.0, 0.0};
-  for (int k = 0; k < na; ++k) pa = pa + (t.wa[SA[k]] / sa) * TA[SA[k]];
-  for (int k = 0; k < nb; ++k) pb = pb + (t.wb[SB[k]] / sb) * TB[SB[k]];
+  if (a0) pa = pa + (t.wa[0] / sa) * TA[0];
+  if (a1) pa = pa + (t.wa[1] / sa) * TA[1];
+  if (a2) pa = pa + (t.wa[2] / sa) * TA[2];
+  if (b0) pb = pb + (t.wb[0] / sb) * TB[0];
+  if (b1) pb = pb + (t.wb[1] / sb) * TB[1];
+  if (b2) pb = pb + (t.wb[2] / sb) * TB[2];
   const D r = pa - pb;
   const double d = sqrt(dot(r, r));
   if (!(d > 0.0)) return 1;
   const D u = (1.0 / d) * r;
   const double e1 = -ks * (1.0 - d / (2.0 * eps)), e2 = ks / (2.0 * eps);
   const D rA = pa - tA, rB = -1.0 * (pb - tB);
-  // directions of the free parameters and the particle (0: A, 1: B) of each
-  D G[2];
-  int own[2];
+  // directions of the free parameters: edges from each feature's first
+  // active vertex to its other active vertices (minus for B's), in order
+  D G[2] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  int own[2] = {0, 0};
   int q = 0;
-  for (int k = 1; k < na; ++k, ++q) { G[q] = TA[SA[k]] - TA[SA[0]]; own[q] = 0; }
-  for (int k = 1; k < nb; ++k, ++q) { G[q] = -1.0 * (TB[SB[k]] - TB[SB[0]]); own[q] = 1; }
-  // (G G^T)^-1
-  double K[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  auto push = [&](const D& g, int o) {
+    if (q == 0) { G[0] = g; own[0] = o; }
+    else { G[1] = g; own[1] = o; }
+    ++q;
+  };
+  const D A0 = a0 ? TA[0] : (a1 ? TA[1] : TA[2]);
+  if (a1 && a0) push(TA[1] - A0, 0);
+  if (a2 && (a0 || a1)) push(TA[2] - A0, 0);
+  const D B0 = b0 ? TB[0] : (b1 ? TB[1] : TB[2]);
+  if (b1 && b0) push(-1.0 * (TB[1] - B0), 1);
+  if (b2 && (b0 || b1)) push(-1.0 * (TB[2] - B0), 1);
+  double K[3] = {0.0, 0.0, 0.0};
   if (nq == 1) {
     const double g11 = dot(G[0], G[0]);
     if (!(g11 > 0.0)) return 2;
-    K[0][0] = 1.0 / g11;
+    K[0] = 1.0 / g11;
   } else if (nq == 2) {
     const double g11 = dot(G[0], G[0]), g12 = dot(G[0], G[1]), g22 = dot(G[1], G[1]);
     const double det = g11 * g22 - g12 * g12;
     if (!(det > 1e-12 * g11 * g22)) return 2;
-    K[0][0] = g22 / det;
-    K[0][1] = K[1][0] = -g12 / det;
-    K[1][1] = g11 / det;
+    K[0] = g22 / det;
+    K[1] = -g12 / det;
+    K[2] = g11 / det;
   }
-  // Z x for a 3-vector x: a 12-vector
-  auto zmul = [&](const D& x, double* o) {
-    const D a = cross(rA, x), b = cross(rB, x);
-    o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = a.x; o[4] = a.y; o[5] = a.z;
-    o[6] = -x.x; o[7] = -x.y; o[8] = -x.z; o[9] = b.x; o[10] = b.y; o[11] = b.z;
-  };
-  double N[2][12];
-  for (int k = 0; k < nq; ++k) {
-    zmul(G[k], N[k]);
-    const D c = cross(G[k], r);
-    const int o = own[k] ? 9 : 3;
-    N[k][o] += c.x; N[k][o + 1] += c.y; N[k][o + 2] += c.z;
+  HessRep& h = *out;
+  h.u[0] = u.x; h.u[1] = u.y; h.u[2] = u.z;
+  h.r[0] = r.x; h.r[1] = r.y; h.r[2] = r.z;
+  h.rA[0] = rA.x; h.rA[1] = rA.y; h.rA[2] = rA.z;
+  h.rB[0] = rB.x; h.rB[1] = rB.y; h.rB[2] = rB.z;
+  for (int k = 0; k < 2; ++k) {
+    h.G[k][0] = G[k].x; h.G[k][1] = G[k].y; h.G[k][2] = G[k].z;
+    h.own[k] = own[k];
   }
-  // Z [(e'' - e'/d) u u^T + (e'/d) I] Z^T = a (Zu)(Zu)^T + b sum_c (Z e_c)(Z e_c)^T
-  double zu[12], ze[3][12];
-  zmul(u, zu);
-  zmul(D{1.0, 0.0, 0.0}, ze[0]);
-  zmul(D{0.0, 1.0, 0.0}, ze[1]);
-  zmul(D{0.0, 0.0, 1.0}, ze[2]);
-  const double a = e2 - e1 / d, b = e1 / d;
-  const D g = e1 * u;
+  for (int k = 0; k < 3; ++k) h.K[k] = K[k];
+  h.a = e2 - e1 / d;
+  h.b = e1 / d;
+  h.g[0] = e1 * u.x; h.g[1] = e1 * u.y; h.g[2] = e1 * u.z;
+  h.nq = nq;
+  return 0;
+}
+
+// Adds the 12x12 block of the contact between world triangles TA (on A) and
+// TB (on B) to out (row-major); the status of contact_hessian_rep.
+MRDEM_HD int contact_hessian_block(const V3<double> TA[3], const V3<double> TB[3],
+                                   const V3<double>& tA, const V3<double>& tB, double ks,
+                                   double eps, double* out) {
+  HessRep h;
+  const int st = contact_hessian_rep(TA, TB, tA, tB, ks, eps, &h);
+  if (st != 0) return st;
   for (int i = 0; i < 12; ++i)
-    for (int j = 0; j < 12; ++j) {
-      double h = a * zu[i] * zu[j] + b * (ze[0][i] * ze[0][j] + ze[1][i] * ze[1][j] +
-                                          ze[2][i] * ze[2][j]);
-      for (int k = 0; k < nq; ++k)
-        for (int l = 0; l < nq; ++l) h -= b * N[k][i] * K[k][l] * N[l][j];
-      out[12 * i + j] += h;
-    }
-  // second-order term of the exponential map in the rotation blocks
-  const D rho[2] = {rA, rB};
-  for (int p = 0; p < 2; ++p) {
-    const int o = p ? 9 : 3;
-    const double gr[3] = {g.x, g.y, g.z}, rr[3] = {rho[p].x, rho[p].y, rho[p].z};
-    const double gdr = dot(g, rho[p]);
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j)
-        out[12 * (o + i) + o + j] += 0.5 * (gr[i] * rr[j] + gr[j] * rr[i]) - (i == j ? gdr : 0.0);
-  }
+    for (int j = 0; j < 12; ++j) out[12 * i + j] += hessian_entry(h, i, j);
   return 0;
 }
 
