@@ -189,15 +189,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# the sources the detection kernels are built from (the traffic table's
+# kernels live in mrdem_detect.cu)
+TRAFFIC_SOURCES = ("mrdem_detect.cu", "mrdem_device.cuh", "mrdem_geometry.cuh", "mrdem_internal.h",
+                   "mrdem_dd.cuh")
+
+
 def _source_hash():
-    """Hash of the library's CUDA/C++ sources without their comments and
+    """Hash of the detection kernels' sources without their comments and
     blank lines (a traffic figure is valid only for the code it was measured
     on; comment edits do not change it)."""
     import re
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2105_12415_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+        if f in TRAFFIC_SOURCES:
             with open(os.path.join(d, f), encoding="utf-8") as fh:
                 src = fh.read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
@@ -502,6 +508,13 @@ def run_packing(args):
     m._lib.check(lib.mrdem_check(ctx.handle, None, None), "Newton iterations")
     newton_ms = a.elapsed_time(b) / Kn
     cg_it = float(info[0].item())
+    # where a Newton iteration's time goes (CUDA events around each call)
+    ctx.profile(True)
+    for _ in range(Kn):
+        newton_iter()
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    newton_parts = {k: round(v[0] / Kn, 4) for k, v in ctx.profile_read().items()}
 
     print(json.dumps({
         "metric": "implicit Euler step, packing: time per Picard iteration (pose update, "
@@ -519,7 +532,8 @@ def run_packing(args):
                    "wall_s": round(picard_s, 3),
                    "ms_per_iteration_kept_candidates": round(cached_ms, 4),
                    "kept_candidates": cand.n(), "margin_w": w},
-        "newton": {"ms_per_iteration": round(newton_ms, 4), "cg_iterations_last": cg_it,
+        "newton": {"ms_per_iteration": round(newton_ms, 4), "ms_parts": newton_parts,
+                   "cg_iterations_last": cg_it,
                    "iterations_to_1e-6": it_n, "wall_s": round(newton_s, 3),
                    "line_search_halvings": [st["halvings"] for st in nst]},
         "agree": float((Vp - Vn).abs().max().item() / Vp.abs().max().item()),
@@ -680,6 +694,8 @@ def main():
         tuning["s"] = round(time.perf_counter() - t_tune, 2)
         tuning["gain"] = tuning["ms_default"] / tuning["ms_tuned"]
 
+    side = torch.cuda.Stream()
+
     def step():
         s = _stream(None)
         cs = contacts.struct()
@@ -693,6 +709,9 @@ def main():
         m._lib.check(lib.mrdem_detect(ctx.handle, hier.handle, P, _p(prob.pairs), _p(prob.eps),
                                       _p(prob.poses), m.api.PRECISION[args.precision],
                                       C.byref(cs), _p(stats), s), "detect")
+        # forces and the adjoint both read the contacts: the adjoint runs on a
+        # second stream beside the forces
+        side.wait_stream(torch.cuda.current_stream())
         m._lib.check(lib.mrdem_contact_forces(ctx.handle, hier.handle, P, _p(prob.pairs),
                                               _p(prob.eps), _p(prob.poses), C.byref(cs),
                                               _p(prob.mass), _p(prob.com), 1000.0, _p(ft),
@@ -700,7 +719,8 @@ def main():
         m._lib.check(lib.mrdem_contact_grad(ctx.handle, hier.handle, P, _p(prob.pairs),
                                             _p(prob.eps), _p(prob.poses), C.byref(cs),
                                             _p(prob.mass), 1000.0, 1.0, _p(gv), _p(gp), _p(jac),
-                                            s), "grad")
+                                            C.c_void_p(side.cuda_stream)), "grad")
+        torch.cuda.current_stream().wait_stream(side)
 
     for _ in range(args.warmup):
         step()

@@ -394,6 +394,18 @@ int mrdem_broad_phase(mrdem_ctx* ctx, int32_t n, const double* poses, const doub
 int mrdem_move_poses(mrdem_ctx* ctx, int32_t n, const double* poses0, const double* vel,
                      double dt, double* poses, mrdem_stream stream);
 
+/* The chain rule of a pose twist (extension of the adjoint, no counterpart
+ * in the paper): for poses moved by twist [n*6] (device FP64: a world
+ * translation v and a rotation vector w per particle, the orientation turned
+ * on the left, as mrdem_move_poses with dt = 1), out [n*6] = the gradient of
+ * the energy in the twist, from grad_pose [n*6] = its gradient in a
+ * translation and a left rotation increment at the moved poses (what
+ * mrdem_contact_grad returns there): out = (g_t, J_l(w)^T g_r), J_l the left
+ * Jacobian of the rotation exponential.  out may alias grad_pose.  Errors:
+ * INVALID, CUDA. */
+int mrdem_twist_grad(mrdem_ctx* ctx, int32_t n, const double* twist, const double* grad_pose,
+                     double* out, mrdem_stream stream);
+
 /* One Picard update of the implicit Euler step (Algorithm 3): from the
  * contact forces and torques at the geometry moved by the guessed
  * velocities, new velocities
@@ -454,11 +466,10 @@ int mrdem_newton_residual(mrdem_ctx* ctx, int32_t n, const double* vel0, const d
  * (mrdem_contact_hessian's layout) placed at its two particles' twists,
  * by conjugate gradients with the diagonal as preconditioner (an entry that
  * is not positive uses M/dt instead), from x = 0, stopping when
- * |r| <= rel_tol |rhs| or after max_iter iterations.  With check_every = 0
- * every iteration is enqueued (no host synchronisation, capturable;
- * iterations after convergence do no work); with check_every = k > 0 the
- * call synchronises the stream every k iterations and stops enqueueing
- * once the solve has finished.  pair_ab int32 [n_pairs*2], blocks double [n_pairs*144], mass and
+ * |r| <= rel_tol |rhs| or after max_iter iterations.  The whole solve is
+ * one cooperative kernel launch that loops and stops on the device (no host
+ * synchronisation); check_every is accepted and ignored.  pair_ab int32
+ * [n_pairs*2], blocks double [n_pairs*144], mass and
  * inertia [n], rhs and x [n*6]: device.  info (device double [4]) receives
  * (iterations, |r|/|rhs|, 1 if p.Ap <= 0 stopped it (K not positive
  * definite enough; x is then the last iterate, or, when the first

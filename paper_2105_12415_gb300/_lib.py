@@ -119,6 +119,7 @@ SIGNATURES = {
     "mrdem_autotune": (C.c_int, [_P, _P, _I64, _P, _P, _P, _I, C.POINTER(mrdem_contacts), _I,
                                  _P, _P]),
     "mrdem_build_hierarchy_device": (C.c_int, [_P, _I, _P, _P, _P, _P, C.POINTER(_P), _P]),
+    "mrdem_twist_grad": (C.c_int, [_P, _I, _P, _P, _P, _P]),
     "mrdem_profile": (C.c_int, [_P, _I]),
     "mrdem_profile_read": (C.c_int, [_P, _I, C.POINTER(C.c_char_p), _P, _P, C.POINTER(_I)]),
 }

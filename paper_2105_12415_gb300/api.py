@@ -820,9 +820,19 @@ class ContactProblem:
     @classmethod
     def from_scene(cls, ctx, hier, scene, device, precision="fp32", k_s=1000.0):
         t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)  # noqa: E731
-        return cls(ctx, hier, t(scene.pairs, torch.int32), t(scene.eps, torch.float64),
+        prob = cls(ctx, hier, t(scene.pairs, torch.int32), t(scene.eps, torch.float64),
                    t(scene.poses, torch.float64), t(scene.mass, torch.float64),
                    t(scene.com, torch.float64), k_s, precision)
+        prob.set_mesh(scene.vert_off, t(scene.verts, torch.float32), scene.tri_off,
+                      t(scene.tris, torch.int32))
+        return prob
+
+    def set_mesh(self, vert_off, verts, tri_off, tris):
+        """The meshes the hierarchy was built from (host offsets, device
+        float32 vertices and int32 local triangles): ContactEnergy rebuilds
+        the trees from other vertex values with them."""
+        self.mesh = (np.ascontiguousarray(vert_off, np.int64), verts.contiguous(),
+                     np.ascontiguousarray(tri_off, np.int64), tris.contiguous())
 
     def detect(self, stats=None, check=True, stream=None):
         self.contacts, st = detect(self.ctx, self.hier, self.pairs, self.eps, self.poses,
@@ -868,13 +878,23 @@ class ContactProblem:
         h, c = self.hier.handle, self.ctx.handle
         L.check(lib.mrdem_detect(c, h, P, _p(self.pairs), _p(self.eps), _p(self.poses), prec,
                                  C.byref(cs), _p(stats), s), "mrdem_detect")
+        # forces and the adjoint both read the contacts: the adjoint runs on a
+        # second stream beside the forces (each call keeps its own tables)
+        want_grad = gv is not None or gp is not None or jac is not None
+        if want_grad:
+            side = getattr(self, "_side", None)
+            if side is None:
+                side = self._side = torch.cuda.Stream(device=self.pairs.device)
+            side.wait_stream(torch.cuda.current_stream())
         L.check(lib.mrdem_contact_forces(c, h, P, _p(self.pairs), _p(self.eps), _p(self.poses),
                                          C.byref(cs), _p(self.mass), _p(self.com), self.k_s,
                                          _p(ft), _p(energy), s), "mrdem_contact_forces")
-        if gv is not None or gp is not None or jac is not None:
+        if want_grad:
             L.check(lib.mrdem_contact_grad(c, h, P, _p(self.pairs), _p(self.eps), _p(self.poses),
                                            C.byref(cs), _p(self.mass), self.k_s, float(scale),
-                                           _p(gv), _p(gp), _p(jac), s), "mrdem_contact_grad")
+                                           _p(gv), _p(gp), _p(jac), C.c_void_p(side.cuda_stream)),
+                    "mrdem_contact_grad")
+            torch.cuda.current_stream().wait_stream(side)
 
     def _check_and_grow(self):
         """Status of the work just enqueued (synchronises the stream): True if
@@ -934,33 +954,69 @@ class ContactProblem:
         raise L.MrdemError(L.MRDEM_ERR_CAPACITY, "ContactProblem.step (retries exhausted)")
 
 
-class ContactEnergy(torch.autograd.Function):
-    """E = sum over contacts of K_s sqrt(mu) eps (1 - d/(2 eps))^2.
+def twist_grad(ctx: Context, twist, grad_pose, out=None, stream=None):
+    """Gradient in the twist of poses moved by it (mrdem_twist_grad)."""
+    n = twist.shape[0]
+    _need(twist, torch.float64, (n, 6), "twist")
+    _need(grad_pose, torch.float64, (n, 6), "grad_pose")
+    if out is None:
+        out = torch.empty_like(grad_pose)
+    L.check(L.load().mrdem_twist_grad(ctx.handle, n, _p(twist), _p(grad_pose), _p(out),
+                                      _stream(stream)), "mrdem_twist_grad")
+    return out
 
-    Inputs: verts (float32 [n_verts, 3], the hierarchy's body-frame vertices;
-    their values are not re-read: the detection uses the hierarchy) and twist
-    (float64 [n_particles, 6], zeros: a world translation and rotation
-    increment about each particle origin).  Backward returns dE/dverts and
-    dE/dtwist at twist = 0, computed by the adjoint kernel."""
+
+class ContactEnergy(torch.autograd.Function):
+    """E(verts, twist) = sum over the contacts of K_s sqrt(mu) eps (1 - d/(2 eps))^2
+    at the geometry the two inputs give.
+
+    verts: body-frame vertices [n_verts, 3] (float32 or float64; the meshes are
+    their float32 values, as the library stores every mesh).  twist: [n, 6]
+    float64, per particle a world translation v and a rotation vector w: the
+    pose moves to centre + v and orientation exp(w) R (mrdem_move_poses with
+    dt = 1).  Forward: when verts differ from the problem's meshes, the
+    surrogate trees are rebuilt from them on the GPU
+    (mrdem_build_hierarchy_device), then the poses are moved, the contacts
+    detected and the energy summed.  Backward: the adjoint kernel at that
+    geometry gives dE/dverts and dE/dpose (a translation and a left rotation
+    increment about each particle origin); the rotation part goes through the
+    exponential map's left Jacobian (mrdem_twist_grad)."""
 
     @staticmethod
     def forward(fctx, verts, twist, problem: ContactProblem):
-        problem.detect()
-        _, energy = problem.forces()
-        fctx.problem = problem
+        ctx = problem.ctx
+        hier = problem.hier
+        v32 = verts.detach().to(torch.float32).contiguous()
+        mesh = getattr(problem, "mesh", None)
+        if mesh is None or not torch.equal(v32, mesh[1]):
+            if mesh is None:
+                raise ValueError("ContactEnergy: the problem has no meshes (set_mesh) to "
+                                 "rebuild the trees from new vertices")
+            hier = Hierarchy.build_device(ctx, mesh[0], v32, mesh[2], mesh[3])
+        tw = twist.detach().to(torch.float64).contiguous()
+        poses = move_poses(ctx, problem.poses, tw, 1.0)
+        contacts, _ = detect(ctx, hier, problem.pairs, problem.eps, poses, problem.precision)
+        _, energy = contact_forces(ctx, hier, problem.pairs, problem.eps, poses, contacts,
+                                   problem.mass, problem.com, problem.k_s)
+        fctx.state = (hier, poses, contacts, tw, problem, verts.dtype)
         return energy[0].clone()
 
     @staticmethod
     def backward(fctx, g):
-        gv, gp, _ = fctx.problem.grad(scale=float(g.item()))
-        return gv, gp, None
+        hier, poses, contacts, tw, problem, vdtype = fctx.state
+        gv, gp, _ = contact_grad(problem.ctx, hier, problem.pairs, problem.eps, poses, contacts,
+                                 problem.mass, problem.k_s, float(g.item()))
+        gt = twist_grad(problem.ctx, tw, gp)
+        return gv.to(vdtype), gt, None
 
 
 def contact_energy(problem: ContactProblem, verts=None, twist=None):
+    """ContactEnergy at the problem's meshes and poses (or the given ones),
+    with the inputs returned as leaves that require gradients."""
     info = problem.hier.info()
     d = problem.pairs.device
     if verts is None:
-        verts = torch.zeros((info["n_verts"], 3), dtype=torch.float32, device=d, requires_grad=True)
+        verts = problem.mesh[1].clone().requires_grad_(True)
     if twist is None:
         twist = torch.zeros((info["n_particles"], 6), dtype=torch.float64, device=d,
                             requires_grad=True)

@@ -196,6 +196,7 @@ int mrdem_destroy(mrdem_ctx* c) {
   cudaFree(c->cg_mem);
   cudaFree(c->refine_mem);
   cudaFree(c->frames);
+  cudaFree(c->frames_grad);
   cudaFree(c->counters);
   cudaFree(c->status);
   delete c;
@@ -283,9 +284,9 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
   size_t sz_slot = al(sizeof(int32_t) * stride), sz_ts = al(sizeof(int32_t) * h.n_tri);
   size_t sz_off = al(sizeof(int64_t) * (h.n_particles + 1));
   size_t sz_root = al(sizeof(int32_t) * h.n_particles), sz_br = al(sizeof(float) * h.n_particles);
-  size_t sz_box = al(sizeof(float4) * 4 * h.n_nodes);
+  size_t sz_box = al(sizeof(float4) * 4 * h.n_nodes), sz_boxw = al(sizeof(float4) * h.n_nodes);
   size_t total = sz_geo + sz_child + sz_tri + sz_vid + sz_slot + sz_ts + sz_off + sz_root + sz_br +
-                 sz_sph + sz_nrm + sz_tsph + sz_box;
+                 sz_sph + sz_nrm + sz_tsph + sz_box + sz_boxw;
   char* base = nullptr;
   if (cudaMalloc(&base, total) != cudaSuccess) {
     cudaGetLastError();
@@ -298,6 +299,7 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     size_t o_slot = o_vid + sz_vid, o_ts = o_slot + sz_slot, o_off = o_ts + sz_ts;
     size_t o_root = o_off + sz_off, o_br = o_root + sz_root, o_sph = o_br + sz_br;
     size_t o_nrm = o_sph + sz_sph, o_tsph = o_nrm + sz_nrm, o_box = o_tsph + sz_tsph;
+    size_t o_boxw = o_box + sz_box;
     float4* geo = (float4*)(p + o_geo);
     for (int64_t n = 0; n < h.n_nodes; ++n) {
       const float* t = &h.node_tri[9 * n];
@@ -347,12 +349,30 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     }
     // oriented boxes: (c.xyz, h0) (u0.xyz, h1) (u1.xyz, h2) (u2.xyz, 0)
     float4* box = (float4*)(p + o_box);
+    float4* boxw = (float4*)(p + o_boxw);
     for (int64_t n = 0; n < h.n_nodes; ++n) {
       const float* b = &h.node_box[16 * n];
       box[4 * n + 0] = make_float4(b[0], b[1], b[2], b[12]);
       box[4 * n + 1] = make_float4(b[3], b[4], b[5], b[13]);
       box[4 * n + 2] = make_float4(b[6], b[7], b[8], b[14]);
       box[4 * n + 3] = make_float4(b[9], b[10], b[11], 0.f);
+      // half width along each own axis u_s: sum_k h_k |u_s . u_k| of the
+      // stored float values, in double, rounded up (1 + 1e-12 covers the
+      // double rounding)
+      float w[3];
+      for (int a = 0; a < 3; ++a) {
+        double acc = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          const double dk = (double)b[3 + 3 * a] * b[3 + 3 * k] + (double)b[4 + 3 * a] * b[4 + 3 * k] +
+                            (double)b[5 + 3 * a] * b[5 + 3 * k];
+          acc += (double)b[12 + k] * std::fabs(dk);
+        }
+        acc *= 1.0 + 1e-12;
+        float f = (float)acc;
+        if ((double)f < acc) f = std::nextafter(f, INFINITY);
+        w[a] = f;
+      }
+      boxw[n] = make_float4(w[0], w[1], w[2], 0.f);
     }
     std::memcpy(p + o_child, h.node_child.data(), sizeof(int32_t) * 2 * h.n_nodes);
     float* tri = (float*)(p + o_tri);
@@ -403,6 +423,7 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     d.node_nrm = (const float4*)(base + o_nrm);
     d.tri_sph = (const float4*)(base + o_tsph);
     d.node_box = (const float4*)(base + o_box);
+    d.node_boxw = (const float4*)(base + o_boxw);
     d.stride = stride;
     d.n_tri = h.n_tri;
     d.n_particles = h.n_particles;
@@ -630,6 +651,14 @@ int mrdem_move_poses(mrdem_ctx* c, int32_t n, const double* poses0, const double
   return launch_move_poses(c, n, poses0, vel, dt, poses, (cudaStream_t)s);
 }
 
+int mrdem_twist_grad(mrdem_ctx* c, int32_t n, const double* twist, const double* grad_pose,
+                     double* out, mrdem_stream s) {
+  if (!c || n < 0) return MRDEM_ERR_INVALID;
+  if (n > 0 && (!twist || !grad_pose || !out)) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_twist_grad(c, n, twist, grad_pose, out, (cudaStream_t)s);
+}
+
 int mrdem_picard_update(mrdem_ctx* c, int32_t n, const double* vel0, const double* force_torque,
                         const double* mass, const double* inertia, const double* gravity,
                         double dt, double* vel, double* norms, mrdem_stream s) {
@@ -725,7 +754,7 @@ int mrdem_motion_bound(mrdem_ctx* c, int32_t n, const double* poses_ref, const d
 static const char* kKernelNames[K_COUNT] = {
     "k_setup", "k_expand", "k_sweep_nodes", "k_tile",  "k_sweep_fine", "k_exact",
     "k_exact64", "k_forces", "k_grad",       "k_plain", "k_tridist", "k_sort",
-    "k_merge", "k_broad", "k_step"};
+    "k_merge", "k_broad", "k_step", "k_hessian", "k_cg"};
 
 int mrdem_profile(mrdem_ctx* c, int32_t enable) {
   if (!c) return MRDEM_ERR_INVALID;

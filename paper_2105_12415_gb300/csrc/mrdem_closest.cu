@@ -204,29 +204,25 @@ __global__ void __launch_bounds__(256) k_cp_items(const AccRec* __restrict__ acc
   }
 }
 
-// The result of an accepted pair: its first crossing in the fixed order, else
-// the first smallest sub-test (point-triangle items before edge-edge items,
-// each in feature order), as in tri_tri_distance.
-__device__ __forceinline__ const ItemRes* best_item(const AccRec& r, const ItemRes* res_pt,
-                                                    const ItemRes* res_ee, const ItemRes* res_cx) {
-  int npt = r.counts & 0xff, nee = (r.counts >> 8) & 0xff, ncx = (r.counts >> 16) & 0xff;
-  for (int q = 0; q < ncx; ++q) {
-    const ItemRes* x = res_cx + r.cx_begin + q;
-    if (x->d2.hi == 0.f) return x;
-  }
-  const ItemRes* best = nullptr;
-  for (int q = 0; q < npt; ++q) {
-    const ItemRes* x = res_pt + r.pt_begin + q;
-    if (!best || x->d2 < best->d2) best = x;
-  }
-  for (int q = 0; q < nee; ++q) {
-    const ItemRes* x = res_ee + r.ee_begin + q;
-    if (!best || x->d2 < best->d2) best = x;
-  }
-  return best;
+// Exact pass: contacts of the accepted candidates.  Eight lanes per
+// accepted pair take its work items in the fixed order (crossings, then
+// point-triangle, then edge-edge items) and reduce them to the pair's
+// result: the first crossing that crossed, else the first smallest squared
+// distance (so a pair's item results are read side by side, not one after
+// another).  This is the choice of tri_tri_distance: a crossing in
+// the fixed order ends the test, else the first minimum wins.
+constexpr int kSelLanes = 8;
+struct SelBest {
+  int cls;    // 0: a crossing, 1: a distance, 2: none
+  int order;  // position in the fixed order
+  dd d2;
+};
+__device__ __forceinline__ bool sel_better(const SelBest& a, const SelBest& b) {
+  if (a.cls != b.cls) return a.cls < b.cls;
+  if (a.cls == 1 && !(a.d2 == b.d2)) return a.d2 < b.d2;
+  return a.order < b.order;
 }
 
-// Exact pass: contacts of the accepted candidates.
 __global__ void __launch_bounds__(256) k_select_exact(HierDev H, const PairXfDD* __restrict__ xfdd,
                                                       const AccRec* __restrict__ acc,
                                                       const ItemRes* __restrict__ res_pt,
@@ -240,25 +236,64 @@ __global__ void __launch_bounds__(256) k_select_exact(HierDev H, const PairXfDD*
   int64_t n = (int64_t)cnt[CNT_ACC];
   if (n > cap_acc) n = cap_acc;
   WarpCount ncon;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-    int64_t k = base + threadIdx.x;
+  const int lane = lane_id(), g = lane / kSelLanes, gl = lane % kSelLanes;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x / kSelLanes;
+  for (int64_t kb = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / kSelLanes; kb < n;
+       kb += stride) {
+    const int64_t k = kb + g;
     bool hit = false;
     int3 c = make_int3(0, 0, 0);
     double d = 0;
     D3 pa = {0, 0, 0}, pb = {0, 0, 0};
+    SelBest best = {2, 1 << 30, dd(INFINITY)};
+    int npt = 0, nee = 0, ncx = 0, ptb = 0, eeb = 0, cxb = 0;
     if (k < n) {
       const AccRec& r = acc[k];
-      const ItemRes* b = best_item(r, res_pt, res_ee, res_cx);
-      if (b) {
-        d = ldexp(to_double(dd_sqrt(b->d2)), r.g.k);
-        hit = d <= r.g.tau;
-        if (hit) {
-          c = cands[r.entry];
-          const PairXfDD& X = xfdd[r.pair];
-          pa = world_point(X, b->pa, r.g.k, r.g.o);
-          pb = world_point(X, b->pb, r.g.k, r.g.o);
+      npt = r.counts & 0xff;
+      nee = (r.counts >> 8) & 0xff;
+      ncx = (r.counts >> 16) & 0xff;
+      ptb = r.pt_begin;
+      eeb = r.ee_begin;
+      cxb = r.cx_begin;
+      for (int t = gl; t < ncx + npt + nee; t += kSelLanes) {
+        SelBest cand;
+        cand.order = t;
+        if (t < ncx) {
+          const ItemRes* x = res_cx + cxb + t;
+          cand.d2 = x->d2;
+          cand.cls = cand.d2.hi == 0.f ? 0 : 2;
+        } else {
+          const int q = t - ncx;
+          const ItemRes* x = q < npt ? res_pt + ptb + q : res_ee + eeb + (q - npt);
+          cand.d2 = x->d2;
+          cand.cls = 1;
         }
+        if (sel_better(cand, best)) best = cand;
+      }
+    }
+    // the group's best (lanes of a group share one pair)
+#pragma unroll
+    for (int o = kSelLanes / 2; o > 0; o >>= 1) {
+      SelBest other;
+      other.cls = __shfl_xor_sync(0xffffffffu, best.cls, o);
+      other.order = __shfl_xor_sync(0xffffffffu, best.order, o);
+      other.d2.hi = __shfl_xor_sync(0xffffffffu, best.d2.hi, o);
+      other.d2.lo = __shfl_xor_sync(0xffffffffu, best.d2.lo, o);
+      if (sel_better(other, best)) best = other;
+    }
+    if (k < n && gl == 0 && best.cls < 2) {
+      const AccRec& r = acc[k];
+      const int t = best.order;
+      const ItemRes* b = t < ncx ? res_cx + cxb + t
+                                 : (t - ncx < npt ? res_pt + ptb + (t - ncx)
+                                                  : res_ee + eeb + (t - ncx - npt));
+      d = ldexp(to_double(dd_sqrt(b->d2)), r.g.k);
+      hit = d <= r.g.tau;
+      if (hit) {
+        c = cands[r.entry];
+        const PairXfDD& X = xfdd[r.pair];
+        pa = world_point(X, b->pa, r.g.k, r.g.o);
+        pb = world_point(X, b->pb, r.g.k, r.g.o);
       }
     }
     ncon.add(hit);
@@ -286,7 +321,8 @@ int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts
                c->res_ee, c->counters);
   launch_after(k_cp_items<2>, ib, 256, 0, s, c->acc, c->items_cx, (int)CNT_CX, c->cap_items,
                c->res_cx, c->counters);
-  launch_after(k_select_exact, eb, threads, 0, s, hier->dev, c->xfdd, c->acc, c->res_pt,
+  // eight lanes per accepted pair: eight times the blocks
+  launch_after(k_select_exact, eb * kSelLanes, threads, 0, s, hier->dev, c->xfdd, c->acc, c->res_pt,
                c->res_ee, c->res_cx, c->cands, c->counters, c->cap_cands, c->status, *out,
                c->pair_cnt);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;

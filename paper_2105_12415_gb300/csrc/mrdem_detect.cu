@@ -248,8 +248,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
         // apart (plus the pair's rounding margin): no fine pair below them
         // can be a contact
         if (keep) {
-          boxed = boxes_apart(load_box(H, o.y + i), move_box(X, load_box(H, o.z + j)),
-                              X.tau + X.margin);
+          boxed = boxes_apart_w(load_box(H, o.y + i), __ldg(H.node_boxw + o.y + i),
+                                move_box(X, load_box(H, o.z + j)), __ldg(H.node_boxw + o.z + j),
+                                X.tau + X.margin);
           keep = !boxed;
         }
       }
@@ -503,15 +504,19 @@ __global__ void __launch_bounds__(WARPS * 32) k_sweep_fine(
     cq.push(s, make_int3(e.x, e.y, e.z), cands, cnt + CNT_CANDS, cap_cands, status + ST_REQ_CANDS);
   };
   const int64_t step = (int64_t)gridDim.x * WARPS * 32;
-  for (int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 32; base < n; base += step) {
+  int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 32;
+  // the next round's entry is loaded a round ahead, so that a round's
+  // gathers (transform, triangles) start at once
+  int4 nxt = base + lane < n ? fine[base + lane] : make_int4(0, 0, 0, 0);
+  for (; base < n; base += step) {
     const int64_t k = base + lane;
     const bool act = k < n;
     bool need = false;
-    int4 e = make_int4(0, 0, 0, 0);
+    const int4 e = nxt;
+    if (k + step < n) nxt = fine[k + step];
     F3 p0, p1, p2, q0, q1, q2;
     float thr = 0.f, ce = 0.f;
     if (act) {
-      e = fine[k];
       PairXf X;
       load_pairxf(xf, e.x, X);
       ce = conv_c * (float)__ldg(eps_d + e.x);

@@ -154,25 +154,38 @@ __device__ __forceinline__ NodeBox move_box(const PairXf& X, const NodeBox& b) {
   }
   return o;
 }
-// Half width of a box along an axis a: sum_k h_k |a . u_k|.
-__device__ __forceinline__ float box_half_width(const NodeBox& b, F3 a) {
-  float r = 0.f;
-  for (int k = 0; k < 3; ++k)
-    r = fmaf(b.h[k], fabsf(fmaf(a.x, b.u[k].x, fmaf(a.y, b.u[k].y, a.z * b.u[k].z))), r);
-  return r;
-}
-// True when one of the six face axes separates the two boxes (same frame)
-// by more than gap: along that axis the centres are farther apart than the
-// two half widths plus gap, so no point of one box comes within gap of the
-// other (a separating-axis test; conservative for any choice of axes).
-__device__ __forceinline__ bool boxes_apart(const NodeBox& A, const NodeBox& B, float gap) {
+// Separating-axis test of two oriented boxes (same frame: A's box, and B's
+// moved into A's frame): along each of the six face axes a, the centres are
+// farther apart than the two half widths plus gap (a box's half width along
+// a is sum_k h_k |a . u_k|), so no point of one box comes within gap of the
+// other.  Each box's half widths along its own axes come from node_boxw
+// (wa, wb: rotation-invariant, so B's unmoved values hold; they differ from
+// the moved axes' float dot products far inside the pair's rounding
+// margin); the nine products of the two axis sets serve both sides' other
+// half widths.  True when one face axis separates the boxes by more than
+// gap.
+__device__ __forceinline__ bool boxes_apart_w(const NodeBox& A, float4 wa, const NodeBox& B,
+                                              float4 wb, float gap) {
   const F3 d = {B.c.x - A.c.x, B.c.y - A.c.y, B.c.z - A.c.z};
+  float M[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      M[i][k] = fabsf(fmaf(A.u[i].x, B.u[k].x, fmaf(A.u[i].y, B.u[k].y, A.u[i].z * B.u[k].z)));
+  const float wA[3] = {wa.x, wa.y, wa.z}, wB[3] = {wb.x, wb.y, wb.z};
   bool apart = false;
 #pragma unroll
-  for (int s = 0; s < 6; ++s) {
-    const F3 a = s < 3 ? A.u[s] : B.u[s - 3];
-    const float dist = fabsf(fmaf(a.x, d.x, fmaf(a.y, d.y, a.z * d.z)));
-    apart = apart || dist > box_half_width(A, a) + box_half_width(B, a) + gap;
+  for (int i = 0; i < 3; ++i) {
+    const float dist = fabsf(fmaf(A.u[i].x, d.x, fmaf(A.u[i].y, d.y, A.u[i].z * d.z)));
+    const float hw = fmaf(B.h[2], M[i][2], fmaf(B.h[1], M[i][1], B.h[0] * M[i][0]));
+    apart = apart || dist > wA[i] + hw + gap;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float dist = fabsf(fmaf(B.u[k].x, d.x, fmaf(B.u[k].y, d.y, B.u[k].z * d.z)));
+    const float hw = fmaf(A.h[2], M[2][k], fmaf(A.h[1], M[1][k], A.h[0] * M[0][k]));
+    apart = apart || dist > hw + wB[k] + gap;
   }
   return apart;
 }

@@ -363,31 +363,36 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
 
 }  // namespace
 
-static int ensure_tables(mrdem_ctx* c, int64_t n, int64_t n_pairs, Tables* T) {
+// Forces and the adjoint keep their tables in separate buffers (which = 0
+// or 1), so that the two calls may run concurrently on two streams.
+static int ensure_tables(mrdem_ctx* c, int which, int64_t n, int64_t n_pairs, Tables* T) {
   // doubles: frames, then pair constants (2 each); floats after them
   const int64_t nd = kFrame * n + 2 * n_pairs, nf = kFrameF * n;
   const int64_t need = nd + (nf + 1) / 2;
-  if (need > c->cap_frames) {
-    cudaFree(c->frames);
-    c->frames = nullptr;
-    c->cap_frames = 0;
-    if (cudaMalloc(&c->frames, sizeof(double) * need) != cudaSuccess) {
+  double*& buf = which ? c->frames_grad : c->frames;
+  int64_t& cap = which ? c->cap_frames_grad : c->cap_frames;
+  if (need > cap) {
+    cudaFree(buf);
+    buf = nullptr;
+    cap = 0;
+    if (cudaMalloc(&buf, sizeof(double) * need) != cudaSuccess) {
       cudaGetLastError();
       return MRDEM_ERR_OOM;
     }
-    c->cap_frames = need;
+    cap = need;
   }
-  T->fr = c->frames;
-  T->pc = reinterpret_cast<double2*>(c->frames + kFrame * n);
-  T->frf = reinterpret_cast<float*>(c->frames + nd);
+  T->fr = buf;
+  T->pc = reinterpret_cast<double2*>(buf + kFrame * n);
+  T->frf = reinterpret_cast<float*>(buf + nd);
   return MRDEM_OK;
 }
 
-static int launch_tables(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
-                         const double* eps, const double* poses, const double* mass,
-                         const double* com, double k_s, Tables* T, cudaStream_t s) {
+static int launch_tables(mrdem_ctx* c, int which, const mrdem_hier* hier, int64_t n_pairs,
+                         const int32_t* ab, const double* eps, const double* poses,
+                         const double* mass, const double* com, double k_s, Tables* T,
+                         cudaStream_t s) {
   int n = hier->dev.n_particles;
-  int st = ensure_tables(c, n, n_pairs, T);
+  int st = ensure_tables(c, which, n, n_pairs, T);
   if (st) return st;
   int64_t m = std::max<int64_t>(n, n_pairs);
   if (m > 0)
@@ -403,7 +408,7 @@ int launch_forces(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
   if (!ft && !energy) return MRDEM_OK;
   ProfScope ps(c, K_FORCES, s);
   Tables T;
-  int st = launch_tables(c, hier, n_pairs, ab, eps, poses, mass, com, k_s, &T, s);
+  int st = launch_tables(c, 0, hier, n_pairs, ab, eps, poses, mass, com, k_s, &T, s);
   if (st) return st;
   launch_after(k_forces, c->n_sms * 16, kForceThreads, 0, s, hier->dev, ab, eps, *con,
                (const double2*)T.pc, (const double*)T.fr, ft, energy, n_pairs);
@@ -418,7 +423,7 @@ int launch_grad(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int
   if (n_pairs == 0) return MRDEM_OK;
   ProfScope ps(c, K_GRAD, s);
   Tables T;
-  int st = launch_tables(c, hier, n_pairs, ab, eps, poses, mass, nullptr, k_s, &T, s);
+  int st = launch_tables(c, 1, hier, n_pairs, ab, eps, poses, mass, nullptr, k_s, &T, s);
   if (st) return st;
   launch_after(k_grad, c->n_sms * 16, kGradThreads, 0, s, hier->dev, ab, eps, (const double*)T.fr,
                (const float*)T.frf, (const double2*)T.pc, *con, scale, dverts, dpose, jac,

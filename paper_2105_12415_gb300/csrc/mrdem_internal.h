@@ -47,6 +47,8 @@ struct HierDev {
   const float4* tri_sph;   // [stride]: body-frame bounding sphere of each fine triangle
   const float4* node_box;  // [n_nodes*4]: oriented box around the node's fine vertices,
                            // (c.xyz, h0) (u0.xyz, h1) (u1.xyz, h2) (u2.xyz, 0)
+  const float4* node_boxw; // [n_nodes]: the box's half widths along its own three axes,
+                           // sum_k h_k |u_s . u_k| (FP64 of the float axes, rounded up), 0
   const int32_t* vid;      // 3 planes: global vertex index of corner k of slot s
   const int32_t* slot_tri; // [stride] local input triangle index (-1 pad)
   const int32_t* tri_slot; // [n_tri] global input triangle -> slot
@@ -168,7 +170,7 @@ constexpr int kSizeClasses = 4;  // particle pairs per call: < 256, < 4096, < 65
 inline int size_class(int64_t n_pairs) {
   return n_pairs < 256 ? 0 : n_pairs < 4096 ? 1 : n_pairs < 65536 ? 2 : 3;
 }
-enum KernelId : int { K_SETUP = 0, K_LEVEL, K_SWEEP_NODES, K_TILE, K_SWEEP_FINE, K_EXACT, K_EXACT64, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_SORT, K_MERGE, K_BROAD, K_STEP, K_COUNT };
+enum KernelId : int { K_SETUP = 0, K_LEVEL, K_SWEEP_NODES, K_TILE, K_SWEEP_FINE, K_EXACT, K_EXACT64, K_FORCES, K_GRAD, K_PLAIN, K_TRIDIST, K_SORT, K_MERGE, K_BROAD, K_STEP, K_HESSIAN, K_CG, K_COUNT };
 struct ProfRec {
   int kernel;
   cudaEvent_t a, b;
@@ -224,6 +226,8 @@ struct mrdem_ctx {
   size_t cap_refine = 0;
   double* frames = nullptr;  // [cap_frames * 16]: per particle R (9), t (3), world com (3)
   int64_t cap_frames = 0;
+  double* frames_grad = nullptr;  // the adjoint's own tables (it may run beside the forces)
+  int64_t cap_frames_grad = 0;
   unsigned long long* counters = nullptr;  // [CNT_TOTAL]
   unsigned long long* status = nullptr;    // [ST_TOTAL]
   // resident blocks per SM of each kernel instance and block shape, filled
@@ -311,6 +315,8 @@ int launch_broad_phase(mrdem_ctx* ctx, int32_t n, const double* poses, const dou
                        int64_t cap, int64_t* count, cudaStream_t s);
 int launch_move_poses(mrdem_ctx* ctx, int32_t n, const double* poses0, const double* vel,
                       double dt, double* poses, cudaStream_t s);
+int launch_twist_grad(mrdem_ctx* ctx, int32_t n, const double* twist, const double* g,
+                      double* out, cudaStream_t s);
 int launch_picard_update(mrdem_ctx* ctx, int32_t n, const double* vel0, const double* ft,
                          const double* mass, const double* inertia, const double* gravity,
                          double dt, double* vel, double* norms, cudaStream_t s);

@@ -20,10 +20,13 @@
 //                 offset and sorts them by j, so the list is ordered by (i, j)
 //                 whatever order the atomics grouped the buckets in.
 // The particles' own FP64 arithmetic lives in mrdem_step.cuh.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "mrdem_device.cuh"
 #include "mrdem_step.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace mrdem {
 
@@ -131,51 +134,93 @@ __global__ void __launch_bounds__(kThreads) k_bp_scatter(BroadIn in, const Broad
   }
 }
 
+// Candidates per particle: a warp per particle, its lanes sharing the
+// particle's cells (a big particle's search box holds many cells of the
+// small particles' grids).
 __global__ void __launch_bounds__(kThreads) k_bp_count(BroadIn in, const BroadGrid* grid,
                                                        BroadWork w, int32_t* cnt) {
   wait_prior_grid();
   const BroadGrid g = *grid;
-  const int32_t step = gridDim.x * blockDim.x;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += step)
-    cnt[i] = g.bad ? 0 : bp_visit(in, g, w, i, [](int32_t, double) {});
+  const int lane = threadIdx.x & 31;
+  const int32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (int32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < in.n; i += warps) {
+    int32_t c = g.bad ? 0 : bp_visit_lane(in, g, w, i, lane, 32, [](int32_t, double) {});
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) cnt[i] = c;
+  }
 }
 
+// The pairs (i, j), j > i, of each particle at its offset, in increasing j:
+// a warp per particle; each lane writes its candidates after those of the
+// lanes before it, then the warp puts them in order by rank (a particle has
+// a few dozen candidates in a packing; more than kBpSortMax are ordered by
+// one lane).
+constexpr int kBpSortMax = 256;
 __global__ void __launch_bounds__(kThreads) k_bp_write(BroadIn in, const BroadGrid* grid,
                                                        BroadWork w, const int32_t* off,
                                                        const int64_t* count, int64_t cap,
                                                        int32_t* pairs, double* pair_eps) {
   wait_prior_grid();
+  __shared__ int32_t sj[kThreads / 32][kBpSortMax];
+  __shared__ double se[kThreads / 32][kBpSortMax];
   const int64_t total = *count;
   const BroadGrid g = *grid;
   if (g.bad || total > cap) return;
-  const int32_t step = gridDim.x * blockDim.x;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += step) {
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (int32_t i = blockIdx.x * (blockDim.x >> 5) + wq; i < in.n; i += warps) {
     const int64_t o = off[i];
     const int64_t m = (i + 1 < in.n ? (int64_t)off[i + 1] : total) - o;
-    int64_t k = 0;
-    bp_visit(in, g, w, i, [&](int32_t j, double e) {
+    // this lane's share, then its place after the lanes before it
+    const int32_t mine = bp_visit_lane(in, g, w, i, lane, 32, [](int32_t, double) {});
+    int32_t incl = mine;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const int32_t got_all = __shfl_sync(0xffffffffu, incl, 31);
+    int64_t k = incl - mine;
+    bp_visit_lane(in, g, w, i, lane, 32, [&](int32_t j, double e) {
       if (k < m) {
         pairs[2 * (o + k) + 1] = j;
         pair_eps[o + k] = e;
       }
       ++k;
     });
-    const int64_t got = k < m ? k : m;
-    // insertion sort of the particle's candidates by j (a few dozen at most
-    // in a packing)
-    for (int64_t a = o + 1; a < o + got; ++a) {
-      const int32_t j = pairs[2 * a + 1];
-      const double e = pair_eps[a];
-      int64_t b = a - 1;
-      while (b >= o && pairs[2 * b + 1] > j) {
-        pairs[2 * (b + 1) + 1] = pairs[2 * b + 1];
-        pair_eps[b + 1] = pair_eps[b];
-        --b;
+    const int64_t got = got_all < m ? got_all : m;
+    __syncwarp();
+    if (got <= kBpSortMax) {
+      // order by j: each entry goes to its rank (the j are distinct)
+      for (int64_t a = lane; a < got; a += 32) {
+        sj[wq][a] = pairs[2 * (o + a) + 1];
+        se[wq][a] = pair_eps[o + a];
       }
-      pairs[2 * (b + 1) + 1] = j;
-      pair_eps[b + 1] = e;
+      __syncwarp();
+      for (int64_t a = lane; a < got; a += 32) {
+        const int32_t j = sj[wq][a];
+        int32_t r = 0;
+        for (int64_t q = 0; q < got; ++q) r += sj[wq][q] < j;
+        pairs[2 * (o + r)] = i;
+        pairs[2 * (o + r) + 1] = j;
+        pair_eps[o + r] = se[wq][a];
+      }
+      __syncwarp();
+    } else if (lane == 0) {
+      for (int64_t a = o + 1; a < o + got; ++a) {
+        const int32_t j = pairs[2 * a + 1];
+        const double e = pair_eps[a];
+        int64_t b = a - 1;
+        while (b >= o && pairs[2 * b + 1] > j) {
+          pairs[2 * (b + 1) + 1] = pairs[2 * b + 1];
+          pair_eps[b + 1] = pair_eps[b];
+          --b;
+        }
+        pairs[2 * (b + 1) + 1] = j;
+        pair_eps[b + 1] = e;
+      }
+      for (int64_t a = o; a < o + got; ++a) pairs[2 * a] = i;
     }
-    for (int64_t a = o; a < o + got; ++a) pairs[2 * a] = i;
+    __syncwarp();
   }
 }
 
@@ -190,6 +235,21 @@ __global__ void __launch_bounds__(kThreads) k_move_poses(int32_t n, const double
     for (int k = 0; k < 6; ++k) v[k] = vel[(int64_t)6 * i + k];
     move_pose(p0, v, dt, out);
     for (int k = 0; k < 7; ++k) poses[(int64_t)7 * i + k] = out[k];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_twist_grad(int32_t n, const double* twist,
+                                                         const double* g, double* out) {
+  wait_prior_grid();
+  const int32_t step = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+    double tw[6], gi[6], o[6];
+    for (int k = 0; k < 6; ++k) {
+      tw[k] = twist[(int64_t)6 * i + k];
+      gi[k] = g[(int64_t)6 * i + k];
+    }
+    twist_gradient(tw, gi, o);
+    for (int k = 0; k < 6; ++k) out[(int64_t)6 * i + k] = o[k];
   }
 }
 
@@ -247,9 +307,24 @@ __device__ __forceinline__ bool world_triangle(const HierDev& H, const double* p
 // entry by entry (a lane per entry, 144 = 4.5 x 32), summing runs of
 // contacts of the same pair (detection lists a pair's contacts together) in
 // registers and adding each run's sums to the pair's block with one atomic
-// per entry.
-constexpr int kHessWarps = 4;
-__global__ void __launch_bounds__(kHessWarps * 32) k_hessian(HierDev H, const int32_t* ab,
+// per entry.  The block is symmetric, so the lanes form its upper triangle
+// (78 entries) and write each off-diagonal sum to both places.
+constexpr int kHessWarps = 2;
+// The block is symmetric: its 78 entries (i <= j) as (i << 4) | j.
+__constant__ unsigned char kHessUpper[78] = {
+    0x00, 0x01, 0x02, 0x03, 0x04, 0x05, 0x06, 0x07, 0x08, 0x09, 0x0a, 0x0b,
+    0x11, 0x12, 0x13, 0x14, 0x15, 0x16, 0x17, 0x18, 0x19, 0x1a, 0x1b,
+    0x22, 0x23, 0x24, 0x25, 0x26, 0x27, 0x28, 0x29, 0x2a, 0x2b,
+    0x33, 0x34, 0x35, 0x36, 0x37, 0x38, 0x39, 0x3a, 0x3b,
+    0x44, 0x45, 0x46, 0x47, 0x48, 0x49, 0x4a, 0x4b,
+    0x55, 0x56, 0x57, 0x58, 0x59, 0x5a, 0x5b,
+    0x66, 0x67, 0x68, 0x69, 0x6a, 0x6b,
+    0x77, 0x78, 0x79, 0x7a, 0x7b,
+    0x88, 0x89, 0x8a, 0x8b,
+    0x99, 0x9a, 0x9b,
+    0xaa, 0xab,
+    0xbb};
+__global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const int32_t* ab,
                                                              const double* eps,
                                                              const double* poses,
                                                              const double* mass, double k_s,
@@ -285,14 +360,25 @@ __global__ void __launch_bounds__(kHessWarps * 32) k_hessian(HierDev H, const in
     }
     rpair[w][lane] = pr;
     __syncwarp();
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    // a lane's entries of the upper triangle: u = lane, lane + 32, lane + 64
+    int ei[3], ej[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const int u = lane + 32 * m;
+      const int c = u < 78 ? kHessUpper[u] : 0;
+      ei[m] = u < 78 ? c >> 4 : -1;
+      ej[m] = c & 15;
+    }
+    double acc[3] = {0.0, 0.0, 0.0};
     int cur = -1;
     auto flush = [&]() {
       double* o = blocks + 144 * (int64_t)cur;
 #pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        const int q = lane + 32 * m;
-        if (q < 144) atomicAdd(o + q, acc[m]);
+      for (int m = 0; m < 3; ++m) {
+        if (ei[m] >= 0) {
+          atomicAdd(o + 12 * ei[m] + ej[m], acc[m]);
+          if (ei[m] != ej[m]) atomicAdd(o + 12 * ej[m] + ei[m], acc[m]);
+        }
         acc[m] = 0.0;
       }
     };
@@ -305,10 +391,8 @@ __global__ void __launch_bounds__(kHessWarps * 32) k_hessian(HierDev H, const in
       if (p < 0) continue;
       const HessRep& h = rep[w][ci];
 #pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        const int q = lane + 32 * m;
-        if (q < 144) acc[m] += hessian_entry(h, q / 12, q % 12);
-      }
+      for (int m = 0; m < 3; ++m)
+        if (ei[m] >= 0) acc[m] += hessian_entry(h, ei[m], ej[m]);
     }
     if (cur >= 0) flush();
     __syncwarp();
@@ -383,23 +467,41 @@ __device__ __forceinline__ double warp_sum_d(double x) {
   return x;
 }
 
-__global__ void __launch_bounds__(kThreads) k_cg_init(CgView v, const double* rhs) {
-  wait_prior_grid();
-  const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step) {
+// The whole solve in one cooperative launch (every block resident, grid-wide
+// barriers between the phases), so that an iteration costs a few barriers
+// instead of six kernel launches, and the loop stops on the device when the
+// residual is small enough.  Phases of iteration k: A p (the M/dt part, then
+// the pair blocks' share with atomics), p.Ap, the step (x, r, z, r.z, r.r),
+// the stopping test (one thread), the next direction.  Sums of one phase are
+// taken with atomics into the iteration's own scalar slots.
+// Values other blocks wrote in an earlier phase are read past the SM's L1
+// (__ldcg), which is not kept coherent with other SMs' writes.
+__device__ __forceinline__ double view_precond(const CgView& v, int64_t i) {
+  return cg_precond(__ldcg(v.diag + i), view_mdt(v, i));  // an indefinite diagonal: M/dt
+}
+
+__device__ __forceinline__ void grid_sum(double* dst, double x) {
+  x = warp_sum_d(x);
+  if ((threadIdx.x & 31) == 0) atomicAdd(dst, x);
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_coop(CgView v, const double* rhs, int64_t n_pairs,
+                                                      const int32_t* ab, const double* blocks,
+                                                      int max_iter, double tol2, double* info) {
+  cg::grid_group grid = cg::this_grid();
+  const int64_t m = (int64_t)6 * v.n;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  volatile CgState* st = v.st;
+  // x = 0, r = rhs, diagonal of M/dt + dt K
+  for (int64_t i = t0; i < m; i += step) {
     v.x[i] = 0.0;
     v.r[i] = rhs[i];
     v.diag[i] = view_mdt(v, i);
   }
-}
-
-// diagonal of the pair blocks into the preconditioner
-__global__ void __launch_bounds__(kThreads) k_cg_diag_pairs(CgView v, int64_t n_pairs,
-                                                            const int32_t* ab,
-                                                            const double* blocks) {
-  wait_prior_grid();
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_pairs; q += step) {
+  grid.sync();
+  for (int64_t q = t0; q < n_pairs; q += step) {
     const int A = ab[2 * q], B = ab[2 * q + 1];
     if (A < 0 || A >= v.n || B < 0 || B >= v.n) continue;
     double da[6], db[6];
@@ -409,136 +511,90 @@ __global__ void __launch_bounds__(kThreads) k_cg_diag_pairs(CgView v, int64_t n_
       atomicAdd(v.diag + (int64_t)6 * B + k, db[k]);
     }
   }
-}
-
-__device__ __forceinline__ double view_precond(const CgView& v, int64_t i) {
-  return cg_precond(v.diag[i], view_mdt(v, i));  // an indefinite diagonal falls back to M/dt
-}
-
-__global__ void __launch_bounds__(kThreads) k_cg_init2(CgView v) {
-  wait_prior_grid();
-  const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
-  double rz = 0.0, rr = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step) {
-    const double r = v.r[i], z = r / view_precond(v, i);
-    v.z[i] = z;
-    v.p[i] = z;
-    rz += r * z;
-    rr += r * r;
-  }
-  rz = warp_sum_d(rz);
-  rr = warp_sum_d(rr);
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(v.rz, rz);
-    atomicAdd(v.rr, rr);
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) k_cg_ap_diag(CgView v) {
-  wait_prior_grid();
-  if (v.st->done) return;
-  const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step)
-    v.ap[i] = view_mdt(v, i) * v.p[i];
-}
-
-__global__ void __launch_bounds__(kThreads) k_cg_ap_pairs(CgView v, int64_t n_pairs,
-                                                          const int32_t* ab,
-                                                          const double* blocks) {
-  wait_prior_grid();
-  if (v.st->done) return;
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_pairs; q += step) {
-    const int A = ab[2 * q], B = ab[2 * q + 1];
-    if (A < 0 || A >= v.n || B < 0 || B >= v.n) continue;
-    double ya[6], yb[6];
-    cg_pair_apply(blocks + 144 * q, v.p + (int64_t)6 * A, v.p + (int64_t)6 * B, v.dt, ya, yb);
-    for (int k = 0; k < 6; ++k) {
-      atomicAdd(v.ap + (int64_t)6 * A + k, ya[k]);
-      atomicAdd(v.ap + (int64_t)6 * B + k, yb[k]);
+  grid.sync();
+  {
+    double rz = 0.0, rr = 0.0;
+    for (int64_t i = t0; i < m; i += step) {
+      const double r = v.r[i], z = r / view_precond(v, i);
+      v.z[i] = z;
+      v.p[i] = z;
+      rz += r * z;
+      rr += r * r;
     }
+    grid_sum(v.rz, rz);
+    grid_sum(v.rr, rr);
   }
-}
-
-__global__ void __launch_bounds__(kThreads) k_cg_pap(CgView v, int k) {
-  wait_prior_grid();
-  if (v.st->done) return;
-  const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
-  double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step)
-    s += v.p[i] * v.ap[i];
-  s = warp_sum_d(s);
-  if ((threadIdx.x & 31) == 0) atomicAdd(v.pap + k, s);
-}
-
-__global__ void __launch_bounds__(kThreads) k_cg_step(CgView v, int k) {
-  wait_prior_grid();
-  if (v.st->done) return;
-  const double pap = v.pap[k];
-  const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
-  if (!(pap > 0.0)) {
-    // breakdown (flagged by k_cg_check): negative curvature along the first
-    // direction still gives a step along it, so that x is not left at zero
-    if (k == 0 && pap < 0.0) {
-      const double a = v.rz[0] / -pap;
-      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step)
-        v.x[i] += a * v.p[i];
+  grid.sync();
+  if (lead && __ldcg(v.rr) <= 0.0) { st->done = 1; st->iters = 0; }
+  grid.sync();
+  for (int k = 0; k < max_iter; ++k) {
+    if (st->done) break;  // read after a barrier: the same on every thread
+    for (int64_t i = t0; i < m; i += step) v.ap[i] = view_mdt(v, i) * v.p[i];
+    grid.sync();
+    for (int64_t q = t0; q < n_pairs; q += step) {
+      const int A = ab[2 * q], B = ab[2 * q + 1];
+      if (A < 0 || A >= v.n || B < 0 || B >= v.n) continue;
+      double ya[6], yb[6], pa[6], pb[6];
+      for (int c = 0; c < 6; ++c) {
+        pa[c] = __ldcg(v.p + (int64_t)6 * A + c);
+        pb[c] = __ldcg(v.p + (int64_t)6 * B + c);
+      }
+      cg_pair_apply(blocks + 144 * q, pa, pb, v.dt, ya, yb);
+      for (int c = 0; c < 6; ++c) {
+        atomicAdd(v.ap + (int64_t)6 * A + c, ya[c]);
+        atomicAdd(v.ap + (int64_t)6 * B + c, yb[c]);
+      }
     }
-    return;
+    grid.sync();
+    {
+      double s = 0.0;
+      for (int64_t i = t0; i < m; i += step) s += v.p[i] * __ldcg(v.ap + i);
+      grid_sum(v.pap + k, s);
+    }
+    grid.sync();
+    const double pap = __ldcg(v.pap + k);
+    if (!(pap > 0.0)) {
+      // not positive definite along p: stop; negative curvature along the
+      // first direction still gives a step along it, so x is not left at 0
+      if (k == 0 && pap < 0.0) {
+        const double a = __ldcg(v.rz) / -pap;
+        for (int64_t i = t0; i < m; i += step) v.x[i] += a * v.p[i];
+      }
+      if (lead) { st->done = 1; st->breakdown = 1; st->iters = k; }
+      break;  // every thread sees the same pap
+    }
+    {
+      const double alpha = __ldcg(v.rz + k) / pap;
+      double rz = 0.0, rr = 0.0;
+      for (int64_t i = t0; i < m; i += step) {
+        v.x[i] += alpha * v.p[i];
+        const double r = v.r[i] - alpha * __ldcg(v.ap + i);
+        const double z = r / view_precond(v, i);
+        v.r[i] = r;
+        v.z[i] = z;
+        rz += r * z;
+        rr += r * r;
+      }
+      grid_sum(v.rz + k + 1, rz);
+      grid_sum(v.rr + k + 1, rr);
+    }
+    grid.sync();
+    if (__ldcg(v.rr + k + 1) <= tol2 * __ldcg(v.rr)) {
+      if (lead) { st->done = 1; st->iters = k + 1; }
+      break;  // every thread sees the same sums
+    }
+    const double beta = __ldcg(v.rz + k + 1) / __ldcg(v.rz + k);
+    for (int64_t i = t0; i < m; i += step) v.p[i] = v.z[i] + beta * v.p[i];
+    grid.sync();
   }
-  const double alpha = v.rz[k] / pap;
-  double rz = 0.0, rr = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step) {
-    v.x[i] += alpha * v.p[i];
-    const double r = v.r[i] - alpha * v.ap[i];
-    const double z = r / view_precond(v, i);
-    v.r[i] = r;
-    v.z[i] = z;
-    rz += r * z;
-    rr += r * r;
+  if (lead) {
+    const int it = st->done ? st->iters : max_iter;
+    info[0] = (double)it;
+    const double r0 = __ldcg(v.rr), ri = __ldcg(v.rr + it);
+    info[1] = r0 > 0.0 ? sqrt(ri / r0) : 0.0;
+    info[2] = (double)st->breakdown;
+    info[3] = sqrt(r0);
   }
-  rz = warp_sum_d(rz);
-  rr = warp_sum_d(rr);
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(v.rz + k + 1, rz);
-    atomicAdd(v.rr + k + 1, rr);
-  }
-}
-
-// one thread: stop on convergence (|r|^2 <= tol2 |r0|^2) or breakdown
-// (p.Ap <= 0: the matrix is not positive definite along p)
-__global__ void k_cg_check(CgView v, int k, double tol2) {
-  wait_prior_grid();
-  CgState s = *v.st;
-  if (s.done) return;
-  if (k >= 0 && !(v.pap[k] > 0.0)) {
-    s.done = 1;
-    s.breakdown = 1;
-    s.iters = k;
-  } else if (v.rr[k + 1] <= tol2 * v.rr[0]) {
-    s.done = 1;
-    s.iters = k + 1;
-  }
-  *v.st = s;
-}
-
-__global__ void __launch_bounds__(kThreads) k_cg_dir(CgView v, int k) {
-  wait_prior_grid();
-  if (v.st->done) return;
-  const double beta = v.rz[k + 1] / v.rz[k];
-  const int64_t m = (int64_t)6 * v.n, step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += step)
-    v.p[i] = v.z[i] + beta * v.p[i];
-}
-
-__global__ void k_cg_finish(CgView v, int max_iter, double* info) {
-  wait_prior_grid();
-  const CgState s = *v.st;
-  const int it = s.done ? s.iters : max_iter;
-  info[0] = (double)it;
-  info[1] = v.rr[0] > 0.0 ? sqrt(v.rr[it] / v.rr[0]) : 0.0;
-  info[2] = (double)s.breakdown;
-  info[3] = sqrt(v.rr[0]);
 }
 
 // ---- contacts of a cached candidate list (the active set kept across the
@@ -709,9 +765,12 @@ int launch_broad_phase(mrdem_ctx* c, int32_t n, const double* poses, const doubl
   launch_after(k_bp_scan, 1, 1024, 0, s, w.bucket_end, t, (int64_t*)nullptr);
   launch_after(k_bp_scan, 1, 1024, 0, s, w.class_end, (int64_t)kMaxClasses, (int64_t*)nullptr);
   launch_after(k_bp_scatter, nb, kThreads, 0, s, in, (const BroadGrid*)grid, w);
-  launch_after(k_bp_count, nb, kThreads, 0, s, in, (const BroadGrid*)grid, w, cnt);
+  // a warp per particle
+  const int wb = (int)std::min<int64_t>(((int64_t)n + kThreads / 32 - 1) / (kThreads / 32),
+                                        (int64_t)c->n_sms * 16);
+  launch_after(k_bp_count, wb, kThreads, 0, s, in, (const BroadGrid*)grid, w, cnt);
   launch_after(k_bp_scan, 1, 1024, 0, s, cnt, (int64_t)n, count);
-  launch_after(k_bp_write, nb, kThreads, 0, s, in, (const BroadGrid*)grid, w,
+  launch_after(k_bp_write, wb, kThreads, 0, s, in, (const BroadGrid*)grid, w,
                (const int32_t*)cnt, (const int64_t*)count, cap, pairs, pair_eps);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
@@ -722,6 +781,15 @@ int launch_move_poses(mrdem_ctx* c, int32_t n, const double* poses0, const doubl
   if (n == 0) return MRDEM_OK;
   ProfScope ps(c, K_STEP, s);
   launch_after(k_move_poses, blocks_for(c, n), kThreads, 0, s, n, poses0, vel, dt, poses);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
+
+int launch_twist_grad(mrdem_ctx* c, int32_t n, const double* twist, const double* g, double* out,
+                      cudaStream_t s) {
+  if (n == 0) return MRDEM_OK;
+  ProfScope ps(c, K_STEP, s);
+  launch_after(k_twist_grad, blocks_for(c, n), kThreads, 0, s, n, twist, g, out);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
@@ -745,7 +813,7 @@ int launch_contact_hessian(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, c
                            const double* mass, double k_s, double* blocks, int64_t* skipped,
                            cudaStream_t s) {
   if (n_pairs == 0 || con->capacity == 0) return MRDEM_OK;
-  ProfScope ps(c, K_STEP, s);
+  ProfScope ps(c, K_HESSIAN, s);
   const int hb = kHessWarps * 32;
   const int64_t nb64 = (con->capacity + hb - 1) / hb;
   const int64_t lim = (int64_t)c->n_sms * 16;
@@ -816,6 +884,7 @@ int launch_newton_solve(mrdem_ctx* c, int32_t n, int64_t n_pairs, const int32_t*
                         const double* blocks, const double* mass, const double* inertia,
                         double dt, const double* rhs, double* x, int32_t max_iter, double rel_tol,
                         int32_t check_every, double* info, cudaStream_t s) {
+  (void)check_every;  // the solve stops on the device
   CgView v;
   int st = ensure_cg(c, n, max_iter, &v);
   if (st) return st;
@@ -825,36 +894,28 @@ int launch_newton_solve(mrdem_ctx* c, int32_t n, int64_t n_pairs, const int32_t*
   v.dt = dt;
   v.n = n;
   const size_t ns = 3 * ((size_t)max_iter + 1);
-  ProfScope ps(c, K_STEP, s);
+  ProfScope ps(c, K_CG, s);
   cudaMemsetAsync(c->cg_mem, 0, 64 + sizeof(double) * ns, s);
-  const int64_t m = (int64_t)6 * n;
-  const int nd = blocks_for(c, m > 0 ? m : 1), np = blocks_for(c, n_pairs > 0 ? n_pairs : 1);
-  const double tol2 = rel_tol * rel_tol;
-  launch_after(k_cg_init, nd, kThreads, 0, s, v, rhs);
-  if (n_pairs > 0) launch_after(k_cg_diag_pairs, np, kThreads, 0, s, v, n_pairs, ab, blocks);
-  launch_after(k_cg_init2, nd, kThreads, 0, s, v);
-  launch_after(k_cg_check, 1, 1, 0, s, v, -1, tol2);
-  for (int k = 0; k < max_iter; ++k) {
-    if (check_every > 0 && k > 0 && k % check_every == 0) {
-      // stop enqueueing once the solve has finished (synchronises the stream)
-      CgState st;
-      if (cudaMemcpyAsync(&st, v.st, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
-        return MRDEM_ERR_CUDA;
-      }
-      if (st.done) break;
-    }
-    launch_after(k_cg_ap_diag, nd, kThreads, 0, s, v);
-    if (n_pairs > 0) launch_after(k_cg_ap_pairs, np, kThreads, 0, s, v, n_pairs, ab, blocks);
-    launch_after(k_cg_pap, nd, kThreads, 0, s, v, k);
-    launch_after(k_cg_step, nd, kThreads, 0, s, v, k);
-    launch_after(k_cg_check, 1, 1, 0, s, v, k, tol2);
-    launch_after(k_cg_dir, nd, kThreads, 0, s, v, k);
+  // every block resident at once (a cooperative launch)
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_coop, kThreads, 0) != cudaSuccess ||
+      occ <= 0) {
+    cudaGetLastError();
+    return MRDEM_ERR_CUDA;
   }
-  launch_after(k_cg_finish, 1, 1, 0, s, v, max_iter, info);
-  const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+  const int64_t m = (int64_t)6 * n, work = m > n_pairs ? m : n_pairs;
+  const int64_t need = (work + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)occ * c->n_sms;
+  const int grid = (int)(need < 1 ? 1 : (need < cap ? need : cap));
+  double tol2 = rel_tol * rel_tol;
+  int64_t np = n_pairs;
+  void* args[] = {&v, (void*)&rhs, &np, (void*)&ab, (void*)&blocks, &max_iter, &tol2, &info};
+  if (cudaLaunchCooperativeKernel((const void*)k_cg_coop, dim3(grid), dim3(kThreads), args, 0, s) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return MRDEM_ERR_CUDA;
+  }
+  return MRDEM_OK;
 }
 
 int launch_refine_contacts(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,

@@ -213,6 +213,56 @@ MRDEM_HD int32_t bp_visit(const BroadIn& in, const BroadGrid& g, const BroadWork
   return found;
 }
 
+// The same visit split over `nl` lanes: lane `l` takes every nl-th unit of
+// work (a cell of a class's search box, or a particle of a class run
+// through directly), so the lanes together visit every candidate of i
+// exactly once.  Returns the candidates this lane found.
+template <typename F>
+MRDEM_HD int32_t bp_visit_lane(const BroadIn& in, const BroadGrid& g, const BroadWork& w, int32_t i,
+                               int l, int nl, F f) {
+  const double* ci = in.poses + (int64_t)7 * i;
+  const double Ri = in.bound[i], ri = in.radius[i];
+  int32_t found = 0;
+  auto test = [&](int32_t j) {
+    if (j <= i) return;
+    const double eij = bp_pair_eps(ri, in.radius[j], in.eps_rel);
+    if (!bp_candidate(ci, in.poses + (int64_t)7 * j, Ri, in.bound[j], eij)) return;
+    f(j, eij);
+    ++found;
+  };
+  for (int b = 0; b < g.classes; ++b) {
+    const int32_t beg = b ? w.class_end[b - 1] : 0, end = w.class_end[b];
+    if (end <= beg) continue;
+    const double rho = (Ri + bp_class_top(g.r_max, b) + 4.0 * in.eps_rel * ri) * kCellSlack;
+    int32_t lo[3], hi[3];
+    double ncells = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      const double pad = (fabs(ci[a]) + fabs(g.lo[a]) + rho) * 0x1p-48;
+      lo[a] = bp_cell(ci[a] - rho - pad, g.lo[a], g.inv_h[b]);
+      hi[a] = bp_cell(ci[a] + rho + pad, g.lo[a], g.inv_h[b]);
+      ncells *= (double)(hi[a] - lo[a] + 1);
+    }
+    if (ncells > (double)(end - beg)) {
+      for (int32_t q = beg + l; q < end; q += nl) test(w.class_order[q]);
+      continue;
+    }
+    const int64_t nx = hi[0] - lo[0] + 1, ny = hi[1] - lo[1] + 1;
+    const int64_t nc = (int64_t)ncells;
+    for (int64_t u = l; u < nc; u += nl) {
+      const int32_t x = lo[0] + (int32_t)(u % nx), y = lo[1] + (int32_t)((u / nx) % ny);
+      const int32_t z = lo[2] + (int32_t)(u / (nx * ny));
+      const uint32_t bk = bp_bucket(x, y, z, b, w.log2_t);
+      const int32_t kb = bk ? w.bucket_end[bk - 1] : 0, ke = w.bucket_end[bk];
+      for (int32_t q = kb; q < ke; ++q) {
+        const int32_t j = w.order[q];
+        const BroadCell cj = w.cell[j];
+        if (cj.k == b && cj.x == x && cj.y == y && cj.z == z) test(j);
+      }
+    }
+  }
+  return found;
+}
+
 // ---- rigid-body update and Picard iteration (Algorithm 3)
 
 // Unit quaternion (w, x, y, z) of the rotation by rotation vector r.
@@ -267,6 +317,33 @@ MRDEM_HD void move_pose(const double* pose0, const double* vel, double dt, doubl
   quat_mul(dq, q0, q);
   const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   for (int k = 0; k < 4; ++k) out[3 + k] = q[k] / n;
+}
+
+// Gradient of E(exp(w) R, t + v) in the twist (v, w) from the gradient g in
+// a left rotation increment at the moved pose: the translation part is g's,
+// the rotation part J_l(w)^T g_rot, with J_l(w) = I + (1 - cos th)/th^2 [w]x
+// + (th - sin th)/th^3 [w]x^2 (th = |w|) the left Jacobian of the rotation
+// group's exponential map: exp(w + e) = exp(J_l(w) e) exp(w) to first order.
+MRDEM_HD void twist_gradient(const double* tw, const double* g, double* out) {
+  for (int k = 0; k < 3; ++k) out[k] = g[k];
+  const double w[3] = {tw[3], tw[4], tw[5]};
+  const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double a, b;  // (1 - cos th)/th^2 and (th - sin th)/th^3
+  if (th2 < 1e-8) {
+    a = 0.5 - th2 / 24.0;
+    b = 1.0 / 6.0 - th2 / 120.0;
+  } else {
+    const double th = sqrt(th2);
+    a = (1.0 - cos(th)) / th2;
+    b = (th - sin(th)) / (th2 * th);
+  }
+  // J^T g = g - a (w x g) + b (w x (w x g))   ([w]x^T = -[w]x, ([w]x^2)^T = [w]x^2)
+  const double* gr = g + 3;
+  const double c1[3] = {w[1] * gr[2] - w[2] * gr[1], w[2] * gr[0] - w[0] * gr[2],
+                        w[0] * gr[1] - w[1] * gr[0]};
+  const double c2[3] = {w[1] * c1[2] - w[2] * c1[1], w[2] * c1[0] - w[0] * c1[2],
+                        w[0] * c1[1] - w[1] * c1[0]};
+  for (int k = 0; k < 3; ++k) out[3 + k] = gr[k] - a * c1[k] + b * c2[k];
 }
 
 // One Picard update of particle i's velocities: new = (v0 + dt (F / m + g),
@@ -328,6 +405,8 @@ struct HessRep {
   double K[3];         // (G G^T)^-1: K00, K01, K11
   double a, b;         // e'' - e'/d and e'/d
   double g[3];         // e' u
+  double zu[12];       // Z u
+  double N[2][12];     // N_q (zero beyond nq)
   int nq;              // free parameters (0..2)
   int own[2];          // particle of each (0: A, 1: B)
 };
@@ -369,15 +448,13 @@ MRDEM_HD double hessian_entry(const HessRep& h, int i, int j) {
   double zi[3], zj[3];
   hess_zrow(h, i, zi);
   hess_zrow(h, j, zj);
-  const double zui = zi[0] * h.u[0] + zi[1] * h.u[1] + zi[2] * h.u[2];
-  const double zuj = zj[0] * h.u[0] + zj[1] * h.u[1] + zj[2] * h.u[2];
-  double v = h.a * zui * zuj + h.b * (zi[0] * zj[0] + zi[1] * zj[1] + zi[2] * zj[2]);
+  double v = h.a * h.zu[i] * h.zu[j] + h.b * (zi[0] * zj[0] + zi[1] * zj[1] + zi[2] * zj[2]);
   if (h.nq > 0) {
-    const double ni0 = hess_n(h, 0, i, zi), nj0 = hess_n(h, 0, j, zj);
+    const double ni0 = h.N[0][i], nj0 = h.N[0][j];
     if (h.nq == 1) {
       v -= h.b * ni0 * h.K[0] * nj0;
     } else {
-      const double ni1 = hess_n(h, 1, i, zi), nj1 = hess_n(h, 1, j, zj);
+      const double ni1 = h.N[1][i], nj1 = h.N[1][j];
       v -= h.b * (ni0 * h.K[0] * nj0 + ni0 * h.K[1] * nj1 + ni1 * h.K[1] * nj0 +
                   ni1 * h.K[2] * nj1);
     }
@@ -469,6 +546,14 @@ MRDEM_HD int contact_hessian_rep(const V3<double> TA[3], const V3<double> TB[3],
   h.b = e1 / d;
   h.g[0] = e1 * u.x; h.g[1] = e1 * u.y; h.g[2] = e1 * u.z;
   h.nq = nq;
+  // Z u and N_q, entry by entry (each entry's row of Z)
+  for (int i = 0; i < 12; ++i) {
+    double z[3];
+    hess_zrow(h, i, z);
+    h.zu[i] = z[0] * h.u[0] + z[1] * h.u[1] + z[2] * h.u[2];
+    h.N[0][i] = nq > 0 ? hess_n(h, 0, i, z) : 0.0;
+    h.N[1][i] = nq > 1 ? hess_n(h, 1, i, z) : 0.0;
+  }
   return 0;
 }
 

@@ -74,8 +74,12 @@ extern "C" long long hs_broad_phase(int n, const double* poses, const double* bo
     order[bucket_end[cell[i].b]++] = i;
     class_order[class_end[cell[i].k]++] = i;
   }
-  // k_bp_count, k_bp_scan
-  for (int i = 0; i < n; ++i) cnt[i] = bp_visit(in, g, w, i, [](int32_t, double) {});
+  // k_bp_count (a warp per particle: the 32 lanes' shares), k_bp_scan
+  for (int i = 0; i < n; ++i) {
+    int32_t c = 0;
+    for (int l = 0; l < 32; ++l) c += bp_visit_lane(in, g, w, i, l, 32, [](int32_t, double) {});
+    cnt[i] = c;
+  }
   long long total = 0;
   for (int i = 0; i < n; ++i) {
     const int c = cnt[i];
@@ -87,13 +91,15 @@ extern "C" long long hs_broad_phase(int n, const double* poses, const double* bo
   for (int i = 0; i < n; ++i) {
     const long long o = cnt[i], m = (i + 1 < n ? cnt[i + 1] : total) - o;
     long long k = 0;
-    bp_visit(in, g, w, i, [&](int32_t j, double e) {
-      if (k < m) {
-        pairs[2 * (o + k) + 1] = j;
-        pair_eps[o + k] = e;
-      }
-      ++k;
-    });
+    // the lanes' candidates one lane after the other, then in order of j
+    for (int l = 0; l < 32; ++l)
+      bp_visit_lane(in, g, w, i, l, 32, [&](int32_t j, double e) {
+        if (k < m) {
+          pairs[2 * (o + k) + 1] = j;
+          pair_eps[o + k] = e;
+        }
+        ++k;
+      });
     for (long long a = o + 1; a < o + m; ++a) {
       const int j = pairs[2 * a + 1];
       const double e = pair_eps[a];

@@ -74,21 +74,25 @@ def test_reference_arm_two_ranks_prints_one_line():
 
 def test_traffic_rows_follow_the_source(tmp_path):
     """roofline.traffic comes from the committed ncu table only while the
-    row's source hash matches the library source: comment edits keep it, a
-    code edit drops it."""
+    row's source hash matches the detection kernels' source: comment edits
+    and other files keep it, a code edit drops it."""
     b = _bench()
     csrc = tmp_path / "paper_2105_12415_gb300" / "csrc"
     csrc.mkdir(parents=True)
     (tmp_path / "profiles").mkdir()
-    (csrc / "k.cu").write_text("// a kernel\n__global__ void k() {}\n")
+    (csrc / "mrdem_detect.cu").write_text("// a kernel\n__global__ void k() {}\n")
+    (csrc / "mrdem_step.cu").write_text("__global__ void other() {}\n")
     b.ROOT = str(tmp_path)
     h = b._source_hash()
     table = f"| kernel | bytes | hash |\n|---|---|---|\n| k_tile | 1234 | {h} |\n| k_old | 99 | 0000 |\n"
     (tmp_path / "profiles" / "dram_traffic_c2_batched.md").write_text(table)
     assert b._traffic_per_launch() == {"k_tile": 1234.0}
-    (csrc / "k.cu").write_text("/* reworded\n comment */\n__global__ void k() {}  // same code\n\n")
+    (csrc / "mrdem_detect.cu").write_text("/* reworded\n comment */\n__global__ void k() {}  // same code\n\n")
     assert b._source_hash() == h and b._traffic_per_launch() == {"k_tile": 1234.0}
-    (csrc / "k.cu").write_text("__global__ void k() { int x = 0; }\n")
+    # a file the detection kernels are not built from does not count
+    (csrc / "mrdem_step.cu").write_text("__global__ void other() { int y = 1; }\n")
+    assert b._source_hash() == h
+    (csrc / "mrdem_detect.cu").write_text("__global__ void k() { int x = 0; }\n")
     assert b._source_hash() != h and b._traffic_per_launch() == {}
 
 

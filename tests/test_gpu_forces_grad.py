@@ -157,12 +157,75 @@ def test_autograd_function(gctx, orc):
     import paper_2105_12415_gb300 as m
     s = scene_c3(n_pairs=1024).subset([5, 9])
     prob = _problem(gctx, s, "fp64")
-    verts = torch.as_tensor(s.verts, device="cuda:0").requires_grad_(True)
-    twist = torch.zeros((s.n_particles, 6), dtype=torch.float64, device="cuda:0", requires_grad=True)
-    E = m.ContactEnergy.apply(verts, twist, prob)
+    E, verts, twist = m.contact_energy(prob)
     (2.0 * E).backward()
     ref = orc.detect(s)
     gv_ref, gp_ref, _ = orc.grad(s, ref)
-    assert abs(float(E) - orc.forces(s, ref)[1]) <= 1e-9 * float(E)
+    assert abs(float(E.detach()) - orc.forces(s, ref)[1]) <= 1e-9 * float(E.detach())
     assert np.abs(twist.grad.cpu().numpy() - 2 * gp_ref).max() <= 1e-9 * np.abs(gp_ref).max() * 2
     assert np.abs(verts.grad.cpu().numpy() - 2 * gv_ref).max() <= 1e-5 * np.abs(gv_ref).max() * 2
+
+
+def test_autograd_energy_is_a_function_of_its_inputs(gctx, orc):
+    """ContactEnergy at moved poses and moved vertices equals the oracle's
+    energy there, and torch.autograd.gradcheck passes on a 2-pair FP64 case:
+    in the twist (FP64, step 1e-6) and in the vertices (steps of 2^-16,
+    exact in the float32 meshes the library stores)."""
+    import dataclasses
+    import torch
+    import paper_2105_12415_gb300 as m
+    from tests.test_oracle_forces_grad import _apply_twist
+    s = scene_c3(n_pairs=1024).subset([5, 9])
+    prob = _problem(gctx, s, "fp64")
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(3)
+    tw = np.zeros((s.n_particles, 6))
+    tw[:, :3] = rng.normal(scale=2e-3, size=(s.n_particles, 3))
+    tw[:, 3:] = rng.normal(scale=2e-3, size=(s.n_particles, 3))
+    verts = torch.as_tensor(s.verts, device=dev).double()
+    verts[:20] += 2.0 ** -10
+    E = m.ContactEnergy.apply(verts, torch.as_tensor(tw, device=dev), prob)
+    # the oracle at the same geometry: poses moved by the twist (translation,
+    # then the rotation vector's turn on the left), vertices moved
+    moved = s.poses.copy()
+    for i in range(s.n_particles):
+        p = moved[i].copy()
+        p[:3] += tw[i, :3]
+        th = np.linalg.norm(tw[i, 3:])
+        if th > 0:
+            ax = tw[i, 3:] / th
+            dq = np.r_[np.cos(th / 2), np.sin(th / 2) * ax]
+            w1, v1, w2, v2 = dq[0], dq[1:], p[3], p[4:].copy()
+            p[3] = w1 * w2 - v1 @ v2
+            p[4:] = w1 * v2 + w2 * v1 + np.cross(v1, v2)
+        moved[i] = p
+    s2 = dataclasses.replace(s, verts=verts.float().cpu().numpy(), poses=moved)
+    e_ref = orc.forces(s2, orc.detect(s2))[1]
+    assert abs(float(E) - e_ref) <= 1e-9 * e_ref
+    # gradcheck in the twist
+    twist = torch.as_tensor(tw, device=dev).requires_grad_(True)
+    v0 = torch.as_tensor(s.verts, device=dev).double()
+    # the adjoint sums contacts with atomics, so two backward passes differ in
+    # the last bits (nondet_tol)
+    assert torch.autograd.gradcheck(lambda t: m.ContactEnergy.apply(v0, t, prob), (twist,),
+                                    eps=1e-6, atol=1e-6, rtol=1e-4, nondet_tol=1e-9)
+    # gradcheck in the vertices of the first three contacts' triangles of A
+    ref = orc.detect(s)
+    vsel = []
+    for c in range(3):
+        A = s.pairs[ref["pair"][c], 0]
+        vsel += list(s.vert_off[A] + s.tris[s.tri_off[A] + ref["ta"][c]])
+    vsel = np.unique(np.asarray(vsel, np.int64))
+    base = torch.as_tensor(s.verts, device=dev).double()
+    sub = base[torch.as_tensor(vsel, device=dev)].clone().requires_grad_(True)
+    idx = torch.as_tensor(vsel, device=dev)
+
+    def energy_of(vs):
+        full = base.index_put((idx,), vs)
+        return m.ContactEnergy.apply(full, torch.zeros_like(twist), prob)
+    # the vertex gradient is a float32 output (entries of order 1e3 here):
+    # an entry whose exact value is 0 carries float rounding of about 1e-7 of
+    # the largest (atol), and float32 atomics make two passes differ in the
+    # last bits (nondet_tol)
+    assert torch.autograd.gradcheck(energy_of, (sub,), eps=2.0 ** -16, atol=5e-3, rtol=1e-3,
+                                    nondet_tol=5e-3)
