@@ -210,7 +210,10 @@ __global__ void __launch_bounds__(256) k_cp_items(const AccRec* __restrict__ acc
 // result: the first crossing that crossed, else the first smallest squared
 // distance (so a pair's item results are read side by side, not one after
 // another).  This is the choice of tri_tri_distance: a crossing in
-// the fixed order ends the test, else the first minimum wins.
+// the fixed order ends the test, else the first minimum wins.  A warp
+// scans its 32 pairs four at a time and hands each pair's choice to the
+// pair's own lane, so that the double-float finishing (world points) runs
+// with every lane busy.
 constexpr int kSelLanes = 8;
 struct SelBest {
   int cls;    // 0: a crossing, 1: a distance, 2: none
@@ -237,63 +240,69 @@ __global__ void __launch_bounds__(256) k_select_exact(HierDev H, const PairXfDD*
   if (n > cap_acc) n = cap_acc;
   WarpCount ncon;
   const int lane = lane_id(), g = lane / kSelLanes, gl = lane % kSelLanes;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x / kSelLanes;
-  for (int64_t kb = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / kSelLanes; kb < n;
+  constexpr int kGroups = 32 / kSelLanes;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t kb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); kb < n;
        kb += stride) {
-    const int64_t k = kb + g;
+    // the warp's 32 pairs in rounds of four: in round r, group g scans pair
+    // kb + 4 r + g, and lane 4 r + g' keeps group g''s choice (its own pair)
+    int mine = -1;
+#pragma unroll 1
+    for (int r = 0; r < kSelLanes; ++r) {
+      const int64_t k = kb + kGroups * r + g;
+      SelBest best = {2, 1 << 30, dd(INFINITY)};
+      if (k < n) {
+        const AccRec& a = acc[k];
+        const int npt = a.counts & 0xff, nee = (a.counts >> 8) & 0xff;
+        const int ncx = (a.counts >> 16) & 0xff;
+        for (int t = gl; t < ncx + npt + nee; t += kSelLanes) {
+          SelBest cand;
+          cand.order = t;
+          if (t < ncx) {
+            cand.d2 = res_cx[a.cx_begin + t].d2;
+            cand.cls = cand.d2.hi == 0.f ? 0 : 2;
+          } else {
+            const int q = t - ncx;
+            cand.d2 = q < npt ? res_pt[a.pt_begin + q].d2 : res_ee[a.ee_begin + (q - npt)].d2;
+            cand.cls = 1;
+          }
+          if (sel_better(cand, best)) best = cand;
+        }
+      }
+      // the group's best (lanes of a group share one pair)
+#pragma unroll
+      for (int o = kSelLanes / 2; o > 0; o >>= 1) {
+        SelBest other;
+        other.cls = __shfl_xor_sync(0xffffffffu, best.cls, o);
+        other.order = __shfl_xor_sync(0xffffffffu, best.order, o);
+        other.d2.hi = __shfl_xor_sync(0xffffffffu, best.d2.hi, o);
+        other.d2.lo = __shfl_xor_sync(0xffffffffu, best.d2.lo, o);
+        if (sel_better(other, best)) best = other;
+      }
+      const int got = __shfl_sync(0xffffffffu, best.cls < 2 ? best.order : -1,
+                                  (lane % kGroups) * kSelLanes);
+      if (lane / kGroups == r) mine = got;
+    }
+    // every lane finishes its own pair kb + lane
+    const int64_t k = kb + lane;
     bool hit = false;
     int3 c = make_int3(0, 0, 0);
     double d = 0;
     D3 pa = {0, 0, 0}, pb = {0, 0, 0};
-    SelBest best = {2, 1 << 30, dd(INFINITY)};
-    int npt = 0, nee = 0, ncx = 0, ptb = 0, eeb = 0, cxb = 0;
-    if (k < n) {
-      const AccRec& r = acc[k];
-      npt = r.counts & 0xff;
-      nee = (r.counts >> 8) & 0xff;
-      ncx = (r.counts >> 16) & 0xff;
-      ptb = r.pt_begin;
-      eeb = r.ee_begin;
-      cxb = r.cx_begin;
-      for (int t = gl; t < ncx + npt + nee; t += kSelLanes) {
-        SelBest cand;
-        cand.order = t;
-        if (t < ncx) {
-          const ItemRes* x = res_cx + cxb + t;
-          cand.d2 = x->d2;
-          cand.cls = cand.d2.hi == 0.f ? 0 : 2;
-        } else {
-          const int q = t - ncx;
-          const ItemRes* x = q < npt ? res_pt + ptb + q : res_ee + eeb + (q - npt);
-          cand.d2 = x->d2;
-          cand.cls = 1;
-        }
-        if (sel_better(cand, best)) best = cand;
-      }
-    }
-    // the group's best (lanes of a group share one pair)
-#pragma unroll
-    for (int o = kSelLanes / 2; o > 0; o >>= 1) {
-      SelBest other;
-      other.cls = __shfl_xor_sync(0xffffffffu, best.cls, o);
-      other.order = __shfl_xor_sync(0xffffffffu, best.order, o);
-      other.d2.hi = __shfl_xor_sync(0xffffffffu, best.d2.hi, o);
-      other.d2.lo = __shfl_xor_sync(0xffffffffu, best.d2.lo, o);
-      if (sel_better(other, best)) best = other;
-    }
-    if (k < n && gl == 0 && best.cls < 2) {
-      const AccRec& r = acc[k];
-      const int t = best.order;
-      const ItemRes* b = t < ncx ? res_cx + cxb + t
-                                 : (t - ncx < npt ? res_pt + ptb + (t - ncx)
-                                                  : res_ee + eeb + (t - ncx - npt));
-      d = ldexp(to_double(dd_sqrt(b->d2)), r.g.k);
-      hit = d <= r.g.tau;
+    if (k < n && mine >= 0) {
+      const AccRec& a = acc[k];
+      const int npt = a.counts & 0xff, ncx = (a.counts >> 16) & 0xff;
+      const int t = mine;
+      const ItemRes* b = t < ncx ? res_cx + a.cx_begin + t
+                                 : (t - ncx < npt ? res_pt + a.pt_begin + (t - ncx)
+                                                  : res_ee + a.ee_begin + (t - ncx - npt));
+      d = ldexp(to_double(dd_sqrt(b->d2)), a.g.k);
+      hit = d <= a.g.tau;
       if (hit) {
-        c = cands[r.entry];
-        const PairXfDD& X = xfdd[r.pair];
-        pa = world_point(X, b->pa, r.g.k, r.g.o);
-        pb = world_point(X, b->pb, r.g.k, r.g.o);
+        c = cands[a.entry];
+        const PairXfDD& X = xfdd[a.pair];
+        pa = world_point(X, b->pa, a.g.k, a.g.o);
+        pb = world_point(X, b->pb, a.g.k, a.g.o);
       }
     }
     ncon.add(hit);
@@ -321,8 +330,7 @@ int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts
                c->res_ee, c->counters);
   launch_after(k_cp_items<2>, ib, 256, 0, s, c->acc, c->items_cx, (int)CNT_CX, c->cap_items,
                c->res_cx, c->counters);
-  // eight lanes per accepted pair: eight times the blocks
-  launch_after(k_select_exact, eb * kSelLanes, threads, 0, s, hier->dev, c->xfdd, c->acc, c->res_pt,
+  launch_after(k_select_exact, eb, threads, 0, s, hier->dev, c->xfdd, c->acc, c->res_pt,
                c->res_ee, c->res_cx, c->cands, c->counters, c->cap_cands, c->status, *out,
                c->pair_cnt);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
