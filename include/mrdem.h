@@ -132,6 +132,25 @@ typedef struct mrdem_contacts {
   double* point_b; /* [capacity * 3] */
 } mrdem_contacts;
 
+/* Active sets of the multiresolution implicit Euler step (Algorithm 6, the
+ * active set A(p_i, p_j) kept per particle pair across Picard iterations).
+ * Per pair, the set is a cut through the product of the two surrogate trees:
+ * node pairs (node_a of particle A, node_b of particle B; hierarchy node
+ * indices) such that every pair of fine triangles lies below exactly one
+ * item, stored in depth-first order of the product tree (a pair's children
+ * (a_i, b_j) follow each other, A's child index major; a leaf side stays as
+ * it is while the other side unfolds, as in Algorithm 5), the pairs one
+ * after another in pair order.  Caller-owned device memory: item
+ * [capacity * 4] int32 (pair, node_a, node_b, flags), count one device
+ * int64 (may exceed capacity; see mrdem_active_set_step).  flags bit 0:
+ * removal vetoed (the memory set U: the item was re-added after its group
+ * had been narrowed); bit 1: made by narrowing. */
+typedef struct mrdem_active_set {
+  int64_t capacity;
+  int64_t* count;
+  int32_t* item;
+} mrdem_active_set;
+
 /* Host-side description of a built hierarchy (see mrdem_hier_export). */
 typedef struct mrdem_hier_info {
   int32_t n_particles;
@@ -506,6 +525,64 @@ int mrdem_refine_contacts(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pair
                           const int32_t* pair_ab, const double* pair_eps, const double* poses,
                           const mrdem_contacts* candidates, const mrdem_contacts* out,
                           mrdem_stream stream);
+
+/* Initial active sets of Algorithm 6: one item (pair, root of A, root of B,
+ * 0) per pair, out->count = n_pairs (an invalid particle index gives nodes
+ * -1, which later steps keep as they are).  Errors: INVALID (null pointers,
+ * out->capacity < n_pairs), CUDA. */
+int mrdem_active_set_init(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
+                          const int32_t* pair_ab, const mrdem_active_set* out,
+                          mrdem_stream stream);
+
+/* One detection of Algorithm 6 on the active sets `in` at `poses`, and the
+ * next active sets in `out` (a distinct buffer).  Each item's two surrogates
+ * get the certified tests of a surrogate level (node spheres, oriented
+ * boxes, the float penalty sweep with its certificate and the face normals,
+ * threshold delta_a + delta_b + 2 eps):
+ *   - certified apart (bottom): kept, unless all items of its sibling group
+ *     (the children of one pair, listed side by side) are bottom and none is
+ *     vetoed: the group is then replaced by that pair, with flag bit 1
+ *     (narrowing);
+ *   - not apart, both nodes leaves: kept; its fine triangle pairs go through
+ *     the finest-level stage and exact distance of mrdem_detect, and the
+ *     contacts (d <= 2 eps) are written to `contacts` grouped by pair;
+ *   - not apart otherwise: replaced by its children (widening; they carry
+ *     flag bit 0 when the item carried bit 0 or 1); when the sweep converged
+ *     and its iterate's distance d is <= delta_a + delta_b + 2 eps, a
+ *     surrogate contact is appended to `surrogate`: pair, tri_a = node_a,
+ *     tri_b = node_b (node indices), dist = d, point_a/point_b the iterate's
+ *     points in the world frame (not ordered).
+ * counts: NULL or device int64[4]: items widened, groups narrowed, pairs of
+ * leaves compared, surrogate contacts.  Stream-ordered, no host
+ * synchronisation (capturable after a first call with the same sizes).  The
+ * context keeps 5 bytes per item of in->capacity.  Device-side failures
+ * latched for mrdem_check: out->count > out->capacity (items beyond
+ * dropped) or more contacts than a buffer holds: CAPACITY; non-finite
+ * input: NONFINITE.  Errors: INVALID (null pointers, in == out, capacities
+ * >= 2^31), OOM, CUDA. */
+int mrdem_active_set_step(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
+                          const int32_t* pair_ab, const double* pair_eps, const double* poses,
+                          int precision, const mrdem_active_set* in,
+                          const mrdem_active_set* out, const mrdem_contacts* contacts,
+                          const mrdem_contacts* surrogate, int64_t* counts,
+                          mrdem_stream stream);
+
+/* Forces of surrogate contacts (Algorithm 6's implicit guess, weighted down
+ * on coarse levels): for each entry of `surrogate` (as mrdem_active_set_step
+ * writes it), with tau = delta_a + delta_b + 2 eps of its two nodes, adds
+ * weight * k_s * sqrt(mu) * max(0, 1 - d / tau) * u to A's force and its
+ * negative to B's (u = (point_a - point_b) / d, or minus A's surrogate normal
+ * in the world frame when d = 0; mu = 1 / (1/m_A + 1/m_B)), applied at
+ * (point_a + point_b) / 2, torques about each particle's centre of mass (com:
+ * device double [n*3], body frame), into force_torque (device double
+ * [n*6], accumulated, not cleared), and weight * k_s * sqrt(mu) * tau / 2 *
+ * (1 - d / tau)^2 per entry into *energy (NULL: not computed).  Errors:
+ * INVALID (weight outside [0, 1], k_s < 0, null pointers), CUDA. */
+int mrdem_surrogate_forces(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
+                           const int32_t* pair_ab, const double* pair_eps, const double* poses,
+                           const mrdem_contacts* surrogate, const double* mass,
+                           const double* com, double k_s, double weight, double* force_torque,
+                           double* energy, mrdem_stream stream);
 
 /* Largest displacement of any point of any particle between poses_ref and
  * poses (device double [n*7] each): |t - t_ref| + theta * bound, theta the

@@ -11,6 +11,7 @@ from .api import (  # noqa: F401
     contact_grad, detect, detect_plain_fp64, merge_contacts, triangle_distance, broad_phase,
     move_poses, picard_update, implicit_euler_step, contact_hessian, newton_residual, newton_solve,
     implicit_euler_step_newton, refine_contacts, motion_bound, KeptCandidates, autotune,
-    twist_grad,
+    twist_grad, ActiveSets, active_sets_init, active_sets_step, surrogate_forces,
+    implicit_euler_step_multires,
 )
 from .buildlib import build  # noqa: F401

@@ -62,6 +62,10 @@ class mrdem_contacts(C.Structure):
     ]
 
 
+class mrdem_active_set(C.Structure):
+    _fields_ = [("capacity", C.c_int64), ("count", C.c_void_p), ("item", C.c_void_p)]
+
+
 class mrdem_hier_info(C.Structure):
     _fields_ = [
         ("n_particles", C.c_int32), ("max_depth", C.c_int32), ("n_nodes", C.c_int64),
@@ -107,6 +111,13 @@ SIGNATURES = {
     "mrdem_refine_contacts": (C.c_int, [_P, _P, _I64, _P, _P, _P, C.POINTER(mrdem_contacts),
                                         C.POINTER(mrdem_contacts), _P]),
     "mrdem_motion_bound": (C.c_int, [_P, _I, _P, _P, _P, _P, _P]),
+    "mrdem_active_set_init": (C.c_int, [_P, _P, _I64, _P, C.POINTER(mrdem_active_set), _P]),
+    "mrdem_active_set_step": (C.c_int, [_P, _P, _I64, _P, _P, _P, _I,
+                                        C.POINTER(mrdem_active_set),
+                                        C.POINTER(mrdem_active_set), C.POINTER(mrdem_contacts),
+                                        C.POINTER(mrdem_contacts), _P, _P]),
+    "mrdem_surrogate_forces": (C.c_int, [_P, _P, _I64, _P, _P, _P, C.POINTER(mrdem_contacts),
+                                         _P, _P, _D, _D, _P, _P, _P]),
     "mrdem_broad_phase": (C.c_int, [_P, _I, _P, _P, _P, _D, _P, _P, _I64, _P, _P]),
     "mrdem_move_poses": (C.c_int, [_P, _I, _P, _P, _D, _P, _P]),
     "mrdem_picard_update": (C.c_int, [_P, _I, _P, _P, _P, _P, _P, _D, _P, _P, _P]),

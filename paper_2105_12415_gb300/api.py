@@ -669,6 +669,171 @@ def implicit_euler_step(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inert
     return poses, vel, it, hist
 
 
+class ActiveSets:
+    """Caller-owned active sets of Algorithm 6 on the device: item
+    [capacity, 4] int32 (pair, node_a, node_b, flags), count one int64
+    (mrdem_active_set)."""
+
+    def __init__(self, capacity: int, device):
+        self.device = torch.device(device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.resize(capacity)
+
+    def resize(self, capacity: int):
+        self.capacity = max(int(capacity), 1)
+        self.item = torch.empty((self.capacity, 4), dtype=torch.int32, device=self.device)
+
+    def struct(self) -> L.mrdem_active_set:
+        return L.mrdem_active_set(self.capacity, self.count.data_ptr(), self.item.data_ptr())
+
+    def n(self) -> int:
+        return min(int(self.count.item()), self.capacity)
+
+    def to_numpy(self):
+        return self.item[:self.n()].cpu().numpy()
+
+
+def active_sets_init(ctx: Context, hier: Hierarchy, pairs, out=None, stream=None):
+    """The initial active sets of Algorithm 6: the two roots of every pair."""
+    P = pairs.shape[0]
+    _need(pairs, torch.int32, (P, 2), "pairs")
+    if out is None or out.capacity < P:
+        out = ActiveSets(max(1024, 16 * P), pairs.device)
+    st = out.struct()
+    L.check(L.load().mrdem_active_set_init(ctx.handle, hier.handle, P, _p(pairs), C.byref(st),
+                                           _stream(stream)), "mrdem_active_set_init")
+    return out
+
+
+def active_sets_step(ctx: Context, hier: Hierarchy, pairs, eps, poses, sets_in, sets_out=None,
+                     precision="fp32", contacts=None, surrogate=None, counts=None, check=True,
+                     stream=None, max_retries=4):
+    """One detection of Algorithm 6 on the active sets sets_in at poses: the
+    fine contacts of the listed pairs of leaves, the surrogate contacts, and
+    the next active sets in sets_out (widened and narrowed;
+    mrdem_active_set_step).  counts: int64 [4] on the device (items widened,
+    groups narrowed, pairs of leaves compared, surrogate contacts).  With
+    check=True the call synchronises, grows overflowing buffers and repeats.
+    Returns (sets_out, contacts, surrogate, counts)."""
+    info = hier.info()
+    P = _pair_args(hier, pairs, eps, poses, info["n_particles"])
+    dev = pairs.device
+    if sets_out is None:
+        sets_out = ActiveSets(max(sets_in.capacity, 1024), dev)
+    if contacts is None:
+        contacts = Contacts(max(1024, 64 * P), dev)
+    if surrogate is None:
+        surrogate = Contacts(max(1024, 4 * P), dev)
+    if counts is None:
+        counts = torch.zeros(4, dtype=torch.int64, device=dev)
+    lib = L.load()
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    for _ in range(max_retries + 1):
+        si, so, cs, ss = sets_in.struct(), sets_out.struct(), contacts.struct(), surrogate.struct()
+        L.check(lib.mrdem_active_set_step(ctx.handle, hier.handle, P, _p(pairs), _p(eps),
+                                          _p(poses), prec, C.byref(si), C.byref(so),
+                                          C.byref(cs), C.byref(ss), _p(counts),
+                                          _stream(stream)), "mrdem_active_set_step")
+        if not check:
+            return sets_out, contacts, surrogate, counts
+        req = np.zeros(5, np.int64)
+        st = lib.mrdem_check(ctx.handle, _stream(stream), _np_ptr(req))
+        if st == L.MRDEM_OK:
+            return sets_out, contacts, surrogate, counts
+        if st != L.MRDEM_ERR_CAPACITY:
+            L.check(st, "mrdem_active_set_step")
+        prm = ctx.params
+        grow = lambda need, cap: int(need * 1.25) + 1024 if need > cap else 0  # noqa: E731
+        ti, ca = grow(req[1], prm.cap_tiles), grow(req[2], prm.cap_candidates)
+        sw = grow(req[4], prm.cap_sweep)
+        if ti or ca or sw:
+            ctx.reserve(0, ti, ca, sw)
+        if req[3] > contacts.capacity:
+            contacts.resize(int(req[3] * 1.25) + 1024)
+        if int(surrogate.count.item()) > surrogate.capacity:
+            surrogate.resize(int(surrogate.count.item() * 1.25) + 1024)
+        if int(sets_out.count.item()) > sets_out.capacity:
+            sets_out.resize(int(sets_out.count.item() * 1.25) + 1024)
+    raise L.MrdemError(L.MRDEM_ERR_CAPACITY, "mrdem_active_set_step (retries exhausted)")
+
+
+def surrogate_forces(ctx, hier, pairs, eps, poses, surrogate, mass, com, k_s=1000.0, weight=0.25,
+                     force_torque=None, energy=None, stream=None):
+    """Forces and torques of surrogate contacts (mrdem_surrogate_forces),
+    accumulated into force_torque [n, 6] and energy [1]."""
+    n = hier.info()["n_particles"]
+    P = _pair_args(hier, pairs, eps, poses, n)
+    _need(mass, torch.float64, (n,), "mass")
+    _need(com, torch.float64, (n, 3), "com")
+    if force_torque is None:
+        force_torque = torch.zeros((n, 6), dtype=torch.float64, device=pairs.device)
+    if energy is None:
+        energy = torch.zeros(1, dtype=torch.float64, device=pairs.device)
+    ss = surrogate.struct()
+    L.check(L.load().mrdem_surrogate_forces(ctx.handle, hier.handle, P, _p(pairs), _p(eps),
+                                            _p(poses), C.byref(ss), _p(mass), _p(com), float(k_s),
+                                            float(weight), _p(force_torque), _p(energy),
+                                            _stream(stream)), "mrdem_surrogate_forces")
+    return force_torque, energy
+
+
+def implicit_euler_step_multires(ctx: Context, hier: Hierarchy, poses0, vel0, mass, inertia,
+                                 pairs, eps, dt, gravity=G_DEFAULT, k_s=1000.0, precision="fp32",
+                                 tol=1e-13, max_iter=200, weight=0.25):
+    """One implicit Euler step by the multiresolution Picard iteration of
+    Algorithm 6: every pair's active set starts at the two roots and is kept
+    across the iterations; each iteration moves the particles from poses0
+    by dt times the guessed velocities, tests the active sets there
+    (mrdem_active_set_step: fine contacts of the pairs of leaves in contact
+    range, surrogate contacts of the other pairs in range, which are widened
+    to their children, and narrowing of groups certainly apart), applies
+    the fine contacts' forces and the surrogate contacts' forces weighted by
+    `weight`, and updates the guess.  It stops when max |new - guess| <=
+    tol * max |new| and the iteration widened and narrowed nothing; the
+    result is then the plain implicit Euler step's fixed point.  One host
+    synchronisation per iteration.  Returns (poses, vel, iterations,
+    history of the relative change, per-iteration record)."""
+    n = poses0.shape[0]
+    dev = poses0.device
+    P = pairs.shape[0]
+    vel = vel0.clone()
+    poses = torch.empty_like(poses0)
+    com = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    ft = torch.zeros((n, 6), dtype=torch.float64, device=dev)
+    energy = torch.zeros(1, dtype=torch.float64, device=dev)
+    norms = torch.empty(2, dtype=torch.float64, device=dev)
+    counts = torch.zeros(4, dtype=torch.int64, device=dev)
+    sets = [active_sets_init(ctx, hier, pairs), None] if P else [None, None]
+    contacts = surrogate = None
+    hist, record = [], []
+    it = 0
+    for it in range(1, max_iter + 1):
+        move_poses(ctx, poses0, vel, dt, out=poses)
+        ft.zero_()
+        items = 0
+        if P:
+            items = sets[0].n()
+            sets[1], contacts, surrogate, counts = active_sets_step(
+                ctx, hier, pairs, eps, poses, sets[0], sets[1], precision, contacts, surrogate,
+                counts)
+            contact_forces(ctx, hier, pairs, eps, poses, contacts, mass, com, k_s,
+                           force_torque=ft, energy=energy)
+            surrogate_forces(ctx, hier, pairs, eps, poses, surrogate, mass, com, k_s, weight,
+                             force_torque=ft, energy=energy)
+            sets.reverse()
+        picard_update(ctx, vel0, ft, mass, inertia, dt, vel, norms, gravity)
+        change, scale = norms.tolist()
+        c = counts.tolist() if P else [0, 0, 0, 0]
+        scale += 1e-300
+        hist.append(change / scale)
+        record.append(dict(items=items, widened=c[0], narrowed=c[1], leaf_pairs=c[2],
+                           surrogate=c[3], contacts=contacts.n() if P else 0))
+        if change <= tol * scale and c[0] == 0 and c[1] == 0:
+            break
+    move_poses(ctx, poses0, vel, dt, out=poses)
+    return poses, vel, it, hist, record
+
+
 def newton_residual(ctx, vel0, vel, force_torque, mass, inertia, dt, res=None, norms=None,
                     gravity=G_DEFAULT, stream=None):
     """Residual M (vel - vel0)/dt - (F, tau) - (m g, 0) of the implicit Euler

@@ -20,7 +20,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 
 CU_SOURCES = ["mrdem_detect.cu", "mrdem_forces.cu", "mrdem_closest.cu", "mrdem_merge.cu",
-              "mrdem_step.cu", "mrdem_build.cu"]
+              "mrdem_step.cu", "mrdem_build.cu", "mrdem_frontier.cu"]
 CPP_SOURCES = ["mrdem_api.cpp", "mrdem_hierarchy.cpp"]
 HEADERS = ["mrdem_geometry.cuh", "mrdem_internal.h", "mrdem_device.cuh", "mrdem_dd.cuh",
            "mrdem_step.cuh"]

@@ -197,6 +197,7 @@ int mrdem_destroy(mrdem_ctx* c) {
   cudaFree(c->refine_mem);
   cudaFree(c->frames);
   cudaFree(c->frames_grad);
+  cudaFree(c->as_status);
   cudaFree(c->counters);
   cudaFree(c->status);
   delete c;
@@ -285,8 +286,9 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
   size_t sz_off = al(sizeof(int64_t) * (h.n_particles + 1));
   size_t sz_root = al(sizeof(int32_t) * h.n_particles), sz_br = al(sizeof(float) * h.n_particles);
   size_t sz_box = al(sizeof(float4) * 4 * h.n_nodes), sz_boxw = al(sizeof(float4) * h.n_nodes);
+  size_t sz_up = al(sizeof(int2) * h.n_nodes);
   size_t total = sz_geo + sz_child + sz_tri + sz_vid + sz_slot + sz_ts + sz_off + sz_root + sz_br +
-                 sz_sph + sz_nrm + sz_tsph + sz_box + sz_boxw;
+                 sz_sph + sz_nrm + sz_tsph + sz_box + sz_boxw + sz_up;
   char* base = nullptr;
   if (cudaMalloc(&base, total) != cudaSuccess) {
     cudaGetLastError();
@@ -299,7 +301,15 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     size_t o_slot = o_vid + sz_vid, o_ts = o_slot + sz_slot, o_off = o_ts + sz_ts;
     size_t o_root = o_off + sz_off, o_br = o_root + sz_root, o_sph = o_br + sz_br;
     size_t o_nrm = o_sph + sz_sph, o_tsph = o_nrm + sz_nrm, o_box = o_tsph + sz_tsph;
-    size_t o_boxw = o_box + sz_box;
+    size_t o_boxw = o_box + sz_box, o_up = o_boxw + sz_boxw;
+    // parent and level of every node (the active sets of the implicit step
+    // find a pair's parent pair from them)
+    int2* up = (int2*)(p + o_up);
+    for (int64_t n = 0; n < h.n_nodes; ++n) up[n] = make_int2(-1, h.node_level[n]);
+    for (int64_t n = 0; n < h.n_nodes; ++n) {
+      const int32_t b = h.node_child[2 * n], cnt = h.node_child[2 * n + 1];
+      for (int32_t k = 0; k < cnt; ++k) up[b + k].x = (int)n;
+    }
     float4* geo = (float4*)(p + o_geo);
     for (int64_t n = 0; n < h.n_nodes; ++n) {
       const float* t = &h.node_tri[9 * n];
@@ -418,6 +428,8 @@ int mrdem_hier_upload(mrdem_ctx* c, mrdem_hier* hier) {
     d.tri_slot = (const int32_t*)(base + o_ts);
     d.tri_off = (const int64_t*)(base + o_off);
     d.root = (const int32_t*)(base + o_root);
+    d.node_up = (const int2*)(base + o_up);
+    d.n_nodes = h.n_nodes;
     d.bound_r = (const float*)(base + o_br);
     d.node_sph = (const float4*)(base + o_sph);
     d.node_nrm = (const float4*)(base + o_nrm);
@@ -560,7 +572,7 @@ int mrdem_check(mrdem_ctx* c, mrdem_stream s, int64_t* required) {
   }
   if (st[ST_NONFINITE]) return MRDEM_ERR_NONFINITE;
   if (st[ST_REQ_LEVEL] || st[ST_REQ_TILES] || st[ST_REQ_CANDS] || st[ST_REQ_CONTACTS] ||
-      st[ST_REQ_SWEEP])
+      st[ST_REQ_SWEEP] || st[ST_REQ_ACTIVE])
     return MRDEM_ERR_CAPACITY;
   return MRDEM_OK;
 }
@@ -749,6 +761,52 @@ int mrdem_motion_bound(mrdem_ctx* c, int32_t n, const double* poses_ref, const d
   if (n > 0 && (!poses_ref || !poses || !bound)) return MRDEM_ERR_INVALID;
   DeviceGuard g(c->device);
   return launch_motion_bound(c, n, poses_ref, poses, bound, out, (cudaStream_t)s);
+}
+
+static bool active_ok(const mrdem_active_set* a) {
+  return a && a->count && a->capacity >= 0 && a->capacity < ((int64_t)1 << 31) &&
+         (a->capacity == 0 || (a->item && ((uintptr_t)a->item & 15) == 0));
+}
+
+int mrdem_active_set_init(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs,
+                          const int32_t* ab, const mrdem_active_set* out, mrdem_stream s) {
+  if (!c || !h || h->ctx != c || !h->d_mem || n_pairs < 0 || !active_ok(out) ||
+      out->capacity < n_pairs || (n_pairs > 0 && !ab))
+    return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_active_init(c, h, n_pairs, ab, out, (cudaStream_t)s);
+}
+
+int mrdem_active_set_step(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
+                          const double* eps, const double* poses, int precision,
+                          const mrdem_active_set* in, const mrdem_active_set* out,
+                          const mrdem_contacts* contacts, const mrdem_contacts* sur,
+                          int64_t* counts, mrdem_stream s) {
+  int st = check_pair_args(c, h, n_pairs, ab, eps, poses);
+  if (st) return st;
+  if (!active_ok(in) || !active_ok(out) || !contacts_ok(contacts) || !contacts_ok(sur) ||
+      (precision != MRDEM_PREC_FP32 && precision != MRDEM_PREC_FP64))
+    return MRDEM_ERR_INVALID;
+  if (in->item == out->item || in->count == out->count || contacts->count == sur->count ||
+      (contacts->pair && contacts->pair == sur->pair))
+    return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_active_step(c, h, n_pairs, ab, eps, poses, precision, in, out, contacts, sur,
+                            counts, (cudaStream_t)s);
+}
+
+int mrdem_surrogate_forces(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,
+                           const double* eps, const double* poses, const mrdem_contacts* sur,
+                           const double* mass, const double* com, double k_s, double weight,
+                           double* ft, double* energy, mrdem_stream s) {
+  int st = check_pair_args(c, h, n_pairs, ab, eps, poses);
+  if (st) return st;
+  if (!contacts_ok(sur) || !mass || !com || !ft || !(k_s >= 0) || !(weight >= 0) ||
+      !(weight <= 1))
+    return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return launch_surrogate_forces(c, h, n_pairs, ab, eps, poses, sur, mass, com, k_s, weight, ft,
+                                 energy, (cudaStream_t)s);
 }
 
 static const char* kKernelNames[K_COUNT] = {

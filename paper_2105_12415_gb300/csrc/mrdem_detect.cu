@@ -38,17 +38,6 @@ namespace mrdem {
 using F3 = V3<float>;
 using D3 = V3<double>;
 
-__device__ __forceinline__ TileItem make_tile(int pair, int na_node, int nb_node, int2 ia, int2 ib) {
-  TileItem t;
-  t.pair = pair;
-  t.node_a = na_node;
-  t.node_b = nb_node;
-  t.slot_a = ia.x;
-  t.slot_b = ib.x;
-  t.counts = (-ia.y) | ((-ib.y) << 8);
-  t.pad0 = t.pad1 = 0;
-  return t;
-}
 // Level item for the children of the node pair (node_a with child info ia,
 // node_b with ib); a leaf side is its own one-element set.
 __device__ __forceinline__ int4 make_level(int pair, int node_a, int node_b, int2 ia, int2 ib) {
@@ -821,7 +810,7 @@ __global__ void k_tridist(int64_t n, const double* __restrict__ Pin, const doubl
 
 // ---------------------------------------------------------------------------
 // launchers
-static int ensure_pairs(mrdem_ctx* c, int64_t n) {
+int ensure_pairs(mrdem_ctx* c, int64_t n) {
   if (n <= c->cap_pairs) return MRDEM_OK;
   int64_t cap = c->cap_pairs ? c->cap_pairs : 1024;
   while (cap < n) cap *= 2;
@@ -950,7 +939,7 @@ static int exact_blocks(const mrdem_ctx* c, int threads, int per_sm_128) {
   return c->n_sms * per_sm_128 * 128 / threads;
 }
 
-static SweepConst sweep_const(const mrdem_params& p) {
+SweepConst sweep_const(const mrdem_params& p) {
   SweepConst sc;
   sc.rho_reg = p.rho_reg;
   sc.rho_iter = p.rho_iter;
@@ -995,7 +984,7 @@ __global__ void __launch_bounds__(256) k_sort_scatter(mrdem_contacts tmp, int32_
 }
 
 // Scratch contact list with the caller's capacity.
-static int ensure_tmp(mrdem_ctx* c, int64_t cap, mrdem_contacts* tmp) {
+int ensure_tmp(mrdem_ctx* c, int64_t cap, mrdem_contacts* tmp) {
   if (cap > c->cap_tmp || !c->tmp_count) {
     cudaFree(c->tmp_i);
     cudaFree(c->tmp_d);
@@ -1030,6 +1019,60 @@ static int ensure_tmp(mrdem_ctx* c, int64_t cap, mrdem_contacts* tmp) {
 static int finish(cudaStream_t) {
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
+
+// The pairs' transforms alone (no root test): float, FP64 and double-float.
+int launch_setup_transforms(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs,
+                            const int32_t* ab, const double* eps, const double* poses,
+                            cudaStream_t s) {
+  if (n_pairs <= 0) return MRDEM_OK;
+  const int threads = 32;
+  const int blocks = (int)std::min<int64_t>((n_pairs + threads - 1) / threads, (int64_t)c->n_sms * 64);
+  ProfScope ps(c, K_SETUP, s);
+  k_setup<<<blocks, threads, 0, s>>>(hier->dev, (int)n_pairs, ab, eps, poses, c->xf, c->xf64,
+                                     c->xfdd, sweep_const(c->params), 0, c->level_list[0],
+                                     c->tiles, c->counters, c->status, c->cap_level, c->cap_tiles);
+  return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
+}
+
+// The finest-level stage and what follows it, on the leaf-pair tiles listed
+// in c->tiles (counter CNT_TILES): fine-vs-surrogate and sphere culls, the
+// fine sweeps, the exact distance into tmp, and the contacts grouped by pair
+// into out (pair_cnt holds each pair's count).
+int launch_fine_tail(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const double* eps,
+                     int precision, const mrdem_contacts* tmp, const mrdem_contacts* out,
+                     const Shape& sh, cudaStream_t s) {
+  const HierDev& H = hier->dev;
+  const mrdem_params& prm = c->params;
+  SweepConst sc = sweep_const(prm);
+  {
+    ProfScope ps(c, K_TILE, s);
+    launch_tile(c, sh, true, s, H, c->xf, c->tiles, c->sweep, c->counters, c->status,
+                c->cap_tiles, c->cap_sweep);
+  }
+  {
+    ProfScope ps(c, K_SWEEP_FINE, s);
+    launch_sweep_fine(c, sh, true, s, H, c->xf, sc, prm.conv_c, c->sweep, c->cands, c->counters,
+                      c->status, c->cap_sweep, c->cap_cands, eps);
+  }
+  const int et = sh.exact_threads;
+  if (precision == MRDEM_PREC_FP64) {
+    ProfScope ps(c, K_EXACT, s);
+    launch_after(k_exact64, exact_blocks(c, et, 8), et, 0, s, H, c->xf64, c->cands, c->counters,
+                 (int)CNT_CANDS, c->cap_cands, c->status, (int)MRDEM_STAT_FP64, *tmp,
+                 c->pair_cnt);
+  } else {
+    int r = launch_exact_fp32(c, hier, tmp, et, s);
+    if (r) return r;
+  }
+  // the contacts, grouped by pair, into the caller's buffers
+  {
+    ProfScope ps(c, K_SORT, s);
+    const int sb = c->n_sms * 4;
+    launch_after(k_sort_scan, 1, 1024, 0, s, c->pair_cnt, n_pairs);
+    launch_after(k_sort_scatter, sb, 256, 0, s, *tmp, c->pair_cnt, *out);
+  }
+  return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
 
 int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
@@ -1071,33 +1114,8 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
                          c->tiles, c->counters, c->status, c->cap_sweep, c->cap_level,
                          c->cap_tiles);
     }
-    {
-      ProfScope ps(c, K_TILE, s);
-      launch_tile(c, sh, true, s, H, c->xf, c->tiles, c->sweep, c->counters, c->status,
-                  c->cap_tiles, c->cap_sweep);
-    }
-    {
-      ProfScope ps(c, K_SWEEP_FINE, s);
-      launch_sweep_fine(c, sh, true, s, H, c->xf, sc, prm.conv_c, c->sweep, c->cands, c->counters,
-                        c->status, c->cap_sweep, c->cap_cands, eps);
-    }
-    const int et = sh.exact_threads;
-    if (precision == MRDEM_PREC_FP64) {
-      ProfScope ps(c, K_EXACT, s);
-      launch_after(k_exact64, exact_blocks(c, et, 8), et, 0, s, H, c->xf64, c->cands, c->counters,
-                   (int)CNT_CANDS, c->cap_cands, c->status, (int)MRDEM_STAT_FP64, tmp,
-                   c->pair_cnt);
-    } else {
-      int r = launch_exact_fp32(c, hier, &tmp, et, s);
-      if (r) return r;
-    }
-    // the contacts, grouped by pair, into the caller's buffers
-    {
-      ProfScope ps(c, K_SORT, s);
-      const int sb = c->n_sms * 4;
-      launch_after(k_sort_scan, 1, 1024, 0, s, c->pair_cnt, n_pairs);
-      launch_after(k_sort_scatter, sb, 256, 0, s, tmp, c->pair_cnt, *out);
-    }
+    int r = launch_fine_tail(c, hier, n_pairs, eps, precision, &tmp, out, sh, s);
+    if (r) return r;
   }
   if (stats)
     cudaMemcpyAsync(stats, c->counters + CNT_STATS, sizeof(int64_t) * MRDEM_STAT_COUNT,

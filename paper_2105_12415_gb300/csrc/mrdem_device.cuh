@@ -116,6 +116,18 @@ struct WarpQueue {
   }
 };
 
+// Tile item of a pair of leaves (ia, ib: their child records, slot ranges).
+__device__ __forceinline__ TileItem make_tile(int pair, int na_node, int nb_node, int2 ia, int2 ib) {
+  TileItem t;
+  t.pair = pair;
+  t.node_a = na_node;
+  t.node_b = nb_node;
+  t.slot_a = ia.x;
+  t.slot_b = ib.x;
+  t.counts = (-ia.y) | ((-ib.y) << 8);
+  t.pad0 = t.pad1 = 0;
+  return t;
+}
 __device__ __forceinline__ F3 xf_point(const PairXf& X, F3 v) {
   return {fmaf(X.R[0], v.x, fmaf(X.R[1], v.y, fmaf(X.R[2], v.z, X.t[0]))),
           fmaf(X.R[3], v.x, fmaf(X.R[4], v.y, fmaf(X.R[5], v.z, X.t[1]))),

@@ -49,6 +49,7 @@ struct HierDev {
                            // (c.xyz, h0) (u0.xyz, h1) (u1.xyz, h2) (u2.xyz, 0)
   const float4* node_boxw; // [n_nodes]: the box's half widths along its own three axes,
                            // sum_k h_k |u_s . u_k| (FP64 of the float axes, rounded up), 0
+  const int2* node_up;     // [n_nodes]: (parent node, -1 for a root; level, roots 1)
   const int32_t* vid;      // 3 planes: global vertex index of corner k of slot s
   const int32_t* slot_tri; // [stride] local input triangle index (-1 pad)
   const int32_t* tri_slot; // [n_tri] global input triangle -> slot
@@ -57,6 +58,7 @@ struct HierDev {
   const float* bound_r;    // [n]
   int64_t stride;          // plane stride (n_tri_pad rounded up)
   int64_t n_tri;
+  int64_t n_nodes;
   int32_t n_particles;
 };
 
@@ -144,6 +146,7 @@ enum Status : int {
   ST_REQ_CANDS,
   ST_REQ_CONTACTS,
   ST_REQ_SWEEP,
+  ST_REQ_ACTIVE,   // active-set items beyond the output's capacity
   ST_TOTAL = 8
 };
 
@@ -224,6 +227,11 @@ struct mrdem_ctx {
   // and a keep flag
   void* refine_mem = nullptr;
   size_t cap_refine = 0;
+  // active sets (Algorithm 6): per input item its outcome and its output
+  // count, then output offset (cap_active entries each)
+  int8_t* as_status = nullptr;
+  int32_t* as_off = nullptr;
+  int64_t cap_active = 0;
   double* frames = nullptr;  // [cap_frames * 16]: per particle R (9), t (3), world com (3)
   int64_t cap_frames = 0;
   double* frames_grad = nullptr;  // the adjoint's own tables (it may run beside the forces)
@@ -290,6 +298,30 @@ int launch_detect(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const
 int launch_plain(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const int32_t* pair_ab,
                  const double* pair_eps, const double* poses, const mrdem_contacts* out,
                  cudaStream_t s);
+// the finest-level stage of a detection whose leaf-pair tiles are listed:
+// tile, fine sweep, exact distance, contacts ordered by pair into out
+int launch_fine_tail(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const double* eps,
+                     int precision, const mrdem_contacts* tmp, const mrdem_contacts* out,
+                     const Shape& sh, cudaStream_t s);
+int ensure_pairs(mrdem_ctx* c, int64_t n);
+int launch_setup_transforms(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs,
+                            const int32_t* ab, const double* eps, const double* poses,
+                            cudaStream_t s);
+int ensure_tmp(mrdem_ctx* c, int64_t cap, mrdem_contacts* tmp);
+SweepConst sweep_const(const mrdem_params& p);
+// active sets of the multiresolution implicit step (mrdem_frontier.cu)
+int launch_active_init(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs,
+                       const int32_t* pair_ab, const mrdem_active_set* out, cudaStream_t s);
+int launch_active_step(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs,
+                       const int32_t* pair_ab, const double* pair_eps, const double* poses,
+                       int precision, const mrdem_active_set* in, const mrdem_active_set* out,
+                       const mrdem_contacts* contacts, const mrdem_contacts* surrogate,
+                       int64_t* counts, cudaStream_t s);
+int launch_surrogate_forces(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs,
+                            const int32_t* pair_ab, const double* pair_eps, const double* poses,
+                            const mrdem_contacts* sur, const double* mass, const double* com,
+                            double k_s, double weight, double* ft, double* energy,
+                            cudaStream_t s);
 // closest-point pipeline (mrdem_closest.cu)
 int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts* out,
                       int threads, cudaStream_t s);
