@@ -517,12 +517,23 @@ def run_packing(args):
     torch.cuda.synchronize()
     m._lib.check(lib.mrdem_check(ctx.handle, None, None), "multiresolution iterations")
     multires_ms = a.elapsed_time(b) / K
+    ctx.profile(True)
+    for _ in range(K):
+        multires_iter()
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    multires_parts = {k: round(v[0] / K, 4) for k, v in ctx.profile_read().items()}
+    flat_stats = stats.cpu().numpy()
     multires = {"ms_per_iteration": round(multires_ms, 4), "iterations_to_1e-6": it_m,
                 "wall_s": round(multires_s, 3), "active_items": act[0].n(),
                 "pairs_of_leaves": int(cnt_m[2].item()),
                 "widening_iterations": sum(r["widened"] > 0 for r in rec_m),
                 "surrogate_contacts_first": [r["surrogate"] for r in rec_m[:6]],
-                "agree_with_picard": float((Vp - Vm).abs().max().item() / Vp.abs().max().item())}
+                "agree_with_picard": float((Vp - Vm).abs().max().item() / Vp.abs().max().item()),
+                "ms_parts": multires_parts,
+                "flat_node_pair_tests": int(flat_stats[m._lib.MRDEM_STAT_TESTS:
+                                                       m._lib.MRDEM_STAT_TESTS + 8].sum()),
+                "flat_leaf_tiles": int(flat_stats[m._lib.MRDEM_STAT_TILES])}
 
     # enqueued Newton iterations: Hessian blocks, CG solve, one residual evaluation
     blocks = torch.zeros((P, 12, 12), dtype=torch.float64, device=dev)

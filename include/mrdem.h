@@ -112,6 +112,9 @@ typedef struct mrdem_params {
   int64_t cap_sweep;      /* capacity of the list of pairs waiting for the penalty sweep */
   int32_t expand_items;   /* k_expand: level items a warp takes per pass, at most (8, 16, 32) */
   int32_t node_threads;   /* k_sweep_nodes: threads per block (128, 256) */
+  int32_t level_kernel;   /* surrogate levels: 0 = two launches per level (k_expand,
+                             k_sweep_nodes); 1 = one cooperative launch over all levels,
+                             grid-wide barriers between the phases */
 } mrdem_params;
 
 /* Contact output.  All arrays are caller-owned device memory of `capacity`
@@ -275,12 +278,14 @@ int mrdem_detect(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const 
  * events, and stores for the batch's size class (n_pairs < 256, < 4096,
  * < 65536, larger) the fastest value of each shape parameter: k_expand warps
  * per block and items per warp, k_sweep_nodes threads, k_tile warps,
- * k_sweep_fine warps, exact-pass threads.  Later mrdem_detect and
+ * k_sweep_fine warps, exact-pass threads; then the chosen shape once more
+ * with the surrogate levels in one cooperative launch (level_kernel 1),
+ * kept when its detection is faster.  Later mrdem_detect and
  * mrdem_detect_noalloc calls of that size class use them; mrdem_set_params
  * clears the table.  Synchronises the device (do not call during stream
  * capture).  The results of every shape are the same contact set; *out holds
- * the last run's.  chosen: NULL or host int32 [6] (the six values in that
- * order); ms: NULL or host double [2], the time of one detection with the
+ * the last run's.  chosen: NULL or host int32 [7] (the six values in that
+ * order, then level_kernel); ms: NULL or host double [2], the time of one detection with the
  * params' shapes and with the chosen ones.  Errors: INVALID, CUDA, CAPACITY
  * or NONFINITE when a run overflowed a list or met a bad input (status left
  * latched for mrdem_check; grow the lists and call again). */

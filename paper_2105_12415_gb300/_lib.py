@@ -50,7 +50,7 @@ class mrdem_params(C.Structure):
         ("cap_tiles", C.c_int64), ("cap_candidates", C.c_int64), ("tile_warps", C.c_int32),
         ("sweep_warps", C.c_int32), ("level_warps", C.c_int32),
         ("exact_threads", C.c_int32), ("cap_sweep", C.c_int64), ("expand_items", C.c_int32),
-        ("node_threads", C.c_int32),
+        ("node_threads", C.c_int32), ("level_kernel", C.c_int32),
     ]
 
 

@@ -278,7 +278,7 @@ def detect(ctx: Context, hier: Hierarchy, pairs, eps, poses, precision="fp32", c
 
 
 TUNED_FIELDS = ("level_warps", "expand_items", "node_threads", "tile_warps", "sweep_warps",
-                "exact_threads")
+                "exact_threads", "level_kernel")
 
 
 def autotune(ctx: Context, hier: Hierarchy, pairs, eps, poses, precision="fp32", contacts=None,
@@ -290,7 +290,7 @@ def autotune(ctx: Context, hier: Hierarchy, pairs, eps, poses, precision="fp32",
     contacts, _ = detect(ctx, hier, pairs, eps, poses, precision, contacts=contacts)
     P = _pair_args(hier, pairs, eps, poses, hier.info()["n_particles"])
     prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
-    chosen = np.zeros(6, np.int32)
+    chosen = np.zeros(len(TUNED_FIELDS), np.int32)
     ms = np.zeros(2)
     cs = contacts.struct()
     L.check(L.load().mrdem_autotune(ctx.handle, hier.handle, P, _p(pairs), _p(eps), _p(poses), prec,

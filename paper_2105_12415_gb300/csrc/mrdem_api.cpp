@@ -33,7 +33,8 @@ bool params_ok(const mrdem_params& p) {
          p.cap_candidates < kMaxCandidates && p.cap_sweep > 0 && p.cap_sweep < (int64_t)1 << 31 &&
          one_of(p.tile_warps, {2, 4, 8}) && one_of(p.sweep_warps, {2, 4, 8}) &&
          one_of(p.level_warps, {2, 4, 8}) && one_of(p.exact_threads, {64, 128, 256}) &&
-         one_of(p.expand_items, {8, 16, 32}) && one_of(p.node_threads, {128, 256});
+         one_of(p.expand_items, {8, 16, 32}) && one_of(p.node_threads, {128, 256}) &&
+         one_of(p.level_kernel, {0, 1});
 }
 
 void free_lists(mrdem_ctx* c) {
@@ -50,6 +51,8 @@ void free_lists(mrdem_ctx* c) {
   cudaFree(c->res_ee);
   cudaFree(c->items_cx);
   cudaFree(c->res_cx);
+  cudaFree(c->d2_pt);
+  c->d2_pt = c->d2_ee = c->d2_cx = nullptr;
   c->acc = nullptr;
   c->items_pt = c->items_ee = c->items_cx = nullptr;
   c->res_pt = c->res_ee = c->res_cx = nullptr;
@@ -73,7 +76,8 @@ int alloc_lists(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca, int64_t sw) {
       cudaMalloc(&c->res_pt, sizeof(ItemRes) * 2 * ca) != cudaSuccess ||
       cudaMalloc(&c->res_ee, sizeof(ItemRes) * 2 * ca) != cudaSuccess ||
       cudaMalloc(&c->items_cx, sizeof(int) * 2 * ca) != cudaSuccess ||
-      cudaMalloc(&c->res_cx, sizeof(ItemRes) * 2 * ca) != cudaSuccess) {
+      cudaMalloc(&c->res_cx, sizeof(ItemRes) * 2 * ca) != cudaSuccess ||
+      cudaMalloc(&c->d2_pt, sizeof(dd) * 3 * 2 * ca) != cudaSuccess) {
     cudaGetLastError();
     free_lists(c);
     return MRDEM_ERR_OOM;
@@ -83,6 +87,8 @@ int alloc_lists(mrdem_ctx* c, int64_t lv, int64_t ti, int64_t ca, int64_t sw) {
   c->cap_cands = ca;
   c->cap_sweep = sw;
   c->cap_items = 2 * ca;
+  c->d2_ee = c->d2_pt + 2 * ca;
+  c->d2_cx = c->d2_ee + 2 * ca;
   return MRDEM_OK;
 }
 
@@ -126,6 +132,7 @@ void mrdem_default_params(mrdem_params* p) {
   p->exact_threads = 128;
   p->expand_items = 32;
   p->node_threads = 256;
+  p->level_kernel = 0;
   p->cap_sweep = (int64_t)1 << 25;
 }
 

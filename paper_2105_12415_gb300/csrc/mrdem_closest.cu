@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) k_cp_float(HierDev H, const PairXf* __res
 template <int KIND>
 __global__ void __launch_bounds__(256) k_cp_items(const AccRec* __restrict__ acc,
                                                   const int* __restrict__ items, int count_slot,
-                                                  int64_t cap_items, ItemRes* res,
+                                                  int64_t cap_items, ItemRes* res, dd* d2_out,
                                                   const unsigned long long* cnt) {
   wait_prior_grid();
   int64_t n = (int64_t)cnt[count_slot];
@@ -201,36 +201,25 @@ __global__ void __launch_bounds__(256) k_cp_items(const AccRec* __restrict__ acc
     o[1] = make_float4(pa.y.hi, pa.y.lo, pa.z.hi, pa.z.lo);
     o[2] = make_float4(pb.x.hi, pb.x.lo, pb.y.hi, pb.y.lo);
     o[3] = make_float4(pb.z.hi, pb.z.lo, 0.f, 0.f);
+    d2_out[k] = d2;
   }
 }
 
-// Exact pass: contacts of the accepted candidates.  Eight lanes per
-// accepted pair take its work items in the fixed order (crossings, then
-// point-triangle, then edge-edge items) and reduce them to the pair's
-// result: the first crossing that crossed, else the first smallest squared
-// distance (so a pair's item results are read side by side, not one after
-// another).  This is the choice of tri_tri_distance: a crossing in
-// the fixed order ends the test, else the first minimum wins.  A warp
-// scans its 32 pairs four at a time and hands each pair's choice to the
-// pair's own lane, so that the double-float finishing (world points) runs
-// with every lane busy.
-constexpr int kSelLanes = 8;
-struct SelBest {
-  int cls;    // 0: a crossing, 1: a distance, 2: none
-  int order;  // position in the fixed order
-  dd d2;
-};
-__device__ __forceinline__ bool sel_better(const SelBest& a, const SelBest& b) {
-  if (a.cls != b.cls) return a.cls < b.cls;
-  if (a.cls == 1 && !(a.d2 == b.d2)) return a.d2 < b.d2;
-  return a.order < b.order;
-}
-
+// Exact pass: contacts of the accepted candidates.  One thread per accepted
+// pair reads its items' squared distances from the packed arrays (a pair's
+// items are contiguous, so a warp's reads share sectors) in the fixed order
+// (crossings, then point-triangle, then edge-edge items) and takes the first
+// crossing that crossed, else the first smallest squared distance: the
+// choice of tri_tri_distance.  Only the chosen item's full record (its
+// closest points) is read.
 __global__ void __launch_bounds__(256) k_select_exact(HierDev H, const PairXfDD* __restrict__ xfdd,
                                                       const AccRec* __restrict__ acc,
                                                       const ItemRes* __restrict__ res_pt,
                                                       const ItemRes* __restrict__ res_ee,
                                                       const ItemRes* __restrict__ res_cx,
+                                                      const dd* __restrict__ d2_pt,
+                                                      const dd* __restrict__ d2_ee,
+                                                      const dd* __restrict__ d2_cx,
                                                       const int3* __restrict__ cands,
                                                       unsigned long long* cnt, int64_t cap_acc,
                                                       unsigned long long* status,
@@ -239,70 +228,44 @@ __global__ void __launch_bounds__(256) k_select_exact(HierDev H, const PairXfDD*
   int64_t n = (int64_t)cnt[CNT_ACC];
   if (n > cap_acc) n = cap_acc;
   WarpCount ncon;
-  const int lane = lane_id(), g = lane / kSelLanes, gl = lane % kSelLanes;
-  constexpr int kGroups = 32 / kSelLanes;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t kb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); kb < n;
-       kb += stride) {
-    // the warp's 32 pairs in rounds of four: in round r, group g scans pair
-    // kb + 4 r + g, and lane 4 r + g' keeps group g''s choice (its own pair)
-    int mine = -1;
-#pragma unroll 1
-    for (int r = 0; r < kSelLanes; ++r) {
-      const int64_t k = kb + kGroups * r + g;
-      SelBest best = {2, 1 << 30, dd(INFINITY)};
-      if (k < n) {
-        const AccRec& a = acc[k];
-        const int npt = a.counts & 0xff, nee = (a.counts >> 8) & 0xff;
-        const int ncx = (a.counts >> 16) & 0xff;
-        for (int t = gl; t < ncx + npt + nee; t += kSelLanes) {
-          SelBest cand;
-          cand.order = t;
-          if (t < ncx) {
-            cand.d2 = res_cx[a.cx_begin + t].d2;
-            cand.cls = cand.d2.hi == 0.f ? 0 : 2;
-          } else {
-            const int q = t - ncx;
-            cand.d2 = q < npt ? res_pt[a.pt_begin + q].d2 : res_ee[a.ee_begin + (q - npt)].d2;
-            cand.cls = 1;
-          }
-          if (sel_better(cand, best)) best = cand;
-        }
-      }
-      // the group's best (lanes of a group share one pair)
-#pragma unroll
-      for (int o = kSelLanes / 2; o > 0; o >>= 1) {
-        SelBest other;
-        other.cls = __shfl_xor_sync(0xffffffffu, best.cls, o);
-        other.order = __shfl_xor_sync(0xffffffffu, best.order, o);
-        other.d2.hi = __shfl_xor_sync(0xffffffffu, best.d2.hi, o);
-        other.d2.lo = __shfl_xor_sync(0xffffffffu, best.d2.lo, o);
-        if (sel_better(other, best)) best = other;
-      }
-      const int got = __shfl_sync(0xffffffffu, best.cls < 2 ? best.order : -1,
-                                  (lane % kGroups) * kSelLanes);
-      if (lane / kGroups == r) mine = got;
-    }
-    // every lane finishes its own pair kb + lane
-    const int64_t k = kb + lane;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t k = base + threadIdx.x;
     bool hit = false;
     int3 c = make_int3(0, 0, 0);
     double d = 0;
     D3 pa = {0, 0, 0}, pb = {0, 0, 0};
-    if (k < n && mine >= 0) {
-      const AccRec& a = acc[k];
-      const int npt = a.counts & 0xff, ncx = (a.counts >> 16) & 0xff;
-      const int t = mine;
-      const ItemRes* b = t < ncx ? res_cx + a.cx_begin + t
-                                 : (t - ncx < npt ? res_pt + a.pt_begin + (t - ncx)
-                                                  : res_ee + a.ee_begin + (t - ncx - npt));
-      d = ldexp(to_double(dd_sqrt(b->d2)), a.g.k);
-      hit = d <= a.g.tau;
-      if (hit) {
-        c = cands[a.entry];
-        const PairXfDD& X = xfdd[a.pair];
-        pa = world_point(X, b->pa, a.g.k, a.g.o);
-        pb = world_point(X, b->pb, a.g.k, a.g.o);
+    if (k < n) {
+      const AccRec& r = acc[k];
+      const int npt = r.counts & 0xff, nee = (r.counts >> 8) & 0xff;
+      const int ncx = (r.counts >> 16) & 0xff;
+      const ItemRes* b = nullptr;
+      for (int q = 0; q < ncx && !b; ++q)
+        if (d2_cx[r.cx_begin + q].hi == 0.f) b = res_cx + r.cx_begin + q;
+      if (!b) {
+        int best = -1;
+        dd bd = dd(INFINITY);
+#pragma unroll 2
+        for (int q = 0; q < npt; ++q) {
+          const dd v = d2_pt[r.pt_begin + q];
+          if (best < 0 || v < bd) { bd = v; best = q; }
+        }
+#pragma unroll 3
+        for (int q = 0; q < nee; ++q) {
+          const dd v = d2_ee[r.ee_begin + q];
+          if (best < 0 || v < bd) { bd = v; best = npt + q; }
+        }
+        if (best >= 0) b = best < npt ? res_pt + r.pt_begin + best : res_ee + r.ee_begin + (best - npt);
+      }
+      if (b) {
+        d = ldexp(to_double(dd_sqrt(b->d2)), r.g.k);
+        hit = d <= r.g.tau;
+        if (hit) {
+          c = cands[r.entry];
+          const PairXfDD& X = xfdd[r.pair];
+          pa = world_point(X, b->pa, r.g.k, r.g.o);
+          pb = world_point(X, b->pb, r.g.k, r.g.o);
+        }
       }
     }
     ncon.add(hit);
@@ -325,13 +288,14 @@ int launch_exact_fp32(mrdem_ctx* c, const mrdem_hier* hier, const mrdem_contacts
                c->counters, c->status);
   int ib = c->n_sms * 8;
   launch_after(k_cp_items<0>, ib, 256, 0, s, c->acc, c->items_pt, (int)CNT_PT, c->cap_items,
-               c->res_pt, c->counters);
+               c->res_pt, c->d2_pt, c->counters);
   launch_after(k_cp_items<1>, ib, 256, 0, s, c->acc, c->items_ee, (int)CNT_EE, c->cap_items,
-               c->res_ee, c->counters);
+               c->res_ee, c->d2_ee, c->counters);
   launch_after(k_cp_items<2>, ib, 256, 0, s, c->acc, c->items_cx, (int)CNT_CX, c->cap_items,
-               c->res_cx, c->counters);
+               c->res_cx, c->d2_cx, c->counters);
   launch_after(k_select_exact, eb, threads, 0, s, hier->dev, c->xfdd, c->acc, c->res_pt,
-               c->res_ee, c->res_cx, c->cands, c->counters, c->cap_cands, c->status, *out,
+               c->res_ee, c->res_cx, (const dd*)c->d2_pt, (const dd*)c->d2_ee,
+               (const dd*)c->d2_cx, c->cands, c->counters, c->cap_cands, c->status, *out,
                c->pair_cnt);
   return cudaGetLastError() == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }

@@ -25,6 +25,7 @@
 //                  contacts (d <= 2 eps) appended to the caller's buffers.
 // The pruning only discards pairs whose certified lower bound exceeds the
 // threshold, so the contact set equals the brute-force one (Lemma 1).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,6 +36,7 @@
 
 namespace mrdem {
 
+namespace cg = cooperative_groups;
 using F3 = V3<float>;
 using D3 = V3<double>;
 
@@ -174,24 +176,40 @@ __global__ void k_setup(HierDev H, int n_pairs, const int32_t* __restrict__ ab,
 // resident wave.
 
 // k_expand --------------------------------------------------------------------
+// Loads of a work list or counter.  COH: the list was written earlier in
+// the same launch by other blocks (the cooperative form), so the load goes
+// through L2 (ld.global.cg), never the non-coherent read-only path.
+template <bool COH>
+__device__ __forceinline__ int4 ld_item(const int4* __restrict__ p) {
+  if (COH) return __ldcg(p);
+  return *p;
+}
+template <bool COH>
+__device__ __forceinline__ int64_t ld_count(const unsigned long long* p) {
+  if (COH) return (int64_t)__ldcg(p);
+  return (int64_t)*p;
+}
+
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* __restrict__ xf,
-                                                       const int4* __restrict__ in, int level,
-                                                       int4* sweep, unsigned long long* cnt,
-                                                       unsigned long long* status,
-                                                       int64_t cap_level, int64_t cap_sweep,
-                                                       int max_items) {
-  wait_prior_grid();
-  __shared__ int soff[WARPS][32];
-  __shared__ int4 sit[WARPS][32];
-  __shared__ int4 sq[WARPS][128];
+struct ExpandSmem {
+  int off[WARPS][32];
+  int4 it[WARPS][32];
+  int4 q[WARPS][128];
+};
+
+template <int WARPS, bool COH>
+__device__ __forceinline__ void expand_level(const HierDev& H, const PairXf* __restrict__ xf,
+                                             const int4* __restrict__ in, int level, int4* sweep,
+                                             unsigned long long* cnt, unsigned long long* status,
+                                             int64_t cap_level, int64_t cap_sweep, int max_items,
+                                             ExpandSmem<WARPS>& sm) {
   const int w = threadIdx.x >> 5, lane = lane_id();
-  int64_t n_in = (int64_t)cnt[CNT_LEVEL + level];
+  int64_t n_in = ld_count<COH>(cnt + CNT_LEVEL + level);
   if (n_in > cap_level) n_in = cap_level;
   const int slot_tests = MRDEM_STAT_TESTS + (level + 1 < MRDEM_STAT_LEVELS ? level + 1 : MRDEM_STAT_LEVELS - 1);
   WarpCount tests, boxcut;
   WarpQueue<int4, 128> outq;
-  outq.buf = sq[w];
+  outq.buf = sm.q[w];
   // items per warp and pass: the smallest power of two that spreads the
   // level over every resident warp, max_items at most (a power of two <= 32)
   const int64_t warps = (int64_t)gridDim.x * WARPS;
@@ -199,17 +217,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
   while (C > 1 && (int64_t)(C >> 1) * warps >= n_in) C >>= 1;
   const int64_t step = warps * C;
   int64_t base = ((int64_t)blockIdx.x * WARPS + w) * C;
-  int4 nxt = lane < C && base + lane < n_in ? in[base + lane] : make_int4(0, 0, 0, 0);
+  int4 nxt = lane < C && base + lane < n_in ? ld_item<COH>(in + base + lane) : make_int4(0, 0, 0, 0);
   for (; base < n_in; base += step) {
     // this warp's C items: child-pair counts, their offsets (exclusive scan)
     const int4 it = nxt;
     const bool valid = lane < C && base + lane < n_in;
-    if (lane < C && base + step + lane < n_in) nxt = in[base + step + lane];
+    if (lane < C && base + step + lane < n_in) nxt = ld_item<COH>(in + base + step + lane);
     const int c = valid ? (it.w & 0xff) * ((it.w >> 8) & 0xff) : 0;
     const int incl = warp_scan(c);
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    soff[w][lane] = incl - c;
-    sit[w][lane] = it;
+    sm.off[w][lane] = incl - c;
+    sm.it[w][lane] = it;
     __syncwarp();
     for (int f0 = 0; f0 < total; f0 += 32) {
       const int f = f0 + lane;
@@ -218,10 +236,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
       // child pairs share the next item's offset and are never picked)
       int l = 0;
       for (int b = C >> 1; b > 0; b >>= 1)
-        if (soff[w][l + b] <= f) l += b;
-      const int4 o = sit[w][l];
+        if (sm.off[w][l + b] <= f) l += b;
+      const int4 o = sm.it[w][l];
       const int nb = (o.w >> 8) & 0xff;
-      const int r = act ? f - soff[w][l] : 0;
+      const int r = act ? f - sm.off[w][l] : 0;
       const int i = (int)(((float)r + 0.5f) * (1.0f / (float)(nb > 0 ? nb : 1)));
       const int j = r - i * nb;
       bool keep = false, boxed = false;
@@ -255,30 +273,47 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
   boxcut.flush(cnt + CNT_STATS + MRDEM_STAT_BOX_PRUNED);
 }
 
-// k_sweep_nodes ---------------------------------------------------------------
-__global__ void __launch_bounds__(256, 4) k_sweep_nodes(HierDev H, const PairXf* __restrict__ xf,
-                                                     SweepConst sc, const int4* __restrict__ sweep,
-                                                     int level, int4* out, TileItem* tiles,
-                                                     unsigned long long* cnt,
-                                                     unsigned long long* status, int64_t cap_sweep,
-                                                     int64_t cap_level, int64_t cap_tiles) {
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* __restrict__ xf,
+                                                       const int4* __restrict__ in, int level,
+                                                       int4* sweep, unsigned long long* cnt,
+                                                       unsigned long long* status,
+                                                       int64_t cap_level, int64_t cap_sweep,
+                                                       int max_items) {
   wait_prior_grid();
-  int64_t n = (int64_t)cnt[CNT_SWEEP + level];
+  __shared__ ExpandSmem<WARPS> sm;
+  expand_level<WARPS, false>(H, xf, in, level, sweep, cnt, status, cap_level, cap_sweep,
+                             max_items, sm);
+}
+
+// k_sweep_nodes ---------------------------------------------------------------
+struct SweepNodesSmem {
+  TileItem tq[8][64];
+  int4 lq[8][64];
+};
+
+template <bool COH>
+__device__ __forceinline__ void sweep_level(const HierDev& H, const PairXf* __restrict__ xf,
+                                            const SweepConst& sc, const int4* __restrict__ sweep,
+                                            int level,
+                                            int4* out, TileItem* tiles, unsigned long long* cnt,
+                                            unsigned long long* status, int64_t cap_sweep,
+                                            int64_t cap_level, int64_t cap_tiles,
+                                            SweepNodesSmem& sm) {
+  int64_t n = ld_count<COH>(cnt + CNT_SWEEP + level);
   if (n > cap_sweep) n = cap_sweep;
   const int slot_surv = MRDEM_STAT_SURVIVORS + (level + 1 < MRDEM_STAT_LEVELS ? level + 1 : MRDEM_STAT_LEVELS - 1);
   WarpCount nsweep, surv;
-  __shared__ TileItem stq[8][64];
-  __shared__ int4 slq[8][64];
   const int w = threadIdx.x >> 5;
   WarpQueue<TileItem, 64> tq;
   WarpQueue<int4, 64> lq;
-  tq.buf = stq[w];
-  lq.buf = slq[w];
+  tq.buf = sm.tq[w];
+  lq.buf = sm.lq[w];
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     int64_t k = base + threadIdx.x;
     bool act = k < n, s = false;
-    int4 e = act ? sweep[k] : make_int4(0, 0, 0, 0);
+    int4 e = act ? ld_item<COH>(sweep + k) : make_int4(0, 0, 0, 0);
     int2 ia = make_int2(0, 1), ib = make_int2(0, 1);
     if (act) {
       PairXf X;
@@ -316,6 +351,47 @@ __global__ void __launch_bounds__(256, 4) k_sweep_nodes(HierDev H, const PairXf*
   lq.flush(out, cnt + CNT_LEVEL + level + 1, cap_level, status + ST_REQ_LEVEL);
   nsweep.flush(cnt + CNT_STATS + MRDEM_STAT_LEVEL_SWEEPS);
   surv.flush(cnt + CNT_STATS + slot_surv);
+}
+
+__global__ void __launch_bounds__(256, 4) k_sweep_nodes(HierDev H, const PairXf* __restrict__ xf,
+                                                     SweepConst sc, const int4* __restrict__ sweep,
+                                                     int level, int4* out, TileItem* tiles,
+                                                     unsigned long long* cnt,
+                                                     unsigned long long* status, int64_t cap_sweep,
+                                                     int64_t cap_level, int64_t cap_tiles) {
+  wait_prior_grid();
+  __shared__ SweepNodesSmem sm;
+  sweep_level<false>(H, xf, sc, sweep, level, out, tiles, cnt, status, cap_sweep, cap_level,
+                     cap_tiles, sm);
+}
+
+// k_levels: every surrogate level in one cooperative launch (level_kernel 1):
+// for each level the expand phase and the sweep phase of the two kernels
+// above, separated by grid-wide barriers, over the same one-wave grid (so
+// the level lists keep their interleaved assignment).  The lists the phases
+// read were written in the same launch, hence the L2 loads.  It saves the
+// launches and the per-launch ramps; each barrier waits for the level's
+// slowest block, as the launch boundary did.
+constexpr int kLevelWarps = 8;
+union LevelSmem {
+  ExpandSmem<kLevelWarps> e;
+  SweepNodesSmem s;
+};
+__global__ void __launch_bounds__(kLevelWarps * 32) k_levels(
+    HierDev H, const PairXf* __restrict__ xf, SweepConst sc, int4* list0, int4* list1,
+    int4* sweep, TileItem* tiles, unsigned long long* cnt, unsigned long long* status,
+    int64_t cap_level, int64_t cap_sweep, int64_t cap_tiles, int steps, int max_items) {
+  wait_prior_grid();
+  __shared__ LevelSmem sm;
+  cg::grid_group g = cg::this_grid();
+  for (int l = 0; l < steps; ++l) {
+    expand_level<kLevelWarps, true>(H, xf, (l & 1) ? list1 : list0, l, sweep, cnt, status,
+                                    cap_level, cap_sweep, max_items, sm.e);
+    g.sync();
+    sweep_level<true>(H, xf, sc, sweep, l, ((l + 1) & 1) ? list1 : list0, tiles, cnt, status,
+                      cap_sweep, cap_level, cap_tiles, sm.s);
+    if (l + 1 < steps) g.sync();
+  }
 }
 
 // k_tile ----------------------------------------------------------------------
@@ -866,7 +942,7 @@ Shape shape_for(const mrdem_ctx* c, int64_t n_pairs) {
   if (c->tuned_ok[k]) return c->tuned[k];
   const mrdem_params& p = c->params;
   return {p.level_warps, p.expand_items, p.node_threads, p.tile_warps, p.sweep_warps,
-          p.exact_threads};
+          p.exact_threads, p.level_kernel};
 }
 
 // Launch helpers over the kernels' block shapes (one template instance per
@@ -932,6 +1008,27 @@ static void launch_sweep_nodes(mrdem_ctx* c, const Shape& sh, bool pdl, cudaStre
   const int t = sh.node_threads;
   launch_pdl(pdl, k_sweep_nodes, one_wave(c, k_sweep_nodes, t, 0), t, s, H, xf, sc, sweep, level,
              out, tiles, cnt, status, cap_sweep, cap_level, cap_tiles);
+}
+// All surrogate levels in one cooperative launch (k_levels) on a one-wave
+// grid: every block is resident, as the grid-wide barriers require.
+static int launch_levels_coop(mrdem_ctx* c, cudaStream_t s, const HierDev& H, SweepConst sc,
+                              int steps, int max_items) {
+  const int grid = one_wave(c, k_levels, kLevelWarps * 32, 0);
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeCooperative;
+  attr.val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kLevelWarps * 32);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_levels, H, (const PairXf*)c->xf, sc,
+                                           c->level_list[0], c->level_list[1], c->sweep, c->tiles,
+                                           c->counters, c->status, c->cap_level, c->cap_sweep,
+                                           c->cap_tiles, steps, max_items);
+  return e == cudaSuccess ? MRDEM_OK : MRDEM_ERR_CUDA;
 }
 // k_exact64 grid: 8 blocks per SM at 128 threads, the same threads per SM
 // otherwise.
@@ -1103,7 +1200,12 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
     }
     int steps = std::min(hier->h.max_depth - 1, kMaxLevels - 1);
     const Shape sh = shape_for(c, n_pairs);
-    for (int l = 0; l < steps; ++l) {
+    if (sh.level_kernel == 1 && steps > 0) {
+      ProfScope ps(c, K_LEVEL, s);
+      int r = launch_levels_coop(c, s, H, sc, steps, sh.expand_items);
+      if (r) return r;
+    }
+    for (int l = 0; l < steps && sh.level_kernel != 1; ++l) {
       {
         ProfScope ps(c, K_LEVEL, s);
         launch_expand(c, sh, true, s, H, c->xf, c->level_list[l & 1], l, c->sweep, c->counters,
@@ -1145,7 +1247,7 @@ int autotune(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_
   }
   const mrdem_params& p = c->params;
   const Shape base = {p.level_warps, p.expand_items, p.node_threads, p.tile_warps, p.sweep_warps,
-                      p.exact_threads};
+                      p.exact_threads, p.level_kernel};
   double t_exp[3][3] = {}, t_nodes[2] = {}, t_tile[3] = {}, t_sweep[3] = {}, t_exact[3] = {};
   int n_exp[3][3] = {}, n_nodes[2] = {}, n_tile[3] = {}, n_sweep[3] = {}, n_exact[3] = {};
   const bool prof_was = c->prof;
@@ -1196,7 +1298,7 @@ int autotune(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_
   };
   for (int i = 0; i < 9 && st == MRDEM_OK; ++i) {
     const int e = i % 3, f = i / 3, g = (i + 1) % 3, q = (i + 2) % 3, x = (i + i / 3) % 3;
-    const Shape sh = {LW[e], EI[f], NT[i % 2], TW[g], SW[q], ET[x]};
+    const Shape sh = {LW[e], EI[f], NT[i % 2], TW[g], SW[q], ET[x], 0};
     double kt[K_COUNT] = {}, tot = 0.0;
     st = run(sh, kt, &tot);
     if (st != MRDEM_OK) break;
@@ -1227,10 +1329,18 @@ int autotune(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_
           bf = f;
         }
     best = {LW[be], EI[bf], NT[argmin(t_nodes, n_nodes, 2)], TW[argmin(t_tile, n_tile, 3)],
-            SW[argmin(t_sweep, n_sweep, 3)], ET[argmin(t_exact, n_exact, 3)]};
-    double t_base = 0.0, t_best = 0.0;
+            SW[argmin(t_sweep, n_sweep, 3)], ET[argmin(t_exact, n_exact, 3)], 0};
+    double t_base = 0.0, t_best = 0.0, t_coop = 0.0;
     st = run(base, nullptr, &t_base);
     if (st == MRDEM_OK) st = run(best, nullptr, &t_best);
+    // the same shape with every surrogate level in one cooperative launch
+    Shape coop = best;
+    coop.level_kernel = 1;
+    if (st == MRDEM_OK) st = run(coop, nullptr, &t_coop);
+    if (st == MRDEM_OK && t_coop < t_best) {
+      best = coop;
+      t_best = t_coop;
+    }
     if (st == MRDEM_OK) {
       const int k = size_class(n_pairs);
       c->tuned[k] = best;
@@ -1246,6 +1356,7 @@ int autotune(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_
         chosen[3] = best.tile_warps;
         chosen[4] = best.sweep_warps;
         chosen[5] = best.exact_threads;
+        chosen[6] = best.level_kernel;
       }
     }
   }

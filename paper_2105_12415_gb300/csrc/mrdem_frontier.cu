@@ -20,8 +20,8 @@
 //                index 0 of its parent pair) checks the items that follow;
 //                when the whole group is listed, bottom and not vetoed, it
 //                emits the parent and the others nothing (narrowing);
-//   k_as_scan    one block: the output offsets, in input order, so the next
-//                sets stay in depth-first order;
+//   k_as_scan_*  the output offsets, in input order, so the next sets stay
+//                in depth-first order (chunk sums, their scan, chunk rescans);
 //   k_as_emit    one thread per item: its output items;
 //   the finest-level stage of mrdem_detect on the tile list (fine culls,
 //   fine sweeps, exact distance, contacts grouped by pair).
@@ -248,10 +248,76 @@ __global__ void __launch_bounds__(kAsThreads) k_as_narrow(HierDev H, int64_t n_p
   narrowed.flush(reinterpret_cast<unsigned long long*>(counts + 1));
 }
 
-__global__ void __launch_bounds__(1024) k_as_scan(mrdem_active_set in, int32_t* em,
-                                                  int64_t* total) {
+// Output offsets: an exclusive scan of the per-item output counts in place,
+// in three passes over a one-wave grid (each block owns one contiguous
+// chunk): chunk sums, one block scanning them (and writing the total), then
+// each chunk rescanned tile by tile from its offset.  Offsets are stored as
+// int32, clamped (an output that large overflows the capacity anyway).
+constexpr int kScanMaxBlocks = 1024;
+__device__ __forceinline__ void chunk_of(int64_t n, int64_t& b, int64_t& e) {
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  b = (int64_t)blockIdx.x * chunk;
+  e = b + chunk < n ? b + chunk : n;
+}
+__global__ void __launch_bounds__(kAsThreads) k_as_scan_part(mrdem_active_set in,
+                                                             const int32_t* __restrict__ em,
+                                                             int64_t* bsum) {
   wait_prior_grid();
-  block_exclusive_scan(em, clamp_count(in), total);
+  __shared__ int64_t wsum[kAsThreads / 32];
+  int64_t b, e;
+  chunk_of(clamp_count(in), b, e);
+  int64_t v = 0;
+  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) v += em[i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane_id() == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kAsThreads / 32; ++w) t += wsum[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+__global__ void __launch_bounds__(kScanMaxBlocks) k_as_scan_top(int64_t* bsum, int nb,
+                                                                int64_t* total) {
+  wait_prior_grid();
+  __shared__ int64_t part[kScanMaxBlocks];
+  const int t = threadIdx.x;
+  const int64_t v = t < nb ? bsum[t] : 0;
+  part[t] = v;
+  __syncthreads();
+  for (int o = 1; o < kScanMaxBlocks; o <<= 1) {
+    const int64_t x = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  if (t < nb) bsum[t] = part[t] - v;
+  if (t == kScanMaxBlocks - 1) *total = part[t];
+}
+__global__ void __launch_bounds__(kAsThreads) k_as_scan_apply(mrdem_active_set in, int32_t* em,
+                                                              const int64_t* __restrict__ bsum) {
+  wait_prior_grid();
+  __shared__ int wtot[kAsThreads / 32];
+  int64_t b, e;
+  chunk_of(clamp_count(in), b, e);
+  int64_t carry = bsum[blockIdx.x];
+  const int w = threadIdx.x >> 5;
+  for (int64_t base = b; base < e; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int v = i < e ? em[i] : 0;
+    const int incl = warp_scan(v);
+    if (lane_id() == 31) wtot[w] = incl;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int k = 0; k < kAsThreads / 32; ++k) {
+      before += k < w ? wtot[k] : 0;
+      all += wtot[k];
+    }
+    const int64_t o = carry + before + incl - v;
+    if (i < e) em[i] = (int32_t)(o < INT32_MAX ? o : INT32_MAX);
+    carry += all;
+    __syncthreads();
+  }
 }
 
 __global__ void __launch_bounds__(kAsThreads) k_as_emit(HierDev H, mrdem_active_set in,
@@ -348,7 +414,12 @@ __global__ void __launch_bounds__(kAsThreads) k_sur_forces(
   }
 }
 
-// Per-item scratch (outcome, count / offset) and four counters.
+// Per-item scratch (outcome, count / offset), four counters and the scan's
+// chunk sums.
+size_t active_off_bytes(int64_t n) { return (size_t)(n + 255) / 256 * 256; }
+size_t active_cnt_bytes(int64_t n) {
+  return (active_off_bytes(n) + sizeof(int32_t) * (size_t)n + 15) / 16 * 16;
+}
 int ensure_active(mrdem_ctx* c, int64_t cap) {
   if (cap <= c->cap_active && c->as_status) return MRDEM_OK;
   cudaFree(c->as_status);
@@ -356,21 +427,20 @@ int ensure_active(mrdem_ctx* c, int64_t cap) {
   c->as_off = nullptr;
   c->cap_active = 0;
   const int64_t n = std::max<int64_t>(cap, 1);
-  const size_t b_st = (size_t)(n + 255) / 256 * 256;
   char* mem = nullptr;
-  if (cudaMalloc(&mem, b_st + sizeof(int32_t) * n + 4 * sizeof(int64_t) + 16) != cudaSuccess) {
+  const size_t bytes = active_cnt_bytes(n) + sizeof(int64_t) * (4 + kScanMaxBlocks);
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
     cudaGetLastError();
     return MRDEM_ERR_OOM;
   }
   c->as_status = reinterpret_cast<int8_t*>(mem);
-  c->as_off = reinterpret_cast<int32_t*>(mem + b_st);
+  c->as_off = reinterpret_cast<int32_t*>(mem + active_off_bytes(n));
   c->cap_active = n;
   return MRDEM_OK;
 }
 int64_t* active_counts(mrdem_ctx* c) {
-  const size_t b_st = (size_t)(c->cap_active + 255) / 256 * 256;
-  const size_t b = b_st + sizeof(int32_t) * c->cap_active;
-  return reinterpret_cast<int64_t*>(reinterpret_cast<char*>(c->as_status) + (b + 15) / 16 * 16);
+  return reinterpret_cast<int64_t*>(reinterpret_cast<char*>(c->as_status) +
+                                    active_cnt_bytes(c->cap_active));
 }
 
 }  // namespace
@@ -415,7 +485,11 @@ int launch_active_step(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs,
                    c->as_off, c->tiles, c->counters, c->status, c->cap_tiles, *sur);
       launch_after(k_as_narrow, blocks, kAsThreads, 0, s, H, n_pairs, *in, c->as_status,
                    c->as_off, cnt4);
-      launch_after(k_as_scan, 1, 1024, 0, s, *in, c->as_off, out->count);
+      const int sb = std::min(kScanMaxBlocks, c->n_sms * 4);
+      int64_t* bsum = cnt4 + 4;
+      launch_after(k_as_scan_part, sb, kAsThreads, 0, s, *in, (const int32_t*)c->as_off, bsum);
+      launch_after(k_as_scan_top, 1, kScanMaxBlocks, 0, s, bsum, sb, out->count);
+      launch_after(k_as_scan_apply, sb, kAsThreads, 0, s, *in, c->as_off, (const int64_t*)bsum);
       launch_after(k_as_emit, blocks, kAsThreads, 0, s, H, *in, (const int8_t*)c->as_status,
                    (const int32_t*)c->as_off, *out, cnt4, c->status);
     }

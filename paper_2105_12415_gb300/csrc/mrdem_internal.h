@@ -168,6 +168,7 @@ struct Shape {
   int tile_warps;     // k_tile: warps per block (2, 4, 8)
   int sweep_warps;    // k_sweep_fine: warps per block (2, 4, 8)
   int exact_threads;  // exact pass: threads per block (64, 128, 256)
+  int level_kernel;   // surrogate levels: 0 per-level launches, 1 one cooperative launch
 };
 constexpr int kSizeClasses = 4;  // particle pairs per call: < 256, < 4096, < 65536, more
 inline int size_class(int64_t n_pairs) {
@@ -195,6 +196,10 @@ struct mrdem_ctx {
   mrdem::ItemRes* res_ee = nullptr;  // [cap_items]
   int* items_cx = nullptr;          // [cap_items] crossing work items
   mrdem::ItemRes* res_cx = nullptr;  // [cap_items]
+  // each item's squared distance again, packed (the selection reads these)
+  mrdem::dd* d2_pt = nullptr;
+  mrdem::dd* d2_ee = nullptr;
+  mrdem::dd* d2_cx = nullptr;
   int64_t cap_items = 0;
   int64_t cap_level = 0, cap_tiles = 0, cap_cands = 0, cap_sweep = 0;
   mrdem::PairXf* xf = nullptr;
