@@ -301,6 +301,21 @@ int mrdem_autotune(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs,
  * latch. */
 int mrdem_check(mrdem_ctx* ctx, mrdem_stream stream, int64_t* required);
 
+/* The same check without a synchronisation of its own, for callers that
+ * synchronise anyway (a step whose results go back to the host): enqueues
+ * on `stream` a copy of the latched status words into host_words and then
+ * clears the latch.  host_words: MRDEM_STATUS_WORDS uint64 of page-locked
+ * (pinned) host memory, owned by the caller, valid once the stream has
+ * reached that point (after a synchronisation of the caller's own); then
+ * mrdem_status_decode reads them.  Stream-ordered, no allocation, no host
+ * synchronisation (capturable).  Errors: INVALID (null pointers), CUDA. */
+#define MRDEM_STATUS_WORDS 8
+int mrdem_status_async(mrdem_ctx* ctx, uint64_t* host_words, mrdem_stream stream);
+/* Decode status words copied by mrdem_status_async, as mrdem_check reports
+ * them: CAPACITY (required[0..4] as in mrdem_check when required != NULL),
+ * NONFINITE or OK.  Host only. */
+int mrdem_status_decode(const uint64_t* host_words, int64_t* required);
+
 /* Penalty forces of a contact set (Sec. 2, F(c)):
  *   F = K_s sqrt(mu) (1 - d/(2 eps)) u on A and -F on B,
  *   mu = 1/(1/M_A + 1/M_B), u = (point_a - point_b)/d (at d = 0: minus the

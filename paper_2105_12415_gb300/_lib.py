@@ -40,6 +40,7 @@ MRDEM_STAT_ITEMS_PT = 28
 MRDEM_STAT_ITEMS_EE = 29
 MRDEM_STAT_BOX_PRUNED = 30
 MRDEM_STAT_COUNT = 32
+MRDEM_STATUS_WORDS = 8
 
 
 class mrdem_params(C.Structure):
@@ -111,6 +112,8 @@ SIGNATURES = {
     "mrdem_refine_contacts": (C.c_int, [_P, _P, _I64, _P, _P, _P, C.POINTER(mrdem_contacts),
                                         C.POINTER(mrdem_contacts), _P]),
     "mrdem_motion_bound": (C.c_int, [_P, _I, _P, _P, _P, _P, _P]),
+    "mrdem_status_async": (C.c_int, [_P, _P, _P]),
+    "mrdem_status_decode": (C.c_int, [_P, _P]),
     "mrdem_active_set_init": (C.c_int, [_P, _P, _I64, _P, C.POINTER(mrdem_active_set), _P]),
     "mrdem_active_set_step": (C.c_int, [_P, _P, _I64, _P, _P, _P, _I,
                                         C.POINTER(mrdem_active_set),

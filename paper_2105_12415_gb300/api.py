@@ -1060,13 +1060,21 @@ class ContactProblem:
                                            _p(gv), _p(gp), _p(jac), C.c_void_p(side.cuda_stream)),
                     "mrdem_contact_grad")
             torch.cuda.current_stream().wait_stream(side)
+        # the status words to pinned host memory at the end of the step (no
+        # synchronisation of their own: the step's one synchronisation covers them)
+        if getattr(self, "_status_host", None) is None:
+            self._status_host = torch.zeros(L.MRDEM_STATUS_WORDS, dtype=torch.int64).pin_memory()
+        L.check(lib.mrdem_status_async(c, C.c_void_p(self._status_host.data_ptr()), s),
+                "mrdem_status_async")
 
     def _check_and_grow(self):
-        """Status of the work just enqueued (synchronises the stream): True if
-        it completed, False after growing an overflowing list."""
+        """Status of the work just enqueued (synchronises the stream once and
+        decodes the status words the step copied to the host): True if it
+        completed, False after growing an overflowing list."""
         lib = L.load()
         req = np.zeros(5, np.int64)
-        st = lib.mrdem_check(self.ctx.handle, _stream(None), _np_ptr(req))
+        torch.cuda.current_stream().synchronize()
+        st = lib.mrdem_status_decode(C.c_void_p(self._status_host.data_ptr()), _np_ptr(req))
         if st == L.MRDEM_OK:
             return True
         if st != L.MRDEM_ERR_CAPACITY:
@@ -1083,11 +1091,14 @@ class ContactProblem:
         return False
 
     def step(self, scale=1.0, want_verts=True, want_pose=True, want_jac=False, graph=True,
-             max_retries=4):
+             max_retries=4, host_out=None):
         """Detection, forces and energy, and the adjoint of the whole batch in
         one call on the current stream.  The status is checked once, at the end
         (one synchronisation); after a list overflow the lists grow and the
-        step runs again.  With graph=True the sequence is captured once into a
+        step runs again.  host_out: None, or a dict of pinned host tensors
+        (keys among "ft", "energy", "gv", "gp", "jac", "count") that receive
+        those results before the synchronisation, so that a caller who wants
+        them on the host needs no synchronisation of its own.  With graph=True the sequence is captured once into a
         CUDA graph (captured again after a list grows or the flags change) and
         replayed, so the inputs must be updated in place (pairs, eps, poses,
         mass, com keep their storage).  Returns tensors owned by the problem,
@@ -1113,6 +1124,11 @@ class ContactProblem:
                 torch.cuda.current_stream().wait_stream(side)
                 self._graph, self._graph_key = g, key
                 g.replay()
+            if host_out:
+                ft, energy, gv, gp, jac, _ = self._outputs(want_verts, want_pose, want_jac)
+                src = dict(ft=ft, energy=energy, gv=gv, gp=gp, jac=jac, count=self.contacts.count)
+                for k, t in host_out.items():
+                    t.copy_(src[k], non_blocking=True)
             if self._check_and_grow():
                 ft, energy, gv, gp, jac, stats = self._outputs(want_verts, want_pose, want_jac)
                 return self.contacts, ft, energy, gv, gp, jac, stats

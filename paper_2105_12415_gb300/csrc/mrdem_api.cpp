@@ -560,16 +560,7 @@ int mrdem_autotune(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int
   return autotune(c, h, n_pairs, ab, eps, poses, precision, out, reps, chosen, ms);
 }
 
-int mrdem_check(mrdem_ctx* c, mrdem_stream s, int64_t* required) {
-  if (!c) return MRDEM_ERR_INVALID;
-  DeviceGuard g(c->device);
-  unsigned long long st[ST_TOTAL];
-  if (cudaStreamSynchronize((cudaStream_t)s) != cudaSuccess ||
-      cudaMemcpy(st, c->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemset(c->status, 0, sizeof(st)) != cudaSuccess) {
-    cudaGetLastError();
-    return MRDEM_ERR_CUDA;
-  }
+static int decode_status(const unsigned long long* st, int64_t* required) {
   if (required) {
     required[0] = (int64_t)st[ST_REQ_LEVEL];
     required[1] = (int64_t)st[ST_REQ_TILES];
@@ -582,6 +573,38 @@ int mrdem_check(mrdem_ctx* c, mrdem_stream s, int64_t* required) {
       st[ST_REQ_SWEEP] || st[ST_REQ_ACTIVE])
     return MRDEM_ERR_CAPACITY;
   return MRDEM_OK;
+}
+
+int mrdem_check(mrdem_ctx* c, mrdem_stream s, int64_t* required) {
+  if (!c) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  unsigned long long st[ST_TOTAL];
+  if (cudaStreamSynchronize((cudaStream_t)s) != cudaSuccess ||
+      cudaMemcpy(st, c->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(c->status, 0, sizeof(st)) != cudaSuccess) {
+    cudaGetLastError();
+    return MRDEM_ERR_CUDA;
+  }
+  return decode_status(st, required);
+}
+
+int mrdem_status_async(mrdem_ctx* c, uint64_t* host_words, mrdem_stream s) {
+  static_assert(MRDEM_STATUS_WORDS == ST_TOTAL, "status words");
+  if (!c || !host_words) return MRDEM_ERR_INVALID;
+  DeviceGuard g(c->device);
+  const size_t bytes = sizeof(unsigned long long) * ST_TOTAL;
+  if (cudaMemcpyAsync(host_words, c->status, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)s) !=
+          cudaSuccess ||
+      cudaMemsetAsync(c->status, 0, bytes, (cudaStream_t)s) != cudaSuccess) {
+    cudaGetLastError();
+    return MRDEM_ERR_CUDA;
+  }
+  return MRDEM_OK;
+}
+
+int mrdem_status_decode(const uint64_t* host_words, int64_t* required) {
+  if (!host_words) return MRDEM_ERR_INVALID;
+  return decode_status(reinterpret_cast<const unsigned long long*>(host_words), required);
 }
 
 int mrdem_contact_forces(mrdem_ctx* c, const mrdem_hier* h, int64_t n_pairs, const int32_t* ab,

@@ -114,3 +114,24 @@ def test_plain_c_caller(tmp_path):
     assert "trees: 2 particles" in r.stdout
     if not torch.cuda.is_available():
         assert "no GPU here" in r.stdout
+
+
+def test_status_words_decode_like_the_check():
+    """mrdem_status_decode on hand-made status words: overflow counts go to
+    `required` in mrdem_check's order and give CAPACITY, a non-finite input
+    gives NONFINITE first, an overflowing active-set list gives CAPACITY."""
+    import numpy as np
+    import paper_2105_12415_gb300 as m
+    lib = m.load()
+    assert m._lib.MRDEM_STATUS_WORDS == 8
+
+    def decode(words):
+        w = np.asarray(words, np.uint64)
+        req = np.full(5, -1, np.int64)
+        st = lib.mrdem_status_decode(C.c_void_p(w.ctypes.data), C.c_void_p(req.ctypes.data))
+        return st, req.tolist()
+    assert decode([0] * 8) == (0, [0, 0, 0, 0, 0])
+    assert decode([0, 7, 0, 0, 123, 0, 0, 0]) == (m._lib.MRDEM_ERR_CAPACITY, [7, 0, 0, 123, 0])
+    assert decode([1, 0, 0, 5, 0, 0, 0, 0])[0] == m._lib.MRDEM_ERR_NONFINITE
+    assert decode([0, 0, 0, 0, 0, 0, 9, 0])[0] == m._lib.MRDEM_ERR_CAPACITY
+    assert lib.mrdem_status_decode(None, None) == m._lib.MRDEM_ERR_INVALID

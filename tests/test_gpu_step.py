@@ -82,3 +82,23 @@ def test_contacts_grouped_by_pair():
     pairs = c.to_numpy(sort=False)["pair"]
     assert len(pairs) > 0
     assert np.all(np.diff(pairs) >= 0)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_step_copies_results_to_pinned_host_buffers(graph):
+    """step(host_out=...) leaves the results of the run that succeeded in the
+    caller's pinned host tensors, also when the first run overflowed its
+    lists and the step grew them and ran again."""
+    import torch
+    s = scene_tiny(n_pairs=12, levels=(1, 2))
+    small = _problem(s, cap_level=16, cap_tiles=16, cap_candidates=16, cap_sweep=16)
+    n = s.n_particles
+    host = {"ft": torch.empty((n, 6), dtype=torch.float64).pin_memory(),
+            "gp": torch.empty((n, 6), dtype=torch.float64).pin_memory(),
+            "energy": torch.empty(1, dtype=torch.float64).pin_memory(),
+            "count": torch.empty(1, dtype=torch.int64).pin_memory()}
+    for _ in range(2):
+        c, ft, e, _, gp, _, _ = small.step(graph=graph, host_out=host)
+        assert np.array_equal(host["ft"].numpy(), ft.cpu().numpy())
+        assert np.array_equal(host["gp"].numpy(), gp.cpu().numpy())
+        assert host["energy"].item() == e.item() and host["count"].item() == c.count.item() > 0
