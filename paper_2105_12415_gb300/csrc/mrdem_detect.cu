@@ -1064,11 +1064,21 @@ __global__ void __launch_bounds__(256) k_sort_scatter(mrdem_contacts tmp, int32_
   int64_t n = *tmp.count;
   if (blockIdx.x == 0 && threadIdx.x == 0) *out.count = n;
   if (n > tmp.capacity) n = tmp.capacity;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int p = tmp.pair[k];
-    const int64_t j = atomicAdd(pair_cnt + p, 1);
-    if (j >= out.capacity) continue;
+  const int lane = lane_id();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t k = base + threadIdx.x;
+    const bool in = k < n;
+    const int p = in ? tmp.pair[k] : -1;
+    // the lanes holding one pair (a warp's contacts mostly share one) take
+    // their slots with one atomic
+    const unsigned grp = __match_any_sync(0xffffffffu, p);
+    const int leader = __ffs(grp) - 1;
+    int j0 = 0;
+    if (in && lane == leader) j0 = atomicAdd(pair_cnt + p, __popc(grp));
+    j0 = __shfl_sync(0xffffffffu, j0, leader);
+    const int64_t j = (int64_t)j0 + __popc(grp & ((1u << lane) - 1u));
+    if (!in || j >= out.capacity) continue;
     out.pair[j] = p;
     out.tri_a[j] = tmp.tri_a[k];
     out.tri_b[j] = tmp.tri_b[k];

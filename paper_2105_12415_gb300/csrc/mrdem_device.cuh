@@ -411,16 +411,25 @@ __device__ __forceinline__ void write_contact(const HierDev& H, const mrdem_cont
   b = __shfl_sync(0xffffffffu, b, leader);
   if (!hit) return;
   unsigned long long idx = b + __popc(m & ((1u << lane_id()) - 1u));
-  if ((int64_t)idx < out.capacity) {
+  const bool stored = (int64_t)idx < out.capacity;
+  if (stored) {
     out.pair[idx] = pair;
     out.tri_a[idx] = H.slot_tri[sa];
     out.tri_b[idx] = H.slot_tri[sb];
     out.dist[idx] = d;
     out.point_a[3 * idx] = pa.x; out.point_a[3 * idx + 1] = pa.y; out.point_a[3 * idx + 2] = pa.z;
     out.point_b[3 * idx] = pb.x; out.point_b[3 * idx + 1] = pb.y; out.point_b[3 * idx + 2] = pb.z;
-    if (pair_cnt) atomicAdd(pair_cnt + pair, 1);
   } else {
     atomicMax(status + ST_REQ_CONTACTS, idx + 1);
+  }
+  // per-pair counts: one atomic per group of stored lanes holding one pair
+  // (the contacts of a warp mostly share their pair)
+  if (pair_cnt) {
+    const unsigned sm = __ballot_sync(m, stored);
+    if (stored) {
+      const unsigned g = __match_any_sync(sm, pair);
+      if ((int)lane_id() == __ffs(g) - 1) atomicAdd(pair_cnt + pair, __popc(g));
+    }
   }
 }
 
