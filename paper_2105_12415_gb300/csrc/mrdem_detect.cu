@@ -371,13 +371,14 @@ __global__ void __launch_bounds__(256, 4) k_sweep_nodes(HierDev H, const PairXf*
 // the level lists keep their interleaved assignment).  The lists the phases
 // read were written in the same launch, hence the L2 loads.  It saves the
 // launches and the per-launch ramps; each barrier waits for the level's
-// slowest block, as the launch boundary did.
+// slowest block, as the launch boundary did.  Three blocks per SM (80
+// registers; the two phases alone would take 111 and allow two).
 constexpr int kLevelWarps = 8;
 union LevelSmem {
   ExpandSmem<kLevelWarps> e;
   SweepNodesSmem s;
 };
-__global__ void __launch_bounds__(kLevelWarps * 32) k_levels(
+__global__ void __launch_bounds__(kLevelWarps * 32, 3) k_levels(
     HierDev H, const PairXf* __restrict__ xf, SweepConst sc, int4* list0, int4* list1,
     int4* sweep, TileItem* tiles, unsigned long long* cnt, unsigned long long* status,
     int64_t cap_level, int64_t cap_sweep, int64_t cap_tiles, int steps, int max_items) {
