@@ -205,6 +205,9 @@ int mrdem_destroy(mrdem_ctx* c) {
   cudaFree(c->frames);
   cudaFree(c->frames_grad);
   cudaFree(c->as_status);
+  if (c->merge_side) cudaStreamDestroy(c->merge_side);
+  for (cudaEvent_t e : c->merge_ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(c->counters);
   cudaFree(c->status);
   delete c;

@@ -221,6 +221,9 @@ struct mrdem_ctx {
   void* merge_mem = nullptr;
   int64_t cap_merge = 0;
   bool merge_smem_set = false;
+  // the large pairs' merge runs beside the small pairs' on a second stream
+  cudaStream_t merge_side = nullptr;
+  cudaEvent_t merge_ev[2] = {nullptr, nullptr};
   // broad phase of the implicit step: grid record, per-particle cells, order
   // and counts, bucket ends (cap_broad bytes)
   void* broad_mem = nullptr;

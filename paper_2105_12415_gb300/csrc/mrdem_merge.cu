@@ -46,7 +46,7 @@ namespace {
 constexpr int kSmallCap = 64;     // contacts of a pair handled by one warp
 constexpr int kLaneSum = 16;      // components up to this size are summed by one thread
 constexpr int kSmallWarps = 4;
-constexpr int kLargeThreads = 256;
+constexpr int kLargeThreads = 512;
 constexpr int kLargeCap = 1024;   // contacts of a pair held in shared memory by one block
 // pa, pb, key, xf, sx, src, px, parent
 constexpr int kEntryBytes = 24 + 24 + 8 + 12 + 4 + 4 + 4 + 4;
@@ -668,7 +668,10 @@ int launch_merge(mrdem_ctx* c, int64_t n_pairs, const double* eps, const mrdem_c
   if (st) return st;
   if (!c->merge_smem_set) {  // the context's device
     if (cudaFuncSetAttribute(k_merge_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kLargeSmem) != cudaSuccess) {
+                             (int)kLargeSmem) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->merge_side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->merge_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->merge_ev[1], cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       return MRDEM_ERR_CUDA;
     }
@@ -685,11 +688,18 @@ int launch_merge(mrdem_ctx* c, int64_t n_pairs, const double* eps, const mrdem_c
   launch_after(k_merge_count, flat, 256, 0, s, *in, n_pairs, eps, seg, c->status);
   launch_after(k_merge_scan, 1, 1024, 0, s, seg, n_pairs, (int64_t*)nullptr);
   launch_after(k_merge_scatter, flat, 256, 0, s, *in, n_pairs, seg, g.idx);
+  // the pairs of more than kSmallCap contacts (few, a block each) run on the
+  // second stream beside the small pairs (a warp each): they write disjoint
+  // segments; both streams join before the scan of the merged counts
+  cudaEventRecord(c->merge_ev[0], s);
+  cudaStreamWaitEvent(c->merge_side, c->merge_ev[0], 0);
+  k_merge_large<<<gl, kLargeThreads, kLargeSmem, c->merge_side>>>(
+      *in, n_pairs, eps, (const int32_t*)seg, g, mcnt);
+  cudaEventRecord(c->merge_ev[1], c->merge_side);
   launch_after(k_merge_small, gs, kSmallWarps * 32, 0, s, *in, n_pairs, eps, (const int32_t*)seg,
                g, mcnt);
-  launch_after(k_merge_large, gl, kLargeThreads, kLargeSmem, s, *in, n_pairs, eps,
-               (const int32_t*)seg, g, mcnt);
-  launch_after(k_merge_scan, 1, 1024, 0, s, mcnt, n_pairs, out->count);
+  cudaStreamWaitEvent(s, c->merge_ev[1], 0);
+  k_merge_scan<<<1, 1024, 0, s>>>(mcnt, n_pairs, out->count);
   launch_after(k_merge_copy, flat, 256, 0, s, g, n_pairs, (const int32_t*)seg,
                (const int32_t*)mcnt, *out, members, c->status);
   const cudaError_t e = cudaGetLastError();
