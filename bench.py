@@ -938,6 +938,7 @@ def main():
         h_gp = torch.empty((scene.n_particles, 6), dtype=torch.float64).pin_memory()
         h_e = torch.empty(1, dtype=torch.float64).pin_memory()
         h_n = torch.empty(1, dtype=torch.int64).pin_memory()
+        host_in = {"poses": h_poses, "pairs": h_pairs, "eps": h_eps}
         host_out = {"ft": h_ft, "gp": h_gp, "energy": h_e, "count": h_n}
         e_ms = 0.0
         for k in range(args.steps):
@@ -946,12 +947,10 @@ def main():
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record()
-            prob.poses.copy_(h_poses, non_blocking=True)
-            prob.pairs.copy_(h_pairs, non_blocking=True)
-            prob.eps.copy_(h_eps, non_blocking=True)
-            # one public call: detect + forces + adjoint, the results copied to
-            # the host and the status checked with one synchronisation
-            prob.step(want_jac=True, host_out=host_out)
+            # one public call: the inputs copied from pinned host memory,
+            # detect + forces + adjoint, the results copied back, the status
+            # checked with one synchronisation
+            prob.step(want_jac=True, host_in=host_in, host_out=host_out)
             b.record()
             b.synchronize()
             e_ms += a.elapsed_time(b)

@@ -1031,9 +1031,11 @@ class ContactProblem:
         return (o["ft"], o["energy"], o["gv"] if want_verts else None,
                 o["gp"] if want_pose else None, o["jac"] if want_jac else None, o["stats"])
 
-    def _enqueue(self, scale, want_verts, want_pose, want_jac):
+    def _enqueue(self, scale, want_verts, want_pose, want_jac, host_in=None, host_out=None):
         lib = L.load()
         ft, energy, gv, gp, jac, stats = self._outputs(want_verts, want_pose, want_jac)
+        for k, t in (host_in or {}).items():
+            getattr(self, k).copy_(t, non_blocking=True)
         for t in (ft, energy, gv, gp, jac):
             if t is not None:
                 t.zero_()
@@ -1060,6 +1062,10 @@ class ContactProblem:
                                            _p(gv), _p(gp), _p(jac), C.c_void_p(side.cuda_stream)),
                     "mrdem_contact_grad")
             torch.cuda.current_stream().wait_stream(side)
+        if host_out:
+            src = dict(ft=ft, energy=energy, gv=gv, gp=gp, jac=jac, count=self.contacts.count)
+            for k, t in host_out.items():
+                t.copy_(src[k], non_blocking=True)
         # the status words to pinned host memory at the end of the step (no
         # synchronisation of their own: the step's one synchronisation covers them)
         if getattr(self, "_status_host", None) is None:
@@ -1091,44 +1097,46 @@ class ContactProblem:
         return False
 
     def step(self, scale=1.0, want_verts=True, want_pose=True, want_jac=False, graph=True,
-             max_retries=4, host_out=None):
+             max_retries=4, host_in=None, host_out=None):
         """Detection, forces and energy, and the adjoint of the whole batch in
         one call on the current stream.  The status is checked once, at the end
         (one synchronisation); after a list overflow the lists grow and the
-        step runs again.  host_out: None, or a dict of pinned host tensors
-        (keys among "ft", "energy", "gv", "gp", "jac", "count") that receive
-        those results before the synchronisation, so that a caller who wants
-        them on the host needs no synchronisation of its own.  With graph=True the sequence is captured once into a
+        step runs again.  host_in: None, or a dict of pinned host tensors
+        (keys among "poses", "pairs", "eps", "mass", "com", shaped like the
+        problem's) copied into the problem's inputs at the start of every
+        step; host_out: None, or a dict of pinned host tensors (keys among
+        "ft", "energy", "gv", "gp", "jac", "count") that receive those
+        results before the synchronisation.  Both copies are part of the
+        step's graph, so a host caller's step is one replay and one
+        synchronisation.  With graph=True the sequence is captured once into a
         CUDA graph (captured again after a list grows or the flags change) and
         replayed, so the inputs must be updated in place (pairs, eps, poses,
         mass, com keep their storage).  Returns tensors owned by the problem,
         overwritten by the next step: (contacts, force_torque, energy,
         dE_dverts, dE_dpose, jac, stats)."""
-        key = (float(scale), bool(want_verts), bool(want_pose), bool(want_jac))
+        io = tuple(sorted((k, t.data_ptr()) for k, t in (host_in or {}).items())) + \
+            tuple(sorted((k, t.data_ptr()) for k, t in (host_out or {}).items()))
+        key = (float(scale), bool(want_verts), bool(want_pose), bool(want_jac), io)
+        run = (scale, want_verts, want_pose, want_jac, host_in, host_out)
         for _ in range(max_retries + 1):
             g = getattr(self, "_graph", None)
             if not graph:
-                self._enqueue(scale, want_verts, want_pose, want_jac)
+                self._enqueue(*run)
             elif g is not None and self._graph_key == key:
                 g.replay()
             else:
                 # an uncaptured run first: it sizes the scratch the graph will use
-                self._enqueue(scale, want_verts, want_pose, want_jac)
+                self._enqueue(*run)
                 if not self._check_and_grow():
                     continue
                 g = torch.cuda.CUDAGraph()
                 side = torch.cuda.Stream()
                 side.wait_stream(torch.cuda.current_stream())
                 with torch.cuda.graph(g, stream=side):
-                    self._enqueue(scale, want_verts, want_pose, want_jac)
+                    self._enqueue(*run)
                 torch.cuda.current_stream().wait_stream(side)
                 self._graph, self._graph_key = g, key
                 g.replay()
-            if host_out:
-                ft, energy, gv, gp, jac, _ = self._outputs(want_verts, want_pose, want_jac)
-                src = dict(ft=ft, energy=energy, gv=gv, gp=gp, jac=jac, count=self.contacts.count)
-                for k, t in host_out.items():
-                    t.copy_(src[k], non_blocking=True)
             if self._check_and_grow():
                 ft, energy, gv, gp, jac, stats = self._outputs(want_verts, want_pose, want_jac)
                 return self.contacts, ft, energy, gv, gp, jac, stats

@@ -102,3 +102,25 @@ def test_step_copies_results_to_pinned_host_buffers(graph):
         assert np.array_equal(host["ft"].numpy(), ft.cpu().numpy())
         assert np.array_equal(host["gp"].numpy(), gp.cpu().numpy())
         assert host["energy"].item() == e.item() and host["count"].item() == c.count.item() > 0
+
+
+def test_step_copies_host_inputs_in_its_graph():
+    """step(host_in=...) copies the inputs from pinned host tensors at every
+    step, replayed graph included: new poses written into the host tensor
+    are what the next step detects at."""
+    import torch
+    s = scene_tiny(n_pairs=12, levels=(1, 2))
+    prob = _problem(s)
+    ref = _problem(s)
+    h_in = {"poses": torch.as_tensor(s.poses, dtype=torch.float64).pin_memory(),
+            "eps": torch.as_tensor(s.eps, dtype=torch.float64).pin_memory()}
+    for shift in (0.0, 0.25, -0.125):
+        moved = s.poses.copy()
+        moved[:, :3] += shift
+        h_in["poses"].copy_(torch.as_tensor(moved))
+        got = prob.step(want_jac=True, graph=True, host_in=h_in)
+        ref.poses.copy_(torch.as_tensor(moved, device="cuda:0"))
+        _same(tuple([got[0].to_numpy()] + [x.cpu().numpy() if hasattr(x, "cpu") else x
+                                          for x in (got[1], float(got[2].item()), got[3],
+                                                    got[4], got[5])]),
+              _separate(ref))
