@@ -310,20 +310,23 @@ __device__ __forceinline__ bool world_triangle(const HierDev& H, const double* p
 // per entry.  The block is symmetric, so the lanes form its upper triangle
 // (78 entries) and write each off-diagonal sum to both places.
 constexpr int kHessWarps = 2;
-// The block is symmetric: its 78 entries (i <= j) as (i << 4) | j.
-__constant__ unsigned char kHessUpper[78] = {
-    0x00, 0x01, 0x02, 0x03, 0x04, 0x05, 0x06, 0x07, 0x08, 0x09, 0x0a, 0x0b,
-    0x11, 0x12, 0x13, 0x14, 0x15, 0x16, 0x17, 0x18, 0x19, 0x1a, 0x1b,
-    0x22, 0x23, 0x24, 0x25, 0x26, 0x27, 0x28, 0x29, 0x2a, 0x2b,
-    0x33, 0x34, 0x35, 0x36, 0x37, 0x38, 0x39, 0x3a, 0x3b,
-    0x44, 0x45, 0x46, 0x47, 0x48, 0x49, 0x4a, 0x4b,
-    0x55, 0x56, 0x57, 0x58, 0x59, 0x5a, 0x5b,
-    0x66, 0x67, 0x68, 0x69, 0x6a, 0x6b,
-    0x77, 0x78, 0x79, 0x7a, 0x7b,
-    0x88, 0x89, 0x8a, 0x8b,
-    0x99, 0x9a, 0x9b,
-    0xaa, 0xab,
-    0xbb};
+// The reduced block H9 is symmetric: its 45 entries (p <= q) as (p << 4) | q,
+// row by row (entry e of row p at p*9 - p(p-1)/2 + q - p).
+__constant__ unsigned char kHessUpper9[45] = {
+    0x00, 0x01, 0x02, 0x03, 0x04, 0x05, 0x06, 0x07, 0x08,
+    0x11, 0x12, 0x13, 0x14, 0x15, 0x16, 0x17, 0x18,
+    0x22, 0x23, 0x24, 0x25, 0x26, 0x27, 0x28,
+    0x33, 0x34, 0x35, 0x36, 0x37, 0x38,
+    0x44, 0x45, 0x46, 0x47, 0x48,
+    0x55, 0x56, 0x57, 0x58,
+    0x66, 0x67, 0x68,
+    0x77, 0x78,
+    0x88};
+__device__ __forceinline__ int hess9_index(int p, int q) {
+  if (p > q) { const int t = p; p = q; q = t; }
+  return p * 9 - (p * (p - 1)) / 2 + (q - p);
+}
+
 __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const int32_t* ab,
                                                              const double* eps,
                                                              const double* poses,
@@ -334,6 +337,7 @@ __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const
   wait_prior_grid();
   __shared__ HessRep rep[kHessWarps][32];
   __shared__ int rpair[kHessWarps][32];
+  __shared__ double sacc[kHessWarps][45];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t n = *c.count;
   if (n > c.capacity) n = c.capacity;
@@ -360,27 +364,35 @@ __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const
     }
     rpair[w][lane] = pr;
     __syncwarp();
-    // a lane's entries of the upper triangle: u = lane, lane + 32, lane + 64
-    int ei[3], ej[3];
+    // a lane's entries of the reduced block's upper triangle: e = lane, lane + 32
+    int ep[2], eq[2];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      const int u = lane + 32 * m;
-      const int c = u < 78 ? kHessUpper[u] : 0;
-      ei[m] = u < 78 ? c >> 4 : -1;
-      ej[m] = c & 15;
+    for (int m = 0; m < 2; ++m) {
+      const int e = lane + 32 * m;
+      const int c = e < 45 ? kHessUpper9[e] : 0;
+      ep[m] = e < 45 ? c >> 4 : -1;
+      eq[m] = c & 15;
     }
-    double acc[3] = {0.0, 0.0, 0.0};
+    double acc[2] = {0.0, 0.0};
     int cur = -1;
+    // a pair's sums: the 45 reduced entries through shared memory, then the
+    // 144 entries of its block, signed (B's translation rows are minus A's)
     auto flush = [&]() {
       double* o = blocks + 144 * (int64_t)cur;
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        if (ei[m] >= 0) {
-          atomicAdd(o + 12 * ei[m] + ej[m], acc[m]);
-          if (ei[m] != ej[m]) atomicAdd(o + 12 * ej[m] + ei[m], acc[m]);
-        }
+      for (int m = 0; m < 2; ++m) {
+        if (ep[m] >= 0) sacc[w][lane + 32 * m] = acc[m];
         acc[m] = 0.0;
       }
+      __syncwarp();
+      for (int x = lane; x < 144; x += 32) {
+        int p9, q9;
+        double si, sj;
+        hess_map(x / 12, &p9, &si);
+        hess_map(x % 12, &q9, &sj);
+        atomicAdd(o + x, si * sj * sacc[w][hess9_index(p9, q9)]);
+      }
+      __syncwarp();
     };
     for (int ci = 0; ci < 32; ++ci) {
       const int p = rpair[w][ci];  // the same on every lane
@@ -391,8 +403,8 @@ __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const
       if (p < 0) continue;
       const HessRep& h = rep[w][ci];
 #pragma unroll
-      for (int m = 0; m < 3; ++m)
-        if (ei[m] >= 0) acc[m] += hessian_entry(h, ei[m], ej[m]);
+      for (int m = 0; m < 2; ++m)
+        if (ep[m] >= 0) acc[m] += hessian_entry9(h, ep[m], eq[m]);
     }
     if (cur >= 0) flush();
     __syncwarp();

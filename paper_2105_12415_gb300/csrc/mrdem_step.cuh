@@ -405,20 +405,31 @@ struct HessRep {
   double K[3];         // (G G^T)^-1: K00, K01, K11
   double a, b;         // e'' - e'/d and e'/d
   double g[3];         // e' u
-  double zu[12];       // Z u
-  double N[2][12];     // N_q (zero beyond nq)
+  double zu[9];        // Z u in the reduced rows (see hess_map)
+  double N[2][9];      // N_q in the reduced rows (zero beyond nq)
   int nq;              // free parameters (0..2)
   int own[2];          // particle of each (0: A, 1: B)
 };
 
-// Row z_i of Z = [I; [rho_A]x; -I; [rho_B]x] (12 x 3).
-MRDEM_HD void hess_zrow(const HessRep& h, int i, double z[3]) {
+// The twelve pose rows (A's translation, A's rotation, B's translation, B's
+// rotation) and the nine reduced rows (translation, A's rotation, B's
+// rotation): B's translation row c is minus A's translation row c in every
+// term of the block (Z, Z u, N_q), and the rotation correction sits in the
+// rotation blocks only, so block(i, j) = s_i s_j H9(m_i, m_j).
+MRDEM_HD void hess_map(int i, int* m, double* s) {
   const int blk = i / 3, c = i % 3;
-  if (blk == 0 || blk == 2) {
-    const double one = blk == 0 ? 1.0 : -1.0;
-    z[0] = c == 0 ? one : 0.0;
-    z[1] = c == 1 ? one : 0.0;
-    z[2] = c == 2 ? one : 0.0;
+  *m = (blk == 2 ? 0 : (blk == 3 ? 2 : blk)) * 3 + c;
+  *s = blk == 2 ? -1.0 : 1.0;
+}
+
+// Reduced row z_p of Z: e_c for the translation, the rows of the
+// cross-product matrices [rho_A]x and [rho_B]x for the rotations.
+MRDEM_HD void hess_zrow9(const HessRep& h, int p, double z[3]) {
+  const int blk = p / 3, c = p % 3;
+  if (blk == 0) {
+    z[0] = c == 0 ? 1.0 : 0.0;
+    z[1] = c == 1 ? 1.0 : 0.0;
+    z[2] = c == 2 ? 1.0 : 0.0;
     return;
   }
   const double* q = blk == 1 ? h.rA : h.rB;
@@ -428,45 +439,55 @@ MRDEM_HD void hess_zrow(const HessRep& h, int i, double z[3]) {
   else { z[0] = -q[1]; z[1] = q[0]; z[2] = 0.0; }
 }
 
-// Entry i of N_k = Z G_k + (G_k x r in the rotation rows of its particle).
-MRDEM_HD double hess_n(const HessRep& h, int k, int i, const double z[3]) {
+// Reduced entry p of N_k = Z G_k + (G_k x r in the rotation rows of its
+// particle).
+MRDEM_HD double hess_n9(const HessRep& h, int k, int p, const double z[3]) {
   const double* G = h.G[k];
   double v = z[0] * G[0] + z[1] * G[1] + z[2] * G[2];
-  const int o = h.own[k] ? 9 : 3;
-  if (i >= o && i < o + 3) {
-    const int m = i - o;
+  const int o = h.own[k] ? 6 : 3;
+  if (p >= o && p < o + 3) {
+    const int m = p - o;
     v += m == 0 ? G[1] * h.r[2] - G[2] * h.r[1]
                 : (m == 1 ? G[2] * h.r[0] - G[0] * h.r[2] : G[0] * h.r[1] - G[1] * h.r[0]);
   }
   return v;
 }
 
-// Entry (i, j) of the block:
-//   a (Zu)_i (Zu)_j + b (Z Z^T)_ij - b sum_kl N_k,i K_kl N_l,j
+// Entry (p, q) of the reduced block H9:
+//   a (Zu)_p (Zu)_q + b (Z Z^T)_pq - b sum_kl N_k,p K_kl N_l,q
 //   + in the rotation blocks sym(g rho^T) - (g . rho) I.
-MRDEM_HD double hessian_entry(const HessRep& h, int i, int j) {
-  double zi[3], zj[3];
-  hess_zrow(h, i, zi);
-  hess_zrow(h, j, zj);
-  double v = h.a * h.zu[i] * h.zu[j] + h.b * (zi[0] * zj[0] + zi[1] * zj[1] + zi[2] * zj[2]);
+MRDEM_HD double hessian_entry9(const HessRep& h, int p, int q) {
+  double zp[3], zq[3];
+  hess_zrow9(h, p, zp);
+  hess_zrow9(h, q, zq);
+  double v = h.a * h.zu[p] * h.zu[q] + h.b * (zp[0] * zq[0] + zp[1] * zq[1] + zp[2] * zq[2]);
   if (h.nq > 0) {
-    const double ni0 = h.N[0][i], nj0 = h.N[0][j];
+    const double np0 = h.N[0][p], nq0 = h.N[0][q];
     if (h.nq == 1) {
-      v -= h.b * ni0 * h.K[0] * nj0;
+      v -= h.b * np0 * h.K[0] * nq0;
     } else {
-      const double ni1 = h.N[1][i], nj1 = h.N[1][j];
-      v -= h.b * (ni0 * h.K[0] * nj0 + ni0 * h.K[1] * nj1 + ni1 * h.K[1] * nj0 +
-                  ni1 * h.K[2] * nj1);
+      const double np1 = h.N[1][p], nq1 = h.N[1][q];
+      v -= h.b * (np0 * h.K[0] * nq0 + np0 * h.K[1] * nq1 + np1 * h.K[1] * nq0 +
+                  np1 * h.K[2] * nq1);
     }
   }
-  const int bi = i / 3, bj = j / 3;
-  if (bi == bj && (bi == 1 || bi == 3)) {
-    const double* rho = bi == 1 ? h.rA : h.rB;
-    const int ii = i % 3, jj = j % 3;
+  const int bp = p / 3, bq = q / 3;
+  if (bp == bq && bp > 0) {
+    const double* rho = bp == 1 ? h.rA : h.rB;
+    const int ii = p % 3, jj = q % 3;
     v += 0.5 * (h.g[ii] * rho[jj] + h.g[jj] * rho[ii]);
     if (ii == jj) v -= h.g[0] * rho[0] + h.g[1] * rho[1] + h.g[2] * rho[2];
   }
   return v;
+}
+
+// Entry (i, j) of the 12x12 block, from the reduced one.
+MRDEM_HD double hessian_entry(const HessRep& h, int i, int j) {
+  int p, q;
+  double si, sj;
+  hess_map(i, &p, &si);
+  hess_map(j, &q, &sj);
+  return si * sj * hessian_entry9(h, p, q);
 }
 
 // The compact block of the contact between world triangles TA (on A) and TB
@@ -546,13 +567,13 @@ MRDEM_HD int contact_hessian_rep(const V3<double> TA[3], const V3<double> TB[3],
   h.b = e1 / d;
   h.g[0] = e1 * u.x; h.g[1] = e1 * u.y; h.g[2] = e1 * u.z;
   h.nq = nq;
-  // Z u and N_q, entry by entry (each entry's row of Z)
-  for (int i = 0; i < 12; ++i) {
+  // Z u and N_q in the reduced rows, entry by entry (each entry's row of Z)
+  for (int p = 0; p < 9; ++p) {
     double z[3];
-    hess_zrow(h, i, z);
-    h.zu[i] = z[0] * h.u[0] + z[1] * h.u[1] + z[2] * h.u[2];
-    h.N[0][i] = nq > 0 ? hess_n(h, 0, i, z) : 0.0;
-    h.N[1][i] = nq > 1 ? hess_n(h, 1, i, z) : 0.0;
+    hess_zrow9(h, p, z);
+    h.zu[p] = z[0] * h.u[0] + z[1] * h.u[1] + z[2] * h.u[2];
+    h.N[0][p] = nq > 0 ? hess_n9(h, 0, p, z) : 0.0;
+    h.N[1][p] = nq > 1 ? hess_n9(h, 1, p, z) : 0.0;
   }
   return 0;
 }
