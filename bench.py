@@ -572,6 +572,23 @@ def run_packing(args):
     torch.cuda.synchronize()
     m._lib.check(lib.mrdem_check(ctx.handle, None, None), "Newton iterations")
     newton_ms = a.elapsed_time(b) / Kn
+    # the same iteration captured once into a CUDA graph and replayed
+    gN = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(gN, stream=side):
+        newton_iter()
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(args.warmup):
+        gN.replay()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(Kn):
+        gN.replay()
+    b.record()
+    torch.cuda.synchronize()
+    m._lib.check(lib.mrdem_check(ctx.handle, None, None), "Newton iterations (graph)")
+    newton_graph_ms = a.elapsed_time(b) / Kn
     cg_it = float(info[0].item())
     # where a Newton iteration's time goes (CUDA events around each call)
     ctx.profile(True)
@@ -598,7 +615,8 @@ def run_packing(args):
                    "ms_per_iteration_kept_candidates": round(cached_ms, 4),
                    "kept_candidates": cand.n(), "margin_w": w},
         "multires": multires,
-        "newton": {"ms_per_iteration": round(newton_ms, 4), "ms_parts": newton_parts,
+        "newton": {"ms_per_iteration": round(newton_ms, 4),
+                   "ms_per_iteration_graph": round(newton_graph_ms, 4), "ms_parts": newton_parts,
                    "cg_iterations_last": cg_it,
                    "iterations_to_1e-6": it_n, "wall_s": round(newton_s, 3),
                    "line_search_halvings": [st["halvings"] for st in nst]},

@@ -919,11 +919,20 @@ int launch_newton_solve(mrdem_ctx* c, int32_t n, int64_t n_pairs, const int32_t*
   const int64_t need = (work + kThreads - 1) / kThreads;
   const int64_t cap = (int64_t)occ * c->n_sms;
   const int grid = (int)(need < 1 ? 1 : (need < cap ? need : cap));
-  double tol2 = rel_tol * rel_tol;
-  int64_t np = n_pairs;
-  void* args[] = {&v, (void*)&rhs, &np, (void*)&ab, (void*)&blocks, &max_iter, &tol2, &info};
-  if (cudaLaunchCooperativeKernel((const void*)k_cg_coop, dim3(grid), dim3(kThreads), args, 0, s) !=
-      cudaSuccess) {
+  const double tol2 = rel_tol * rel_tol;
+  // a cooperative launch through the launch attribute (also valid as a node
+  // of a captured CUDA graph)
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeCooperative;
+  attr.val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = s;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_cg_coop, v, rhs, n_pairs, ab, blocks, (int)max_iter, tol2,
+                         info) != cudaSuccess) {
     cudaGetLastError();
     return MRDEM_ERR_CUDA;
   }
