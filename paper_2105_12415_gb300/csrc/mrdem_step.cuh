@@ -490,6 +490,45 @@ MRDEM_HD double hessian_entry(const HessRep& h, int i, int j) {
   return si * sj * hessian_entry9(h, p, q);
 }
 
+// Closest points of two world triangles for the contact Hessian, screened
+// as the exact pass screens its candidates: the fifteen sub-tests in float
+// on coordinates relative to A's first vertex with their error bound, then
+// FP64 only for the sub-tests that may hold the minimum (the first smallest
+// in the fixed sub-test order wins, as in tri_tri_distance); crossing or
+// nearly touching triangles take the full FP64 test, and pairs certainly
+// beyond tau come back with d > tau.
+MRDEM_HD TriTriResult<double> tri_tri_screened(const V3<double> TA[3], const V3<double> TB[3],
+                                               double tau) {
+  const V3<double> o = TA[0];
+  CandGeom g;
+  V3<float> Pf[3], Qf[3];
+  for (int k = 0; k < 3; ++k) {
+    g.P[k] = TA[k] - o;
+    g.Q[k] = TB[k] - o;
+    Pf[k] = {(float)g.P[k].x, (float)g.P[k].y, (float)g.P[k].z};
+    Qf[k] = {(float)g.Q[k].x, (float)g.Q[k].y, (float)g.Q[k].z};
+  }
+  g.o = o;
+  g.tau = tau;
+  unsigned mask = 0;
+  const int st = cand_float_stage(Pf, Qf, tau, 0.f, &mask);
+  if (st < 0) return tri_tri_distance<double>(TA, TB);
+  TriTriResult<double> r;
+  r.feature = -1;
+  r.near_parallel = false;
+  for (int k = 0; k < 3; ++k) r.wa[k] = r.wb[k] = 0.0;
+  if (st == 0) {
+    r.d = 2.0 * tau + 1.0;
+    r.pa = r.pb = o;
+    return r;
+  }
+  V3<double> pa = o, pb = o;
+  r.d = cand_double_stage(g, mask, pa, pb, r.wa, r.wb);
+  r.pa = pa + o;
+  r.pb = pb + o;
+  return r;
+}
+
 // The compact block of the contact between world triangles TA (on A) and TB
 // (on B).  Returns 0 when the contact has a block, 1 when the triangles are
 // more than 2 eps apart or cross (d = 0: not differentiable), 2 when the
@@ -499,7 +538,7 @@ MRDEM_HD int contact_hessian_rep(const V3<double> TA[3], const V3<double> TB[3],
                                  const V3<double>& tA, const V3<double>& tB, double ks,
                                  double eps, HessRep* out) {
   typedef V3<double> D;
-  const TriTriResult<double> t = tri_tri_distance<double>(TA, TB);
+  const TriTriResult<double> t = tri_tri_screened(TA, TB, 2.0 * eps);
   if (!(t.d > 0.0) || t.d > 2.0 * eps) return 1;
   // active vertices of the two features (no array indexed by a variable, so
   // that everything stays in registers)
