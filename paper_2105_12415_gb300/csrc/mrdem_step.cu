@@ -302,13 +302,13 @@ __device__ __forceinline__ bool world_triangle(const HierDev& H, const double* p
 }
 
 // Contact Hessian blocks: a warp takes 32 contacts; each lane finds its
-// contact's closest points in FP64 and stores the block in compact form
-// (HessRep, mrdem_step.cuh) in shared memory; then the warp forms the blocks
-// entry by entry (a lane per entry, 144 = 4.5 x 32), summing runs of
+// contact's closest points (screened in float, FP64 where it decides) and
+// stores the block in compact form (HessRep, mrdem_step.cuh) in shared
+// memory; then each half-warp forms the reduced 9x9 block (45 entries of
+// the upper triangle, three per lane) of its 16 contacts, summing runs of
 // contacts of the same pair (detection lists a pair's contacts together) in
-// registers and adding each run's sums to the pair's block with one atomic
-// per entry.  The block is symmetric, so the lanes form its upper triangle
-// (78 entries) and write each off-diagonal sum to both places.
+// registers, and adds each run's sums to the pair's 12x12 block, signed,
+// with one atomic per entry.
 constexpr int kHessWarps = 2;
 // The reduced block H9 is symmetric: its 45 entries (p <= q) as (p << 4) | q,
 // row by row (entry e of row p at p*9 - p(p-1)/2 + q - p).
@@ -327,6 +327,46 @@ __device__ __forceinline__ int hess9_index(int p, int q) {
   return p * 9 - (p * (p - 1)) / 2 + (q - p);
 }
 
+// Entry (p, q) of the reduced block (the formula of hessian_entry9) with
+// value selects in place of its branches on the row kind, since the lanes
+// of a warp hold different entries: a divergent FP64 instruction costs the
+// FP64 pipe as much as a full one.
+__device__ __forceinline__ void hess9_zrow_sel(const HessRep& h, int p, double z[3]) {
+  const int blk = p / 3, c = p % 3;
+  const bool a = blk == 1;
+  const double q0 = a ? h.rA[0] : h.rB[0], q1 = a ? h.rA[1] : h.rB[1];
+  const double q2 = a ? h.rA[2] : h.rB[2];
+  const double x0 = c == 0 ? 0.0 : (c == 1 ? q2 : -q1);
+  const double x1 = c == 0 ? -q2 : (c == 1 ? 0.0 : q0);
+  const double x2 = c == 0 ? q1 : (c == 1 ? -q0 : 0.0);
+  const bool t = blk == 0;
+  z[0] = t ? (c == 0 ? 1.0 : 0.0) : x0;
+  z[1] = t ? (c == 1 ? 1.0 : 0.0) : x1;
+  z[2] = t ? (c == 2 ? 1.0 : 0.0) : x2;
+}
+__device__ __forceinline__ double hess9_entry_sel(const HessRep& h, int p, int q) {
+  double zp[3], zq[3];
+  hess9_zrow_sel(h, p, zp);
+  hess9_zrow_sel(h, q, zq);
+  double v = h.a * h.zu[p] * h.zu[q] + h.b * (zp[0] * zq[0] + zp[1] * zq[1] + zp[2] * zq[2]);
+  if (h.nq > 0) {  // the same for every lane of a contact
+    const double np0 = h.N[0][p], nq0 = h.N[0][q];
+    const double np1 = h.N[1][p], nq1 = h.N[1][q];  // zero beyond nq
+    v -= h.b * (np0 * h.K[0] * nq0 + np0 * h.K[1] * nq1 + np1 * h.K[1] * nq0 +
+                np1 * h.K[2] * nq1);
+  }
+  const int bp = p / 3, ii = p % 3, jj = q % 3;
+  const bool rot = bp == q / 3 && bp > 0;
+  const bool a = bp == 1;
+  const double r0 = a ? h.rA[0] : h.rB[0], r1 = a ? h.rA[1] : h.rB[1];
+  const double r2 = a ? h.rA[2] : h.rB[2];
+  const double ri = ii == 0 ? r0 : (ii == 1 ? r1 : r2), rj = jj == 0 ? r0 : (jj == 1 ? r1 : r2);
+  const double gi = h.g[ii], gj = h.g[jj];
+  const double gr = h.g[0] * r0 + h.g[1] * r1 + h.g[2] * r2;
+  const double corr = 0.5 * (gi * rj + gj * ri) - (ii == jj ? gr : 0.0);
+  return rot ? v + corr : v;
+}
+
 __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const int32_t* ab,
                                                              const double* eps,
                                                              const double* poses,
@@ -337,7 +377,7 @@ __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const
   wait_prior_grid();
   __shared__ HessRep rep[kHessWarps][32];
   __shared__ int rpair[kHessWarps][32];
-  __shared__ double sacc[kHessWarps][45];
+  __shared__ double sacc[kHessWarps][2][45];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t n = *c.count;
   if (n > c.capacity) n = c.capacity;
@@ -364,38 +404,43 @@ __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const
     }
     rpair[w][lane] = pr;
     __syncwarp();
-    // a lane's entries of the reduced block's upper triangle: e = lane, lane + 32
-    int ep[2], eq[2];
+    // each half-warp takes 16 of the warp's contacts in order; a lane holds
+    // the reduced entries e = hl, hl + 16, hl + 32 of its half's contacts
+    // (45 entries over 16 lanes: three rounds, 94 % of the lanes busy)
+    const int half = lane >> 4, hl = lane & 15;
+    const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
+    int ep[3], eq[3];
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      const int e = lane + 32 * m;
+    for (int m = 0; m < 3; ++m) {
+      const int e = hl + 16 * m;
       const int c = e < 45 ? kHessUpper9[e] : 0;
       ep[m] = e < 45 ? c >> 4 : -1;
       eq[m] = c & 15;
     }
-    double acc[2] = {0.0, 0.0};
+    double acc[3] = {0.0, 0.0, 0.0};
     int cur = -1;
-    // a pair's sums: the 45 reduced entries through shared memory, then the
-    // 144 entries of its block, signed (B's translation rows are minus A's)
+    // a pair's run: the 45 sums through shared memory, then the 144 entries
+    // of its block, signed (B's translation rows are minus A's)
     auto flush = [&]() {
       double* o = blocks + 144 * (int64_t)cur;
 #pragma unroll
-      for (int m = 0; m < 2; ++m) {
-        if (ep[m] >= 0) sacc[w][lane + 32 * m] = acc[m];
+      for (int m = 0; m < 3; ++m) {
+        if (ep[m] >= 0) sacc[w][half][hl + 16 * m] = acc[m];
         acc[m] = 0.0;
       }
-      __syncwarp();
-      for (int x = lane; x < 144; x += 32) {
+      __syncwarp(hmask);
+      for (int x = hl; x < 144; x += 16) {
         int p9, q9;
         double si, sj;
         hess_map(x / 12, &p9, &si);
         hess_map(x % 12, &q9, &sj);
-        atomicAdd(o + x, si * sj * sacc[w][hess9_index(p9, q9)]);
+        atomicAdd(o + x, si * sj * sacc[w][half][hess9_index(p9, q9)]);
       }
-      __syncwarp();
+      __syncwarp(hmask);
     };
-    for (int ci = 0; ci < 32; ++ci) {
-      const int p = rpair[w][ci];  // the same on every lane
+    for (int kk = 0; kk < 16; ++kk) {
+      const int ci = 16 * half + kk;
+      const int p = rpair[w][ci];  // the same on every lane of the half
       if (p != cur) {
         if (cur >= 0) flush();
         cur = p;
@@ -403,8 +448,8 @@ __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const
       if (p < 0) continue;
       const HessRep& h = rep[w][ci];
 #pragma unroll
-      for (int m = 0; m < 2; ++m)
-        if (ep[m] >= 0) acc[m] += hessian_entry9(h, ep[m], eq[m]);
+      for (int m = 0; m < 3; ++m)
+        if (ep[m] >= 0) acc[m] += hess9_entry_sel(h, ep[m], eq[m]);
     }
     if (cur >= 0) flush();
     __syncwarp();

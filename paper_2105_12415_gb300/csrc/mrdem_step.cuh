@@ -439,20 +439,6 @@ MRDEM_HD void hess_zrow9(const HessRep& h, int p, double z[3]) {
   else { z[0] = -q[1]; z[1] = q[0]; z[2] = 0.0; }
 }
 
-// Reduced entry p of N_k = Z G_k + (G_k x r in the rotation rows of its
-// particle).
-MRDEM_HD double hess_n9(const HessRep& h, int k, int p, const double z[3]) {
-  const double* G = h.G[k];
-  double v = z[0] * G[0] + z[1] * G[1] + z[2] * G[2];
-  const int o = h.own[k] ? 6 : 3;
-  if (p >= o && p < o + 3) {
-    const int m = p - o;
-    v += m == 0 ? G[1] * h.r[2] - G[2] * h.r[1]
-                : (m == 1 ? G[2] * h.r[0] - G[0] * h.r[2] : G[0] * h.r[1] - G[1] * h.r[0]);
-  }
-  return v;
-}
-
 // Entry (p, q) of the reduced block H9:
 //   a (Zu)_p (Zu)_q + b (Z Z^T)_pq - b sum_kl N_k,p K_kl N_l,q
 //   + in the rotation blocks sym(g rho^T) - (g . rho) I.
@@ -606,13 +592,23 @@ MRDEM_HD int contact_hessian_rep(const V3<double> TA[3], const V3<double> TB[3],
   h.b = e1 / d;
   h.g[0] = e1 * u.x; h.g[1] = e1 * u.y; h.g[2] = e1 * u.z;
   h.nq = nq;
-  // Z u and N_q in the reduced rows, entry by entry (each entry's row of Z)
-  for (int p = 0; p < 9; ++p) {
-    double z[3];
-    hess_zrow9(h, p, z);
-    h.zu[p] = z[0] * h.u[0] + z[1] * h.u[1] + z[2] * h.u[2];
-    h.N[0][p] = nq > 0 ? hess_n9(h, 0, p, z) : 0.0;
-    h.N[1][p] = nq > 1 ? hess_n9(h, 1, p, z) : 0.0;
+  // Z u and N_q in the reduced rows, in closed form: Z x = (x, rho_A x x,
+  // rho_B x x), and N_k = Z G_k plus G_k x r in the rotation rows of the
+  // particle that owns parameter k
+  const D zA = cross(rA, u), zB = cross(rB, u);
+  h.zu[0] = u.x; h.zu[1] = u.y; h.zu[2] = u.z;
+  h.zu[3] = zA.x; h.zu[4] = zA.y; h.zu[5] = zA.z;
+  h.zu[6] = zB.x; h.zu[7] = zB.y; h.zu[8] = zB.z;
+  for (int k = 0; k < 2; ++k) {
+    const bool on = k < nq;
+    const D gk = on ? G[k] : D{0.0, 0.0, 0.0};
+    const D gr = cross(gk, r);
+    const D nA = cross(rA, gk) + (own[k] == 0 ? gr : D{0.0, 0.0, 0.0});
+    const D nB = cross(rB, gk) + (own[k] == 1 ? gr : D{0.0, 0.0, 0.0});
+    double* N = h.N[k];
+    N[0] = gk.x; N[1] = gk.y; N[2] = gk.z;
+    N[3] = nA.x; N[4] = nA.y; N[5] = nA.z;
+    N[6] = nB.x; N[7] = nB.y; N[8] = nB.z;
   }
   return 0;
 }
