@@ -328,31 +328,135 @@ def scene_particle_on_plane(levels=(3, 3, 4, 5), gaps=(-0.5, 0.3, 1.5, 2.5), eps
     return _assemble(meshes, poses, radii, pairs, eps_l, "particle-on-plane")
 
 
+class _OverlapEnergy:
+    """Soft-sphere overlap energy of spheres (centres c, radii R) in the cube
+    [0, side]^3: E = 1/2 sum over overlapping pairs (R_i + R_j - |c_i - c_j|)^2
+    plus 1/2 sum over wall penetrations (R_i - c_ik)^2 and (c_ik + R_i - side)^2,
+    with its gradient.  Candidate pairs come from a neighbour list within
+    R_i + R_j + skin, rebuilt when a centre has moved by half the skin.  Once
+    every overlap is at most `slack` times its pair's radius sum (and every
+    wall penetration `slack` times the radius) the energy reports zero with
+    a zero gradient, which ends the minimisation there."""
+
+    def __init__(self, R, side, skin, slack=0.0):
+        self.R, self.side, self.skin, self.slack, self.ref = R, side, skin, slack, None
+
+    def _neighbours(self, c):
+        from scipy.spatial import cKDTree
+        p = cKDTree(c).query_pairs(2.0 * self.R.max() + self.skin, output_type="ndarray")
+        d = np.linalg.norm(c[p[:, 1]] - c[p[:, 0]], axis=1)
+        p = p[d < self.R[p[:, 0]] + self.R[p[:, 1]] + self.skin]
+        self.i0, self.i1 = p[:, 0], p[:, 1]
+        self.S = self.R[self.i0] + self.R[self.i1]
+        self.ref = c.copy()
+
+    def __call__(self, x):
+        c = x.reshape(-1, 3)
+        n = len(c)
+        if self.ref is None or np.abs(c - self.ref).max() > 0.5 * self.skin:
+            self._neighbours(c)
+        v = c[self.i1] - c[self.i0]
+        d = np.sqrt((v * v).sum(1))
+        ov = self.S - d
+        lo = np.maximum(self.R[:, None] - c, 0.0)
+        hi = np.maximum(c + self.R[:, None] - self.side, 0.0)
+        lim = self.slack * self.R[:, None]
+        if (ov <= self.slack * self.S).all() and (lo <= lim).all() and (hi <= lim).all():
+            return 0.0, np.zeros(x.shape)
+        m = ov > 0
+        e = 0.5 * float((ov[m] ** 2).sum())
+        f = (ov[m] / np.maximum(d[m], 1e-300))[:, None] * v[m]
+        g = np.empty_like(c)
+        for k in range(3):
+            g[:, k] = (np.bincount(self.i0[m], f[:, k], n)
+                       - np.bincount(self.i1[m], f[:, k], n))
+        e += 0.5 * float((lo ** 2).sum() + (hi ** 2).sum())
+        g += hi - lo
+        return e, g.ravel()
+
+
+def _spheres_disjoint(c, R, side):
+    """True when no two spheres overlap and every sphere lies in the cube."""
+    from scipy.spatial import cKDTree
+    p = cKDTree(c).query_pairs(2.0 * R.max(), output_type="ndarray")
+    d = np.linalg.norm(c[p[:, 1]] - c[p[:, 0]], axis=1)
+    return bool((d >= R[p[:, 0]] + R[p[:, 1]]).all() and (c >= R[:, None]).all()
+                and (c <= side - R[:, None]).all())
+
+
+def _compress_packing(R, vol, fraction, rng, start=0.3, step=0.1, margin=1e-3):
+    """Dense random packing of spheres of radii R (nominal volume `vol`) by
+    compression with soft-sphere energy minimisation, the jamming protocol of
+    O'Hern, Silbert, Liu and Nagel (Phys. Rev. E 68, 011306, 2003): uniform
+    random centres in a cube sized for the volume fraction `start`, the
+    overlap energy of the spheres inflated by (1 + margin) minimised
+    (L-BFGS) until no inflated overlap exceeds half the margin; then the cube
+    shrinks (centres mapped affinely) to the next fraction, `step` higher,
+    up to `fraction`, minimising again each time.  Below the jamming fraction
+    the minimum is zero and the true spheres end disjoint; the first stage
+    that leaves them overlapping stops the compression.  Returns (centres,
+    side) of the last disjoint stage."""
+    from scipy.optimize import minimize
+    fr = [f for f in np.arange(start, fraction - 1e-9, step)] + [fraction]
+    sides = [(vol / f) ** (1.0 / 3.0) for f in fr]
+    side = sides[0]
+    c = rng.uniform(R[:, None], side - R[:, None], size=(len(R), 3))
+    good = None
+    for s_new in sides:
+        span_old = np.maximum(side - 2.0 * R[:, None], 1e-12)
+        c = R[:, None] + (c - R[:, None]) * (s_new - 2.0 * R[:, None]) / span_old
+        side = s_new
+        energy = _OverlapEnergy(R * (1.0 + margin), side, 0.3 * float(R.min()),
+                                0.5 * margin / (1.0 + margin))
+        res = minimize(energy, c.ravel(), jac=True, method="L-BFGS-B",
+                       options=dict(maxiter=20000, maxfun=40000, ftol=0.0, gtol=1e-12,
+                                    maxcor=20))
+        c = res.x.reshape(-1, 3).copy()
+        if not _spheres_disjoint(c, R, side):
+            break
+        good = (c, side)
+    if good is None:
+        raise ValueError(f"no disjoint packing of {len(R)} spheres at volume fraction {start}")
+    return good
+
+
 def scene_packing(n: int = 64, fraction: float = 0.3, levels=(2, 3, 4), r_min: float = 1.0,
                   r_max: float = 10.0, eps_rel: float = 0.01, overlap: float = 0.3,
-                  seed: int = 10, amp: float = 0.05, tries_per_particle: int = 200):
+                  seed: int = 10, amp: float = 0.05, tries_per_particle: int = 200,
+                  method: str = "rsa"):
     """Many-particle packing (the implicit-step workload): n bumped
     sphere-like particles, subdivision uniform in `levels`, radius log-uniform
-    in [r_min, r_max], placed by random sequential addition, largest first,
-    in a cube sized for the requested volume fraction of the nominal spheres
-    (a particle's bounding radius 1.05 r may not overlap an earlier
-    particle's).  Random sequential addition jams well below dense packings:
-    when a particle finds no place in `tries_per_particle` attempts the cube
-    grows by 1 % and the placement goes on, so every particle is placed and
-    the achieved fraction is returned.  A share `overlap` of the particles is
-    then moved towards its nearest neighbour until their bounding spheres
-    overlap by eps / 2, so that contacts exist.  eps of a pair =
-    eps_rel * min(diameters).  The scene's pair list is empty (pairs come
-    from a broad phase).  Returns (scene, achieved fraction, velocities
-    [n, 6] = (v, omega), zero)."""
+    in [r_min, r_max], in a cube sized for the requested volume fraction of
+    the nominal spheres; a particle's bounding radius 1.05 r (its vertices lie
+    within [0.95 r, 1.05 r]) may not overlap another particle's nor leave the
+    cube.  method "rsa": random sequential addition, largest first; it jams
+    well below dense packings, so when a particle finds no place in
+    `tries_per_particle` attempts the cube grows by 1 % and the placement goes
+    on.  method "compress": compression by soft-sphere energy minimisation
+    (`_compress_packing`), which reaches dense random packings (0.55 of
+    nominal spheres, 0.64 of bounding spheres, for 10 000 particles) and
+    stops at the last disjoint stage below a jam.  Either way the achieved
+    fraction is returned.  A share `overlap` of the particles is then moved
+    towards its nearest neighbour until their bounding spheres overlap by
+    eps / 2, so that contacts exist.  eps of a pair = eps_rel *
+    min(diameters).  The scene's pair list is empty (pairs come from a broad
+    phase).  Returns (scene, achieved fraction, velocities [n, 6] = (v,
+    omega), zero)."""
     from scipy.spatial import cKDTree
     rng = np.random.default_rng([BASE_SEED, seed, 17])
     radius = np.sort(np.exp(rng.uniform(np.log(r_min), np.log(r_max), size=n)))[::-1]
     R = 1.05 * radius
-    side = ((4.0 / 3.0) * np.pi * (radius ** 3).sum() / fraction) ** (1.0 / 3.0)
-    centres = np.zeros((n, 3))
+    vol = (4.0 / 3.0) * np.pi * (radius ** 3).sum()
+    side = (vol / fraction) ** (1.0 / 3.0)
+    if method == "compress":
+        centres, side = _compress_packing(R, vol, fraction, rng)
+        i = n
+    elif method == "rsa":
+        centres = np.zeros((n, 3))
+        i = 0
+    else:
+        raise ValueError(f"unknown packing method {method!r}")
     tree, in_tree = None, 0
-    i = 0
     while i < n:
         ok = False
         for _ in range(tries_per_particle):
@@ -385,7 +489,7 @@ def scene_packing(n: int = 64, fraction: float = 0.3, levels=(2, 3, 4), r_min: f
         shift = d[j] - (R[k] + R[j] - 0.5 * e)
         if shift > 0:
             poses[k, :3] += shift * (poses[j, :3] - poses[k, :3]) / d[j]
-    achieved = (4.0 / 3.0) * np.pi * (radius ** 3).sum() / side ** 3
+    achieved = vol / side ** 3
     s = _assemble(meshes, poses, radius, np.zeros((0, 2), np.int32), np.zeros(0), "packing")
     return s, float(achieved), np.zeros((n, 6))
 

@@ -266,6 +266,29 @@ def test_packing_generator():
     assert frac2 == frac and np.array_equal(s2.poses, s.poses) and np.array_equal(s2.verts, s.verts)
 
 
+def test_packing_generator_compressed():
+    """The compressed packing (soft-sphere energy minimisation) reaches a
+    denser packing than random sequential addition on the same particles,
+    with every bounding sphere (1.05 r, which holds every vertex) disjoint
+    from the others and inside the cube, and the stated fraction equal to the
+    nominal spheres' volume over the cube's."""
+    n = 400
+    s, frac, _ = scene_packing(n, 0.55, seed=31, overlap=0.0, method="compress")
+    _, frac_rsa, _ = scene_packing(n, 0.55, seed=31, overlap=0.0)
+    assert frac >= frac_rsa + 0.1 and frac <= 0.55 + 1e-12, (frac, frac_rsa)
+    r, c = s.radius, s.poses[:, :3]
+    vmax = np.array([np.linalg.norm(s.particle(i)[0].astype(np.float64), axis=1).max()
+                     for i in range(n)])
+    assert (vmax <= 1.05 * r * (1 + 1e-6)).all()
+    side = ((4.0 / 3.0) * np.pi * (r ** 3).sum() / frac) ** (1 / 3)
+    R = 1.05 * r
+    d = np.linalg.norm(c[:, None] - c[None], axis=-1) + np.eye(n) * 1e9
+    assert (d >= R[:, None] + R[None]).all()
+    assert (c >= R[:, None] * (1 - 1e-12)).all() and (c <= side - R[:, None] * (1 - 1e-12)).all()
+    with pytest.raises(ValueError):
+        scene_packing(8, 0.3, method="lattice")
+
+
 def test_disparity_generator():
     from gen import scene_disparity
     s = scene_disparity(3)
