@@ -400,6 +400,13 @@ def run_packing(args):
     tb, tr = t(bound), t(s.radius)
     pairs, eps = m.broad_phase(ctx, poses0, tb, tr)
     P = pairs.shape[0]
+    # launch shapes for this batch's size class (untimed preparation)
+    tuning = None
+    if not args.no_autotune:
+        t_tune = time.perf_counter()
+        tuning = m.autotune(ctx, hier, pairs, eps, poses0, args.precision)
+        tuning["s"] = round(time.perf_counter() - t_tune, 2)
+        tuning["gain"] = tuning["ms_default"] / tuning["ms_tuned"]
     count = torch.zeros(1, dtype=torch.int64, device=dev)
     a, b = ev(), ev()
     reps = 20
@@ -617,7 +624,8 @@ def run_packing(args):
                                f"dt = 1e-4",
                    "volume_fraction": round(achieved, 4),
                    "particles": n, "triangles": int(np.diff(s.tri_off).sum()), "pairs": P,
-                   "contacts": contacts.n(), "precision": args.precision},
+                   "contacts": contacts.n(), "precision": args.precision,
+                   "launch_shapes": tuning},
         "broad_phase_ms": round(bp_ms, 4),
         "picard": {"ms_per_iteration": round(picard_ms, 4), "iterations_to_1e-6": it_p,
                    "wall_s": round(picard_s, 3),

@@ -195,7 +195,34 @@ struct ExpandSmem {
   int off[WARPS][32];
   int4 it[WARPS][32];
   int4 q[WARPS][128];
+  int4 bq[WARPS][64];  // sphere survivors waiting for the box test
 };
+
+// The oriented-box test of the last `take` entries of a warp's box queue
+// (bq, fill level nb, warp-uniform): the two children's fine geometry 2 eps
+// apart (plus the pair's rounding margin) means no fine pair below them can
+// be a contact; the others go to the sweep list.  Warp-collective.
+template <int CAP>
+__device__ __forceinline__ void expand_box_stage(const HierDev& H, const PairXf* __restrict__ xf,
+                                                 int4* bq, int& nb, int take,
+                                                 WarpQueue<int4, CAP>& outq, int4* sweep,
+                                                 unsigned long long* cnt_sweep, int64_t cap_sweep,
+                                                 unsigned long long* req, WarpCount& boxcut) {
+  const int lane = lane_id();
+  const bool have = lane < take;
+  const int4 e = have ? bq[nb - take + lane] : make_int4(0, 0, 0, 0);
+  __syncwarp();
+  nb -= take;
+  bool boxed = false;
+  if (have) {
+    PairXf X;
+    load_pairxf(xf, e.x, X);
+    boxed = boxes_apart_w(load_box(H, e.y), __ldg(H.node_boxw + e.y), move_box(X, load_box(H, e.z)),
+                          __ldg(H.node_boxw + e.z), X.tau + X.margin);
+  }
+  boxcut.add(boxed);
+  outq.push(have && !boxed, e, sweep, cnt_sweep, cap_sweep, req);
+}
 
 template <int WARPS, bool COH>
 __device__ __forceinline__ void expand_level(const HierDev& H, const PairXf* __restrict__ xf,
@@ -210,6 +237,8 @@ __device__ __forceinline__ void expand_level(const HierDev& H, const PairXf* __r
   WarpCount tests, boxcut;
   WarpQueue<int4, 128> outq;
   outq.buf = sm.q[w];
+  int4* bq = sm.bq[w];
+  int nbq = 0;  // box-queue fill level (warp-uniform)
   // items per warp and pass: the smallest power of two that spreads the
   // level over every resident warp, max_items at most (a power of two <= 32)
   const int64_t warps = (int64_t)gridDim.x * WARPS;
@@ -242,7 +271,7 @@ __device__ __forceinline__ void expand_level(const HierDev& H, const PairXf* __r
       const int r = act ? f - sm.off[w][l] : 0;
       const int i = (int)(((float)r + 0.5f) * (1.0f / (float)(nb > 0 ? nb : 1)));
       const int j = r - i * nb;
-      bool keep = false, boxed = false;
+      bool keep = false;
       if (act) {
         PairXf X;
         load_pairxf(xf, o.x, X);
@@ -251,23 +280,22 @@ __device__ __forceinline__ void expand_level(const HierDev& H, const PairXf* __r
         float dx = p.x - cq.x, dy = p.y - cq.y, dz = p.z - cq.z;
         float lim = p.w + q.w + X.tau + X.margin;
         keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
-        // the oriented boxes of the two children's fine geometry, 2 eps
-        // apart (plus the pair's rounding margin): no fine pair below them
-        // can be a contact
-        if (keep) {
-          boxed = boxes_apart_w(load_box(H, o.y + i), __ldg(H.node_boxw + o.y + i),
-                                move_box(X, load_box(H, o.z + j)), __ldg(H.node_boxw + o.z + j),
-                                X.tau + X.margin);
-          keep = !boxed;
-        }
       }
       tests.add(act);
-      boxcut.add(boxed);
-      outq.push(keep, make_int4(o.x, o.y + i, o.z + j, 0), sweep, cnt + CNT_SWEEP + level, cap_sweep,
-                status + ST_REQ_SWEEP);
+      // sphere survivors queue for the box test, which runs on full warps
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) bq[nbq + __popc(m & ((1u << lane) - 1u))] = make_int4(o.x, o.y + i, o.z + j, 0);
+      nbq += __popc(m);
+      __syncwarp();
+      if (nbq >= 32)
+        expand_box_stage(H, xf, bq, nbq, 32, outq, sweep, cnt + CNT_SWEEP + level, cap_sweep,
+                         status + ST_REQ_SWEEP, boxcut);
     }
     __syncwarp();
   }
+  if (nbq > 0)
+    expand_box_stage(H, xf, bq, nbq, nbq, outq, sweep, cnt + CNT_SWEEP + level, cap_sweep,
+                     status + ST_REQ_SWEEP, boxcut);
   outq.flush(sweep, cnt + CNT_SWEEP + level, cap_sweep, status + ST_REQ_SWEEP);
   tests.flush(cnt + CNT_STATS + slot_tests);
   boxcut.flush(cnt + CNT_STATS + MRDEM_STAT_BOX_PRUNED);

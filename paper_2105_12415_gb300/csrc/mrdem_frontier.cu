@@ -8,9 +8,10 @@
 // major; a leaf side stays while the other unfolds, as in Algorithm 5).  One
 // call tests every item at the iteration's poses and writes the next sets:
 //   k_setup      the pairs' transforms (mrdem_detect.cu);
-//   k_as_test    one thread per item: the certified tests of a surrogate
-//                level (node spheres, oriented boxes, the float penalty sweep
-//                with its certificate and the face normals) against
+//   k_as_test    per item, in stages joined by per-warp queues: the
+//                certified tests of a surrogate level (node spheres,
+//                oriented boxes, the float penalty sweep with its
+//                certificate and the face normals) against
 //                delta_a + delta_b + 2 eps.  Apart: bottom.  Otherwise a pair
 //                of leaves goes to the tile list of the finest-level stage,
 //                any other pair is widened (its output count is its number
@@ -40,6 +41,10 @@ namespace {
 constexpr int kAsThreads = 256;
 constexpr int32_t kVeto = 1, kNarrowed = 2;
 enum : int8_t { AS_BOT = 0, AS_LEAF = 1, AS_WIDEN = 2, AS_PARENT = 3, AS_MERGED = 4 };
+// Added by k_as_test to the outcome of an item that may not be narrowed (a
+// vetoed item, or one that is not a valid node pair), so that k_as_narrow
+// reads a group's eligibility from its status bytes alone.
+constexpr int8_t AS_KEEP = 0x10;
 
 using F3 = V3<float>;
 using D3 = V3<double>;
@@ -122,87 +127,171 @@ __device__ __forceinline__ float node_sweep(F3 p0, F3 p1, F3 p2, F3 q0, F3 q1, F
   return sweep_certificate<true, NIT>(p0, p1, p2, q0, q1, q2, sc, tol2, cv, x);
 }
 
-__global__ void __launch_bounds__(kAsThreads) k_as_test(
-    HierDev H, const PairXf* __restrict__ xf, const PairXf64* __restrict__ xf64, SweepConst sc,
-    float conv_c, const double* __restrict__ eps, int64_t n_pairs, mrdem_active_set in,
-    int8_t* st, int32_t* em, TileItem* tiles, unsigned long long* cnt, unsigned long long* status,
-    int64_t cap_tiles, mrdem_contacts sur) {
-  wait_prior_grid();
-  const int64_t n = clamp_count(in);
-  const int4* items = reinterpret_cast<const int4*>(in.item);
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  // every lane of a warp runs the same rounds (the appends are warp-collective)
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += step) {
-    const int64_t k = base + threadIdx.x;
-    const int4 it = k < n ? items[k] : make_int4(-1, -1, -1, 0);
-    int s = AS_BOT, e = 1;
-    int2 ia = make_int2(0, 1), ib = make_int2(0, 1);
-    bool hit = false;
-    double d = 0.0;
-    D3 pw = {0, 0, 0}, qw = {0, 0, 0};
-    if (k < n && item_ok(H, it, n_pairs)) {
-      PairXf X;
-      load_pairxf(xf, it.x, X);
-      const int a = it.y, b = it.z;
-      const float4 sa = __ldg(H.node_sph + a), sb = __ldg(H.node_sph + b);
-      const F3 cb = xf_point(X, {sb.x, sb.y, sb.z});
-      const float dx = sa.x - cb.x, dy = sa.y - cb.y, dz = sa.z - cb.z;
-      const float lim = sa.w + sb.w + X.tau + X.margin;
-      bool apart = !(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim);
-      if (!apart)
-        apart = boxes_apart_w(load_box(H, a), __ldg(H.node_boxw + a), move_box(X, load_box(H, b)),
-                              __ldg(H.node_boxw + b), X.tau + X.margin);
-      if (!apart) {
-        const float4 a0 = __ldg(H.node_geo + 3 * a), a1 = __ldg(H.node_geo + 3 * a + 1);
-        const float4 a2 = __ldg(H.node_geo + 3 * a + 2);
-        const float4 b0 = __ldg(H.node_geo + 3 * b), b1 = __ldg(H.node_geo + 3 * b + 1);
-        const float4 b2 = __ldg(H.node_geo + 3 * b + 2);
-        const F3 p0 = {a0.x, a0.y, a0.z}, p1 = {a1.x, a1.y, a1.z}, p2 = {a2.x, a2.y, a2.z};
-        const F3 q0 = xf_point(X, {b0.x, b0.y, b0.z}), q1 = xf_point(X, {b1.x, b1.y, b1.z});
-        const F3 q2 = xf_point(X, {b2.x, b2.y, b2.z});
-        const float ce = conv_c * (float)__ldg(eps + it.x);
-        bool cv = false;
-        float x[4];
-        float gap = sc.n_iter == 4 ? node_sweep<4>(p0, p1, p2, q0, q1, q2, sc, ce * ce, &cv, x)
-                                   : node_sweep<0>(p0, p1, p2, q0, q1, q2, sc, ce * ce, &cv, x);
-        const float thr = a0.w + b0.w + X.tau + X.margin;
-        if (!(gap > thr))
-          gap = fmaxf(axis_gap(cross(p1 - p0, p2 - p0), p0, p1, p2, q0, q1, q2),
-                      axis_gap(cross(q1 - q0, q2 - q0), p0, p1, p2, q0, q1, q2));
-        apart = gap > thr;
-        if (!apart) {
-          ia = __ldg(H.node_child + a);
-          ib = __ldg(H.node_child + b);
-          if (ia.y < 0 && ib.y < 0) {
-            s = AS_LEAF;
-          } else {
-            s = AS_WIDEN;
-            e = (ia.y > 0 ? ia.y : 1) * (ib.y > 0 ? ib.y : 1);
-            // the iterate's points (A's frame): a surrogate contact when the
-            // sweep converged within the surrogates' threshold
-            const F3 pp = p0 + x[0] * (p1 - p0) + x[1] * (p2 - p0);
-            const F3 qq = q0 + x[2] * (q1 - q0) + x[3] * (q2 - q0);
-            const F3 r = pp - qq;
-            if (cv && sqrtf(dot(r, r)) <= a0.w + b0.w + X.tau) {
-              const PairXf64& X64 = xf64[it.x];
-              pw = xf_point64(X64.RA, X64.tA, D3{(double)pp.x, (double)pp.y, (double)pp.z});
-              qw = xf_point64(X64.RA, X64.tA, D3{(double)qq.x, (double)qq.y, (double)qq.z});
-              const D3 w = pw - qw;
-              d = sqrt(dot(w, w));
-              hit = true;
-            }
-          }
+// k_as_test runs an item's tests in three stages joined by two per-warp
+// queues of item indices in shared memory: the node spheres for every
+// item; the oriented boxes for the sphere survivors, 32 at a time; the
+// float sweep, its certificate, the face normals and the outcome for the box
+// survivors, 32 at a time.  So the two costlier tests run on full warps
+// instead of on the few lanes of a round whose items survived.
+constexpr int kAsQueue = 64;
+struct AsQueues {
+  int64_t box[kAsQueue];
+  int64_t sweep[kAsQueue];
+};
+struct AsTestArgs {
+  HierDev H;
+  const PairXf* xf;
+  const PairXf64* xf64;
+  SweepConst sc;
+  float conv_c;
+  const double* eps;
+  const int4* items;
+  int8_t* st;
+  int32_t* em;
+  TileItem* tiles;
+  unsigned long long* cnt;
+  unsigned long long* status;
+  int64_t cap_tiles;
+  mrdem_contacts sur;
+};
+
+__device__ __forceinline__ void as_bottom(const AsTestArgs& A, int64_t k, bool keep) {
+  A.st[k] = (int8_t)(keep ? AS_BOT | AS_KEEP : AS_BOT);
+  A.em[k] = 1;
+}
+// Queue the lanes with `pred` (warp-collective); n is warp-uniform.
+__device__ __forceinline__ void as_push(int64_t* q, int& n, bool pred, int64_t k) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (pred) q[n + __popc(m & ((1u << lane_id()) - 1u))] = k;
+  n += __popc(m);
+  __syncwarp();
+}
+
+// The sweep stage on the last `take` entries of the sweep queue.
+__device__ __forceinline__ void as_sweep_stage(const AsTestArgs& A, AsQueues& Q, int& nq,
+                                               int take) {
+  const int lane = lane_id();
+  const bool have = lane < take;
+  const int64_t k = have ? Q.sweep[nq - take + lane] : -1;
+  __syncwarp();
+  nq -= take;
+  const HierDev& H = A.H;
+  int s = AS_BOT, e = 1;
+  int2 ia = make_int2(0, 1), ib = make_int2(0, 1);
+  int4 it = make_int4(-1, -1, -1, 0);
+  bool hit = false;
+  double d = 0.0;
+  D3 pw = {0, 0, 0}, qw = {0, 0, 0};
+  if (have) {
+    it = A.items[k];
+    PairXf X;
+    load_pairxf(A.xf, it.x, X);
+    const int a = it.y, b = it.z;
+    const float4 a0 = __ldg(H.node_geo + 3 * a), a1 = __ldg(H.node_geo + 3 * a + 1);
+    const float4 a2 = __ldg(H.node_geo + 3 * a + 2);
+    const float4 b0 = __ldg(H.node_geo + 3 * b), b1 = __ldg(H.node_geo + 3 * b + 1);
+    const float4 b2 = __ldg(H.node_geo + 3 * b + 2);
+    const F3 p0 = {a0.x, a0.y, a0.z}, p1 = {a1.x, a1.y, a1.z}, p2 = {a2.x, a2.y, a2.z};
+    const F3 q0 = xf_point(X, {b0.x, b0.y, b0.z}), q1 = xf_point(X, {b1.x, b1.y, b1.z});
+    const F3 q2 = xf_point(X, {b2.x, b2.y, b2.z});
+    const float ce = A.conv_c * (float)__ldg(A.eps + it.x);
+    bool cv = false;
+    float x[4];
+    float gap = A.sc.n_iter == 4 ? node_sweep<4>(p0, p1, p2, q0, q1, q2, A.sc, ce * ce, &cv, x)
+                                 : node_sweep<0>(p0, p1, p2, q0, q1, q2, A.sc, ce * ce, &cv, x);
+    const float thr = a0.w + b0.w + X.tau + X.margin;
+    if (!(gap > thr))
+      gap = fmaxf(axis_gap(cross(p1 - p0, p2 - p0), p0, p1, p2, q0, q1, q2),
+                  axis_gap(cross(q1 - q0, q2 - q0), p0, p1, p2, q0, q1, q2));
+    if (!(gap > thr)) {
+      ia = __ldg(H.node_child + a);
+      ib = __ldg(H.node_child + b);
+      if (ia.y < 0 && ib.y < 0) {
+        s = AS_LEAF;
+      } else {
+        s = AS_WIDEN;
+        e = (ia.y > 0 ? ia.y : 1) * (ib.y > 0 ? ib.y : 1);
+        // the iterate's points (A's frame): a surrogate contact when the
+        // sweep converged within the surrogates' threshold
+        const F3 pp = p0 + x[0] * (p1 - p0) + x[1] * (p2 - p0);
+        const F3 qq = q0 + x[2] * (q1 - q0) + x[3] * (q2 - q0);
+        const F3 r = pp - qq;
+        if (cv && sqrtf(dot(r, r)) <= a0.w + b0.w + X.tau) {
+          const PairXf64& X64 = A.xf64[it.x];
+          pw = xf_point64(X64.RA, X64.tA, D3{(double)pp.x, (double)pp.y, (double)pp.z});
+          qw = xf_point64(X64.RA, X64.tA, D3{(double)qq.x, (double)qq.y, (double)qq.z});
+          const D3 w = pw - qw;
+          d = sqrt(dot(w, w));
+          hit = true;
         }
       }
     }
-    warp_append(s == AS_LEAF, make_tile(it.x, it.y, it.z, ia, ib), tiles, cnt + CNT_TILES,
-                cap_tiles, status + ST_REQ_TILES);
-    write_surrogate(sur, status, hit, it.x, it.y, it.z, d, pw, qw);
-    if (k < n) {
-      st[k] = (int8_t)s;
-      em[k] = e;
-    }
   }
+  warp_append(s == AS_LEAF, make_tile(it.x, it.y, it.z, ia, ib), A.tiles, A.cnt + CNT_TILES,
+              A.cap_tiles, A.status + ST_REQ_TILES);
+  write_surrogate(A.sur, A.status, hit, it.x, it.y, it.z, d, pw, qw);
+  if (have) {
+    A.st[k] = (int8_t)(s == AS_BOT && (it.w & kVeto) ? AS_BOT | AS_KEEP : s);
+    A.em[k] = e;
+  }
+}
+
+// The box stage on the last `take` entries of the box queue; survivors go
+// to the sweep queue, which is drained in full warps.
+__device__ __forceinline__ void as_box_stage(const AsTestArgs& A, AsQueues& Q, int& nb, int& ns,
+                                             int take) {
+  const int lane = lane_id();
+  const bool have = lane < take;
+  const int64_t k = have ? Q.box[nb - take + lane] : -1;
+  __syncwarp();
+  nb -= take;
+  bool keep = false;
+  if (have) {
+    const int4 it = A.items[k];
+    PairXf X;
+    load_pairxf(A.xf, it.x, X);
+    const int a = it.y, b = it.z;
+    keep = !boxes_apart_w(load_box(A.H, a), __ldg(A.H.node_boxw + a),
+                          move_box(X, load_box(A.H, b)), __ldg(A.H.node_boxw + b),
+                          X.tau + X.margin);
+    if (!keep) as_bottom(A, k, it.w & kVeto);
+  }
+  as_push(Q.sweep, ns, keep, k);
+  if (ns >= 32) as_sweep_stage(A, Q, ns, 32);
+}
+
+__global__ void __launch_bounds__(kAsThreads) k_as_test(const __grid_constant__ AsTestArgs A,
+                                                        int64_t n_pairs, mrdem_active_set in) {
+  wait_prior_grid();
+  __shared__ AsQueues queues[kAsThreads / 32];
+  AsQueues& Q = queues[threadIdx.x >> 5];
+  const HierDev& H = A.H;
+  const int64_t n = clamp_count(in);
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  int nb = 0, ns = 0;  // queue fill levels (warp-uniform)
+  // every lane of a warp runs the same rounds (the stages are warp-collective)
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += step) {
+    const int64_t k = base + threadIdx.x;
+    bool keep = false;
+    if (k < n) {
+      const int4 it = A.items[k];
+      const bool ok = item_ok(H, it, n_pairs);
+      if (ok) {
+        PairXf X;
+        load_pairxf(A.xf, it.x, X);
+        const float4 sa = __ldg(H.node_sph + it.y), sb = __ldg(H.node_sph + it.z);
+        const F3 cb = xf_point(X, {sb.x, sb.y, sb.z});
+        const float dx = sa.x - cb.x, dy = sa.y - cb.y, dz = sa.z - cb.z;
+        const float lim = sa.w + sb.w + X.tau + X.margin;
+        keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
+      }
+      if (!keep) as_bottom(A, k, !ok || (it.w & kVeto));
+    }
+    as_push(Q.box, nb, keep, k);
+    if (nb >= 32) as_box_stage(A, Q, nb, ns, 32);
+  }
+  while (nb > 0) as_box_stage(A, Q, nb, ns, nb < 32 ? nb : 32);
+  while (ns > 0) as_sweep_stage(A, Q, ns, ns < 32 ? ns : 32);
 }
 
 __global__ void __launch_bounds__(kAsThreads) k_as_narrow(HierDev H, int64_t n_pairs,
@@ -216,23 +305,26 @@ __global__ void __launch_bounds__(kAsThreads) k_as_narrow(HierDev H, int64_t n_p
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += step) {
     const int64_t k = base + threadIdx.x;
     bool lead = false;
-    // Only the group's first child (child index 0) decides, and it alone
-    // writes the group's other entries; an entry of another group that a
-    // failing check reads may change meanwhile, but such a check fails on
-    // that entry's parent either way.
+    // Only the group's first child (child index 0) decides.  The sets are in
+    // depth-first order, so when the item size - 1 places further is the
+    // same parent's last child, the items between are its other children
+    // (each child's part of the cut is one item, the child itself): the
+    // group is complete, and it is narrowed when every member is bottom and
+    // may be narrowed (status byte AS_BOT exactly).  The leader alone reads
+    // and writes its members' bytes.
     if (k < n && st[k] == AS_BOT) {
       const int4 it = items[k];
       int pa, pb, size;
-      if (!(it.w & kVeto) && item_ok(H, it, n_pairs) && parent_pair(H, it.y, it.z, pa, pb) &&
+      if (parent_pair(H, it.y, it.z, pa, pb) &&
           child_index(H, it.y, it.z, pa, pb, &size) == 0 && k + size <= n) {
         bool ok = true;
-        for (int j = 1; j < size && ok; ++j) {
-          const int4 o = items[k + j];
+        if (size > 1) {
+          const int4 o = items[k + size - 1];
           int qa, qb, sz;
-          ok = o.x == it.x && st[k + j] == AS_BOT && !(o.w & kVeto) && item_ok(H, o, n_pairs) &&
-               parent_pair(H, o.y, o.z, qa, qb) && qa == pa && qb == pb &&
-               child_index(H, o.y, o.z, pa, pb, &sz) == j;
+          ok = o.x == it.x && item_ok(H, o, n_pairs) && parent_pair(H, o.y, o.z, qa, qb) &&
+               qa == pa && qb == pb && child_index(H, o.y, o.z, pa, pb, &sz) == size - 1;
         }
+        for (int j = 1; j < size && ok; ++j) ok = st[k + j] == AS_BOT;
         if (ok) {
           lead = true;
           for (int j = 1; j < size; ++j) {
@@ -267,7 +359,10 @@ __global__ void __launch_bounds__(kAsThreads) k_as_scan_part(mrdem_active_set in
   int64_t b, e;
   chunk_of(clamp_count(in), b, e);
   int64_t v = 0;
-  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) v += em[i];
+  const int64_t bt = blockDim.x;
+  int64_t i = b + threadIdx.x;
+  for (; i + 3 * bt < e; i += 4 * bt) v += (int64_t)em[i] + em[i + bt] + em[i + 2 * bt] + em[i + 3 * bt];
+  for (; i < e; i += bt) v += em[i];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (lane_id() == 0) wsum[threadIdx.x >> 5] = v;
   __syncthreads();
@@ -302,10 +397,16 @@ __global__ void __launch_bounds__(kAsThreads) k_as_scan_apply(mrdem_active_set i
   chunk_of(clamp_count(in), b, e);
   int64_t carry = bsum[blockIdx.x];
   const int w = threadIdx.x >> 5;
-  for (int64_t base = b; base < e; base += blockDim.x) {
-    const int64_t i = base + threadIdx.x;
-    const int v = i < e ? em[i] : 0;
-    const int incl = warp_scan(v);
+  // four consecutive counts per thread and pass
+  for (int64_t base = b; base < e; base += 4 * (int64_t)blockDim.x) {
+    const int64_t i = base + 4 * (int64_t)threadIdx.x;
+    int v[4], sum = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v[u] = i + u < e ? em[i + u] : 0;
+      sum += v[u];
+    }
+    const int incl = warp_scan(sum);
     if (lane_id() == 31) wtot[w] = incl;
     __syncthreads();
     int before = 0, all = 0;
@@ -313,8 +414,12 @@ __global__ void __launch_bounds__(kAsThreads) k_as_scan_apply(mrdem_active_set i
       before += k < w ? wtot[k] : 0;
       all += wtot[k];
     }
-    const int64_t o = carry + before + incl - v;
-    if (i < e) em[i] = (int32_t)(o < INT32_MAX ? o : INT32_MAX);
+    int64_t o = carry + before + incl - sum;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (i + u < e) em[i + u] = (int32_t)(o < INT32_MAX ? o : INT32_MAX);
+      o += v[u];
+    }
     carry += all;
     __syncthreads();
   }
@@ -480,9 +585,21 @@ int launch_active_step(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs,
     const int blocks = c->n_sms * (2048 / kAsThreads);
     {
       ProfScope ps(c, K_LEVEL, s);
-      launch_after(k_as_test, blocks, kAsThreads, 0, s, H, c->xf, c->xf64,
-                   sweep_const(c->params), c->params.conv_c, eps, n_pairs, *in, c->as_status,
-                   c->as_off, c->tiles, c->counters, c->status, c->cap_tiles, *sur);
+      const AsTestArgs ta = {H,
+                             c->xf,
+                             c->xf64,
+                             sweep_const(c->params),
+                             c->params.conv_c,
+                             eps,
+                             reinterpret_cast<const int4*>(in->item),
+                             c->as_status,
+                             c->as_off,
+                             c->tiles,
+                             c->counters,
+                             c->status,
+                             c->cap_tiles,
+                             *sur};
+      launch_after(k_as_test, blocks, kAsThreads, 0, s, ta, n_pairs, *in);
       launch_after(k_as_narrow, blocks, kAsThreads, 0, s, H, n_pairs, *in, c->as_status,
                    c->as_off, cnt4);
       const int sb = std::min(kScanMaxBlocks, c->n_sms * 4);
