@@ -404,7 +404,7 @@ def run_packing(args):
     tuning = None
     if not args.no_autotune:
         t_tune = time.perf_counter()
-        tuning = m.autotune(ctx, hier, pairs, eps, poses0, args.precision)
+        tuning = m.autotune(ctx, hier, pairs, eps, poses0, args.precision, reps=10)
         tuning["s"] = round(time.perf_counter() - t_tune, 2)
         tuning["gain"] = tuning["ms_default"] / tuning["ms_tuned"]
     count = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -791,7 +791,7 @@ def main():
     elif not args.no_autotune:
         t_tune = time.perf_counter()
         tuning = m.autotune(ctx, hier, prob.pairs, prob.eps, prob.poses, args.precision,
-                            contacts=contacts)
+                            contacts=contacts, reps=10)
         tuning["s"] = round(time.perf_counter() - t_tune, 2)
         tuning["gain"] = tuning["ms_default"] / tuning["ms_tuned"]
 

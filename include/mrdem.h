@@ -114,7 +114,9 @@ typedef struct mrdem_params {
   int32_t node_threads;   /* k_sweep_nodes: threads per block (128, 256) */
   int32_t level_kernel;   /* surrogate levels: 0 = two launches per level (k_expand,
                              k_sweep_nodes); 1 = one cooperative launch over all levels,
-                             grid-wide barriers between the phases */
+                             grid-wide barriers between the phases; 2 = one launch per
+                             level (k_level: the expand phase's survivors swept by the
+                             same warp; level_warps and expand_items set its shape) */
 } mrdem_params;
 
 /* Contact output.  All arrays are caller-owned device memory of `capacity`
@@ -279,8 +281,9 @@ int mrdem_detect(mrdem_ctx* ctx, const mrdem_hier* hier, int64_t n_pairs, const 
  * < 65536, larger) the fastest value of each shape parameter: k_expand warps
  * per block and items per warp, k_sweep_nodes threads, k_tile warps,
  * k_sweep_fine warps, exact-pass threads; then the chosen shape once more
- * with the surrogate levels in one cooperative launch (level_kernel 1),
- * kept when its detection is faster.  Later mrdem_detect and
+ * with the surrogate levels in one cooperative launch (level_kernel 1) and
+ * three times with one launch per level (level_kernel 2, at 2, 4 and 8
+ * warps per block), the fastest of these kept.  Later mrdem_detect and
  * mrdem_detect_noalloc calls of that size class use them; mrdem_set_params
  * clears the table.  Synchronises the device (do not call during stream
  * capture).  The results of every shape are the same contact set; *out holds
@@ -659,8 +662,9 @@ int mrdem_triangle_distance(mrdem_ctx* ctx, int64_t n, const double* P, const do
  * this call in the paper; it is a deployment variant of mrdem_detect.
  *
  * Arguments: as mrdem_detect, without a context: hier must have been
- * uploaded (its context supplies the device and the sweep constants); stats
- * is required (device int64 [MRDEM_STAT_COUNT]).
+ * uploaded (its context supplies the device, the sweep constants and the
+ * launch shapes; the surrogate levels always take two launches each, as
+ * level_kernel 0); stats is required (device int64 [MRDEM_STAT_COUNT]).
  * Limits: n_pairs <= 1024 (larger: MRDEM_ERR_INVALID, nothing enqueued); per
  * call at most 65536 node-pair items per level, 65536 leaf-pair tiles, 131072
  * pairs waiting for a sweep and 65536 fine candidates.  Work beyond a limit

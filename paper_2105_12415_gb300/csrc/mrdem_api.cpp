@@ -34,7 +34,7 @@ bool params_ok(const mrdem_params& p) {
          one_of(p.tile_warps, {2, 4, 8}) && one_of(p.sweep_warps, {2, 4, 8}) &&
          one_of(p.level_warps, {2, 4, 8}) && one_of(p.exact_threads, {64, 128, 256}) &&
          one_of(p.expand_items, {8, 16, 32}) && one_of(p.node_threads, {128, 256}) &&
-         one_of(p.level_kernel, {0, 1});
+         one_of(p.level_kernel, {0, 1, 2});
 }
 
 void free_lists(mrdem_ctx* c) {

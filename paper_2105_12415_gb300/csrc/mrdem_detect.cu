@@ -198,47 +198,42 @@ struct ExpandSmem {
   int4 bq[WARPS][64];  // sphere survivors waiting for the box test
 };
 
-// The oriented-box test of the last `take` entries of a warp's box queue
-// (bq, fill level nb, warp-uniform): the two children's fine geometry 2 eps
-// apart (plus the pair's rounding margin) means no fine pair below them can
-// be a contact; the others go to the sweep list.  Warp-collective.
-template <int CAP>
-__device__ __forceinline__ void expand_box_stage(const HierDev& H, const PairXf* __restrict__ xf,
-                                                 int4* bq, int& nb, int take,
-                                                 WarpQueue<int4, CAP>& outq, int4* sweep,
-                                                 unsigned long long* cnt_sweep, int64_t cap_sweep,
-                                                 unsigned long long* req, WarpCount& boxcut) {
-  const int lane = lane_id();
-  const bool have = lane < take;
-  const int4 e = have ? bq[nb - take + lane] : make_int4(0, 0, 0, 0);
-  __syncwarp();
-  nb -= take;
-  bool boxed = false;
-  if (have) {
-    PairXf X;
-    load_pairxf(xf, e.x, X);
-    boxed = boxes_apart_w(load_box(H, e.y), __ldg(H.node_boxw + e.y), move_box(X, load_box(H, e.z)),
-                          __ldg(H.node_boxw + e.z), X.tau + X.margin);
-  }
-  boxcut.add(boxed);
-  outq.push(have && !boxed, e, sweep, cnt_sweep, cap_sweep, req);
-}
-
-template <int WARPS, bool COH>
+// The expand phase of a surrogate level (k_expand, k_levels, k_level): the
+// child pairs of the level items get the node-sphere test; the sphere
+// survivors queue per warp for the oriented-box test, which runs on full
+// warps; the box survivors go to `sink` (warp-collective push(keep, item)).
+// A warp takes up to max_items level items per pass.
+template <int WARPS, bool COH, typename Sink>
 __device__ __forceinline__ void expand_level(const HierDev& H, const PairXf* __restrict__ xf,
-                                             const int4* __restrict__ in, int level, int4* sweep,
-                                             unsigned long long* cnt, unsigned long long* status,
-                                             int64_t cap_level, int64_t cap_sweep, int max_items,
-                                             ExpandSmem<WARPS>& sm) {
+                                             const int4* __restrict__ in, int level,
+                                             unsigned long long* cnt, int64_t cap_level,
+                                             int max_items, int* off, int4* its, int4* bq,
+                                             Sink& sink) {
   const int w = threadIdx.x >> 5, lane = lane_id();
   int64_t n_in = ld_count<COH>(cnt + CNT_LEVEL + level);
   if (n_in > cap_level) n_in = cap_level;
   const int slot_tests = MRDEM_STAT_TESTS + (level + 1 < MRDEM_STAT_LEVELS ? level + 1 : MRDEM_STAT_LEVELS - 1);
   WarpCount tests, boxcut;
-  WarpQueue<int4, 128> outq;
-  outq.buf = sm.q[w];
-  int4* bq = sm.bq[w];
   int nbq = 0;  // box-queue fill level (warp-uniform)
+  // the oriented boxes of the last `take` queued sphere survivors: the two
+  // children's fine geometry 2 eps apart (plus the pair's rounding margin)
+  // means no fine pair below them can be a contact
+  auto box_stage = [&](int take) {
+    const bool have = lane < take;
+    const int4 e = have ? bq[nbq - take + lane] : make_int4(0, 0, 0, 0);
+    __syncwarp();
+    nbq -= take;
+    bool boxed = false;
+    if (have) {
+      PairXf X;
+      load_pairxf(xf, e.x, X);
+      boxed = boxes_apart_w(load_box(H, e.y), __ldg(H.node_boxw + e.y),
+                            move_box(X, load_box(H, e.z)), __ldg(H.node_boxw + e.z),
+                            X.tau + X.margin);
+    }
+    boxcut.add(boxed);
+    sink.push(have && !boxed, e);
+  };
   // items per warp and pass: the smallest power of two that spreads the
   // level over every resident warp, max_items at most (a power of two <= 32)
   const int64_t warps = (int64_t)gridDim.x * WARPS;
@@ -255,8 +250,8 @@ __device__ __forceinline__ void expand_level(const HierDev& H, const PairXf* __r
     const int c = valid ? (it.w & 0xff) * ((it.w >> 8) & 0xff) : 0;
     const int incl = warp_scan(c);
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    sm.off[w][lane] = incl - c;
-    sm.it[w][lane] = it;
+    off[lane] = incl - c;
+    its[lane] = it;
     __syncwarp();
     for (int f0 = 0; f0 < total; f0 += 32) {
       const int f = f0 + lane;
@@ -265,10 +260,10 @@ __device__ __forceinline__ void expand_level(const HierDev& H, const PairXf* __r
       // child pairs share the next item's offset and are never picked)
       int l = 0;
       for (int b = C >> 1; b > 0; b >>= 1)
-        if (sm.off[w][l + b] <= f) l += b;
-      const int4 o = sm.it[w][l];
+        if (off[l + b] <= f) l += b;
+      const int4 o = its[l];
       const int nb = (o.w >> 8) & 0xff;
-      const int r = act ? f - sm.off[w][l] : 0;
+      const int r = act ? f - off[l] : 0;
       const int i = (int)(((float)r + 0.5f) * (1.0f / (float)(nb > 0 ? nb : 1)));
       const int j = r - i * nb;
       bool keep = false;
@@ -282,24 +277,30 @@ __device__ __forceinline__ void expand_level(const HierDev& H, const PairXf* __r
         keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim;
       }
       tests.add(act);
-      // sphere survivors queue for the box test, which runs on full warps
       const unsigned m = __ballot_sync(0xffffffffu, keep);
       if (keep) bq[nbq + __popc(m & ((1u << lane) - 1u))] = make_int4(o.x, o.y + i, o.z + j, 0);
       nbq += __popc(m);
       __syncwarp();
-      if (nbq >= 32)
-        expand_box_stage(H, xf, bq, nbq, 32, outq, sweep, cnt + CNT_SWEEP + level, cap_sweep,
-                         status + ST_REQ_SWEEP, boxcut);
+      if (nbq >= 32) box_stage(32);
     }
     __syncwarp();
   }
-  if (nbq > 0)
-    expand_box_stage(H, xf, bq, nbq, nbq, outq, sweep, cnt + CNT_SWEEP + level, cap_sweep,
-                     status + ST_REQ_SWEEP, boxcut);
-  outq.flush(sweep, cnt + CNT_SWEEP + level, cap_sweep, status + ST_REQ_SWEEP);
+  if (nbq > 0) box_stage(nbq);
+  sink.finish();
   tests.flush(cnt + CNT_STATS + slot_tests);
   boxcut.flush(cnt + CNT_STATS + MRDEM_STAT_BOX_PRUNED);
 }
+
+// Box survivors to the sweep list of the level (k_expand, k_levels).
+struct SweepListSink {
+  WarpQueue<int4, 128> q;
+  int4* sweep;
+  unsigned long long* counter;
+  int64_t cap;
+  unsigned long long* req;
+  __device__ __forceinline__ void push(bool keep, int4 e) { q.push(keep, e, sweep, counter, cap, req); }
+  __device__ __forceinline__ void finish() { q.flush(sweep, counter, cap, req); }
+};
 
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* __restrict__ xf,
@@ -310,8 +311,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_expand(HierDev H, const PairXf* 
                                                        int max_items) {
   wait_prior_grid();
   __shared__ ExpandSmem<WARPS> sm;
-  expand_level<WARPS, false>(H, xf, in, level, sweep, cnt, status, cap_level, cap_sweep,
-                             max_items, sm);
+  const int w = threadIdx.x >> 5;
+  SweepListSink sink = {{sm.q[w]}, sweep, cnt + CNT_SWEEP + level, cap_sweep, status + ST_REQ_SWEEP};
+  expand_level<WARPS, false>(H, xf, in, level, cnt, cap_level, max_items, sm.off[w], sm.it[w],
+                             sm.bq[w], sink);
 }
 
 // k_sweep_nodes ---------------------------------------------------------------
@@ -319,6 +322,37 @@ struct SweepNodesSmem {
   TileItem tq[8][64];
   int4 lq[8][64];
 };
+
+// The surrogate-level test of one node pair e (pair, node of A, node of B)
+// that passed the culls: the float penalty sweep with its certificate
+// against delta_a + delta_b + 2 eps, then the surrogates' face normals as
+// further separating axes.  True when the pair may hold a contact; ia, ib
+// get the two nodes' child records.
+__device__ __forceinline__ bool node_pair_survives(const HierDev& H, const PairXf* __restrict__ xf,
+                                                   const SweepConst& sc, int4 e, int2& ia,
+                                                   int2& ib) {
+  PairXf X;
+  load_pairxf(xf, e.x, X);
+  float4 a0 = __ldg(H.node_geo + 3 * e.y), a1 = __ldg(H.node_geo + 3 * e.y + 1);
+  float4 a2 = __ldg(H.node_geo + 3 * e.y + 2);
+  float4 b0 = __ldg(H.node_geo + 3 * e.z), b1 = __ldg(H.node_geo + 3 * e.z + 1);
+  float4 b2 = __ldg(H.node_geo + 3 * e.z + 2);
+  ia = __ldg(H.node_child + e.y);
+  ib = __ldg(H.node_child + e.z);
+  F3 q0 = xf_point(X, {b0.x, b0.y, b0.z}), q1 = xf_point(X, {b1.x, b1.y, b1.z});
+  F3 q2 = xf_point(X, {b2.x, b2.y, b2.z});
+  bool cv;
+  float gap;
+  F3 p0 = {a0.x, a0.y, a0.z}, p1 = {a1.x, a1.y, a1.z}, p2 = {a2.x, a2.y, a2.z};
+  if (sc.n_iter == 4)
+    gap = sweep_certificate<false, 4>(p0, p1, p2, q0, q1, q2, sc, 0.f, &cv, nullptr);
+  else
+    gap = sweep_certificate<false, 0>(p0, p1, p2, q0, q1, q2, sc, 0.f, &cv, nullptr);
+  const float thr = a0.w + b0.w + X.tau + X.margin;
+  if (!(gap > thr)) gap = fmaxf(axis_gap(cross(p1 - p0, p2 - p0), p0, p1, p2, q0, q1, q2),
+                                axis_gap(cross(q1 - q0, q2 - q0), p0, p1, p2, q0, q1, q2));
+  return !(gap > thr);
+}
 
 template <bool COH>
 __device__ __forceinline__ void sweep_level(const HierDev& H, const PairXf* __restrict__ xf,
@@ -343,30 +377,7 @@ __device__ __forceinline__ void sweep_level(const HierDev& H, const PairXf* __re
     bool act = k < n, s = false;
     int4 e = act ? ld_item<COH>(sweep + k) : make_int4(0, 0, 0, 0);
     int2 ia = make_int2(0, 1), ib = make_int2(0, 1);
-    if (act) {
-      PairXf X;
-      load_pairxf(xf, e.x, X);
-      float4 a0 = __ldg(H.node_geo + 3 * e.y), a1 = __ldg(H.node_geo + 3 * e.y + 1);
-      float4 a2 = __ldg(H.node_geo + 3 * e.y + 2);
-      float4 b0 = __ldg(H.node_geo + 3 * e.z), b1 = __ldg(H.node_geo + 3 * e.z + 1);
-      float4 b2 = __ldg(H.node_geo + 3 * e.z + 2);
-      ia = __ldg(H.node_child + e.y);
-      ib = __ldg(H.node_child + e.z);
-      F3 q0 = xf_point(X, {b0.x, b0.y, b0.z}), q1 = xf_point(X, {b1.x, b1.y, b1.z});
-      F3 q2 = xf_point(X, {b2.x, b2.y, b2.z});
-      bool cv;
-      float gap;
-      F3 p0 = {a0.x, a0.y, a0.z}, p1 = {a1.x, a1.y, a1.z}, p2 = {a2.x, a2.y, a2.z};
-      if (sc.n_iter == 4)
-        gap = sweep_certificate<false, 4>(p0, p1, p2, q0, q1, q2, sc, 0.f, &cv, nullptr);
-      else
-        gap = sweep_certificate<false, 0>(p0, p1, p2, q0, q1, q2, sc, 0.f, &cv, nullptr);
-      const float thr = a0.w + b0.w + X.tau + X.margin;
-      // the surrogates' face normals as further separating axes
-      if (!(gap > thr)) gap = fmaxf(axis_gap(cross(p1 - p0, p2 - p0), p0, p1, p2, q0, q1, q2),
-                                    axis_gap(cross(q1 - q0, q2 - q0), p0, p1, p2, q0, q1, q2));
-      s = !(gap > thr);
-    }
+    if (act) s = node_pair_survives(H, xf, sc, e, ia, ib);
     bool leaves = ia.y < 0 && ib.y < 0;
     nsweep.add(act);
     surv.add(s);
@@ -413,14 +424,96 @@ __global__ void __launch_bounds__(kLevelWarps * 32, 3) k_levels(
   wait_prior_grid();
   __shared__ LevelSmem sm;
   cg::grid_group g = cg::this_grid();
+  const int w = threadIdx.x >> 5;
   for (int l = 0; l < steps; ++l) {
-    expand_level<kLevelWarps, true>(H, xf, (l & 1) ? list1 : list0, l, sweep, cnt, status,
-                                    cap_level, cap_sweep, max_items, sm.e);
+    SweepListSink sink = {{sm.e.q[w]}, sweep, cnt + CNT_SWEEP + l, cap_sweep, status + ST_REQ_SWEEP};
+    expand_level<kLevelWarps, true>(H, xf, (l & 1) ? list1 : list0, l, cnt, cap_level, max_items,
+                                    sm.e.off[w], sm.e.it[w], sm.e.bq[w], sink);
     g.sync();
     sweep_level<true>(H, xf, sc, sweep, l, ((l + 1) & 1) ? list1 : list0, tiles, cnt, status,
                       cap_sweep, cap_level, cap_tiles, sm.s);
     if (l + 1 < steps) g.sync();
   }
+}
+
+// k_level: one surrogate level in one launch (level_kernel 2).  The expand
+// phase's box survivors queue per warp in shared memory and are swept by
+// the same warp 32 at a time (the sweep phase above), so no sweep list goes
+// through memory and a level is one launch instead of two.
+template <int WARPS>
+struct LevelFusedSmem {
+  int off[WARPS][32];
+  int4 it[WARPS][32];
+  int4 bq[WARPS][64];
+  int4 sq[WARPS][64];
+  int4 lq[WARPS][64];
+  TileItem tq[WARPS][64];
+};
+struct SweepHereSink {
+  const HierDev& H;
+  const PairXf* xf;
+  const SweepConst& sc;
+  int4* sq;
+  int ns;  // queue fill level (warp-uniform)
+  WarpQueue<TileItem, 64> tq;
+  WarpQueue<int4, 64> lq;
+  int4* out;
+  TileItem* tiles;
+  unsigned long long* cnt;
+  unsigned long long* status;
+  int level;
+  int64_t cap_level, cap_tiles;
+  WarpCount nsweep, surv;
+  // the sweep phase on the last `take` queued node pairs
+  __device__ __forceinline__ void stage(int take) {
+    const int lane = lane_id();
+    const bool have = lane < take;
+    const int4 e = have ? sq[ns - take + lane] : make_int4(0, 0, 0, 0);
+    __syncwarp();
+    ns -= take;
+    int2 ia = make_int2(0, 1), ib = make_int2(0, 1);
+    const bool s = have && node_pair_survives(H, xf, sc, e, ia, ib);
+    const bool leaves = ia.y < 0 && ib.y < 0;
+    nsweep.add(have);
+    surv.add(s);
+    tq.push(s && leaves, make_tile(e.x, e.y, e.z, ia, ib), tiles, cnt + CNT_TILES, cap_tiles,
+            status + ST_REQ_TILES);
+    lq.push(s && !leaves, make_level(e.x, e.y, e.z, ia, ib), out, cnt + CNT_LEVEL + level + 1,
+            cap_level, status + ST_REQ_LEVEL);
+  }
+  __device__ __forceinline__ void push(bool keep, int4 e) {
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) sq[ns + __popc(m & ((1u << lane_id()) - 1u))] = e;
+    ns += __popc(m);
+    __syncwarp();
+    if (ns >= 32) stage(32);
+  }
+  __device__ __forceinline__ void finish() {
+    if (ns > 0) stage(ns);
+    tq.flush(tiles, cnt + CNT_TILES, cap_tiles, status + ST_REQ_TILES);
+    lq.flush(out, cnt + CNT_LEVEL + level + 1, cap_level, status + ST_REQ_LEVEL);
+    const int slot_surv = MRDEM_STAT_SURVIVORS + (level + 1 < MRDEM_STAT_LEVELS ? level + 1 : MRDEM_STAT_LEVELS - 1);
+    nsweep.flush(cnt + CNT_STATS + MRDEM_STAT_LEVEL_SWEEPS);
+    surv.flush(cnt + CNT_STATS + slot_surv);
+  }
+};
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_level(HierDev H, const PairXf* __restrict__ xf,
+                                                      SweepConst sc, const int4* __restrict__ in,
+                                                      int level, int4* out, TileItem* tiles,
+                                                      unsigned long long* cnt,
+                                                      unsigned long long* status,
+                                                      int64_t cap_level, int64_t cap_tiles,
+                                                      int max_items) {
+  wait_prior_grid();
+  __shared__ LevelFusedSmem<WARPS> sm;
+  const int w = threadIdx.x >> 5;
+  SweepHereSink sink = {H, xf, sc, sm.sq[w], 0, {}, {}, out, tiles, cnt, status, level,
+                        cap_level, cap_tiles, {}, {}};
+  sink.tq.buf = sm.tq[w];
+  sink.lq.buf = sm.lq[w];
+  expand_level<WARPS, false>(H, xf, in, level, cnt, cap_level, max_items, sm.off[w], sm.it[w],
+                             sm.bq[w], sink);
 }
 
 // k_tile ----------------------------------------------------------------------
@@ -1038,6 +1131,24 @@ static void launch_sweep_nodes(mrdem_ctx* c, const Shape& sh, bool pdl, cudaStre
   launch_pdl(pdl, k_sweep_nodes, one_wave(c, k_sweep_nodes, t, 0), t, s, H, xf, sc, sweep, level,
              out, tiles, cnt, status, cap_sweep, cap_level, cap_tiles);
 }
+template <int W>
+static void level_w(mrdem_ctx* c, bool pdl, cudaStream_t s, const HierDev& H, const PairXf* xf,
+                    SweepConst sc, const int4* in, int level, int4* out, TileItem* tiles,
+                    unsigned long long* cnt, unsigned long long* status, int64_t cap_level,
+                    int64_t cap_tiles, int items) {
+  launch_pdl(pdl, k_level<W>, one_wave(c, k_level<W>, W * 32, 0), W * 32, s, H, xf, sc, in, level,
+             out, tiles, cnt, status, cap_level, cap_tiles, items);
+}
+// One surrogate level in one launch (k_level, level_kernel 2), with the
+// k_expand shape's warps per block and items per warp.
+static void launch_level_fused(mrdem_ctx* c, const Shape& sh, bool pdl, cudaStream_t s,
+                               const HierDev& H, const PairXf* xf, SweepConst sc, const int4* in,
+                               int level, int4* out, TileItem* tiles, unsigned long long* cnt,
+                               unsigned long long* status, int64_t cap_level, int64_t cap_tiles) {
+  if (sh.level_warps == 2) level_w<2>(c, pdl, s, H, xf, sc, in, level, out, tiles, cnt, status, cap_level, cap_tiles, sh.expand_items);
+  else if (sh.level_warps == 4) level_w<4>(c, pdl, s, H, xf, sc, in, level, out, tiles, cnt, status, cap_level, cap_tiles, sh.expand_items);
+  else level_w<8>(c, pdl, s, H, xf, sc, in, level, out, tiles, cnt, status, cap_level, cap_tiles, sh.expand_items);
+}
 // All surrogate levels in one cooperative launch (k_levels) on a one-wave
 // grid: every block is resident, as the grid-wide barriers require.
 static int launch_levels_coop(mrdem_ctx* c, cudaStream_t s, const HierDev& H, SweepConst sc,
@@ -1245,6 +1356,13 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
       if (r) return r;
     }
     for (int l = 0; l < steps && sh.level_kernel != 1; ++l) {
+      if (sh.level_kernel == 2) {
+        ProfScope ps(c, K_LEVEL, s);
+        launch_level_fused(c, sh, true, s, H, c->xf, sc, c->level_list[l & 1], l,
+                           c->level_list[(l + 1) & 1], c->tiles, c->counters, c->status,
+                           c->cap_level, c->cap_tiles);
+        continue;
+      }
       {
         ProfScope ps(c, K_LEVEL, s);
         launch_expand(c, sh, true, s, H, c->xf, c->level_list[l & 1], l, c->sweep, c->counters,
@@ -1272,7 +1390,10 @@ int launch_detect(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const i
 // that each value is timed three or more times (the kernels run one after
 // another on lists of the same content whatever the shapes, so each kernel's
 // time depends on its own shape only).  Each shape runs reps + 1 times, the
-// first untimed; kernels are timed by the context's event pairs.
+// first untimed; kernels are timed by the context's event pairs.  The
+// combined shape is then timed as a whole against the same shape with the
+// levels in one cooperative launch and with one launch per level at each
+// block size, and the fastest is kept.
 int autotune(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_t* ab,
              const double* eps, const double* poses, int precision, const mrdem_contacts* out,
              int reps, int32_t* chosen, double* ms) {
@@ -1379,6 +1500,19 @@ int autotune(mrdem_ctx* c, const mrdem_hier* hier, int64_t n_pairs, const int32_
     if (st == MRDEM_OK && t_coop < t_best) {
       best = coop;
       t_best = t_coop;
+    }
+    // and with each level's two phases in one launch (k_level), whose
+    // register use differs from k_expand's: each of its block sizes
+    for (int e = 0; e < 3 && st == MRDEM_OK; ++e) {
+      Shape fused = coop;
+      fused.level_kernel = 2;
+      fused.level_warps = LW[e];
+      double t_fused = 0.0;
+      st = run(fused, nullptr, &t_fused);
+      if (st == MRDEM_OK && t_fused < t_best) {
+        best = fused;
+        t_best = t_fused;
+      }
     }
     if (st == MRDEM_OK) {
       const int k = size_class(n_pairs);

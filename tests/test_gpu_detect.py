@@ -246,7 +246,7 @@ def test_autotune_keeps_results(orc, precision):
     r = m.autotune(ctx, hier, t["pairs"], t["eps"], t["poses"], precision, reps=2)
     allowed = {"level_warps": {2, 4, 8}, "expand_items": {8, 16, 32}, "node_threads": {128, 256},
                "tile_warps": {2, 4, 8}, "sweep_warps": {2, 4, 8}, "exact_threads": {64, 128, 256},
-               "level_kernel": {0, 1}}
+               "level_kernel": {0, 1, 2}}
     for k, v in r["chosen"].items():
         assert v in allowed[k], (k, v)
     assert r["ms_default"] > 0 and r["ms_tuned"] > 0
@@ -259,10 +259,11 @@ def test_autotune_keeps_results(orc, precision):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_cooperative_levels_equal_per_level_launches(c2_oracle_subset, precision):
-    """All surrogate levels in one cooperative launch (level_kernel 1) test
-    the same pairs as the per-level launches: the same contact set (the
-    same distances and points, bit for bit) and the same counters, eagerly
-    and replayed from a CUDA graph."""
+    """All surrogate levels in one cooperative launch (level_kernel 1), and
+    one launch per level with the sweep in the expanding warp (level_kernel
+    2), test the same pairs as the two launches per level: the same contact
+    set (the same distances and points, bit for bit) and the same counters,
+    eagerly and replayed from a CUDA graph."""
     import torch
     import paper_2105_12415_gb300 as m
     s, _, _ = c2_oracle_subset
@@ -270,27 +271,29 @@ def test_cooperative_levels_equal_per_level_launches(c2_oracle_subset, precision
     hier = m.Hierarchy.from_scene(ctx, s)
     t = gpu_scene_tensors(s, torch.device("cuda:0"))
     res = {}
-    for lk in (0, 1):
+    for lk in (0, 1, 2):
         ctx.set_params(level_kernel=lk)
         c, st = m.detect(ctx, hier, t["pairs"], t["eps"], t["poses"], precision)
         res[lk] = (c.to_numpy(), st.cpu().numpy())
-    for k in ("pair", "ta", "tb", "d", "pa", "pb"):
-        assert np.array_equal(res[0][0][k], res[1][0][k]), k
-    assert np.array_equal(res[0][1], res[1][1])
+    for lk in (1, 2):
+        for k in ("pair", "ta", "tb", "d", "pa", "pb"):
+            assert np.array_equal(res[0][0][k], res[lk][0][k]), (lk, k)
+        assert np.array_equal(res[0][1], res[lk][1]), lk
     # captured into a CUDA graph and replayed
-    ctx.set_params(level_kernel=1)
-    c, st = m.detect(ctx, hier, t["pairs"], t["eps"], t["poses"], precision)   # sizes the lists
-    g = torch.cuda.CUDAGraph()
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.graph(g, stream=side):
-        m.detect(ctx, hier, t["pairs"], t["eps"], t["poses"], precision, contacts=c, stats=st,
-                 check=False)
-    torch.cuda.current_stream().wait_stream(side)
-    c.count.zero_()
-    g.replay()
-    torch.cuda.synchronize()
-    assert m.load().mrdem_check(ctx.handle, None, None) == 0
-    got = c.to_numpy()
-    for k in ("pair", "ta", "tb", "d"):
-        assert np.array_equal(got[k], res[0][0][k]), k
+    for lk in (1, 2):
+        ctx.set_params(level_kernel=lk)
+        c, st = m.detect(ctx, hier, t["pairs"], t["eps"], t["poses"], precision)   # sizes the lists
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(g, stream=side):
+            m.detect(ctx, hier, t["pairs"], t["eps"], t["poses"], precision, contacts=c, stats=st,
+                     check=False)
+        torch.cuda.current_stream().wait_stream(side)
+        c.count.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert m.load().mrdem_check(ctx.handle, None, None) == 0
+        got = c.to_numpy()
+        for k in ("pair", "ta", "tb", "d"):
+            assert np.array_equal(got[k], res[0][0][k]), (lk, k)
