@@ -865,13 +865,18 @@ def main():
     value = _whole_job_rate(args.steps, P, world, ms_max)
     st = stats.cpu().numpy()
     n_contacts = int(contacts.count.item())
-    # our kernels per step: k_setup, (k_expand, k_sweep_nodes) per surrogate
-    # level below the roots, k_tile, k_sweep_fine, the exact pass (FP32 form:
-    # k_cp_float, 3 x k_cp_items, k_select_exact; FP64 form: k_exact64), the
-    # ordering by pair (k_sort_scan, k_sort_scatter), then k_frames + k_forces
-    # and k_frames + k_grad
+    # our kernels per step: k_setup, the surrogate levels below the roots
+    # (per level k_expand + k_sweep_nodes, or one k_level; or one k_levels
+    # for all), k_tile, k_sweep_fine, the exact pass (FP32 form: k_cp_float,
+    # 3 x k_cp_items, k_select_exact; FP64 form: k_exact64), the ordering by
+    # pair (k_sort_scan, k_sort_scatter), then k_frames + k_forces and
+    # k_frames + k_grad
     exact_launches = 5 if args.precision == "fp32" else 1
-    launches_per_step = 1 + 2 * max(0, info["max_depth"] - 1) + 2 + exact_launches + 2 + 4
+    levels = max(0, info["max_depth"] - 1)
+    lk = int(tuning["chosen"].get("level_kernel", ctx.params.level_kernel) if tuning
+             else ctx.params.level_kernel)
+    level_launches = {0: 2 * levels, 1: min(levels, 1), 2: levels}[int(lk)]
+    launches_per_step = 1 + level_launches + 2 + exact_launches + 2 + 4
 
     # ---- per-kernel timing (same steps, outside the graph, events per kernel)
     ctx.profile(True)
