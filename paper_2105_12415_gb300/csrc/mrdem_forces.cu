@@ -209,18 +209,24 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(
   }
 }
 
-// Adjoint, one thread per contact.  Per lane in shared memory: the Gauss-
-// Newton vector W = (u, (pa - t_A) x u, (pb - t_B) x u), e''(d) W, and the
-// pose gradient (e' u, (pa - t_A) x e' u, (pb - t_B) x (-e' u)).  The 12-row
-// J = (W0, W1, -W0, -W2) makes J J^T a signed copy of the 9x9 Gram matrix of
-// W, so a pair's block needs 45 sums, one FMA per contact each.
+// Adjoint, one thread per contact, in double-float on the FP32 units (the
+// FP64 rate of this part is 1/64 of its FP32 rate, and this kernel was bound
+// by it): the FP64 inputs are first reduced to the differences the formulas
+// need (closest points minus each other and minus the particles' positions,
+// and the two scalar coefficients) and rounded to double-float once; the
+// direction u, the lever arms, the Gauss-Newton vector W = (u, (pa - t_A) x u,
+// (pb - t_B) x u), e''(d) W, the pose-gradient terms (e' u, (pa - t_A) x e' u,
+// (pb - t_B) x (-e' u)) and the per-pair sums over a warp's contacts then run
+// in double-float (relative error about 2^-44 per operation), and each sum
+// is rounded to double for its atomic.  The 12-row J = (W0, W1, -W0, -W2)
+// makes J J^T a signed copy of the 9x9 Gram matrix of W, so a pair's block
+// needs 45 sums.
 constexpr int kGradThreads = 128;
 struct GradSmem {
-  double w[32][9];
-  double hw[32][9];
-  double g[32][9];
+  dd w[32][9];
+  dd hw[32][9];
+  dd g[32][9];
   double gram[45];
-  double one;
 };
 // Row of the 12 pose unknowns -> (index into W, sign).
 __device__ __forceinline__ int w_index(int r, double& sgn) {
@@ -237,6 +243,29 @@ __device__ __forceinline__ void gram_pair(int e, int& i, int& j) {
   }
   j = i + e;
 }
+// warp_group_sums with double-float sums: term(l) is a double-float, the
+// sum is accumulated in double-float in lane order and handed to emit
+// rounded to double.
+template <typename Val, typename Emit, typename Post>
+__device__ __forceinline__ void warp_group_sums_dd(bool ok, int key, int nq, Val val, Emit emit,
+                                                   Post post) {
+  const int lane = lane_id();
+  unsigned pending = __ballot_sync(0xffffffffu, ok);
+  while (pending) {
+    const int k = __shfl_sync(0xffffffffu, key, __ffs(pending) - 1);
+    const unsigned grp = __ballot_sync(0xffffffffu, ok && key == k);
+    pending &= ~grp;
+    for (int e = lane; e < nq; e += 32) {
+      const auto term = val(e);
+      dd acc(0.f, 0.f);
+      for (unsigned g = grp; g; g &= g - 1) acc = acc + term(__ffs(g) - 1);
+      emit(k, e, to_double(acc));
+    }
+    __syncwarp();
+    post(k);
+    __syncwarp();
+  }
+}
 
 __global__ void __launch_bounds__(kGradThreads) k_grad(
     HierDev H, const int32_t* __restrict__ ab, const double* __restrict__ eps,
@@ -246,8 +275,6 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
   __shared__ GradSmem smem[kGradThreads / 32];
   GradSmem& S = smem[threadIdx.x >> 5];
   const int lane = lane_id();
-  if (lane == 0) S.one = 1.0;
-  __syncwarp();
   int64_t n = *c.count;
   if (n > c.capacity) n = c.capacity;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -269,20 +296,20 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
       D3 pb = {c.point_b[3 * k], c.point_b[3 * k + 1], c.point_b[3 * k + 2]};
       int sa = H.tri_slot[H.tri_off[A] + c.tri_a[k]];
       int sb = H.tri_slot[H.tri_off[B] + c.tri_b[k]];
-      D3 u;
+      V3<dd> u;
       if (d > 0.0) {
-        u = (1.0 / d) * (pa - pb);
+        u = (dd(1.f) / dd(d)) * to_dd(pa - pb);
       } else {
         double RA[9];
         frame_R(fr, A, RA);
-        u = contact_dir(H, d, pa, pb, sa, RA);
+        u = to_dd(contact_dir(H, d, pa, pb, sa, RA));
       }
-      D3 gv = (-ks * (1.0 - d * inv2e) * scale) * u;
-      D3 ra = pa - frame_vec(fr, A, 9), rb = pb - frame_vec(fr, B, 9);
+      const V3<dd> gv = dd(-ks * (1.0 - d * inv2e) * scale) * u;
+      const V3<dd> ra = to_dd(pa - frame_vec(fr, A, 9)), rb = to_dd(pb - frame_vec(fr, B, 9));
       if (dverts) {
         // a float output: body-frame closest points and their weights in
-        // float from the world offsets (differences taken in double); the
-        // gradient of a body-frame vertex is R^T of the world one
+        // float from the world offsets; the gradient of a body-frame vertex
+        // is R^T of the world one
         float RA[9], RB[9];
         frame_Rf(frf, A, RA);
         frame_Rf(frf, B, RB);
@@ -290,9 +317,9 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
         load_tri(H, sa, VA);
         load_tri(H, sb, VB);
         float wa[3], wb[3];
-        barycentric_f(VA, mul_tf(RA, to_f3(ra)), wa);
-        barycentric_f(VB, mul_tf(RB, to_f3(rb)), wb);
-        const F3 g = to_f3(gv);
+        barycentric_f(VA, mul_tf(RA, F3{ra.x.hi, ra.y.hi, ra.z.hi}), wa);
+        barycentric_f(VB, mul_tf(RB, F3{rb.x.hi, rb.y.hi, rb.z.hi}), wb);
+        const F3 g = {gv.x.hi, gv.y.hi, gv.z.hi};
         const F3 gA = mul_tf(RA, g), gB = mul_tf(RB, g);
         for (int v = 0; v < 3; ++v) {
           int64_t ia = 3 * (int64_t)H.vid[v * H.stride + sa], ib = 3 * (int64_t)H.vid[v * H.stride + sb];
@@ -304,33 +331,33 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
           atomicAdd(dverts + ib + 2, -wb[v] * gB.z);
         }
       }
-      D3 c1 = cross(ra, u), c2 = cross(rb, u);
-      D3 t1 = cross(ra, gv), t2 = cross(rb, -1.0 * gv);
-      const double W[9] = {u.x, u.y, u.z, c1.x, c1.y, c1.z, c2.x, c2.y, c2.z};
-      const double h = ks * inv2e * scale;
+      const V3<dd> c1 = cross(ra, u), c2 = cross(rb, u);
+      const V3<dd> t1 = cross(ra, gv), t2 = cross(gv, rb);  // (pb - t_B) x (-e' u)
+      const dd h(ks * inv2e * scale);
+      const dd W[9] = {u.x, u.y, u.z, c1.x, c1.y, c1.z, c2.x, c2.y, c2.z};
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
         S.w[lane][q] = W[q];
         S.hw[lane][q] = h * W[q];
       }
-      double* g = S.g[lane];
+      dd* g = S.g[lane];
       g[0] = gv.x; g[1] = gv.y; g[2] = gv.z; g[3] = t1.x; g[4] = t1.y; g[5] = t1.z;
       g[6] = t2.x; g[7] = t2.y; g[8] = t2.z;
     }
     if (!dpose && !jac) continue;
     __syncwarp();
     const int q0 = jac ? 0 : 45, q1 = dpose ? 54 : 45;
-    warp_group_sums(
+    warp_group_sums_dd(
         ok, p, q1 - q0,
         [&](int q) {
           q += q0;
-          // Gram sums read (hw_i, w_j) of each lane; pose sums (g_q, 1)
+          // Gram sums read (hw_i, w_j) of each lane; pose sums g_q
           int i, j;
           gram_pair(q < 45 ? q : 0, i, j);
-          const double* x = q < 45 ? &S.hw[0][i] : &S.g[0][q - 45];
-          const double* y = q < 45 ? &S.w[0][j] : &S.one;
-          const int ys = q < 45 ? 9 : 0;
-          return [x, y, ys](int l) { return x[9 * l] * y[ys * l]; };
+          const dd* x = q < 45 ? &S.hw[0][i] : &S.g[0][q - 45];
+          const dd* y = &S.w[0][j];
+          const bool prod = q < 45;
+          return [x, y, prod](int l) { return prod ? x[9 * l] * y[9 * l] : x[9 * l]; };
         },
         [&](int pk, int q, double v) {
           q += q0;
