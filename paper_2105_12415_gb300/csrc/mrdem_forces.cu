@@ -15,12 +15,19 @@
 //   dE/dt = +-e'(d) u, dE/dtheta = (p - t) x (+-e'(d) u),
 //   jac  += e''(d) J J^T, J = [u, (pa - t_A) x u, -u, -(pb - t_B) x u].
 // Per-pair outputs (forces, pose gradients, Jacobian blocks) are summed over
-// the contacts of a pair within a warp first, one atomic per group.
+// the contacts of a pair within a warp first, one atomic per group.  Both
+// kernels reduce their FP64 inputs to the differences the formulas need
+// (closest points minus each other and minus the particles' positions or
+// centres of mass) in FP64, round those to double-float by integer
+// operations (mrdem_split.cuh) and do the rest, the per-pair sums included,
+// in double-float on the FP32 units; the sums are rounded to double for the
+// atomics.  The energy stays in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "mrdem_device.cuh"
+#include "mrdem_split.cuh"
 
 namespace mrdem {
 
@@ -142,6 +149,30 @@ __device__ __forceinline__ void barycentric_f(const F3 V[3], F3 x, float w[3]) {
   w[0] = 1.f - w[1] - w[2];
 }
 
+// warp_group_sums with double-float sums: term(l) is a double-float, the
+// sum is accumulated in double-float in lane order and handed to emit
+// rounded to double.
+template <typename Val, typename Emit, typename Post>
+__device__ __forceinline__ void warp_group_sums_dd(bool ok, int key, int nq, Val val, Emit emit,
+                                                   Post post) {
+  const int lane = lane_id();
+  unsigned pending = __ballot_sync(0xffffffffu, ok);
+  while (pending) {
+    const int k = __shfl_sync(0xffffffffu, key, __ffs(pending) - 1);
+    const unsigned grp = __ballot_sync(0xffffffffu, ok && key == k);
+    pending &= ~grp;
+    for (int e = lane; e < nq; e += 32) {
+      const auto term = val(e);
+      dd acc(0.f, 0.f);
+      for (unsigned g = grp; g; g &= g - 1) acc = acc + term(__ffs(g) - 1);
+      emit(k, e, to_double(acc));
+    }
+    __syncwarp();
+    post(k);
+    __syncwarp();
+  }
+}
+
 constexpr int kForceThreads = 128;
 
 __global__ void __launch_bounds__(kForceThreads) k_forces(
@@ -149,8 +180,8 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(
     const double2* __restrict__ pc, const double* __restrict__ fr, double* ft, double* energy,
     int64_t n_pairs) {
   wait_prior_grid();
-  __shared__ double sF[kForceThreads / 32][32][9];  // F, (x - c_A) x F, (x - c_B) x (-F)
-  double(*F9)[9] = sF[threadIdx.x >> 5];
+  __shared__ dd sF[kForceThreads / 32][32][9];  // F, (x - c_A) x F, (x - c_B) x (-F)
+  dd(*F9)[9] = sF[threadIdx.x >> 5];
   const int lane = lane_id();
   int64_t n = *c.count;
   if (n > c.capacity) n = c.capacity;
@@ -167,27 +198,34 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(
       const double ks = kc.x;
       D3 pa = {c.point_a[3 * k], c.point_a[3 * k + 1], c.point_a[3 * k + 2]};
       D3 pb = {c.point_b[3 * k], c.point_b[3 * k + 1], c.point_b[3 * k + 2]};
-      D3 u;
+      // double-float from here on (the FP64 inputs reduced to differences
+      // first): u, F and the torques about the centres of mass, with the
+      // lever arms x - c_A = (pa - c_A) - (pa - pb)/2 and
+      // x - c_B = (pb - c_B) + (pa - pb)/2
+      const V3<dd> diff = split_double(pa - pb);
+      V3<dd> u;
       if (d > 0.0) {
-        u = (1.0 / d) * (pa - pb);
+        u = (dd(1.f) / split_double(d)) * diff;
       } else {
         double RA[9];
         frame_R(fr, A, RA);
-        u = contact_dir(H, d, pa, pb, H.tri_slot[H.tri_off[A] + c.tri_a[k]], RA);
+        u = split_double(contact_dir(H, d, pa, pb, H.tri_slot[H.tri_off[A] + c.tri_a[k]], RA));
       }
-      double s = 1.0 - d * kc.y;
-      D3 F = (ks * s) * u;
+      const double s = 1.0 - d * kc.y;
+      const V3<dd> F = split_double(ks * s) * u;
       e_k = ks * e * s * s;
-      D3 xc = 0.5 * (pa + pb);
-      D3 cA = frame_vec(fr, A, 12), cB = frame_vec(fr, B, 12);
-      D3 tA = cross(xc - cA, F), tB = cross(xc - cB, -1.0 * F);
+      const V3<dd> half = {dd(0.5f * diff.x.hi, 0.5f * diff.x.lo), dd(0.5f * diff.y.hi, 0.5f * diff.y.lo),
+                           dd(0.5f * diff.z.hi, 0.5f * diff.z.lo)};
+      const V3<dd> la = split_double(pa - frame_vec(fr, A, 12)) - half;
+      const V3<dd> lb = split_double(pb - frame_vec(fr, B, 12)) + half;
+      const V3<dd> tA = cross(la, F), tB = cross(F, lb);  // (x - c_B) x (-F)
       F9[lane][0] = F.x; F9[lane][1] = F.y; F9[lane][2] = F.z;
       F9[lane][3] = tA.x; F9[lane][4] = tA.y; F9[lane][5] = tA.z;
       F9[lane][6] = tB.x; F9[lane][7] = tB.y; F9[lane][8] = tB.z;
     }
     if (ft) {
       __syncwarp();
-      warp_group_sums(
+      warp_group_sums_dd(
           ok, p, 9, [&](int q) { return [&, q](int l) { return F9[l][q]; }; },
           [&](int pk, int q, double v) {
             int A = ab[2 * pk], B = ab[2 * pk + 1];
@@ -243,30 +281,6 @@ __device__ __forceinline__ void gram_pair(int e, int& i, int& j) {
   }
   j = i + e;
 }
-// warp_group_sums with double-float sums: term(l) is a double-float, the
-// sum is accumulated in double-float in lane order and handed to emit
-// rounded to double.
-template <typename Val, typename Emit, typename Post>
-__device__ __forceinline__ void warp_group_sums_dd(bool ok, int key, int nq, Val val, Emit emit,
-                                                   Post post) {
-  const int lane = lane_id();
-  unsigned pending = __ballot_sync(0xffffffffu, ok);
-  while (pending) {
-    const int k = __shfl_sync(0xffffffffu, key, __ffs(pending) - 1);
-    const unsigned grp = __ballot_sync(0xffffffffu, ok && key == k);
-    pending &= ~grp;
-    for (int e = lane; e < nq; e += 32) {
-      const auto term = val(e);
-      dd acc(0.f, 0.f);
-      for (unsigned g = grp; g; g &= g - 1) acc = acc + term(__ffs(g) - 1);
-      emit(k, e, to_double(acc));
-    }
-    __syncwarp();
-    post(k);
-    __syncwarp();
-  }
-}
-
 __global__ void __launch_bounds__(kGradThreads) k_grad(
     HierDev H, const int32_t* __restrict__ ab, const double* __restrict__ eps,
     const double* __restrict__ fr, const float* __restrict__ frf, const double2* __restrict__ pc,
@@ -298,14 +312,15 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
       int sb = H.tri_slot[H.tri_off[B] + c.tri_b[k]];
       V3<dd> u;
       if (d > 0.0) {
-        u = (dd(1.f) / dd(d)) * to_dd(pa - pb);
+        u = (dd(1.f) / split_double(d)) * split_double(pa - pb);
       } else {
         double RA[9];
         frame_R(fr, A, RA);
-        u = to_dd(contact_dir(H, d, pa, pb, sa, RA));
+        u = split_double(contact_dir(H, d, pa, pb, sa, RA));
       }
-      const V3<dd> gv = dd(-ks * (1.0 - d * inv2e) * scale) * u;
-      const V3<dd> ra = to_dd(pa - frame_vec(fr, A, 9)), rb = to_dd(pb - frame_vec(fr, B, 9));
+      const V3<dd> gv = split_double(-ks * (1.0 - d * inv2e) * scale) * u;
+      const V3<dd> ra = split_double(pa - frame_vec(fr, A, 9));
+      const V3<dd> rb = split_double(pb - frame_vec(fr, B, 9));
       if (dverts) {
         // a float output: body-frame closest points and their weights in
         // float from the world offsets; the gradient of a body-frame vertex
@@ -333,7 +348,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
       }
       const V3<dd> c1 = cross(ra, u), c2 = cross(rb, u);
       const V3<dd> t1 = cross(ra, gv), t2 = cross(gv, rb);  // (pb - t_B) x (-e' u)
-      const dd h(ks * inv2e * scale);
+      const dd h = split_double(ks * inv2e * scale);
       const dd W[9] = {u.x, u.y, u.z, c1.x, c1.y, c1.z, c2.x, c2.y, c2.z};
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
