@@ -21,9 +21,11 @@
 //                 whatever order the atomics grouped the buckets in.
 // The particles' own FP64 arithmetic lives in mrdem_step.cuh.
 #include <cooperative_groups.h>
+#include <cstddef>
 #include <cuda_runtime.h>
 
 #include "mrdem_device.cuh"
+#include "mrdem_split.cuh"
 #include "mrdem_step.cuh"
 
 namespace cg = cooperative_groups;
@@ -327,43 +329,88 @@ __device__ __forceinline__ int hess9_index(int p, int q) {
   return p * 9 - (p * (p - 1)) / 2 + (q - p);
 }
 
+// The compact block in double-float: the same layout as HessRep with a
+// double-float (two floats, 8 bytes) in place of each double, so that the
+// lane that built a contact's HessRep in shared memory converts it field by
+// field in place (integer split of each double, mrdem_split.cuh).  The
+// entries are then formed in double-float on the FP32 units: the FP64 rate
+// of this part is 1/64 of its FP32 rate, and the entry phase was bound by it.
+struct HessRepDD {
+  dd u[3], r[3];
+  dd rA[3], rB[3];
+  dd G[2][3];
+  dd K[3];
+  dd a, b;
+  dd g[3];
+  dd zu[9];
+  dd N[2][9];
+  int nq;
+  int own[2];
+};
+union HessSlot {
+  HessRep d;
+  HessRepDD f;
+};
+static_assert(sizeof(dd) == sizeof(double), "double-float slot size");
+static_assert(offsetof(HessRep, N) == offsetof(HessRepDD, N), "HessRepDD layout");
+static_assert(offsetof(HessRep, nq) == offsetof(HessRepDD, nq), "HessRepDD layout");
+__device__ __forceinline__ void hess_rep_to_dd(HessSlot& s) {
+  // each slot read as a double, then written back as a double-float
+#define MRDEM_SPLIT_FIELD(x) s.f.x = split_double(s.d.x)
+  for (int k = 0; k < 3; ++k) {
+    MRDEM_SPLIT_FIELD(rA[k]);
+    MRDEM_SPLIT_FIELD(rB[k]);
+    MRDEM_SPLIT_FIELD(K[k]);
+    MRDEM_SPLIT_FIELD(g[k]);
+  }
+  MRDEM_SPLIT_FIELD(a);
+  MRDEM_SPLIT_FIELD(b);
+  for (int k = 0; k < 9; ++k) {
+    MRDEM_SPLIT_FIELD(zu[k]);
+    MRDEM_SPLIT_FIELD(N[0][k]);
+    MRDEM_SPLIT_FIELD(N[1][k]);
+  }
+#undef MRDEM_SPLIT_FIELD
+}
+
 // Entry (p, q) of the reduced block (the formula of hessian_entry9) with
 // value selects in place of its branches on the row kind, since the lanes
-// of a warp hold different entries: a divergent FP64 instruction costs the
-// FP64 pipe as much as a full one.
-__device__ __forceinline__ void hess9_zrow_sel(const HessRep& h, int p, double z[3]) {
+// of a warp hold different entries.
+__device__ __forceinline__ void hess9_zrow_sel(const HessRepDD& h, int p, dd z[3]) {
   const int blk = p / 3, c = p % 3;
   const bool a = blk == 1;
-  const double q0 = a ? h.rA[0] : h.rB[0], q1 = a ? h.rA[1] : h.rB[1];
-  const double q2 = a ? h.rA[2] : h.rB[2];
-  const double x0 = c == 0 ? 0.0 : (c == 1 ? q2 : -q1);
-  const double x1 = c == 0 ? -q2 : (c == 1 ? 0.0 : q0);
-  const double x2 = c == 0 ? q1 : (c == 1 ? -q0 : 0.0);
+  const dd q0 = a ? h.rA[0] : h.rB[0], q1 = a ? h.rA[1] : h.rB[1];
+  const dd q2 = a ? h.rA[2] : h.rB[2];
+  const dd zero(0.f, 0.f), one(1.f, 0.f);
+  const dd x0 = c == 0 ? zero : (c == 1 ? q2 : -q1);
+  const dd x1 = c == 0 ? -q2 : (c == 1 ? zero : q0);
+  const dd x2 = c == 0 ? q1 : (c == 1 ? -q0 : zero);
   const bool t = blk == 0;
-  z[0] = t ? (c == 0 ? 1.0 : 0.0) : x0;
-  z[1] = t ? (c == 1 ? 1.0 : 0.0) : x1;
-  z[2] = t ? (c == 2 ? 1.0 : 0.0) : x2;
+  z[0] = t ? (c == 0 ? one : zero) : x0;
+  z[1] = t ? (c == 1 ? one : zero) : x1;
+  z[2] = t ? (c == 2 ? one : zero) : x2;
 }
-__device__ __forceinline__ double hess9_entry_sel(const HessRep& h, int p, int q) {
-  double zp[3], zq[3];
+__device__ __forceinline__ dd hess9_entry_sel(const HessRepDD& h, int p, int q) {
+  dd zp[3], zq[3];
   hess9_zrow_sel(h, p, zp);
   hess9_zrow_sel(h, q, zq);
-  double v = h.a * h.zu[p] * h.zu[q] + h.b * (zp[0] * zq[0] + zp[1] * zq[1] + zp[2] * zq[2]);
+  dd v = h.a * h.zu[p] * h.zu[q] + h.b * (zp[0] * zq[0] + zp[1] * zq[1] + zp[2] * zq[2]);
   if (h.nq > 0) {  // the same for every lane of a contact
-    const double np0 = h.N[0][p], nq0 = h.N[0][q];
-    const double np1 = h.N[1][p], nq1 = h.N[1][q];  // zero beyond nq
-    v -= h.b * (np0 * h.K[0] * nq0 + np0 * h.K[1] * nq1 + np1 * h.K[1] * nq0 +
-                np1 * h.K[2] * nq1);
+    const dd np0 = h.N[0][p], nq0 = h.N[0][q];
+    const dd np1 = h.N[1][p], nq1 = h.N[1][q];  // zero beyond nq
+    v = v - h.b * (np0 * h.K[0] * nq0 + np0 * h.K[1] * nq1 + np1 * h.K[1] * nq0 +
+                   np1 * h.K[2] * nq1);
   }
   const int bp = p / 3, ii = p % 3, jj = q % 3;
   const bool rot = bp == q / 3 && bp > 0;
   const bool a = bp == 1;
-  const double r0 = a ? h.rA[0] : h.rB[0], r1 = a ? h.rA[1] : h.rB[1];
-  const double r2 = a ? h.rA[2] : h.rB[2];
-  const double ri = ii == 0 ? r0 : (ii == 1 ? r1 : r2), rj = jj == 0 ? r0 : (jj == 1 ? r1 : r2);
-  const double gi = h.g[ii], gj = h.g[jj];
-  const double gr = h.g[0] * r0 + h.g[1] * r1 + h.g[2] * r2;
-  const double corr = 0.5 * (gi * rj + gj * ri) - (ii == jj ? gr : 0.0);
+  const dd r0 = a ? h.rA[0] : h.rB[0], r1 = a ? h.rA[1] : h.rB[1];
+  const dd r2 = a ? h.rA[2] : h.rB[2];
+  const dd ri = ii == 0 ? r0 : (ii == 1 ? r1 : r2), rj = jj == 0 ? r0 : (jj == 1 ? r1 : r2);
+  const dd gi = h.g[ii], gj = h.g[jj];
+  const dd gr = h.g[0] * r0 + h.g[1] * r1 + h.g[2] * r2;
+  const dd sym = gi * rj + gj * ri;
+  const dd corr = dd(0.5f * sym.hi, 0.5f * sym.lo) - (ii == jj ? gr : dd(0.f, 0.f));
   return rot ? v + corr : v;
 }
 
@@ -375,7 +422,7 @@ __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const
                                                              double* blocks,
                                                              unsigned long long* skipped) {
   wait_prior_grid();
-  __shared__ HessRep rep[kHessWarps][32];
+  __shared__ HessSlot rep[kHessWarps][32];
   __shared__ int rpair[kHessWarps][32];
   __shared__ double sacc[kHessWarps][2][45];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -396,8 +443,11 @@ __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const
             world_triangle(H, poses, B, c.tri_b[k], TB, &tB)) {
           const double mA = mass[A], mB = mass[B];
           const double ks = k_s * sqrt(mA * mB / (mA + mB));
-          const int st = contact_hessian_rep(TA, TB, tA, tB, ks, eps[p], &rep[w][lane]);
-          if (st == 0) pr = p;
+          const int st = contact_hessian_rep(TA, TB, tA, tB, ks, eps[p], &rep[w][lane].d);
+          if (st == 0) {
+            pr = p;
+            hess_rep_to_dd(rep[w][lane]);
+          }
           else if (st == 2) ++parallel;
         }
       }
@@ -417,7 +467,7 @@ __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const
       ep[m] = e < 45 ? c >> 4 : -1;
       eq[m] = c & 15;
     }
-    double acc[3] = {0.0, 0.0, 0.0};
+    dd acc[3] = {dd(0.f, 0.f), dd(0.f, 0.f), dd(0.f, 0.f)};
     int cur = -1;
     // a pair's run: the 45 sums through shared memory, then the 144 entries
     // of its block, signed (B's translation rows are minus A's)
@@ -425,8 +475,8 @@ __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const
       double* o = blocks + 144 * (int64_t)cur;
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        if (ep[m] >= 0) sacc[w][half][hl + 16 * m] = acc[m];
-        acc[m] = 0.0;
+        if (ep[m] >= 0) sacc[w][half][hl + 16 * m] = to_double(acc[m]);
+        acc[m] = dd(0.f, 0.f);
       }
       __syncwarp(hmask);
       for (int x = hl; x < 144; x += 16) {
@@ -446,10 +496,10 @@ __global__ void __launch_bounds__(kHessWarps * 32, 2) k_hessian(HierDev H, const
         cur = p;
       }
       if (p < 0) continue;
-      const HessRep& h = rep[w][ci];
+      const HessRepDD& h = rep[w][ci].f;
 #pragma unroll
       for (int m = 0; m < 3; ++m)
-        if (ep[m] >= 0) acc[m] += hess9_entry_sel(h, ep[m], eq[m]);
+        if (ep[m] >= 0) acc[m] = acc[m] + hess9_entry_sel(h, ep[m], eq[m]);
     }
     if (cur >= 0) flush();
     __syncwarp();
