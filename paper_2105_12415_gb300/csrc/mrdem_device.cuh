@@ -262,8 +262,8 @@ __device__ __forceinline__ void block_exclusive_scan(int32_t* cnt, int64_t n, in
 // runs on every lane.  Contacts of one particle pair sit mostly next to each
 // other in a contact list, so a warp holds few groups and a per-pair output
 // gets one atomic per group instead of one per contact.  Sums run in lane
-// order.
-template <typename Val, typename Emit, typename Post>
+// order, in the type Acc of the terms (double, or double-float).
+template <typename Acc, typename Val, typename Emit, typename Post>
 __device__ __forceinline__ void warp_group_sums(bool ok, int key, int nq, Val val, Emit emit,
                                                 Post post) {
   const int lane = lane_id();
@@ -274,8 +274,8 @@ __device__ __forceinline__ void warp_group_sums(bool ok, int key, int nq, Val va
     pending &= ~grp;
     for (int e = lane; e < nq; e += 32) {
       const auto term = val(e);
-      double acc = 0.0;
-      for (unsigned g = grp; g; g &= g - 1) acc += term(__ffs(g) - 1);
+      Acc acc(0);
+      for (unsigned g = grp; g; g &= g - 1) acc = acc + term(__ffs(g) - 1);
       emit(k, e, acc);
     }
     __syncwarp();

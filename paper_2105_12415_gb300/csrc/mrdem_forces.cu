@@ -131,7 +131,6 @@ __device__ __forceinline__ F3 mul_tf(const float R[9], F3 v) {
   return {fmaf(R[0], v.x, fmaf(R[3], v.y, R[6] * v.z)), fmaf(R[1], v.x, fmaf(R[4], v.y, R[7] * v.z)),
           fmaf(R[2], v.x, fmaf(R[5], v.y, R[8] * v.z))};
 }
-__device__ __forceinline__ F3 to_f3(D3 v) { return {(float)v.x, (float)v.y, (float)v.z}; }
 // Barycentric weights of a point x of triangle V, in float: least squares in
 // the triangle's plane; a degenerate triangle puts all weight on V0.
 __device__ __forceinline__ void barycentric_f(const F3 V[3], F3 x, float w[3]) {
@@ -147,30 +146,6 @@ __device__ __forceinline__ void barycentric_f(const F3 V[3], F3 x, float w[3]) {
   w[1] = (d22 * r1 - d12 * r2) * inv;
   w[2] = (d11 * r2 - d12 * r1) * inv;
   w[0] = 1.f - w[1] - w[2];
-}
-
-// warp_group_sums with double-float sums: term(l) is a double-float, the
-// sum is accumulated in double-float in lane order and handed to emit
-// rounded to double.
-template <typename Val, typename Emit, typename Post>
-__device__ __forceinline__ void warp_group_sums_dd(bool ok, int key, int nq, Val val, Emit emit,
-                                                   Post post) {
-  const int lane = lane_id();
-  unsigned pending = __ballot_sync(0xffffffffu, ok);
-  while (pending) {
-    const int k = __shfl_sync(0xffffffffu, key, __ffs(pending) - 1);
-    const unsigned grp = __ballot_sync(0xffffffffu, ok && key == k);
-    pending &= ~grp;
-    for (int e = lane; e < nq; e += 32) {
-      const auto term = val(e);
-      dd acc(0.f, 0.f);
-      for (unsigned g = grp; g; g &= g - 1) acc = acc + term(__ffs(g) - 1);
-      emit(k, e, to_double(acc));
-    }
-    __syncwarp();
-    post(k);
-    __syncwarp();
-  }
 }
 
 constexpr int kForceThreads = 128;
@@ -225,9 +200,10 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(
     }
     if (ft) {
       __syncwarp();
-      warp_group_sums_dd(
+      warp_group_sums<dd>(
           ok, p, 9, [&](int q) { return [&, q](int l) { return F9[l][q]; }; },
-          [&](int pk, int q, double v) {
+          [&](int pk, int q, dd sum) {
+            const double v = to_double(sum);
             int A = ab[2 * pk], B = ab[2 * pk + 1];
             if (q < 3) {
               atomicAdd(ft + 6 * (int64_t)A + q, v);
@@ -362,7 +338,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
     if (!dpose && !jac) continue;
     __syncwarp();
     const int q0 = jac ? 0 : 45, q1 = dpose ? 54 : 45;
-    warp_group_sums_dd(
+    warp_group_sums<dd>(
         ok, p, q1 - q0,
         [&](int q) {
           q += q0;
@@ -374,7 +350,8 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(
           const bool prod = q < 45;
           return [x, y, prod](int l) { return prod ? x[9 * l] * y[9 * l] : x[9 * l]; };
         },
-        [&](int pk, int q, double v) {
+        [&](int pk, int q, dd sum) {
+          const double v = to_double(sum);
           q += q0;
           if (q < 45) {
             S.gram[q] = v;
