@@ -124,6 +124,53 @@ def test_unfolded_sets_are_cuts_and_find_every_contact(mr, imp, orc):
     assert len(F) < full
 
 
+def _last_member_rule(T, frontier, seen):
+    """In a cut listed in depth-first order, a first child's sibling group is
+    listed in full (the parent's children side by side, in child order) if
+    and only if the item size - 1 places after it is the same parent's last
+    child: the items between are then the other children themselves.  The
+    GPU's narrowing checks completeness this way; `seen` counts the groups
+    found complete and incomplete."""
+    n = len(frontier)
+
+    def is_child(i, p, par, k):
+        q, a, b, _ = frontier[i]
+        return (q == p and T.parent_pair(a, b) == par
+                and T.child_index(a, b, par)[0] == k)
+
+    for i, (p, a, b, _) in enumerate(frontier):
+        par = T.parent_pair(a, b)
+        if par is None:
+            continue
+        c, size = T.child_index(a, b, par)
+        if c != 0:
+            continue
+        full = i + size <= n and all(is_child(i + k, p, par, k) for k in range(size))
+        last = i + size <= n and is_child(i + size - 1, p, par, size - 1)
+        assert full == last, (i, p, par, size)
+        seen[full] += 1
+
+
+def test_group_completeness_from_its_last_member(mr, imp):
+    """The completeness shortcut holds on every active set the unfolding and
+    the narrowing back to the roots produce, with both outcomes occurring."""
+    s, pairs, eps, ex = _chain(imp)
+    T = mr.Trees(ex)
+    seen = {True: 0, False: 0}
+    F, _, _, _ = _unfold(mr, s, T, s.poses, pairs, eps, mr.initial_frontier(T, pairs),
+                         check=lambda f: _last_member_rule(T, f, seen))
+    far = s.poses.copy()
+    far[:, :3] *= 20.0
+    G = [(p, a, b, 0) for p, a, b, _ in F]
+    for _ in range(10):
+        st, _, _ = mr.frontier_test(s, T, far, pairs, eps, G)
+        G, _, n = mr.frontier_update(T, G, st)
+        _last_member_rule(T, G, seen)
+        if n == 0:
+            break
+    assert seen[True] > 0 and seen[False] > 0, seen
+
+
 def test_separated_pairs_narrow_to_their_roots(mr, imp):
     """Unfold at the contact poses, then move the particles far apart: with
     the flags cleared every group narrows, one level per iteration, back to
