@@ -18,8 +18,9 @@
 //                of children) and, when the sweep converged within that
 //                threshold, is a surrogate contact (the implicit guess);
 //   k_as_narrow  one thread per item: the first child of a group (child
-//                index 0 of its parent pair) checks the items that follow;
-//                when the whole group is listed, bottom and not vetoed, it
+//                index 0 of its parent pair) checks that the group's last
+//                child sits where a complete group ends and that every
+//                member's status byte says bottom and not vetoed; then it
 //                emits the parent and the others nothing (narrowing);
 //   k_as_scan_*  the output offsets, in input order, so the next sets stay
 //                in depth-first order (chunk sums, their scan, chunk rescans);
