@@ -224,8 +224,9 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(
 }
 
 // Adjoint, one thread per contact, in double-float on the FP32 units (the
-// FP64 rate of this part is 1/64 of its FP32 rate, and this kernel was bound
-// by it): the FP64 inputs are first reduced to the differences the formulas
+// FP64 rate of this part is about 1/61 of its FP32 rate, and this kernel
+// was bound by it): the FP64 inputs are first reduced to the differences the
+// formulas
 // need (closest points minus each other and minus the particles' positions,
 // and the two scalar coefficients) and rounded to double-float once; the
 // direction u, the lever arms, the Gauss-Newton vector W = (u, (pa - t_A) x u,

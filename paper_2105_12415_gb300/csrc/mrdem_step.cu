@@ -334,7 +334,8 @@ __device__ __forceinline__ int hess9_index(int p, int q) {
 // lane that built a contact's HessRep in shared memory converts it field by
 // field in place (integer split of each double, mrdem_split.cuh).  The
 // entries are then formed in double-float on the FP32 units: the FP64 rate
-// of this part is 1/64 of its FP32 rate, and the entry phase was bound by it.
+// of this part is about 1/61 of its FP32 rate (measured), and the entry
+// phase was bound by it.
 struct HessRepDD {
   dd u[3], r[3];
   dd rA[3], rB[3];
