@@ -225,17 +225,16 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(
 
 // Adjoint, one thread per contact, in double-float on the FP32 units (the
 // FP64 rate of this part is about 1/61 of its FP32 rate, and this kernel
-// was bound by it): the FP64 inputs are first reduced to the differences the
-// formulas
-// need (closest points minus each other and minus the particles' positions,
-// and the two scalar coefficients) and rounded to double-float once; the
-// direction u, the lever arms, the Gauss-Newton vector W = (u, (pa - t_A) x u,
-// (pb - t_B) x u), e''(d) W, the pose-gradient terms (e' u, (pa - t_A) x e' u,
-// (pb - t_B) x (-e' u)) and the per-pair sums over a warp's contacts then run
-// in double-float (relative error about 2^-44 per operation), and each sum
-// is rounded to double for its atomic.  The 12-row J = (W0, W1, -W0, -W2)
-// makes J J^T a signed copy of the 9x9 Gram matrix of W, so a pair's block
-// needs 45 sums.
+// was bound by it): the FP64 inputs are first reduced to the differences
+// the formulas need (closest points minus each other and minus the
+// particles' positions, and the two scalar coefficients) and rounded to
+// double-float once; the direction u, the lever arms, the Gauss-Newton
+// vector W = (u, (pa - t_A) x u, (pb - t_B) x u), e''(d) W, the
+// pose-gradient terms (e' u, (pa - t_A) x e' u, (pb - t_B) x (-e' u)) and
+// the per-pair sums over a warp's contacts then run in double-float
+// (relative error about 2^-44 per operation), and each sum is rounded to
+// double for its atomic.  The 12-row J = (W0, W1, -W0, -W2) makes J J^T a
+// signed copy of the 9x9 Gram matrix of W, so a pair's block needs 45 sums.
 constexpr int kGradThreads = 128;
 struct GradSmem {
   dd w[32][9];
