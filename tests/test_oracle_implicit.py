@@ -289,6 +289,27 @@ def test_packing_generator_compressed():
         scene_packing(8, 0.3, method="lattice")
 
 
+def test_packing_overlap_energy_gradient():
+    """The compression's soft-sphere energy (gen.icosphere._OverlapEnergy)
+    returns its own gradient: central differences agree on a small
+    overlapping configuration with wall contacts, and the energy reports zero
+    once every overlap is within the slack."""
+    from gen.icosphere import _OverlapEnergy
+    rng = np.random.default_rng(3)
+    R = rng.uniform(0.5, 2.0, size=12)
+    x = rng.uniform(0.0, 6.0, size=(12, 3)).ravel()
+    en = _OverlapEnergy(R, 6.0, 0.5)
+    e0, g = en(x)
+    assert e0 > 0
+    h = 1e-6
+    fd = np.array([(en(x + h * np.eye(len(x))[i])[0] - en(x - h * np.eye(len(x))[i])[0]) / (2 * h)
+                   for i in range(len(x))])
+    assert np.abs(fd - g).max() <= 1e-6 * max(1.0, np.abs(g).max())
+    far = np.array([[10.0 * i + 3.0, 3.0, 3.0] for i in range(3)]).ravel()
+    e1, g1 = _OverlapEnergy(np.full(3, 1.0), 40.0, 0.5, slack=1e-3)(far)
+    assert e1 == 0.0 and not g1.any()
+
+
 def test_disparity_generator():
     from gen import scene_disparity
     s = scene_disparity(3)
